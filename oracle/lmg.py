@@ -1,0 +1,305 @@
+"""Oracle: plain, slow FP64 CPU implementation of the learnable multigrid.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only
+the tests, the package's smoke check and the benchmark's CPU-baseline leg do.
+It shares no code with the CUDA path: it builds its own prolongation, Galerkin
+coarse operators, graphs and coarsest-level factorisation from the inputs
+produced by `workloads`, with scipy sparse products as the only primitives.
+
+Every function follows the paper's definitions in the paper's order:
+
+  graph of A (Sec. 2.1)        E = {(i,j): A_ij != 0, i != j}
+  prolongation (Sec. 2.2)      P_l = natural inclusion of the coarse P1 space
+  restriction (Sec. 2.2)       R_l = P_l^T
+  Galerkin coarsening (Sec. 2.2)  A_{l+1} = R_l A_l P_l
+  SAGEConv, mean (Sec. 3.2)    Phi(x)_i = w1 x_i + w2 mean_{j in N(i)} x_j
+                               (matrix form, Eq. graph-conv-matrix:
+                                Phi = w1 I + w2 D_g^{-1} A_g)
+  learnable smoother (Sec. 3)  delta = theta B (f - A u),  B = D_A^{-1};
+                               u <- u + eta Phi_B(delta)
+  learnable transfers (Sec. 3) r_c = R Phi_R(r);  e = Phi_P(P e_c)
+  learnable V-cycle            Algorithm 2
+  training loss                mean_b ||r_K||^2 / ||r_0||^2 after K cycles
+
+Readings where the paper is silent or ambiguous (kept identical in the CUDA
+path and listed with reasons in the design notes):
+  * the convolution graph is the algebraic graph of each level's operator,
+    after dropping |A_ij| <= 1e-12 max(|A_ii|, |A_jj|) (exact zeros of P1 on
+    right triangles, and round-off from Galerkin products);
+  * deg_i counts the neighbours of i in that graph before the Dirichlet rows
+    and columns are removed, so the mean divides by the full stencil count
+    while the removed boundary values enter as zero;
+  * the convolutions carry no bias, so the cycle is linear in (f, u);
+  * the coarsest level is solved exactly by a dense Cholesky factorisation.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+DROP_TOL = 1e-12
+
+
+# ---------------------------------------------------------------- setup ----
+
+def prolongation_full(parent: np.ndarray, nv_coarse: int) -> sp.csr_matrix:
+    """Natural inclusion of the coarse P1 space in the fine one (Sec. 2.2): a
+    fine vertex on a coarse vertex takes its value, a fine vertex at the
+    midpoint of a coarse edge takes the mean of the edge's two end values."""
+    rows, cols, vals = [], [], []
+    for i, (a, b) in enumerate(parent):
+        if b < 0:
+            rows.append(i); cols.append(a); vals.append(1.0)
+        else:
+            rows += [i, i]; cols += [a, b]; vals += [0.5, 0.5]
+    return sp.csr_matrix((vals, (rows, cols)), shape=(parent.shape[0], nv_coarse))
+
+
+def drop_small(A: sp.csr_matrix) -> sp.csr_matrix:
+    """Remove off-diagonal entries that are zero up to round-off."""
+    C = A.tocoo()
+    d = np.abs(A.diagonal())
+    off = C.row != C.col
+    small = np.abs(C.data) <= DROP_TOL * np.maximum(d[C.row], d[C.col])
+    keep = ~(off & small)
+    return sp.csr_matrix((C.data[keep], (C.row[keep], C.col[keep])), shape=A.shape)
+
+
+@dataclass
+class Level:
+    A: sp.csr_matrix            # operator on interior DOFs
+    diag: np.ndarray            # D_A
+    G: sp.csr_matrix            # 0/1 adjacency of the algebraic graph (interior)
+    inv_deg: np.ndarray         # 1/deg_i, deg over the graph before elimination
+    P: sp.csr_matrix | None     # interior fine x interior coarse
+
+
+@dataclass
+class Hierarchy:
+    levels: list[Level]
+    chol: tuple                 # cho_factor of A_J (dense)
+
+    @property
+    def J(self) -> int:
+        return len(self.levels)
+
+
+def build_hierarchy(problem) -> Hierarchy:
+    """Levels 1..J of Sec. 2.2 from the mesh hierarchy and the finest stiffness
+    matrix over all vertices; Dirichlet rows/columns are removed per level."""
+    mesh = problem.mesh
+    A_full = drop_small(problem.A_full.tocsr())
+    levels = []
+    for lev, ML in enumerate(mesh.levels):
+        I = ML.interior
+        pattern = A_full.copy()
+        pattern.data = np.ones_like(pattern.data)
+        pattern.setdiag(0)
+        pattern.eliminate_zeros()
+        deg = np.asarray(pattern.sum(axis=1)).ravel()[I]
+        A = A_full[I][:, I].tocsr()
+        G = pattern[I][:, I].tocsr()
+        P = None
+        if lev < mesh.J - 1:
+            nvc = mesh.levels[lev + 1].nv
+            P_full = prolongation_full(ML.parent, nvc)
+            Ic = mesh.levels[lev + 1].interior
+            P = P_full[I][:, Ic].tocsr()
+            A_full = drop_small((P_full.T @ A_full @ P_full).tocsr())
+        levels.append(Level(A=A, diag=A.diagonal().copy(), G=G, inv_deg=1.0 / deg, P=P))
+    AJ = levels[-1].A.toarray()
+    return Hierarchy(levels, sla.cho_factor(AJ, lower=True))
+
+
+# ----------------------------------------------------------- parameters ----
+
+@dataclass
+class Params:
+    """Theta = {theta_l, eta_l, Theta_B,l, Theta_R,l, Theta_P,l : l = 1..J-1}
+    (Sec. 3).  With scalar features each SAGEConv holds (w1, w2)."""
+    theta: np.ndarray
+    eta: np.ndarray
+    wB: np.ndarray
+    wR: np.ndarray
+    wP: np.ndarray
+    nu_pre: int = 2
+    nu_post: int = 2
+
+    @staticmethod
+    def identity(J: int, omega: float = 2.0 / 3.0, nu: int = 2) -> "Params":
+        """Initialisation of Sec. 3.4: W1 = I, W2 = 0, theta = omega, eta = 1,
+        which makes the learnable cycle the classical damped-Jacobi V-cycle."""
+        m = J - 1
+        one = np.tile([1.0, 0.0], (m, 1))
+        return Params(np.full(m, omega), np.ones(m), one.copy(), one.copy(), one.copy(), nu, nu)
+
+    def copy(self) -> "Params":
+        return Params(self.theta.copy(), self.eta.copy(), self.wB.copy(), self.wR.copy(),
+                      self.wP.copy(), self.nu_pre, self.nu_post)
+
+    def astype(self, dtype) -> "Params":
+        return Params(self.theta.astype(dtype), self.eta.astype(dtype), self.wB.astype(dtype),
+                      self.wR.astype(dtype), self.wP.astype(dtype), self.nu_pre, self.nu_post)
+
+    # flat view used for gradients: per level [theta, eta, wB1, wB2, wR1, wR2, wP1, wP2]
+    def flat(self) -> np.ndarray:
+        return np.concatenate([self.theta[:, None], self.eta[:, None], self.wB, self.wR,
+                               self.wP], axis=1).ravel()
+
+    @staticmethod
+    def from_flat(x: np.ndarray, nu_pre: int = 2, nu_post: int = 2) -> "Params":
+        x = np.asarray(x).reshape(-1, 8)
+        return Params(x[:, 0].copy(), x[:, 1].copy(), x[:, 2:4].copy(), x[:, 4:6].copy(),
+                      x[:, 6:8].copy(), nu_pre, nu_post)
+
+
+# ---------------------------------------------------------------- cycle ----
+
+def conv(L: Level, x: np.ndarray, w1, w2) -> np.ndarray:
+    """SAGEConv with mean aggregation (Sec. 3.2): w1 x_i + w2 mean_{N(i)} x_j."""
+    return w1 * x + w2 * (L.inv_deg[:, None] * (L.G @ x))
+
+
+def smooth(L: Level, f, u, theta, eta, wB):
+    """One learnable smoothing step (Sec. 3): delta = theta D_A^{-1}(f - A u),
+    u <- u + eta Phi_B(delta)."""
+    delta = theta * (f - L.A @ u) / L.diag[:, None]
+    return u + eta * conv(L, delta, wB[0], wB[1])
+
+
+def lmg(H: Hierarchy, p: Params, lev: int, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Algorithm 2, u = LMG(A_l, f, u, l, Theta); lev is 0-based (paper l-1)."""
+    if lev == H.J - 1:
+        return sla.cho_solve(H.chol, f)
+    L = H.levels[lev]
+    for _ in range(p.nu_pre):
+        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev])
+    r = f - L.A @ u
+    rc = L.P.T @ conv(L, r, p.wR[lev][0], p.wR[lev][1])
+    ec = lmg(H, p, lev + 1, rc, np.zeros_like(rc))
+    e = conv(L, L.P @ ec, p.wP[lev][0], p.wP[lev][1])
+    u = u + e
+    for _ in range(p.nu_post):
+        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev])
+    return u
+
+
+def vcycle(H: Hierarchy, p: Params, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    return lmg(H, p, 0, f, u)
+
+
+def residual(H: Hierarchy, f, u):
+    return f - H.levels[0].A @ u
+
+
+def relres(H: Hierarchy, f, u) -> np.ndarray:
+    """||f - A u||_2 / ||f||_2 per right-hand side (column)."""
+    r = residual(H, f, u)
+    return np.sqrt((r * r).sum(0)) / np.sqrt((f * f).sum(0))
+
+
+@dataclass
+class SolveResult:
+    u: np.ndarray
+    iters: np.ndarray
+    relres: np.ndarray
+    history: list = field(default_factory=list)
+
+
+def solve_vcycles(H: Hierarchy, p: Params, f: np.ndarray, tol: float,
+                  max_iter: int = 200) -> SolveResult:
+    """Stationary iteration u^m = LMG(A, f, u^{m-1}) from u^0 = 0, each column
+    stopping as soon as ||f - A u||/||f|| < tol (checked before each cycle)."""
+    u = np.zeros_like(f)
+    B = f.shape[1]
+    iters = np.zeros(B, dtype=np.int64)
+    active = np.ones(B, dtype=bool)
+    hist = []
+    for _ in range(max_iter + 1):
+        rr = relres(H, f, u)
+        hist.append(rr.copy())
+        active &= rr >= tol
+        if not active.any():
+            break
+        if iters[active].max() >= max_iter:
+            break
+        cols = np.flatnonzero(active)
+        u[:, cols] = vcycle(H, p, f[:, cols], u[:, cols])
+        iters[cols] += 1
+    return SolveResult(u, iters, relres(H, f, u), hist)
+
+
+def solve_refinement(H: Hierarchy, p: Params, f: np.ndarray, tol: float,
+                     max_iter: int = 100) -> SolveResult:
+    """Iterative refinement with the V-cycle as the inner solve: r = f - A u,
+    c = LMG(A, r, 0), u <- u + c, until ||r||/||f|| < tol (per column).  In the
+    oracle every step is FP64; the CUDA path runs the inner cycle in FP32."""
+    u = np.zeros_like(f)
+    B = f.shape[1]
+    iters = np.zeros(B, dtype=np.int64)
+    active = np.ones(B, dtype=bool)
+    hist = []
+    for _ in range(max_iter + 1):
+        r = residual(H, f, u)
+        rr = np.sqrt((r * r).sum(0)) / np.sqrt((f * f).sum(0))
+        hist.append(rr.copy())
+        active &= rr >= tol
+        if not active.any() or iters[active].max() >= max_iter:
+            break
+        cols = np.flatnonzero(active)
+        c = vcycle(H, p, r[:, cols], np.zeros((f.shape[0], cols.size), dtype=f.dtype))
+        u[:, cols] += c
+        iters[cols] += 1
+    return SolveResult(u, iters, relres(H, f, u), hist)
+
+
+# -------------------------------------------------------------- training ----
+
+def unrolled_loss(H: Hierarchy, p: Params, f: np.ndarray, K: int,
+                  u0: np.ndarray | None = None) -> np.ndarray:
+    """Loss of K unrolled cycles: mean over columns of ||r_K||^2 / ||r_0||^2,
+    with r_k = f - A u_k, u_{k+1} = LMG(A, f, u_k).  Written with x*x instead
+    of |x|^2 so that it stays analytic (complex-step differentiable)."""
+    u = np.zeros_like(f) if u0 is None else u0
+    r0 = residual(H, f, u)
+    n0 = (r0 * r0).sum(0)
+    for _ in range(K):
+        u = vcycle(H, p, f, u)
+    r = residual(H, f, u)
+    return ((r * r).sum(0) / n0).mean()
+
+
+def loss_gradient_complex_step(H: Hierarchy, p: Params, f: np.ndarray, K: int,
+                               u0: np.ndarray | None = None, h: float = 1e-30):
+    """d loss / d Theta by complex-step differentiation: for each flat
+    parameter x_k, Im L(x + i h e_k) / h.  The loss is a polynomial in Theta,
+    so this is exact to rounding, independent of any hand-written adjoint."""
+    x = p.flat()
+    g = np.zeros_like(x)
+    fc = f.astype(np.complex128)
+    u0c = None if u0 is None else u0.astype(np.complex128)
+    for k in range(x.size):
+        xc = x.astype(np.complex128)
+        xc[k] += 1j * h
+        pc = Params.from_flat(xc, p.nu_pre, p.nu_post)
+        g[k] = np.imag(unrolled_loss(H, pc, fc, K, u0c)) / h
+    return unrolled_loss(H, p, f, K, u0), g
+
+
+def loss_gradient_fd(H: Hierarchy, p: Params, f: np.ndarray, K: int,
+                     u0: np.ndarray | None = None, h: float = 1e-6):
+    """Central finite differences of the same loss (second-order accurate)."""
+    x = p.flat()
+    g = np.zeros_like(x)
+    for k in range(x.size):
+        xp, xm = x.copy(), x.copy()
+        step = h * max(1.0, abs(x[k]))
+        xp[k] += step
+        xm[k] -= step
+        lp = unrolled_loss(H, Params.from_flat(xp, p.nu_pre, p.nu_post), f, K, u0)
+        lm = unrolled_loss(H, Params.from_flat(xm, p.nu_pre, p.nu_post), f, K, u0)
+        g[k] = (lp - lm) / (2 * step)
+    return g

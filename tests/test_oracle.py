@@ -1,0 +1,306 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's own formula: each compares it with an
+independent form (closed-form spectra, dense error-propagation matrices,
+direct solves, complex-step derivatives vs finite differences, invariants).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+import oracle as O
+import workloads as W
+from workloads import fields, meshes
+
+
+@pytest.fixture(scope="module")
+def poisson33():
+    p = W.poisson_square(33, 4, batch=3, seed=1)
+    return p, O.build_hierarchy(p)
+
+
+@pytest.fixture(scope="module")
+def checker17():
+    p = W.checkerboard_square(N=17, J=3, ncell=4, values=(1.0, 1e4), batch=2, seed=2)
+    return p, O.build_hierarchy(p)
+
+
+def random_params(J, seed, spread=0.3):
+    r = np.random.default_rng(seed)
+    p = O.Params.identity(J)
+    m = J - 1
+    p.theta = p.theta * (1 + spread * r.uniform(-1, 1, m))
+    p.eta = p.eta * (1 + spread * r.uniform(-1, 1, m))
+    for w in (p.wB, p.wR, p.wP):
+        w[:, 0] += spread * r.uniform(-1, 1, m)
+        w[:, 1] += spread * r.uniform(-1, 1, m)
+    return p
+
+
+# ---------------------------------------------------------------- setup ----
+
+def test_p1_poisson_is_five_point(poisson33):
+    """P1 on right triangles gives the (4, -1) five-point stencil exactly."""
+    p, H = poisson33
+    A = H.levels[0].A.toarray()
+    N = 31
+    T = 2 * np.eye(N) - np.eye(N, k=1) - np.eye(N, k=-1)
+    ref = np.kron(np.eye(N), T) + np.kron(T, np.eye(N))
+    assert np.array_equal(A, ref)
+
+
+@pytest.mark.parametrize("case", ["poisson", "checker"])
+def test_galerkin_equals_rediscretisation(case):
+    """Nested P1 with P = natural inclusion: P^T A P equals the stiffness
+    matrix assembled directly on the coarse mesh (coefficient aligned with it)."""
+    N = 33
+    if case == "poisson":
+        p = W.poisson_square(N, 3)
+        kc = None
+        Lc = p.mesh.levels[1]
+    else:
+        p = W.checkerboard_square(N, 3, ncell=4, values=(1.0, 1e4), seed=5)
+        Lc = p.mesh.levels[1]
+        kc = fields.checkerboard(Lc, 4, (1.0, 1e4), 5)
+    H = O.build_hierarchy(p)
+    Ac = fields.assemble_p1(Lc, k=kc)
+    I = Lc.interior
+    ref = Ac[I][:, I].toarray()
+    got = H.levels[1].A.toarray()
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_prolongation_column_sums(poisson33):
+    """Each coarse vertex away from the boundary spreads to itself (1) and its
+    six fine edge midpoints (1/2): column sums of P are 4."""
+    _, H = poisson33
+    P = H.levels[0].P
+    cs = np.asarray(P.sum(axis=0)).ravel().reshape(15, 15)
+    assert np.allclose(cs[1:-1, 1:-1], 4.0)
+    assert (P.getnnz(axis=1) <= 2).all()
+
+
+def test_degree_counts_full_stencil(poisson33):
+    """Degree counts every algebraic neighbour including eliminated Dirichlet
+    vertices: 4 everywhere for the five-point stencil."""
+    _, H = poisson33
+    for L in H.levels:
+        assert np.all(1.0 / L.inv_deg == 4.0)
+
+
+# ------------------------------------------------------------- smoother ----
+
+def dense_smoother(L, theta, eta, wB):
+    n = L.A.shape[0]
+    I = np.eye(n)
+    return O.smooth(L, np.zeros((n, n)), I, theta, eta, wB)  # f = 0: u -> S u
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_smoother_spectrum_closed_form(poisson33, seed):
+    """Eq. (eigenvalue-S): sigma = 1 - eta theta (w1 + w2 lambda_hat) lambda with
+    lambda = 1 - (cos p pi h + cos q pi h)/2 and lambda_hat = 1 - lambda for the
+    five-point Laplacian, for arbitrary (w1, w2, theta, eta)."""
+    _, H = poisson33
+    r = np.random.default_rng(seed)
+    theta, eta = r.uniform(0.3, 1.0), r.uniform(0.5, 1.5)
+    wB = (r.uniform(0.5, 1.5), r.uniform(-0.8, 0.8))
+    S = dense_smoother(H.levels[0], theta, eta, wB)
+    h = 1.0 / 32
+    pq = np.arange(1, 32)
+    lam = 1 - (np.cos(pq[:, None] * np.pi * h) + np.cos(pq[None, :] * np.pi * h)) / 2
+    lam_hat = 1 - lam
+    sigma = 1 - eta * theta * (wB[0] + wB[1] * lam_hat) * lam
+    ev = np.sort(np.linalg.eigvals(S).real)
+    assert np.abs(ev - np.sort(sigma.ravel())).max() < 1e-12
+
+
+def test_jacobi_recovery(poisson33):
+    """Remark (recovery of classical methods): w1=1, w2=0, theta=omega, eta=1
+    gives S = I - omega D_A^{-1} A with eigenvalues 1 - omega lambda."""
+    _, H = poisson33
+    L = H.levels[0]
+    omega = 2.0 / 3.0
+    S = dense_smoother(L, omega, 1.0, (1.0, 0.0))
+    ref = np.eye(961) - omega * (L.A.toarray() / L.diag[:, None])
+    assert np.abs(S - ref).max() < 1e-15
+
+
+# ---------------------------------------------------------------- cycle ----
+
+def dense_error_propagation(H, p):
+    """E_l = S_l^nu_post (I - C_l) S_l^nu_pre with
+    C_l = Phi_P P (I - E_{l+1}) A_{l+1}^{-1} P^T Phi_R A_l, E_J = 0."""
+    J = H.J
+    E = np.zeros((H.levels[-1].A.shape[0],) * 2)
+    for lev in range(J - 2, -1, -1):
+        L, Lc = H.levels[lev], H.levels[lev + 1]
+        A = L.A.toarray()
+        n = A.shape[0]
+        Ag = L.inv_deg[:, None] * L.G.toarray()
+        phi = lambda w: w[0] * np.eye(n) + w[1] * Ag  # noqa: E731
+        S = np.eye(n) - p.eta[lev] * p.theta[lev] * phi(p.wB[lev]) @ (A / L.diag[:, None])
+        P = L.P.toarray()
+        Ac = Lc.A.toarray()
+        C = phi(p.wP[lev]) @ P @ (np.eye(Ac.shape[0]) - E) @ np.linalg.solve(Ac, P.T @ phi(p.wR[lev]) @ A)
+        E = np.linalg.matrix_power(S, p.nu_post) @ (np.eye(n) - C) @ np.linalg.matrix_power(S, p.nu_pre)
+    return E
+
+
+@pytest.mark.parametrize("which", ["identity", "random"])
+def test_vcycle_matches_dense_error_propagation(poisson33, which):
+    p, H = poisson33
+    th = O.Params.identity(H.J) if which == "identity" else random_params(H.J, 7)
+    E = dense_error_propagation(H, th)
+    A = H.levels[0].A.toarray()
+    r = np.random.default_rng(3)
+    f = r.standard_normal((961, 2))
+    u0 = r.standard_normal((961, 2))
+    ustar = np.linalg.solve(A, f)
+    got = O.vcycle(H, th, f, u0)
+    ref = ustar + E @ (u0 - ustar)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_vcycle_dense_on_jump_coefficients(checker17):
+    p, H = checker17
+    th = random_params(H.J, 11)
+    E = dense_error_propagation(H, th)
+    A = H.levels[0].A.toarray()
+    f = p.f
+    u0 = np.random.default_rng(0).standard_normal(f.shape)
+    ustar = np.linalg.solve(A, f)
+    got = O.vcycle(H, th, f, u0)
+    ref = ustar + E @ (u0 - ustar)
+    assert np.abs(got - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+def test_jacobi_equivalent_reproduces_classical_factor(poisson33):
+    """With the identity initialisation the learnable cycle is the classical
+    damped-Jacobi V-cycle (Sec. 3.4): its observed asymptotic factor equals the
+    spectral radius of Algorithm 1's error propagation built with B = omega D^{-1}
+    and no convolutions."""
+    _, H = poisson33
+    J = H.J
+    omega = 2.0 / 3.0
+    E = np.zeros((H.levels[-1].A.shape[0],) * 2)
+    for lev in range(J - 2, -1, -1):
+        L, Lc = H.levels[lev], H.levels[lev + 1]
+        A = L.A.toarray()
+        n = A.shape[0]
+        S = np.eye(n) - omega * A / np.diag(A)[:, None]
+        P = L.P.toarray()
+        Ac = P.T @ A @ P
+        CGC = np.eye(n) - P @ (np.eye(Ac.shape[0]) - E) @ np.linalg.solve(Ac, P.T @ A)
+        E = S @ S @ CGC @ S @ S
+    rho = np.abs(np.linalg.eigvals(E)).max()
+    th = O.Params.identity(J)
+    n = E.shape[0]
+    E_orc = O.vcycle(H, th, np.zeros((n, n)), np.eye(n))  # f = 0: error -> E error
+    assert np.abs(E_orc - E).max() < 1e-13
+    rho_orc = np.abs(np.linalg.eigvals(E_orc)).max()
+    assert abs(rho_orc - rho) < 1e-10
+    assert rho < 0.35
+
+
+def test_converges_to_direct_solve(poisson33):
+    p, H = poisson33
+    res = O.solve_vcycles(H, O.Params.identity(H.J), p.f, 1e-10)
+    assert (res.relres < 1e-10).all()
+    ref = spla.spsolve(H.levels[0].A.tocsc(), p.f)
+    assert np.abs(res.u - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_refinement_converges(checker17):
+    p, H = checker17
+    res = O.solve_refinement(H, random_params(H.J, 3, 0.1), p.f, 1e-10)
+    assert (res.relres < 1e-10).all()
+    ref = np.linalg.solve(H.levels[0].A.toarray(), p.f)
+    assert np.abs(res.u - ref).max() <= 1e-8 * np.abs(ref).max()
+
+
+# ----------------------------------------------------------- invariants ----
+
+def test_linearity(poisson33):
+    _, H = poisson33
+    th = random_params(H.J, 5)
+    r = np.random.default_rng(4)
+    f1, f2, u1, u2 = (r.standard_normal((961, 1)) for _ in range(4))
+    a, b = 0.7, -1.3
+    lhs = O.vcycle(H, th, a * f1 + b * f2, a * u1 + b * u2)
+    rhs = a * O.vcycle(H, th, f1, u1) + b * O.vcycle(H, th, f2, u2)
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max()
+
+
+def test_identity_cycle_is_symmetric(poisson33):
+    """R = P^T, symmetric smoother, nu_pre = nu_post: M = (I - E) A^{-1} is SPD."""
+    _, H = poisson33
+    th = O.Params.identity(H.J)
+    n = 961
+    M = O.vcycle(H, th, np.eye(n), np.zeros((n, n)))  # columns M e_k
+    assert np.abs(M - M.T).max() < 1e-13 * np.abs(M).max()
+    assert np.linalg.eigvalsh(0.5 * (M + M.T)).min() > 0
+
+
+def test_permutation_equivariance():
+    """Relabelling the finest vertices relabels the result (mean aggregation is
+    permutation invariant)."""
+    p = W.checkerboard_square(N=17, J=3, ncell=4, values=(1.0, 1e4), batch=1, seed=9)
+    H = O.build_hierarchy(p)
+    th = random_params(H.J, 13)
+    L0 = p.mesh.levels[0]
+    perm = np.random.default_rng(0).permutation(L0.nv)   # new -> old
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(perm.size)
+    L0p = meshes.MeshLevel(L0.xy[perm], inv[L0.tri], L0.boundary[perm], L0.parent[perm])
+    Hm = meshes.MeshHierarchy([L0p] + p.mesh.levels[1:])
+    Ap = p.A_full[perm][:, perm].tocsr()
+    # interior DOF order of the permuted mesh, expressed in old interior indices
+    old_int = {v: k for k, v in enumerate(L0.interior)}
+    dof_perm = np.array([old_int[perm[v]] for v in L0p.interior])
+    pp = W.Problem("perm", Hm, Ap, p.f[dof_perm], {})
+    Hp = O.build_hierarchy(pp)
+    u0 = np.random.default_rng(1).standard_normal(p.f.shape)
+    got = O.vcycle(Hp, th, pp.f, u0[dof_perm])
+    ref = O.vcycle(H, th, p.f, u0)[dof_perm]
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+# ------------------------------------------------------------- gradient ----
+
+def test_unrolled_loss_dense(poisson33):
+    """r_K = A E^K A^{-1} f from u_0 = 0, so the loss has a dense closed form."""
+    p, H = poisson33
+    th = random_params(H.J, 21, 0.2)
+    E = dense_error_propagation(H, th)
+    A = H.levels[0].A.toarray()
+    f = p.f
+    rK = A @ np.linalg.matrix_power(E, 3) @ np.linalg.solve(A, f)
+    ref = ((rK * rK).sum(0) / (f * f).sum(0)).mean()
+    got = O.unrolled_loss(H, th, f, 3)
+    assert abs(got - ref) < 1e-11 * ref
+
+
+def test_complex_step_gradient_matches_finite_differences(checker17):
+    p, H = checker17
+    th = random_params(H.J, 17, 0.2)
+    loss, g_cs = O.loss_gradient_complex_step(H, th, p.f, 2)
+    g_fd = O.loss_gradient_fd(H, th, p.f, 2)
+    scale = np.abs(g_cs).max()
+    assert np.abs(g_cs - g_fd).max() < 1e-6 * scale
+    assert loss > 0
+
+
+def test_shared_weight_gradient_is_sum_over_levels(checker17):
+    """Sharing one SAGEConv across levels: the derivative along the shared
+    direction (all levels perturbed at once) equals the sum of the per-level
+    derivatives."""
+    p, H = checker17
+    th = random_params(H.J, 19, 0.2)
+    _, g = O.loss_gradient_complex_step(H, th, p.f, 2)
+    g = g.reshape(H.J - 1, 8)
+    x = th.flat().astype(np.complex128).reshape(H.J - 1, 8)
+    x[:, 5] += 1e-30j  # wR2 at every level
+    lc = O.unrolled_loss(H, O.Params.from_flat(x.ravel()), p.f.astype(np.complex128), 2)
+    assert abs(np.imag(lc) / 1e-30 - g[:, 5].sum()) < 1e-12 * max(1.0, abs(g[:, 5]).sum())

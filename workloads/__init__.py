@@ -1,0 +1,8 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+Holds meshes, coefficient fields, the finest-level stiffness matrix and
+right-hand sides, and nothing of the multigrid method itself.
+"""
+from .configs import (Problem, checkerboard_square, lognormal_square,  # noqa: F401
+                      lshape_anisotropic, poisson_square, training_square)
+from .meshes import MeshHierarchy, MeshLevel  # noqa: F401

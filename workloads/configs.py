@@ -1,0 +1,94 @@
+"""Named synthetic workloads shaped like the paper's model problems.
+
+Each builder returns a Problem: a nested mesh hierarchy, the finest-level P1
+stiffness matrix over all vertices and seeded right-hand sides on the interior
+vertices.  The five workloads and their sizes:
+
+  poisson_square      -Laplace u = f, 33x33 nodes (961 DOF), 4 levels
+  checkerboard_square -div(k grad u) = f, 513x513 (261121 DOF), 9 levels,
+                      k in {1, 1e4} on an 8x8 checkerboard
+  training_square     257x257 (65025 DOF), 8 levels, Poisson or a 4x4
+                      {1, 1e3} checkerboard, 64 right-hand sides
+  lognormal_square    65^2 .. 1025^2, k = exp(1.5 g), g a Gaussian field
+                      with correlation length 0.1 (serving requests)
+  lshape_anisotropic  jittered L-shape, 7 red refinements (about 3.1M DOF),
+                      8 levels, K = R(30 deg) diag(1, 1e-3) R(30 deg)^T
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import fields, meshes
+
+
+@dataclass
+class Problem:
+    name: str
+    mesh: meshes.MeshHierarchy
+    A_full: sp.csr_matrix          # finest level, all vertices, FP64
+    f: np.ndarray                  # (n_interior, batch) FP64
+    info: dict
+
+    @property
+    def J(self) -> int:
+        return self.mesh.J
+
+    @property
+    def n(self) -> int:
+        return int(self.f.shape[0])
+
+    @property
+    def batch(self) -> int:
+        return int(self.f.shape[1])
+
+
+def poisson_square(N: int = 33, J: int = 4, batch: int = 1, seed: int = 0) -> Problem:
+    H = meshes.square_hierarchy(N, J)
+    A = fields.assemble_p1(H.levels[0])
+    n = H.levels[0].interior.size
+    return Problem(f"poisson_{N}", H, A, fields.rhs(n, batch, seed),
+                   dict(N=N, J=J, batch=batch, seed=seed, coefficient="1"))
+
+
+def checkerboard_square(N: int = 513, J: int = 9, ncell: int = 8,
+                        values=(1.0, 1e4), batch: int = 1, seed: int = 0) -> Problem:
+    H = meshes.square_hierarchy(N, J)
+    k = fields.checkerboard(H.levels[0], ncell, values, seed)
+    A = fields.assemble_p1(H.levels[0], k=k)
+    n = H.levels[0].interior.size
+    return Problem(f"checker{ncell}_{N}", H, A, fields.rhs(n, batch, seed),
+                   dict(N=N, J=J, batch=batch, seed=seed,
+                        coefficient=f"checkerboard {ncell}x{ncell} {values}"))
+
+
+def training_square(kind: str = "poisson", N: int = 257, J: int = 8, batch: int = 64,
+                    seed: int = 0) -> Problem:
+    if kind == "poisson":
+        return poisson_square(N, J, batch, seed)
+    return checkerboard_square(N, J, 4, (1.0, 1e3), batch, seed)
+
+
+def lognormal_square(N: int, seed: int, sigma: float = 1.5, corr_len: float = 0.1,
+                     batch: int = 1, J: int | None = None) -> Problem:
+    J = J if J is not None else int(round(np.log2(N - 1)))
+    H = meshes.square_hierarchy(N, J)
+    k = fields.lognormal(H.levels[0], sigma, corr_len, seed)
+    A = fields.assemble_p1(H.levels[0], k=k)
+    n = H.levels[0].interior.size
+    return Problem(f"lognormal_{N}_s{seed}", H, A, fields.rhs(n, batch, seed),
+                   dict(N=N, J=J, batch=batch, seed=seed,
+                        coefficient=f"lognormal sigma={sigma} corr={corr_len}"))
+
+
+def lshape_anisotropic(refinements: int = 7, batch: int = 16, seed: int = 0,
+                       eps: float = 1e-3, angle: float = 30.0) -> Problem:
+    H = meshes.lshape_hierarchy(refinements, 8, 0.2, seed)
+    K = fields.rotated_anisotropy(eps, angle)
+    A = fields.assemble_p1(H.levels[0], K=K)
+    n = H.levels[0].interior.size
+    return Problem(f"lshape_r{refinements}", H, A, fields.rhs(n, batch, seed),
+                   dict(refinements=refinements, J=H.J, batch=batch, seed=seed,
+                        coefficient=f"anisotropic diag(1,{eps}) rotated {angle} deg"))
