@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Time to 1e-8 relative residual, learned FP32 V-cycle + FP64 refinement vs
+plain FP64 geometric multigrid, on one B300.
+
+Workload (default): -div(k grad u) = f, P1 on a 513 x 513 uniform right-
+triangle mesh of the unit square (261121 interior DOF), 9 Galerkin levels,
+k in {1, 1e4} on an 8 x 8 checkerboard drawn from the seed, f ~ N(0, 1),
+one right-hand side.  A step is one complete solve from u = 0 to
+||f - A u|| / ||f|| < 1e-8.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+on the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TOL = 1e-8
+MAX_ITER = 400
+WORKLOAD = ("checkerboard 513x513 P1, 9 levels, k in {1,1e4} on 8x8 cells, f~N(0,1), "
+            "1 rhs, tol 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--params", default=None,
+                    help="JSON file of trained parameters (default: the package's trained set)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def make_problem(seed: int):
+    import workloads as W
+    return W.checkerboard_square(N=513, J=9, ncell=8, values=(1.0, 1e4), batch=1, seed=seed)
+
+
+# ------------------------------------------------------------ clocks -------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "100"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            try:
+                out, _ = self.p.communicate(timeout=5)
+            except Exception:
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------ algorithmic bytes --
+
+def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
+    """Minimum bytes one launch must move: every array touched read (or
+    written) once; neighbour values of a vector counted once."""
+    n = hier.sizes[lev]
+    nnz_off = hier.A[lev].data.size - n
+    nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
+    nnzP = hier.P[lev].data.size if lev < hier.J - 1 else 0
+    conv_bytes = 0
+    if name == "jacobi_smooth":
+        return nnz_off * (4 + b) + 2 * n * b + 3 * B * n * b
+    if name == "residual_scaled":
+        return nnz_off * (4 + b) + 2 * n * b + 3 * B * n * b
+    if name == "sage_conv_update":
+        return nnz_off * 4 + n * b + 3 * B * n * b
+    if name == "residual":
+        return nnz_off * (4 + b) + n * b + 3 * B * n * b
+    if name == "restrict_conv":
+        return nnzP * (4 + b) + B * n * b + B * nc * b + conv_bytes
+    if name == "prolong_conv":
+        return nnzP * (4 + b) + B * nc * b + 2 * B * n * b
+    if name == "coarse_cholesky":
+        return 2 * n * n * 8 + 2 * B * n * b
+    if name == "outer_residual_fp64":
+        return nnz_off * 12 + 2 * n * 8 + B * n * (8 + 8 + 4)
+    raise KeyError(name)
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- ours ------
+
+def run_ours(args):
+    import torch
+    import paper_2608_29082_b300 as lmg
+    from paper_2608_29082_b300 import trained
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    prob = make_problem(seed=rank)
+    hier = lmg.Hierarchy.from_problem(prob)
+    J = hier.J
+    learned = trained.load(args.params, J)
+    plain = lmg.LMGParams.identity(J)
+    S32 = lmg.Solver(hier, learned, precision=32, max_batch=1)
+    S64 = lmg.Solver(hier, plain, precision=64, max_batch=1)
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    u = torch.zeros_like(f)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def timed(S):
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for _ in range(args.warmup):
+            u.zero_()
+            S.solve(f, u, tol=TOL, max_iter=MAX_ITER)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        k0 = S.kernel_launches()
+        infos = []
+        for k in range(args.steps):
+            flush.zero_()
+            u.zero_()
+            starts[k].record()
+            _, info = S.solve(f, u, tol=TOL, max_iter=MAX_ITER)
+            ends[k].record()
+            infos.append(info)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        return float(np.mean(ms)), infos[-1], S.kernel_launches() - k0
+
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms32, info32, nk32 = timed(S32)
+        ms64, info64, nk64 = timed(S64)
+    clocks = clk.summary()
+    u32 = u.clone()
+    # max over ranks
+    if pg:
+        t = torch.tensor([ms32, ms64], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms32, ms64 = t.tolist()
+
+    # end to end through the public host API (pinned host buffers)
+    fh = torch.tensor(prob.f, dtype=torch.float64).pin_memory().numpy()
+    uh = torch.zeros_like(torch.from_numpy(fh)).pin_memory().numpy()
+    e2e = []
+    for k in range(args.warmup + args.steps):
+        uh[:] = 0.0
+        t0 = time.perf_counter()
+        S32.solve_host(fh, uh, tol=TOL, max_iter=MAX_ITER)
+        t1 = time.perf_counter()
+        if k >= args.warmup:
+            e2e.append((t1 - t0) * 1e3)
+    e2e_ms = float(np.mean(e2e))
+
+    # dominant kernel: per-launch device times from CUDA events on the stream
+    rhat = (f / torch.linalg.norm(f)).float()
+    c = torch.zeros_like(rhat)
+    agg = {}
+    reps = 5
+    for _ in range(reps):
+        c.zero_()
+        for name, lev, t in S32.vcycle_profile(rhat, c):
+            key = (name, lev)
+            a = agg.setdefault(key, [0.0, 0])
+            a[0] += t
+            a[1] += 1
+    # the FP64 refinement residual, once per iteration
+    r64 = torch.empty_like(f)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(20):
+        S32.level_apply(0, "outer_residual", f, u32, r64)
+    ev1.record()
+    torch.cuda.synchronize()
+    agg[("outer_residual_fp64", 0)] = [ev0.elapsed_time(ev1) / 20 * reps, reps]
+    per_cycle = {k: v[0] / reps for k, v in agg.items()}
+    total = sum(per_cycle.values())
+    (dname, dlev), dms = max(per_cycle.items(), key=lambda kv: kv[1])
+    launches_per_cycle = agg[(dname, dlev)][1] / reps
+    avg_launch_ms = dms / launches_per_cycle
+    b = 8 if dname == "outer_residual_fp64" else 4
+    nbytes = kernel_bytes(dname, dlev, hier, 1, b)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6400.0))
+    achieved = nbytes / (avg_launch_ms * 1e-3) / 1e9
+    shares = sorted(((f"{k[0]}@L{k[1]}", round(v / total, 4)) for k, v in per_cycle.items()),
+                    key=lambda kv: -kv[1])[:8]
+
+    # oracle on the host cores, same workload (rank 0 at N=1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(prob)
+
+    if rank == 0:
+        out = {
+            "metric": "time to 1e-8 relative residual (learned FP32 V-cycle + FP64 refinement)",
+            "value": round(ms32, 4),
+            "unit": "ms/solve",
+            "n_gpus": ws,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms32, 4),
+            "higher_is_better": False,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32 cycle + f64 refinement",
+            "data": "synthetic (seeded checkerboard coefficient and N(0,1) source)",
+            "config": {"workload": WORKLOAD, "dof": hier.sizes[0], "levels": J, "nrhs": 1,
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "l2": "flushed (256 MB write) before every timed solve",
+                       "params": trained.describe(args.params)},
+            "learned_iters": int(info32.iters[0]),
+            "learned_relres": float(info32.relres[0]),
+            "plain_fp64_ms": round(ms64, 4),
+            "plain_fp64_iters": int(info64.iters[0]),
+            "plain_fp64_relres": float(info64.relres[0]),
+            "speedup_vs_plain_fp64": round(ms64 / ms32, 3),
+            "e2e": {"value": round(e2e_ms, 4), "unit": "ms/solve",
+                    "h2d_bytes_per_step": int(2 * fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)},
+            "gpu_launches": int(nk32 + nk64),
+            "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "algorithmic_bytes_per_launch": int(nbytes),
+                         "avg_launch_us": round(avg_launch_ms * 1e3, 3),
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                         "note": "working set fits in L2 (126 MB); see DESIGN.md"},
+            "kernel_shares_per_vcycle": shares,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    if pg:
+        pg.destroy_process_group()
+
+
+def cpu_baseline(prob):
+    import oracle as O
+    t0 = time.perf_counter()
+    H = O.build_hierarchy(prob)
+    setup = time.perf_counter() - t0
+    p = O.Params.identity(H.J)
+    t0 = time.perf_counter()
+    r = O.solve_refinement(H, p, prob.f, TOL, max_iter=MAX_ITER)
+    dt = time.perf_counter() - t0
+    return {"value": round(dt * 1e3, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
+            "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, identity "
+                      f"parameters) of the same workload; setup {setup:.2f}s excluded; "
+                      "scipy sparse products, single thread"}
+
+
+# ---------------------------------------------------------- reference ------
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    prob = make_problem(seed=0)
+    H = O.build_hierarchy(prob)
+    p = O.Params.identity(H.J)
+    times, iters = [], 0
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = O.solve_refinement(H, p, prob.f, TOL, max_iter=MAX_ITER)
+        dt = (time.perf_counter() - t0) * 1e3
+        iters = int(r.iters[0])
+        if k >= args.warmup:
+            times.append(dt)
+    v = float(np.mean(times))
+    out = {"impl": "reference",
+           "metric": "time to 1e-8 relative residual (learned FP32 V-cycle + FP64 refinement)",
+           "value": round(v, 2), "unit": "ms/solve", "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "nrhs": 1},
+           "cpu_baseline": {"value": round(v, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
+                            "sample": f"full FP64 oracle refinement solve ({iters} V-cycles) per step"},
+           "e2e": {"value": round(v, 2), "unit": "ms/solve", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

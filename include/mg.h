@@ -1,0 +1,247 @@
+/*
+ * mg.h - C ABI of libmg.so, a B300 (sm_103a) learnable geometric multigrid.
+ *
+ * The library runs the learnable V-cycle of "A Learnable Multigrid Framework
+ * via Graph Convolutions" (Algorithm 2): damped-Jacobi smoothing whose update
+ * passes through a mean-aggregation SAGEConv (Sec. 3, Sec. 3.2), restriction
+ * r_c = P^T Phi_R(r) and prolongation e = Phi_P(P e_c) (Sec. 3), Galerkin
+ * coarse operators A_{l+1} = P^T A_l P (Sec. 2.2) and an exact Cholesky solve
+ * on the coarsest level.  It is used as a solver, as an FP32 preconditioner
+ * inside FP64 iterative refinement, and differentiated for training
+ * (Algorithm 3).
+ *
+ * Conventions for every entry point
+ *  - Level 0 is the finest level (the paper's l = 1); level J-1 the coarsest.
+ *  - Vectors are node features X[n][nrhs]: row-major, right-hand-side index
+ *    fastest, contiguous, on the device unless the name says host.
+ *  - Host arrays passed in are copied; the caller keeps ownership.  A context
+ *    owns every device buffer it allocates.  Caller-provided device buffers
+ *    stay owned by the caller and must not alias one another unless stated.
+ *  - Work is ordered on the CUDA stream passed in (NULL = the legacy default
+ *    stream).  Only calls that return host results synchronise that stream.
+ *  - Every call returns mg_status.  On failure mg_last_error() gives a
+ *    message (per context, or global for calls without a context).
+ *  - A context is not thread-safe: use one context per host thread.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_NOT_CONVERGED = 1,       /* mg_solve hit max_iter before tol            */
+  MG_ERR_INVALID = -1,        /* bad argument, size or layout                */
+  MG_ERR_OOM = -2,            /* device or host allocation failed            */
+  MG_ERR_NOT_SPD = -3,        /* Cholesky of the coarsest operator failed    */
+  MG_ERR_CUDA = -4,           /* a CUDA runtime call failed                  */
+  MG_ERR_TIMEOUT = -5,        /* a bounded device-side wait gave up          */
+  MG_ERR_DIVERGED = -6,       /* non-finite residual in mg_solve             */
+  MG_ERR_NOT_IMPLEMENTED = -7,
+  MG_ERR_STATE = -8           /* call order violated (e.g. backward first)   */
+} mg_status;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Host CSR matrix, FP64 values, 32-bit indices (nnz < 2^31). */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int32_t nnz;
+  const int32_t* rowptr;  /* [n_rows + 1] */
+  const int32_t* col;     /* [nnz]        */
+  const double* val;      /* [nnz]        */
+} mg_csr;
+
+/* CSR matrix whose arrays were allocated by the library (malloc); release
+ * with mg_csr_owned_free(). */
+typedef struct {
+  int32_t n_rows;
+  int32_t n_cols;
+  int32_t nnz;
+  int32_t* rowptr;
+  int32_t* col;
+  double* val;
+} mg_csr_owned;
+
+/* Transfer and graph data of a hierarchy with J levels (host). */
+typedef struct {
+  int32_t n_levels;                /* J >= 2                                       */
+  const mg_csr* P;                 /* [J-1]; P[l] is n_l x n_{l+1}, <= 2 entries   */
+                                   /* per row (natural inclusion, Sec. 2.2)        */
+  const double* const* inv_deg;    /* [J]; inv_deg[l][i] = 1/|N(i)| on level l,    */
+                                   /* the mean of the SAGEConv (Sec. 3.2)          */
+} mg_hierarchy;
+
+/* Learnable parameters Theta (Sec. 3): per level l = 0..J-2 the scalings
+ * theta_l, eta_l and the scalar SAGEConv weights (w1, w2) of Phi_B, Phi_R,
+ * Phi_P.  The identity initialisation of Sec. 3.4 is theta = omega, eta = 1,
+ * w = (1, 0), which is the classical damped-Jacobi V-cycle. */
+typedef struct {
+  int32_t n_levels;      /* J, must match the hierarchy          */
+  int32_t nu_pre;        /* pre-smoothing steps per level, >= 0  */
+  int32_t nu_post;       /* post-smoothing steps per level, >= 0 */
+  const double* theta;   /* [J-1]                                */
+  const double* eta;     /* [J-1]                                */
+  const double* wB;      /* [J-1][2] (w1, w2) of Phi_B           */
+  const double* wR;      /* [J-1][2] of Phi_R                    */
+  const double* wP;      /* [J-1][2] of Phi_P                    */
+} mg_params;
+
+/* ---------------------------------------------------------------------
+ * Host set-up helpers (native, FP64).  They turn a nested mesh hierarchy
+ * into the operators mg_setup takes; they do not touch the GPU.
+ * ------------------------------------------------------------------- */
+
+/* Galerkin coarsening A_c = P^T A P (Sec. 2.2, Eq. for A_{l+1}) over ALL
+ * vertices of a nested P1 pair, with P the natural inclusion given by a
+ * parent map: parent[2*i] = c, parent[2*i+1] = -1 when fine vertex i is
+ * coarse vertex c; (a, b) when it is the midpoint of coarse edge a-b
+ * (P_ia = P_ib = 1/2).  Off-diagonal results with
+ * |a_IJ| <= drop_tol * max(|a_II|, |a_JJ|) are removed (round-off of the
+ * product).  out is allocated by the library.  Errors: MG_ERR_INVALID for
+ * out-of-range parents or non-square A, MG_ERR_OOM. */
+mg_status mg_galerkin(const mg_csr* A_full, const int32_t* parent, int32_t nv_coarse,
+                      double drop_tol, mg_csr_owned* out);
+
+/* Dirichlet elimination of one level: keeps the rows and columns of the
+ * vertices with boundary[i] == 0 (in vertex order; this is the DOF order),
+ * dropping off-diagonal entries as in mg_galerkin.  inv_deg_out[k] (host,
+ * [number of interior vertices]) receives 1/deg of interior vertex k, where
+ * deg counts its neighbours in the algebraic graph {(i,j): A_ij != 0, i != j}
+ * (Sec. 2.1) of the operator BEFORE elimination, so eliminated boundary
+ * neighbours are counted and enter the mean as zeros. */
+mg_status mg_eliminate(const mg_csr* A_full, const uint8_t* boundary, double drop_tol,
+                       mg_csr_owned* A_int, double* inv_deg_out);
+
+/* Interior prolongation P (n_int_fine x n_int_coarse) from the parent map:
+ * the natural inclusion (Sec. 2.2) restricted to interior vertices. */
+mg_status mg_prolongation(const int32_t* parent, int32_t nv_fine, const uint8_t* boundary_fine,
+                          int32_t nv_coarse, const uint8_t* boundary_coarse, mg_csr_owned* P_int);
+
+void mg_csr_owned_free(mg_csr_owned* m);
+
+/* ---------------------------------------------------------------------
+ * Context
+ * ------------------------------------------------------------------- */
+
+/* Copies the hierarchy to the device and prepares the cycle.
+ *  A_levels  [J] interior operators (SPD), A_levels[l] is n_l x n_l; its
+ *            off-diagonal pattern is the convolution graph of level l.
+ *  precision 64: the V-cycle runs in FP64 (plain / parity path);
+ *            32: the V-cycle runs in FP32 (values, weights, accumulation)
+ *            and mg_solve wraps it in FP64 iterative refinement.
+ *  max_batch largest nrhs any later call will pass (sizes the workspace).
+ * The coarsest operator is factorised by dense FP64 Cholesky here
+ * (MG_ERR_NOT_SPD if that fails; n_{J-1} <= 2048).  Matrices are stored as
+ * SELL-32 slices (off-diagonals) plus diagonal arrays.  *out is NULL on
+ * failure; the message is then available from mg_last_error(NULL, ...). */
+mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr* A_levels,
+                   const mg_params* p, int32_t max_batch, int32_t precision, void* stream);
+
+/* Replaces Theta (same J); cheap: the device copy is updated on the next
+ * call's stream.  Changing whether a w2 is zero switches kernels. */
+mg_status mg_set_params(mg_ctx* ctx, const mg_params* p);
+
+/* One learnable V-cycle (Algorithm 2) on level 0: u <- LMG(A, f, u, 1, Theta).
+ * f_dev, u_dev: [n_0][nrhs] in the context precision (double for 64, float
+ * for 32); u_dev is the initial guess and is overwritten; f_dev and u_dev
+ * must not overlap.  1 <= nrhs <= max_batch. */
+mg_status mg_vcycle(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, void* stream);
+
+/* Solves A u = f to ||f - A u||_2 / ||f||_2 < tol for every right-hand side.
+ * f_dev, u_dev: FP64 [n_0][nrhs] on the device; u_dev holds the initial guess.
+ * precision 64: u <- LMG(f, u) repeated (plain stationary multigrid);
+ * precision 32: FP64 iterative refinement, r = f - A u in FP64, c = LMG_32(r,0)
+ * in FP32, u += c in FP64.  A right-hand side stops changing as soon as it
+ * meets tol, so its result does not depend on the others in the batch.
+ * iters_out, relres_out: host arrays [nrhs] (may be NULL).  Synchronises the
+ * stream.  Returns MG_NOT_CONVERGED if any right-hand side did not meet tol
+ * within max_iter, MG_ERR_DIVERGED on a non-finite residual. */
+mg_status mg_solve(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
+                   int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
+
+/* mg_solve with HOST f and u (pageable or pinned): copies f and the initial
+ * u to the device, solves, copies u back.  Same semantics otherwise. */
+mg_status mg_solve_host(mg_ctx* ctx, const double* f_host, double* u_host, int32_t nrhs,
+                        double tol, int32_t max_iter, int32_t* iters_out, double* relres_out,
+                        void* stream);
+
+/* Single steps of Algorithm 2 on one level, for step-by-step checking.
+ * All vectors device, context precision, [n][nrhs]; out must not alias inputs.
+ *   MG_OP_SMOOTH    out = u + eta Phi_B(theta D^{-1}(f - A u))   x = f, y = u
+ *   MG_OP_RESIDUAL  out = f - A u                                x = f, y = u
+ *   MG_OP_RESTRICT  out = P^T Phi_R(x)  (out on level+1)         x = r
+ *   MG_OP_PROLONG   out = y + Phi_P(P x) (x on level+1)          x = e_c, y = u
+ *   MG_OP_COARSE    out = A^{-1} x (level must be J-1, FP64 Cholesky)
+ *   MG_OP_OUTER_RESIDUAL  out = f - A u in FP64 on level 0 whatever the
+ *                   context precision (the refinement residual); x = f,
+ *                   y = u, out double
+ */
+typedef enum {
+  MG_OP_SMOOTH = 0,
+  MG_OP_RESIDUAL = 1,
+  MG_OP_RESTRICT = 2,
+  MG_OP_PROLONG = 3,
+  MG_OP_COARSE = 4,
+  MG_OP_OUTER_RESIDUAL = 5
+} mg_op;
+
+mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, const void* y,
+                         void* out, int32_t nrhs, void* stream);
+
+/* Kernel kinds reported by mg_vcycle_profile. */
+typedef enum {
+  MG_K_JACOBI = 0,          /* smoothing step with Phi_B = w1 I, one pass      */
+  MG_K_RESIDUAL_SCALED = 1, /* delta = theta D^{-1} (f - A u)                  */
+  MG_K_CONV_UPDATE = 2,     /* u += eta Phi_B(delta), mean over N(i)           */
+  MG_K_RESIDUAL = 3,        /* r = f - A u before restriction                  */
+  MG_K_RESTRICT = 4,        /* r_c = P^T Phi_R(r)                              */
+  MG_K_PROLONG = 5,         /* u += Phi_P(P e_c)                               */
+  MG_K_COARSE_CHOL = 6,     /* e_J = A_J^{-1} r_J                              */
+  MG_K_OUTER_RESIDUAL = 7   /* FP64 refinement residual                        */
+} mg_kernel_kind;
+
+typedef struct {
+  int32_t kernel;  /* mg_kernel_kind */
+  int32_t level;
+  float ms;        /* device time between CUDA events around the launch */
+} mg_kernel_time;
+
+/* One V-cycle exactly like mg_vcycle (same kernels, same result), but every
+ * kernel is launched directly with a CUDA event pair around it on `stream`
+ * instead of replaying a graph.  Writes up to max_out records (launch order)
+ * to out and their count to *n_out.  Synchronises the stream. */
+mg_status mg_vcycle_profile(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs,
+                            mg_kernel_time* out, int32_t max_out, int32_t* n_out, void* stream);
+
+/* Static name of a kernel kind ("unknown" if out of range). */
+const char* mg_kernel_name(int32_t kind);
+
+/* Sizes: n_rows_out[l] for l < J (host array of J). */
+mg_status mg_level_sizes(const mg_ctx* ctx, int32_t* n_levels_out, int32_t* n_rows_out);
+
+/* Device bytes mg_setup would allocate for this hierarchy and batch
+ * (used for admission by memory footprint). */
+mg_status mg_footprint_bytes(const mg_hierarchy* h, const mg_csr* A_levels, int32_t max_batch,
+                             int32_t precision, size_t* bytes);
+
+/* Copies the last error message of ctx (or the global one if ctx is NULL). */
+mg_status mg_last_error(const mg_ctx* ctx, char* buf, size_t len);
+
+/* Number of kernels this context has launched (graph replays counted by the
+ * kernels they contain). */
+int64_t mg_kernel_launches(const mg_ctx* ctx);
+
+void mg_destroy(mg_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

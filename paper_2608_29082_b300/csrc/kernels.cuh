@@ -1,0 +1,363 @@
+// Device kernels of the learnable V-cycle (Algorithm 2) for sm_103a.
+//
+// Data layout per level (n rows, B right-hand sides):
+//   vectors      X[n][B], right-hand-side index fastest
+//   off-diagonal SELL-32: rows grouped in slices of 32; entry k of row i at
+//                sl_ptr[i/32] + 32*k + i%32 (column-major inside a slice, so a
+//                warp's loads of one k are contiguous); col = -1 pads a slice
+//   diag, dinv   A_ii and 1/A_ii
+//   invdeg       1/|N(i)|, the mean of the SAGEConv (Sec. 3.2)
+//   p_idx, p_w   prolongation rows, [2][n] (second parent -1 when absent)
+//   r_idx, r_w   restriction R = P^T as coarse-row gather lists, [KR][nc]
+//
+// The off-diagonal pattern of A is the convolution graph (Sec. 2.1), so the
+// same column array serves the residual and the mean aggregation.
+// Arithmetic uses explicit fma() so that every right-hand side is computed in
+// the same order whatever the batch size: results do not depend on B.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mgk {
+
+constexpr int kThreads = 256;
+constexpr int kSlice = 32;
+
+// Parameter block per level, in the order used everywhere:
+// theta, eta, wB1, wB2, wR1, wR2, wP1, wP2.
+enum { P_THETA = 0, P_ETA, P_WB1, P_WB2, P_WR1, P_WR2, P_WP1, P_WP2, P_COUNT };
+
+template <class T>
+struct LV {
+  int n, nc, KR;
+  const int* __restrict__ sl_ptr;
+  const int* __restrict__ col;
+  const T* __restrict__ val;
+  const T* __restrict__ diag;
+  const T* __restrict__ dinv;
+  const T* __restrict__ invdeg;
+  const int* __restrict__ p_idx;
+  const T* __restrict__ p_w;
+  const int* __restrict__ r_idx;
+  const T* __restrict__ r_w;
+};
+
+__device__ __forceinline__ int slice_begin(const int* sl_ptr, int i) {
+  return sl_ptr[i >> 5] + (i & 31);
+}
+
+// sum_{j != i} a_ij x_j  and  sum_{j in N(i)} x_j for one right-hand side.
+template <class T>
+__device__ __forceinline__ void row_offdiag(const LV<T>& L, int i, const T* __restrict__ x,
+                                            int B, int b, T& ax, T& sx) {
+  const int beg = slice_begin(L.sl_ptr, i);
+  const int end = L.sl_ptr[(i >> 5) + 1];
+  T a_acc = T(0), s_acc = T(0);
+  for (int e = beg; e < end; e += kSlice) {
+    const int c = L.col[e];
+    if (c >= 0) {
+      const T xv = x[(size_t)c * B + b];
+      a_acc = fma(L.val[e], xv, a_acc);
+      s_acc += xv;
+    }
+  }
+  ax = a_acc;
+  sx = s_acc;
+}
+
+template <class T>
+__device__ __forceinline__ T row_ax(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
+  const int beg = slice_begin(L.sl_ptr, i);
+  const int end = L.sl_ptr[(i >> 5) + 1];
+  T a_acc = T(0);
+  for (int e = beg; e < end; e += kSlice) {
+    const int c = L.col[e];
+    if (c >= 0) a_acc = fma(L.val[e], x[(size_t)c * B + b], a_acc);
+  }
+  return a_acc;
+}
+
+template <class T>
+__device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
+  const int beg = slice_begin(L.sl_ptr, i);
+  const int end = L.sl_ptr[(i >> 5) + 1];
+  T s_acc = T(0);
+  for (int e = beg; e < end; e += kSlice) {
+    const int c = L.col[e];
+    if (c >= 0) s_acc += x[(size_t)c * B + b];
+  }
+  return s_acc;
+}
+
+// out = alpha * [dinv] * (f - A u).  u_zero: u is taken as 0 and not read.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restrict__ f,
+                                                       const T* __restrict__ u, T* __restrict__ out,
+                                                       int B, const T* __restrict__ prm, int scale,
+                                                       int u_zero) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  T r = f[t];
+  if (!u_zero) {
+    const T ax = row_ax(L, i, u, B, b);
+    r = fma(-L.diag[i], u[t], r) - ax;
+  }
+  if (scale) r = prm[P_THETA] * (r * L.dinv[i]);
+  out[t] = r;
+}
+
+// u <- u + eta * (wB1 * x + wB2 * mean_{N(i)} x)   (Phi_B applied to delta = x)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
+                                                          T* __restrict__ u, int B,
+                                                          const T* __restrict__ prm, int u_zero) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  const T s = row_sum(L, i, x, B, b);
+  const T phi = fma(prm[P_WB1], x[t], prm[P_WB2] * (L.invdeg[i] * s));
+  const T u0 = u_zero ? T(0) : u[t];
+  u[t] = fma(prm[P_ETA], phi, u0);
+}
+
+// Smoothing step with Phi_B = w1 I (w2 = 0): one pass, Jacobi needs the old
+// iterate everywhere, so the result goes to a second buffer.
+// uout = uin + eta * w1 * theta * dinv * (f - A uin)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
+                                                     const T* __restrict__ uin, T* __restrict__ uout,
+                                                     int B, const T* __restrict__ prm, int u_zero) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  T r = f[t];
+  T u0 = T(0);
+  if (!u_zero) {
+    u0 = uin[t];
+    const T ax = row_ax(L, i, uin, B, b);
+    r = fma(-L.diag[i], u0, r) - ax;
+  }
+  const T delta = prm[P_THETA] * (r * L.dinv[i]);
+  uout[t] = fma(prm[P_ETA], prm[P_WB1] * delta, u0);
+}
+
+// fc_I = sum_{i in children(I)} P_iI * (wR1 r_i + wR2 mean_{N(i)} r)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restrict__ r,
+                                                       T* __restrict__ fc, int B,
+                                                       const T* __restrict__ prm, int conv) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.nc * B) return;
+  const int I = (int)(t / B), b = (int)(t - (size_t)I * B);
+  const T w1 = prm[P_WR1], w2 = prm[P_WR2];
+  T acc = T(0);
+  for (int k = 0; k < L.KR; ++k) {
+    const int i = L.r_idx[(size_t)k * L.nc + I];
+    if (i < 0) break;
+    T phi = w1 * r[(size_t)i * B + b];
+    if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
+    acc = fma(L.r_w[(size_t)k * L.nc + I], phi, acc);
+  }
+  fc[t] = acc;
+}
+
+template <class T>
+__device__ __forceinline__ T prolong_at(const LV<T>& L, int j, const T* __restrict__ ec, int B,
+                                        int b) {
+  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
+  T v = T(0);
+  if (a >= 0) v = L.p_w[j] * ec[(size_t)a * B + b];
+  if (c >= 0) v = fma(L.p_w[(size_t)L.n + j], ec[(size_t)c * B + b], v);
+  return v;
+}
+
+// u_i += wP1 (P ec)_i + wP2 mean_{N(i)} (P ec)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restrict__ ec,
+                                                      const T* uin, T* u,
+                                                      int B, const T* __restrict__ prm, int conv) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  T phi = prm[P_WP1] * prolong_at(L, i, ec, B, b);
+  if (conv) {
+    const int beg = slice_begin(L.sl_ptr, i);
+    const int end = L.sl_ptr[(i >> 5) + 1];
+    T s = T(0);
+    for (int e = beg; e < end; e += kSlice) {
+      const int c = L.col[e];
+      if (c >= 0) s += prolong_at(L, c, ec, B, b);
+    }
+    phi = fma(prm[P_WP2], L.invdeg[i] * s, phi);
+  }
+  u[t] = uin[t] + phi;
+}
+
+// Coarsest level: u = A_J^{-1} f by the FP64 Cholesky factor A_J = L L^T.
+// Lc: L column-major (L[i + j n]); Uc: L^T column-major; dinv: 1/L_jj.
+// One warp per right-hand side, column-oriented substitution in shared memory.
+template <class T>
+__global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __restrict__ Uc,
+                              const double* __restrict__ dinv, int n, const T* __restrict__ f,
+                              T* __restrict__ u, int B) {
+  extern __shared__ double ys[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* y = ys + (size_t)warp * n;
+  for (int b = warp; b < B; b += nw) {
+    for (int i = lane; i < n; i += 32) y[i] = (double)f[(size_t)i * B + b];
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {  // L y = f
+      const double yj = y[j] * dinv[j];
+      __syncwarp();
+      for (int i = j + 1 + lane; i < n; i += 32) y[i] = fma(-Lc[i + (size_t)j * n], yj, y[i]);
+      if (lane == 0) y[j] = yj;
+      __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+      const double xj = y[j] * dinv[j];
+      __syncwarp();
+      for (int i = lane; i < j; i += 32) y[i] = fma(-Uc[i + (size_t)j * n], xj, y[i]);
+      if (lane == 0) y[j] = xj;
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) u[(size_t)i * B + b] = (T)y[i];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 outer loop (iterative refinement / plain solve) with deterministic
+// per-right-hand-side reductions.  A block covers R = blockDim/B rows for all
+// B right-hand sides (B <= kThreads); per-block partial sums go to
+// partial[blk * B + b] and are summed in a fixed order by k_reduce.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void block_rows_reduce(double* sh, int R, int B) {
+  const int t = threadIdx.x;
+  const int row = t / B;
+  int p2 = 1;
+  while (p2 < R) p2 <<= 1;
+  for (int s = p2 >> 1; s >= 1; s >>= 1) {
+    if (row < s && row + s < R && t < R * B) sh[t] += sh[t + s * B];
+    __syncthreads();
+  }
+}
+
+// r = f - A u in FP64; optionally rhat = float(r * 2^-sexp[b]); partial sums
+// of r^2.  u_zero: u taken as 0.
+__global__ void __launch_bounds__(kThreads) k_resid64(LV<double> L, const double* __restrict__ f,
+                                                      const double* __restrict__ u,
+                                                      float* __restrict__ rhat,
+                                                      const int* __restrict__ sexp, int B,
+                                                      double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const int R = kThreads / B;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * R + t / B, b = t % B;
+  double r = 0.0;
+  if (t < R * B && i < L.n) {
+    const size_t k = (size_t)i * B + b;
+    const double ax = row_ax(L, i, u, B, b);
+    r = fma(-L.diag[i], u[k], f[k]) - ax;
+    if (rhat) rhat[k] = (float)ldexp(r, -sexp[b]);
+  }
+  sh[t] = r * r;
+  __syncthreads();
+  block_rows_reduce(sh, R, B);
+  if (t < B) partial[(size_t)blockIdx.x * B + t] = sh[t];
+}
+
+// r = f - A u in FP64 with the same arithmetic as k_resid64 (single-step check).
+__global__ void __launch_bounds__(kThreads) k_outer_residual64(LV<double> L,
+                                                               const double* __restrict__ f,
+                                                               const double* __restrict__ u,
+                                                               double* __restrict__ out, int B) {
+  const int R = kThreads / B;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * R + t / B, b = t % B;
+  if (t < R * B && i < L.n) {
+    const size_t k = (size_t)i * B + b;
+    out[k] = fma(-L.diag[i], u[k], f[k]) - row_ax(L, i, u, B, b);
+  }
+}
+
+// partial sums of x^2 (FP64), same block mapping as k_resid64.
+__global__ void __launch_bounds__(kThreads) k_sumsq64(const double* __restrict__ x, int n, int B,
+                                                      double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const int R = kThreads / B;
+  const int t = threadIdx.x;
+  const int i = blockIdx.x * R + t / B;
+  double v = 0.0;
+  if (t < R * B && i < n) v = x[(size_t)i * B + t % B];
+  sh[t] = v * v;
+  __syncthreads();
+  block_rows_reduce(sh, R, B);
+  if (t < B) partial[(size_t)blockIdx.x * B + t] = sh[t];
+}
+
+// out[b] = sum over blocks of partial[blk * B + b]; grid = B blocks.
+__global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ partial, int nblk,
+                                                     int B, double* __restrict__ out) {
+  __shared__ double sh[kThreads];
+  const int b = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += kThreads) s += partial[(size_t)k * B + b];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[b] = sh[0];
+}
+
+// Convergence test per right-hand side; one block.  state[0] = number still
+// active, state[1] = 1 if a residual is not finite.
+__global__ void k_check(const double* __restrict__ rsum, const double* __restrict__ fsum, int B,
+                        const double* __restrict__ tolp, int* __restrict__ active, double* __restrict__ relres,
+                        int* __restrict__ sexp, int* __restrict__ state) {
+  __shared__ int cnt, bad;
+  const double tol = *tolp;
+  if (threadIdx.x == 0) { cnt = 0; bad = 0; }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double rn = sqrt(rsum[b]), fn = sqrt(fsum[b]);
+    const double rel = fn > 0.0 ? rn / fn : rn;
+    relres[b] = rel;
+    if (!isfinite(rel)) atomicAdd(&bad, 1);
+    if (active[b] && !(rel < tol) && isfinite(rel)) atomicAdd(&cnt, 1);
+    else active[b] = 0;
+    sexp[b] = rn > 0.0 && isfinite(rn) ? ilogb(rn) : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) { state[0] = cnt; state[1] = bad; }
+}
+
+// u += 2^sexp[b] * c for the right-hand sides still active (refinement update).
+__global__ void __launch_bounds__(kThreads) k_refine_update(double* __restrict__ u,
+                                                            const float* __restrict__ c,
+                                                            const int* __restrict__ sexp,
+                                                            const int* __restrict__ active, int n,
+                                                            int B, int* __restrict__ iters) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (size_t)B && active[t]) iters[t] += 1;
+  if (t >= (size_t)n * B) return;
+  const int b = (int)(t % B);
+  if (active[b]) u[t] += ldexp((double)c[t], sexp[b]);
+}
+
+// u <- w for the right-hand sides still active (plain solve, B > 1).
+__global__ void __launch_bounds__(kThreads) k_masked_copy(double* __restrict__ u,
+                                                          const double* __restrict__ w,
+                                                          const int* __restrict__ active, int n,
+                                                          int B, int* __restrict__ iters) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (size_t)B && active[t]) iters[t] += 1;
+  if (t >= (size_t)n * B) return;
+  if (active[t % B]) u[t] = w[t];
+}
+
+}  // namespace mgk

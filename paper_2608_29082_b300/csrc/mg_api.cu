@@ -1,0 +1,968 @@
+// libmg.so: context, device set-up and the learnable V-cycle driver.
+//
+// One mg_ctx holds a hierarchy on one GPU.  The V-cycle (Algorithm 2) is
+// issued as a fixed sequence of level kernels, captured once per (buffers,
+// batch) into a CUDA graph and replayed; parameters live in device memory so
+// that changing Theta (training) does not invalidate the graphs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <type_traits>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "kernels.cuh"
+#include "mg.h"
+#include "mg_internal.h"
+
+using mgk::kThreads;
+using mgk::LV;
+
+// ------------------------------------------------------------ errors ------
+
+namespace {
+std::mutex g_err_mu;
+std::string g_err;
+}  // namespace
+
+namespace mgi {
+mg_status set_global_error(mg_status s, const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = msg;
+  return s;
+}
+const std::string& global_error() { return g_err; }
+}  // namespace mgi
+
+// ------------------------------------------------------- host packing -----
+
+namespace {
+
+struct HostLevel {
+  int n = 0, nc = 0, KR = 0;
+  std::vector<int> sl_ptr, col, p_idx, r_idx;
+  std::vector<double> val, diag, dinv, invdeg, p_w, r_w;
+};
+
+template <class T>
+struct DevLevel {
+  int n = 0, nc = 0, KR = 0, nsl = 0;
+  size_t nent = 0;
+  int *sl_ptr = nullptr, *col = nullptr, *p_idx = nullptr, *r_idx = nullptr;
+  T *val = nullptr, *diag = nullptr, *dinv = nullptr, *invdeg = nullptr, *p_w = nullptr,
+    *r_w = nullptr;
+  T *u = nullptr, *f = nullptr, *t = nullptr, *u2 = nullptr;  // workspace [n][maxB]
+  LV<T> view() const {
+    LV<T> v;
+    v.n = n;
+    v.nc = nc;
+    v.KR = KR;
+    v.sl_ptr = sl_ptr;
+    v.col = col;
+    v.val = val;
+    v.diag = diag;
+    v.dinv = dinv;
+    v.invdeg = invdeg;
+    v.p_idx = p_idx;
+    v.p_w = p_w;
+    v.r_idx = r_idx;
+    v.r_w = r_w;
+    return v;
+  }
+};
+
+template <class T>
+void free_level(DevLevel<T>& L) {
+  void* ptrs[] = {L.sl_ptr, L.col, L.p_idx, L.r_idx, L.val, L.diag, L.dinv, L.invdeg,
+                  L.p_w,    L.r_w, L.u,     L.f,     L.t,   L.u2};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  L = DevLevel<T>();
+}
+
+std::string csr_check(const mg_csr& A, int nr, int nc, const char* what) {
+  char buf[256];
+  if (A.n_rows != nr || A.n_cols != nc) {
+    snprintf(buf, sizeof buf, "%s: expected %d x %d, got %d x %d", what, nr, nc, A.n_rows,
+             A.n_cols);
+    return buf;
+  }
+  if (!A.rowptr || (A.nnz > 0 && (!A.col || !A.val)) || A.rowptr[0] != 0 ||
+      A.rowptr[nr] != A.nnz)
+    return std::string(what) + ": inconsistent CSR arrays";
+  for (int i = 0; i < nr; ++i)
+    if (A.rowptr[i + 1] < A.rowptr[i]) return std::string(what) + ": rowptr not monotone";
+  for (int k = 0; k < A.nnz; ++k)
+    if (A.col[k] < 0 || A.col[k] >= nc) return std::string(what) + ": column out of range";
+  return "";
+}
+
+// SELL-32 packing of the off-diagonal part; transfer lists.
+std::string pack_level(const mg_csr& A, const double* invdeg, const mg_csr* P, HostLevel& H) {
+  const int n = A.n_rows;
+  H.n = n;
+  H.diag.assign(n, 0.0);
+  H.dinv.assign(n, 0.0);
+  H.invdeg.assign(invdeg, invdeg + n);
+  std::vector<int> cnt(n, 0);
+  for (int i = 0; i < n; ++i)
+    for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+      if (A.col[k] == i)
+        H.diag[i] += A.val[k];
+      else if (A.val[k] != 0.0)
+        cnt[i]++;
+    }
+  for (int i = 0; i < n; ++i) {
+    if (!(H.diag[i] > 0.0)) return "operator has a non-positive diagonal entry";
+    if (!(invdeg[i] > 0.0) || !std::isfinite(invdeg[i])) return "inv_deg must be positive";
+    H.dinv[i] = 1.0 / H.diag[i];
+  }
+  const int nsl = (n + mgk::kSlice - 1) / mgk::kSlice;
+  H.sl_ptr.assign(nsl + 1, 0);
+  for (int s = 0; s < nsl; ++s) {
+    int K = 0;
+    for (int i = s * 32; i < std::min(n, s * 32 + 32); ++i) K = std::max(K, cnt[i]);
+    H.sl_ptr[s + 1] = H.sl_ptr[s] + 32 * K;
+  }
+  H.col.assign(H.sl_ptr[nsl], -1);
+  H.val.assign(H.sl_ptr[nsl], 0.0);
+  for (int i = 0; i < n; ++i) {
+    int k = 0;
+    const int base = H.sl_ptr[i / 32] + (i % 32);
+    for (int e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
+      if (A.col[e] == i || A.val[e] == 0.0) continue;
+      H.col[base + 32 * k] = A.col[e];
+      H.val[base + 32 * k] = A.val[e];
+      ++k;
+    }
+  }
+  if (P) {
+    const int nc = P->n_cols;
+    H.nc = nc;
+    H.p_idx.assign(2 * (size_t)n, -1);
+    H.p_w.assign(2 * (size_t)n, 0.0);
+    std::vector<int> ccount(nc, 0);
+    for (int i = 0; i < n; ++i) {
+      int k = 0;
+      for (int e = P->rowptr[i]; e < P->rowptr[i + 1]; ++e) {
+        if (P->val[e] == 0.0) continue;
+        if (k == 2) return "prolongation rows may hold at most 2 entries";
+        H.p_idx[(size_t)k * n + i] = P->col[e];
+        H.p_w[(size_t)k * n + i] = P->val[e];
+        ccount[P->col[e]]++;
+        ++k;
+      }
+    }
+    int KR = 0;
+    for (int I = 0; I < nc; ++I) KR = std::max(KR, ccount[I]);
+    H.KR = KR;
+    H.r_idx.assign((size_t)KR * nc, -1);
+    H.r_w.assign((size_t)KR * nc, 0.0);
+    std::vector<int> fill(nc, 0);
+    for (int i = 0; i < n; ++i)
+      for (int k = 0; k < 2; ++k) {
+        const int I = H.p_idx[(size_t)k * n + i];
+        if (I < 0) continue;
+        H.r_idx[(size_t)fill[I] * nc + I] = i;
+        H.r_w[(size_t)fill[I] * nc + I] = H.p_w[(size_t)k * n + i];
+        fill[I]++;
+      }
+  }
+  return "";
+}
+
+// Dense FP64 Cholesky A = L L^T (column-major L).  Returns false if A is not
+// numerically SPD.
+bool cholesky(const mg_csr& A, std::vector<double>& Lc) {
+  const int n = A.n_rows;
+  Lc.assign((size_t)n * n, 0.0);
+  std::vector<double> M((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) M[(size_t)i * n + A.col[k]] += A.val[k];
+  for (int j = 0; j < n; ++j) {
+    double d = M[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) d -= Lc[j + (size_t)k * n] * Lc[j + (size_t)k * n];
+    if (!(d > 0.0)) return false;
+    const double ljj = std::sqrt(d);
+    Lc[j + (size_t)j * n] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double s = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= Lc[i + (size_t)k * n] * Lc[j + (size_t)k * n];
+      Lc[i + (size_t)j * n] = s / ljj;
+    }
+  }
+  return true;
+}
+
+struct GraphEntry {
+  cudaGraphExec_t exec = nullptr;
+  int nkernels = 0;
+};
+
+}  // namespace
+
+// ------------------------------------------------------------ context -----
+
+struct mg_ctx {
+  int J = 0, prec = 64, maxB = 1, nJ = 0;
+  std::vector<int> n;
+  std::vector<DevLevel<double>> d64;
+  std::vector<DevLevel<float>> d32;
+  double *cholL = nullptr, *cholU = nullptr, *cholDinv = nullptr;
+  int nu_pre = 2, nu_post = 2;
+  std::vector<double> prm;  // [J-1][P_COUNT]
+  double* prm64 = nullptr;
+  float* prm32 = nullptr;
+  bool prm_dirty = true;
+  uint32_t structure = 0;
+  // outer-loop workspace
+  int nblk_max = 0;
+  double *partial = nullptr, *rsum = nullptr, *fsum = nullptr, *relres = nullptr, *w64 = nullptr;
+  int *active = nullptr, *iters = nullptr, *sexp = nullptr, *sexp_prev = nullptr,
+      *state = nullptr;
+  float *c32 = nullptr, *rhat32 = nullptr;
+  int* h_state = nullptr;  // pinned [2]
+  double* tol_dev = nullptr;
+  double *hf = nullptr, *hu = nullptr;  // device buffers for mg_solve_host
+  cudaStream_t cap = nullptr;
+  std::map<std::tuple<int, const void*, const void*, int, uint32_t>, GraphEntry> graphs;
+  std::string err;
+  int64_t launches = 0;
+
+  mg_status fail(mg_status s, const std::string& m) {
+    err = m;
+    return s;
+  }
+};
+
+#define MG_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return c->fail(e_ == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,          \
+                     std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+namespace {
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& src) {
+  if (src.empty()) {
+    *dst = nullptr;
+    return cudaSuccess;
+  }
+  cudaError_t e = cudaMalloc((void**)dst, src.size() * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+template <class T>
+std::vector<T> cast(const std::vector<double>& v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+template <class T>
+cudaError_t upload_level(const HostLevel& H, DevLevel<T>& D, int maxB, bool vectors) {
+  cudaError_t e;
+  D.n = H.n;
+  D.nc = H.nc;
+  D.KR = H.KR;
+  D.nsl = (int)H.sl_ptr.size() - 1;
+  D.nent = H.col.size();
+  if ((e = upload(&D.sl_ptr, H.sl_ptr)) != cudaSuccess) return e;
+  if ((e = upload(&D.col, H.col)) != cudaSuccess) return e;
+  if ((e = upload(&D.val, cast<T>(H.val))) != cudaSuccess) return e;
+  if ((e = upload(&D.diag, cast<T>(H.diag))) != cudaSuccess) return e;
+  if ((e = upload(&D.dinv, cast<T>(H.dinv))) != cudaSuccess) return e;
+  if ((e = upload(&D.invdeg, cast<T>(H.invdeg))) != cudaSuccess) return e;
+  if ((e = upload(&D.p_idx, H.p_idx)) != cudaSuccess) return e;
+  if ((e = upload(&D.p_w, cast<T>(H.p_w))) != cudaSuccess) return e;
+  if ((e = upload(&D.r_idx, H.r_idx)) != cudaSuccess) return e;
+  if ((e = upload(&D.r_w, cast<T>(H.r_w))) != cudaSuccess) return e;
+  if (vectors) {
+    const size_t bytes = (size_t)H.n * maxB * sizeof(T);
+    for (T** p : {&D.u, &D.f, &D.t, &D.u2}) {
+      if ((e = cudaMalloc((void**)p, bytes)) != cudaSuccess) return e;
+      if ((e = cudaMemset(*p, 0, bytes)) != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+uint32_t structure_of(const std::vector<double>& prm, int J) {
+  uint32_t s = 0;
+  for (int l = 0; l < J - 1 && l < 10; ++l) {
+    const double* p = &prm[(size_t)l * mgk::P_COUNT];
+    s |= (p[mgk::P_WB2] != 0.0 ? 1u : 0u) << (3 * l);
+    s |= (p[mgk::P_WR2] != 0.0 ? 1u : 0u) << (3 * l + 1);
+    s |= (p[mgk::P_WP2] != 0.0 ? 1u : 0u) << (3 * l + 2);
+  }
+  if (J - 1 > 10) s |= 1u << 31;  // deep hierarchies: recapture on every change
+  return s;
+}
+
+std::string read_params(const mg_params* p, int J, std::vector<double>& out, int& nu_pre,
+                        int& nu_post) {
+  if (!p) return "params is NULL";
+  if (p->n_levels != J) return "params.n_levels does not match the hierarchy";
+  if (p->nu_pre < 0 || p->nu_post < 0 || p->nu_pre > 64 || p->nu_post > 64)
+    return "smoothing step counts must be in [0, 64]";
+  if (!p->theta || !p->eta || !p->wB || !p->wR || !p->wP) return "params arrays are NULL";
+  out.assign((size_t)(J - 1) * mgk::P_COUNT, 0.0);
+  for (int l = 0; l < J - 1; ++l) {
+    double* q = &out[(size_t)l * mgk::P_COUNT];
+    q[mgk::P_THETA] = p->theta[l];
+    q[mgk::P_ETA] = p->eta[l];
+    q[mgk::P_WB1] = p->wB[2 * l];
+    q[mgk::P_WB2] = p->wB[2 * l + 1];
+    q[mgk::P_WR1] = p->wR[2 * l];
+    q[mgk::P_WR2] = p->wR[2 * l + 1];
+    q[mgk::P_WP1] = p->wP[2 * l];
+    q[mgk::P_WP2] = p->wP[2 * l + 1];
+  }
+  for (double v : out)
+    if (!std::isfinite(v)) return "params must be finite";
+  nu_pre = p->nu_pre;
+  nu_post = p->nu_post;
+  return "";
+}
+
+inline dim3 grid_for(size_t work) { return dim3((unsigned)((work + kThreads - 1) / kThreads)); }
+
+// Issues the kernels of one V-cycle (or one level step) on a stream.
+template <class T>
+struct Issue {
+  mg_ctx* c;
+  std::vector<DevLevel<T>>& L;
+  const T* prm;  // device [J-1][P_COUNT]
+  cudaStream_t s;
+  int B;
+  int nk = 0;
+  // optional per-kernel timing: an event pair around every launch
+  std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>>* rec = nullptr;
+
+  void pre(int kind, int lev) {
+    if (!rec) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+    rec->emplace_back(kind, lev, a, b);
+  }
+  void post() {
+    if (rec) cudaEventRecord(std::get<3>(rec->back()), s);
+  }
+
+  const T* P(int lev) const { return prm + (size_t)lev * mgk::P_COUNT; }
+  bool conv(int lev, int which) const {
+    return c->prm[(size_t)lev * mgk::P_COUNT + which] != 0.0;
+  }
+
+  // nu smoothing steps on level lev; u updated in place.  zero: u is 0 on entry.
+  void smooth(int lev, const T* f, T* u, int nu, bool zero) {
+    DevLevel<T>& D = L[lev];
+    const dim3 g = grid_for((size_t)D.n * B);
+    if (nu == 0) {
+      if (zero) cudaMemsetAsync(u, 0, (size_t)D.n * B * sizeof(T), s);
+      return;
+    }
+    if (!conv(lev, mgk::P_WB2)) {
+      T* cur = u;
+      T* oth = D.u2;
+      for (int k = 0; k < nu; ++k) {
+        pre(MG_K_JACOBI, lev);
+        mgk::k_jacobi<T><<<g, kThreads, 0, s>>>(D.view(), f, cur, oth, B, P(lev), zero && k == 0);
+        post();
+        ++nk;
+        std::swap(cur, oth);
+      }
+      if (cur != u) cudaMemcpyAsync(u, cur, (size_t)D.n * B * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      return;
+    }
+    for (int k = 0; k < nu; ++k) {
+      const int z = zero && k == 0;
+      pre(MG_K_RESIDUAL_SCALED, lev);
+      mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, u, D.t, B, P(lev), 1, z);
+      post();
+      pre(MG_K_CONV_UPDATE, lev);
+      mgk::k_conv_update<T><<<g, kThreads, 0, s>>>(D.view(), D.t, u, B, P(lev), z);
+      post();
+      nk += 2;
+    }
+  }
+
+  void restrict_(int lev, const T* f, const T* u) {
+    DevLevel<T>& D = L[lev];
+    pre(MG_K_RESIDUAL, lev);
+    mgk::k_residual<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), f, u, D.t, B,
+                                                                      P(lev), 0, 0);
+    post();
+    pre(MG_K_RESTRICT, lev);
+    mgk::k_restrict<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
+        D.view(), D.t, L[lev + 1].f, B, P(lev), conv(lev, mgk::P_WR2));
+    post();
+    nk += 2;
+  }
+
+  void prolong(int lev, const T* ec, T* u) {
+    DevLevel<T>& D = L[lev];
+    pre(MG_K_PROLONG, lev);
+    mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
+        D.view(), ec, u, u, B, P(lev), conv(lev, mgk::P_WP2));
+    post();
+    ++nk;
+  }
+
+  void coarse(const T* f, T* u) {
+    const int nw = std::max(1, std::min(std::min(B, 8), 6144 / std::max(1, c->nJ)));
+    pre(MG_K_COARSE_CHOL, c->J - 1);
+    mgk::k_coarse_chol<T><<<1, 32 * nw, (size_t)nw * c->nJ * sizeof(double), s>>>(
+        c->cholL, c->cholU, c->cholDinv, c->nJ, f, u, B);
+    post();
+    ++nk;
+  }
+
+  // Algorithm 2 from level 0 with f0/u0 as the level-0 vectors.
+  void vcycle(const T* f0, T* u0, bool u0_zero) {
+    const int J = c->J;
+    for (int lev = 0; lev < J - 1; ++lev) {
+      const T* f = lev == 0 ? f0 : L[lev].f;
+      T* u = lev == 0 ? u0 : L[lev].u;
+      smooth(lev, f, u, c->nu_pre, lev == 0 ? u0_zero : true);
+      restrict_(lev, f, u);
+    }
+    coarse(L[J - 1].f, L[J - 1].u);
+    for (int lev = J - 2; lev >= 0; --lev) {
+      const T* f = lev == 0 ? f0 : L[lev].f;
+      T* u = lev == 0 ? u0 : L[lev].u;
+      prolong(lev, L[lev + 1].u, u);
+      smooth(lev, f, u, c->nu_post, false);
+    }
+  }
+};
+
+mg_status sync_params(mg_ctx* c, cudaStream_t s) {
+  if (!c->prm_dirty) return MG_OK;
+  if (c->prec == 64) {
+    MG_CUDA(cudaMemcpyAsync(c->prm64, c->prm.data(), c->prm.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s));
+  } else {
+    std::vector<float> f(c->prm.begin(), c->prm.end());
+    MG_CUDA(cudaMemcpyAsync(c->prm32, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice,
+                            s));
+    // the FP32 copy is pageable and goes out of scope: make the copy complete
+    MG_CUDA(cudaStreamSynchronize(s));
+  }
+  c->prm_dirty = false;
+  return MG_OK;
+}
+
+// Captures fn(stream) into a graph stored under key (or reuses it) and
+// launches it on s.
+template <class Fn>
+mg_status run_graph(mg_ctx* c, const std::tuple<int, const void*, const void*, int, uint32_t>& key,
+                    cudaStream_t s, Fn&& fn) {
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    MG_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+    int nk = fn(c->cap);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return c->fail(MG_ERR_CUDA, std::string("graph capture failed: ") +
+                                      cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    }
+    GraphEntry ge;
+    ge.nkernels = nk;
+    cudaError_t e3 = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess)
+      return c->fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
+    if (c->graphs.size() > 64) {  // bounded cache
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+    }
+    it = c->graphs.emplace(key, ge).first;
+  }
+  MG_CUDA(cudaGraphLaunch(it->second.exec, s));
+  c->launches += it->second.nkernels;
+  return MG_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ C ABI -------
+
+extern "C" mg_status mg_last_error(const mg_ctx* ctx, char* buf, size_t len) {
+  if (!buf || len == 0) return MG_ERR_INVALID;
+  std::string m;
+  if (ctx) {
+    m = ctx->err;
+  } else {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    m = g_err;
+  }
+  snprintf(buf, len, "%s", m.c_str());
+  return MG_OK;
+}
+
+extern "C" int64_t mg_kernel_launches(const mg_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+extern "C" void mg_destroy(mg_ctx* c) {
+  if (!c) return;
+  if (c->cap) cudaStreamSynchronize(c->cap);
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  for (auto& L : c->d64) free_level(L);
+  for (auto& L : c->d32) free_level(L);
+  void* ptrs[] = {c->cholL,  c->cholU,  c->cholDinv, c->prm64,  c->prm32, c->partial,
+                  c->rsum,   c->fsum,   c->relres,   c->w64,    c->active, c->iters,
+                  c->sexp,   c->sexp_prev, c->state, c->c32,    c->rhat32, c->hf, c->hu,
+                  c->tol_dev};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->h_state) cudaFreeHost(c->h_state);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+static mg_status validate_hierarchy(const mg_hierarchy* h, const mg_csr* A, int32_t maxB,
+                                    int32_t precision, std::string& why) {
+  if (!h || !A) { why = "hierarchy or A_levels is NULL"; return MG_ERR_INVALID; }
+  if (h->n_levels < 2 || h->n_levels > 32) { why = "n_levels must be in [2, 32]"; return MG_ERR_INVALID; }
+  if (!h->P || !h->inv_deg) { why = "hierarchy arrays are NULL"; return MG_ERR_INVALID; }
+  if (maxB < 1 || maxB > kThreads) { why = "max_batch must be in [1, 256]"; return MG_ERR_INVALID; }
+  if (precision != 64 && precision != 32) { why = "precision must be 64 or 32"; return MG_ERR_INVALID; }
+  const int J = h->n_levels;
+  for (int l = 0; l < J; ++l) {
+    const int n = A[l].n_rows;
+    if (n < 1) { why = "empty level"; return MG_ERR_INVALID; }
+    std::string m = csr_check(A[l], n, n, "A_levels");
+    if (!m.empty()) { why = m + " (level " + std::to_string(l) + ")"; return MG_ERR_INVALID; }
+    if (!h->inv_deg[l]) { why = "inv_deg is NULL"; return MG_ERR_INVALID; }
+    if (l < J - 1) {
+      m = csr_check(h->P[l], n, A[l + 1].n_rows, "P");
+      if (!m.empty()) { why = m + " (level " + std::to_string(l) + ")"; return MG_ERR_INVALID; }
+    }
+  }
+  if (A[J - 1].n_rows > 2048) { why = "coarsest level larger than 2048 rows"; return MG_ERR_INVALID; }
+  return MG_OK;
+}
+
+extern "C" mg_status mg_footprint_bytes(const mg_hierarchy* h, const mg_csr* A, int32_t maxB,
+                                        int32_t precision, size_t* bytes) {
+  std::string why;
+  if (!bytes) return mgi::set_global_error(MG_ERR_INVALID, "bytes is NULL");
+  mg_status st = validate_hierarchy(h, A, maxB, precision, why);
+  if (st != MG_OK) return mgi::set_global_error(st, "mg_footprint_bytes: " + why);
+  const size_t tb = precision == 64 ? 8 : 4;
+  size_t total = 0;
+  for (int l = 0; l < h->n_levels; ++l) {
+    const size_t n = A[l].n_rows;
+    const size_t nnz = A[l].nnz;
+    // SELL (padding bounded by slice maxima: estimate with nnz), diag/dinv/invdeg,
+    // transfer lists, 4 work vectors.
+    total += nnz * (4 + tb) + 3 * n * tb + 2 * n * (4 + tb) + 8 * n * (4 + tb) +
+             4 * n * maxB * tb;
+    if (precision == 32 && l == 0) total += nnz * 12 + 3 * n * 8;
+  }
+  const size_t nJ = A[h->n_levels - 1].n_rows;
+  total += 3 * nJ * nJ * 8;
+  const size_t n0 = A[0].n_rows;
+  total += 3 * n0 * maxB * 8 + n0 * maxB * 8;  // outer-loop vectors
+  *bytes = total;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr* A,
+                              const mg_params* p, int32_t maxB, int32_t precision, void* stream) {
+  if (!out) return mgi::set_global_error(MG_ERR_INVALID, "mg_setup: out is NULL");
+  *out = nullptr;
+  std::string why;
+  mg_status st = validate_hierarchy(h, A, maxB, precision, why);
+  if (st != MG_OK) return mgi::set_global_error(st, "mg_setup: " + why);
+  const int J = h->n_levels;
+  mg_ctx* c = new mg_ctx();
+  c->J = J;
+  c->prec = precision;
+  c->maxB = maxB;
+  why = read_params(p, J, c->prm, c->nu_pre, c->nu_post);
+  if (!why.empty()) {
+    delete c;
+    return mgi::set_global_error(MG_ERR_INVALID, "mg_setup: " + why);
+  }
+  c->structure = structure_of(c->prm, J);
+  // pack on the host
+  std::vector<HostLevel> H(J);
+  for (int l = 0; l < J; ++l) {
+    why = pack_level(A[l], h->inv_deg[l], l < J - 1 ? &h->P[l] : nullptr, H[l]);
+    if (!why.empty()) {
+      delete c;
+      return mgi::set_global_error(MG_ERR_INVALID,
+                                   "mg_setup: level " + std::to_string(l) + ": " + why);
+    }
+    c->n.push_back(H[l].n);
+  }
+  std::vector<double> Lc;
+  if (!cholesky(A[J - 1], Lc)) {
+    delete c;
+    return mgi::set_global_error(MG_ERR_NOT_SPD, "mg_setup: coarsest operator is not SPD");
+  }
+  const int nJ = A[J - 1].n_rows;
+  c->nJ = nJ;
+  std::vector<double> Uc((size_t)nJ * nJ), dj(nJ);
+  for (int i = 0; i < nJ; ++i)
+    for (int j = 0; j < nJ; ++j) Uc[i + (size_t)j * nJ] = Lc[j + (size_t)i * nJ];
+  for (int j = 0; j < nJ; ++j) dj[j] = 1.0 / Lc[j + (size_t)j * nJ];
+
+  auto bail = [&](cudaError_t e) {
+    std::string m = std::string("mg_setup: ") + cudaGetErrorString(e);
+    mg_destroy(c);
+    return mgi::set_global_error(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA, m);
+  };
+  cudaError_t e;
+  if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+  if (precision == 64) {
+    c->d64.resize(J);
+    for (int l = 0; l < J; ++l)
+      if ((e = upload_level(H[l], c->d64[l], maxB, true)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&c->prm64, c->prm.size() * sizeof(double))) != cudaSuccess) return bail(e);
+  } else {
+    c->d32.resize(J);
+    for (int l = 0; l < J; ++l)
+      if ((e = upload_level(H[l], c->d32[l], maxB, true)) != cudaSuccess) return bail(e);
+    c->d64.resize(1);  // FP64 finest operator for the refinement residual
+    HostLevel H0 = H[0];
+    H0.p_idx.clear(); H0.p_w.clear(); H0.r_idx.clear(); H0.r_w.clear(); H0.nc = 0; H0.KR = 0;
+    if ((e = upload_level(H0, c->d64[0], maxB, false)) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&c->prm32, c->prm.size() * sizeof(float))) != cudaSuccess) return bail(e);
+  }
+  if ((e = upload(&c->cholL, Lc)) != cudaSuccess) return bail(e);
+  if ((e = upload(&c->cholU, Uc)) != cudaSuccess) return bail(e);
+  if ((e = upload(&c->cholDinv, dj)) != cudaSuccess) return bail(e);
+  // outer-loop workspace
+  const int n0 = H[0].n;
+  c->nblk_max = n0;  // R >= 1 rows per block
+  const size_t v64 = (size_t)n0 * maxB * sizeof(double);
+  if ((e = cudaMalloc(&c->partial, (size_t)c->nblk_max * maxB * sizeof(double))) != cudaSuccess) return bail(e);
+  for (double** q : {&c->rsum, &c->fsum, &c->relres})
+    if ((e = cudaMalloc(q, maxB * sizeof(double))) != cudaSuccess) return bail(e);
+  for (int** q : {&c->active, &c->iters, &c->sexp, &c->sexp_prev})
+    if ((e = cudaMalloc(q, maxB * sizeof(int))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->state, 2 * sizeof(int))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->tol_dev, sizeof(double))) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->h_state, 2 * sizeof(int))) != cudaSuccess) return bail(e);
+  if (precision == 64) {
+    if ((e = cudaMalloc(&c->w64, v64)) != cudaSuccess) return bail(e);
+  } else {
+    if ((e = cudaMalloc(&c->c32, (size_t)n0 * maxB * sizeof(float))) != cudaSuccess) return bail(e);
+    if ((e = cudaMalloc(&c->rhat32, (size_t)n0 * maxB * sizeof(float))) != cudaSuccess) return bail(e);
+  }
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e);
+  *out = c;
+  (void)stream;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_set_params(mg_ctx* c, const mg_params* p) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_params: ctx is NULL");
+  std::vector<double> prm;
+  int a, b;
+  std::string why = read_params(p, c->J, prm, a, b);
+  if (!why.empty()) return c->fail(MG_ERR_INVALID, "mg_set_params: " + why);
+  if (a != c->nu_pre || b != c->nu_post) {  // the cycle's shape changed
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+  }
+  c->prm = prm;
+  c->nu_pre = a;
+  c->nu_post = b;
+  c->structure = structure_of(prm, c->J);
+  c->prm_dirty = true;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_level_sizes(const mg_ctx* c, int32_t* J, int32_t* n) {
+  if (!c || !J) return MG_ERR_INVALID;
+  *J = c->J;
+  if (n)
+    for (int l = 0; l < c->J; ++l) n[l] = c->n[l];
+  return MG_OK;
+}
+
+extern "C" mg_status mg_vcycle(mg_ctx* c, const void* f, void* u, int32_t B, void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_vcycle: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB) return c->fail(MG_ERR_INVALID, "mg_vcycle: bad arguments");
+  if (f == u) return c->fail(MG_ERR_INVALID, "mg_vcycle: f and u must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  auto key = std::make_tuple(0, f, (const void*)u, (int)B, c->structure);
+  if (c->prec == 64)
+    return run_graph(c, key, s, [&](cudaStream_t cs) {
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
+      is.vcycle((const double*)f, (double*)u, false);
+      return is.nk;
+    });
+  return run_graph(c, key, s, [&](cudaStream_t cs) {
+    Issue<float> is{c, c->d32, c->prm32, cs, B};
+    is.vcycle((const float*)f, (float*)u, false);
+    return is.nk;
+  });
+}
+
+namespace {
+
+__global__ void k_init_solve(const double* __restrict__ fsum, int B, int* __restrict__ active,
+                             int* __restrict__ iters, int* __restrict__ sexp) {
+  const int b = threadIdx.x + blockIdx.x * blockDim.x;
+  if (b >= B) return;
+  active[b] = 1;
+  iters[b] = 0;
+  const double fn = sqrt(fsum[b]);
+  sexp[b] = fn > 0.0 && isfinite(fn) ? ilogb(fn) : 0;
+}
+
+__global__ void k_shift_sexp(int* __restrict__ sexp, int* __restrict__ sexp_prev, int B) {
+  const int b = threadIdx.x;
+  if (b < B) sexp_prev[b] = sexp[b];
+}
+
+__global__ void k_bump_iters(const int* __restrict__ active, int* __restrict__ iters, int B) {
+  const int b = threadIdx.x;
+  if (b < B && active[b]) iters[b] += 1;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
+                              int32_t max_iter, int32_t* iters_out, double* relres_out,
+                              void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB || max_iter < 0 || !(tol > 0.0))
+    return c->fail(MG_ERR_INVALID, "mg_solve: bad arguments");
+  if ((const void*)f == (const void*)u) return c->fail(MG_ERR_INVALID, "mg_solve: f and u alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  const int n0 = c->n[0];
+  const int R = kThreads / B;
+  const int nblk = (n0 + R - 1) / R;
+  const LV<double> L0 = c->d64[0].view();
+  const bool p32 = c->prec == 32;
+
+  // residual of the current iterate, its norms and the convergence test
+  auto check_tail = [&](cudaStream_t cs) {
+    mgk::k_resid64<<<nblk, kThreads, 0, cs>>>(L0, f, u, p32 ? c->rhat32 : nullptr, c->sexp, B,
+                                              c->partial);
+    mgk::k_reduce<<<B, kThreads, 0, cs>>>(c->partial, nblk, B, c->rsum);
+    if (p32) k_shift_sexp<<<1, kThreads, 0, cs>>>(c->sexp, c->sexp_prev, B);
+    mgk::k_check<<<1, kThreads, 0, cs>>>(c->rsum, c->fsum, B, c->tol_dev, c->active, c->relres, c->sexp,
+                                         c->state);
+    return p32 ? 4 : 3;
+  };
+  MG_CUDA(cudaMemcpyAsync(c->tol_dev, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
+  auto kinit = std::make_tuple(10, (const void*)f, (const void*)u, (int)B, c->structure);
+  st = run_graph(c, kinit, s, [&](cudaStream_t cs) {
+    mgk::k_sumsq64<<<nblk, kThreads, 0, cs>>>(f, n0, B, c->partial);
+    mgk::k_reduce<<<B, kThreads, 0, cs>>>(c->partial, nblk, B, c->fsum);
+    k_init_solve<<<1, kThreads, 0, cs>>>(c->fsum, B, c->active, c->iters, c->sexp);
+    return 3 + check_tail(cs);
+  });
+  if (st != MG_OK) return st;
+  auto kiter = std::make_tuple(11, (const void*)f, (const void*)u, (int)B, c->structure);
+  int it = 0;
+  mg_status result = MG_OK;
+  for (;;) {
+    MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    if (c->h_state[1]) { result = MG_ERR_DIVERGED; break; }
+    if (c->h_state[0] == 0) break;
+    if (it == max_iter) { result = MG_NOT_CONVERGED; break; }
+    st = run_graph(c, kiter, s, [&](cudaStream_t cs) {
+      int nk = 0;
+      if (p32) {
+        Issue<float> is{c, c->d32, c->prm32, cs, B};
+        is.vcycle(c->rhat32, c->c32, true);
+        nk += is.nk;
+        mgk::k_refine_update<<<grid_for((size_t)n0 * B), kThreads, 0, cs>>>(
+            u, c->c32, c->sexp_prev, c->active, n0, B, c->iters);
+        ++nk;
+      } else if (B == 1) {
+        Issue<double> is{c, c->d64, c->prm64, cs, B};
+        is.vcycle(f, u, false);
+        nk += is.nk;
+        k_bump_iters<<<1, kThreads, 0, cs>>>(c->active, c->iters, B);
+        ++nk;
+      } else {
+        cudaMemcpyAsync(c->w64, u, (size_t)n0 * B * sizeof(double), cudaMemcpyDeviceToDevice, cs);
+        Issue<double> is{c, c->d64, c->prm64, cs, B};
+        is.vcycle(f, c->w64, false);
+        nk += is.nk;
+        mgk::k_masked_copy<<<grid_for((size_t)n0 * B), kThreads, 0, cs>>>(u, c->w64, c->active,
+                                                                           n0, B, c->iters);
+        ++nk;
+      }
+      return nk + check_tail(cs);
+    });
+    if (st != MG_OK) return st;
+    ++it;
+  }
+  if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
+  if (relres_out)
+    MG_CUDA(cudaMemcpy(relres_out, c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
+  if (result == MG_ERR_DIVERGED) c->err = "mg_solve: non-finite residual";
+  if (result == MG_NOT_CONVERGED) c->err = "mg_solve: tolerance not met within max_iter";
+  return result;
+}
+
+extern "C" mg_status mg_solve_host(mg_ctx* c, const double* fh, double* uh, int32_t B, double tol,
+                                   int32_t max_iter, int32_t* iters_out, double* relres_out,
+                                   void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve_host: ctx is NULL");
+  if (!fh || !uh || B < 1 || B > c->maxB) return c->fail(MG_ERR_INVALID, "mg_solve_host: bad arguments");
+  const size_t bytes = (size_t)c->n[0] * B * sizeof(double);
+  if (!c->hf) {
+    MG_CUDA(cudaMalloc(&c->hf, (size_t)c->n[0] * c->maxB * sizeof(double)));
+    MG_CUDA(cudaMalloc(&c->hu, (size_t)c->n[0] * c->maxB * sizeof(double)));
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  MG_CUDA(cudaMemcpyAsync(c->hf, fh, bytes, cudaMemcpyHostToDevice, s));
+  MG_CUDA(cudaMemcpyAsync(c->hu, uh, bytes, cudaMemcpyHostToDevice, s));
+  mg_status st = mg_solve(c, c->hf, c->hu, B, tol, max_iter, iters_out, relres_out, stream);
+  if (st < 0) return st;
+  MG_CUDA(cudaMemcpyAsync(uh, c->hu, bytes, cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  return st;
+}
+
+extern "C" mg_status mg_level_apply(mg_ctx* c, int32_t lev, int32_t op, const void* x,
+                                    const void* y, void* out, int32_t B, void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_level_apply: ctx is NULL");
+  if (lev < 0 || lev >= c->J || B < 1 || B > c->maxB || !x || !out)
+    return c->fail(MG_ERR_INVALID, "mg_level_apply: bad arguments");
+  if ((op == MG_OP_SMOOTH || op == MG_OP_RESIDUAL || op == MG_OP_PROLONG) && !y)
+    return c->fail(MG_ERR_INVALID, "mg_level_apply: y is required for this op");
+  if ((op == MG_OP_RESTRICT || op == MG_OP_PROLONG || op == MG_OP_SMOOTH) && lev == c->J - 1)
+    return c->fail(MG_ERR_INVALID, "mg_level_apply: no transfer/smoother on the coarsest level");
+  if (op == MG_OP_COARSE && lev != c->J - 1)
+    return c->fail(MG_ERR_INVALID, "mg_level_apply: coarse solve only on the coarsest level");
+  if (op < MG_OP_SMOOTH || op > MG_OP_OUTER_RESIDUAL)
+    return c->fail(MG_ERR_INVALID, "mg_level_apply: op");
+  if (op == MG_OP_OUTER_RESIDUAL) {
+    if (lev != 0 || !y) return c->fail(MG_ERR_INVALID, "mg_level_apply: outer residual needs level 0, f, u");
+    if (out == x || out == y) return c->fail(MG_ERR_INVALID, "mg_level_apply: out aliases an input");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int R = kThreads / B;
+    const int nblk = (c->n[0] + R - 1) / R;
+    mgk::k_outer_residual64<<<nblk, kThreads, 0, s>>>(c->d64[0].view(), (const double*)x,
+                                                       (const double*)y, (double*)out, B);
+    MG_CUDA(cudaGetLastError());
+    c->launches += 1;
+    return MG_OK;
+  }
+  if (out == x || out == y) return c->fail(MG_ERR_INVALID, "mg_level_apply: out aliases an input");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  auto go = [&](auto& levels, auto* prm) -> mg_status {
+    using T = std::remove_pointer_t<decltype(prm)>;
+    Issue<T> is{c, levels, prm, s, B};
+    auto& D = levels[lev];
+    const T* X = (const T*)x;
+    const T* Y = (const T*)y;
+    T* O = (T*)out;
+    const size_t vb = (size_t)D.n * B * sizeof(T);
+    switch (op) {
+      case MG_OP_SMOOTH:
+        MG_CUDA(cudaMemcpyAsync(O, Y, vb, cudaMemcpyDeviceToDevice, s));
+        is.smooth(lev, X, O, 1, false);
+        break;
+      case MG_OP_RESIDUAL:
+        mgk::k_residual<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), X, Y, O, B,
+                                                                          is.P(lev), 0, 0);
+        is.nk++;
+        break;
+      case MG_OP_RESTRICT:
+        mgk::k_restrict<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
+            D.view(), X, O, B, is.P(lev), is.conv(lev, mgk::P_WR2));
+        is.nk++;
+        break;
+      case MG_OP_PROLONG:
+        mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
+            D.view(), X, Y, O, B, is.P(lev), is.conv(lev, mgk::P_WP2));
+        is.nk++;
+        break;
+      case MG_OP_COARSE:
+        is.coarse(X, O);
+        break;
+    }
+    MG_CUDA(cudaGetLastError());
+    c->launches += is.nk;
+    return MG_OK;
+  };
+  if (c->prec == 64) return go(c->d64, c->prm64);
+  return go(c->d32, c->prm32);
+}
+
+extern "C" const char* mg_kernel_name(int32_t kind) {
+  switch (kind) {
+    case MG_K_JACOBI: return "jacobi_smooth";
+    case MG_K_RESIDUAL_SCALED: return "residual_scaled";
+    case MG_K_CONV_UPDATE: return "sage_conv_update";
+    case MG_K_RESIDUAL: return "residual";
+    case MG_K_RESTRICT: return "restrict_conv";
+    case MG_K_PROLONG: return "prolong_conv";
+    case MG_K_COARSE_CHOL: return "coarse_cholesky";
+    case MG_K_OUTER_RESIDUAL: return "outer_residual_fp64";
+    default: return "unknown";
+  }
+}
+
+extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_t B,
+                                       mg_kernel_time* out, int32_t max_out, int32_t* n_out,
+                                       void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_vcycle_profile: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB || !out || !n_out || max_out < 0)
+    return c->fail(MG_ERR_INVALID, "mg_vcycle_profile: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>> rec;
+  if (c->prec == 64) {
+    Issue<double> is{c, c->d64, c->prm64, s, B};
+    is.rec = &rec;
+    is.vcycle((const double*)f, (double*)u, false);
+    c->launches += is.nk;
+  } else {
+    Issue<float> is{c, c->d32, c->prm32, s, B};
+    is.rec = &rec;
+    is.vcycle((const float*)f, (float*)u, false);
+    c->launches += is.nk;
+  }
+  cudaError_t e = cudaStreamSynchronize(s);
+  int k = 0;
+  for (auto& r : rec) {
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, std::get<2>(r), std::get<3>(r));
+    if (k < max_out) {
+      out[k].kernel = std::get<0>(r);
+      out[k].level = std::get<1>(r);
+      out[k].ms = ms;
+    }
+    ++k;
+    cudaEventDestroy(std::get<2>(r));
+    cudaEventDestroy(std::get<3>(r));
+  }
+  *n_out = std::min(k, max_out);
+  MG_CUDA(e);
+  return MG_OK;
+}

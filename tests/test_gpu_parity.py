@@ -1,0 +1,290 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances: FP64 per-cycle parity 1e-12 relative (||r_gpu - r_orc|| / ||f||
+and ||u_gpu - u_orc|| / ||u_orc||); single FP64 steps 1e-13 relative; the FP32
+cycle is compared with the FP64 oracle and must stay within 1e-5 relative
+(FP32 unit round-off 6e-8 times the growth of a few dozen operations).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+import oracle as O
+import workloads as W
+from paper_2608_29082_b300 import Hierarchy, LMGParams, MGError, Solver
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def rand_params(J, seed, spread=0.3, conv=True):
+    r = np.random.default_rng(seed)
+    p = LMGParams.identity(J)
+    m = J - 1
+    p.theta = p.theta * (1 + spread * r.uniform(-1, 1, m))
+    p.eta = p.eta * (1 + spread * r.uniform(-1, 1, m))
+    for w in (p.wB, p.wR, p.wP):
+        w[:, 0] += spread * r.uniform(-1, 1, m)
+        if conv:
+            w[:, 1] += spread * r.uniform(-1, 1, m)
+    return p
+
+
+def to_oracle(p: LMGParams) -> O.Params:
+    return O.Params(p.theta.copy(), p.eta.copy(), p.wB.copy(), p.wR.copy(), p.wP.copy(),
+                    p.nu_pre, p.nu_post)
+
+
+CASES = {
+    "poisson33": lambda: W.poisson_square(33, 4, batch=3, seed=1),
+    "checker65": lambda: W.checkerboard_square(65, 6, ncell=8, values=(1.0, 1e4), batch=2, seed=3),
+    "lognormal65": lambda: W.lognormal_square(65, seed=5, batch=2),
+    "lshape_r2": lambda: W.lshape_anisotropic(refinements=2, batch=2, seed=2),
+}
+
+_cache = {}
+
+
+def problem(name):
+    if name not in _cache:
+        p = CASES[name]()
+        _cache[name] = (p, O.build_hierarchy(p), Hierarchy.from_problem(p))
+    return _cache[name]
+
+
+def t64(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def rel(a, b, scale=None):
+    s = np.linalg.norm(b) if scale is None else scale
+    return np.linalg.norm(a - b) / max(s, 1e-300)
+
+
+# ------------------------------------------------------------- steps ------
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("conv", [False, True])
+def test_single_steps_fp64(name, conv):
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 3, conv=conv)
+    po = to_oracle(prm)
+    S = Solver(Hp, prm, precision=64, max_batch=4)
+    r = np.random.default_rng(0)
+    for lev in range(Hp.J - 1):
+        Lo = Ho.levels[lev]
+        n, nc = Hp.sizes[lev], Hp.sizes[lev + 1]
+        f, u = r.standard_normal((n, 3)), r.standard_normal((n, 3))
+        ec = r.standard_normal((nc, 3))
+        out = torch.empty((n, 3), dtype=torch.float64, device=DEV)
+        S.level_apply(lev, "smooth", t64(f), t64(u), out)
+        ref = O.smooth(Lo, f, u, po.theta[lev], po.eta[lev], po.wB[lev])
+        assert rel(out.cpu().numpy(), ref) < 1e-13, ("smooth", lev)
+        S.level_apply(lev, "residual", t64(f), t64(u), out)
+        assert rel(out.cpu().numpy(), f - Lo.A @ u) < 1e-13, ("residual", lev)
+        outc = torch.empty((nc, 3), dtype=torch.float64, device=DEV)
+        S.level_apply(lev, "restrict", t64(f), None, outc)
+        ref = Lo.P.T @ O.conv(Lo, f, po.wR[lev][0], po.wR[lev][1])
+        assert rel(outc.cpu().numpy(), ref) < 1e-13, ("restrict", lev)
+        S.level_apply(lev, "prolong", t64(ec), t64(u), out)
+        ref = u + O.conv(Lo, Lo.P @ ec, po.wP[lev][0], po.wP[lev][1])
+        assert rel(out.cpu().numpy(), ref) < 1e-13, ("prolong", lev)
+    nJ = Hp.sizes[-1]
+    fJ = r.standard_normal((nJ, 3))
+    outJ = torch.empty((nJ, 3), dtype=torch.float64, device=DEV)
+    S.level_apply(Hp.J - 1, "coarse", t64(fJ), None, outJ)
+    assert rel(outJ.cpu().numpy(), sla.cho_solve(Ho.chol, fJ)) < 1e-13
+    S.close()
+
+
+# ------------------------------------------------------------- cycles -----
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("which", ["identity", "learned"])
+def test_vcycle_fp64_per_cycle_parity(name, which):
+    p, Ho, Hp = problem(name)
+    prm = LMGParams.identity(Hp.J) if which == "identity" else rand_params(Hp.J, 11, 0.2)
+    po = to_oracle(prm)
+    f = p.f
+    S = Solver(Hp, prm, precision=64, max_batch=f.shape[1])
+    fg = t64(f)
+    ug = torch.zeros_like(fg)
+    uo = np.zeros_like(f)
+    fn = np.linalg.norm(f)
+    for m in range(8):
+        S.vcycle(fg, ug)
+        uo = O.vcycle(Ho, po, f, uo)
+        ugn = ug.cpu().numpy()
+        ro, rg = O.residual(Ho, f, uo), O.residual(Ho, f, ugn)
+        assert np.linalg.norm(rg - ro) / fn < 1e-12, m
+        assert rel(ugn, uo) < 1e-12, m
+    S.close()
+
+
+def test_batch_independence_bitwise():
+    p, Ho, Hp = problem("checker65")
+    prm = rand_params(Hp.J, 5, 0.2)
+    f = np.random.default_rng(9).standard_normal((Hp.sizes[0], 5))
+    S5 = Solver(Hp, prm, precision=64, max_batch=5)
+    S1 = Solver(Hp, prm, precision=64, max_batch=1)
+    u5 = torch.zeros((Hp.sizes[0], 5), dtype=torch.float64, device=DEV)
+    S5.vcycle(t64(f), u5)
+    S5.vcycle(t64(f), u5)
+    for b in range(5):
+        u1 = torch.zeros((Hp.sizes[0], 1), dtype=torch.float64, device=DEV)
+        f1 = t64(f[:, [b]])
+        S1.vcycle(f1, u1)
+        S1.vcycle(f1, u1)
+        assert torch.equal(u1[:, 0], u5[:, b])
+
+
+@pytest.mark.parametrize("name", ["poisson33", "checker65", "lshape_r2"])
+def test_vcycle_fp32_error_vs_oracle(name):
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 13, 0.2)
+    po = to_oracle(prm)
+    f = p.f
+    S = Solver(Hp, prm, precision=32, max_batch=f.shape[1])
+    fg = torch.tensor(f, dtype=torch.float32, device=DEV)
+    ug = torch.zeros_like(fg)
+    uo = np.zeros_like(f)
+    for m in range(3):
+        # one FP32 cycle from the same FP32-representable iterate
+        uo = O.vcycle(Ho, po, f.astype(np.float32).astype(np.float64),
+                      ug.double().cpu().numpy())
+        S.vcycle(fg, ug)
+        err = rel(ug.double().cpu().numpy(), uo)
+        assert err < 1e-5, (m, err)
+    S.close()
+
+
+# ------------------------------------------------------------- solves -----
+
+def test_plain_fp64_solve_matches_oracle_iterations():
+    p, Ho, Hp = problem("poisson33")
+    prm = LMGParams.identity(Hp.J)
+    S = Solver(Hp, prm, precision=64, max_batch=3)
+    u, info = S.solve(t64(p.f), tol=1e-10, max_iter=100)
+    ref = O.solve_vcycles(Ho, to_oracle(prm), p.f, 1e-10)
+    assert info.status == 0
+    assert np.array_equal(info.iters, ref.iters)
+    rr = O.relres(Ho, p.f, u.cpu().numpy())
+    assert (rr < 1e-10).all()
+    assert np.allclose(info.relres, rr, rtol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["checker65", "lognormal65", "lshape_r2"])
+def test_fp32_refinement_reaches_tolerance(name):
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 17, 0.05)
+    S = Solver(Hp, prm, precision=32, max_batch=p.f.shape[1])
+    u, info = S.solve(t64(p.f), tol=1e-8, max_iter=400)
+    assert info.status == 0
+    rr = O.relres(Ho, p.f, u.cpu().numpy())  # re-evaluated by the oracle in FP64
+    assert (rr < 1e-8).all(), rr
+    ref = O.solve_refinement(Ho, to_oracle(prm), p.f, 1e-8, max_iter=400)
+    # FP32 inner cycles: iteration counts within a few of the FP64 oracle's
+    assert np.all(np.abs(info.iters - ref.iters) <= max(2, 0.1 * ref.iters.max()))
+
+
+def test_solve_result_independent_of_batch():
+    p, Ho, Hp = problem("lognormal65")
+    prm = rand_params(Hp.J, 19, 0.05)
+    f = np.random.default_rng(4).standard_normal((Hp.sizes[0], 4))
+    f[:, 2] *= 1e-3  # different scale and convergence history
+    S4 = Solver(Hp, prm, precision=32, max_batch=4)
+    S1 = Solver(Hp, prm, precision=32, max_batch=1)
+    u4, i4 = S4.solve(t64(f), tol=1e-8, max_iter=200)
+    for b in range(4):
+        u1, i1 = S1.solve(t64(f[:, [b]]), tol=1e-8, max_iter=200)
+        assert i1.iters[0] == i4.iters[b]
+        assert torch.equal(u1[:, 0], u4[:, b])
+
+
+def test_solve_host_equals_device():
+    p, Ho, Hp = problem("checker65")
+    prm = LMGParams.identity(Hp.J)
+    S = Solver(Hp, prm, precision=32, max_batch=2)
+    ud, infod = S.solve(t64(p.f), tol=1e-8, max_iter=400)
+    uh, infoh = S.solve_host(p.f, tol=1e-8, max_iter=400)
+    assert np.array_equal(ud.cpu().numpy(), uh)
+    assert np.array_equal(infod.iters, infoh.iters)
+
+
+# ------------------------------------------------------------ edge cases --
+
+def test_odd_and_zero_smoothing_steps():
+    p, Ho, Hp = problem("checker65")
+    for nu_pre, nu_post in [(1, 0), (0, 3), (3, 1)]:
+        for conv in (False, True):
+            prm = rand_params(Hp.J, 23, 0.2, conv=conv)
+            prm.nu_pre, prm.nu_post = nu_pre, nu_post
+            po = to_oracle(prm)
+            S = Solver(Hp, prm, precision=64, max_batch=2)
+            ug = torch.zeros((Hp.sizes[0], 2), dtype=torch.float64, device=DEV)
+            S.vcycle(t64(p.f), ug)
+            S.vcycle(t64(p.f), ug)
+            uo = O.vcycle(Ho, po, p.f, O.vcycle(Ho, po, p.f, np.zeros_like(p.f)))
+            assert rel(ug.cpu().numpy(), uo) < 1e-12, (nu_pre, nu_post, conv)
+            S.close()
+
+
+def test_set_params_switches_kernels():
+    p, Ho, Hp = problem("poisson33")
+    S = Solver(Hp, LMGParams.identity(Hp.J), precision=64, max_batch=3)
+    for k, prm in enumerate([LMGParams.identity(Hp.J), rand_params(Hp.J, 29, 0.2),
+                             LMGParams.identity(Hp.J), rand_params(Hp.J, 31, 0.2, conv=False)]):
+        S.set_params(prm)
+        ug = torch.zeros((Hp.sizes[0], 3), dtype=torch.float64, device=DEV)
+        S.vcycle(t64(p.f), ug)
+        uo = O.vcycle(Ho, to_oracle(prm), p.f, np.zeros_like(p.f))
+        assert rel(ug.cpu().numpy(), uo) < 1e-12, k
+
+
+def test_invalid_calls_raise():
+    p, Ho, Hp = problem("poisson33")
+    S = Solver(Hp, LMGParams.identity(Hp.J), precision=64, max_batch=2)
+    f = torch.zeros((Hp.sizes[0], 3), dtype=torch.float64, device=DEV)
+    with pytest.raises(ValueError):
+        S.vcycle(f, torch.zeros_like(f))  # batch 3 > max_batch 2
+    with pytest.raises(MGError):
+        S.level_apply(0, "coarse", f[:, :1].contiguous(), None, torch.zeros_like(f[:, :1]))
+    bad = LMGParams.identity(Hp.J + 1)
+    with pytest.raises(MGError):
+        S.set_params(bad)
+
+
+def test_zero_rhs_and_not_converged():
+    p, Ho, Hp = problem("checker65")
+    S = Solver(Hp, LMGParams.identity(Hp.J), precision=32, max_batch=2)
+    f = torch.zeros((Hp.sizes[0], 2), dtype=torch.float64, device=DEV)
+    f[:, 1] = 1.0
+    u, info = S.solve(f, tol=1e-8, max_iter=2)
+    assert info.status == 1  # MG_NOT_CONVERGED: column 1 needs more than 2 iterations
+    assert info.iters[0] == 0 and info.iters[1] == 2
+    assert torch.all(u[:, 0] == 0)
+
+
+# ------------------------------------------------- full-size workload -----
+
+@pytest.mark.slow
+def test_full_size_checkerboard_513():
+    """The 513^2, 9-level jump-coefficient workload in the benchmark's launch
+    configuration: one FP64 cycle against the oracle, and the FP32 + FP64
+    refinement solve re-checked by the oracle."""
+    p = W.checkerboard_square()
+    Ho = O.build_hierarchy(p)
+    Hp = Hierarchy.from_problem(p)
+    prm = LMGParams.identity(Hp.J)
+    S64 = Solver(Hp, prm, precision=64, max_batch=1)
+    ug = torch.zeros((Hp.sizes[0], 1), dtype=torch.float64, device=DEV)
+    S64.vcycle(t64(p.f), ug)
+    uo = O.vcycle(Ho, to_oracle(prm), p.f, np.zeros_like(p.f))
+    assert rel(ug.cpu().numpy(), uo) < 1e-12
+    S64.close()
+    S32 = Solver(Hp, prm, precision=32, max_batch=1)
+    u, info = S32.solve(t64(p.f), tol=1e-8, max_iter=400)
+    assert info.status == 0
+    assert O.relres(Ho, p.f, u.cpu().numpy())[0] < 1e-8
