@@ -240,6 +240,38 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
 
 void mg_destroy(mg_ctx* ctx);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free entry point.  The paper has no counterpart: this is an
+ * interface for callers that cannot call cudaMalloc (a host application
+ * that owns all device memory and forbids plug-ins to allocate, or a
+ * latency-critical loop that cannot take an allocation's implicit device
+ * synchronisation).
+ * ------------------------------------------------------------------- */
+
+/* Size of the static device scratch used by mg_smooth_noalloc, in doubles
+ * (4 MiB): n * nrhs must not exceed it. */
+#define MG_NOALLOC_MAX_ELEMS 524288
+
+/* nu learnable smoothing steps, delta = theta D^{-1} (f - A u),
+ * u <- u + eta (w1 delta + w2 mean_{N(i)} delta), in FP64 on an operator
+ * the caller holds in DEVICE memory: CSR rowptr[n+1], col[nnz], val[nnz]
+ * (diagonal included; the off-diagonal nonzeros are the graph N(i)),
+ * inv_deg[n] = 1/deg_i, f and u [n][nrhs].  u is updated in place; f and u
+ * must not overlap.  Nothing is allocated: delta lives in a file-scope
+ * __device__ array of MG_NOALLOC_MAX_ELEMS doubles that every GPU loading
+ * the library holds until exit.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress, with the device current);
+ * make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (nothing needs clearing: each
+ * step overwrites delta before reading it); calls that overlap on the GPU
+ * race on it.  Returns MG_ERR_INVALID if n * nrhs exceeds
+ * MG_NOALLOC_MAX_ELEMS or an argument is invalid (message via
+ * mg_last_error(NULL, ...)); work is queued on stream and not waited for. */
+mg_status mg_smooth_noalloc(int32_t n, const int32_t* rowptr_dev, const int32_t* col_dev,
+                            const double* val_dev, const double* inv_deg_dev, const double* f_dev,
+                            double* u_dev, int32_t nrhs, int32_t nu, double theta, double eta,
+                            double w1, double w2, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
