@@ -223,6 +223,42 @@ mg_status mg_vcycle_profile(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t
 /* Static name of a kernel kind ("unknown" if out of range). */
 const char* mg_kernel_name(int32_t kind);
 
+/* ---------------------------------------------------------------------
+ * Training (Algorithm 3): K unrolled cycles, their hand-written adjoint and
+ * the residual loss, all in the context precision.
+ * ------------------------------------------------------------------- */
+
+/* Runs K cycles u <- LMG(A, f, u) (Algorithm 2) in place and records, per
+ * cycle, the level-0 input iterate and every coarse level's right-hand side
+ * and output (per-level checkpoints; f is copied).  The checkpoints stay
+ * valid until the next mg_forward_record or mg_set_params.  f, u: device
+ * [n_0][nrhs] in the context precision; 1 <= K <= 1000. */
+mg_status mg_forward_record(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs,
+                            int32_t n_cycles, void* stream);
+
+/* Reverse mode through the recorded cycles: given grad_u_out = dL/du_K,
+ * writes grad_u_in = dL/du_0 (may be NULL), grad_f = dL/df summed over the
+ * cycles (may be NULL) and grad_params = dL/dTheta, a DEVICE FP64 array
+ * [J-1][8] in the order theta, eta, wB1, wB2, wR1, wR2, wP1, wP2 (per level,
+ * not summed over shared parameters).  Each level's smoothing iterates are
+ * recomputed from its checkpoint; reductions are deterministic.  n_cycles
+ * must equal the recorded K; MG_ERR_STATE if nothing was recorded or the
+ * parameters changed since. */
+mg_status mg_vcycle_backward(mg_ctx* ctx, int32_t n_cycles, const void* grad_u_out_dev,
+                             void* grad_u_in_dev, void* grad_f_dev, double* grad_params_dev,
+                             void* stream);
+
+/* Residual loss on level 0: s_b = ||f_b - A u_b||^2 per right-hand side.
+ * per_rhs_dev [nrhs] (device FP64, may be NULL) receives s_b;
+ * loss_dev (device FP64 scalar, may be NULL) receives sum_b w_b s_b and
+ * grad_u_dev (context precision [n_0][nrhs], may be NULL) receives its
+ * gradient -2 w_b A (f_b - A u_b); both need weights_dev [nrhs] (device).
+ * With weights 1/(nrhs ||r_0,b||^2) this is the training loss
+ * mean_b ||r_K||^2 / ||r_0||^2. */
+mg_status mg_residual_loss(mg_ctx* ctx, const void* f_dev, const void* u_dev, int32_t nrhs,
+                           const double* weights_dev, double* loss_dev, double* per_rhs_dev,
+                           void* grad_u_dev, void* stream);
+
 /* Sizes: n_rows_out[l] for l < J (host array of J). */
 mg_status mg_level_sizes(const mg_ctx* ctx, int32_t* n_levels_out, int32_t* n_rows_out);
 

@@ -84,6 +84,9 @@ def lib() -> C.CDLL:
         "mg_vcycle_profile": ([vp, vp, vp, C.c_int32, C.POINTER(KernelTime), C.c_int32, i32p,
                                vp], C.c_int),
         "mg_kernel_name": ([C.c_int32], C.c_char_p),
+        "mg_forward_record": ([vp, vp, vp, C.c_int32, C.c_int32, vp], C.c_int),
+        "mg_vcycle_backward": ([vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),
+        "mg_residual_loss": ([vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),
         "mg_smooth_noalloc": ([C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_int32,
                                C.c_double, C.c_double, C.c_double, C.c_double, vp], C.c_int),
         "mg_last_error": ([vp, C.c_char_p, C.c_size_t], C.c_int),

@@ -1,0 +1,270 @@
+// Adjoint (reverse-mode) kernels of the learnable V-cycle, for training
+// (Algorithm 3's "compute gradients via backpropagation").
+//
+// Notation per level: M = D_g^{-1} A_g is the mean over graph neighbours,
+// (M x)_i = invdeg_i sum_{j in N(i)} x_j, and its transpose gathers
+// (M^T x)_i = sum_{j in N(i)} invdeg_j x_j (the graph is symmetric).
+// A is symmetric (SPD), so A^T = A.  For a step y = g(x; p) with adjoint
+// ybar, each kernel produces xbar and the dot products <ybar, dg/dp> that
+// make the parameter gradients; the dots are reduced per block in a fixed
+// order and summed over blocks in a fixed order (deterministic).
+//
+// Forward smoothing step (Sec. 3):  r = f - A u,  delta = theta D^{-1} r,
+//   u' = u + eta (w1 delta + w2 M delta)
+// Adjoint given ubar' (adjoint of u'):
+//   phibar = eta ubar',  deltabar = w1 phibar + w2 M^T phibar,
+//   rbar = theta D^{-1} deltabar,  ubar = ubar' - A rbar,  fbar += rbar,
+//   d eta = <ubar', w1 delta + w2 M delta>, d w1 = eta <ubar', delta>,
+//   d w2 = eta <ubar', M delta>,  d theta = <deltabar, D^{-1} r>.
+// Restriction r_c = P^T (w1 r + w2 M r), r = f - A u: given rcbar,
+//   phibar = P rcbar, rbar = w1 phibar + w2 M^T phibar,
+//   d w1 = <phibar, r>, d w2 = <phibar, M r>; then ubar -= A rbar, fbar += rbar.
+// Prolongation u' = u + w1 P e + w2 M P e: given ubar',
+//   ebar = P^T (w1 ubar' + w2 M^T ubar'),  d w1 = <ubar', P e>,
+//   d w2 = <ubar', M P e>.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace mgk {
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sums Q values over the block (fixed order) and writes partial[blk*Q + q].
+template <int Q>
+__device__ __forceinline__ void block_dots(const double (&v)[Q], double* __restrict__ partial) {
+  __shared__ double sh[Q][kThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const double s = warp_sum(v[q]);
+    if (lane == 0) sh[q][warp] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < Q) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[threadIdx.x][w];
+    partial[(size_t)blockIdx.x * Q + threadIdx.x] = s;
+  }
+}
+
+// grad[idx_q] += sum_k partial[k*Q + q]; one block per q.
+__global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restrict__ partial,
+                                                         int nblk, int Q, double* __restrict__ grad,
+                                                         int i0, int i1, int i2, int i3) {
+  __shared__ double sh[kThreads];
+  const int q = blockIdx.x;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nblk; k += kThreads) s += partial[(size_t)k * Q + q];
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = kThreads / 2; w >= 1; w >>= 1) {
+    if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const int idx = q == 0 ? i0 : q == 1 ? i1 : q == 2 ? i2 : i3;
+    grad[idx] += sh[0];
+  }
+}
+
+// sum_{j in N(i)} invdeg_j x_j   (row i of M^T x, without the outer factor)
+template <class T>
+__device__ __forceinline__ T row_mt(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
+  const int beg = slice_begin(L.sl_ptr, i);
+  const int end = L.sl_ptr[(i >> 5) + 1];
+  T s = T(0);
+  for (int e = beg; e < end; e += kSlice) {
+    const int c = L.col[e];
+    if (c >= 0) s = fma(L.invdeg[c], x[(size_t)c * B + b], s);
+  }
+  return s;
+}
+
+// sum_{j in N(i)} dinv_j x_j
+template <class T>
+__device__ __forceinline__ T row_sum_dinv(const LV<T>& L, int i, const T* __restrict__ x, int B,
+                                          int b) {
+  const int beg = slice_begin(L.sl_ptr, i);
+  const int end = L.sl_ptr[(i >> 5) + 1];
+  T s = T(0);
+  for (int e = beg; e < end; e += kSlice) {
+    const int c = L.col[e];
+    if (c >= 0) s = fma(L.dinv[c], x[(size_t)c * B + b], s);
+  }
+  return s;
+}
+
+// Smoothing step, part 1: from ubar' and the step's residual r, write
+// rbar = theta D^{-1} deltabar and the dots (eta, w1, w2, theta).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_adj_smooth(LV<T> L, const T* __restrict__ ubar,
+                                                         const T* __restrict__ r,
+                                                         T* __restrict__ rbar, int B,
+                                                         const T* __restrict__ prm,
+                                                         double* __restrict__ partial) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (t < (size_t)L.n * B) {
+    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    const T theta = prm[P_THETA], eta = prm[P_ETA], w1 = prm[P_WB1], w2 = prm[P_WB2];
+    const T ub = ubar[t];
+    const T phib = eta * ub;
+    const T mtphib = eta * row_mt(L, i, ubar, B, b);          // M^T phibar
+    const T deltab = fma(w1, phib, w2 * mtphib);
+    const T dr = L.dinv[i] * r[t];                             // D^{-1} r
+    rbar[t] = theta * (L.dinv[i] * deltab);
+    const T delta = theta * dr;
+    const T mdelta = L.invdeg[i] * (theta * row_sum_dinv(L, i, r, B, b));  // M delta
+    v[0] = (double)ub * ((double)w1 * delta + (double)w2 * mdelta);       // d eta
+    v[1] = (double)eta * ((double)ub * delta);                             // d w1
+    v[2] = (double)eta * ((double)ub * mdelta);                            // d w2
+    v[3] = (double)deltab * dr;                                            // d theta
+  }
+  block_dots<4>(v, partial);
+}
+
+// ubar <- ubar - A rbar ; fbar (+)= rbar   (fbar_set: overwrite instead)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_adj_apply_a(LV<T> L, T* __restrict__ ubar,
+                                                          const T* __restrict__ rbar,
+                                                          T* __restrict__ fbar, int B,
+                                                          int fbar_set) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  const T rb = rbar[t];
+  if (ubar) {
+    const T ax = row_ax(L, i, rbar, B, b);
+    ubar[t] = ubar[t] - fma(L.diag[i], rb, ax);
+  }
+  fbar[t] = fbar_set ? rb : fbar[t] + rb;
+}
+
+// Restriction adjoint, fine rows: phibar = P rcbar, rbar = w1 phibar +
+// w2 M^T phibar; dots (wR1, wR2) with the residual r.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __restrict__ rcbar,
+                                                           const T* __restrict__ r,
+                                                           T* __restrict__ rbar, int B,
+                                                           const T* __restrict__ prm,
+                                                           double* __restrict__ partial) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (t < (size_t)L.n * B) {
+    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    const T w1 = prm[P_WR1], w2 = prm[P_WR2];
+    const T phib = prolong_at(L, i, rcbar, B, b);
+    const int beg = slice_begin(L.sl_ptr, i);
+    const int end = L.sl_ptr[(i >> 5) + 1];
+    T mt = T(0), sr = T(0);
+    for (int e = beg; e < end; e += kSlice) {
+      const int c = L.col[e];
+      if (c >= 0) {
+        mt = fma(L.invdeg[c], prolong_at(L, c, rcbar, B, b), mt);
+        sr += r[(size_t)c * B + b];
+      }
+    }
+    rbar[t] = fma(w1, phib, w2 * mt);
+    v[0] = (double)phib * r[t];
+    v[1] = (double)phib * (L.invdeg[i] * sr);
+  }
+  block_dots<2>(v, partial);
+}
+
+// Prolongation adjoint, coarse rows: ebar_I = sum_children P_iI (w1 ubar_i +
+// w2 (M^T ubar)_i).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_adj_prolong(LV<T> L, const T* __restrict__ ubar,
+                                                          T* __restrict__ ebar, int B,
+                                                          const T* __restrict__ prm) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.nc * B) return;
+  const int I = (int)(t / B), b = (int)(t - (size_t)I * B);
+  const T w1 = prm[P_WP1], w2 = prm[P_WP2];
+  T acc = T(0);
+  for (int k = 0; k < L.KR; ++k) {
+    const int i = L.r_idx[(size_t)k * L.nc + I];
+    if (i < 0) break;
+    const T g = fma(w1, ubar[(size_t)i * B + b], w2 * row_mt(L, i, ubar, B, b));
+    acc = fma(L.r_w[(size_t)k * L.nc + I], g, acc);
+  }
+  ebar[t] = acc;
+}
+
+// Prolongation parameter dots, fine rows: <ubar, P e>, <ubar, M P e>.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T* __restrict__ ubar,
+                                                               const T* __restrict__ ec, int B,
+                                                               double* __restrict__ partial) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double v[2] = {0.0, 0.0};
+  if (t < (size_t)L.n * B) {
+    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    const T pe = prolong_at(L, i, ec, B, b);
+    const int beg = slice_begin(L.sl_ptr, i);
+    const int end = L.sl_ptr[(i >> 5) + 1];
+    T s = T(0);
+    for (int e = beg; e < end; e += kSlice) {
+      const int c = L.col[e];
+      if (c >= 0) s += prolong_at(L, c, ec, B, b);
+    }
+    const double ub = (double)ubar[t];
+    v[0] = ub * pe;
+    v[1] = ub * (L.invdeg[i] * s);
+  }
+  block_dots<2>(v, partial);
+}
+
+// Residual loss: r = f - A u; per block, per rhs partial sums of r^2 (same
+// mapping as k_resid64); optionally keeps r for the gradient.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_loss_resid(LV<T> L, const T* __restrict__ f,
+                                                         const T* __restrict__ u, T* __restrict__ r,
+                                                         int B, double* __restrict__ partial) {
+  __shared__ double sh[kThreads];
+  const int R = kThreads / B;
+  const int tt = threadIdx.x;
+  const int i = blockIdx.x * R + tt / B, b = tt % B;
+  double rv = 0.0;
+  if (tt < R * B && i < L.n) {
+    const size_t k = (size_t)i * B + b;
+    const T ax = row_ax(L, i, u, B, b);
+    const T rr = fma(-L.diag[i], u[k], f[k]) - ax;
+    if (r) r[k] = rr;
+    rv = (double)rr;
+  }
+  sh[tt] = rv * rv;
+  __syncthreads();
+  block_rows_reduce(sh, R, B);
+  if (tt < B) partial[(size_t)blockIdx.x * B + tt] = sh[tt];
+}
+
+// ubar = -2 w_b A r  (gradient of sum_b w_b ||f_b - A u_b||^2 w.r.t. u)
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_loss_grad(LV<T> L, const T* __restrict__ r,
+                                                        const double* __restrict__ w,
+                                                        T* __restrict__ ubar, int B) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)L.n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  const T ar = fma(L.diag[i], r[t], row_ax(L, i, r, B, b));
+  ubar[t] = (T)(-2.0 * w[b]) * ar;
+}
+
+// loss = sum_b w_b s_b ; per_rhs[b] = s_b (optional)
+__global__ void k_loss_combine(const double* __restrict__ s, const double* __restrict__ w, int B,
+                               double* __restrict__ loss, double* __restrict__ per_rhs) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double acc = 0.0;
+  for (int b = 0; b < B; ++b) {
+    if (per_rhs) per_rhs[b] = s[b];
+    if (w) acc += w[b] * s[b];
+  }
+  if (loss) *loss = acc;
+}
+
+}  // namespace mgk

@@ -18,6 +18,7 @@
 
 #include <cuda_runtime.h>
 
+#include "adjoint.cuh"
 #include "kernels.cuh"
 #include "mg.h"
 #include "mg_internal.h"
@@ -235,6 +236,15 @@ struct mg_ctx {
   std::map<std::tuple<int, const void*, const void*, int, uint32_t>, GraphEntry> graphs;
   std::string err;
   int64_t launches = 0;
+  // training state (device buffers in the context precision)
+  int64_t param_version = 0, rec_version = -1;
+  int trK = 0, trB = 0, tr_nu_pre = -1, tr_nu_post = -1;
+  bool tr_recorded = false;
+  std::vector<void*> tr_alloc;
+  std::vector<std::vector<void*>> ck_f, ck_e, bw_it;  // [K][J], [K][J], [J][nu_pre+nu_post+2]
+  std::vector<void*> ck_u, bw_ubar, bw_fbar, bw_r, bw_rbar;
+  void* ck_f0 = nullptr;
+  double* bw_partial = nullptr;
 
   mg_status fail(mg_status s, const std::string& m) {
     err = m;
@@ -406,7 +416,7 @@ struct Issue {
     post();
     pre(MG_K_RESTRICT, lev);
     mgk::k_restrict<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
-        D.view(), D.t, L[lev + 1].f, B, P(lev), conv(lev, mgk::P_WR2));
+        D.view(), D.t, Fl(lev + 1), B, P(lev), conv(lev, mgk::P_WR2));
     post();
     nk += 2;
   }
@@ -430,19 +440,25 @@ struct Issue {
   }
 
   // Algorithm 2 from level 0 with f0/u0 as the level-0 vectors.
+  // Level vectors of levels >= 1; training points them at checkpoint storage.
+  T* const* fov = nullptr;
+  T* const* uov = nullptr;
+  T* Fl(int lev) const { return fov ? fov[lev] : L[lev].f; }
+  T* Ul(int lev) const { return uov ? uov[lev] : L[lev].u; }
+
   void vcycle(const T* f0, T* u0, bool u0_zero) {
     const int J = c->J;
     for (int lev = 0; lev < J - 1; ++lev) {
-      const T* f = lev == 0 ? f0 : L[lev].f;
-      T* u = lev == 0 ? u0 : L[lev].u;
+      const T* f = lev == 0 ? f0 : Fl(lev);
+      T* u = lev == 0 ? u0 : Ul(lev);
       smooth(lev, f, u, c->nu_pre, lev == 0 ? u0_zero : true);
       restrict_(lev, f, u);
     }
-    coarse(L[J - 1].f, L[J - 1].u);
+    coarse(Fl(J - 1), Ul(J - 1));
     for (int lev = J - 2; lev >= 0; --lev) {
-      const T* f = lev == 0 ? f0 : L[lev].f;
-      T* u = lev == 0 ? u0 : L[lev].u;
-      prolong(lev, L[lev + 1].u, u);
+      const T* f = lev == 0 ? f0 : Fl(lev);
+      T* u = lev == 0 ? u0 : Ul(lev);
+      prolong(lev, Ul(lev + 1), u);
       smooth(lev, f, u, c->nu_post, false);
     }
   }
@@ -528,6 +544,8 @@ extern "C" void mg_destroy(mg_ctx* c) {
                   c->sexp,   c->sexp_prev, c->state, c->c32,    c->rhat32, c->hf, c->hu,
                   c->tol_dev};
   for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (void* p : c->tr_alloc)
     if (p) cudaFree(p);
   if (c->h_state) cudaFreeHost(c->h_state);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -687,6 +705,7 @@ extern "C" mg_status mg_set_params(mg_ctx* c, const mg_params* p) {
   c->nu_post = b;
   c->structure = structure_of(prm, c->J);
   c->prm_dirty = true;
+  c->param_version++;
   return MG_OK;
 }
 
@@ -966,3 +985,5 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
   MG_CUDA(e);
   return MG_OK;
 }
+
+#include "train_impl.cuh"

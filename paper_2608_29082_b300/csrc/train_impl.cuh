@@ -1,0 +1,321 @@
+// Training entry points of libmg.so: checkpointed forward of K unrolled
+// cycles, the hand-written adjoint of those cycles, and the residual loss.
+// Included at the end of mg_api.cu (same translation unit).
+//
+// Checkpoints per cycle k (context precision T):
+//   ck_u[k]      level-0 iterate entering cycle k
+//   ck_f[k][l]   right-hand side of level l >= 1 (the restricted residual)
+//   ck_e[k][l]   output of level l >= 1 (the coarse correction e_c)
+// plus one copy of f.  The backward pass recomputes, level by level, the
+// smoothing iterates from these (per-level checkpointing), so memory is
+// O(K * sum_l n_l * B) instead of O(K * steps * n * B).
+
+namespace {
+
+template <class T>
+std::vector<DevLevel<T>>& levels_of(mg_ctx* c);
+template <>
+std::vector<DevLevel<double>>& levels_of<double>(mg_ctx* c) { return c->d64; }
+template <>
+std::vector<DevLevel<float>>& levels_of<float>(mg_ctx* c) { return c->d32; }
+template <class T>
+const T* prm_of(mg_ctx* c);
+template <>
+const double* prm_of<double>(mg_ctx* c) { return c->prm64; }
+template <>
+const float* prm_of<float>(mg_ctx* c) { return c->prm32; }
+
+mg_status train_alloc(mg_ctx* c, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess)
+    return c->fail(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
+                   std::string("training workspace: ") + cudaGetErrorString(e));
+  c->tr_alloc.push_back(*p);
+  return MG_OK;
+}
+
+void train_free(mg_ctx* c) {
+  for (void* p : c->tr_alloc)
+    if (p) cudaFree(p);
+  c->tr_alloc.clear();
+  c->ck_f.clear();
+  c->ck_e.clear();
+  c->bw_it.clear();
+  c->ck_u.clear();
+  c->bw_ubar.clear();
+  c->bw_fbar.clear();
+  c->bw_r.clear();
+  c->bw_rbar.clear();
+  c->ck_f0 = nullptr;
+  c->bw_partial = nullptr;
+  c->trK = c->trB = 0;
+  c->tr_recorded = false;
+}
+
+mg_status ensure_train(mg_ctx* c, int K, int B) {
+  if (c->trK == K && c->trB == B && c->tr_nu_pre == c->nu_pre && c->tr_nu_post == c->nu_post)
+    return MG_OK;
+  cudaDeviceSynchronize();
+  // captured forward graphs point at the old checkpoint buffers
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+  train_free(c);
+  const size_t tb = c->prec == 64 ? 8 : 4;
+  const int J = c->J;
+  mg_status st;
+  auto vec = [&](int lev, void** p) { return train_alloc(c, p, (size_t)c->n[lev] * B * tb); };
+  c->ck_u.assign(K, nullptr);
+  c->ck_f.assign(K, std::vector<void*>(J, nullptr));
+  c->ck_e.assign(K, std::vector<void*>(J, nullptr));
+  for (int k = 0; k < K; ++k) {
+    if ((st = vec(0, &c->ck_u[k])) != MG_OK) return st;
+    for (int l = 1; l < J; ++l) {
+      if ((st = vec(l, &c->ck_f[k][l])) != MG_OK) return st;
+      if ((st = vec(l, &c->ck_e[k][l])) != MG_OK) return st;
+    }
+  }
+  if ((st = vec(0, &c->ck_f0)) != MG_OK) return st;
+  const int nit = c->nu_pre + c->nu_post + 2;
+  c->bw_it.assign(J, std::vector<void*>(nit, nullptr));
+  c->bw_ubar.assign(J, nullptr);
+  c->bw_fbar.assign(J, nullptr);
+  c->bw_r.assign(J, nullptr);
+  c->bw_rbar.assign(J, nullptr);
+  for (int l = 0; l < J; ++l) {
+    for (int k = 0; k < nit; ++k)
+      if ((st = vec(l, &c->bw_it[l][k])) != MG_OK) return st;
+    if ((st = vec(l, &c->bw_ubar[l])) != MG_OK) return st;
+    if ((st = vec(l, &c->bw_fbar[l])) != MG_OK) return st;
+    if ((st = vec(l, &c->bw_r[l])) != MG_OK) return st;
+    if ((st = vec(l, &c->bw_rbar[l])) != MG_OK) return st;
+  }
+  const size_t nblk = ((size_t)c->n[0] * B + kThreads - 1) / kThreads + 1;
+  if ((st = train_alloc(c, (void**)&c->bw_partial, nblk * 4 * sizeof(double))) != MG_OK) return st;
+  c->trK = K;
+  c->trB = B;
+  c->tr_nu_pre = c->nu_pre;
+  c->tr_nu_post = c->nu_post;
+  return MG_OK;
+}
+
+template <class T>
+struct Backward {
+  mg_ctx* c;
+  Issue<T>& is;
+  std::vector<DevLevel<T>>& L;
+  cudaStream_t s;
+  int B;
+  double* grad;  // device [J-1][P_COUNT]
+  int k = 0;     // cycle being reversed
+
+  T* V(void* p) const { return (T*)p; }
+  size_t vbytes(int lev) const { return (size_t)c->n[lev] * B * sizeof(T); }
+
+  // One forward smoothing step uin -> uout (uout != uin), same arithmetic as
+  // the forward cycle.  zero: uin is the zero vector (not read).
+  void step(int lev, const T* f, const T* uin, T* uout, bool zero) {
+    DevLevel<T>& D = L[lev];
+    const dim3 g = grid_for((size_t)D.n * B);
+    if (!is.conv(lev, mgk::P_WB2)) {
+      mgk::k_jacobi<T><<<g, kThreads, 0, s>>>(D.view(), f, uin, uout, B, is.P(lev), zero);
+      is.nk++;
+    } else {
+      if (zero)
+        cudaMemsetAsync(uout, 0, vbytes(lev), s);
+      else
+        cudaMemcpyAsync(uout, uin, vbytes(lev), cudaMemcpyDeviceToDevice, s);
+      mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, uout, D.t, B, is.P(lev), 1, zero);
+      mgk::k_conv_update<T><<<g, kThreads, 0, s>>>(D.view(), D.t, uout, B, is.P(lev), zero);
+      is.nk += 2;
+    }
+  }
+
+  void accum(int lev, int Q, size_t nblk, int a, int b2, int c2, int d) {
+    const int base = lev * mgk::P_COUNT;
+    mgk::k_grad_accum<<<Q, kThreads, 0, s>>>(c->bw_partial, (int)nblk, Q, grad, base + a,
+                                             base + b2, base + (c2 < 0 ? a : c2),
+                                             base + (d < 0 ? a : d));
+    is.nk++;
+  }
+
+  // Adjoint of the smoothing step uin -> (next); ubar holds the adjoint of
+  // the step's output on entry and of uin on exit; fbar accumulates.
+  void adj_step(int lev, const T* f, const T* uin, bool zero, T* ubar, T* fbar) {
+    DevLevel<T>& D = L[lev];
+    const size_t work = (size_t)D.n * B;
+    const dim3 g = grid_for(work);
+    T* r = V(c->bw_r[lev]);
+    T* rbar = V(c->bw_rbar[lev]);
+    mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, uin, r, B, is.P(lev), 0, zero);
+    mgk::k_adj_smooth<T><<<g, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B, is.P(lev),
+                                                 c->bw_partial);
+    accum(lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
+    mgk::k_adj_apply_a<T><<<g, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    is.nk += 3;
+  }
+
+  // Level lev of cycle k: ubar (adjoint of the level's output) -> adjoint of
+  // its input u_in; fbar (zeroed by the caller) accumulates the adjoint of f.
+  void level(int lev, const T* f, const T* uin, T* ubar, T* fbar) {
+    const int J = c->J;
+    if (lev == J - 1) {  // e = A_J^{-1} f  =>  fbar = A_J^{-1} ebar
+      is.coarse(ubar, fbar);
+      return;
+    }
+    DevLevel<T>& D = L[lev];
+    const int np = c->nu_pre, nq = c->nu_post;
+    std::vector<void*>& it = c->bw_it[lev];
+    const bool zero_in = uin == nullptr;
+    // forward recompute of this level's iterates
+    if (zero_in)
+      cudaMemsetAsync(it[0], 0, vbytes(lev), s);
+    else
+      cudaMemcpyAsync(it[0], uin, vbytes(lev), cudaMemcpyDeviceToDevice, s);
+    for (int j = 0; j < np; ++j) step(lev, f, V(it[j]), V(it[j + 1]), zero_in && j == 0);
+    const T* ec = V(c->ck_e[k][lev + 1]);
+    mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
+        D.view(), ec, V(it[np]), V(it[np + 1]), B, is.P(lev), is.conv(lev, mgk::P_WP2));
+    is.nk++;
+    for (int j = 0; j < nq; ++j) step(lev, f, V(it[np + 1 + j]), V(it[np + 2 + j]), false);
+    // reverse: post-smoothing
+    for (int j = nq - 1; j >= 0; --j) adj_step(lev, f, V(it[np + 1 + j]), false, ubar, fbar);
+    // prolongation: ebar = P^T Phi_P^T ubar, dots <ubar, P e>, <ubar, M P e>
+    T* ebar = V(c->bw_ubar[lev + 1]);
+    const dim3 gf = grid_for((size_t)D.n * B);
+    mgk::k_adj_prolong<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(D.view(), ubar, ebar, B,
+                                                                          is.P(lev));
+    mgk::k_adj_prolong_dots<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, ec, B, c->bw_partial);
+    is.nk += 2;
+    accum(lev, 2, gf.x, mgk::P_WP1, mgk::P_WP2, -1, -1);
+    // coarse level (its input iterate is zero)
+    T* fcbar = V(c->bw_fbar[lev + 1]);
+    cudaMemsetAsync(fcbar, 0, vbytes(lev + 1), s);
+    level(lev + 1, V(c->ck_f[k][lev + 1]), nullptr, ebar, fcbar);
+    // restriction: r = f - A u_pre, r_c = P^T Phi_R r
+    T* r = V(c->bw_r[lev]);
+    T* rbar = V(c->bw_rbar[lev]);
+    mgk::k_residual<T><<<gf, kThreads, 0, s>>>(D.view(), f, V(it[np]), r, B, is.P(lev), 0,
+                                                zero_in && np == 0);
+    mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), fcbar, r, rbar, B, is.P(lev),
+                                                    c->bw_partial);
+    accum(lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
+    mgk::k_adj_apply_a<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    is.nk += 3;
+    // reverse: pre-smoothing
+    for (int j = np - 1; j >= 0; --j) adj_step(lev, f, V(it[j]), zero_in && j == 0, ubar, fbar);
+  }
+};
+
+template <class T>
+mg_status forward_record(mg_ctx* c, const T* f, T* u, int B, int K, cudaStream_t s) {
+  mg_status st = ensure_train(c, K, B);
+  if (st != MG_OK) return st;
+  MG_CUDA(cudaMemcpyAsync(c->ck_f0, f, (size_t)c->n[0] * B * sizeof(T), cudaMemcpyDeviceToDevice,
+                          s));
+  const int J = c->J;
+  std::vector<std::vector<T*>> fo(K, std::vector<T*>(J, nullptr)), uo(K, std::vector<T*>(J, nullptr));
+  for (int k = 0; k < K; ++k)
+    for (int l = 1; l < J; ++l) {
+      fo[k][l] = (T*)c->ck_f[k][l];
+      uo[k][l] = (T*)c->ck_e[k][l];
+    }
+  auto key = std::make_tuple(20 + K, (const void*)f, (const void*)u, B, c->structure);
+  st = run_graph(c, key, s, [&](cudaStream_t cs) {
+    Issue<T> is{c, levels_of<T>(c), prm_of<T>(c), cs, B};
+    for (int k = 0; k < K; ++k) {
+      cudaMemcpyAsync(c->ck_u[k], u, (size_t)c->n[0] * B * sizeof(T), cudaMemcpyDeviceToDevice, cs);
+      is.fov = fo[k].data();
+      is.uov = uo[k].data();
+      is.vcycle((const T*)c->ck_f0, u, false);
+    }
+    return is.nk;
+  });
+  if (st != MG_OK) return st;
+  c->tr_recorded = true;
+  c->rec_version = c->param_version;
+  return MG_OK;
+}
+
+template <class T>
+mg_status backward(mg_ctx* c, int K, const T* gout, T* gin, T* gf, double* gparams,
+                   cudaStream_t s) {
+  const int B = c->trB;
+  const size_t v0 = (size_t)c->n[0] * B * sizeof(T);
+  MG_CUDA(cudaMemsetAsync(gparams, 0, (size_t)(c->J - 1) * mgk::P_COUNT * sizeof(double), s));
+  T* fbar0 = gf ? gf : (T*)c->bw_fbar[0];
+  MG_CUDA(cudaMemsetAsync(fbar0, 0, v0, s));
+  T* ubar = (T*)c->bw_ubar[0];
+  MG_CUDA(cudaMemcpyAsync(ubar, gout, v0, cudaMemcpyDeviceToDevice, s));
+  Issue<T> is{c, levels_of<T>(c), prm_of<T>(c), s, B};
+  Backward<T> bw{c, is, levels_of<T>(c), s, B, gparams};
+  for (int k = K - 1; k >= 0; --k) {
+    bw.k = k;
+    bw.level(0, (const T*)c->ck_f0, (const T*)c->ck_u[k], ubar, fbar0);
+  }
+  if (gin) MG_CUDA(cudaMemcpyAsync(gin, ubar, v0, cudaMemcpyDeviceToDevice, s));
+  MG_CUDA(cudaGetLastError());
+  c->launches += is.nk;
+  return MG_OK;
+}
+
+template <class T>
+mg_status residual_loss(mg_ctx* c, const T* f, const T* u, int B, const double* w, double* loss,
+                        double* per_rhs, T* grad_u, cudaStream_t s) {
+  DevLevel<T>& D = levels_of<T>(c)[0];
+  const int R = kThreads / B;
+  const int nblk = (D.n + R - 1) / R;
+  T* r = grad_u ? D.t : nullptr;
+  mgk::k_loss_resid<T><<<nblk, kThreads, 0, s>>>(D.view(), f, u, r, B, c->partial);
+  mgk::k_reduce<<<B, kThreads, 0, s>>>(c->partial, nblk, B, c->rsum);
+  mgk::k_loss_combine<<<1, 32, 0, s>>>(c->rsum, w, B, loss, per_rhs);
+  int nk = 3;
+  if (grad_u) {
+    mgk::k_loss_grad<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), D.t, w, grad_u, B);
+    ++nk;
+  }
+  MG_CUDA(cudaGetLastError());
+  c->launches += nk;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_forward_record(mg_ctx* c, const void* f, void* u, int32_t B, int32_t K,
+                                       void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_forward_record: ctx is NULL");
+  if (!f || !u || f == u || B < 1 || B > c->maxB || K < 1 || K > 1000)
+    return c->fail(MG_ERR_INVALID, "mg_forward_record: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  if (c->prec == 64) return forward_record<double>(c, (const double*)f, (double*)u, B, K, s);
+  return forward_record<float>(c, (const float*)f, (float*)u, B, K, s);
+}
+
+extern "C" mg_status mg_vcycle_backward(mg_ctx* c, int32_t K, const void* gout, void* gin, void* gf,
+                                        double* gparams, void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_vcycle_backward: ctx is NULL");
+  if (!c->tr_recorded) return c->fail(MG_ERR_STATE, "mg_vcycle_backward: no recorded forward");
+  if (K != c->trK) return c->fail(MG_ERR_STATE, "mg_vcycle_backward: n_cycles differs from the recorded forward");
+  if (c->rec_version != c->param_version)
+    return c->fail(MG_ERR_STATE, "mg_vcycle_backward: parameters changed since the forward");
+  if (!gout || !gparams) return c->fail(MG_ERR_INVALID, "mg_vcycle_backward: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->prec == 64)
+    return backward<double>(c, K, (const double*)gout, (double*)gin, (double*)gf, gparams, s);
+  return backward<float>(c, K, (const float*)gout, (float*)gin, (float*)gf, gparams, s);
+}
+
+extern "C" mg_status mg_residual_loss(mg_ctx* c, const void* f, const void* u, int32_t B,
+                                      const double* w, double* loss, double* per_rhs, void* grad_u,
+                                      void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_residual_loss: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB || (grad_u && !w) || (loss && !w))
+    return c->fail(MG_ERR_INVALID, "mg_residual_loss: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (c->prec == 64)
+    return residual_loss<double>(c, (const double*)f, (const double*)u, B, w, loss, per_rhs,
+                                 (double*)grad_u, s);
+  return residual_loss<float>(c, (const float*)f, (const float*)u, B, w, loss, per_rhs,
+                              (float*)grad_u, s);
+}

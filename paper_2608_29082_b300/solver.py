@@ -194,5 +194,46 @@ class Solver:
         return [(self.lib.mg_kernel_name(buf[k].kernel).decode(), buf[k].level, buf[k].ms)
                 for k in range(n.value)]
 
+    # ------------------------------------------------------------ training
+    def forward_record(self, f: torch.Tensor, u: torch.Tensor, n_cycles: int) -> torch.Tensor:
+        """n_cycles cycles on u in place, recording per-level checkpoints."""
+        f2 = self._vec(f, self.n[0], self.dtype, "f")
+        u2 = self._vec(u, self.n[0], self.dtype, "u")
+        L.check(self.lib.mg_forward_record(self.ctx, C.c_void_p(f2.data_ptr()),
+                                           C.c_void_p(u2.data_ptr()), f2.shape[1], int(n_cycles),
+                                           _stream_handle()), self.ctx)
+        return u
+
+    def backward(self, grad_u_out: torch.Tensor, n_cycles: int, want_inputs: bool = True):
+        """Adjoint of the recorded cycles: (dL/du_0, dL/df, dL/dTheta [J-1, 8] FP64)."""
+        g = self._vec(grad_u_out, self.n[0], self.dtype, "grad_u_out")
+        gin = torch.empty_like(g) if want_inputs else None
+        gf = torch.empty_like(g) if want_inputs else None
+        gp = torch.empty((self.hier.J - 1, 8), dtype=torch.float64, device=self.device)
+        L.check(self.lib.mg_vcycle_backward(
+            self.ctx, int(n_cycles), C.c_void_p(g.data_ptr()),
+            C.c_void_p(gin.data_ptr()) if gin is not None else None,
+            C.c_void_p(gf.data_ptr()) if gf is not None else None,
+            C.c_void_p(gp.data_ptr()), _stream_handle()), self.ctx)
+        return gin, gf, gp
+
+    def residual_loss(self, f: torch.Tensor, u: torch.Tensor, weights: torch.Tensor | None = None,
+                      grad: bool = False):
+        """(sum_b w_b ||f_b - A u_b||^2, per-rhs ||r_b||^2, gradient w.r.t. u or None),
+        all device tensors."""
+        f2 = self._vec(f, self.n[0], self.dtype, "f")
+        u2 = self._vec(u, self.n[0], self.dtype, "u")
+        B = f2.shape[1]
+        per = torch.empty(B, dtype=torch.float64, device=self.device)
+        loss = torch.empty((), dtype=torch.float64, device=self.device) if weights is not None else None
+        g = torch.empty_like(u2) if (grad and weights is not None) else None
+        L.check(self.lib.mg_residual_loss(
+            self.ctx, C.c_void_p(f2.data_ptr()), C.c_void_p(u2.data_ptr()), B,
+            C.c_void_p(weights.data_ptr()) if weights is not None else None,
+            C.c_void_p(loss.data_ptr()) if loss is not None else None,
+            C.c_void_p(per.data_ptr()), C.c_void_p(g.data_ptr()) if g is not None else None,
+            _stream_handle()), self.ctx)
+        return loss, per, g
+
     def kernel_launches(self) -> int:
         return int(self.lib.mg_kernel_launches(self.ctx))
