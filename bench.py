@@ -28,6 +28,10 @@ if ROOT not in sys.path:
 
 TOL = 1e-8
 MAX_ITER = 400
+TRAIN_PRESET = "shared_conv"   # SAGEConv weights shared over levels, theta/eta per level
+TRAIN_K = 20
+TRAIN_BATCH = 8
+TRAIN_EPOCHS = 100
 WORKLOAD = ("checkerboard 513x513 P1, 9 levels, k in {1,1e4} on 8x8 cells, f~N(0,1), "
             "1 rhs, tol 1e-8")
 
@@ -126,6 +130,14 @@ def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
         return 2 * n * n * 8 + 2 * B * n * b
     if name == "outer_residual_fp64":
         return nnz_off * 12 + 2 * n * 8 + B * n * (8 + 8 + 4)
+    if name == "small_levels_block":  # levels lev..J-1, 2+2 learned smoothing steps each
+        tot = 0.0
+        for l in range(lev, hier.J - 1):
+            tot += 4 * (kernel_bytes("residual_scaled", l, hier, B, b)
+                        + kernel_bytes("sage_conv_update", l, hier, B, b))
+            tot += kernel_bytes("residual", l, hier, B, b) + kernel_bytes("restrict_conv", l, hier, B, b)
+            tot += kernel_bytes("prolong_conv", l, hier, B, b)
+        return tot + kernel_bytes("coarse_cholesky", hier.J - 1, hier, B, b)
     raise KeyError(name)
 
 
@@ -155,8 +167,28 @@ def run_ours(args):
     prob = make_problem(seed=rank)
     hier = lmg.Hierarchy.from_problem(prob)
     J = hier.J
-    learned = trained.load(args.params, J)
     plain = lmg.LMGParams.identity(J)
+    training = None
+    if args.params:
+        learned = trained.load(args.params, J)
+    else:
+        # Algorithm 3 on this operator, FP32 forward/adjoint, Rprop; training
+        # right-hand sides come from a different seed than the solved source
+        from paper_2608_29082_b300.train_cli import PRESETS
+        from paper_2608_29082_b300.training import ParamMap, Trainer
+        from workloads import fields
+        ftr = torch.tensor(fields.rhs(hier.sizes[0], TRAIN_BATCH, 1000 + rank),
+                           dtype=torch.float32, device=dev)
+        Str = lmg.Solver(hier, plain, precision=32, max_batch=TRAIN_BATCH)
+        t0 = time.perf_counter()
+        log = Trainer(Str, ParamMap(J, **PRESETS[TRAIN_PRESET]), n_cycles=TRAIN_K).train(
+            ftr, plain, max_epochs=TRAIN_EPOCHS)
+        torch.cuda.synchronize()
+        learned = log.params
+        training = {"preset": TRAIN_PRESET, "epochs": len(log.losses), "unrolled_cycles": TRAIN_K,
+                    "rhs": TRAIN_BATCH, "seconds": round(time.perf_counter() - t0, 2),
+                    "loss_ratio": float(log.best_loss / log.losses[0])}
+        Str.close()
     S32 = lmg.Solver(hier, learned, precision=32, max_batch=1)
     S64 = lmg.Solver(hier, plain, precision=64, max_batch=1)
     f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
@@ -252,7 +284,7 @@ def run_ours(args):
     # oracle on the host cores, same workload (rank 0 at N=1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(prob)
+        cpu = cpu_baseline(prob, learned)
 
     if rank == 0:
         out = {
@@ -271,7 +303,9 @@ def run_ours(args):
             "config": {"workload": WORKLOAD, "dof": hier.sizes[0], "levels": J, "nrhs": 1,
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "flushed (256 MB write) before every timed solve",
-                       "params": trained.describe(args.params)},
+                       "params": trained.describe(args.params) if args.params else
+                       "trained at start-up (Algorithm 3, see training)"},
+            "training": training,
             "learned_iters": int(info32.iters[0]),
             "learned_relres": float(info32.relres[0]),
             "plain_fp64_ms": round(ms64, 4),
@@ -297,18 +331,21 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
-def cpu_baseline(prob):
+def cpu_baseline(prob, params):
+    """The FP64 oracle's refinement solve of the same workload with the same
+    (learned) parameters."""
     import oracle as O
     t0 = time.perf_counter()
     H = O.build_hierarchy(prob)
     setup = time.perf_counter() - t0
-    p = O.Params.identity(H.J)
+    p = O.Params(params.theta.copy(), params.eta.copy(), params.wB.copy(), params.wR.copy(),
+                 params.wP.copy(), params.nu_pre, params.nu_post)
     t0 = time.perf_counter()
     r = O.solve_refinement(H, p, prob.f, TOL, max_iter=MAX_ITER)
     dt = time.perf_counter() - t0
     return {"value": round(dt * 1e3, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
-            "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, identity "
-                      f"parameters) of the same workload; setup {setup:.2f}s excluded; "
+            "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, the same "
+                      f"learned parameters) of the same workload; setup {setup:.2f}s excluded; "
                       "scipy sparse products, single thread"}
 
 

@@ -195,6 +195,17 @@ typedef enum {
 mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, const void* y,
                          void* out, int32_t nrhs, void* stream);
 
+/* Execution options of a context (they change launch shapes, never results
+ * beyond rounding order: every option gives bitwise the same cycle).
+ *   MG_OPT_TAIL_WORK  levels with rows * nrhs <= value, and all coarser ones,
+ *                     run in one thread block with block barriers instead of
+ *                     one grid kernel per step (default 8192; 0 disables)
+ *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
+ *                     dependent launch; 0: plain stream order */
+typedef enum { MG_OPT_TAIL_WORK = 0, MG_OPT_PDL = 1 } mg_option;
+
+mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);
+
 /* Kernel kinds reported by mg_vcycle_profile. */
 typedef enum {
   MG_K_JACOBI = 0,          /* smoothing step with Phi_B = w1 I, one pass      */
@@ -204,7 +215,8 @@ typedef enum {
   MG_K_RESTRICT = 4,        /* r_c = P^T Phi_R(r)                              */
   MG_K_PROLONG = 5,         /* u += Phi_P(P e_c)                               */
   MG_K_COARSE_CHOL = 6,     /* e_J = A_J^{-1} r_J                              */
-  MG_K_OUTER_RESIDUAL = 7   /* FP64 refinement residual                        */
+  MG_K_OUTER_RESIDUAL = 7,  /* FP64 refinement residual                        */
+  MG_K_TAIL = 8             /* all small levels of a cycle in one thread block */
 } mg_kernel_kind;
 
 typedef struct {

@@ -14,6 +14,7 @@ MG_NOT_CONVERGED = 1
 STATUS = {0: "MG_OK", 1: "MG_NOT_CONVERGED", -1: "MG_ERR_INVALID", -2: "MG_ERR_OOM",
           -3: "MG_ERR_NOT_SPD", -4: "MG_ERR_CUDA", -5: "MG_ERR_TIMEOUT", -6: "MG_ERR_DIVERGED",
           -7: "MG_ERR_NOT_IMPLEMENTED", -8: "MG_ERR_STATE"}
+OPTIONS = {"tail_work": 0, "pdl": 1}
 OPS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "coarse": 4,
        "outer_residual": 5}
 
@@ -84,6 +85,7 @@ def lib() -> C.CDLL:
         "mg_vcycle_profile": ([vp, vp, vp, C.c_int32, C.POINTER(KernelTime), C.c_int32, i32p,
                                vp], C.c_int),
         "mg_kernel_name": ([C.c_int32], C.c_char_p),
+        "mg_set_option": ([vp, C.c_int32, C.c_int64], C.c_int),
         "mg_forward_record": ([vp, vp, vp, C.c_int32, C.c_int32, vp], C.c_int),
         "mg_vcycle_backward": ([vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),
         "mg_residual_loss": ([vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),

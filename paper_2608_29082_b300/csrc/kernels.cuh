@@ -14,6 +14,15 @@
 // same column array serves the residual and the mean aggregation.
 // Arithmetic uses explicit fma() so that every right-hand side is computed in
 // the same order whatever the batch size: results do not depend on B.
+//
+// Every step is a per-element device function (one (row, rhs) pair) used by
+// two launch forms: a grid kernel per step for large levels, and k_tail,
+// one thread block that runs all small levels of a cycle with block
+// barriers between the steps.  Every kernel starts with griddepcontrol.wait
+// followed by griddepcontrol.launch_dependents: with programmatic dependent
+// launch the next kernel of a captured cycle is scheduled while this one
+// runs, and its own griddepcontrol.wait holds it until this grid has
+// completed and its memory is visible.
 #pragma once
 
 #include <cstdint>
@@ -23,6 +32,8 @@ namespace mgk {
 
 constexpr int kThreads = 256;
 constexpr int kSlice = 32;
+constexpr int kMaxLevels = 16;
+constexpr int kTailThreads = 1024;
 
 // Parameter block per level, in the order used everywhere:
 // theta, eta, wB1, wB2, wR1, wR2, wP1, wP2.
@@ -43,27 +54,11 @@ struct LV {
   const T* __restrict__ r_w;
 };
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 __device__ __forceinline__ int slice_begin(const int* sl_ptr, int i) {
   return sl_ptr[i >> 5] + (i & 31);
-}
-
-// sum_{j != i} a_ij x_j  and  sum_{j in N(i)} x_j for one right-hand side.
-template <class T>
-__device__ __forceinline__ void row_offdiag(const LV<T>& L, int i, const T* __restrict__ x,
-                                            int B, int b, T& ax, T& sx) {
-  const int beg = slice_begin(L.sl_ptr, i);
-  const int end = L.sl_ptr[(i >> 5) + 1];
-  T a_acc = T(0), s_acc = T(0);
-  for (int e = beg; e < end; e += kSlice) {
-    const int c = L.col[e];
-    if (c >= 0) {
-      const T xv = x[(size_t)c * B + b];
-      a_acc = fma(L.val[e], xv, a_acc);
-      s_acc += xv;
-    }
-  }
-  ax = a_acc;
-  sx = s_acc;
 }
 
 template <class T>
@@ -90,14 +85,25 @@ __device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict_
   return s_acc;
 }
 
-// out = alpha * [dinv] * (f - A u).  u_zero: u is taken as 0 and not read.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restrict__ f,
-                                                       const T* __restrict__ u, T* __restrict__ out,
-                                                       int B, const T* __restrict__ prm, int scale,
-                                                       int u_zero) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.n * B) return;
+__device__ __forceinline__ T prolong_at(const LV<T>& L, int j, const T* __restrict__ ec, int B,
+                                        int b) {
+  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
+  T v = T(0);
+  if (a >= 0) v = L.p_w[j] * ec[(size_t)a * B + b];
+  if (c >= 0) v = fma(L.p_w[(size_t)L.n + j], ec[(size_t)c * B + b], v);
+  return v;
+}
+
+// ------------------------------------------------------ element steps ----
+// t indexes (row, rhs) = (t / B, t % B) of the level the step writes.
+
+// out = [theta dinv] (f - A u).  u_zero: u is taken as 0 and not read.
+template <class T>
+__device__ __forceinline__ void residual_el(const LV<T>& L, const T* __restrict__ f,
+                                            const T* __restrict__ u, T* __restrict__ out, int B,
+                                            const T* __restrict__ prm, int scale, int u_zero,
+                                            size_t t) {
   const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
   T r = f[t];
   if (!u_zero) {
@@ -110,11 +116,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restr
 
 // u <- u + eta * (wB1 * x + wB2 * mean_{N(i)} x)   (Phi_B applied to delta = x)
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
-                                                          T* __restrict__ u, int B,
-                                                          const T* __restrict__ prm, int u_zero) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.n * B) return;
+__device__ __forceinline__ void conv_update_el(const LV<T>& L, const T* __restrict__ x,
+                                               T* __restrict__ u, int B, const T* __restrict__ prm,
+                                               int u_zero, size_t t) {
   const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
   const T s = row_sum(L, i, x, B, b);
   const T phi = fma(prm[P_WB1], x[t], prm[P_WB2] * (L.invdeg[i] * s));
@@ -122,15 +126,13 @@ __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __re
   u[t] = fma(prm[P_ETA], phi, u0);
 }
 
-// Smoothing step with Phi_B = w1 I (w2 = 0): one pass, Jacobi needs the old
-// iterate everywhere, so the result goes to a second buffer.
+// Smoothing step with Phi_B = w1 I (w2 = 0) in one pass; Jacobi needs the
+// old iterate everywhere, so the result goes to a second buffer.
 // uout = uin + eta * w1 * theta * dinv * (f - A uin)
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
-                                                     const T* __restrict__ uin, T* __restrict__ uout,
-                                                     int B, const T* __restrict__ prm, int u_zero) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.n * B) return;
+__device__ __forceinline__ void jacobi_el(const LV<T>& L, const T* __restrict__ f,
+                                          const T* __restrict__ uin, T* __restrict__ uout, int B,
+                                          const T* __restrict__ prm, int u_zero, size_t t) {
   const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
   T r = f[t];
   T u0 = T(0);
@@ -143,13 +145,11 @@ __global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restric
   uout[t] = fma(prm[P_ETA], prm[P_WB1] * delta, u0);
 }
 
-// fc_I = sum_{i in children(I)} P_iI * (wR1 r_i + wR2 mean_{N(i)} r)
+// fc_I = sum_{i in children(I)} P_iI * (wR1 r_i + wR2 mean_{N(i)} r); t over nc*B
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restrict__ r,
-                                                       T* __restrict__ fc, int B,
-                                                       const T* __restrict__ prm, int conv) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.nc * B) return;
+__device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict__ r,
+                                            T* __restrict__ fc, int B, const T* __restrict__ prm,
+                                            int conv, size_t t) {
   const int I = (int)(t / B), b = (int)(t - (size_t)I * B);
   const T w1 = prm[P_WR1], w2 = prm[P_WR2];
   T acc = T(0);
@@ -163,23 +163,11 @@ __global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restr
   fc[t] = acc;
 }
 
+// u_i = uin_i + wP1 (P ec)_i + wP2 mean_{N(i)} (P ec)   (uin may equal u)
 template <class T>
-__device__ __forceinline__ T prolong_at(const LV<T>& L, int j, const T* __restrict__ ec, int B,
-                                        int b) {
-  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
-  T v = T(0);
-  if (a >= 0) v = L.p_w[j] * ec[(size_t)a * B + b];
-  if (c >= 0) v = fma(L.p_w[(size_t)L.n + j], ec[(size_t)c * B + b], v);
-  return v;
-}
-
-// u_i += wP1 (P ec)_i + wP2 mean_{N(i)} (P ec)
-template <class T>
-__global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restrict__ ec,
-                                                      const T* uin, T* u,
-                                                      int B, const T* __restrict__ prm, int conv) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.n * B) return;
+__device__ __forceinline__ void prolong_el(const LV<T>& L, const T* __restrict__ ec, const T* uin,
+                                           T* u, int B, const T* __restrict__ prm, int conv,
+                                           size_t t) {
   const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
   T phi = prm[P_WP1] * prolong_at(L, i, ec, B, b);
   if (conv) {
@@ -197,13 +185,16 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restri
 
 // Coarsest level: u = A_J^{-1} f by the FP64 Cholesky factor A_J = L L^T.
 // Lc: L column-major (L[i + j n]); Uc: L^T column-major; dinv: 1/L_jj.
-// One warp per right-hand side, column-oriented substitution in shared memory.
+// Warps 0..nw-1 of the block take one right-hand side each in turn; column-
+// oriented substitution in shared memory ys[nw][n].
 template <class T>
-__global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __restrict__ Uc,
-                              const double* __restrict__ dinv, int n, const T* __restrict__ f,
-                              T* __restrict__ u, int B) {
-  extern __shared__ double ys[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+__device__ __forceinline__ void coarse_chol_block(const double* __restrict__ Lc,
+                                                  const double* __restrict__ Uc,
+                                                  const double* __restrict__ dinv, int n,
+                                                  const T* __restrict__ f, T* __restrict__ u,
+                                                  int B, int nw, double* ys) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp >= nw) return;
   double* y = ys + (size_t)warp * n;
   for (int b = warp; b < B; b += nw) {
     for (int i = lane; i < n; i += 32) y[i] = (double)f[(size_t)i * B + b];
@@ -225,6 +216,226 @@ __global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __res
     for (int i = lane; i < n; i += 32) u[(size_t)i * B + b] = (T)y[i];
     __syncwarp();
   }
+}
+
+// ------------------------------------------------------- grid kernels ----
+
+#define MG_GRID_PROLOGUE(N)                                                 \
+  pdl_wait();                                                               \
+  pdl_launch();                                                             \
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;           \
+  const bool in_range = t < (size_t)(N);
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restrict__ f,
+                                                       const T* __restrict__ u, T* __restrict__ out,
+                                                       int B, const T* __restrict__ prm, int scale,
+                                                       int u_zero) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) residual_el(L, f, u, out, B, prm, scale, u_zero, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
+                                                          T* __restrict__ u, int B,
+                                                          const T* __restrict__ prm, int u_zero) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) conv_update_el(L, x, u, B, prm, u_zero, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
+                                                     const T* __restrict__ uin, T* __restrict__ uout,
+                                                     int B, const T* __restrict__ prm, int u_zero) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) jacobi_el(L, f, uin, uout, B, prm, u_zero, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restrict__ r,
+                                                       T* __restrict__ fc, int B,
+                                                       const T* __restrict__ prm, int conv) {
+  MG_GRID_PROLOGUE((size_t)L.nc * B)
+  if (in_range) restrict_el(L, r, fc, B, prm, conv, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restrict__ ec,
+                                                      const T* uin, T* u, int B,
+                                                      const T* __restrict__ prm, int conv) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) prolong_el(L, ec, uin, u, B, prm, conv, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_copy(const T* __restrict__ x, T* __restrict__ y,
+                                                   size_t n) {
+  MG_GRID_PROLOGUE(n)
+  if (in_range) y[t] = x[t];
+  pdl_launch();
+}
+
+template <class T>
+__global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __restrict__ Uc,
+                              const double* __restrict__ dinv, int n, const T* __restrict__ f,
+                              T* __restrict__ u, int B) {
+  extern __shared__ double ys[];
+  pdl_wait();
+  pdl_launch();
+  coarse_chol_block(Lc, Uc, dinv, n, f, u, B, (int)(blockDim.x >> 5), ys);
+  pdl_launch();
+}
+
+// ------------------------------------------------------ small levels -----
+
+// All levels lt..J-1 of one V-cycle in a single block: down (smoothing,
+// residual, restriction), the coarsest Cholesky solve, up (prolongation,
+// smoothing).  Level lt's right-hand side is f[lt]; its result is u[lt].
+template <class T>
+struct TailArgs {
+  int lt, J, B, nu_pre, nu_post, nJ, cwarps, lt_zero, smem_vectors;
+  unsigned convB, convR, convP;  // bit l: w2 != 0 on level l
+  LV<T> L[kMaxLevels];
+  const T* f[kMaxLevels];
+  T* u[kMaxLevels];
+  T* t[kMaxLevels];
+  T* u2[kMaxLevels];
+  const T* prm;
+  const double* cL;
+  const double* cU;
+  const double* cDinv;
+};
+
+// Vectors of the small levels: in shared memory when a.smem_vectors (the
+// usual case), else the global level buffers.
+template <class T>
+struct TailVecs {
+  T* u[kMaxLevels];
+  T* f[kMaxLevels];
+  T* t[kMaxLevels];
+  T* u2[kMaxLevels];
+};
+
+__host__ __device__ inline size_t tail_align(size_t x) { return (x + 15) & ~size_t(15); }
+
+// Dynamic shared memory of k_tail: Cholesky scratch, then u, f, t, u2 of
+// every level lt..J-1 when the vectors live in shared memory.
+template <class T>
+__host__ __device__ inline size_t tail_smem_bytes(const int* n, int lt, int J, int B, int nJ,
+                                                  int cwarps, bool vectors) {
+  size_t off = tail_align((size_t)cwarps * nJ * sizeof(double));
+  if (vectors)
+    for (int l = lt; l < J; ++l) off += 4 * tail_align((size_t)n[l] * B * sizeof(T));
+  return off;
+}
+
+template <class T>
+__device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const TailVecs<T>& v, int l,
+                                            int nu, bool zero) {
+  const LV<T>& L = a.L[l];
+  const size_t N = (size_t)L.n * a.B;
+  const T* prm = a.prm + (size_t)l * P_COUNT;
+  if ((a.convB >> l) & 1u) {
+    for (int k = 0; k < nu; ++k) {
+      const int z = zero && k == 0;
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 1, z, t);
+      __syncthreads();
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        conv_update_el(L, (const T*)v.t[l], v.u[l], a.B, prm, z, t);
+      __syncthreads();
+    }
+  } else {
+    T* cur = v.u[l];
+    T* oth = v.u2[l];
+    for (int k = 0; k < nu; ++k) {
+      const int z = zero && k == 0;
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        jacobi_el(L, (const T*)v.f[l], (const T*)cur, oth, a.B, prm, z, t);
+      __syncthreads();
+      T* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+    if (cur != v.u[l]) {
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x) v.u[l][t] = cur[t];
+      __syncthreads();
+    }
+  }
+  if (nu == 0 && zero) {
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x) v.u[l][t] = T(0);
+    __syncthreads();
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char tail_smem[];
+  double* ys = (double*)tail_smem;
+  pdl_wait();
+  pdl_launch();
+  const int J = a.J, lt = a.lt;
+  TailVecs<T> v;
+  if (a.smem_vectors) {
+    size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+    for (int l = lt; l < J; ++l) {
+      const size_t bytes = tail_align((size_t)a.L[l].n * a.B * sizeof(T));
+      v.u[l] = (T*)(tail_smem + off);
+      v.f[l] = (T*)(tail_smem + off + bytes);
+      v.t[l] = (T*)(tail_smem + off + 2 * bytes);
+      v.u2[l] = (T*)(tail_smem + off + 3 * bytes);
+      off += 4 * bytes;
+    }
+    const size_t N = (size_t)a.L[lt].n * a.B;
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x) {
+      v.f[lt][t] = a.f[lt][t];
+      if (!a.lt_zero) v.u[lt][t] = a.u[lt][t];
+    }
+    __syncthreads();
+  } else {
+    for (int l = lt; l < J; ++l) {
+      v.u[l] = a.u[l];
+      v.f[l] = (T*)a.f[l];
+      v.t[l] = a.t[l];
+      v.u2[l] = a.u2[l];
+    }
+  }
+  for (int l = lt; l < J - 1; ++l) {
+    const LV<T>& L = a.L[l];
+    const T* prm = a.prm + (size_t)l * P_COUNT;
+    tail_smooth(a, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true);
+    const size_t N = (size_t)L.n * a.B;
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 0, 0, t);
+    __syncthreads();
+    const size_t Nc = (size_t)L.nc * a.B;
+    for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
+      restrict_el(L, (const T*)v.t[l], v.f[l + 1], a.B, prm, (int)((a.convR >> l) & 1u), t);
+    __syncthreads();
+  }
+  coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, a.cwarps,
+                    ys);
+  __syncthreads();
+  for (int l = J - 2; l >= lt; --l) {
+    const LV<T>& L = a.L[l];
+    const T* prm = a.prm + (size_t)l * P_COUNT;
+    const size_t N = (size_t)L.n * a.B;
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], a.B, prm,
+                 (int)((a.convP >> l) & 1u), t);
+    __syncthreads();
+    tail_smooth(a, v, l, a.nu_post, false);
+  }
+  if (a.smem_vectors) {
+    const size_t N = (size_t)a.L[lt].n * a.B;
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x) a.u[lt][t] = v.u[lt][t];
+  }
+  pdl_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -252,6 +463,7 @@ __global__ void __launch_bounds__(kThreads) k_resid64(LV<double> L, const double
                                                       float* __restrict__ rhat,
                                                       const int* __restrict__ sexp, int B,
                                                       double* __restrict__ partial) {
+  pdl_wait();
   __shared__ double sh[kThreads];
   const int R = kThreads / B;
   const int t = threadIdx.x;
@@ -274,6 +486,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual64(LV<double> L,
                                                                const double* __restrict__ f,
                                                                const double* __restrict__ u,
                                                                double* __restrict__ out, int B) {
+  pdl_wait();
   const int R = kThreads / B;
   const int t = threadIdx.x;
   const int i = blockIdx.x * R + t / B, b = t % B;
@@ -286,6 +499,7 @@ __global__ void __launch_bounds__(kThreads) k_outer_residual64(LV<double> L,
 // partial sums of x^2 (FP64), same block mapping as k_resid64.
 __global__ void __launch_bounds__(kThreads) k_sumsq64(const double* __restrict__ x, int n, int B,
                                                       double* __restrict__ partial) {
+  pdl_wait();
   __shared__ double sh[kThreads];
   const int R = kThreads / B;
   const int t = threadIdx.x;
@@ -301,6 +515,7 @@ __global__ void __launch_bounds__(kThreads) k_sumsq64(const double* __restrict__
 // out[b] = sum over blocks of partial[blk * B + b]; grid = B blocks.
 __global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ partial, int nblk,
                                                      int B, double* __restrict__ out) {
+  pdl_wait();
   __shared__ double sh[kThreads];
   const int b = blockIdx.x;
   double s = 0.0;
@@ -314,13 +529,18 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ 
   if (threadIdx.x == 0) out[b] = sh[0];
 }
 
-// Convergence test per right-hand side; one block.  state[0] = number still
-// active, state[1] = 1 if a residual is not finite.
+// Convergence test per right-hand side; one block.  ctl = (tol, max_iter).
+// state[0] = right-hand sides still active, state[1] = 1 if a residual is not
+// finite, state[2] = iterations done (reset when inc == 0, else +1).  Sets
+// the enclosing while-node's condition: continue while some right-hand side
+// is active, all residuals are finite and fewer than max_iter iterations ran.
 __global__ void k_check(const double* __restrict__ rsum, const double* __restrict__ fsum, int B,
-                        const double* __restrict__ tolp, int* __restrict__ active, double* __restrict__ relres,
-                        int* __restrict__ sexp, int* __restrict__ state) {
+                        const double* __restrict__ ctl, int* __restrict__ active,
+                        double* __restrict__ relres, int* __restrict__ sexp,
+                        int* __restrict__ state, int inc, cudaGraphConditionalHandle h) {
+  pdl_wait();
   __shared__ int cnt, bad;
-  const double tol = *tolp;
+  const double tol = ctl[0];
   if (threadIdx.x == 0) { cnt = 0; bad = 0; }
   __syncthreads();
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
@@ -333,7 +553,14 @@ __global__ void k_check(const double* __restrict__ rsum, const double* __restric
     sexp[b] = rn > 0.0 && isfinite(rn) ? ilogb(rn) : 0;
   }
   __syncthreads();
-  if (threadIdx.x == 0) { state[0] = cnt; state[1] = bad; }
+  if (threadIdx.x == 0) {
+    const int it = inc ? state[2] + 1 : 0;
+    state[0] = cnt;
+    state[1] = bad;
+    state[2] = it;
+    const int go = cnt > 0 && bad == 0 && (double)it < ctl[1];
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+  }
 }
 
 // u += 2^sexp[b] * c for the right-hand sides still active (refinement update).
@@ -342,6 +569,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_update(double* __restrict__
                                                             const int* __restrict__ sexp,
                                                             const int* __restrict__ active, int n,
                                                             int B, int* __restrict__ iters) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < (size_t)B && active[t]) iters[t] += 1;
   if (t >= (size_t)n * B) return;
@@ -354,6 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_masked_copy(double* __restrict__ u
                                                           const double* __restrict__ w,
                                                           const int* __restrict__ active, int n,
                                                           int B, int* __restrict__ iters) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < (size_t)B && active[t]) iters[t] += 1;
   if (t >= (size_t)n * B) return;

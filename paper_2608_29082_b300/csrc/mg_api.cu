@@ -204,7 +204,8 @@ bool cholesky(const mg_csr& A, std::vector<double>& Lc) {
 
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
-  int nkernels = 0;
+  int nkernels = 0;  // kernels per launch (outside any loop body)
+  int nbody = 0;     // kernels per iteration of a while-node body
 };
 
 }  // namespace
@@ -230,12 +231,16 @@ struct mg_ctx {
       *state = nullptr;
   float *c32 = nullptr, *rhat32 = nullptr;
   int* h_state = nullptr;  // pinned [2]
-  double* tol_dev = nullptr;
+  double* tol_dev = nullptr;      // device [2]: tol, max_iter
+  double solve_ctl[2] = {0, 0};   // host staging of tol_dev
   double *hf = nullptr, *hu = nullptr;  // device buffers for mg_solve_host
   cudaStream_t cap = nullptr;
   std::map<std::tuple<int, const void*, const void*, int, uint32_t>, GraphEntry> graphs;
   std::string err;
   int64_t launches = 0;
+  // options (mg_set_option)
+  int64_t opt_tail_work = 2048;  // rows x rhs at or below which levels run in k_tail
+  int opt_pdl = 1;               // programmatic dependent launch between kernels
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
   int trK = 0, trB = 0, tr_nu_pre = -1, tr_nu_post = -1;
@@ -346,6 +351,9 @@ std::string read_params(const mg_params* p, int J, std::vector<double>& out, int
 
 inline dim3 grid_for(size_t work) { return dim3((unsigned)((work + kThreads - 1) / kThreads)); }
 
+// Dynamic shared memory the small-level block may use (of 227 KB per block).
+constexpr size_t kTailSmemMax = 200 * 1024;
+
 // Issues the kernels of one V-cycle (or one level step) on a stream.
 template <class T>
 struct Issue {
@@ -375,12 +383,32 @@ struct Issue {
     return c->prm[(size_t)lev * mgk::P_COUNT + which] != 0.0;
   }
 
+  // Kernel launch; with programmatic dependent launch enabled the next
+  // kernel in the stream (or captured graph) is scheduled while this one
+  // drains and waits in griddepcontrol.wait for its completion.
+  template <class... KArgs, class... Args>
+  void launch(void (*kern)(KArgs...), dim3 g, dim3 b, size_t smem, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->opt_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+    ++nk;
+  }
+
   // nu smoothing steps on level lev; u updated in place.  zero: u is 0 on entry.
   void smooth(int lev, const T* f, T* u, int nu, bool zero) {
     DevLevel<T>& D = L[lev];
-    const dim3 g = grid_for((size_t)D.n * B);
+    const size_t N = (size_t)D.n * B;
+    const dim3 g = grid_for(N);
     if (nu == 0) {
-      if (zero) cudaMemsetAsync(u, 0, (size_t)D.n * B * sizeof(T), s);
+      if (zero) cudaMemsetAsync(u, 0, N * sizeof(T), s);
       return;
     }
     if (!conv(lev, mgk::P_WB2)) {
@@ -388,58 +416,110 @@ struct Issue {
       T* oth = D.u2;
       for (int k = 0; k < nu; ++k) {
         pre(MG_K_JACOBI, lev);
-        mgk::k_jacobi<T><<<g, kThreads, 0, s>>>(D.view(), f, cur, oth, B, P(lev), zero && k == 0);
+        launch(mgk::k_jacobi<T>, g, kThreads, 0, D.view(), (const T*)f, (const T*)cur, oth, B,
+               P(lev), (int)(zero && k == 0));
         post();
-        ++nk;
         std::swap(cur, oth);
       }
-      if (cur != u) cudaMemcpyAsync(u, cur, (size_t)D.n * B * sizeof(T), cudaMemcpyDeviceToDevice, s);
+      if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
       return;
     }
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       pre(MG_K_RESIDUAL_SCALED, lev);
-      mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, u, D.t, B, P(lev), 1, z);
+      launch(mgk::k_residual<T>, g, kThreads, 0, D.view(), (const T*)f, (const T*)u, D.t, B,
+             P(lev), 1, z);
       post();
       pre(MG_K_CONV_UPDATE, lev);
-      mgk::k_conv_update<T><<<g, kThreads, 0, s>>>(D.view(), D.t, u, B, P(lev), z);
+      launch(mgk::k_conv_update<T>, g, kThreads, 0, D.view(), (const T*)D.t, u, B, P(lev), z);
       post();
-      nk += 2;
     }
   }
 
   void restrict_(int lev, const T* f, const T* u) {
     DevLevel<T>& D = L[lev];
     pre(MG_K_RESIDUAL, lev);
-    mgk::k_residual<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), f, u, D.t, B,
-                                                                      P(lev), 0, 0);
+    launch(mgk::k_residual<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), (const T*)f,
+           (const T*)u, D.t, B, P(lev), 0, 0);
     post();
     pre(MG_K_RESTRICT, lev);
-    mgk::k_restrict<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
-        D.view(), D.t, Fl(lev + 1), B, P(lev), conv(lev, mgk::P_WR2));
+    launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
+           (const T*)D.t, Fl(lev + 1), B, P(lev), (int)conv(lev, mgk::P_WR2));
     post();
-    nk += 2;
   }
 
   void prolong(int lev, const T* ec, T* u) {
     DevLevel<T>& D = L[lev];
     pre(MG_K_PROLONG, lev);
-    mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
-        D.view(), ec, u, u, B, P(lev), conv(lev, mgk::P_WP2));
+    launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec,
+           (const T*)u, u, B, P(lev), (int)conv(lev, mgk::P_WP2));
     post();
-    ++nk;
+  }
+
+  int coarse_warps(int cap) const {
+    return std::max(1, std::min(std::min(B, cap), 6144 / std::max(1, c->nJ)));
   }
 
   void coarse(const T* f, T* u) {
-    const int nw = std::max(1, std::min(std::min(B, 8), 6144 / std::max(1, c->nJ)));
+    const int nw = coarse_warps(8);
     pre(MG_K_COARSE_CHOL, c->J - 1);
-    mgk::k_coarse_chol<T><<<1, 32 * nw, (size_t)nw * c->nJ * sizeof(double), s>>>(
-        c->cholL, c->cholU, c->cholDinv, c->nJ, f, u, B);
+    launch(mgk::k_coarse_chol<T>, dim3(1), dim3(32 * nw), (size_t)nw * c->nJ * sizeof(double),
+           (const double*)c->cholL, (const double*)c->cholU, (const double*)c->cholDinv, c->nJ,
+           f, u, B);
     post();
-    ++nk;
   }
 
-  // Algorithm 2 from level 0 with f0/u0 as the level-0 vectors.
+  // First level handled by the single-block tail for this batch size (J-1:
+  // no tail, only the coarse solve).
+  int tail_level() const {
+    if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels) return c->J - 1;
+    int lt = c->J - 1;
+    while (lt > 0 && (int64_t)c->n[lt - 1] * B <= c->opt_tail_work) --lt;
+    // the small levels' vectors must fit in shared memory
+    while (lt < c->J - 1 &&
+           mgk::tail_smem_bytes<T>(c->n.data(), lt, c->J, B, c->nJ, coarse_warps(32), true) >
+               kTailSmemMax)
+      ++lt;
+    return lt;
+  }
+
+  void tail(int lt, const T* f0, T* u0, bool u0_zero) {
+    mgk::TailArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.lt = lt;
+    a.J = c->J;
+    a.B = B;
+    a.nu_pre = c->nu_pre;
+    a.nu_post = c->nu_post;
+    a.nJ = c->nJ;
+    a.cwarps = coarse_warps(32);
+    a.lt_zero = lt == 0 ? (int)u0_zero : 1;
+    for (int l = 0; l < c->J; ++l) {
+      a.L[l] = L[l].view();
+      a.f[l] = l == 0 ? f0 : Fl(l);
+      a.u[l] = l == 0 ? u0 : Ul(l);
+      a.t[l] = L[l].t;
+      a.u2[l] = L[l].u2;
+      if (l < c->J - 1) {
+        a.convB |= (conv(l, mgk::P_WB2) ? 1u : 0u) << l;
+        a.convR |= (conv(l, mgk::P_WR2) ? 1u : 0u) << l;
+        a.convP |= (conv(l, mgk::P_WP2) ? 1u : 0u) << l;
+      }
+    }
+    a.prm = prm;
+    a.cL = c->cholL;
+    a.cU = c->cholU;
+    a.cDinv = c->cholDinv;
+    // a recorded forward must leave every level's f and u in its checkpoint
+    // buffers, so it keeps the small levels' vectors in global memory
+    const bool smv = fov == nullptr && uov == nullptr;
+    a.smem_vectors = smv ? 1 : 0;
+    pre(MG_K_TAIL, lt);
+    launch(mgk::k_tail<T>, dim3(1), dim3(mgk::kTailThreads),
+           mgk::tail_smem_bytes<T>(c->n.data(), lt, c->J, B, c->nJ, a.cwarps, smv), a);
+    post();
+  }
+
   // Level vectors of levels >= 1; training points them at checkpoint storage.
   T* const* fov = nullptr;
   T* const* uov = nullptr;
@@ -448,14 +528,18 @@ struct Issue {
 
   void vcycle(const T* f0, T* u0, bool u0_zero) {
     const int J = c->J;
-    for (int lev = 0; lev < J - 1; ++lev) {
+    const int lt = tail_level();
+    for (int lev = 0; lev < lt; ++lev) {
       const T* f = lev == 0 ? f0 : Fl(lev);
       T* u = lev == 0 ? u0 : Ul(lev);
       smooth(lev, f, u, c->nu_pre, lev == 0 ? u0_zero : true);
       restrict_(lev, f, u);
     }
-    coarse(Fl(J - 1), Ul(J - 1));
-    for (int lev = J - 2; lev >= 0; --lev) {
+    if (lt < J - 1)
+      tail(lt, f0, u0, u0_zero);
+    else
+      coarse(Fl(J - 1), Ul(J - 1));
+    for (int lev = lt - 1; lev >= 0; --lev) {
       const T* f = lev == 0 ? f0 : Fl(lev);
       T* u = lev == 0 ? u0 : Ul(lev);
       prolong(lev, Ul(lev + 1), u);
@@ -648,6 +732,12 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
+  if ((e = cudaFuncSetAttribute(mgk::k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTailSmemMax)) != cudaSuccess)
+    return bail(e);
+  if ((e = cudaFuncSetAttribute(mgk::k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kTailSmemMax)) != cudaSuccess)
+    return bail(e);
   if (precision == 64) {
     c->d64.resize(J);
     for (int l = 0; l < J; ++l)
@@ -675,9 +765,9 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
     if ((e = cudaMalloc(q, maxB * sizeof(double))) != cudaSuccess) return bail(e);
   for (int** q : {&c->active, &c->iters, &c->sexp, &c->sexp_prev})
     if ((e = cudaMalloc(q, maxB * sizeof(int))) != cudaSuccess) return bail(e);
-  if ((e = cudaMalloc(&c->state, 2 * sizeof(int))) != cudaSuccess) return bail(e);
-  if ((e = cudaMalloc(&c->tol_dev, sizeof(double))) != cudaSuccess) return bail(e);
-  if ((e = cudaMallocHost(&c->h_state, 2 * sizeof(int))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->state, 4 * sizeof(int))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->tol_dev, 2 * sizeof(double))) != cudaSuccess) return bail(e);
+  if ((e = cudaMallocHost(&c->h_state, 4 * sizeof(int))) != cudaSuccess) return bail(e);
   if (precision == 64) {
     if ((e = cudaMalloc(&c->w64, v64)) != cudaSuccess) return bail(e);
   } else {
@@ -777,64 +867,125 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
   const int nblk = (n0 + R - 1) / R;
   const LV<double> L0 = c->d64[0].view();
   const bool p32 = c->prec == 32;
+  c->solve_ctl[0] = tol;
+  c->solve_ctl[1] = (double)max_iter;
+  MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
 
-  // residual of the current iterate, its norms and the convergence test
-  auto check_tail = [&](cudaStream_t cs) {
-    mgk::k_resid64<<<nblk, kThreads, 0, cs>>>(L0, f, u, p32 ? c->rhat32 : nullptr, c->sexp, B,
-                                              c->partial);
-    mgk::k_reduce<<<B, kThreads, 0, cs>>>(c->partial, nblk, B, c->rsum);
-    if (p32) k_shift_sexp<<<1, kThreads, 0, cs>>>(c->sexp, c->sexp_prev, B);
-    mgk::k_check<<<1, kThreads, 0, cs>>>(c->rsum, c->fsum, B, c->tol_dev, c->active, c->relres, c->sexp,
-                                         c->state);
-    return p32 ? 4 : 3;
-  };
-  MG_CUDA(cudaMemcpyAsync(c->tol_dev, &tol, sizeof(double), cudaMemcpyHostToDevice, s));
-  auto kinit = std::make_tuple(10, (const void*)f, (const void*)u, (int)B, c->structure);
-  st = run_graph(c, kinit, s, [&](cudaStream_t cs) {
-    mgk::k_sumsq64<<<nblk, kThreads, 0, cs>>>(f, n0, B, c->partial);
-    mgk::k_reduce<<<B, kThreads, 0, cs>>>(c->partial, nblk, B, c->fsum);
-    k_init_solve<<<1, kThreads, 0, cs>>>(c->fsum, B, c->active, c->iters, c->sexp);
-    return 3 + check_tail(cs);
-  });
-  if (st != MG_OK) return st;
-  auto kiter = std::make_tuple(11, (const void*)f, (const void*)u, (int)B, c->structure);
-  int it = 0;
-  mg_status result = MG_OK;
-  for (;;) {
-    MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
-    MG_CUDA(cudaStreamSynchronize(s));
-    if (c->h_state[1]) { result = MG_ERR_DIVERGED; break; }
-    if (c->h_state[0] == 0) break;
-    if (it == max_iter) { result = MG_NOT_CONVERGED; break; }
-    st = run_graph(c, kiter, s, [&](cudaStream_t cs) {
-      int nk = 0;
-      if (p32) {
-        Issue<float> is{c, c->d32, c->prm32, cs, B};
-        is.vcycle(c->rhat32, c->c32, true);
-        nk += is.nk;
-        mgk::k_refine_update<<<grid_for((size_t)n0 * B), kThreads, 0, cs>>>(
-            u, c->c32, c->sexp_prev, c->active, n0, B, c->iters);
-        ++nk;
-      } else if (B == 1) {
-        Issue<double> is{c, c->d64, c->prm64, cs, B};
+  auto key = std::make_tuple(30, (const void*)f, (const void*)u, (int)B, c->structure);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    // residual of the current iterate, its norms and the convergence test;
+    // the test sets the while-node condition
+    auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc) {
+      is.launch(mgk::k_resid64, dim3(nblk), dim3(kThreads), 0, L0, (const double*)f,
+                (const double*)u, p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B,
+                c->partial);
+      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
+                (int)B, c->rsum);
+      if (p32) is.launch(k_shift_sexp, dim3(1), dim3(kThreads), 0, c->sexp, c->sexp_prev, (int)B);
+      is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+                (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
+                c->sexp, c->state, inc, h);
+    };
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    int nk_init = 0, nk_body = 0;
+    MG_CUDA(cudaGraphCreate(&g, 0));
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    {
+      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
+      is.launch(mgk::k_sumsq64, dim3(nblk), dim3(kThreads), 0, f, n0, (int)B, c->partial);
+      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
+                (int)B, c->fsum);
+      is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B,
+                c->active, c->iters, c->sexp);
+      check_tail(is, h, 0);
+      nk_init = is.nk;
+    }
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    cudaGraphNode_t wnode;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, &edges, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, capg, deps, edges, ndeps, &np);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return c->fail(MG_ERR_CUDA, std::string("mg_solve: graph build: ") +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    if (p32) {
+      Issue<float> is{c, c->d32, c->prm32, c->cap, B};
+      is.vcycle(c->rhat32, c->c32, true);
+      is.launch(mgk::k_refine_update, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
+                (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0,
+                (int)B, c->iters);
+      nk_body += is.nk;
+      Issue<double> is2{c, c->d64, c->prm64, c->cap, B};
+      check_tail(is2, h, 1);
+      nk_body += is2.nk;
+    } else {
+      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
+      if (B == 1) {
         is.vcycle(f, u, false);
-        nk += is.nk;
-        k_bump_iters<<<1, kThreads, 0, cs>>>(c->active, c->iters, B);
-        ++nk;
+        is.launch(k_bump_iters, dim3(1), dim3(kThreads), 0, (const int*)c->active, c->iters,
+                  (int)B);
       } else {
-        cudaMemcpyAsync(c->w64, u, (size_t)n0 * B * sizeof(double), cudaMemcpyDeviceToDevice, cs);
-        Issue<double> is{c, c->d64, c->prm64, cs, B};
+        is.launch(mgk::k_copy<double>, grid_for((size_t)n0 * B), dim3(kThreads), 0,
+                  (const double*)u, c->w64, (size_t)n0 * B);
         is.vcycle(f, c->w64, false);
-        nk += is.nk;
-        mgk::k_masked_copy<<<grid_for((size_t)n0 * B), kThreads, 0, cs>>>(u, c->w64, c->active,
-                                                                           n0, B, c->iters);
-        ++nk;
+        is.launch(mgk::k_masked_copy, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
+                  (const double*)c->w64, (const int*)c->active, n0, (int)B, c->iters);
       }
-      return nk + check_tail(cs);
-    });
-    if (st != MG_OK) return st;
-    ++it;
+      check_tail(is, h, 1);
+      nk_body += is.nk;
+    }
+    cudaGraph_t body_out = nullptr;
+    e = cudaGetLastError();
+    e2 = cudaStreamEndCapture(c->cap, &body_out);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return c->fail(MG_ERR_CUDA, std::string("mg_solve: body capture: ") +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    GraphEntry ge;
+    ge.nkernels = nk_init;
+    ge.nbody = nk_body;
+    e = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+      return c->fail(MG_ERR_CUDA, std::string("mg_solve: instantiate: ") + cudaGetErrorString(e));
+    if (c->graphs.size() > 64) {
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+    }
+    it = c->graphs.emplace(key, ge).first;
   }
+  MG_CUDA(cudaGraphLaunch(it->second.exec, s));
+  MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  const int iters_done = c->h_state[2];
+  c->launches += it->second.nkernels + (int64_t)iters_done * it->second.nbody;
+  mg_status result = MG_OK;
+  if (c->h_state[1])
+    result = MG_ERR_DIVERGED;
+  else if (c->h_state[0] > 0)
+    result = MG_NOT_CONVERGED;
   if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
   if (relres_out)
     MG_CUDA(cudaMemcpy(relres_out, c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
@@ -942,6 +1093,7 @@ extern "C" const char* mg_kernel_name(int32_t kind) {
     case MG_K_PROLONG: return "prolong_conv";
     case MG_K_COARSE_CHOL: return "coarse_cholesky";
     case MG_K_OUTER_RESIDUAL: return "outer_residual_fp64";
+    case MG_K_TAIL: return "small_levels_block";
     default: return "unknown";
   }
 }
@@ -987,3 +1139,21 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
 }
 
 #include "train_impl.cuh"
+
+extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_option: ctx is NULL");
+  switch (option) {
+    case MG_OPT_TAIL_WORK:
+      if (value < 0) return c->fail(MG_ERR_INVALID, "mg_set_option: tail work must be >= 0");
+      c->opt_tail_work = value;
+      break;
+    case MG_OPT_PDL:
+      c->opt_pdl = value != 0;
+      break;
+    default:
+      return c->fail(MG_ERR_INVALID, "mg_set_option: unknown option");
+  }
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+  return MG_OK;
+}

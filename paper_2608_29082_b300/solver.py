@@ -194,6 +194,10 @@ class Solver:
         return [(self.lib.mg_kernel_name(buf[k].kernel).decode(), buf[k].level, buf[k].ms)
                 for k in range(n.value)]
 
+    def set_option(self, name: str, value: int):
+        """Launch-shape options ("tail_work", "pdl"); results are unchanged."""
+        L.check(self.lib.mg_set_option(self.ctx, L.OPTIONS[name], int(value)), self.ctx)
+
     # ------------------------------------------------------------ training
     def forward_record(self, f: torch.Tensor, u: torch.Tensor, n_cycles: int) -> torch.Tensor:
         """n_cycles cycles on u in place, recording per-level checkpoints."""

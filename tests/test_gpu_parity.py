@@ -288,3 +288,47 @@ def test_full_size_checkerboard_513():
     u, info = S32.solve(t64(p.f), tol=1e-8, max_iter=400)
     assert info.status == 0
     assert O.relres(Ho, p.f, u.cpu().numpy())[0] < 1e-8
+
+
+# --------------------------------------------------------- launch options --
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("conv", [False, True])
+def test_launch_options_are_bitwise_neutral(prec, conv):
+    """The single-block small-level kernel and programmatic dependent launch
+    change launch shapes only: the cycle and the solve are bitwise identical."""
+    p, Ho, Hp = problem("checker65")
+    prm = rand_params(Hp.J, 37, 0.1, conv=conv)
+    dt = torch.float64 if prec == 64 else torch.float32
+    outs = []
+    for tail, pdl in [(8192, 1), (0, 1), (8192, 0), (1 << 30, 1)]:
+        S = Solver(Hp, prm, precision=prec, max_batch=2)
+        S.set_option("tail_work", tail)
+        S.set_option("pdl", pdl)
+        u = torch.zeros((Hp.sizes[0], 2), dtype=dt, device=DEV)
+        f = torch.tensor(p.f, dtype=dt, device=DEV)
+        S.vcycle(f, u)
+        S.vcycle(f, u)
+        us, info = S.solve(t64(p.f), tol=1e-9, max_iter=300)
+        outs.append((u.clone(), us.clone(), info.iters.copy()))
+        S.close()
+    for u, us, it in outs[1:]:
+        assert torch.equal(u, outs[0][0])
+        assert torch.equal(us, outs[0][1])
+        assert np.array_equal(it, outs[0][2])
+
+
+def test_whole_cycle_in_one_block_matches_oracle():
+    """Tiny hierarchy: with the tail threshold above level 0 the entire cycle
+    runs in one thread block; FP64 parity with the oracle still holds."""
+    p, Ho, Hp = problem("poisson33")
+    prm = rand_params(Hp.J, 41, 0.2)
+    S = Solver(Hp, prm, precision=64, max_batch=3)
+    S.set_option("tail_work", 1 << 30)
+    f = t64(p.f)
+    u = torch.zeros_like(f)
+    uo = np.zeros_like(p.f)
+    for m in range(4):
+        S.vcycle(f, u)
+        uo = O.vcycle(Ho, to_oracle(prm), p.f, uo)
+        assert rel(u.cpu().numpy(), uo) < 1e-12
