@@ -110,22 +110,31 @@ def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
     """Minimum bytes one launch must move: every array touched read (or
     written) once; neighbour values of a vector counted once."""
     n = hier.sizes[lev]
-    nnz_off = hier.A[lev].data.size - n
+    A = hier.A[lev]
+    nnz_off = A.data.size - n
+    # column indices are read only by the SELL layout; DIA levels (off-
+    # diagonals on at most 8 diagonals) compute neighbour addresses
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    offs = np.unique(A.indices[A.indices != rows] - rows[A.indices != rows])
+    col_b = 0 if offs.size <= 8 else 4
     nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
     nnzP = hier.P[lev].data.size if lev < hier.J - 1 else 0
-    conv_bytes = 0
     if name == "jacobi_smooth":
-        return nnz_off * (4 + b) + 2 * n * b + 3 * B * n * b
+        return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
     if name == "residual_scaled":
-        return nnz_off * (4 + b) + 2 * n * b + 3 * B * n * b
+        return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
     if name == "sage_conv_update":
-        return nnz_off * 4 + n * b + 3 * B * n * b
+        return nnz_off * (col_b or b) + n * b + 3 * B * n * b
     if name == "residual":
-        return nnz_off * (4 + b) + n * b + 3 * B * n * b
-    if name == "restrict_conv":
-        return nnzP * (4 + b) + B * n * b + B * nc * b + conv_bytes
-    if name == "prolong_conv":
-        return nnzP * (4 + b) + B * nc * b + 2 * B * n * b
+        return nnz_off * (col_b + b) + n * b + 3 * B * n * b
+    if name == "restrict_conv_fine":   # Phi_R(r) per fine row
+        return nnz_off * (col_b or b) + n * b + 2 * B * n * b
+    if name == "restrict_conv":        # gather P^T
+        return nnzP * (4 + b) + B * n * b + B * nc * b
+    if name == "prolong_fine":         # P e_c per fine row
+        return nnzP * (4 + b) + B * nc * b + B * n * b
+    if name == "prolong_conv":         # u += Phi_P(P e_c)
+        return nnz_off * (col_b or b) + n * b + 3 * B * n * b
     if name == "coarse_cholesky":
         return 2 * n * n * 8 + 2 * B * n * b
     if name == "outer_residual_fp64":

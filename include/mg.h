@@ -144,6 +144,15 @@ void mg_csr_owned_free(mg_csr_owned* m);
 mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr* A_levels,
                    const mg_params* p, int32_t max_batch, int32_t precision, void* stream);
 
+/* Matrix layout chosen by later mg_setup calls (process-wide):
+ *   0 (default): per level, DIA (values on at most 8 diagonals, neighbour
+ *      addresses computed, no column indices) when all off-diagonals lie on
+ *      at most 8 diagonals and the CSR rows are sorted, else SELL-32;
+ *   1: SELL-32 on every level.
+ * Both layouts visit a row's entries in ascending column order, so results
+ * do not depend on the layout. */
+mg_status mg_set_layout_policy(int32_t policy);
+
 /* Replaces Theta (same J); cheap: the device copy is updated on the next
  * call's stream.  Changing whether a w2 is zero switches kernels. */
 mg_status mg_set_params(mg_ctx* ctx, const mg_params* p);
@@ -216,7 +225,9 @@ typedef enum {
   MG_K_PROLONG = 5,         /* u += Phi_P(P e_c)                               */
   MG_K_COARSE_CHOL = 6,     /* e_J = A_J^{-1} r_J                              */
   MG_K_OUTER_RESIDUAL = 7,  /* FP64 refinement residual                        */
-  MG_K_TAIL = 8             /* all small levels of a cycle in one thread block */
+  MG_K_TAIL = 8,            /* all small levels of a cycle in one thread block */
+  MG_K_CONV_R = 9,          /* Phi_R(r) per fine row (then MG_K_RESTRICT gathers) */
+  MG_K_PE = 10              /* P e_c per fine row (then MG_K_PROLONG applies Phi_P) */
 } mg_kernel_kind;
 
 typedef struct {

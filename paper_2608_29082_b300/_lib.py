@@ -86,6 +86,7 @@ def lib() -> C.CDLL:
                                vp], C.c_int),
         "mg_kernel_name": ([C.c_int32], C.c_char_p),
         "mg_set_option": ([vp, C.c_int32, C.c_int64], C.c_int),
+        "mg_set_layout_policy": ([C.c_int32], C.c_int),
         "mg_forward_record": ([vp, vp, vp, C.c_int32, C.c_int32, vp], C.c_int),
         "mg_vcycle_backward": ([vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),
         "mg_residual_loss": ([vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),

@@ -38,7 +38,9 @@ def up_to_date() -> bool:
 def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
     if not force and up_to_date():
         return LIB
-    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC,-O2",
+    # -fmad=false: the kernels fuse multiply-adds only where they call fma()
+    # explicitly, so every launch form of a step rounds identically
+    cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
            "-shared", "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp", *sources(), "-lcudart"]
     if ptxas_v:
         cmd.insert(1, "-Xptxas=-v")

@@ -74,13 +74,11 @@ __global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restric
 // sum_{j in N(i)} invdeg_j x_j   (row i of M^T x, without the outer factor)
 template <class T>
 __device__ __forceinline__ T row_mt(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
-  const int beg = slice_begin(L.sl_ptr, i);
-  const int end = L.sl_ptr[(i >> 5) + 1];
   T s = T(0);
-  for (int e = beg; e < end; e += kSlice) {
-    const int c = L.col[e];
-    if (c >= 0) s = fma(L.invdeg[c], x[(size_t)c * B + b], s);
-  }
+  for_nb(L, i, [&](int c, T, bool nb) {
+    const T w = nb ? L.invdeg[c] : T(0);
+    s = fma(w, x[(size_t)c * B + b], s);
+  });
   return s;
 }
 
@@ -88,13 +86,11 @@ __device__ __forceinline__ T row_mt(const LV<T>& L, int i, const T* __restrict__
 template <class T>
 __device__ __forceinline__ T row_sum_dinv(const LV<T>& L, int i, const T* __restrict__ x, int B,
                                           int b) {
-  const int beg = slice_begin(L.sl_ptr, i);
-  const int end = L.sl_ptr[(i >> 5) + 1];
   T s = T(0);
-  for (int e = beg; e < end; e += kSlice) {
-    const int c = L.col[e];
-    if (c >= 0) s = fma(L.dinv[c], x[(size_t)c * B + b], s);
-  }
+  for_nb(L, i, [&](int c, T, bool nb) {
+    const T w = nb ? L.dinv[c] : T(0);
+    s = fma(w, x[(size_t)c * B + b], s);
+  });
   return s;
 }
 
@@ -109,7 +105,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth(LV<T> L, const T* __res
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[4] = {0.0, 0.0, 0.0, 0.0};
   if (t < (size_t)L.n * B) {
-    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    int i, b;
+    split_rb(t, B, i, b);
     const T theta = prm[P_THETA], eta = prm[P_ETA], w1 = prm[P_WB1], w2 = prm[P_WB2];
     const T ub = ubar[t];
     const T phib = eta * ub;
@@ -155,19 +152,17 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0.0, 0.0};
   if (t < (size_t)L.n * B) {
-    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    int i, b;
+    split_rb(t, B, i, b);
     const T w1 = prm[P_WR1], w2 = prm[P_WR2];
     const T phib = prolong_at(L, i, rcbar, B, b);
-    const int beg = slice_begin(L.sl_ptr, i);
-    const int end = L.sl_ptr[(i >> 5) + 1];
     T mt = T(0), sr = T(0);
-    for (int e = beg; e < end; e += kSlice) {
-      const int c = L.col[e];
-      if (c >= 0) {
-        mt = fma(L.invdeg[c], prolong_at(L, c, rcbar, B, b), mt);
-        sr += r[(size_t)c * B + b];
-      }
-    }
+    for_nb(L, i, [&](int c, T, bool nb) {
+      const T w = nb ? L.invdeg[c] : T(0);
+      mt = fma(w, prolong_at(L, c, rcbar, B, b), mt);
+      const T rv = r[(size_t)c * B + b];
+      sr += nb ? rv : T(0);
+    });
     rbar[t] = fma(w1, phib, w2 * mt);
     v[0] = (double)phib * r[t];
     v[1] = (double)phib * (L.invdeg[i] * sr);
@@ -203,15 +198,14 @@ __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T*
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0.0, 0.0};
   if (t < (size_t)L.n * B) {
-    const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+    int i, b;
+    split_rb(t, B, i, b);
     const T pe = prolong_at(L, i, ec, B, b);
-    const int beg = slice_begin(L.sl_ptr, i);
-    const int end = L.sl_ptr[(i >> 5) + 1];
     T s = T(0);
-    for (int e = beg; e < end; e += kSlice) {
-      const int c = L.col[e];
-      if (c >= 0) s += prolong_at(L, c, ec, B, b);
-    }
+    for_nb(L, i, [&](int c, T, bool nb) {
+      const T pv = prolong_at(L, c, ec, B, b);
+      s += nb ? pv : T(0);
+    });
     const double ub = (double)ubar[t];
     v[0] = ub * pe;
     v[1] = ub * (L.invdeg[i] * s);

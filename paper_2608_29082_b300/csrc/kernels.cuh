@@ -39,9 +39,21 @@ constexpr int kTailThreads = 1024;
 // theta, eta, wB1, wB2, wR1, wR2, wP1, wP2.
 enum { P_THETA = 0, P_ETA, P_WB1, P_WB2, P_WR1, P_WR2, P_WP1, P_WP2, P_COUNT };
 
+constexpr int kMaxDia = 8;
+constexpr int kMaxKR = 8;  // restriction children handled with a fixed trip count
+
+// Level view.  Off-diagonals are stored either as SELL-32 (sl_ptr, col, val)
+// or, when every off-diagonal of the level lies on at most kMaxDia diagonals
+// (structured meshes), as DIA: ndia > 0, offsets doff[k] in ascending order
+// and values dval[k][n] (zero where row i has no entry on diagonal k).  The
+// graph neighbours of i are exactly its nonzero off-diagonals in either form,
+// visited in ascending column order, so both forms give the same arithmetic.
 template <class T>
 struct LV {
   int n, nc, KR;
+  int ndia;
+  int doff[kMaxDia];
+  const T* __restrict__ dval;
   const int* __restrict__ sl_ptr;
   const int* __restrict__ col;
   const T* __restrict__ val;
@@ -57,31 +69,63 @@ struct LV {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
 
+// (row, rhs) of a flat index t into X[n][B]; n * B < 2^31 is checked at set-up.
+__device__ __forceinline__ void split_rb(size_t t, int B, int& i, int& b) {
+  if (B == 1) {
+    i = (int)t;
+    b = 0;
+  } else {
+    const unsigned tt = (unsigned)t;
+    i = (int)(tt / (unsigned)B);
+    b = (int)(tt - (unsigned)i * (unsigned)B);
+  }
+}
+
 __device__ __forceinline__ int slice_begin(const int* sl_ptr, int i) {
   return sl_ptr[i >> 5] + (i & 31);
 }
 
+// Calls fn(c, a_ic, is_neighbour) for the off-diagonals of row i in ascending
+// column order.  DIA: every diagonal is visited; absent entries have a_ic = 0,
+// is_neighbour = false and a clamped in-range c, so the value and the
+// neighbour loads of a row are independent of each other.
+template <class T, class F>
+__device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
+  if (L.ndia > 0) {
+#pragma unroll
+    for (int k = 0; k < kMaxDia; ++k) {
+      if (k < L.ndia) {
+        const T v = L.dval[(size_t)k * L.n + i];
+        const int c = min(max(i + L.doff[k], 0), L.n - 1);
+        fn(c, v, v != T(0));
+      }
+    }
+  } else {
+    const int beg = slice_begin(L.sl_ptr, i);
+    const int end = L.sl_ptr[(i >> 5) + 1];
+    for (int e = beg; e < end; e += kSlice) {
+      const int c = L.col[e];
+      if (c >= 0) fn(c, L.val[e], true);
+    }
+  }
+}
+
+// sum_{j != i} a_ij x_j
 template <class T>
 __device__ __forceinline__ T row_ax(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
-  const int beg = slice_begin(L.sl_ptr, i);
-  const int end = L.sl_ptr[(i >> 5) + 1];
   T a_acc = T(0);
-  for (int e = beg; e < end; e += kSlice) {
-    const int c = L.col[e];
-    if (c >= 0) a_acc = fma(L.val[e], x[(size_t)c * B + b], a_acc);
-  }
+  for_nb(L, i, [&](int c, T v, bool) { a_acc = fma(v, x[(size_t)c * B + b], a_acc); });
   return a_acc;
 }
 
+// sum_{j in N(i)} x_j
 template <class T>
 __device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
-  const int beg = slice_begin(L.sl_ptr, i);
-  const int end = L.sl_ptr[(i >> 5) + 1];
   T s_acc = T(0);
-  for (int e = beg; e < end; e += kSlice) {
-    const int c = L.col[e];
-    if (c >= 0) s_acc += x[(size_t)c * B + b];
-  }
+  for_nb(L, i, [&](int c, T, bool nb) {
+    const T xv = x[(size_t)c * B + b];
+    s_acc += nb ? xv : T(0);
+  });
   return s_acc;
 }
 
@@ -104,7 +148,8 @@ __device__ __forceinline__ void residual_el(const LV<T>& L, const T* __restrict_
                                             const T* __restrict__ u, T* __restrict__ out, int B,
                                             const T* __restrict__ prm, int scale, int u_zero,
                                             size_t t) {
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  int i, b;
+  split_rb(t, B, i, b);
   T r = f[t];
   if (!u_zero) {
     const T ax = row_ax(L, i, u, B, b);
@@ -119,7 +164,8 @@ template <class T>
 __device__ __forceinline__ void conv_update_el(const LV<T>& L, const T* __restrict__ x,
                                                T* __restrict__ u, int B, const T* __restrict__ prm,
                                                int u_zero, size_t t) {
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  int i, b;
+  split_rb(t, B, i, b);
   const T s = row_sum(L, i, x, B, b);
   const T phi = fma(prm[P_WB1], x[t], prm[P_WB2] * (L.invdeg[i] * s));
   const T u0 = u_zero ? T(0) : u[t];
@@ -133,7 +179,8 @@ template <class T>
 __device__ __forceinline__ void jacobi_el(const LV<T>& L, const T* __restrict__ f,
                                           const T* __restrict__ uin, T* __restrict__ uout, int B,
                                           const T* __restrict__ prm, int u_zero, size_t t) {
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  int i, b;
+  split_rb(t, B, i, b);
   T r = f[t];
   T u0 = T(0);
   if (!u_zero) {
@@ -150,15 +197,36 @@ template <class T>
 __device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict__ r,
                                             T* __restrict__ fc, int B, const T* __restrict__ prm,
                                             int conv, size_t t) {
-  const int I = (int)(t / B), b = (int)(t - (size_t)I * B);
+  int I, b;
+  split_rb(t, B, I, b);
   const T w1 = prm[P_WR1], w2 = prm[P_WR2];
   T acc = T(0);
-  for (int k = 0; k < L.KR; ++k) {
-    const int i = L.r_idx[(size_t)k * L.nc + I];
-    if (i < 0) break;
-    T phi = w1 * r[(size_t)i * B + b];
-    if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
-    acc = fma(L.r_w[(size_t)k * L.nc + I], phi, acc);
+  if (L.KR <= kMaxKR) {
+    // fixed trip count, no early exit: every child's loads issue together
+    int idx[kMaxKR];
+    T wk[kMaxKR];
+#pragma unroll
+    for (int k = 0; k < kMaxKR; ++k) {
+      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.nc + I] : -1;
+      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.nc + I] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxKR; ++k) {
+      if (idx[k] >= 0) {
+        const int i = idx[k];
+        T phi = w1 * r[(size_t)i * B + b];
+        if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
+        acc = fma(wk[k], phi, acc);
+      }
+    }
+  } else {
+    for (int k = 0; k < L.KR; ++k) {
+      const int i = L.r_idx[(size_t)k * L.nc + I];
+      if (i < 0) break;
+      T phi = w1 * r[(size_t)i * B + b];
+      if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
+      acc = fma(L.r_w[(size_t)k * L.nc + I], phi, acc);
+    }
   }
   fc[t] = acc;
 }
@@ -168,18 +236,83 @@ template <class T>
 __device__ __forceinline__ void prolong_el(const LV<T>& L, const T* __restrict__ ec, const T* uin,
                                            T* u, int B, const T* __restrict__ prm, int conv,
                                            size_t t) {
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  int i, b;
+  split_rb(t, B, i, b);
   T phi = prm[P_WP1] * prolong_at(L, i, ec, B, b);
   if (conv) {
-    const int beg = slice_begin(L.sl_ptr, i);
-    const int end = L.sl_ptr[(i >> 5) + 1];
     T s = T(0);
-    for (int e = beg; e < end; e += kSlice) {
-      const int c = L.col[e];
-      if (c >= 0) s += prolong_at(L, c, ec, B, b);
-    }
+    for_nb(L, i, [&](int c, T, bool nb) {
+      const T pv = prolong_at(L, c, ec, B, b);
+      s += nb ? pv : T(0);
+    });
     phi = fma(prm[P_WP2], L.invdeg[i] * s, phi);
   }
+  u[t] = uin[t] + phi;
+}
+
+// Split forms of the convolution transfers: the fused steps above evaluate
+// the convolution of every child (restriction) or neighbour (prolongation)
+// inside one thread; these evaluate it once per fine row in its own pass.
+// Values and summation order are those of restrict_el / prolong_el.
+
+// phi_i = wR1 r_i + wR2 mean_{N(i)} r   (fine rows)
+template <class T>
+__device__ __forceinline__ void conv_r_el(const LV<T>& L, const T* __restrict__ r,
+                                          T* __restrict__ phi, int B, const T* __restrict__ prm,
+                                          size_t t) {
+  int i, b;
+  split_rb(t, B, i, b);
+  T p = prm[P_WR1] * r[t];
+  p = fma(prm[P_WR2], L.invdeg[i] * row_sum(L, i, r, B, b), p);
+  phi[t] = p;
+}
+
+// fc_I = sum_{i in children(I)} P_iI phi_i   (coarse rows)
+template <class T>
+__device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ phi,
+                                          T* __restrict__ fc, int B, size_t t) {
+  int I, b;
+  split_rb(t, B, I, b);
+  T acc = T(0);
+  if (L.KR <= kMaxKR) {
+    int idx[kMaxKR];
+    T wk[kMaxKR];
+#pragma unroll
+    for (int k = 0; k < kMaxKR; ++k) {
+      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.nc + I] : -1;
+      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.nc + I] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxKR; ++k)
+      if (idx[k] >= 0) acc = fma(wk[k], phi[(size_t)idx[k] * B + b], acc);
+  } else {
+    for (int k = 0; k < L.KR; ++k) {
+      const int i = L.r_idx[(size_t)k * L.nc + I];
+      if (i < 0) break;
+      acc = fma(L.r_w[(size_t)k * L.nc + I], phi[(size_t)i * B + b], acc);
+    }
+  }
+  fc[t] = acc;
+}
+
+// pe_i = (P ec)_i   (fine rows)
+template <class T>
+__device__ __forceinline__ void pe_el(const LV<T>& L, const T* __restrict__ ec,
+                                      T* __restrict__ pe, int B, size_t t) {
+  int i, b;
+  split_rb(t, B, i, b);
+  pe[t] = prolong_at(L, i, ec, B, b);
+}
+
+// u_i = uin_i + wP1 pe_i + wP2 mean_{N(i)} pe   (uin may equal u)
+template <class T>
+__device__ __forceinline__ void prolong_conv_el(const LV<T>& L, const T* __restrict__ pe,
+                                                const T* uin, T* u, int B,
+                                                const T* __restrict__ prm, size_t t) {
+  int i, b;
+  split_rb(t, B, i, b);
+  T phi = prm[P_WP1] * pe[t];
+  phi = fma(prm[P_WP2], L.invdeg[i] * row_sum(L, i, pe, B, b), phi);
   u[t] = uin[t] + phi;
 }
 
@@ -273,6 +406,40 @@ __global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restri
 }
 
 template <class T>
+__global__ void __launch_bounds__(kThreads) k_conv_r(LV<T> L, const T* __restrict__ r,
+                                                     T* __restrict__ phi, int B,
+                                                     const T* __restrict__ prm) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) conv_r_el(L, r, phi, B, prm, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gather(LV<T> L, const T* __restrict__ phi,
+                                                     T* __restrict__ fc, int B) {
+  MG_GRID_PROLOGUE((size_t)L.nc * B)
+  if (in_range) gather_el(L, phi, fc, B, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_pe(LV<T> L, const T* __restrict__ ec,
+                                                 T* __restrict__ pe, int B) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) pe_el(L, ec, pe, B, t);
+  pdl_launch();
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_prolong_conv(LV<T> L, const T* __restrict__ pe,
+                                                           const T* uin, T* u, int B,
+                                                           const T* __restrict__ prm) {
+  MG_GRID_PROLOGUE((size_t)L.n * B)
+  if (in_range) prolong_conv_el(L, pe, uin, u, B, prm, t);
+  pdl_launch();
+}
+
+template <class T>
 __global__ void __launch_bounds__(kThreads) k_copy(const T* __restrict__ x, T* __restrict__ y,
                                                    size_t n) {
   MG_GRID_PROLOGUE(n)
@@ -298,8 +465,10 @@ __global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __res
 // smoothing).  Level lt's right-hand side is f[lt]; its result is u[lt].
 template <class T>
 struct TailArgs {
-  int lt, J, B, nu_pre, nu_post, nJ, cwarps, lt_zero, smem_vectors;
+  int lt, J, B, nu_pre, nu_post, nJ, cwarps, lt_zero, smem_vectors, smem_matrix;
   unsigned convB, convR, convP;  // bit l: w2 != 0 on level l
+  int nsl[kMaxLevels];           // SELL slices per level (0 for DIA levels)
+  int nent[kMaxLevels];          // SELL entries per level
   LV<T> L[kMaxLevels];
   const T* f[kMaxLevels];
   T* u[kMaxLevels];
@@ -323,21 +492,77 @@ struct TailVecs {
 
 __host__ __device__ inline size_t tail_align(size_t x) { return (x + 15) & ~size_t(15); }
 
-// Dynamic shared memory of k_tail: Cholesky scratch, then u, f, t, u2 of
-// every level lt..J-1 when the vectors live in shared memory.
+// Shared-memory bytes of one small level: its four vectors (vec) and its
+// read-only arrays (mat): DIA values or SELL slices, diag, dinv, invdeg and,
+// above the coarsest level, the prolongation and restriction lists.
 template <class T>
-__host__ __device__ inline size_t tail_smem_bytes(const int* n, int lt, int J, int B, int nJ,
-                                                  int cwarps, bool vectors) {
-  size_t off = tail_align((size_t)cwarps * nJ * sizeof(double));
-  if (vectors)
-    for (int l = lt; l < J; ++l) off += 4 * tail_align((size_t)n[l] * B * sizeof(T));
+__host__ __device__ inline size_t tail_level_bytes(int n, int nc, int KR, int ndia, int nsl,
+                                                   int nent, int B, bool last, bool vec,
+                                                   bool mat) {
+  size_t s = 0;
+  if (vec) s += 4 * tail_align((size_t)n * B * sizeof(T));
+  if (mat) {
+    if (ndia > 0) {
+      s += tail_align((size_t)ndia * n * sizeof(T));
+    } else {
+      s += tail_align((size_t)(nsl + 1) * sizeof(int)) + tail_align((size_t)nent * sizeof(int)) +
+           tail_align((size_t)nent * sizeof(T));
+    }
+    s += 3 * tail_align((size_t)n * sizeof(T));
+    if (!last) {
+      s += tail_align((size_t)2 * n * sizeof(int)) + tail_align((size_t)2 * n * sizeof(T));
+      s += tail_align((size_t)KR * nc * sizeof(int)) + tail_align((size_t)KR * nc * sizeof(T));
+    }
+  }
+  return s;
+}
+
+// Dynamic shared memory of k_tail: Cholesky scratch, then every level
+// lt..J-1 as laid out by tail_level_bytes.
+template <class T>
+__host__ __device__ inline size_t tail_smem_bytes(const TailArgs<T>& a, int lt) {
+  size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+  for (int l = lt; l < a.J; ++l)
+    off += tail_level_bytes<T>(a.L[l].n, a.L[l].nc, a.L[l].KR, a.L[l].ndia, a.nsl[l], a.nent[l],
+                               a.B, l == a.J - 1, a.smem_vectors != 0, a.smem_matrix != 0);
   return off;
 }
 
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+// Starts copying count elements into shared memory at base + off (all
+// threads of the block take part; 16-byte cp.async transfers stay in flight
+// until cp_async_wait_all) and advances off; returns the shared-memory copy.
+// Bytes past the last whole 16-byte chunk are copied with plain loads, so
+// nothing beyond src + count is read.
+template <class U>
+__device__ __forceinline__ U* smem_take(unsigned char* base, size_t& off, const U* src,
+                                        size_t count) {
+  U* dst = (U*)(base + off);
+  off += tail_align(count * sizeof(U));
+  const size_t bytes = count * sizeof(U);
+  const char* s = (const char*)src;
+  char* d = (char*)dst;
+  if ((((uintptr_t)s) & 15) == 0) {
+    const size_t nchunk = bytes / 16;
+    for (size_t k = threadIdx.x; k < nchunk; k += blockDim.x) cp_async16(d + 16 * k, s + 16 * k);
+    for (size_t k = nchunk * 16 + threadIdx.x; k < bytes; k += blockDim.x) d[k] = s[k];
+  } else {
+    for (size_t k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
+  }
+  return dst;
+}
+
 template <class T>
-__device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const TailVecs<T>& v, int l,
-                                            int nu, bool zero) {
-  const LV<T>& L = a.L[l];
+__device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* Ls,
+                                            const TailVecs<T>& v, int l, int nu, bool zero) {
+  const LV<T>& L = Ls[l];
   const size_t N = (size_t)L.n * a.B;
   const T* prm = a.prm + (size_t)l * P_COUNT;
   if ((a.convB >> l) & 1u) {
@@ -376,60 +601,103 @@ __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const TailVecs
 template <class T>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs<T> a) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
+  __shared__ LV<T> sL[kMaxLevels];
   double* ys = (double*)tail_smem;
   pdl_wait();
   pdl_launch();
   const int J = a.J, lt = a.lt;
   TailVecs<T> v;
-  if (a.smem_vectors) {
-    size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
-    for (int l = lt; l < J; ++l) {
-      const size_t bytes = tail_align((size_t)a.L[l].n * a.B * sizeof(T));
+  // Lay out every small level in shared memory (the same order as
+  // tail_level_bytes): vectors first, then the read-only arrays, copied
+  // once per cycle with all threads.
+  size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+  for (int l = lt; l < J; ++l) {
+    const LV<T>& G = a.L[l];
+    const size_t nB = (size_t)G.n * a.B;
+    if (a.smem_vectors) {
+      const size_t bytes = tail_align(nB * sizeof(T));
       v.u[l] = (T*)(tail_smem + off);
       v.f[l] = (T*)(tail_smem + off + bytes);
       v.t[l] = (T*)(tail_smem + off + 2 * bytes);
       v.u2[l] = (T*)(tail_smem + off + 3 * bytes);
+      if (l == lt) {
+        size_t o2 = off + bytes;
+        smem_take(tail_smem, o2, a.f[lt], nB);
+        if (!a.lt_zero) {
+          o2 = off;
+          smem_take(tail_smem, o2, (const T*)a.u[lt], nB);
+        }
+      }
       off += 4 * bytes;
-    }
-    const size_t N = (size_t)a.L[lt].n * a.B;
-    for (size_t t = threadIdx.x; t < N; t += blockDim.x) {
-      v.f[lt][t] = a.f[lt][t];
-      if (!a.lt_zero) v.u[lt][t] = a.u[lt][t];
-    }
-    __syncthreads();
-  } else {
-    for (int l = lt; l < J; ++l) {
+    } else {
       v.u[l] = a.u[l];
       v.f[l] = (T*)a.f[l];
       v.t[l] = a.t[l];
       v.u2[l] = a.u2[l];
     }
+    LV<T> S = G;
+    if (a.smem_matrix) {
+      if (G.ndia > 0) {
+        S.dval = smem_take(tail_smem, off, G.dval, (size_t)G.ndia * G.n);
+      } else {
+        S.sl_ptr = smem_take(tail_smem, off, G.sl_ptr, (size_t)a.nsl[l] + 1);
+        S.col = smem_take(tail_smem, off, G.col, (size_t)a.nent[l]);
+        S.val = smem_take(tail_smem, off, G.val, (size_t)a.nent[l]);
+      }
+      S.diag = smem_take(tail_smem, off, G.diag, (size_t)G.n);
+      S.dinv = smem_take(tail_smem, off, G.dinv, (size_t)G.n);
+      S.invdeg = smem_take(tail_smem, off, G.invdeg, (size_t)G.n);
+      if (l < J - 1) {
+        S.p_idx = smem_take(tail_smem, off, G.p_idx, (size_t)2 * G.n);
+        S.p_w = smem_take(tail_smem, off, G.p_w, (size_t)2 * G.n);
+        S.r_idx = smem_take(tail_smem, off, G.r_idx, (size_t)G.KR * G.nc);
+        S.r_w = smem_take(tail_smem, off, G.r_w, (size_t)G.KR * G.nc);
+      }
+    }
+    if (threadIdx.x == 0) sL[l] = S;
   }
+  cp_async_wait_all();
+  __syncthreads();
   for (int l = lt; l < J - 1; ++l) {
-    const LV<T>& L = a.L[l];
+    const LV<T>& L = sL[l];
     const T* prm = a.prm + (size_t)l * P_COUNT;
-    tail_smooth(a, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true);
+    tail_smooth(a, sL, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true);
     const size_t N = (size_t)L.n * a.B;
     for (size_t t = threadIdx.x; t < N; t += blockDim.x)
       residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 0, 0, t);
     __syncthreads();
     const size_t Nc = (size_t)L.nc * a.B;
-    for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
-      restrict_el(L, (const T*)v.t[l], v.f[l + 1], a.B, prm, (int)((a.convR >> l) & 1u), t);
+    if ((a.convR >> l) & 1u) {  // Phi_R per fine row, then the gather P^T
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        conv_r_el(L, (const T*)v.t[l], v.u2[l], a.B, prm, t);
+      __syncthreads();
+      for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
+        gather_el(L, (const T*)v.u2[l], v.f[l + 1], a.B, t);
+    } else {
+      for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
+        restrict_el(L, (const T*)v.t[l], v.f[l + 1], a.B, prm, 0, t);
+    }
     __syncthreads();
   }
   coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, a.cwarps,
                     ys);
   __syncthreads();
   for (int l = J - 2; l >= lt; --l) {
-    const LV<T>& L = a.L[l];
+    const LV<T>& L = sL[l];
     const T* prm = a.prm + (size_t)l * P_COUNT;
     const size_t N = (size_t)L.n * a.B;
-    for (size_t t = threadIdx.x; t < N; t += blockDim.x)
-      prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], a.B, prm,
-                 (int)((a.convP >> l) & 1u), t);
+    if ((a.convP >> l) & 1u) {  // P e_c per fine row, then Phi_P and the update
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        pe_el(L, (const T*)v.u[l + 1], v.t[l], a.B, t);
+      __syncthreads();
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        prolong_conv_el(L, (const T*)v.t[l], (const T*)v.u[l], v.u[l], a.B, prm, t);
+    } else {
+      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+        prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], a.B, prm, 0, t);
+    }
     __syncthreads();
-    tail_smooth(a, v, l, a.nu_post, false);
+    tail_smooth(a, sL, v, l, a.nu_post, false);
   }
   if (a.smem_vectors) {
     const size_t N = (size_t)a.L[lt].n * a.B;

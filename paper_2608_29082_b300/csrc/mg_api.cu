@@ -47,24 +47,33 @@ const std::string& global_error() { return g_err; }
 namespace {
 
 struct HostLevel {
-  int n = 0, nc = 0, KR = 0;
+  int n = 0, nc = 0, KR = 0, ndia = 0;
+  int doff[mgk::kMaxDia] = {0};
   std::vector<int> sl_ptr, col, p_idx, r_idx;
-  std::vector<double> val, diag, dinv, invdeg, p_w, r_w;
+  std::vector<double> val, diag, dinv, invdeg, p_w, r_w, dval;
 };
+
+// 0: DIA where a level's off-diagonals lie on at most kMaxDia diagonals,
+// SELL-32 elsewhere; 1: SELL-32 everywhere (mg_set_layout_policy).
+int g_layout_policy = 0;
 
 template <class T>
 struct DevLevel {
-  int n = 0, nc = 0, KR = 0, nsl = 0;
+  int n = 0, nc = 0, KR = 0, nsl = 0, ndia = 0;
+  int doff[mgk::kMaxDia] = {0};
   size_t nent = 0;
   int *sl_ptr = nullptr, *col = nullptr, *p_idx = nullptr, *r_idx = nullptr;
   T *val = nullptr, *diag = nullptr, *dinv = nullptr, *invdeg = nullptr, *p_w = nullptr,
-    *r_w = nullptr;
+    *r_w = nullptr, *dval = nullptr;
   T *u = nullptr, *f = nullptr, *t = nullptr, *u2 = nullptr;  // workspace [n][maxB]
   LV<T> view() const {
     LV<T> v;
     v.n = n;
     v.nc = nc;
     v.KR = KR;
+    v.ndia = ndia;
+    for (int k = 0; k < mgk::kMaxDia; ++k) v.doff[k] = doff[k];
+    v.dval = dval;
     v.sl_ptr = sl_ptr;
     v.col = col;
     v.val = val;
@@ -82,7 +91,7 @@ struct DevLevel {
 template <class T>
 void free_level(DevLevel<T>& L) {
   void* ptrs[] = {L.sl_ptr, L.col, L.p_idx, L.r_idx, L.val, L.diag, L.dinv, L.invdeg,
-                  L.p_w,    L.r_w, L.u,     L.f,     L.t,   L.u2};
+                  L.p_w,    L.r_w, L.u,     L.f,     L.t,   L.u2,  L.dval};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = DevLevel<T>();
@@ -125,7 +134,35 @@ std::string pack_level(const mg_csr& A, const double* invdeg, const mg_csr* P, H
     if (!(invdeg[i] > 0.0) || !std::isfinite(invdeg[i])) return "inv_deg must be positive";
     H.dinv[i] = 1.0 / H.diag[i];
   }
-  const int nsl = (n + mgk::kSlice - 1) / mgk::kSlice;
+  // DIA when the off-diagonals lie on few diagonals (ascending offsets keep
+  // the column order of the CSR rows, hence the same accumulation order)
+  std::vector<int> offs;
+  bool dia = g_layout_policy == 0;
+  for (int i = 0; i < n && dia; ++i)
+    for (int k = A.rowptr[i]; k < A.rowptr[i + 1] && dia; ++k) {
+      if (k > A.rowptr[i] && A.col[k] <= A.col[k - 1]) dia = false;  // unsorted or duplicate
+      if (!dia || A.col[k] == i || A.val[k] == 0.0) continue;
+      const int o = A.col[k] - i;
+      if (std::find(offs.begin(), offs.end(), o) == offs.end()) {
+        if ((int)offs.size() == mgk::kMaxDia)
+          dia = false;
+        else
+          offs.push_back(o);
+      }
+    }
+  if (dia && !offs.empty()) {
+    std::sort(offs.begin(), offs.end());
+    H.ndia = (int)offs.size();
+    for (int k = 0; k < H.ndia; ++k) H.doff[k] = offs[k];
+    H.dval.assign((size_t)H.ndia * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) {
+        if (A.col[k] == i || A.val[k] == 0.0) continue;
+        const int d = (int)(std::find(offs.begin(), offs.end(), A.col[k] - i) - offs.begin());
+        H.dval[(size_t)d * n + i] = A.val[k];
+      }
+  }
+  const int nsl = H.ndia > 0 ? 0 : (n + mgk::kSlice - 1) / mgk::kSlice;
   H.sl_ptr.assign(nsl + 1, 0);
   for (int s = 0; s < nsl; ++s) {
     int K = 0;
@@ -134,7 +171,7 @@ std::string pack_level(const mg_csr& A, const double* invdeg, const mg_csr* P, H
   }
   H.col.assign(H.sl_ptr[nsl], -1);
   H.val.assign(H.sl_ptr[nsl], 0.0);
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n && H.ndia == 0; ++i) {
     int k = 0;
     const int base = H.sl_ptr[i / 32] + (i % 32);
     for (int e = A.rowptr[i]; e < A.rowptr[i + 1]; ++e) {
@@ -291,6 +328,9 @@ cudaError_t upload_level(const HostLevel& H, DevLevel<T>& D, int maxB, bool vect
   D.KR = H.KR;
   D.nsl = (int)H.sl_ptr.size() - 1;
   D.nent = H.col.size();
+  D.ndia = H.ndia;
+  for (int k = 0; k < mgk::kMaxDia; ++k) D.doff[k] = H.doff[k];
+  if ((e = upload(&D.dval, cast<T>(H.dval))) != cudaSuccess) return e;
   if ((e = upload(&D.sl_ptr, H.sl_ptr)) != cudaSuccess) return e;
   if ((e = upload(&D.col, H.col)) != cudaSuccess) return e;
   if ((e = upload(&D.val, cast<T>(H.val))) != cudaSuccess) return e;
@@ -442,18 +482,39 @@ struct Issue {
     launch(mgk::k_residual<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), (const T*)f,
            (const T*)u, D.t, B, P(lev), 0, 0);
     post();
-    pre(MG_K_RESTRICT, lev);
-    launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
-           (const T*)D.t, Fl(lev + 1), B, P(lev), (int)conv(lev, mgk::P_WR2));
-    post();
+    if (conv(lev, mgk::P_WR2)) {  // Phi_R per fine row, then the gather P^T
+      pre(MG_K_CONV_R, lev);
+      launch(mgk::k_conv_r<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), (const T*)D.t,
+             D.u2, B, P(lev));
+      post();
+      pre(MG_K_RESTRICT, lev);
+      launch(mgk::k_gather<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
+             (const T*)D.u2, Fl(lev + 1), B);
+      post();
+    } else {
+      pre(MG_K_RESTRICT, lev);
+      launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
+             (const T*)D.t, Fl(lev + 1), B, P(lev), 0);
+      post();
+    }
   }
 
   void prolong(int lev, const T* ec, T* u) {
     DevLevel<T>& D = L[lev];
-    pre(MG_K_PROLONG, lev);
-    launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec,
-           (const T*)u, u, B, P(lev), (int)conv(lev, mgk::P_WP2));
-    post();
+    if (conv(lev, mgk::P_WP2)) {  // P e_c per fine row, then Phi_P and the update
+      pre(MG_K_PE, lev);
+      launch(mgk::k_pe<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec, D.t, B);
+      post();
+      pre(MG_K_PROLONG, lev);
+      launch(mgk::k_prolong_conv<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(),
+             (const T*)D.t, (const T*)u, u, B, P(lev));
+      post();
+    } else {
+      pre(MG_K_PROLONG, lev);
+      launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec,
+             (const T*)u, u, B, P(lev), 0);
+      post();
+    }
   }
 
   int coarse_warps(int cap) const {
@@ -471,31 +532,20 @@ struct Issue {
 
   // First level handled by the single-block tail for this batch size (J-1:
   // no tail, only the coarse solve).
-  int tail_level() const {
-    if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels) return c->J - 1;
-    int lt = c->J - 1;
-    while (lt > 0 && (int64_t)c->n[lt - 1] * B <= c->opt_tail_work) --lt;
-    // the small levels' vectors must fit in shared memory
-    while (lt < c->J - 1 &&
-           mgk::tail_smem_bytes<T>(c->n.data(), lt, c->J, B, c->nJ, coarse_warps(32), true) >
-               kTailSmemMax)
-      ++lt;
-    return lt;
-  }
-
-  void tail(int lt, const T* f0, T* u0, bool u0_zero) {
-    mgk::TailArgs<T> a;
+  // Small-level arguments for every level (lt chosen by the caller).
+  void tail_args(mgk::TailArgs<T>& a, const T* f0, T* u0, bool u0_zero) const {
     std::memset(&a, 0, sizeof(a));
-    a.lt = lt;
     a.J = c->J;
     a.B = B;
     a.nu_pre = c->nu_pre;
     a.nu_post = c->nu_post;
     a.nJ = c->nJ;
     a.cwarps = coarse_warps(32);
-    a.lt_zero = lt == 0 ? (int)u0_zero : 1;
+    a.lt_zero = (int)u0_zero;
     for (int l = 0; l < c->J; ++l) {
       a.L[l] = L[l].view();
+      a.nsl[l] = L[l].ndia > 0 ? 0 : L[l].nsl;
+      a.nent[l] = L[l].ndia > 0 ? 0 : (int)L[l].nent;
       a.f[l] = l == 0 ? f0 : Fl(l);
       a.u[l] = l == 0 ? u0 : Ul(l);
       a.t[l] = L[l].t;
@@ -512,11 +562,31 @@ struct Issue {
     a.cDinv = c->cholDinv;
     // a recorded forward must leave every level's f and u in its checkpoint
     // buffers, so it keeps the small levels' vectors in global memory
-    const bool smv = fov == nullptr && uov == nullptr;
-    a.smem_vectors = smv ? 1 : 0;
+    a.smem_vectors = fov == nullptr && uov == nullptr ? 1 : 0;
+    a.smem_matrix = 1;
+  }
+
+  // First level run by the single-block kernel (J-1: none): levels with
+  // rows x rhs <= the threshold, reduced until their data fits in shared
+  // memory.
+  int tail_level() const {
+    if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels) return c->J - 1;
+    int lt = c->J - 1;
+    while (lt > 0 && (int64_t)c->n[lt - 1] * B <= c->opt_tail_work) --lt;
+    if (lt == c->J - 1) return lt;
+    mgk::TailArgs<T> a;
+    tail_args(a, nullptr, nullptr, false);
+    while (lt < c->J - 1 && mgk::tail_smem_bytes<T>(a, lt) > kTailSmemMax) ++lt;
+    return lt;
+  }
+
+  void tail(int lt, const T* f0, T* u0, bool u0_zero) {
+    mgk::TailArgs<T> a;
+    tail_args(a, f0, u0, u0_zero);
+    a.lt = lt;
+    if (lt > 0) a.lt_zero = 1;  // coarse levels start from zero
     pre(MG_K_TAIL, lt);
-    launch(mgk::k_tail<T>, dim3(1), dim3(mgk::kTailThreads),
-           mgk::tail_smem_bytes<T>(c->n.data(), lt, c->J, B, c->nJ, a.cwarps, smv), a);
+    launch(mgk::k_tail<T>, dim3(1), dim3(mgk::kTailThreads), mgk::tail_smem_bytes<T>(a, lt), a);
     post();
   }
 
@@ -647,6 +717,10 @@ static mg_status validate_hierarchy(const mg_hierarchy* h, const mg_csr* A, int3
   for (int l = 0; l < J; ++l) {
     const int n = A[l].n_rows;
     if (n < 1) { why = "empty level"; return MG_ERR_INVALID; }
+    if ((int64_t)n * maxB >= ((int64_t)1 << 31)) {
+      why = "rows x max_batch must stay below 2^31";
+      return MG_ERR_INVALID;
+    }
     std::string m = csr_check(A[l], n, n, "A_levels");
     if (!m.empty()) { why = m + " (level " + std::to_string(l) + ")"; return MG_ERR_INVALID; }
     if (!h->inv_deg[l]) { why = "inv_deg is NULL"; return MG_ERR_INVALID; }
@@ -1094,6 +1168,8 @@ extern "C" const char* mg_kernel_name(int32_t kind) {
     case MG_K_COARSE_CHOL: return "coarse_cholesky";
     case MG_K_OUTER_RESIDUAL: return "outer_residual_fp64";
     case MG_K_TAIL: return "small_levels_block";
+    case MG_K_CONV_R: return "restrict_conv_fine";
+    case MG_K_PE: return "prolong_fine";
     default: return "unknown";
   }
 }
@@ -1155,5 +1231,12 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   }
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
+  return MG_OK;
+}
+
+extern "C" mg_status mg_set_layout_policy(int32_t policy) {
+  if (policy != 0 && policy != 1)
+    return mgi::set_global_error(MG_ERR_INVALID, "mg_set_layout_policy: policy must be 0 or 1");
+  g_layout_policy = policy;
   return MG_OK;
 }

@@ -318,6 +318,34 @@ def test_launch_options_are_bitwise_neutral(prec, conv):
         assert np.array_equal(it, outs[0][2])
 
 
+@pytest.mark.parametrize("prec", [64, 32])
+def test_dia_and_sell_layouts_agree_bitwise(prec):
+    """Structured levels are stored as DIA by default; forcing SELL-32 must
+    give bitwise the same cycle, solve and parameter gradient."""
+    from paper_2608_29082_b300 import _lib as Lb
+    p, Ho, Hp = problem("checker65")
+    prm = rand_params(Hp.J, 43, 0.1)
+    dt = torch.float64 if prec == 64 else torch.float32
+    outs = []
+    try:
+        for policy in (0, 1):
+            Lb.check(Lb.lib().mg_set_layout_policy(policy))
+            S = Solver(Hp, prm, precision=prec, max_batch=2)
+            f = torch.tensor(p.f, dtype=dt, device=DEV)
+            u = torch.zeros_like(f)
+            S.vcycle(f, u)
+            us, info = S.solve(t64(p.f), tol=1e-9, max_iter=300)
+            u2 = torch.zeros_like(f)
+            S.forward_record(f, u2, 2)
+            _, _, gp = S.backward(torch.ones_like(f), 2, want_inputs=False)
+            outs.append((u, us, gp))
+            S.close()
+    finally:
+        Lb.lib().mg_set_layout_policy(0)
+    for a, b in zip(outs[0], outs[1]):
+        assert torch.equal(a, b)
+
+
 def test_whole_cycle_in_one_block_matches_oracle():
     """Tiny hierarchy: with the tail threshold above level 0 the entire cycle
     runs in one thread block; FP64 parity with the oracle still holds."""
