@@ -93,7 +93,11 @@ class Solver:
         self.hier = hier
         self.precision = int(precision)
         self.max_batch = int(max_batch)
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if isinstance(device, torch.device):
+            self.device = device
+        else:
+            self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                       else int(device))
         self.dtype = torch.float64 if self.precision == 64 else torch.float32
         self.params = params
         h, Aarr, keep = hier.c_structs()

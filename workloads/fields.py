@@ -41,11 +41,27 @@ def lognormal(L: MeshLevel, sigma: float, corr_len: float, seed: int,
     w = r.standard_normal((n_features, 2)) / corr_len
     b = r.uniform(0.0, 2.0 * np.pi, size=n_features)
     c = centroids(L)
-    g = np.empty(c.shape[0])
-    step = 65536
-    for s in range(0, c.shape[0], step):
-        g[s:s + step] = np.sqrt(2.0 / n_features) * np.cos(c[s:s + step] @ w.T + b).sum(1)
-    return np.exp(sigma * g)
+    g = _rff_tensor_grid(c, w, b)
+    if g is None:
+        g = np.empty(c.shape[0])
+        step = 65536
+        for s in range(0, c.shape[0], step):
+            g[s:s + step] = np.cos(c[s:s + step] @ w.T + b).sum(1)
+    return np.exp(sigma * np.sqrt(2.0 / n_features) * g)
+
+
+def _rff_tensor_grid(c: np.ndarray, w: np.ndarray, b: np.ndarray):
+    """sum_m cos(w_m . c + b_m) for centroids that form a few tensor grids
+    (uniform square meshes: one grid per triangle orientation), as
+    Re(Ey diag(e^{ib}) Ex^T), a complex matrix product; None otherwise."""
+    xs, xi = np.unique(np.round(c[:, 0], 12), return_inverse=True)
+    ys, yi = np.unique(np.round(c[:, 1], 12), return_inverse=True)
+    if xs.size * ys.size > 8 * c.shape[0] or xs.size * ys.size > 2 ** 26:
+        return None
+    ex = np.exp(1j * np.outer(xs, w[:, 0]))              # (nx, M)
+    ey = np.exp(1j * np.outer(ys, w[:, 1]) + 1j * b)     # (ny, M)
+    G = (ey @ ex.T).real                                  # (ny, nx)
+    return G[yi, xi]
 
 
 def rotated_anisotropy(eps: float, angle_deg: float) -> np.ndarray:
