@@ -204,12 +204,12 @@ def run_ours(args):
     u = torch.zeros_like(f)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def timed(S):
+    def timed(S, method="refine"):
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         for _ in range(args.warmup):
             u.zero_()
-            S.solve(f, u, tol=TOL, max_iter=MAX_ITER)
+            S.solve(f, u, tol=TOL, max_iter=MAX_ITER, method=method)
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -219,7 +219,7 @@ def run_ours(args):
             flush.zero_()
             u.zero_()
             starts[k].record()
-            _, info = S.solve(f, u, tol=TOL, max_iter=MAX_ITER)
+            _, info = S.solve(f, u, tol=TOL, max_iter=MAX_ITER, method=method)
             ends[k].record()
             infos.append(info)
         torch.cuda.synchronize()
@@ -233,6 +233,8 @@ def run_ours(args):
         ms64, info64, nk64 = timed(S64)
     clocks = clk.summary()
     u32 = u.clone()
+    # the same learned cycle as preconditioner of flexible CG (FP64 outer)
+    msfcg, infofcg, nkfcg = timed(S32, method="fcg")
     # max over ranks
     if pg:
         t = torch.tensor([ms32, ms64], device=dev)
@@ -320,6 +322,9 @@ def run_ours(args):
             "plain_fp64_ms": round(ms64, 4),
             "plain_fp64_iters": int(info64.iters[0]),
             "plain_fp64_relres": float(info64.relres[0]),
+            "learned_fcg_ms": round(msfcg, 4),
+            "learned_fcg_iters": int(infofcg.iters[0]),
+            "learned_fcg_relres": float(infofcg.relres[0]),
             "speedup_vs_plain_fp64": round(ms64 / ms32, 3),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms/solve",
                     "h2d_bytes_per_step": int(2 * fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)},

@@ -175,6 +175,16 @@ mg_status mg_vcycle(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, v
 mg_status mg_solve(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
                    int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
 
+/* Flexible conjugate gradients (one stored direction, Notay's FCG) in FP64
+ * with the context's V-cycle as a variable preconditioner: z = LMG(A, r, 0),
+ * in FP32 on a power-of-two-scaled residual for precision-32 contexts.
+ * Same arguments, stopping rule and batch independence as mg_solve; the
+ * relres reported is that of the true residual f - A u of the final iterate.
+ * Krylov acceleration of the cycle is the paper's preconditioner use (Sec. 4.2),
+ * with flexible CG in place of FGMRES for SPD operators. */
+mg_status mg_solve_fcg(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
+                       int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
+
 /* mg_solve with HOST f and u (pageable or pinned): copies f and the initial
  * u to the device, solves, copies u back.  Same semantics otherwise. */
 mg_status mg_solve_host(mg_ctx* ctx, const double* f_host, double* u_host, int32_t nrhs,

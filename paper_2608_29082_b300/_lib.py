@@ -76,6 +76,7 @@ def lib() -> C.CDLL:
         "mg_set_params": ([vp, C.POINTER(Params)], C.c_int),
         "mg_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_solve": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
+        "mg_solve_fcg": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
         "mg_solve_host": ([vp, f64p, f64p, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp],
                           C.c_int),
         "mg_level_apply": ([vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int32, vp], C.c_int),

@@ -213,28 +213,28 @@ __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T*
   block_dots<2>(v, partial);
 }
 
-// Residual loss: r = f - A u; per block, per rhs partial sums of r^2 (same
-// mapping as k_resid64); optionally keeps r for the gradient.
+// Residual loss: r = f - A u; per block, per rhs partial sums of r^2 (the
+// batch-independent tiling of k_resid64); optionally keeps r for the gradient.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_loss_resid(LV<T> L, const T* __restrict__ f,
-                                                         const T* __restrict__ u, T* __restrict__ r,
-                                                         int B, double* __restrict__ partial) {
-  __shared__ double sh[kThreads];
-  const int R = kThreads / B;
-  const int tt = threadIdx.x;
-  const int i = blockIdx.x * R + tt / B, b = tt % B;
+__global__ void __launch_bounds__(kRedMax) k_loss_resid(LV<T> L, const T* __restrict__ f,
+                                                        const T* __restrict__ u, T* __restrict__ r,
+                                                        int B, double* __restrict__ partial) {
+  __shared__ double sh[kRedMax];
+  int i, b;
+  bool ok;
+  red_tile(L.n, B, i, b, ok);
   double rv = 0.0;
-  if (tt < R * B && i < L.n) {
+  if (ok) {
     const size_t k = (size_t)i * B + b;
     const T ax = row_ax(L, i, u, B, b);
     const T rr = fma(-L.diag[i], u[k], f[k]) - ax;
     if (r) r[k] = rr;
     rv = (double)rr;
   }
-  sh[tt] = rv * rv;
+  sh[threadIdx.x] = rv * rv;
   __syncthreads();
-  block_rows_reduce(sh, R, B);
-  if (tt < B) partial[(size_t)blockIdx.x * B + tt] = sh[tt];
+  block_rows_reduce32(sh);
+  red_store(sh, B, partial);
 }
 
 // ubar = -2 w_b A r  (gradient of sum_b w_b ||f_b - A u_b||^2 w.r.t. u)

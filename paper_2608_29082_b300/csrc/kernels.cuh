@@ -458,6 +458,7 @@ __global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __res
   pdl_launch();
 }
 
+
 // ------------------------------------------------------ small levels -----
 
 // All levels lt..J-1 of one V-cycle in a single block: down (smoothing,
@@ -557,6 +558,53 @@ __device__ __forceinline__ U* smem_take(unsigned char* base, size_t& off, const 
     for (size_t k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
   }
   return dst;
+}
+
+// Offset of column j of a packed column-major lower triangle of order n.
+__device__ __forceinline__ size_t packed_col(int n, int j) {
+  return (size_t)j * n - (size_t)j * (j - 1) / 2;
+}
+
+// The same substitutions as coarse_chol_block with the factor staged in
+// shared memory as a packed lower triangle (column j holds rows j..n-1):
+// every step reads the factor at shared-memory latency.  Same values and
+// order, hence the same results.
+template <class T>
+__global__ void k_coarse_chol_packed(const double* __restrict__ Lp, const double* __restrict__ dinv,
+                                     int n, const T* __restrict__ f, T* __restrict__ u, int B) {
+  extern __shared__ __align__(16) unsigned char cs_smem[];
+  pdl_wait();
+  pdl_launch();
+  size_t off = 0;
+  const double* P = smem_take(cs_smem, off, Lp, (size_t)n * (n + 1) / 2);
+  const double* di = smem_take(cs_smem, off, dinv, (size_t)n);
+  double* ys = (double*)(cs_smem + off);
+  cp_async_wait_all();
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* y = ys + (size_t)warp * n;
+  for (int b = warp; b < B; b += nw) {
+    for (int i = lane; i < n; i += 32) y[i] = (double)f[(size_t)i * B + b];
+    __syncwarp();
+    for (int j = 0; j < n; ++j) {  // L y = f
+      const double yj = y[j] * di[j];
+      const double* col = P + packed_col(n, j) - j;  // col[i] = L_ij
+      __syncwarp();
+      for (int i = j + 1 + lane; i < n; i += 32) y[i] = fma(-col[i], yj, y[i]);
+      if (lane == 0) y[j] = yj;
+      __syncwarp();
+    }
+    for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+      const double xj = y[j] * di[j];
+      __syncwarp();
+      for (int i = lane; i < j; i += 32) y[i] = fma(-P[packed_col(n, i) + (j - i)], xj, y[i]);
+      if (lane == 0) y[j] = xj;
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) u[(size_t)i * B + b] = (T)y[i];
+    __syncwarp();
+  }
+  pdl_launch();
 }
 
 template <class T>
@@ -707,77 +755,99 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 }
 
 // ---------------------------------------------------------------------------
-// FP64 outer loop (iterative refinement / plain solve) with deterministic
-// per-right-hand-side reductions.  A block covers R = blockDim/B rows for all
-// B right-hand sides (B <= kThreads); per-block partial sums go to
-// partial[blk * B + b] and are summed in a fixed order by k_reduce.
+// FP64 outer loops (refinement, plain solve, flexible CG) with deterministic
+// per-right-hand-side reductions whose grouping does not depend on the batch:
+// a block covers kRedRows = 32 rows and bt = min(B, 32) right-hand-side
+// columns (blockDim = 32 * bt, grid = (ceil(n / 32), ceil(B / bt))), sums its
+// 32 rows per column with a fixed tree into partial[blockIdx.x * B + b], and
+// k_reduce adds the blocks in a fixed order.  So every right-hand side's
+// norms and dot products are bitwise the same whatever else is in the batch.
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ void block_rows_reduce(double* sh, int R, int B) {
+constexpr int kRedRows = 32;
+constexpr int kRedMax = 1024;  // kRedRows x 32 columns
+
+// (row, rhs) of this thread in the reduction tiling.
+__device__ __forceinline__ void red_tile(int n, int B, int& i, int& b, bool& ok) {
+  const int bt = blockDim.x / kRedRows;
   const int t = threadIdx.x;
-  const int row = t / B;
-  int p2 = 1;
-  while (p2 < R) p2 <<= 1;
-  for (int s = p2 >> 1; s >= 1; s >>= 1) {
-    if (row < s && row + s < R && t < R * B) sh[t] += sh[t + s * B];
+  i = blockIdx.x * kRedRows + t / bt;
+  b = blockIdx.y * bt + t % bt;
+  ok = i < n && b < B;
+}
+
+// sh[r * bt + c] summed over the 32 rows r (fixed tree) into sh[c].
+__device__ __forceinline__ void block_rows_reduce32(double* sh) {
+  const int bt = blockDim.x / kRedRows;
+  const int t = threadIdx.x;
+  const int r = t / bt;
+  for (int s = kRedRows / 2; s >= 1; s >>= 1) {
+    if (r < s) sh[t] += sh[t + s * bt];
     __syncthreads();
   }
 }
 
-// r = f - A u in FP64; optionally rhat = float(r * 2^-sexp[b]); partial sums
-// of r^2.  u_zero: u taken as 0.
-__global__ void __launch_bounds__(kThreads) k_resid64(LV<double> L, const double* __restrict__ f,
-                                                      const double* __restrict__ u,
-                                                      float* __restrict__ rhat,
-                                                      const int* __restrict__ sexp, int B,
-                                                      double* __restrict__ partial) {
-  pdl_wait();
-  __shared__ double sh[kThreads];
-  const int R = kThreads / B;
+// Writes the block's column sums (row 0 of sh) to partial[blk * B + b].
+__device__ __forceinline__ void red_store(const double* sh, int B, double* __restrict__ partial) {
+  const int bt = blockDim.x / kRedRows;
   const int t = threadIdx.x;
-  const int i = blockIdx.x * R + t / B, b = t % B;
+  const int b = blockIdx.y * bt + t;
+  if (t < bt && b < B) partial[(size_t)blockIdx.x * B + b] = sh[t];
+}
+
+// r = f - A u in FP64; optionally rhat = float(r * 2^-sexp[b]); partial sums
+// of r^2.
+__global__ void __launch_bounds__(kRedMax) k_resid64(LV<double> L, const double* __restrict__ f,
+                                                     const double* __restrict__ u,
+                                                     float* __restrict__ rhat,
+                                                     const int* __restrict__ sexp, int B,
+                                                     double* __restrict__ partial) {
+  pdl_wait();
+  __shared__ double sh[kRedMax];
+  int i, b;
+  bool ok;
+  red_tile(L.n, B, i, b, ok);
   double r = 0.0;
-  if (t < R * B && i < L.n) {
+  if (ok) {
     const size_t k = (size_t)i * B + b;
     const double ax = row_ax(L, i, u, B, b);
     r = fma(-L.diag[i], u[k], f[k]) - ax;
     if (rhat) rhat[k] = (float)ldexp(r, -sexp[b]);
   }
-  sh[t] = r * r;
+  sh[threadIdx.x] = r * r;
   __syncthreads();
-  block_rows_reduce(sh, R, B);
-  if (t < B) partial[(size_t)blockIdx.x * B + t] = sh[t];
+  block_rows_reduce32(sh);
+  red_store(sh, B, partial);
 }
 
-// r = f - A u in FP64 with the same arithmetic as k_resid64 (single-step check).
-__global__ void __launch_bounds__(kThreads) k_outer_residual64(LV<double> L,
-                                                               const double* __restrict__ f,
-                                                               const double* __restrict__ u,
-                                                               double* __restrict__ out, int B) {
+// r = f - A u in FP64 with the same arithmetic as k_resid64.
+__global__ void __launch_bounds__(kRedMax) k_outer_residual64(LV<double> L,
+                                                              const double* __restrict__ f,
+                                                              const double* __restrict__ u,
+                                                              double* __restrict__ out, int B) {
   pdl_wait();
-  const int R = kThreads / B;
-  const int t = threadIdx.x;
-  const int i = blockIdx.x * R + t / B, b = t % B;
-  if (t < R * B && i < L.n) {
+  int i, b;
+  bool ok;
+  red_tile(L.n, B, i, b, ok);
+  if (ok) {
     const size_t k = (size_t)i * B + b;
     out[k] = fma(-L.diag[i], u[k], f[k]) - row_ax(L, i, u, B, b);
   }
 }
 
-// partial sums of x^2 (FP64), same block mapping as k_resid64.
-__global__ void __launch_bounds__(kThreads) k_sumsq64(const double* __restrict__ x, int n, int B,
-                                                      double* __restrict__ partial) {
+// partial sums of x^2 (FP64), same tiling as k_resid64.
+__global__ void __launch_bounds__(kRedMax) k_sumsq64(const double* __restrict__ x, int n, int B,
+                                                     double* __restrict__ partial) {
   pdl_wait();
-  __shared__ double sh[kThreads];
-  const int R = kThreads / B;
-  const int t = threadIdx.x;
-  const int i = blockIdx.x * R + t / B;
-  double v = 0.0;
-  if (t < R * B && i < n) v = x[(size_t)i * B + t % B];
-  sh[t] = v * v;
+  __shared__ double sh[kRedMax];
+  int i, b;
+  bool ok;
+  red_tile(n, B, i, b, ok);
+  const double v = ok ? x[(size_t)i * B + b] : 0.0;
+  sh[threadIdx.x] = v * v;
   __syncthreads();
-  block_rows_reduce(sh, R, B);
-  if (t < B) partial[(size_t)blockIdx.x * B + t] = sh[t];
+  block_rows_reduce32(sh);
+  red_store(sh, B, partial);
 }
 
 // out[b] = sum over blocks of partial[blk * B + b]; grid = B blocks.

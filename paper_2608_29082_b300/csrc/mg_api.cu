@@ -20,6 +20,7 @@
 
 #include "adjoint.cuh"
 #include "kernels.cuh"
+#include "krylov.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -255,6 +256,10 @@ struct mg_ctx {
   std::vector<DevLevel<double>> d64;
   std::vector<DevLevel<float>> d32;
   double *cholL = nullptr, *cholU = nullptr, *cholDinv = nullptr;
+  double* cholP = nullptr;  // packed column-major lower triangle of the factor
+  // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
+  double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
+  double *k_partial = nullptr, *k_small = nullptr;
   int nu_pre = 2, nu_post = 2;
   std::vector<double> prm;  // [J-1][P_COUNT]
   double* prm64 = nullptr;
@@ -522,6 +527,19 @@ struct Issue {
   }
 
   void coarse(const T* f, T* u) {
+    const size_t nJ = (size_t)c->nJ;
+    const size_t fixed = mgk::tail_align(nJ * (nJ + 1) / 2 * sizeof(double)) +
+                         mgk::tail_align(nJ * sizeof(double));
+    const int nwp = std::max(1, std::min(B, 32));
+    if (fixed + (size_t)nwp * nJ * sizeof(double) <= kTailSmemMax) {
+      // factor staged in shared memory as a packed triangle
+      pre(MG_K_COARSE_CHOL, c->J - 1);
+      launch(mgk::k_coarse_chol_packed<T>, dim3(1), dim3(32 * nwp),
+             fixed + (size_t)nwp * nJ * sizeof(double), (const double*)c->cholP,
+             (const double*)c->cholDinv, c->nJ, f, u, B);
+      post();
+      return;
+    }
     const int nw = coarse_warps(8);
     pre(MG_K_COARSE_CHOL, c->J - 1);
     launch(mgk::k_coarse_chol<T>, dim3(1), dim3(32 * nw), (size_t)nw * c->nJ * sizeof(double),
@@ -693,6 +711,9 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   for (auto& L : c->d64) free_level(L);
   for (auto& L : c->d32) free_level(L);
+  for (void* p : {(void*)c->cholP, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
+                  (void*)c->k_partial, (void*)c->k_small})
+    if (p) cudaFree(p);
   void* ptrs[] = {c->cholL,  c->cholU,  c->cholDinv, c->prm64,  c->prm32, c->partial,
                   c->rsum,   c->fsum,   c->relres,   c->w64,    c->active, c->iters,
                   c->sexp,   c->sexp_prev, c->state, c->c32,    c->rhat32, c->hf, c->hu,
@@ -812,6 +833,14 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   if ((e = cudaFuncSetAttribute(mgk::k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kTailSmemMax)) != cudaSuccess)
     return bail(e);
+  if ((e = cudaFuncSetAttribute(mgk::k_coarse_chol_packed<float>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)) !=
+      cudaSuccess)
+    return bail(e);
+  if ((e = cudaFuncSetAttribute(mgk::k_coarse_chol_packed<double>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)) !=
+      cudaSuccess)
+    return bail(e);
   if (precision == 64) {
     c->d64.resize(J);
     for (int l = 0; l < J; ++l)
@@ -830,6 +859,13 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   if ((e = upload(&c->cholL, Lc)) != cudaSuccess) return bail(e);
   if ((e = upload(&c->cholU, Uc)) != cudaSuccess) return bail(e);
   if ((e = upload(&c->cholDinv, dj)) != cudaSuccess) return bail(e);
+  {
+    std::vector<double> Pk;
+    Pk.reserve((size_t)nJ * (nJ + 1) / 2);
+    for (int j = 0; j < nJ; ++j)
+      for (int i = j; i < nJ; ++i) Pk.push_back(Lc[i + (size_t)j * nJ]);
+    if ((e = upload(&c->cholP, Pk)) != cudaSuccess) return bail(e);
+  }
   // outer-loop workspace
   const int n0 = H[0].n;
   c->nblk_max = n0;  // R >= 1 rows per block
@@ -937,8 +973,9 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
   mg_status st = sync_params(c, s);
   if (st != MG_OK) return st;
   const int n0 = c->n[0];
-  const int R = kThreads / B;
-  const int nblk = (n0 + R - 1) / R;
+  const int bt = std::min((int)B, 32);  // reduction tiling (kernels.cuh red_tile)
+  const int nblk = (n0 + mgk::kRedRows - 1) / mgk::kRedRows;
+  const dim3 rgrid(nblk, (B + bt - 1) / bt), rblock(mgk::kRedRows * bt);
   const LV<double> L0 = c->d64[0].view();
   const bool p32 = c->prec == 32;
   c->solve_ctl[0] = tol;
@@ -951,7 +988,7 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
     // residual of the current iterate, its norms and the convergence test;
     // the test sets the while-node condition
     auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc) {
-      is.launch(mgk::k_resid64, dim3(nblk), dim3(kThreads), 0, L0, (const double*)f,
+      is.launch(mgk::k_resid64, rgrid, rblock, 0, L0, (const double*)f,
                 (const double*)u, p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B,
                 c->partial);
       is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
@@ -970,7 +1007,7 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
                                           cudaStreamCaptureModeThreadLocal));
     {
       Issue<double> is{c, c->d64, c->prm64, c->cap, B};
-      is.launch(mgk::k_sumsq64, dim3(nblk), dim3(kThreads), 0, f, n0, (int)B, c->partial);
+      is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
       is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
                 (int)B, c->fsum);
       is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B,
@@ -1105,10 +1142,10 @@ extern "C" mg_status mg_level_apply(mg_ctx* c, int32_t lev, int32_t op, const vo
     if (lev != 0 || !y) return c->fail(MG_ERR_INVALID, "mg_level_apply: outer residual needs level 0, f, u");
     if (out == x || out == y) return c->fail(MG_ERR_INVALID, "mg_level_apply: out aliases an input");
     cudaStream_t s = (cudaStream_t)stream;
-    const int R = kThreads / B;
-    const int nblk = (c->n[0] + R - 1) / R;
-    mgk::k_outer_residual64<<<nblk, kThreads, 0, s>>>(c->d64[0].view(), (const double*)x,
-                                                       (const double*)y, (double*)out, B);
+    const int bt = std::min((int)B, 32);
+    const dim3 rgrid((c->n[0] + mgk::kRedRows - 1) / mgk::kRedRows, (B + bt - 1) / bt);
+    mgk::k_outer_residual64<<<rgrid, mgk::kRedRows * bt, 0, s>>>(
+        c->d64[0].view(), (const double*)x, (const double*)y, (double*)out, B);
     MG_CUDA(cudaGetLastError());
     c->launches += 1;
     return MG_OK;
@@ -1215,6 +1252,7 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
 }
 
 #include "train_impl.cuh"
+#include "krylov_impl.cuh"
 
 extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_option: ctx is NULL");

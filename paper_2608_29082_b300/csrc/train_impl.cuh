@@ -262,10 +262,11 @@ template <class T>
 mg_status residual_loss(mg_ctx* c, const T* f, const T* u, int B, const double* w, double* loss,
                         double* per_rhs, T* grad_u, cudaStream_t s) {
   DevLevel<T>& D = levels_of<T>(c)[0];
-  const int R = kThreads / B;
-  const int nblk = (D.n + R - 1) / R;
+  const int bt = std::min(B, 32);
+  const int nblk = (D.n + mgk::kRedRows - 1) / mgk::kRedRows;
   T* r = grad_u ? D.t : nullptr;
-  mgk::k_loss_resid<T><<<nblk, kThreads, 0, s>>>(D.view(), f, u, r, B, c->partial);
+  mgk::k_loss_resid<T><<<dim3(nblk, (B + bt - 1) / bt), mgk::kRedRows * bt, 0, s>>>(
+      D.view(), f, u, r, B, c->partial);
   mgk::k_reduce<<<B, kThreads, 0, s>>>(c->partial, nblk, B, c->rsum);
   mgk::k_loss_combine<<<1, 32, 0, s>>>(c->rsum, w, B, loss, per_rhs);
   int nk = 3;

@@ -1,0 +1,218 @@
+"""Measurements of the other workloads (one JSON line each).
+
+    python -m paper_2608_29082_b300.workload_bench lshape [--refinements 7 --batch 16]
+        Jittered L-shape, anisotropic diffusion (about 3.1M DOF at 7 red
+        refinements), 16 right-hand sides: Theta trained on the operator
+        (Algorithm 3), then time to 1e-8 for the learned FP32 cycle in FP64
+        refinement and for the plain FP64 multigrid, and per-kernel achieved
+        bandwidth (algorithmic bytes / CUDA-event time) against the measured
+        HBM peak.  The working set is far larger than L2.
+    python -m paper_2608_29082_b300.workload_bench training [--kind checker --batch 64]
+        One training step of Algorithm 3 on the 257^2 workloads: K = 10
+        unrolled FP32 cycles with per-level checkpoints, the residual loss
+        and the hand-written adjoint, for 64 right-hand sides.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2608_29082_b300 import Hierarchy, LMGParams, Solver  # noqa: E402
+from paper_2608_29082_b300.training import ParamMap, Trainer  # noqa: E402
+from paper_2608_29082_b300.train_cli import PRESETS  # noqa: E402
+
+
+def hbm_peak() -> float:
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except Exception:
+        return 6400.0
+
+
+def level_bytes(name: str, hier, lev: int, B: int, b: int) -> float:
+    """Algorithmic bytes of one launch (each array read or written once)."""
+    n = hier.sizes[lev]
+    A = hier.A[lev]
+    nnz_off = A.data.size - n
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    m = A.indices != rows
+    col_b = 0 if np.unique(A.indices[m] - rows[m]).size <= 8 else 4
+    nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
+    nnzP = hier.P[lev].data.size if lev < hier.J - 1 else 0
+    table = {
+        "jacobi_smooth": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
+        "residual_scaled": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
+        "sage_conv_update": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
+        "residual": nnz_off * (col_b + b) + n * b + 3 * B * n * b,
+        "restrict_conv_fine": nnz_off * (col_b or b) + n * b + 2 * B * n * b,
+        "restrict_conv": nnzP * (4 + b) + B * n * b + B * nc * b,
+        "prolong_fine": nnzP * (4 + b) + B * nc * b + B * n * b,
+        "prolong_conv": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
+        "outer_residual_fp64": nnz_off * (col_b + 8) + 2 * n * 8 + B * n * 24,
+    }
+    return table.get(name, float("nan"))
+
+
+def kernel_table(S: Solver, hier, f: torch.Tensor, reps: int = 3):
+    B = f.shape[1]
+    b = 4 if S.precision == 32 else 8
+    u = torch.zeros_like(f)
+    agg = {}
+    for _ in range(reps):
+        u.zero_()
+        for name, lev, ms in S.vcycle_profile(f, u):
+            a = agg.setdefault((name, lev), [0.0, 0])
+            a[0] += ms
+            a[1] += 1
+    peak = hbm_peak()
+    out = []
+    total = sum(v[0] for v in agg.values()) / reps
+    for (name, lev), (ms, cnt) in sorted(agg.items(), key=lambda kv: -kv[1][0]):
+        per = ms / cnt
+        nb = level_bytes(name, hier, lev, B, b)
+        gbs = nb / (per * 1e-3) / 1e9 if np.isfinite(nb) else None
+        out.append({"kernel": name, "level": lev, "launches_per_cycle": cnt / reps,
+                    "us_per_launch": round(per * 1e3, 2), "share": round(ms / reps / total, 4),
+                    "algorithmic_MB": round(nb / 1e6, 2) if np.isfinite(nb) else None,
+                    "GBps": round(gbs, 1) if gbs else None,
+                    "frac_of_hbm": round(gbs / peak, 3) if gbs else None})
+    return out, total * 1e3
+
+
+def timed_solve(S: Solver, f64: torch.Tensor, tol: float, reps: int = 3, method="refine"):
+    u = torch.zeros_like(f64)
+    S.solve(f64, u, tol=tol, max_iter=400, method=method)
+    ms = []
+    for _ in range(reps):
+        u.zero_()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        _, info = S.solve(f64, u, tol=tol, max_iter=400, method=method)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms)), info, u
+
+
+def run_lshape(a):
+    from oracle.lmg import drop_small
+    import workloads as W
+    from workloads import fields
+    t0 = time.perf_counter()
+    prob = W.lshape_anisotropic(refinements=a.refinements, batch=a.batch, seed=a.seed)
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    hier = Hierarchy.from_problem(prob)
+    t_setup = time.perf_counter() - t0
+    J = hier.J
+    dev = torch.device("cuda")
+    plain = LMGParams.identity(J)
+    learned, training = plain, None
+    if a.train_epochs > 0:
+        ftr = torch.tensor(fields.rhs(hier.sizes[0], a.train_batch, 1000 + a.seed),
+                           dtype=torch.float32, device=dev)
+        Str = Solver(hier, plain, precision=32, max_batch=a.train_batch)
+        t0 = time.perf_counter()
+        log = Trainer(Str, ParamMap(J, **PRESETS[a.preset]), n_cycles=a.K).train(
+            ftr, plain, max_epochs=a.train_epochs)
+        torch.cuda.synchronize()
+        training = {"preset": a.preset, "epochs": len(log.losses), "K": a.K,
+                    "rhs": a.train_batch, "seconds": round(time.perf_counter() - t0, 2),
+                    "loss_ratio": float(log.best_loss / log.losses[0])}
+        learned = log.params
+        Str.close()
+    f64 = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    S32 = Solver(hier, learned, precision=32, max_batch=a.batch)
+    ms32, info32, u32 = timed_solve(S32, f64, a.tol)
+    kt32, cyc32 = kernel_table(S32, hier, f64.float())
+    msf32, infof32, uf32 = timed_solve(S32, f64, a.tol, method="fcg")
+    S64 = Solver(hier, plain, precision=64, max_batch=a.batch)
+    ms64, info64, _ = timed_solve(S64, f64, a.tol)
+    msf64, infof64, _ = timed_solve(S64, f64, a.tol, method="fcg")
+    kt64, cyc64 = kernel_table(S64, hier, f64)
+    # oracle re-check of the learned result (its own fine operator)
+    Ao = drop_small(prob.A_full.tocsr())
+    I = prob.mesh.levels[0].interior
+    A_int = Ao[I][:, I]
+    def oracle_relres(uu):
+        un = uu.cpu().numpy()
+        r = prob.f - A_int @ un
+        return np.sqrt((r * r).sum(0)) / np.sqrt((prob.f * prob.f).sum(0))
+    rr = oracle_relres(u32)
+    rrf = oracle_relres(uf32)
+    out = {"workload": f"L-shape anisotropic, {a.refinements} red refinements, {hier.sizes[0]} DOF, "
+                       f"{J} levels, {a.batch} rhs, tol {a.tol}",
+           "levels": hier.sizes, "generate_s": round(t_gen, 1), "setup_s": round(t_setup, 1),
+           "training": training,
+           "learned_fp32_ms": round(ms32, 3), "learned_iters": int(info32.iters.max()),
+           "plain_fp64_ms": round(ms64, 3), "plain_iters": int(info64.iters.max()),
+           "speedup": round(ms64 / ms32, 3), "oracle_max_relres": float(rr.max()),
+           "learned_fp32_fcg_ms": round(msf32, 3), "learned_fcg_iters": int(infof32.iters.max()),
+           "oracle_max_relres_fcg": float(rrf.max()),
+           "plain_fp64_fcg_ms": round(msf64, 3), "plain_fcg_iters": int(infof64.iters.max()),
+           "speedup_fcg_learned_vs_plain_stationary": round(ms64 / msf32, 3),
+           "cycle_us_fp32_profiled": round(cyc32, 1), "cycle_us_fp64_profiled": round(cyc64, 1),
+           "hbm_peak_gbs": hbm_peak(), "kernels_fp32": kt32[:8], "kernels_fp64": kt64[:6]}
+    print(json.dumps(out), flush=True)
+
+
+def run_training(a):
+    import workloads as W
+    prob = W.training_square(a.kind, N=257, J=8, batch=a.batch, seed=a.seed)
+    hier = Hierarchy.from_problem(prob)
+    J = hier.J
+    p = LMGParams.identity(J)
+    S = Solver(hier, p, precision=32, max_batch=a.batch)
+    f = torch.tensor(prob.f, dtype=torch.float32, device="cuda")
+    tr = Trainer(S, ParamMap(J, shared=("wB1", "wB2", "wR1", "wR2", "wP1", "wP2")), n_cycles=a.K)
+    for _ in range(2):
+        tr.loss_and_grad(p, f, torch.zeros_like(f))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    e0.record()
+    for _ in range(a.steps):
+        loss, g, _ = tr.loss_and_grad(p, f, torch.zeros_like(f))
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    t0 = time.perf_counter()
+    log = tr.train(f, p, max_epochs=a.epochs)
+    t_train = time.perf_counter() - t0
+    print(json.dumps({"workload": f"training {a.kind} 257^2, {J} levels, {a.batch} rhs, K={a.K}",
+                      "ms_per_training_step": round(ms, 3), "loss0": log.losses[0],
+                      "best_loss": log.best_loss, "epochs": len(log.losses),
+                      "train_seconds": round(t_train, 2)}), flush=True)
+
+
+if __name__ == "__main__":
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    l = sub.add_parser("lshape")
+    l.add_argument("--refinements", type=int, default=7)
+    l.add_argument("--batch", type=int, default=16)
+    l.add_argument("--tol", type=float, default=1e-8)
+    l.add_argument("--train-epochs", type=int, default=60)
+    l.add_argument("--train-batch", type=int, default=4)
+    l.add_argument("--K", type=int, default=10)
+    l.add_argument("--preset", default="shared_conv")
+    l.add_argument("--seed", type=int, default=0)
+    t = sub.add_parser("training")
+    t.add_argument("--kind", default="checker")
+    t.add_argument("--batch", type=int, default=64)
+    t.add_argument("--K", type=int, default=10)
+    t.add_argument("--steps", type=int, default=5)
+    t.add_argument("--epochs", type=int, default=30)
+    t.add_argument("--seed", type=int, default=0)
+    a = ap.parse_args()
+    torch.cuda.set_device(0)
+    run_lshape(a) if a.cmd == "lshape" else run_training(a)

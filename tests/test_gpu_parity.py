@@ -290,6 +290,49 @@ def test_full_size_checkerboard_513():
     assert O.relres(Ho, p.f, u.cpu().numpy())[0] < 1e-8
 
 
+# ------------------------------------------------------ flexible CG outer --
+
+@pytest.mark.parametrize("name", ["checker65", "lognormal65", "lshape_r2"])
+@pytest.mark.parametrize("prec", [64, 32])
+def test_fcg_reaches_tolerance_with_fewer_iterations(name, prec):
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 47, 0.05)
+    S = Solver(Hp, prm, precision=prec, max_batch=p.f.shape[1])
+    u, info = S.solve(t64(p.f), tol=1e-8, max_iter=400, method="fcg")
+    assert info.status == 0
+    rr = O.relres(Ho, p.f, u.cpu().numpy())  # true residual, re-evaluated by the oracle
+    assert (rr < 1e-8).all(), rr
+    assert np.allclose(info.relres, rr, rtol=1e-6)
+    _, info_r = S.solve(t64(p.f), tol=1e-8, max_iter=400, method="refine")
+    assert info.iters.max() <= info_r.iters.max()
+
+
+def test_fcg_result_independent_of_batch():
+    p, Ho, Hp = problem("lognormal65")
+    prm = rand_params(Hp.J, 53, 0.05)
+    f = np.random.default_rng(8).standard_normal((Hp.sizes[0], 3))
+    f[:, 1] *= 1e-4
+    S3 = Solver(Hp, prm, precision=32, max_batch=3)
+    S1 = Solver(Hp, prm, precision=32, max_batch=1)
+    u3, i3 = S3.solve(t64(f), tol=1e-8, max_iter=200, method="fcg")
+    for b in range(3):
+        u1, i1 = S1.solve(t64(f[:, [b]]), tol=1e-8, max_iter=200, method="fcg")
+        assert i1.iters[0] == i3.iters[b]
+        assert torch.equal(u1[:, 0], u3[:, b])
+
+
+def test_packed_coarse_solve_matches_cholesky():
+    """The L-shape coarsest level (161 rows) uses the shared-memory packed
+    factor: same values as scipy's Cholesky solve."""
+    p, Ho, Hp = problem("lshape_r2")
+    S = Solver(Hp, rand_params(Hp.J, 59), precision=64, max_batch=4)
+    nJ = Hp.sizes[-1]
+    fJ = np.random.default_rng(2).standard_normal((nJ, 4))
+    out = torch.empty((nJ, 4), dtype=torch.float64, device=DEV)
+    S.level_apply(Hp.J - 1, "coarse", t64(fJ), None, out)
+    assert rel(out.cpu().numpy(), sla.cho_solve(Ho.chol, fJ)) < 1e-13
+
+
 # --------------------------------------------------------- launch options --
 
 @pytest.mark.parametrize("prec", [64, 32])
