@@ -220,8 +220,11 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     run in one thread block with block barriers instead of
  *                     one grid kernel per step (default 8192; 0 disables)
  *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
- *                     dependent launch; 0: plain stream order */
-typedef enum { MG_OPT_TAIL_WORK = 0, MG_OPT_PDL = 1 } mg_option;
+ *                     dependent launch; 0: plain stream order
+ *   MG_OPT_MULTI_RHS  1 (default): with nrhs > 1, one thread owns a row and a
+ *                     tile of right-hand sides (matrix read once per row,
+ *                     16-byte vector loads); 0: one thread per (row, rhs) */
+typedef enum { MG_OPT_TAIL_WORK = 0, MG_OPT_PDL = 1, MG_OPT_MULTI_RHS = 2 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);
 

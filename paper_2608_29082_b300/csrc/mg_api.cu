@@ -21,6 +21,7 @@
 #include "adjoint.cuh"
 #include "kernels.cuh"
 #include "krylov.cuh"
+#include "multi_rhs.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -283,6 +284,7 @@ struct mg_ctx {
   // options (mg_set_option)
   int64_t opt_tail_work = 2048;  // rows x rhs at or below which levels run in k_tail
   int opt_pdl = 1;               // programmatic dependent launch between kernels
+  int opt_multi_rhs = 1;         // multi-rhs kernels (a row and a tile of rhs per thread)
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
   int trK = 0, trB = 0, tr_nu_pre = -1, tr_nu_post = -1;
@@ -447,6 +449,120 @@ struct Issue {
     ++nk;
   }
 
+  // Right-hand sides per thread of the multi-rhs kernels (0: one thread per
+  // (row, rhs)): the widest tile of 16-byte vectors that divides B.
+  int mbv() const {
+    if (B < 2 || !c->opt_multi_rhs) return 0;
+    const int vmax = sizeof(T) == 4 ? 16 : 8;
+    for (int bv = vmax; bv >= 2; bv >>= 1)
+      if (B % bv == 0) return bv;
+    return 0;
+  }
+  dim3 mb_grid(int rows, int bv) const {
+    return dim3((unsigned)((rows + kThreads - 1) / kThreads), (unsigned)(B / bv));
+  }
+  // Calls fn(std::integral_constant<int, BV>) for the chosen tile width.
+  template <class F>
+  void with_bv(int bv, F&& fn) {
+    switch (bv) {
+      case 16: fn(std::integral_constant<int, 16>{}); break;
+      case 8: fn(std::integral_constant<int, 8>{}); break;
+      case 4: fn(std::integral_constant<int, 4>{}); break;
+      default: fn(std::integral_constant<int, 2>{}); break;
+    }
+  }
+
+  void op_residual(int lev, const T* f, const T* u, T* out, int scale, int zero) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_residual_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
+               D.view(), f, u, out, B, P(lev), scale, zero);
+      });
+    } else {
+      launch(mgk::k_residual<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, u, out, B,
+             P(lev), scale, zero);
+    }
+  }
+  void op_conv_update(int lev, const T* x, T* u, int zero) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_conv_update_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
+               D.view(), x, u, B, P(lev), zero);
+      });
+    } else {
+      launch(mgk::k_conv_update<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, u, B,
+             P(lev), zero);
+    }
+  }
+  void op_jacobi(int lev, const T* f, const T* uin, T* uout, int zero) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_jacobi_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(),
+               f, uin, uout, B, P(lev), zero);
+      });
+    } else {
+      launch(mgk::k_jacobi<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, uin, uout, B,
+             P(lev), zero);
+    }
+  }
+  void op_conv_r(int lev, const T* r, T* phi) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_conv_r_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(),
+               r, phi, B, P(lev));
+      });
+    } else {
+      launch(mgk::k_conv_r<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), r, phi, B,
+             P(lev));
+    }
+  }
+  // fc = P^T x (after Phi_R) or P^T (wR1 x) (plain restriction)
+  void op_gather(int lev, const T* x, T* fc, int scale) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_gather_mb<T, decltype(k)::value>, mb_grid(D.nc, bv), kThreads, 0,
+               D.view(), x, fc, B, P(lev), scale);
+      });
+    } else if (scale) {
+      launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B,
+             P(lev), 0);
+    } else {
+      launch(mgk::k_gather<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B);
+    }
+  }
+  void op_pe(int lev, const T* ec, T* pe) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_pe_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(), ec,
+               pe, B);
+      });
+    } else {
+      launch(mgk::k_pe<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec, pe, B);
+    }
+  }
+  // u = uin + Phi_P(x) with x = P e_c (conv), or u = uin + wP1 P x (plain)
+  void op_prolong(int lev, const T* x, const T* uin, T* u, int conv_p) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_prolong_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
+               D.view(), x, uin, u, B, P(lev), conv_p);
+      });
+    } else if (conv_p) {
+      launch(mgk::k_prolong_conv<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u,
+             B, P(lev));
+    } else {
+      launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u, B,
+             P(lev), 0);
+    }
+  }
+
   // nu smoothing steps on level lev; u updated in place.  zero: u is 0 on entry.
   void smooth(int lev, const T* f, T* u, int nu, bool zero) {
     DevLevel<T>& D = L[lev];
@@ -461,8 +577,7 @@ struct Issue {
       T* oth = D.u2;
       for (int k = 0; k < nu; ++k) {
         pre(MG_K_JACOBI, lev);
-        launch(mgk::k_jacobi<T>, g, kThreads, 0, D.view(), (const T*)f, (const T*)cur, oth, B,
-               P(lev), (int)(zero && k == 0));
+        op_jacobi(lev, f, cur, oth, (int)(zero && k == 0));
         post();
         std::swap(cur, oth);
       }
@@ -472,11 +587,10 @@ struct Issue {
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       pre(MG_K_RESIDUAL_SCALED, lev);
-      launch(mgk::k_residual<T>, g, kThreads, 0, D.view(), (const T*)f, (const T*)u, D.t, B,
-             P(lev), 1, z);
+      op_residual(lev, f, u, D.t, 1, z);
       post();
       pre(MG_K_CONV_UPDATE, lev);
-      launch(mgk::k_conv_update<T>, g, kThreads, 0, D.view(), (const T*)D.t, u, B, P(lev), z);
+      op_conv_update(lev, D.t, u, z);
       post();
     }
   }
@@ -484,22 +598,18 @@ struct Issue {
   void restrict_(int lev, const T* f, const T* u) {
     DevLevel<T>& D = L[lev];
     pre(MG_K_RESIDUAL, lev);
-    launch(mgk::k_residual<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), (const T*)f,
-           (const T*)u, D.t, B, P(lev), 0, 0);
+    op_residual(lev, f, u, D.t, 0, 0);
     post();
     if (conv(lev, mgk::P_WR2)) {  // Phi_R per fine row, then the gather P^T
       pre(MG_K_CONV_R, lev);
-      launch(mgk::k_conv_r<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), (const T*)D.t,
-             D.u2, B, P(lev));
+      op_conv_r(lev, D.t, D.u2);
       post();
       pre(MG_K_RESTRICT, lev);
-      launch(mgk::k_gather<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
-             (const T*)D.u2, Fl(lev + 1), B);
+      op_gather(lev, D.u2, Fl(lev + 1), 0);
       post();
     } else {
       pre(MG_K_RESTRICT, lev);
-      launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(),
-             (const T*)D.t, Fl(lev + 1), B, P(lev), 0);
+      op_gather(lev, D.t, Fl(lev + 1), 1);
       post();
     }
   }
@@ -508,16 +618,14 @@ struct Issue {
     DevLevel<T>& D = L[lev];
     if (conv(lev, mgk::P_WP2)) {  // P e_c per fine row, then Phi_P and the update
       pre(MG_K_PE, lev);
-      launch(mgk::k_pe<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec, D.t, B);
+      op_pe(lev, ec, D.t);
       post();
       pre(MG_K_PROLONG, lev);
-      launch(mgk::k_prolong_conv<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(),
-             (const T*)D.t, (const T*)u, u, B, P(lev));
+      op_prolong(lev, D.t, u, u, 1);
       post();
     } else {
       pre(MG_K_PROLONG, lev);
-      launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec,
-             (const T*)u, u, B, P(lev), 0);
+      op_prolong(lev, ec, u, u, 0);
       post();
     }
   }
@@ -1263,6 +1371,9 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       break;
     case MG_OPT_PDL:
       c->opt_pdl = value != 0;
+      break;
+    case MG_OPT_MULTI_RHS:
+      c->opt_multi_rhs = value != 0;
       break;
     default:
       return c->fail(MG_ERR_INVALID, "mg_set_option: unknown option");

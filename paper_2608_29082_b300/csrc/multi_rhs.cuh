@@ -1,0 +1,271 @@
+// Multi-right-hand-side forms of the level steps: one thread owns a row i
+// and BV consecutive right-hand sides b0..b0+BV-1 (b0 = blockIdx.y * BV).
+// The row's matrix entries are read once for all BV columns and a
+// neighbour's BV values are fetched as 16-byte vectors (X[n][B] keeps a
+// row's right-hand sides contiguous).  For every (row, rhs) the arithmetic is
+// the sequence of the scalar element functions in kernels.cuh, so results
+// are identical to the one-thread-per-(row, rhs) form.
+#pragma once
+
+#include <cstring>
+
+#include "kernels.cuh"
+
+namespace mgk {
+
+// BV values of row r (offset r * B + b0), vectorised when 16-byte aligned:
+// B * sizeof(T) and b0 * sizeof(T) are multiples of 16 whenever BV * sizeof(T)
+// is (launches use BV | B).
+template <class T, int BV>
+__device__ __forceinline__ void ldv(const T* __restrict__ x, size_t off, T (&out)[BV]) {
+  constexpr int W = 16 / (int)sizeof(T);
+  if constexpr (BV % W == 0) {
+    const uint4* q = reinterpret_cast<const uint4*>(x + off);
+#pragma unroll
+    for (int k = 0; k < BV / W; ++k) {
+      const uint4 w = q[k];
+      memcpy(&out[k * W], &w, 16);
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) out[b] = x[off + b];
+  }
+}
+
+template <class T, int BV>
+__device__ __forceinline__ void stv(T* __restrict__ x, size_t off, const T (&in)[BV]) {
+  constexpr int W = 16 / (int)sizeof(T);
+  if constexpr (BV % W == 0) {
+    uint4* q = reinterpret_cast<uint4*>(x + off);
+#pragma unroll
+    for (int k = 0; k < BV / W; ++k) {
+      uint4 w;
+      memcpy(&w, &in[k * W], 16);
+      q[k] = w;
+    }
+  } else {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) x[off + b] = in[b];
+  }
+}
+
+#define MG_MB_PROLOGUE(NROWS)                                   \
+  pdl_wait();                                                   \
+  pdl_launch();                                                 \
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;          \
+  if (i >= (NROWS)) return;                                     \
+  const int b0 = blockIdx.y * BV;                               \
+  const size_t base = (size_t)i * B + b0;
+
+// sum_{j != i} a_ij x_j for BV columns
+template <class T, int BV>
+__device__ __forceinline__ void row_ax_mb(const LV<T>& L, int i, const T* __restrict__ x, int B,
+                                          int b0, T (&ax)[BV]) {
+#pragma unroll
+  for (int b = 0; b < BV; ++b) ax[b] = T(0);
+  for_nb(L, i, [&](int c, T v, bool) {
+    T xv[BV];
+    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) ax[b] = fma(v, xv[b], ax[b]);
+  });
+}
+
+// sum_{j in N(i)} x_j for BV columns
+template <class T, int BV>
+__device__ __forceinline__ void row_sum_mb(const LV<T>& L, int i, const T* __restrict__ x, int B,
+                                           int b0, T (&s)[BV]) {
+#pragma unroll
+  for (int b = 0; b < BV; ++b) s[b] = T(0);
+  for_nb(L, i, [&](int c, T, bool nb) {
+    T xv[BV];
+    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) s[b] += nb ? xv[b] : T(0);
+  });
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_residual_mb(LV<T> L, const T* __restrict__ f,
+                                                          const T* __restrict__ u,
+                                                          T* __restrict__ out, int B,
+                                                          const T* __restrict__ prm, int scale,
+                                                          int u_zero) {
+  MG_MB_PROLOGUE(L.n)
+  T r[BV];
+  ldv<T, BV>(f, base, r);
+  if (!u_zero) {
+    T ax[BV], uu[BV];
+    row_ax_mb<T, BV>(L, i, u, B, b0, ax);
+    ldv<T, BV>(u, base, uu);
+    const T d = L.diag[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) r[b] = fma(-d, uu[b], r[b]) - ax[b];
+  }
+  if (scale) {
+    const T th = prm[P_THETA], di = L.dinv[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) r[b] = th * (r[b] * di);
+  }
+  stv<T, BV>(out, base, r);
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_conv_update_mb(LV<T> L, const T* __restrict__ x,
+                                                             T* __restrict__ u, int B,
+                                                             const T* __restrict__ prm,
+                                                             int u_zero) {
+  MG_MB_PROLOGUE(L.n)
+  T s[BV], xi[BV], uu[BV];
+  row_sum_mb<T, BV>(L, i, x, B, b0, s);
+  ldv<T, BV>(x, base, xi);
+  if (u_zero) {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) uu[b] = T(0);
+  } else {
+    ldv<T, BV>(u, base, uu);
+  }
+  const T w1 = prm[P_WB1], w2 = prm[P_WB2], eta = prm[P_ETA], id = L.invdeg[i];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) {
+    const T phi = fma(w1, xi[b], w2 * (id * s[b]));
+    uu[b] = fma(eta, phi, uu[b]);
+  }
+  stv<T, BV>(u, base, uu);
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __restrict__ f,
+                                                        const T* __restrict__ uin,
+                                                        T* __restrict__ uout, int B,
+                                                        const T* __restrict__ prm, int u_zero) {
+  MG_MB_PROLOGUE(L.n)
+  T r[BV], u0[BV];
+  ldv<T, BV>(f, base, r);
+  if (u_zero) {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) u0[b] = T(0);
+  } else {
+    T ax[BV];
+    ldv<T, BV>(uin, base, u0);
+    row_ax_mb<T, BV>(L, i, uin, B, b0, ax);
+    const T d = L.diag[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) r[b] = fma(-d, u0[b], r[b]) - ax[b];
+  }
+  const T th = prm[P_THETA], eta = prm[P_ETA], w1 = prm[P_WB1], di = L.dinv[i];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) {
+    const T delta = th * (r[b] * di);
+    r[b] = fma(eta, w1 * delta, u0[b]);
+  }
+  stv<T, BV>(uout, base, r);
+}
+
+// phi_i = wR1 r_i + wR2 mean_{N(i)} r
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_conv_r_mb(LV<T> L, const T* __restrict__ r,
+                                                        T* __restrict__ phi, int B,
+                                                        const T* __restrict__ prm) {
+  MG_MB_PROLOGUE(L.n)
+  T s[BV], ri[BV];
+  row_sum_mb<T, BV>(L, i, r, B, b0, s);
+  ldv<T, BV>(r, base, ri);
+  const T w1 = prm[P_WR1], w2 = prm[P_WR2], id = L.invdeg[i];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) {
+    T p = w1 * ri[b];
+    ri[b] = fma(w2, id * s[b], p);
+  }
+  stv<T, BV>(phi, base, ri);
+}
+
+// fc_I = sum_children P_iI phi_i (coarse rows); scale: phi = w1 * x (plain
+// restriction), else phi = x (after k_conv_r_mb)
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __restrict__ x,
+                                                        T* __restrict__ fc, int B,
+                                                        const T* __restrict__ prm, int scale) {
+  MG_MB_PROLOGUE(L.nc)
+  T acc[BV];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) acc[b] = T(0);
+  const T w1 = prm[P_WR1];
+  for (int k = 0; k < L.KR; ++k) {
+    const int c = L.r_idx[(size_t)k * L.nc + i];
+    if (c < 0) break;
+    const T w = L.r_w[(size_t)k * L.nc + i];
+    T xv[BV];
+    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) acc[b] = fma(w, scale ? w1 * xv[b] : xv[b], acc[b]);
+  }
+  stv<T, BV>(fc, base, acc);
+}
+
+// pe_i = (P ec)_i
+template <class T, int BV>
+__device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __restrict__ ec,
+                                              int B, int b0, T (&v)[BV]) {
+  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) v[b] = T(0);
+  if (a >= 0) {
+    T e[BV];
+    ldv<T, BV>(ec, (size_t)a * B + b0, e);
+    const T w = L.p_w[j];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) v[b] = w * e[b];
+  }
+  if (c >= 0) {
+    T e[BV];
+    ldv<T, BV>(ec, (size_t)c * B + b0, e);
+    const T w = L.p_w[(size_t)L.n + j];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) v[b] = fma(w, e[b], v[b]);
+  }
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_pe_mb(LV<T> L, const T* __restrict__ ec,
+                                                    T* __restrict__ pe, int B) {
+  MG_MB_PROLOGUE(L.n)
+  T v[BV];
+  prolong_at_mb<T, BV>(L, i, ec, B, b0, v);
+  stv<T, BV>(pe, base, v);
+}
+
+// u_i = uin_i + wP1 x_i + wP2 mean_{N(i)} x with x = pe (conv), or
+// u_i = uin_i + wP1 (P ec)_i (plain prolongation: x = ec, conv = 0)
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __restrict__ x,
+                                                         const T* uin, T* u, int B,
+                                                         const T* __restrict__ prm, int conv) {
+  MG_MB_PROLOGUE(L.n)
+  T phi[BV], ui[BV];
+  const T w1 = prm[P_WP1];
+  if (conv) {
+    T s[BV], xi[BV];
+    ldv<T, BV>(x, base, xi);
+    row_sum_mb<T, BV>(L, i, x, B, b0, s);
+    const T w2 = prm[P_WP2], id = L.invdeg[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) {
+      T p = w1 * xi[b];
+      phi[b] = fma(w2, id * s[b], p);
+    }
+  } else {
+    T v[BV];
+    prolong_at_mb<T, BV>(L, i, x, B, b0, v);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) phi[b] = w1 * v[b];
+  }
+  ldv<T, BV>(uin, base, ui);
+#pragma unroll
+  for (int b = 0; b < BV; ++b) ui[b] = ui[b] + phi[b];
+  stv<T, BV>(u, base, ui);
+}
+
+#undef MG_MB_PROLOGUE
+
+}  // namespace mgk

@@ -344,12 +344,15 @@ def test_launch_options_are_bitwise_neutral(prec, conv):
     prm = rand_params(Hp.J, 37, 0.1, conv=conv)
     dt = torch.float64 if prec == 64 else torch.float32
     outs = []
-    for tail, pdl in [(8192, 1), (0, 1), (8192, 0), (1 << 30, 1)]:
-        S = Solver(Hp, prm, precision=prec, max_batch=2)
+    f4 = np.concatenate([p.f, 0.5 * p.f[:, ::-1]], axis=1)  # 4 rhs: multi-rhs tiles of 4
+    for tail, pdl, mrhs in [(8192, 1, 1), (0, 1, 1), (8192, 0, 1), (1 << 30, 1, 1),
+                            (8192, 1, 0), (0, 1, 0)]:
+        S = Solver(Hp, prm, precision=prec, max_batch=4)
         S.set_option("tail_work", tail)
         S.set_option("pdl", pdl)
-        u = torch.zeros((Hp.sizes[0], 2), dtype=dt, device=DEV)
-        f = torch.tensor(p.f, dtype=dt, device=DEV)
+        S.set_option("multi_rhs", mrhs)
+        u = torch.zeros((Hp.sizes[0], 4), dtype=dt, device=DEV)
+        f = torch.tensor(f4, dtype=dt, device=DEV)
         S.vcycle(f, u)
         S.vcycle(f, u)
         us, info = S.solve(t64(p.f), tol=1e-9, max_iter=300)
