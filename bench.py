@@ -20,7 +20,16 @@ import subprocess
 import sys
 import time
 
-import numpy as np
+# The oracle legs (--impl reference, and the cpu_baseline child process) run
+# on one host core: BLAS / OpenMP pools are fixed to one thread before numpy
+# is imported.  Scipy's sparse products are single-threaded anyway.
+ORACLE_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                      "BLIS_NUM_THREADS", "NUMEXPR_NUM_THREADS")
+if "--oracle-leg" in sys.argv or ("--impl" in sys.argv and "reference" in sys.argv):
+    for _v in ORACLE_THREAD_VARS:
+        os.environ[_v] = "1"
+
+import numpy as np  # noqa: E402
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
@@ -45,6 +54,13 @@ def parse():
     ap.add_argument("--params", default=None,
                     help="JSON file of trained parameters (default: the package's trained set)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-lshape", action="store_true",
+                    help="skip the L-shape (3.1M DOF, 16 rhs) bandwidth section")
+    ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive the solve iterations from the host (plain CUDA graphs) so that "
+                         "a profiler that does not trace inside conditional graph nodes sees "
+                         "every kernel; slower, for launch lists only")
     return ap.parse_args()
 
 
@@ -200,6 +216,9 @@ def run_ours(args):
         Str.close()
     S32 = lmg.Solver(hier, learned, precision=32, max_batch=1)
     S64 = lmg.Solver(hier, plain, precision=64, max_batch=1)
+    if args.host_loop:
+        S32.set_option("device_loop", 0)
+        S64.set_option("device_loop", 0)
     f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
     u = torch.zeros_like(f)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
@@ -292,6 +311,11 @@ def run_ours(args):
     shares = sorted(((f"{k[0]}@L{k[1]}", round(v / total, 4)) for k, v in per_cycle.items()),
                     key=lambda kv: -kv[1])[:8]
 
+    # HBM-bound workload: the L-shape level kernels, working set > L2
+    lshape = None
+    if rank == 0 and not args.no_lshape:
+        lshape = lshape_roofline(dev, peak)
+
     # oracle on the host cores, same workload (rank 0 at N=1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -328,14 +352,18 @@ def run_ours(args):
             "speedup_vs_plain_fp64": round(ms64 / ms32, 3),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms/solve",
                     "h2d_bytes_per_step": int(2 * fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)},
-            "gpu_launches": int(nk32 + nk64),
+            "gpu_launches": int(nk32),
+            "gpu_launches_by_region": {"learned_refinement": int(nk32), "plain_fp64": int(nk64),
+                                       "learned_fcg": int(nkfcg)},
             "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": None,
                          "algorithmic_bytes_per_launch": int(nbytes),
                          "avg_launch_us": round(avg_launch_ms * 1e3, 3),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                         "note": "working set fits in L2 (126 MB); see DESIGN.md"},
+                         "note": "latency-bound: the whole FP32 hierarchy (about 30 MB) stays "
+                                 "in L2 during a solve; the HBM-bound case is roofline_lshape"},
+            "roofline_lshape": lshape,
             "kernel_shares_per_vcycle": shares,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -345,22 +373,77 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def lshape_roofline(dev, peak):
+    """The dominant FP32 V-cycle kernel on the jittered anisotropic L-shape
+    (7 red refinements, 3141633 DOF, 16 rhs): per-launch CUDA-event times of
+    the eagerly launched cycle, algorithmic bytes per launch, achieved GB/s."""
+    import torch
+    import paper_2608_29082_b300 as lmg
+    import workloads as W
+    from paper_2608_29082_b300.workload_bench import kernel_table
+    t0 = time.perf_counter()
+    prob = W.lshape_anisotropic(refinements=7, batch=16, seed=0)
+    hier = lmg.Hierarchy.from_problem(prob)
+    p = lmg.LMGParams.identity(hier.J)
+    p.wB[:, 1], p.wR[:, 1], p.wP[:, 1] = 0.1, 0.05, -0.05  # convolutions active on every level
+    S = lmg.Solver(hier, p, precision=32, max_batch=16)
+    f = torch.tensor(prob.f, dtype=torch.float32, device=dev)
+    u = torch.zeros_like(f)
+    for _ in range(3):
+        S.vcycle(f, u)
+    rows, cycle_us = kernel_table(S, hier, f, reps=3)
+    S.close()
+    top = rows[0]
+    hbm = [r for r in rows if r["GBps"] and r["level"] == 0]
+    return {"workload": f"L-shape anisotropic, {hier.sizes[0]} DOF, {hier.J} levels, 16 rhs, "
+                        "FP32 learned cycle",
+            "bound": "hbm", "kernel": f"{top['kernel']}@level{top['level']}",
+            "achieved": top["GBps"], "peak": peak, "unit": "GB/s",
+            "frac": round(top["GBps"] / peak, 4) if top["GBps"] else None,
+            "algorithmic_bytes_per_launch": int(top["algorithmic_MB"] * 1e6),
+            "avg_launch_us": top["us_per_launch"], "share_of_cycle": top["share"],
+            "cycle_us": round(cycle_us, 1),
+            "level0_kernels": [[r["kernel"], r["GBps"], r["frac_of_hbm"]] for r in hbm],
+            "setup_s": round(time.perf_counter() - t0, 1)}
+
+
 def cpu_baseline(prob, params):
     """The FP64 oracle's refinement solve of the same workload with the same
-    (learned) parameters."""
+    (learned) parameters, in a child process on one host core."""
+    import tempfile
+    from paper_2608_29082_b300 import trained
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "params.json")
+        trained.save(params, path)
+        env = dict(os.environ, **{v: "1" for v in ORACLE_THREAD_VARS})
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-leg", path],
+                           capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        return {"value": None, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+                "sample": "oracle leg failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def oracle_leg(path):
+    """Child process of cpu_baseline: one full oracle refinement solve."""
     import oracle as O
+    from paper_2608_29082_b300 import trained
+    prob = make_problem(seed=0)
     t0 = time.perf_counter()
     H = O.build_hierarchy(prob)
     setup = time.perf_counter() - t0
-    p = O.Params(params.theta.copy(), params.eta.copy(), params.wB.copy(), params.wR.copy(),
-                 params.wP.copy(), params.nu_pre, params.nu_post)
+    lp = trained.read(path).with_levels(H.J)
+    p = O.Params(lp.theta.copy(), lp.eta.copy(), lp.wB.copy(), lp.wR.copy(), lp.wP.copy(),
+                 lp.nu_pre, lp.nu_post)
     t0 = time.perf_counter()
     r = O.solve_refinement(H, p, prob.f, TOL, max_iter=MAX_ITER)
     dt = time.perf_counter() - t0
-    return {"value": round(dt * 1e3, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
-            "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, the same "
-                      f"learned parameters) of the same workload; setup {setup:.2f}s excluded; "
-                      "scipy sparse products, single thread"}
+    print(json.dumps({
+        "value": round(dt * 1e3, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
+        "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, the same learned "
+                  f"parameters, final relres {float(r.relres[0]):.2e}) of the same workload; "
+                  f"setup {setup:.2f}s excluded; one thread (BLAS/OpenMP pools set to 1)"}),
+        flush=True)
 
 
 # ---------------------------------------------------------- reference ------
@@ -370,9 +453,14 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle as O
+    from paper_2608_29082_b300 import trained
     prob = make_problem(seed=0)
     H = O.build_hierarchy(prob)
-    p = O.Params.identity(H.J)
+    # the learned parameters the GPU arm solves with (the package's trained
+    # set for this workload), so both arms compute the same iteration
+    lp = trained.load(args.params, H.J)
+    p = O.Params(lp.theta.copy(), lp.eta.copy(), lp.wB.copy(), lp.wR.copy(), lp.wP.copy(),
+                 lp.nu_pre, lp.nu_post)
     times, iters = [], 0
     for k in range(args.warmup + args.steps):
         t0 = time.perf_counter()
@@ -389,7 +477,9 @@ def run_reference(args):
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "nrhs": 1},
            "cpu_baseline": {"value": round(v, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
-                            "sample": f"full FP64 oracle refinement solve ({iters} V-cycles) per step"},
+                            "sample": f"full FP64 oracle refinement solve ({iters} V-cycles, "
+                                      f"learned parameters: {trained.describe(args.params)}) "
+                                      "per step"},
            "e2e": {"value": round(v, 2), "unit": "ms/solve", "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -397,7 +487,9 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.oracle_leg:
+        oracle_leg(a.oracle_leg)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

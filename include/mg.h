@@ -218,13 +218,27 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  * beyond rounding order: every option gives bitwise the same cycle).
  *   MG_OPT_TAIL_WORK  levels with rows * nrhs <= value, and all coarser ones,
  *                     run in one thread block with block barriers instead of
- *                     one grid kernel per step (default 8192; 0 disables)
+ *                     one grid kernel per step (default 2048; 0 disables)
  *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
  *                     dependent launch; 0: plain stream order
- *   MG_OPT_MULTI_RHS  1 (default): with nrhs > 1, one thread owns a row and a
- *                     tile of right-hand sides (matrix read once per row,
- *                     16-byte vector loads); 0: one thread per (row, rhs) */
-typedef enum { MG_OPT_TAIL_WORK = 0, MG_OPT_PDL = 1, MG_OPT_MULTI_RHS = 2 } mg_option;
+ *   MG_OPT_MULTI_RHS  with nrhs > 1, one thread owns a row and a tile of
+ *                     right-hand sides (matrix read once per row, 16-byte
+ *                     vector loads).  1 (default): the widest tile of at
+ *                     most 8 dividing nrhs; 2, 4, 8 or 16 (FP32 only): at most
+ *                     that many right-hand sides per thread; 0: one thread
+ *                     per (row, rhs).  Other values: MG_ERR_INVALID.
+ *   MG_OPT_DEVICE_LOOP 1 (default): mg_solve / mg_solve_fcg run their whole
+ *                     iteration as one CUDA graph with a conditional while
+ *                     node (one host synchronisation per solve); 0: the host
+ *                     replays a plain graph of the same per-iteration kernels
+ *                     and reads the convergence flag after each one (for
+ *                     profilers that do not trace inside conditional nodes) */
+typedef enum {
+  MG_OPT_TAIL_WORK = 0,
+  MG_OPT_PDL = 1,
+  MG_OPT_MULTI_RHS = 2,
+  MG_OPT_DEVICE_LOOP = 3
+} mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);
 

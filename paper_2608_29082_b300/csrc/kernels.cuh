@@ -869,13 +869,15 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ 
 
 // Convergence test per right-hand side; one block.  ctl = (tol, max_iter).
 // state[0] = right-hand sides still active, state[1] = 1 if a residual is not
-// finite, state[2] = iterations done (reset when inc == 0, else +1).  Sets
-// the enclosing while-node's condition: continue while some right-hand side
-// is active, all residuals are finite and fewer than max_iter iterations ran.
+// finite, state[2] = iterations done (reset when inc == 0, else +1),
+// state[3] = continue: some right-hand side is active, all residuals are
+// finite and fewer than max_iter iterations ran.  With set_cond the same
+// value becomes the enclosing while-node's condition (h is ignored otherwise).
 __global__ void k_check(const double* __restrict__ rsum, const double* __restrict__ fsum, int B,
                         const double* __restrict__ ctl, int* __restrict__ active,
                         double* __restrict__ relres, int* __restrict__ sexp,
-                        int* __restrict__ state, int inc, cudaGraphConditionalHandle h) {
+                        int* __restrict__ state, int inc, cudaGraphConditionalHandle h,
+                        int set_cond) {
   pdl_wait();
   __shared__ int cnt, bad;
   const double tol = ctl[0];
@@ -897,7 +899,8 @@ __global__ void k_check(const double* __restrict__ rsum, const double* __restric
     state[1] = bad;
     state[2] = it;
     const int go = cnt > 0 && bad == 0 && (double)it < ctl[1];
-    cudaGraphSetConditional(h, go ? 1u : 0u);
+    state[3] = go;  // read by the host when it drives the loop
+    if (set_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
   }
 }
 

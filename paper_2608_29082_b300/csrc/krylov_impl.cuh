@@ -65,157 +65,98 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
   c->solve_ctl[1] = (double)max_iter;
   MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
 
-  auto key = std::make_tuple(40, (const void*)f, (const void*)u, (int)B, c->structure);
-  auto it = c->graphs.find(key);
-  if (it == c->graphs.end()) {
-    // z = M(r): one V-cycle from zero on the (scaled) residual
-    auto precondition = [&](cudaStream_t cs) {
-      int nk = 0;
-      if (p32) {
-        Issue<double> is0{c, c->d64, c->prm64, cs, B};
-        is0.launch(mgk::k_scale_to_f32, grid_for(N), dim3(kThreads), 0, (const double*)c->k_r,
-                   (const int*)c->sexp, c->rhat32, n0, (int)B);
-        Issue<float> is{c, c->d32, c->prm32, cs, B};
-        is.vcycle(c->rhat32, c->c32, true);
-        is.launch(mgk::k_scale_from_f32, grid_for(N), dim3(kThreads), 0, (const float*)c->c32,
-                  (const int*)c->sexp, c->k_z, n0, (int)B);
-        nk += is0.nk + is.nk;
-      } else {
-        Issue<double> is{c, c->d64, c->prm64, cs, B};
-        is.vcycle(c->k_r, c->k_z, true);
-        nk += is.nk;
-      }
-      return nk;
-    };
-    // q = A p, (p, q), (p, r), alpha
-    auto direction_tail = [&](Issue<double>& is) {
-      is.launch(mgk::k_spmv_dots, rgrid, rblock, 0, L0, (const double*)c->k_p,
-                (const double*)c->k_r, c->k_q, (int)B, c->k_partial);
-      is.launch(mgk::k_reduce, dim3(2 * B), dim3(kThreads), 0, (const double*)c->k_partial, nblk,
-                (int)(2 * B), sums);
-      is.launch(mgk::k_fcg_alpha, dim3(1), dim3(kThreads), 0, (const double*)sums,
-                (const int*)c->active, (int)B, alpha, pq);
-    };
-    cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle h;
-    int nk_init = 0, nk_body = 0;
-    MG_CUDA(cudaGraphCreate(&g, 0));
-    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-    {
-      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
-      is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->fsum);
-      is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B,
-                c->active, c->iters, c->sexp);
-      is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u,
-                c->k_r, (int)B);
-      is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r,
-                (const double*)c->k_r, (const double*)nullptr, (const double*)nullptr, n0, (int)B,
-                c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->rsum);
-      is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-                (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-                c->sexp, c->state, 0, h);
-      nk_init += is.nk;
-      nk_init += precondition(c->cap);
-      Issue<double> is2{c, c->d64, c->prm64, c->cap, B};
-      is2.launch(mgk::k_fcg_direction, grid_for(N), dim3(kThreads), 0, c->k_p,
-                 (const double*)c->k_z, (const double*)zq, (const double*)pq, n0, (int)B, 1);
-      direction_tail(is2);
-      nk_init += is2.nk;
+  // z = M(r): one V-cycle from zero on the (scaled) residual
+  auto precondition = [&](cudaStream_t cs) {
+    int nk = 0;
+    if (p32) {
+      Issue<double> is0{c, c->d64, c->prm64, cs, B};
+      is0.launch(mgk::k_scale_to_f32, grid_for(N), dim3(kThreads), 0, (const double*)c->k_r,
+                 (const int*)c->sexp, c->rhat32, n0, (int)B);
+      Issue<float> is{c, c->d32, c->prm32, cs, B};
+      is.vcycle(c->rhat32, c->c32, true);
+      is.launch(mgk::k_scale_from_f32, grid_for(N), dim3(kThreads), 0, (const float*)c->c32,
+                (const int*)c->sexp, c->k_z, n0, (int)B);
+      nk += is0.nk + is.nk;
+    } else {
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
+      is.vcycle(c->k_r, c->k_z, true);
+      nk += is.nk;
     }
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t capg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    const cudaGraphEdgeData* edges = nullptr;
-    size_t ndeps = 0;
-    cudaGraphNode_t wnode;
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, &edges, &ndeps);
-    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, capg, deps, edges, ndeps, &np);
-    if (e == cudaSuccess)
-      e = cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1,
-                                              cudaStreamSetCaptureDependencies);
-    // after the loop: the true residual of the final iterate
-    if (e == cudaSuccess) {
-      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
-      is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u,
-                c->k_r, (int)B);
-      is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r,
-                (const double*)c->k_r, (const double*)nullptr, (const double*)nullptr, n0, (int)B,
-                c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->rsum);
-      is.launch(k_true_relres, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-                (const double*)c->fsum, (int)B, c->relres);
-      nk_init += is.nk;
-    }
-    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      if (g) cudaGraphDestroy(g);
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve_fcg: graph build: ") +
-                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-    {
-      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
-      is.launch(k_fcg_count, dim3(1), dim3(kThreads), 0, (const int*)c->active, c->iters, (int)B);
-      is.launch(mgk::k_fcg_update, rgrid, rblock, 0, u, c->k_r,
-                (const double*)c->k_p, (const double*)c->k_q, (const double*)alpha,
-                (const int*)c->active, n0, (int)B, c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->rsum);
-      is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-                (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-                c->sexp, c->state, 1, h);
-      nk_body += is.nk;
-      nk_body += precondition(c->cap);
-      Issue<double> is2{c, c->d64, c->prm64, c->cap, B};
-      is2.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_z,
-                 (const double*)c->k_q, (const double*)nullptr, (const double*)nullptr, n0,
-                 (int)B, c->partial);
-      is2.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                 (int)B, zq);
-      is2.launch(mgk::k_fcg_direction, grid_for(N), dim3(kThreads), 0, c->k_p,
-                 (const double*)c->k_z, (const double*)zq, (const double*)pq, n0, (int)B, 0);
-      direction_tail(is2);
-      nk_body += is2.nk;
-    }
-    cudaGraph_t body_out = nullptr;
-    e = cudaGetLastError();
-    e2 = cudaStreamEndCapture(c->cap, &body_out);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve_fcg: body capture: ") +
-                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
-    GraphEntry ge;
-    ge.nkernels = nk_init;
-    ge.nbody = nk_body;
-    e = cudaGraphInstantiate(&ge.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess)
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve_fcg: instantiate: ") + cudaGetErrorString(e));
-    if (c->graphs.size() > 64) {
-      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
-      c->graphs.clear();
-    }
-    it = c->graphs.emplace(key, ge).first;
-  }
-  MG_CUDA(cudaGraphLaunch(it->second.exec, s));
-  MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  MG_CUDA(cudaStreamSynchronize(s));
-  c->launches += it->second.nkernels + (int64_t)c->h_state[2] * it->second.nbody;
+    return nk;
+  };
+  // q = A p, (p, q), (p, r), alpha
+  auto direction_tail = [&](Issue<double>& is) {
+    is.launch(mgk::k_spmv_dots, rgrid, rblock, 0, L0, (const double*)c->k_p,
+              (const double*)c->k_r, c->k_q, (int)B, c->k_partial);
+    is.launch(mgk::k_reduce, dim3(2 * B), dim3(kThreads), 0, (const double*)c->k_partial, nblk,
+              (int)(2 * B), sums);
+    is.launch(mgk::k_fcg_alpha, dim3(1), dim3(kThreads), 0, (const double*)sums,
+              (const int*)c->active, (int)B, alpha, pq);
+  };
+  // ||f||, r = f - A u, the first test, z = M r, p = z and its direction terms
+  auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    int nk = 0;
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->fsum);
+    is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B, c->active,
+              c->iters, c->sexp);
+    is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u, c->k_r, (int)B);
+    is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r, (const double*)c->k_r,
+              (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->rsum);
+    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
+              c->sexp, c->state, 0, h, cond);
+    nk += is.nk;
+    nk += precondition(cs);
+    Issue<double> is2{c, c->d64, c->prm64, cs, B};
+    is2.launch(mgk::k_fcg_direction, grid_for(N), dim3(kThreads), 0, c->k_p, (const double*)c->k_z,
+               (const double*)zq, (const double*)pq, n0, (int)B, 1);
+    direction_tail(is2);
+    return nk + is2.nk;
+  };
+  // u += alpha p, r -= alpha q, the test, z = M r, the new direction
+  auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    int nk = 0;
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(k_fcg_count, dim3(1), dim3(kThreads), 0, (const int*)c->active, c->iters, (int)B);
+    is.launch(mgk::k_fcg_update, rgrid, rblock, 0, u, c->k_r, (const double*)c->k_p,
+              (const double*)c->k_q, (const double*)alpha, (const int*)c->active, n0, (int)B,
+              c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->rsum);
+    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
+              c->sexp, c->state, 1, h, cond);
+    nk += is.nk;
+    nk += precondition(cs);
+    Issue<double> is2{c, c->d64, c->prm64, cs, B};
+    is2.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_z, (const double*)c->k_q,
+               (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
+    is2.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+               zq);
+    is2.launch(mgk::k_fcg_direction, grid_for(N), dim3(kThreads), 0, c->k_p, (const double*)c->k_z,
+               (const double*)zq, (const double*)pq, n0, (int)B, 0);
+    direction_tail(is2);
+    return nk + is2.nk;
+  };
+  // after the loop: the true residual of the final iterate
+  auto post = [&](cudaStream_t cs) {
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u, c->k_r, (int)B);
+    is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r, (const double*)c->k_r,
+              (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->rsum);
+    is.launch(k_true_relres, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, (int)B, c->relres);
+    return is.nk;
+  };
+  st = run_loop(c, 40, f, u, (int)B, s, "mg_solve_fcg", pre, body, post, true);
+  if (st != MG_OK) return st;
   mg_status result = MG_OK;
   if (c->h_state[1])
     result = MG_ERR_DIVERGED;

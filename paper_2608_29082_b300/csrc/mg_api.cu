@@ -284,7 +284,8 @@ struct mg_ctx {
   // options (mg_set_option)
   int64_t opt_tail_work = 2048;  // rows x rhs at or below which levels run in k_tail
   int opt_pdl = 1;               // programmatic dependent launch between kernels
-  int opt_multi_rhs = 1;         // multi-rhs kernels (a row and a tile of rhs per thread)
+  int opt_multi_rhs = 1;         // multi-rhs kernels: 0 off, 1 widest tile, else max tile
+  int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
   int trK = 0, trB = 0, tr_nu_pre = -1, tr_nu_post = -1;
@@ -450,16 +451,22 @@ struct Issue {
   }
 
   // Right-hand sides per thread of the multi-rhs kernels (0: one thread per
-  // (row, rhs)): the widest tile of 16-byte vectors that divides B.
+  // (row, rhs)): the widest tile of at most 8 values that divides B, or of at
+  // most the option's value.  8 is the measured optimum on the 3.1M-row
+  // L-shape with 16 rhs in both precisions: 16 FP32 values per thread cost
+  // occupancy (64 registers), fewer values cost matrix re-reads.
   int mbv() const {
     if (B < 2 || !c->opt_multi_rhs) return 0;
-    const int vmax = sizeof(T) == 4 ? 16 : 8;
+    int vmax = 8;
+    if (c->opt_multi_rhs > 1) vmax = std::min(sizeof(T) == 4 ? 16 : 8, c->opt_multi_rhs);
+    if (c->opt_multi_rhs > 1) vmax = std::min(vmax, c->opt_multi_rhs);
     for (int bv = vmax; bv >= 2; bv >>= 1)
       if (B % bv == 0) return bv;
     return 0;
   }
   dim3 mb_grid(int rows, int bv) const {
-    return dim3((unsigned)((rows + kThreads - 1) / kThreads), (unsigned)(B / bv));
+    const size_t threads = (size_t)rows * (size_t)(B / bv);
+    return dim3((unsigned)((threads + kThreads - 1) / kThreads));
   }
   // Calls fn(std::integral_constant<int, BV>) for the chosen tile width.
   template <class F>
@@ -794,6 +801,104 @@ mg_status run_graph(mg_ctx* c, const std::tuple<int, const void*, const void*, i
   return MG_OK;
 }
 
+// An iterative solve: pre once (it ends with k_check), then body while
+// k_check says continue, then post (when has_post).  Each of pre/body is
+// fn(stream, while-node handle, set_cond) -> kernels issued; post is
+// fn(stream) -> kernels issued.
+//   device loop (default): one graph, the body inside a conditional while
+//     node whose condition k_check sets; one launch and one host sync per solve.
+//   host loop (MG_OPT_DEVICE_LOOP = 0): three plain graphs; the host reads
+//     state[3] after pre and after every body launch.  Same kernels in the
+//     same order with the same arguments, so the same results; a profiler
+//     that cannot see inside conditional nodes sees every kernel.
+// On return state[0..3] is in c->h_state.
+template <class Pre, class Body, class Post>
+mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaStream_t s,
+                   const char* who, Pre&& pre, Body&& body, Post&& post, bool has_post) {
+  if (!c->opt_device_loop) {
+    auto key = [&](int sub) { return std::make_tuple(id + sub, f, u, B, c->structure); };
+    const cudaGraphConditionalHandle h0 = 0;
+    mg_status st = run_graph(c, key(1), s, [&](cudaStream_t cs) { return pre(cs, h0, 0); });
+    for (;;) {
+      if (st != MG_OK) return st;
+      MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      MG_CUDA(cudaStreamSynchronize(s));
+      if (!c->h_state[3]) break;
+      st = run_graph(c, key(2), s, [&](cudaStream_t cs) { return body(cs, h0, 0); });
+    }
+    if (has_post) {
+      st = run_graph(c, key(3), s, [&](cudaStream_t cs) { return post(cs); });
+      if (st != MG_OK) return st;
+      MG_CUDA(cudaStreamSynchronize(s));
+    }
+    return MG_OK;
+  }
+  auto key = std::make_tuple(id, f, u, B, c->structure);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle h;
+    int nk_init = 0, nk_body = 0;
+    MG_CUDA(cudaGraphCreate(&g, 0));
+    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
+    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    nk_init += pre(c->cap, h, 1);
+    cudaStreamCaptureStatus cst;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* edges = nullptr;
+    size_t ndeps = 0;
+    cudaGraphNode_t wnode;
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, &edges, &ndeps);
+    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, capg, deps, edges, ndeps, &np);
+    if (e == cudaSuccess)
+      e = cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1,
+                                              cudaStreamSetCaptureDependencies);
+    if (e == cudaSuccess && has_post) nk_init += post(c->cap);
+    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return c->fail(MG_ERR_CUDA, std::string(who) + ": graph build: " +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    cudaGraph_t bodyg = np.conditional.phGraph_out[0];
+    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, bodyg, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeThreadLocal));
+    nk_body += body(c->cap, h, 1);
+    cudaGraph_t body_out = nullptr;
+    e = cudaGetLastError();
+    e2 = cudaStreamEndCapture(c->cap, &body_out);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      cudaGraphDestroy(g);
+      return c->fail(MG_ERR_CUDA, std::string(who) + ": body capture: " +
+                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    GraphEntry ge;
+    ge.nkernels = nk_init;
+    ge.nbody = nk_body;
+    e = cudaGraphInstantiate(&ge.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess)
+      return c->fail(MG_ERR_CUDA, std::string(who) + ": instantiate: " + cudaGetErrorString(e));
+    if (c->graphs.size() > 64) {
+      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+      c->graphs.clear();
+    }
+    it = c->graphs.emplace(key, ge).first;
+  }
+  MG_CUDA(cudaGraphLaunch(it->second.exec, s));
+  MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
+  c->launches += it->second.nkernels + (int64_t)c->h_state[2] * it->second.nbody;
+  return MG_OK;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ C ABI -------
@@ -1090,76 +1195,41 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
   c->solve_ctl[1] = (double)max_iter;
   MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
 
-  auto key = std::make_tuple(30, (const void*)f, (const void*)u, (int)B, c->structure);
-  auto it = c->graphs.find(key);
-  if (it == c->graphs.end()) {
-    // residual of the current iterate, its norms and the convergence test;
-    // the test sets the while-node condition
-    auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc) {
-      is.launch(mgk::k_resid64, rgrid, rblock, 0, L0, (const double*)f,
-                (const double*)u, p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B,
-                c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->rsum);
-      if (p32) is.launch(k_shift_sexp, dim3(1), dim3(kThreads), 0, c->sexp, c->sexp_prev, (int)B);
-      is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-                (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-                c->sexp, c->state, inc, h);
-    };
-    cudaGraph_t g = nullptr;
-    cudaGraphConditionalHandle h;
-    int nk_init = 0, nk_body = 0;
-    MG_CUDA(cudaGraphCreate(&g, 0));
-    MG_CUDA(cudaGraphConditionalHandleCreate(&h, g, 0, 0));
-    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, g, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
-    {
-      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
-      is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
-      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                (int)B, c->fsum);
-      is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B,
-                c->active, c->iters, c->sexp);
-      check_tail(is, h, 0);
-      nk_init = is.nk;
-    }
-    cudaStreamCaptureStatus cst;
-    cudaGraph_t capg = nullptr;
-    const cudaGraphNode_t* deps = nullptr;
-    const cudaGraphEdgeData* edges = nullptr;
-    size_t ndeps = 0;
-    cudaGraphNode_t wnode;
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = h;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, &edges, &ndeps);
-    if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, capg, deps, edges, ndeps, &np);
-    if (e == cudaSuccess)
-      e = cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1,
-                                              cudaStreamSetCaptureDependencies);
-    cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve: graph build: ") +
-                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
-    cudaGraph_t body = np.conditional.phGraph_out[0];
-    MG_CUDA(cudaStreamBeginCaptureToGraph(c->cap, body, nullptr, nullptr, 0,
-                                          cudaStreamCaptureModeThreadLocal));
+  // residual of the current iterate, its norms and the convergence test
+  auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
+    is.launch(mgk::k_resid64, rgrid, rblock, 0, L0, (const double*)f, (const double*)u,
+              p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->rsum);
+    if (p32) is.launch(k_shift_sexp, dim3(1), dim3(kThreads), 0, c->sexp, c->sexp_prev, (int)B);
+    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
+              c->sexp, c->state, inc, h, cond);
+  };
+  auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->fsum);
+    is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B, c->active,
+              c->iters, c->sexp);
+    check_tail(is, h, 0, cond);
+    return is.nk;
+  };
+  auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    int nk = 0;
     if (p32) {
-      Issue<float> is{c, c->d32, c->prm32, c->cap, B};
+      Issue<float> is{c, c->d32, c->prm32, cs, B};
       is.vcycle(c->rhat32, c->c32, true);
       is.launch(mgk::k_refine_update, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
-                (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0,
-                (int)B, c->iters);
-      nk_body += is.nk;
-      Issue<double> is2{c, c->d64, c->prm64, c->cap, B};
-      check_tail(is2, h, 1);
-      nk_body += is2.nk;
+                (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0, (int)B,
+                c->iters);
+      nk += is.nk;
+      Issue<double> is2{c, c->d64, c->prm64, cs, B};
+      check_tail(is2, h, 1, cond);
+      nk += is2.nk;
     } else {
-      Issue<double> is{c, c->d64, c->prm64, c->cap, B};
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
       if (B == 1) {
         is.vcycle(f, u, false);
         is.launch(k_bump_iters, dim3(1), dim3(kThreads), 0, (const int*)c->active, c->iters,
@@ -1171,35 +1241,14 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
         is.launch(mgk::k_masked_copy, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
                   (const double*)c->w64, (const int*)c->active, n0, (int)B, c->iters);
       }
-      check_tail(is, h, 1);
-      nk_body += is.nk;
+      check_tail(is, h, 1, cond);
+      nk += is.nk;
     }
-    cudaGraph_t body_out = nullptr;
-    e = cudaGetLastError();
-    e2 = cudaStreamEndCapture(c->cap, &body_out);
-    if (e != cudaSuccess || e2 != cudaSuccess) {
-      cudaGraphDestroy(g);
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve: body capture: ") +
-                                      cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
-    GraphEntry ge;
-    ge.nkernels = nk_init;
-    ge.nbody = nk_body;
-    e = cudaGraphInstantiate(&ge.exec, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess)
-      return c->fail(MG_ERR_CUDA, std::string("mg_solve: instantiate: ") + cudaGetErrorString(e));
-    if (c->graphs.size() > 64) {
-      for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
-      c->graphs.clear();
-    }
-    it = c->graphs.emplace(key, ge).first;
-  }
-  MG_CUDA(cudaGraphLaunch(it->second.exec, s));
-  MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  MG_CUDA(cudaStreamSynchronize(s));
-  const int iters_done = c->h_state[2];
-  c->launches += it->second.nkernels + (int64_t)iters_done * it->second.nbody;
+    return nk;
+  };
+  st = run_loop(c, 30, f, u, (int)B, s, "mg_solve", pre, body,
+                [](cudaStream_t) { return 0; }, false);
+  if (st != MG_OK) return st;
   mg_status result = MG_OK;
   if (c->h_state[1])
     result = MG_ERR_DIVERGED;
@@ -1373,7 +1422,12 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       c->opt_pdl = value != 0;
       break;
     case MG_OPT_MULTI_RHS:
-      c->opt_multi_rhs = value != 0;
+      if (value != 0 && value != 1 && value != 2 && value != 4 && value != 8 && value != 16)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: multi-rhs tile must be 0, 1, 2, 4, 8 or 16");
+      c->opt_multi_rhs = (int)value;
+      break;
+    case MG_OPT_DEVICE_LOOP:
+      c->opt_device_loop = value != 0;
       break;
     default:
       return c->fail(MG_ERR_INVALID, "mg_set_option: unknown option");

@@ -1,10 +1,11 @@
 // Multi-right-hand-side forms of the level steps: one thread owns a row i
-// and BV consecutive right-hand sides b0..b0+BV-1 (b0 = blockIdx.y * BV).
-// The row's matrix entries are read once for all BV columns and a
-// neighbour's BV values are fetched as 16-byte vectors (X[n][B] keeps a
-// row's right-hand sides contiguous).  For every (row, rhs) the arithmetic is
-// the sequence of the scalar element functions in kernels.cuh, so results
-// are identical to the one-thread-per-(row, rhs) form.
+// and BV consecutive right-hand sides b0..b0+BV-1.  The B / BV threads of a
+// row are adjacent lanes (b0 = (thread % (B / BV)) * BV), so a warp's 16-byte
+// loads of a neighbour's values cover whole contiguous runs of X[n][B]
+// rather than one piece of each of 32 rows.  The row's matrix entries are
+// read once per BV columns.  For every (row, rhs) the arithmetic is the
+// sequence of the scalar element functions in kernels.cuh, so results are
+// identical to the one-thread-per-(row, rhs) form.
 #pragma once
 
 #include <cstring>
@@ -49,12 +50,15 @@ __device__ __forceinline__ void stv(T* __restrict__ x, size_t off, const T (&in)
   }
 }
 
+// Launch: 1-D grid of ceil(NROWS * (B / BV) / kThreads) blocks.
 #define MG_MB_PROLOGUE(NROWS)                                   \
   pdl_wait();                                                   \
   pdl_launch();                                                 \
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;          \
+  const int nq = B / BV;                                        \
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;          \
+  const int i = g / nq;                                         \
   if (i >= (NROWS)) return;                                     \
-  const int b0 = blockIdx.y * BV;                               \
+  const int b0 = (g - i * nq) * BV;                             \
   const size_t base = (size_t)i * B + b0;
 
 // sum_{j != i} a_ij x_j for BV columns

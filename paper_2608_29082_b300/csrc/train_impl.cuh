@@ -219,7 +219,7 @@ mg_status forward_record(mg_ctx* c, const T* f, T* u, int B, int K, cudaStream_t
       fo[k][l] = (T*)c->ck_f[k][l];
       uo[k][l] = (T*)c->ck_e[k][l];
     }
-  auto key = std::make_tuple(20 + K, (const void*)f, (const void*)u, B, c->structure);
+  auto key = std::make_tuple(1000 + K, (const void*)f, (const void*)u, B, c->structure);
   st = run_graph(c, key, s, [&](cudaStream_t cs) {
     Issue<T> is{c, levels_of<T>(c), prm_of<T>(c), cs, B};
     for (int k = 0; k < K; ++k) {

@@ -203,7 +203,8 @@ class Solver:
                 for k in range(n.value)]
 
     def set_option(self, name: str, value: int):
-        """Launch-shape options ("tail_work", "pdl"); results are unchanged."""
+        """Launch-shape options ("tail_work", "pdl", "multi_rhs", "device_loop"); results are
+        bitwise unchanged."""
         L.check(self.lib.mg_set_option(self.ctx, L.OPTIONS[name], int(value)), self.ctx)
 
     # ------------------------------------------------------------ training

@@ -118,6 +118,21 @@ def run_lshape(a):
     dev = torch.device("cuda")
     plain = LMGParams.identity(J)
     learned, training = plain, None
+    if a.cycles_only:
+        # a few FP32 cycles with convolutions on every level (profiling target)
+        p = LMGParams.identity(J)
+        p.wB[:, 1], p.wR[:, 1], p.wP[:, 1] = 0.1, 0.05, -0.05
+        S = Solver(hier, p, precision=32, max_batch=a.batch)
+        f = torch.tensor(prob.f, dtype=torch.float32, device=dev)
+        u = torch.zeros_like(f)
+        for _ in range(a.cycles_only):
+            S.vcycle(f, u)
+        kt, cyc = kernel_table(S, hier, f, reps=1)
+        torch.cuda.synchronize()
+        print(json.dumps({"workload": f"L-shape r{a.refinements}, {hier.sizes[0]} DOF, "
+                          f"{a.batch} rhs", "cycle_us_profiled": round(cyc, 1),
+                          "kernels_fp32": kt[:6]}), flush=True)
+        return
     if a.train_epochs > 0:
         ftr = torch.tensor(fields.rhs(hier.sizes[0], a.train_batch, 1000 + a.seed),
                            dtype=torch.float32, device=dev)
@@ -206,6 +221,8 @@ if __name__ == "__main__":
     l.add_argument("--K", type=int, default=10)
     l.add_argument("--preset", default="shared_conv")
     l.add_argument("--seed", type=int, default=0)
+    l.add_argument("--cycles-only", type=int, default=0,
+                   help="only run this many FP32 cycles and the per-kernel table")
     t = sub.add_parser("training")
     t.add_argument("--kind", default="checker")
     t.add_argument("--batch", type=int, default=64)

@@ -365,6 +365,63 @@ def test_launch_options_are_bitwise_neutral(prec, conv):
 
 
 @pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("method", ["refine", "fcg"])
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_host_driven_loop_matches_device_loop(prec, method, nrhs):
+    """A solve whose iterations the host drives (plain graphs, the flag read
+    after every iteration) is bitwise the solve whose loop is a device while
+    node: same iterate, iteration counts and residuals."""
+    p, Ho, Hp = problem("checker65")
+    prm = rand_params(Hp.J, 67, 0.1)
+    f = t64(np.random.default_rng(8).standard_normal((Hp.sizes[0], nrhs)))
+    res = []
+    for loop in (1, 0):
+        S = Solver(Hp, prm, precision=prec, max_batch=nrhs)
+        S.set_option("device_loop", loop)
+        u, info = S.solve(f, tol=1e-9, max_iter=300, method=method)
+        n0 = S.kernel_launches()
+        u2, info2 = S.solve(f, tol=1e-9, max_iter=300, method=method)
+        res.append((u.clone(), info.iters.copy(), info.relres.copy(), S.kernel_launches() - n0))
+        assert torch.equal(u, u2)
+        S.close()
+    (ua, ia, ra, ka), (ub, ib, rb, kb) = res
+    assert torch.equal(ua, ub)
+    assert np.array_equal(ia, ib) and np.array_equal(ra, rb)
+    assert ia.max() > 1 and (ra < 1e-9).all()
+    assert ka == kb  # both forms count the same kernels
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("nrhs", [12, 16])
+def test_multi_rhs_tiles_are_bitwise_neutral(prec, nrhs):
+    """Every right-hand-side tile width (several adjacent lanes per row, a
+    non-power-of-two lane count for 12 rhs) gives the one-thread-per-(row,
+    rhs) cycle bitwise, on a SELL level (L-shape) and on DIA levels."""
+    from paper_2608_29082_b300._lib import MGError
+    for name in ("lshape_r2", "checker65"):
+        p, Ho, Hp = problem(name)
+        prm = rand_params(Hp.J, 61, 0.1, conv=True)
+        dt = torch.float64 if prec == 64 else torch.float32
+        f = torch.tensor(np.random.default_rng(5).standard_normal((Hp.sizes[0], nrhs)),
+                         dtype=dt, device=DEV)
+        S = Solver(Hp, prm, precision=prec, max_batch=nrhs)
+        S.set_option("tail_work", 0)
+        outs = []
+        for tile in (0, 1, 2, 4, 8, 16):
+            S.set_option("multi_rhs", tile)
+            u = torch.zeros_like(f)
+            S.vcycle(f, u)
+            S.vcycle(f, u)
+            outs.append(u.clone())
+        with pytest.raises(MGError):
+            S.set_option("multi_rhs", 3)
+        S.close()
+        assert torch.isfinite(outs[0]).all()
+        for u in outs[1:]:
+            assert torch.equal(u, outs[0])
+
+
+@pytest.mark.parametrize("prec", [64, 32])
 def test_dia_and_sell_layouts_agree_bitwise(prec):
     """Structured levels are stored as DIA by default; forcing SELL-32 must
     give bitwise the same cycle, solve and parameter gradient."""
