@@ -151,6 +151,12 @@ def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
         return nnzP * (4 + b) + B * nc * b + B * n * b
     if name == "prolong_conv":         # u += Phi_P(P e_c)
         return nnz_off * (col_b or b) + n * b + 3 * B * n * b
+    if name == "smooth_halo":          # delta and u += eta Phi_B(delta), u_in -> u_out
+        return nnz_off * (col_b + b) + 3 * n * b + 3 * B * n * b
+    if name == "restrict_conv_halo":   # r and Phi_R(r) per fine row
+        return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
+    if name == "prolong_halo":         # P e_c, Phi_P and u += per fine row
+        return nnzP * (4 + b) + nnz_off * (col_b or b) + n * b + B * nc * b + 2 * B * n * b
     if name == "coarse_cholesky":
         return 2 * n * n * 8 + 2 * B * n * b
     if name == "outer_residual_fp64":
@@ -164,6 +170,15 @@ def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
             tot += kernel_bytes("prolong_conv", l, hier, B, b)
         return tot + kernel_bytes("coarse_cholesky", hier.J - 1, hier, B, b)
     raise KeyError(name)
+
+
+def max_over_ranks(values, pg, device):
+    """Element-wise maximum of per-rank timings (replicas: the job takes as
+    long as its slowest rank)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return t.tolist()
 
 
 def dist_env():
@@ -256,9 +271,7 @@ def run_ours(args):
     msfcg, infofcg, nkfcg = timed(S32, method="fcg")
     # max over ranks
     if pg:
-        t = torch.tensor([ms32, ms64], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms32, ms64 = t.tolist()
+        ms32, ms64, msfcg = max_over_ranks([ms32, ms64, msfcg], pg, dev)
 
     # end to end through the public host API (pinned host buffers)
     fh = torch.tensor(prob.f, dtype=torch.float64).pin_memory().numpy()

@@ -232,12 +232,23 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     node (one host synchronisation per solve); 0: the host
  *                     replays a plain graph of the same per-iteration kernels
  *                     and reads the convergence flag after each one (for
- *                     profilers that do not trace inside conditional nodes) */
+ *                     profilers that do not trace inside conditional nodes)
+ *   MG_OPT_HALO_ROWS  rows per thread block of the halo-fused steps on DIA
+ *                     levels (default 256; 0: unfused): each block evaluates
+ *                     a step's first stage (delta, r or P e_c) on its rows
+ *                     plus H = max|offset| halo rows on each side in shared
+ *                     memory and applies the SAGEConv mean from there, one
+ *                     kernel instead of two.  Used on a level when the tile
+ *                     is at least H rows, tile plus halos fit in 48 KB for
+ *                     the batch, and the first stage over all tiles fits in
+ *                     one wave of the GPU; otherwise the two-kernel form.
+ *                     Other values than [0, 2^30]: MG_ERR_INVALID. */
 typedef enum {
   MG_OPT_TAIL_WORK = 0,
   MG_OPT_PDL = 1,
   MG_OPT_MULTI_RHS = 2,
-  MG_OPT_DEVICE_LOOP = 3
+  MG_OPT_DEVICE_LOOP = 3,
+  MG_OPT_HALO_ROWS = 4
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);
@@ -254,7 +265,10 @@ typedef enum {
   MG_K_OUTER_RESIDUAL = 7,  /* FP64 refinement residual                        */
   MG_K_TAIL = 8,            /* all small levels of a cycle in one thread block */
   MG_K_CONV_R = 9,          /* Phi_R(r) per fine row (then MG_K_RESTRICT gathers) */
-  MG_K_PE = 10              /* P e_c per fine row (then MG_K_PROLONG applies Phi_P) */
+  MG_K_PE = 10,             /* P e_c per fine row (then MG_K_PROLONG applies Phi_P) */
+  MG_K_SMOOTH_HALO = 11,    /* smoothing step, both stages in one halo-tiled kernel */
+  MG_K_RESTRICT_HALO = 12,  /* r and Phi_R(r) in one halo-tiled kernel            */
+  MG_K_PROLONG_HALO = 13    /* u += Phi_P(P e_c) in one halo-tiled kernel         */
 } mg_kernel_kind;
 
 typedef struct {

@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "adjoint.cuh"
+#include "halo.cuh"
 #include "kernels.cuh"
 #include "krylov.cuh"
 #include "multi_rhs.cuh"
@@ -286,6 +287,8 @@ struct mg_ctx {
   int opt_pdl = 1;               // programmatic dependent launch between kernels
   int opt_multi_rhs = 1;         // multi-rhs kernels: 0 off, 1 widest tile, else max tile
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
+  int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
+  int64_t wave_threads = 148 * 2048;  // SMs x resident threads per SM (set in mg_setup)
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
   int trK = 0, trB = 0, tr_nu_pre = -1, tr_nu_post = -1;
@@ -401,6 +404,8 @@ inline dim3 grid_for(size_t work) { return dim3((unsigned)((work + kThreads - 1)
 
 // Dynamic shared memory the small-level block may use (of 227 KB per block).
 constexpr size_t kTailSmemMax = 200 * 1024;
+// Shared memory of a halo-fused block (default limit, no opt-in needed).
+constexpr size_t kHaloSmemMax = 48 * 1024;
 
 // Issues the kernels of one V-cycle (or one level step) on a stream.
 template <class T>
@@ -571,6 +576,44 @@ struct Issue {
   }
 
   // nu smoothing steps on level lev; u updated in place.  zero: u is 0 on entry.
+  // Halo-fused steps (halo.cuh) on a DIA level: rows per block TR and halo
+  // H, or 0 (two-kernel form) when the level is SELL or the option is off;
+  // when a tile would be narrower than its halo (each block redoing more
+  // than 3x its rows); when the tile does not fit kHaloSmemMax for B
+  // right-hand sides; or when the first stage over all tiles and halos
+  // exceeds one wave of the GPU.  Past that point the level fills the GPU
+  // and the redundant halo work costs more than the kernel boundary it
+  // saves (measured: the 511^2-row level of the 513^2 mesh runs faster
+  // unfused, its coarser levels fused).
+  int halo_rows(int lev, int& H, size_t& smem, int& threads) const {
+    const DevLevel<T>& D = L[lev];
+    if (c->opt_halo_rows <= 0 || D.ndia == 0) return 0;
+    H = 0;
+    for (int k = 0; k < D.ndia; ++k) H = std::max(H, std::abs(D.doff[k]));
+    const size_t per_row = (size_t)B * sizeof(T);
+    const int64_t cap_rows = (int64_t)(kHaloSmemMax / per_row);
+    int64_t tr = std::min<int64_t>(c->opt_halo_rows, cap_rows - 2 * (int64_t)H);
+    if (tr >= D.n) {
+      tr = D.n;  // one block, no halo
+    } else if (tr < std::max<int64_t>(H, 1)) {
+      return 0;
+    }
+    const int64_t span = std::min<int64_t>(tr + 2 * (int64_t)H, D.n);
+    if (span > cap_rows) return 0;
+    const int64_t nblk = (D.n + tr - 1) / tr;
+    if (nblk * span * B > c->wave_threads) return 0;
+    smem = (size_t)span * per_row;
+    threads = (int)std::min<int64_t>(mgk::kTailThreads, (span * B + 31) / 32 * 32);
+    return (int)tr;
+  }
+  template <int MODE>
+  void op_halo(int lev, int TR, int H, size_t smem, int threads, const T* f, const T* x, T* y,
+               int zero) {
+    DevLevel<T>& D = L[lev];
+    launch(mgk::k_halo_dia<T, MODE>, dim3((unsigned)((D.n + TR - 1) / TR)), dim3(threads), smem,
+           D.view(), f, x, y, B, P(lev), TR, H, zero);
+  }
+
   void smooth(int lev, const T* f, T* u, int nu, bool zero) {
     DevLevel<T>& D = L[lev];
     const size_t N = (size_t)D.n * B;
@@ -591,6 +634,20 @@ struct Issue {
       if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
       return;
     }
+    int H = 0, nth = 0;
+    size_t smem = 0;
+    if (const int TR = halo_rows(lev, H, smem, nth)) {  // one fused kernel per step
+      T* cur = u;
+      T* oth = D.u2;
+      for (int k = 0; k < nu; ++k) {
+        pre(MG_K_SMOOTH_HALO, lev);
+        op_halo<mgk::HALO_SMOOTH>(lev, TR, H, smem, nth, f, cur, oth, (int)(zero && k == 0));
+        post();
+        std::swap(cur, oth);
+      }
+      if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
+      return;
+    }
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       pre(MG_K_RESIDUAL_SCALED, lev);
@@ -604,6 +661,18 @@ struct Issue {
 
   void restrict_(int lev, const T* f, const T* u) {
     DevLevel<T>& D = L[lev];
+    int H = 0, nth = 0;
+    size_t smem = 0;
+    const int TR = conv(lev, mgk::P_WR2) ? halo_rows(lev, H, smem, nth) : 0;
+    if (TR) {  // residual and Phi_R in one kernel, then the gather P^T
+      pre(MG_K_RESTRICT_HALO, lev);
+      op_halo<mgk::HALO_RESTRICT>(lev, TR, H, smem, nth, f, u, D.u2, 0);
+      post();
+      pre(MG_K_RESTRICT, lev);
+      op_gather(lev, D.u2, Fl(lev + 1), 0);
+      post();
+      return;
+    }
     pre(MG_K_RESIDUAL, lev);
     op_residual(lev, f, u, D.t, 0, 0);
     post();
@@ -623,6 +692,15 @@ struct Issue {
 
   void prolong(int lev, const T* ec, T* u) {
     DevLevel<T>& D = L[lev];
+    int H = 0, nth = 0;
+    size_t smem = 0;
+    const int TR = conv(lev, mgk::P_WP2) ? halo_rows(lev, H, smem, nth) : 0;
+    if (TR) {  // P e_c, Phi_P and the update in one kernel
+      pre(MG_K_PROLONG_HALO, lev);
+      op_halo<mgk::HALO_PROLONG>(lev, TR, H, smem, nth, (const T*)nullptr, ec, u, 0);
+      post();
+      return;
+    }
     if (conv(lev, mgk::P_WP2)) {  // P e_c per fine row, then Phi_P and the update
       pre(MG_K_PE, lev);
       op_pe(lev, ec, D.t);
@@ -1004,6 +1082,14 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   c->J = J;
   c->prec = precision;
   c->maxB = maxB;
+  {
+    int dev = 0, sms = 0, tpm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&tpm, cudaDevAttrMaxThreadsPerMultiProcessor, dev) == cudaSuccess &&
+        sms > 0 && tpm > 0)
+      c->wave_threads = (int64_t)sms * tpm;
+  }
   why = read_params(p, J, c->prm, c->nu_pre, c->nu_post);
   if (!why.empty()) {
     delete c;
@@ -1364,6 +1450,9 @@ extern "C" const char* mg_kernel_name(int32_t kind) {
     case MG_K_TAIL: return "small_levels_block";
     case MG_K_CONV_R: return "restrict_conv_fine";
     case MG_K_PE: return "prolong_fine";
+    case MG_K_SMOOTH_HALO: return "smooth_halo";
+    case MG_K_RESTRICT_HALO: return "restrict_conv_halo";
+    case MG_K_PROLONG_HALO: return "prolong_halo";
     default: return "unknown";
   }
 }
@@ -1428,6 +1517,11 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       break;
     case MG_OPT_DEVICE_LOOP:
       c->opt_device_loop = value != 0;
+      break;
+    case MG_OPT_HALO_ROWS:
+      if (value < 0 || value > (1 << 30))
+        return c->fail(MG_ERR_INVALID, "mg_set_option: halo rows must be in [0, 2^30]");
+      c->opt_halo_rows = value;
       break;
     default:
       return c->fail(MG_ERR_INVALID, "mg_set_option: unknown option");

@@ -59,6 +59,10 @@ def level_bytes(name: str, hier, lev: int, B: int, b: int) -> float:
         "prolong_fine": nnzP * (4 + b) + B * nc * b + B * n * b,
         "prolong_conv": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
         "outer_residual_fp64": nnz_off * (col_b + 8) + 2 * n * 8 + B * n * 24,
+        "smooth_halo": nnz_off * (col_b + b) + 3 * n * b + 3 * B * n * b,
+        "restrict_conv_halo": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
+        "prolong_halo": nnzP * (4 + b) + nnz_off * (col_b or b) + n * b + B * nc * b
+                        + 2 * B * n * b,
     }
     return table.get(name, float("nan"))
 

@@ -337,21 +337,28 @@ def test_packed_coarse_solve_matches_cholesky():
 
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("conv", [False, True])
-def test_launch_options_are_bitwise_neutral(prec, conv):
-    """The single-block small-level kernel and programmatic dependent launch
-    change launch shapes only: the cycle and the solve are bitwise identical."""
+@pytest.mark.parametrize("nrhs", [1, 4])
+def test_launch_options_are_bitwise_neutral(prec, conv, nrhs):
+    """The single-block small-level kernel, programmatic dependent launch, the
+    multi-rhs tiles and the halo-fused DIA steps (tiles of many blocks, a tile
+    narrower than the finest level's halo that falls back there, one block per
+    level) change launch
+    shapes only: the cycle and the solve are bitwise identical."""
     p, Ho, Hp = problem("checker65")
     prm = rand_params(Hp.J, 37, 0.1, conv=conv)
     dt = torch.float64 if prec == 64 else torch.float32
     outs = []
-    f4 = np.concatenate([p.f, 0.5 * p.f[:, ::-1]], axis=1)  # 4 rhs: multi-rhs tiles of 4
-    for tail, pdl, mrhs in [(8192, 1, 1), (0, 1, 1), (8192, 0, 1), (1 << 30, 1, 1),
-                            (8192, 1, 0), (0, 1, 0)]:
+    f4 = np.concatenate([p.f, 0.5 * p.f[:, ::-1]], axis=1)[:, :nrhs]
+    for tail, pdl, mrhs, halo in [(8192, 1, 1, 2048), (0, 1, 1, 2048), (8192, 0, 1, 2048),
+                                  (1 << 30, 1, 1, 2048), (8192, 1, 0, 2048), (0, 1, 0, 2048),
+                                  (8192, 1, 1, 0), (0, 1, 1, 256), (0, 1, 0, 50),
+                                  (0, 0, 1, 1 << 20)]:
         S = Solver(Hp, prm, precision=prec, max_batch=4)
         S.set_option("tail_work", tail)
         S.set_option("pdl", pdl)
         S.set_option("multi_rhs", mrhs)
-        u = torch.zeros((Hp.sizes[0], 4), dtype=dt, device=DEV)
+        S.set_option("halo_rows", halo)
+        u = torch.zeros((Hp.sizes[0], nrhs), dtype=dt, device=DEV)
         f = torch.tensor(f4, dtype=dt, device=DEV)
         S.vcycle(f, u)
         S.vcycle(f, u)
