@@ -34,8 +34,6 @@ template <class T, int MODE>
 __global__ void __launch_bounds__(kTailThreads)
     k_halo_dia(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B,
                const T* __restrict__ prm, int TR, int H, int zero) {
-  pdl_wait();
-  pdl_launch();
   extern __shared__ __align__(16) unsigned char halo_raw[];
   T* sz = reinterpret_cast<T*>(halo_raw);
   const int r0 = blockIdx.x * TR;
@@ -43,6 +41,13 @@ __global__ void __launch_bounds__(kTailThreads)
   const int lo = max(r0 - H, 0), hi = min(r1 + H, L.n);
   const size_t base = (size_t)lo * B;
   const size_t nz = (size_t)(hi - lo) * B;
+  // read-only operator rows of the tile before waiting for the predecessor
+  for (int j = lo + (int)threadIdx.x; j < hi; j += blockDim.x) {
+    if constexpr (MODE == HALO_PROLONG) prefetch_p(L, j);
+    prefetch_row(L, j);
+  }
+  pdl_wait();
+  pdl_launch();
 
   // first stage on own rows and halo
   for (size_t e = threadIdx.x; e < nz; e += blockDim.x) {

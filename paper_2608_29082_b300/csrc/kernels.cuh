@@ -85,6 +85,53 @@ __device__ __forceinline__ int slice_begin(const int* sl_ptr, int i) {
   return sl_ptr[i >> 5] + (i & 31);
 }
 
+// Read-only operator data is fetched towards L1 before griddepcontrol.wait:
+// it never depends on the preceding kernel (only vectors do), so its latency
+// overlaps that kernel's drain.  These are hints; the values are loaded
+// again where they are used.
+__device__ __forceinline__ void prefetch_l1(const void* p) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
+// Row i's off-diagonals (DIA values, or the SELL slice pointer), diagonal,
+// its inverse and 1/deg.
+template <class T>
+__device__ __forceinline__ void prefetch_row(const LV<T>& L, int i) {
+  if (L.ndia > 0) {
+#pragma unroll
+    for (int k = 0; k < kMaxDia; ++k)
+      if (k < L.ndia) prefetch_l1(L.dval + (size_t)k * L.n + i);
+  } else {
+    prefetch_l1(L.sl_ptr + (i >> 5));
+  }
+  prefetch_l1(L.diag + i);
+  prefetch_l1(L.dinv + i);
+  prefetch_l1(L.invdeg + i);
+}
+
+// Fine row i's prolongation entries.
+template <class T>
+__device__ __forceinline__ void prefetch_p(const LV<T>& L, int i) {
+  prefetch_l1(L.p_idx + i);
+  prefetch_l1(L.p_idx + (size_t)L.n + i);
+  prefetch_l1(L.p_w + i);
+  prefetch_l1(L.p_w + (size_t)L.n + i);
+}
+
+// Coarse row I's restriction gather list.
+template <class T>
+__device__ __forceinline__ void prefetch_r(const LV<T>& L, int I) {
+  for (int k = 0; k < L.KR && k < kMaxKR; ++k) {
+    prefetch_l1(L.r_idx + (size_t)k * L.nc + I);
+    prefetch_l1(L.r_w + (size_t)k * L.nc + I);
+  }
+}
+
+// Row of flat index t into X[n][B].
+__device__ __forceinline__ int row_of(size_t t, int B) {
+  return B == 1 ? (int)t : (int)((unsigned)t / (unsigned)B);
+}
+
 // Calls fn(c, a_ic, is_neighbour) for the off-diagonals of row i in ascending
 // column order.  DIA: every diagonal is visited; absent entries have a_ic = 0,
 // is_neighbour = false and a clamped in-range c, so the value and the
@@ -353,18 +400,21 @@ __device__ __forceinline__ void coarse_chol_block(const double* __restrict__ Lc,
 
 // ------------------------------------------------------- grid kernels ----
 
-#define MG_GRID_PROLOGUE(N)                                                 \
-  pdl_wait();                                                               \
-  pdl_launch();                                                             \
+// PF: prefetch statement for the thread's row (read-only data only), run
+// before griddepcontrol.wait.
+#define MG_GRID_PROLOGUE(N, PF)                                             \
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;           \
-  const bool in_range = t < (size_t)(N);
+  const bool in_range = t < (size_t)(N);                                    \
+  if (in_range) { PF; }                                                     \
+  pdl_wait();                                                               \
+  pdl_launch();
 
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restrict__ f,
                                                        const T* __restrict__ u, T* __restrict__ out,
                                                        int B, const T* __restrict__ prm, int scale,
                                                        int u_zero) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) residual_el(L, f, u, out, B, prm, scale, u_zero, t);
   pdl_launch();
 }
@@ -373,7 +423,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
                                                           T* __restrict__ u, int B,
                                                           const T* __restrict__ prm, int u_zero) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) conv_update_el(L, x, u, B, prm, u_zero, t);
   pdl_launch();
 }
@@ -382,7 +432,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
                                                      const T* __restrict__ uin, T* __restrict__ uout,
                                                      int B, const T* __restrict__ prm, int u_zero) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) jacobi_el(L, f, uin, uout, B, prm, u_zero, t);
   pdl_launch();
 }
@@ -391,7 +441,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restrict__ r,
                                                        T* __restrict__ fc, int B,
                                                        const T* __restrict__ prm, int conv) {
-  MG_GRID_PROLOGUE((size_t)L.nc * B)
+  MG_GRID_PROLOGUE((size_t)L.nc * B, prefetch_r(L, row_of(t, B)))
   if (in_range) restrict_el(L, r, fc, B, prm, conv, t);
   pdl_launch();
 }
@@ -400,7 +450,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restrict__ ec,
                                                       const T* uin, T* u, int B,
                                                       const T* __restrict__ prm, int conv) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_p(L, row_of(t, B)))
   if (in_range) prolong_el(L, ec, uin, u, B, prm, conv, t);
   pdl_launch();
 }
@@ -409,7 +459,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_conv_r(LV<T> L, const T* __restrict__ r,
                                                      T* __restrict__ phi, int B,
                                                      const T* __restrict__ prm) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) conv_r_el(L, r, phi, B, prm, t);
   pdl_launch();
 }
@@ -417,7 +467,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_r(LV<T> L, const T* __restric
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_gather(LV<T> L, const T* __restrict__ phi,
                                                      T* __restrict__ fc, int B) {
-  MG_GRID_PROLOGUE((size_t)L.nc * B)
+  MG_GRID_PROLOGUE((size_t)L.nc * B, prefetch_r(L, row_of(t, B)))
   if (in_range) gather_el(L, phi, fc, B, t);
   pdl_launch();
 }
@@ -425,7 +475,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(LV<T> L, const T* __restric
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_pe(LV<T> L, const T* __restrict__ ec,
                                                  T* __restrict__ pe, int B) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_p(L, row_of(t, B)))
   if (in_range) pe_el(L, ec, pe, B, t);
   pdl_launch();
 }
@@ -434,7 +484,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong_conv(LV<T> L, const T* __restrict__ pe,
                                                            const T* uin, T* u, int B,
                                                            const T* __restrict__ prm) {
-  MG_GRID_PROLOGUE((size_t)L.n * B)
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) prolong_conv_el(L, pe, uin, u, B, prm, t);
   pdl_launch();
 }
@@ -442,7 +492,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_conv(LV<T> L, const T* __r
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_copy(const T* __restrict__ x, T* __restrict__ y,
                                                    size_t n) {
-  MG_GRID_PROLOGUE(n)
+  MG_GRID_PROLOGUE(n, (void)0)
   if (in_range) y[t] = x[t];
   pdl_launch();
 }
@@ -651,14 +701,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
   extern __shared__ __align__(16) unsigned char tail_smem[];
   __shared__ LV<T> sL[kMaxLevels];
   double* ys = (double*)tail_smem;
-  pdl_wait();
-  pdl_launch();
   const int J = a.J, lt = a.lt;
   TailVecs<T> v;
   // Lay out every small level in shared memory (the same order as
   // tail_level_bytes): vectors first, then the read-only arrays, copied
-  // once per cycle with all threads.
+  // once per cycle with all threads.  The read-only arrays never depend on
+  // the preceding kernel, so their copies are issued before
+  // griddepcontrol.wait and overlap its drain; the level-lt vectors it
+  // writes are copied after the wait.
   size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+  const size_t off_lt_vec = off;
   for (int l = lt; l < J; ++l) {
     const LV<T>& G = a.L[l];
     const size_t nB = (size_t)G.n * a.B;
@@ -668,14 +720,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
       v.f[l] = (T*)(tail_smem + off + bytes);
       v.t[l] = (T*)(tail_smem + off + 2 * bytes);
       v.u2[l] = (T*)(tail_smem + off + 3 * bytes);
-      if (l == lt) {
-        size_t o2 = off + bytes;
-        smem_take(tail_smem, o2, a.f[lt], nB);
-        if (!a.lt_zero) {
-          o2 = off;
-          smem_take(tail_smem, o2, (const T*)a.u[lt], nB);
-        }
-      }
       off += 4 * bytes;
     } else {
       v.u[l] = a.u[l];
@@ -703,6 +747,17 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
       }
     }
     if (threadIdx.x == 0) sL[l] = S;
+  }
+  pdl_wait();
+  pdl_launch();
+  if (a.smem_vectors) {
+    const size_t nB = (size_t)a.L[lt].n * a.B;
+    size_t o2 = off_lt_vec + tail_align(nB * sizeof(T));
+    smem_take(tail_smem, o2, a.f[lt], nB);
+    if (!a.lt_zero) {
+      o2 = off_lt_vec;
+      smem_take(tail_smem, o2, (const T*)a.u[lt], nB);
+    }
   }
   cp_async_wait_all();
   __syncthreads();

@@ -50,14 +50,17 @@ __device__ __forceinline__ void stv(T* __restrict__ x, size_t off, const T (&in)
   }
 }
 
-// Launch: 1-D grid of ceil(NROWS * (B / BV) / kThreads) blocks.
-#define MG_MB_PROLOGUE(NROWS)                                   \
-  pdl_wait();                                                   \
-  pdl_launch();                                                 \
+// Launch: 1-D grid of ceil(NROWS * (B / BV) / kThreads) blocks.  PF: the
+// row's read-only prefetch (kernels.cuh), before griddepcontrol.wait.
+#define MG_MB_PROLOGUE(NROWS, PF)                               \
   const int nq = B / BV;                                        \
   const int g = blockIdx.x * blockDim.x + threadIdx.x;          \
   const int i = g / nq;                                         \
-  if (i >= (NROWS)) return;                                     \
+  const bool in_rows = i < (NROWS);                             \
+  if (in_rows) { PF; }                                          \
+  pdl_wait();                                                   \
+  pdl_launch();                                                 \
+  if (!in_rows) return;                                         \
   const int b0 = (g - i * nq) * BV;                             \
   const size_t base = (size_t)i * B + b0;
 
@@ -95,7 +98,7 @@ __global__ void __launch_bounds__(kThreads) k_residual_mb(LV<T> L, const T* __re
                                                           T* __restrict__ out, int B,
                                                           const T* __restrict__ prm, int scale,
                                                           int u_zero) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T r[BV];
   ldv<T, BV>(f, base, r);
   if (!u_zero) {
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_update_mb(LV<T> L, const T* _
                                                              T* __restrict__ u, int B,
                                                              const T* __restrict__ prm,
                                                              int u_zero) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T s[BV], xi[BV], uu[BV];
   row_sum_mb<T, BV>(L, i, x, B, b0, s);
   ldv<T, BV>(x, base, xi);
@@ -143,7 +146,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __rest
                                                         const T* __restrict__ uin,
                                                         T* __restrict__ uout, int B,
                                                         const T* __restrict__ prm, int u_zero) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T r[BV], u0[BV];
   ldv<T, BV>(f, base, r);
   if (u_zero) {
@@ -171,7 +174,7 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_conv_r_mb(LV<T> L, const T* __restrict__ r,
                                                         T* __restrict__ phi, int B,
                                                         const T* __restrict__ prm) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T s[BV], ri[BV];
   row_sum_mb<T, BV>(L, i, r, B, b0, s);
   ldv<T, BV>(r, base, ri);
@@ -190,7 +193,7 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __restrict__ x,
                                                         T* __restrict__ fc, int B,
                                                         const T* __restrict__ prm, int scale) {
-  MG_MB_PROLOGUE(L.nc)
+  MG_MB_PROLOGUE(L.nc, prefetch_r(L, i))
   T acc[BV];
 #pragma unroll
   for (int b = 0; b < BV; ++b) acc[b] = T(0);
@@ -233,7 +236,7 @@ __device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __
 template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_pe_mb(LV<T> L, const T* __restrict__ ec,
                                                     T* __restrict__ pe, int B) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_p(L, i))
   T v[BV];
   prolong_at_mb<T, BV>(L, i, ec, B, b0, v);
   stv<T, BV>(pe, base, v);
@@ -245,7 +248,7 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __restrict__ x,
                                                          const T* uin, T* u, int B,
                                                          const T* __restrict__ prm, int conv) {
-  MG_MB_PROLOGUE(L.n)
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i); prefetch_p(L, i))
   T phi[BV], ui[BV];
   const T w1 = prm[P_WP1];
   if (conv) {
