@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restric
 template <class T>
 __device__ __forceinline__ T row_mt(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
   T s = T(0);
-  for_nb(L, i, [&](int c, T, bool nb) {
+  for_nb<T, false>(L, i, [&](int c, T, bool nb) {
     const T w = nb ? L.invdeg[c] : T(0);
     s = fma(w, x[(size_t)c * B + b], s);
   });
@@ -87,7 +87,7 @@ template <class T>
 __device__ __forceinline__ T row_sum_dinv(const LV<T>& L, int i, const T* __restrict__ x, int B,
                                           int b) {
   T s = T(0);
-  for_nb(L, i, [&](int c, T, bool nb) {
+  for_nb<T, false>(L, i, [&](int c, T, bool nb) {
     const T w = nb ? L.dinv[c] : T(0);
     s = fma(w, x[(size_t)c * B + b], s);
   });
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
     const T w1 = prm[P_WR1], w2 = prm[P_WR2];
     const T phib = prolong_at(L, i, rcbar, B, b);
     T mt = T(0), sr = T(0);
-    for_nb(L, i, [&](int c, T, bool nb) {
+    for_nb<T, false>(L, i, [&](int c, T, bool nb) {
       const T w = nb ? L.invdeg[c] : T(0);
       mt = fma(w, prolong_at(L, c, rcbar, B, b), mt);
       const T rv = r[(size_t)c * B + b];
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T*
     split_rb(t, B, i, b);
     const T pe = prolong_at(L, i, ec, B, b);
     T s = T(0);
-    for_nb(L, i, [&](int c, T, bool nb) {
+    for_nb<T, false>(L, i, [&](int c, T, bool nb) {
       const T pv = prolong_at(L, c, ec, B, b);
       s += nb ? pv : T(0);
     });

@@ -77,7 +77,7 @@ __global__ void __launch_bounds__(kTailThreads)
     int i, b;
     split_rb(t, B, i, b);
     T s = T(0);
-    for_nb(L, i, [&](int c, T, bool nb) {
+    for_nb<T, false>(L, i, [&](int c, T, bool nb) {
       const T zv = sz[(size_t)(c - lo) * B + b];
       s += nb ? zv : T(0);
     });

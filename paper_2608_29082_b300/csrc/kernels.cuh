@@ -135,8 +135,15 @@ __device__ __forceinline__ int row_of(size_t t, int B) {
 // Calls fn(c, a_ic, is_neighbour) for the off-diagonals of row i in ascending
 // column order.  DIA: every diagonal is visited; absent entries have a_ic = 0,
 // is_neighbour = false and a clamped in-range c, so the value and the
-// neighbour loads of a row are independent of each other.
-template <class T, class F>
+// neighbour loads of a row are independent of each other.  SELL: a loop
+// over the row's slice entries; with kPreload and a slice at most kMaxDia
+// wide (every mesh here), all column indices (and, with kVal, values) are
+// loaded before the first call, so the neighbour loads inside fn do not
+// wait on one another's index loads.  kPreload is used by the multi-rhs
+// kernels, where it is measured faster; it costs registers that the
+// one-value-per-thread kernels (also used on DIA levels) cannot spare.
+// kVal = false: fn ignores a_ic (mean aggregation), SELL values are not read.
+template <class T, bool kVal = true, bool kPreload = false, class F>
 __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
   if (L.ndia > 0) {
 #pragma unroll
@@ -148,11 +155,26 @@ __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
       }
     }
   } else {
-    const int beg = slice_begin(L.sl_ptr, i);
+    const int s0 = L.sl_ptr[i >> 5];
     const int end = L.sl_ptr[(i >> 5) + 1];
-    for (int e = beg; e < end; e += kSlice) {
-      const int c = L.col[e];
-      if (c >= 0) fn(c, L.val[e], true);
+    const int beg = s0 + (i & 31);
+    if (kPreload && end - s0 <= kMaxDia * kSlice) {
+      int cs[kMaxDia];
+      T vs[kMaxDia];
+#pragma unroll
+      for (int k = 0; k < kMaxDia; ++k) {
+        const int e = beg + k * kSlice;
+        cs[k] = e < end ? L.col[e] : -1;
+        vs[k] = kVal && e < end ? L.val[e] : T(0);
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxDia; ++k)
+        if (cs[k] >= 0) fn(cs[k], vs[k], true);
+    } else {
+      for (int e = beg; e < end; e += kSlice) {
+        const int c = L.col[e];
+        if (c >= 0) fn(c, kVal ? L.val[e] : T(0), true);
+      }
     }
   }
 }
@@ -169,7 +191,7 @@ __device__ __forceinline__ T row_ax(const LV<T>& L, int i, const T* __restrict__
 template <class T>
 __device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
   T s_acc = T(0);
-  for_nb(L, i, [&](int c, T, bool nb) {
+  for_nb<T, false>(L, i, [&](int c, T, bool nb) {
     const T xv = x[(size_t)c * B + b];
     s_acc += nb ? xv : T(0);
   });
@@ -288,7 +310,7 @@ __device__ __forceinline__ void prolong_el(const LV<T>& L, const T* __restrict__
   T phi = prm[P_WP1] * prolong_at(L, i, ec, B, b);
   if (conv) {
     T s = T(0);
-    for_nb(L, i, [&](int c, T, bool nb) {
+    for_nb<T, false>(L, i, [&](int c, T, bool nb) {
       const T pv = prolong_at(L, c, ec, B, b);
       s += nb ? pv : T(0);
     });

@@ -70,7 +70,7 @@ __device__ __forceinline__ void row_ax_mb(const LV<T>& L, int i, const T* __rest
                                           int b0, T (&ax)[BV]) {
 #pragma unroll
   for (int b = 0; b < BV; ++b) ax[b] = T(0);
-  for_nb(L, i, [&](int c, T v, bool) {
+  for_nb<T, true, true>(L, i, [&](int c, T v, bool) {
     T xv[BV];
     ldv<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
@@ -78,13 +78,15 @@ __device__ __forceinline__ void row_ax_mb(const LV<T>& L, int i, const T* __rest
   });
 }
 
-// sum_{j in N(i)} x_j for BV columns
-template <class T, int BV>
+// sum_{j in N(i)} x_j for BV columns (kPre: SELL column preload, see for_nb;
+// measured faster in the prolongation, slower in the two mean-only steps,
+// whose extra registers cost occupancy)
+template <class T, int BV, bool kPre = false>
 __device__ __forceinline__ void row_sum_mb(const LV<T>& L, int i, const T* __restrict__ x, int B,
                                            int b0, T (&s)[BV]) {
 #pragma unroll
   for (int b = 0; b < BV; ++b) s[b] = T(0);
-  for_nb(L, i, [&](int c, T, bool nb) {
+  for_nb<T, false, kPre>(L, i, [&](int c, T, bool nb) {
     T xv[BV];
     ldv<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
@@ -254,7 +256,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __res
   if (conv) {
     T s[BV], xi[BV];
     ldv<T, BV>(x, base, xi);
-    row_sum_mb<T, BV>(L, i, x, B, b0, s);
+    row_sum_mb<T, BV, true>(L, i, x, B, b0, s);
     const T w2 = prm[P_WP2], id = L.invdeg[i];
 #pragma unroll
     for (int b = 0; b < BV; ++b) {
