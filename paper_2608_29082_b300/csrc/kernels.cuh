@@ -928,11 +928,11 @@ __global__ void __launch_bounds__(kRedMax) k_sumsq64(const double* __restrict__ 
 }
 
 // out[b] = sum over blocks of partial[blk * B + b]; grid = B blocks.
-__global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ partial, int nblk,
-                                                     int B, double* __restrict__ out) {
-  pdl_wait();
-  __shared__ double sh[kThreads];
-  const int b = blockIdx.x;
+// Sum of the partials of right-hand side b in a fixed order (strided per
+// thread, then a fixed tree); one block of kThreads threads; every thread
+// returns the sum.
+__device__ __forceinline__ double block_sum_partials(const double* __restrict__ partial,
+                                                     int nblk, int B, int b, double* sh) {
   double s = 0.0;
   for (int k = threadIdx.x; k < nblk; k += kThreads) s += partial[(size_t)k * B + b];
   sh[threadIdx.x] = s;
@@ -941,21 +941,34 @@ __global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ 
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) out[b] = sh[0];
+  const double r = sh[0];
+  __syncthreads();
+  return r;
 }
 
-// Convergence test per right-hand side; one block.  ctl = (tol, max_iter).
-// state[0] = right-hand sides still active, state[1] = 1 if a residual is not
-// finite, state[2] = iterations done (reset when inc == 0, else +1),
-// state[3] = continue: some right-hand side is active, all residuals are
-// finite and fewer than max_iter iterations ran.  With set_cond the same
-// value becomes the enclosing while-node's condition (h is ignored otherwise).
-__global__ void k_check(const double* __restrict__ rsum, const double* __restrict__ fsum, int B,
-                        const double* __restrict__ ctl, int* __restrict__ active,
-                        double* __restrict__ relres, int* __restrict__ sexp,
-                        int* __restrict__ state, int inc, cudaGraphConditionalHandle h,
-                        int set_cond) {
+// out[b] = sum of the partials of right-hand side b; one block per b.
+__global__ void __launch_bounds__(kThreads) k_reduce(const double* __restrict__ partial, int nblk,
+                                                     int B, double* __restrict__ out) {
   pdl_wait();
+  __shared__ double sh[kThreads];
+  const int b = blockIdx.x;
+  const double r = block_sum_partials(partial, nblk, B, b, sh);
+  if (threadIdx.x == 0) out[b] = r;
+}
+
+// Convergence test per right-hand side (body of k_check and k_reduce_check,
+// one block).  ctl = (tol, max_iter).  state[0] = right-hand sides still
+// active, state[1] = 1 if a residual is not finite, state[2] = iterations
+// done (reset when inc == 0, else +1), state[3] = continue: some right-hand
+// side is active, all residuals are finite and fewer than max_iter
+// iterations ran.  With set_cond the same value becomes the enclosing
+// while-node's condition (h is ignored otherwise).
+__device__ __forceinline__ void check_block(const double* __restrict__ rsum,
+                                            const double* __restrict__ fsum, int B,
+                                            const double* __restrict__ ctl,
+                                            int* __restrict__ active, double* __restrict__ relres,
+                                            int* __restrict__ sexp, int* __restrict__ state,
+                                            int inc, cudaGraphConditionalHandle h, int set_cond) {
   __shared__ int cnt, bad;
   const double tol = ctl[0];
   if (threadIdx.x == 0) { cnt = 0; bad = 0; }
@@ -979,6 +992,37 @@ __global__ void k_check(const double* __restrict__ rsum, const double* __restric
     state[3] = go;  // read by the host when it drives the loop
     if (set_cond) cudaGraphSetConditional(h, go ? 1u : 0u);
   }
+}
+
+__global__ void k_check(const double* __restrict__ rsum, const double* __restrict__ fsum, int B,
+                        const double* __restrict__ ctl, int* __restrict__ active,
+                        double* __restrict__ relres, int* __restrict__ sexp,
+                        int* __restrict__ state, int inc, cudaGraphConditionalHandle h,
+                        int set_cond) {
+  pdl_wait();
+  check_block(rsum, fsum, B, ctl, active, relres, sexp, state, inc, h, set_cond);
+}
+
+// k_reduce, the copy sexp_prev = sexp (when sexp_prev is given) and k_check
+// in one block of kThreads threads, for small B * nblk (the sums run one
+// right-hand side after another, each in k_reduce's order, so the results
+// are those of the three kernels).
+__global__ void __launch_bounds__(kThreads)
+    k_reduce_check(const double* __restrict__ partial, int nblk, double* __restrict__ rsum,
+                   int* __restrict__ sexp_prev, const double* __restrict__ fsum, int B,
+                   const double* __restrict__ ctl, int* __restrict__ active,
+                   double* __restrict__ relres, int* __restrict__ sexp, int* __restrict__ state,
+                   int inc, cudaGraphConditionalHandle h, int set_cond) {
+  pdl_wait();
+  __shared__ double sh[kThreads];
+  for (int b = 0; b < B; ++b) {
+    const double r = block_sum_partials(partial, nblk, B, b, sh);
+    if (threadIdx.x == 0) rsum[b] = r;
+  }
+  if (sexp_prev)
+    for (int b = threadIdx.x; b < B; b += blockDim.x) sexp_prev[b] = sexp[b];
+  __syncthreads();
+  check_block(rsum, fsum, B, ctl, active, relres, sexp, state, inc, h, set_cond);
 }
 
 // u += 2^sexp[b] * c for the right-hand sides still active (refinement update).

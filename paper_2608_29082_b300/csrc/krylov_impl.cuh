@@ -105,11 +105,7 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
     is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u, c->k_r, (int)B);
     is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r, (const double*)c->k_r,
               (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
-    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
-              c->rsum);
-    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-              c->sexp, c->state, 0, h, cond);
+    reduce_and_check(is, c, nblk, (int)B, (int*)nullptr, 0, h, cond);
     nk += is.nk;
     nk += precondition(cs);
     Issue<double> is2{c, c->d64, c->prm64, cs, B};
@@ -126,11 +122,7 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
     is.launch(mgk::k_fcg_update, rgrid, rblock, 0, u, c->k_r, (const double*)c->k_p,
               (const double*)c->k_q, (const double*)alpha, (const int*)c->active, n0, (int)B,
               c->partial);
-    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
-              c->rsum);
-    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-              c->sexp, c->state, 1, h, cond);
+    reduce_and_check(is, c, nblk, (int)B, (int*)nullptr, 1, h, cond);
     nk += is.nk;
     nk += precondition(cs);
     Issue<double> is2{c, c->d64, c->prm64, cs, B};

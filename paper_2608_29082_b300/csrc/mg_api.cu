@@ -1259,6 +1259,28 @@ __global__ void k_bump_iters(const int* __restrict__ active, int* __restrict__ i
   if (b < B && active[b]) iters[b] += 1;
 }
 
+// Per-right-hand-side sums of c->partial into c->rsum, the copy
+// sexp_prev = sexp (when given) and the convergence test.  For small
+// B * nblk one block does all three (k_reduce_check: the same sums in the
+// same order, two launches fewer per iteration of a latency-bound solve);
+// otherwise k_reduce over B blocks, the copy and k_check.
+constexpr int64_t kMergeReduceMax = 32768;
+void reduce_and_check(Issue<double>& is, mg_ctx* c, int nblk, int B, int* sexp_prev, int inc,
+                      cudaGraphConditionalHandle h, int cond) {
+  if ((int64_t)B * nblk <= kMergeReduceMax) {
+    is.launch(mgk::k_reduce_check, dim3(1), dim3(kThreads), 0, (const double*)c->partial, nblk,
+              c->rsum, sexp_prev, (const double*)c->fsum, B, (const double*)c->tol_dev, c->active,
+              c->relres, c->sexp, c->state, inc, h, cond);
+    return;
+  }
+  is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, B,
+            c->rsum);
+  if (sexp_prev) is.launch(k_shift_sexp, dim3(1), dim3(kThreads), 0, c->sexp, sexp_prev, B);
+  is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+            (const double*)c->fsum, B, (const double*)c->tol_dev, c->active, c->relres, c->sexp,
+            c->state, inc, h, cond);
+}
+
 }  // namespace
 
 extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
@@ -1285,12 +1307,7 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
   auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
     is.launch(mgk::k_resid64, rgrid, rblock, 0, L0, (const double*)f, (const double*)u,
               p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B, c->partial);
-    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
-              c->rsum);
-    if (p32) is.launch(k_shift_sexp, dim3(1), dim3(kThreads), 0, c->sexp, c->sexp_prev, (int)B);
-    is.launch(mgk::k_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
-              (const double*)c->fsum, (int)B, (const double*)c->tol_dev, c->active, c->relres,
-              c->sexp, c->state, inc, h, cond);
+    reduce_and_check(is, c, nblk, (int)B, p32 ? c->sexp_prev : (int*)nullptr, inc, h, cond);
   };
   auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
     Issue<double> is{c, c->d64, c->prm64, cs, B};

@@ -288,6 +288,18 @@ def test_full_size_checkerboard_513():
     u, info = S32.solve(t64(p.f), tol=1e-8, max_iter=400)
     assert info.status == 0
     assert O.relres(Ho, p.f, u.cpu().numpy())[0] < 1e-8
+    # 5 rhs at this size take the per-rhs reduction blocks, 1 rhs the merged
+    # reduce-and-test block: the same sums in the same order, so every rhs is
+    # bitwise its solve alone (refinement and flexible CG)
+    f5 = np.concatenate([p.f, np.random.default_rng(21).standard_normal((Hp.sizes[0], 4))], 1)
+    S5 = Solver(Hp, prm, precision=32, max_batch=5)
+    for method in ("refine", "fcg"):
+        u5, i5 = S5.solve(t64(f5), tol=1e-8, max_iter=400, method=method)
+        for b in (0, 3):
+            u1, i1 = S32.solve(t64(f5[:, [b]]), tol=1e-8, max_iter=400, method=method)
+            assert torch.equal(u1[:, 0], u5[:, b]), (method, b)
+            assert i1.iters[0] == i5.iters[b] and i1.relres[0] == i5.relres[b]
+    S5.close()
 
 
 # ------------------------------------------------------ flexible CG outer --
