@@ -122,6 +122,15 @@ class ClockSampler:
 
 # ------------------------------------------------------ algorithmic bytes --
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one
+# ncu capture, cold cache) of the kernel the default workload's roofline
+# names, with the profiles/ summary it comes from.  A kernel changed since
+# its capture must lose its entry (traffic is then reported as null).
+NCU_TRAFFIC = {
+    "small_levels_block@level4": (175872, "profiles/k_tail_f32_checker513.md"),
+}
+
+
 def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
     """Minimum bytes one launch must move: every array touched read (or
     written) once; neighbour values of a vector counted once."""
@@ -370,7 +379,10 @@ def run_ours(args):
                                        "learned_fcg": int(nkfcg)},
             "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "frac": round(achieved / peak, 4),
+                         "traffic": NCU_TRAFFIC.get(f"{dname}@level{dlev}", (None,))[0],
+                         "traffic_source": NCU_TRAFFIC.get(f"{dname}@level{dlev}",
+                                                           (None, None))[1],
                          "algorithmic_bytes_per_launch": int(nbytes),
                          "avg_launch_us": round(avg_launch_ms * 1e3, 3),
                          "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
