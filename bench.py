@@ -128,6 +128,7 @@ class ClockSampler:
 # its capture must lose its entry (traffic is then reported as null).
 NCU_TRAFFIC = {
     "small_levels_block@level4": (175872, "profiles/k_tail_f32_checker513.md"),
+    "lshape:residual_scaled@level0": (770840000, "profiles/k_residual_mb_f32_lshape.md"),
 }
 
 
@@ -425,6 +426,9 @@ def lshape_roofline(dev, peak):
             "bound": "hbm", "kernel": f"{top['kernel']}@level{top['level']}",
             "achieved": top["GBps"], "peak": peak, "unit": "GB/s",
             "frac": round(top["GBps"] / peak, 4) if top["GBps"] else None,
+            "traffic": NCU_TRAFFIC.get(f"lshape:{top['kernel']}@level{top['level']}", (None,))[0],
+            "traffic_source": NCU_TRAFFIC.get(f"lshape:{top['kernel']}@level{top['level']}",
+                                              (None, None))[1],
             "algorithmic_bytes_per_launch": int(top["algorithmic_MB"] * 1e6),
             "avg_launch_us": top["us_per_launch"], "share_of_cycle": top["share"],
             "cycle_us": round(cycle_us, 1),
