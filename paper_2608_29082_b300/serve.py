@@ -92,7 +92,12 @@ class ClassWorker(threading.Thread):
         self.klass = klass
         self.queue: deque[Request] = deque()
         self.lock = threading.Lock()
-        self.stream = torch.cuda.Stream(device=server.device)
+        # the smaller half of the size classes gets a high-priority stream, so
+        # their short kernels are scheduled ahead of the large classes' full-
+        # GPU kernels instead of queueing behind them (latency of small
+        # requests); priorities change scheduling only, never results
+        small = klass <= server.classes[(len(server.classes) - 1) // 2]
+        self.stream = torch.cuda.Stream(device=server.device, priority=-1 if small else 0)
         self.stop = False
         self.error: BaseException | None = None
 
@@ -193,7 +198,7 @@ class Server:
     thread per class during run()."""
 
     def __init__(self, hierarchies: dict, sources: dict, params: LMGParams,
-                 slots: int = 8, tol: float = 1e-8, iters_per_tick: int = 2,
+                 slots: int = 8, tol: float = 1e-8, iters_per_tick: int = 6,
                  max_iter: int = 400, budget_bytes: int | None = None, device=None,
                  keep_results: bool = False, idle_evict_s: float = 0.02):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -344,7 +349,7 @@ def main():
     ap.add_argument("--ops", type=int, default=2)
     ap.add_argument("--srcs", type=int, default=4)
     ap.add_argument("--slots", type=int, default=16)
-    ap.add_argument("--iters-per-tick", type=int, default=2)
+    ap.add_argument("--iters-per-tick", type=int, default=6)
     ap.add_argument("--params", default=None)
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
