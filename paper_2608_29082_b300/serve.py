@@ -57,7 +57,11 @@ class OperatorContext:
 
     def __init__(self, key, hier: Hierarchy, params: LMGParams, slots: int, device, nbytes: int):
         self.key = key
-        self.solver = Solver(hier, params.with_levels(hier.J), precision=32, max_batch=slots,
+        # one parameter set for all classes: each class takes the trained
+        # levels whose mesh widths match its own (the classes share the unit
+        # square and its coarsest meshes, so they differ at the fine end)
+        self.solver = Solver(hier, params.with_levels(hier.J, align="coarse"), precision=32,
+                             max_batch=slots,
                              device=device)
         n = hier.sizes[0]
         self.n = n
