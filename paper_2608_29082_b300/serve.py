@@ -57,11 +57,7 @@ class OperatorContext:
 
     def __init__(self, key, hier: Hierarchy, params: LMGParams, slots: int, device, nbytes: int):
         self.key = key
-        # one parameter set for all classes: each class takes the trained
-        # levels whose mesh widths match its own (the classes share the unit
-        # square and its coarsest meshes, so they differ at the fine end)
-        self.solver = Solver(hier, params.with_levels(hier.J, align="coarse"), precision=32,
-                             max_batch=slots,
+        self.solver = Solver(hier, params.with_levels(hier.J), precision=32, max_batch=slots,
                              device=device)
         n = hier.sizes[0]
         self.n = n
@@ -201,7 +197,7 @@ class Server:
     within a device-memory budget, or ahead of time by warm()), and one worker
     thread per class during run()."""
 
-    def __init__(self, hierarchies: dict, sources: dict, params: LMGParams,
+    def __init__(self, hierarchies: dict, sources: dict, params,
                  slots: int = 8, tol: float = 1e-8, iters_per_tick: int = 6,
                  max_iter: int = 400, budget_bytes: int | None = None, device=None,
                  keep_results: bool = False, idle_evict_s: float = 0.02):
@@ -209,7 +205,7 @@ class Server:
         self.hierarchies = hierarchies          # (klass, op) -> Hierarchy
         self.sources = {k: torch.as_tensor(v, dtype=torch.float64).to(self.device)
                         for k, v in sources.items()}  # (klass, src) -> (n,) f
-        self.params = params
+        self.params = params  # LMGParams, or {size class: LMGParams}
         self.slots = slots
         self.tol = tol
         self.iters_per_tick = iters_per_tick
@@ -246,7 +242,8 @@ class Server:
 
     def create(self, key) -> OperatorContext:
         """Sets up a context whose bytes are already reserved."""
-        ctx = OperatorContext(key, self.hierarchies[key], self.params, self.slots, self.device,
+        prm = self.params[key[0]] if isinstance(self.params, dict) else self.params
+        ctx = OperatorContext(key, self.hierarchies[key], prm, self.slots, self.device,
                               self.need[key])
         self.contexts[key[0]][key] = ctx
         return ctx
@@ -354,14 +351,23 @@ def main():
     ap.add_argument("--srcs", type=int, default=4)
     ap.add_argument("--slots", type=int, default=16)
     ap.add_argument("--iters-per-tick", type=int, default=6)
-    ap.add_argument("--params", default=None)
+    ap.add_argument("--params", default=None,
+                    help="parameter set of every class (default: the package's trained set)")
+    ap.add_argument("--class-params", default=None,
+                    help="per-class sets N=path[,N=path]; default: the 1025^2 class uses the "
+                         "set trained on a 1025^2 lognormal operator")
     ap.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     from . import trained
     classes = [int(x) for x in a.classes.split(",")]
     t_setup = time.perf_counter()
     hier, src, _ = make_pools(classes, a.ops, a.srcs, a.seed)
-    params = trained.load(a.params, max(h.J for h in hier.values()))
+    base = trained.load(a.params, max(h.J for h in hier.values()))
+    spec = a.class_params
+    if spec is None and os.path.exists(trained.LOGNORMAL1025):
+        spec = f"1025={trained.LOGNORMAL1025}"
+    over = dict((int(k), v) for k, v in (x.split("=", 1) for x in spec.split(","))) if spec else {}
+    params = {k: trained.read(over[k]) if k in over else base for k in classes}
     t_setup = time.perf_counter() - t_setup
     reqs = poisson_requests(a.rate, a.duration, classes, a.ops, a.srcs, a.seed)
     srv = Server(hier, src, params, slots=a.slots, iters_per_tick=a.iters_per_tick)
@@ -376,7 +382,9 @@ def main():
            "offered_rate_per_s": a.rate, "duration_s": a.duration, "classes": classes,
            "operators_per_class": a.ops, "slots": a.slots, "iters_per_tick": a.iters_per_tick,
            "wall_s": round(wall, 3), "setup_s": round(t_setup, 2),
-           "peak_device_bytes": srv.peak, "budget_bytes": srv.budget}
+           "peak_device_bytes": srv.peak, "budget_bytes": srv.budget,
+           "params": {str(k): os.path.basename(over[k]) if k in over else
+                      trained.describe(a.params).split(":")[0] for k in classes}}
     out.update(summarize(done, wall))
     print(json.dumps(out), flush=True)
 

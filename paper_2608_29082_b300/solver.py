@@ -49,16 +49,12 @@ class LMGParams:
         return LMGParams(x[:, 0].copy(), x[:, 1].copy(), x[:, 2:4].copy(), x[:, 4:6].copy(),
                          x[:, 6:8].copy(), nu_pre, nu_post)
 
-    def with_levels(self, J: int, align: str = "fine") -> "LMGParams":
+    def with_levels(self, J: int) -> "LMGParams":
         """Weight transfer to a hierarchy with J levels: levels beyond the
-        trained ones copy the deepest trained level (Sec. 4.2 transfer rule).
-        A shallower hierarchy takes the first J-1 trained levels (align =
-        "fine"), or, with align = "coarse", the last J-1: for nested meshes of
-        one domain that differ in their finest mesh, those are the trained
-        levels with the same mesh widths as its own."""
+        trained ones copy the deepest trained level (Sec. 4.2 transfer rule)."""
         x = self.flat().reshape(-1, 8)
         if J - 1 <= x.shape[0]:
-            y = x[x.shape[0] - (J - 1):] if align == "coarse" else x[:J - 1]
+            y = x[:J - 1]
         else:
             y = np.concatenate([x, np.repeat(x[-1:], J - 1 - x.shape[0], axis=0)], 0)
         return LMGParams.from_flat(y, self.nu_pre, self.nu_post)

@@ -16,6 +16,7 @@ from .solver import LMGParams
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT = os.path.join(HERE, "params", "checker513_learned.json")
+LOGNORMAL1025 = os.path.join(HERE, "params", "lognormal1025_learned.json")
 
 
 def save(params: LMGParams, path: str, **meta) -> None:
