@@ -298,6 +298,7 @@ struct mg_ctx {
   std::vector<void*> ck_u, bw_ubar, bw_fbar, bw_r, bw_rbar;
   void* ck_f0 = nullptr;
   double* bw_partial = nullptr;
+  double* bw_gp = nullptr;  // parameter gradients of the captured backward [J-1][P_COUNT]
 
   mg_status fail(mg_status s, const std::string& m) {
     err = m;

@@ -48,6 +48,7 @@ void train_free(mg_ctx* c) {
   c->bw_rbar.clear();
   c->ck_f0 = nullptr;
   c->bw_partial = nullptr;
+  c->bw_gp = nullptr;
   c->trK = c->trB = 0;
   c->tr_recorded = false;
 }
@@ -91,6 +92,9 @@ mg_status ensure_train(mg_ctx* c, int K, int B) {
   }
   const size_t nblk = ((size_t)c->n[0] * B + kThreads - 1) / kThreads + 1;
   if ((st = train_alloc(c, (void**)&c->bw_partial, nblk * 4 * sizeof(double))) != MG_OK) return st;
+  if ((st = train_alloc(c, (void**)&c->bw_gp, (size_t)(J - 1) * mgk::P_COUNT * sizeof(double))) !=
+      MG_OK)
+    return st;
   c->trK = K;
   c->trB = B;
   c->tr_nu_pre = c->nu_pre;
@@ -241,20 +245,29 @@ mg_status backward(mg_ctx* c, int K, const T* gout, T* gin, T* gf, double* gpara
                    cudaStream_t s) {
   const int B = c->trB;
   const size_t v0 = (size_t)c->n[0] * B * sizeof(T);
-  MG_CUDA(cudaMemsetAsync(gparams, 0, (size_t)(c->J - 1) * mgk::P_COUNT * sizeof(double), s));
-  T* fbar0 = gf ? gf : (T*)c->bw_fbar[0];
-  MG_CUDA(cudaMemsetAsync(fbar0, 0, v0, s));
+  const size_t gpb = (size_t)(c->J - 1) * mgk::P_COUNT * sizeof(double);
   T* ubar = (T*)c->bw_ubar[0];
+  T* fbar0 = (T*)c->bw_fbar[0];
   MG_CUDA(cudaMemcpyAsync(ubar, gout, v0, cudaMemcpyDeviceToDevice, s));
-  Issue<T> is{c, levels_of<T>(c), prm_of<T>(c), s, B};
-  Backward<T> bw{c, is, levels_of<T>(c), s, B, gparams};
-  for (int k = K - 1; k >= 0; --k) {
-    bw.k = k;
-    bw.level(0, (const T*)c->ck_f0, (const T*)c->ck_u[k], ubar, fbar0);
-  }
+  // The reverse pass (about 40 kernels per level and cycle) touches context
+  // buffers only, so it is captured once per (K, B, convolution structure)
+  // and replayed; the caller's buffers are copied in before and out after.
+  auto key = std::make_tuple(2000 + K, (const void*)c->bw_gp, (const void*)ubar, B, c->structure);
+  mg_status st = run_graph(c, key, s, [&](cudaStream_t cs) {
+    cudaMemsetAsync(c->bw_gp, 0, gpb, cs);
+    cudaMemsetAsync(fbar0, 0, v0, cs);
+    Issue<T> is{c, levels_of<T>(c), prm_of<T>(c), cs, B};
+    Backward<T> bw{c, is, levels_of<T>(c), cs, B, c->bw_gp};
+    for (int k = K - 1; k >= 0; --k) {
+      bw.k = k;
+      bw.level(0, (const T*)c->ck_f0, (const T*)c->ck_u[k], ubar, fbar0);
+    }
+    return is.nk;
+  });
+  if (st != MG_OK) return st;
+  MG_CUDA(cudaMemcpyAsync(gparams, c->bw_gp, gpb, cudaMemcpyDeviceToDevice, s));
+  if (gf) MG_CUDA(cudaMemcpyAsync(gf, fbar0, v0, cudaMemcpyDeviceToDevice, s));
   if (gin) MG_CUDA(cudaMemcpyAsync(gin, ubar, v0, cudaMemcpyDeviceToDevice, s));
-  MG_CUDA(cudaGetLastError());
-  c->launches += is.nk;
   return MG_OK;
 }
 
