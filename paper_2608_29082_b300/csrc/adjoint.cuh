@@ -28,20 +28,25 @@
 
 namespace mgk {
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <class W>
+__device__ __forceinline__ W warp_sum(W v) {
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
 // Sums Q values over the block (fixed order) and writes partial[blk*Q + q].
-template <int Q>
-__device__ __forceinline__ void block_dots(const double (&v)[Q], double* __restrict__ partial) {
+// Each thread's terms and the sum within a warp are in the context precision
+// W; the warp sums and everything after are FP64.  (Forming the terms in FP64
+// for an FP32 context put the whole kernel on the B300's FP64 pipe, which
+// made it 8x slower than its neighbours.)
+template <int Q, class W>
+__device__ __forceinline__ void block_dots(const W (&v)[Q], double* __restrict__ partial) {
   __shared__ double sh[Q][kThreads / 32];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
-    const double s = warp_sum(v[q]);
-    if (lane == 0) sh[q][warp] = s;
+    const W s = warp_sum(v[q]);
+    if (lane == 0) sh[q][warp] = (double)s;
   }
   __syncthreads();
   if (threadIdx.x < Q) {
@@ -103,7 +108,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth(LV<T> L, const T* __res
                                                          const T* __restrict__ prm,
                                                          double* __restrict__ partial) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  T v[4] = {T(0), T(0), T(0), T(0)};
   if (t < (size_t)L.n * B) {
     int i, b;
     split_rb(t, B, i, b);
@@ -116,10 +121,10 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth(LV<T> L, const T* __res
     rbar[t] = theta * (L.dinv[i] * deltab);
     const T delta = theta * dr;
     const T mdelta = L.invdeg[i] * (theta * row_sum_dinv(L, i, r, B, b));  // M delta
-    v[0] = (double)ub * ((double)w1 * delta + (double)w2 * mdelta);       // d eta
-    v[1] = (double)eta * ((double)ub * delta);                             // d w1
-    v[2] = (double)eta * ((double)ub * mdelta);                            // d w2
-    v[3] = (double)deltab * dr;                                            // d theta
+    v[0] = ub * (w1 * delta + w2 * mdelta);  // d eta
+    v[1] = eta * (ub * delta);               // d w1
+    v[2] = eta * (ub * mdelta);              // d w2
+    v[3] = deltab * dr;                      // d theta
   }
   block_dots<4>(v, partial);
 }
@@ -150,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
                                                            const T* __restrict__ prm,
                                                            double* __restrict__ partial) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double v[2] = {0.0, 0.0};
+  T v[2] = {T(0), T(0)};
   if (t < (size_t)L.n * B) {
     int i, b;
     split_rb(t, B, i, b);
@@ -164,8 +169,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
       sr += nb ? rv : T(0);
     });
     rbar[t] = fma(w1, phib, w2 * mt);
-    v[0] = (double)phib * r[t];
-    v[1] = (double)phib * (L.invdeg[i] * sr);
+    v[0] = phib * r[t];
+    v[1] = phib * (L.invdeg[i] * sr);
   }
   block_dots<2>(v, partial);
 }
@@ -196,7 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T*
                                                                const T* __restrict__ ec, int B,
                                                                double* __restrict__ partial) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double v[2] = {0.0, 0.0};
+  T v[2] = {T(0), T(0)};
   if (t < (size_t)L.n * B) {
     int i, b;
     split_rb(t, B, i, b);
@@ -206,7 +211,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T*
       const T pv = prolong_at(L, c, ec, B, b);
       s += nb ? pv : T(0);
     });
-    const double ub = (double)ubar[t];
+    const T ub = ubar[t];
     v[0] = ub * pe;
     v[1] = ub * (L.invdeg[i] * s);
   }
