@@ -116,21 +116,19 @@ struct Backward {
   size_t vbytes(int lev) const { return (size_t)c->n[lev] * B * sizeof(T); }
 
   // One forward smoothing step uin -> uout (uout != uin), same arithmetic as
-  // the forward cycle.  zero: uin is the zero vector (not read).
+  // the forward cycle (the Issue launch forms: multi-rhs kernels when B > 1).
+  // zero: uin is the zero vector (not read).
   void step(int lev, const T* f, const T* uin, T* uout, bool zero) {
     DevLevel<T>& D = L[lev];
-    const dim3 g = grid_for((size_t)D.n * B);
     if (!is.conv(lev, mgk::P_WB2)) {
-      mgk::k_jacobi<T><<<g, kThreads, 0, s>>>(D.view(), f, uin, uout, B, is.P(lev), zero);
-      is.nk++;
+      is.op_jacobi(lev, f, uin, uout, zero);
     } else {
       if (zero)
         cudaMemsetAsync(uout, 0, vbytes(lev), s);
       else
         cudaMemcpyAsync(uout, uin, vbytes(lev), cudaMemcpyDeviceToDevice, s);
-      mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, uout, D.t, B, is.P(lev), 1, zero);
-      mgk::k_conv_update<T><<<g, kThreads, 0, s>>>(D.view(), D.t, uout, B, is.P(lev), zero);
-      is.nk += 2;
+      is.op_residual(lev, f, uout, D.t, 1, zero);
+      is.op_conv_update(lev, D.t, uout, zero);
     }
   }
 
@@ -150,12 +148,12 @@ struct Backward {
     const dim3 g = grid_for(work);
     T* r = V(c->bw_r[lev]);
     T* rbar = V(c->bw_rbar[lev]);
-    mgk::k_residual<T><<<g, kThreads, 0, s>>>(D.view(), f, uin, r, B, is.P(lev), 0, zero);
+    is.op_residual(lev, f, uin, r, 0, zero);
     mgk::k_adj_smooth<T><<<g, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B, is.P(lev),
                                                  c->bw_partial);
     accum(lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
     mgk::k_adj_apply_a<T><<<g, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
-    is.nk += 3;
+    is.nk += 2;
   }
 
   // Level lev of cycle k: ubar (adjoint of the level's output) -> adjoint of
@@ -177,9 +175,12 @@ struct Backward {
       cudaMemcpyAsync(it[0], uin, vbytes(lev), cudaMemcpyDeviceToDevice, s);
     for (int j = 0; j < np; ++j) step(lev, f, V(it[j]), V(it[j + 1]), zero_in && j == 0);
     const T* ec = V(c->ck_e[k][lev + 1]);
-    mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
-        D.view(), ec, V(it[np]), V(it[np + 1]), B, is.P(lev), is.conv(lev, mgk::P_WP2));
-    is.nk++;
+    if (is.conv(lev, mgk::P_WP2)) {  // P e_c per fine row, then Phi_P and the update
+      is.op_pe(lev, ec, D.t);
+      is.op_prolong(lev, D.t, V(it[np]), V(it[np + 1]), 1);
+    } else {
+      is.op_prolong(lev, ec, V(it[np]), V(it[np + 1]), 0);
+    }
     for (int j = 0; j < nq; ++j) step(lev, f, V(it[np + 1 + j]), V(it[np + 2 + j]), false);
     // reverse: post-smoothing
     for (int j = nq - 1; j >= 0; --j) adj_step(lev, f, V(it[np + 1 + j]), false, ubar, fbar);
@@ -198,13 +199,12 @@ struct Backward {
     // restriction: r = f - A u_pre, r_c = P^T Phi_R r
     T* r = V(c->bw_r[lev]);
     T* rbar = V(c->bw_rbar[lev]);
-    mgk::k_residual<T><<<gf, kThreads, 0, s>>>(D.view(), f, V(it[np]), r, B, is.P(lev), 0,
-                                                zero_in && np == 0);
+    is.op_residual(lev, f, V(it[np]), r, 0, zero_in && np == 0);
     mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), fcbar, r, rbar, B, is.P(lev),
                                                     c->bw_partial);
     accum(lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
     mgk::k_adj_apply_a<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
-    is.nk += 3;
+    is.nk += 2;
     // reverse: pre-smoothing
     for (int j = np - 1; j >= 0; --j) adj_step(lev, f, V(it[j]), zero_in && j == 0, ubar, fbar);
   }
