@@ -25,6 +25,7 @@
 #pragma once
 
 #include "kernels.cuh"
+#include "multi_rhs.cuh"
 
 namespace mgk {
 
@@ -264,6 +265,100 @@ __global__ void k_loss_combine(const double* __restrict__ s, const double* __res
     if (w) acc += w[b] * s[b];
   }
   if (loss) *loss = acc;
+}
+
+// Multi-right-hand-side forms (one thread per row and BV consecutive rhs,
+// the B / BV threads of a row adjacent, as in multi_rhs.cuh; launch:
+// 1-D grid of ceil(n * (B / BV) / kThreads) blocks).  rbar, ubar and fbar
+// are computed with the arithmetic of the one-thread-per-(row, rhs) kernels
+// above; each thread adds its BV terms of a parameter dot before the block
+// sum, so the dots round differently (still in a fixed order).
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_adj_smooth_mb(LV<T> L, const T* __restrict__ ubar,
+                                                            const T* __restrict__ r,
+                                                            T* __restrict__ rbar, int B,
+                                                            const T* __restrict__ prm,
+                                                            double* __restrict__ partial) {
+  const int nq = B / BV;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = g / nq;
+  T v[4] = {T(0), T(0), T(0), T(0)};
+  if (i < L.n) {
+    const int b0 = (g - i * nq) * BV;
+    const size_t base = (size_t)i * B + b0;
+    const T theta = prm[P_THETA], eta = prm[P_ETA], w1 = prm[P_WB1], w2 = prm[P_WB2];
+    T ub[BV], rr[BV], mt[BV], sd[BV], rb[BV];
+    ldv<T, BV>(ubar, base, ub);
+    ldv<T, BV>(r, base, rr);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) mt[b] = sd[b] = T(0);
+    // M^T ubar and sum_{N(i)} dinv_j r_j, each accumulated in row_mt's and
+    // row_sum_dinv's order
+    for_nb<T, false, true>(L, i, [&](int c, T, bool nb) {
+      const T wm = nb ? L.invdeg[c] : T(0);
+      const T wd = nb ? L.dinv[c] : T(0);
+      T uc[BV], rc[BV];
+      ldv<T, BV>(ubar, (size_t)c * B + b0, uc);
+      ldv<T, BV>(r, (size_t)c * B + b0, rc);
+#pragma unroll
+      for (int b = 0; b < BV; ++b) {
+        mt[b] = fma(wm, uc[b], mt[b]);
+        sd[b] = fma(wd, rc[b], sd[b]);
+      }
+    });
+    const T di = L.dinv[i], id = L.invdeg[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) {
+      const T phib = eta * ub[b];
+      const T mtphib = eta * mt[b];
+      const T deltab = fma(w1, phib, w2 * mtphib);
+      const T dr = di * rr[b];
+      rb[b] = theta * (di * deltab);
+      const T delta = theta * dr;
+      const T mdelta = id * (theta * sd[b]);
+      v[0] += ub[b] * (w1 * delta + w2 * mdelta);
+      v[1] += eta * (ub[b] * delta);
+      v[2] += eta * (ub[b] * mdelta);
+      v[3] += deltab * dr;
+    }
+    stv<T, BV>(rbar, base, rb);
+  }
+  block_dots<4>(v, partial);
+}
+
+// ubar <- ubar - A rbar (when ubar is given); fbar (+)= rbar
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_adj_apply_a_mb(LV<T> L, T* __restrict__ ubar,
+                                                             const T* __restrict__ rbar,
+                                                             T* __restrict__ fbar, int B,
+                                                             int fbar_set) {
+  const int nq = B / BV;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = g / nq;
+  if (i >= L.n) return;
+  const int b0 = (g - i * nq) * BV;
+  const size_t base = (size_t)i * B + b0;
+  T rb[BV];
+  ldv<T, BV>(rbar, base, rb);
+  if (ubar) {
+    T ax[BV], ub[BV];
+    row_ax_mb<T, BV>(L, i, rbar, B, b0, ax);
+    ldv<T, BV>(ubar, base, ub);
+    const T d = L.diag[i];
+#pragma unroll
+    for (int b = 0; b < BV; ++b) ub[b] = ub[b] - fma(d, rb[b], ax[b]);
+    stv<T, BV>(ubar, base, ub);
+  }
+  T fb[BV];
+  if (fbar_set) {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) fb[b] = rb[b];
+  } else {
+    ldv<T, BV>(fbar, base, fb);
+#pragma unroll
+    for (int b = 0; b < BV; ++b) fb[b] = fb[b] + rb[b];
+  }
+  stv<T, BV>(fbar, base, fb);
 }
 
 }  // namespace mgk

@@ -149,10 +149,21 @@ struct Backward {
     T* r = V(c->bw_r[lev]);
     T* rbar = V(c->bw_rbar[lev]);
     is.op_residual(lev, f, uin, r, 0, zero);
-    mgk::k_adj_smooth<T><<<g, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B, is.P(lev),
-                                                 c->bw_partial);
-    accum(lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
-    mgk::k_adj_apply_a<T><<<g, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    if (const int bv = is.mbv()) {  // multi-rhs forms (B > 1)
+      is.with_bv(bv, [&](auto kk) {
+        constexpr int BV = decltype(kk)::value;
+        const dim3 gm = is.mb_grid(D.n, bv);
+        mgk::k_adj_smooth_mb<T, BV><<<gm, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B,
+                                                             is.P(lev), c->bw_partial);
+        accum(lev, 4, gm.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
+        mgk::k_adj_apply_a_mb<T, BV><<<gm, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+      });
+    } else {
+      mgk::k_adj_smooth<T><<<g, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B, is.P(lev),
+                                                   c->bw_partial);
+      accum(lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
+      mgk::k_adj_apply_a<T><<<g, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    }
     is.nk += 2;
   }
 
@@ -203,7 +214,14 @@ struct Backward {
     mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), fcbar, r, rbar, B, is.P(lev),
                                                     c->bw_partial);
     accum(lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
-    mgk::k_adj_apply_a<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    if (const int bv = is.mbv()) {
+      is.with_bv(bv, [&](auto kk) {
+        mgk::k_adj_apply_a_mb<T, decltype(kk)::value><<<is.mb_grid(D.n, bv), kThreads, 0, s>>>(
+            D.view(), ubar, rbar, fbar, B, 0);
+      });
+    } else {
+      mgk::k_adj_apply_a<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+    }
     is.nk += 2;
     // reverse: pre-smoothing
     for (int j = np - 1; j >= 0; --j) adj_step(lev, f, V(it[j]), zero_in && j == 0, ubar, fbar);
