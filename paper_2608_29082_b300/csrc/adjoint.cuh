@@ -147,10 +147,11 @@ __global__ void __launch_bounds__(kThreads) k_adj_apply_a(LV<T> L, T* __restrict
   fbar[t] = fbar_set ? rb : fbar[t] + rb;
 }
 
-// Restriction adjoint, fine rows: phibar = P rcbar, rbar = w1 phibar +
-// w2 M^T phibar; dots (wR1, wR2) with the residual r.
+// Restriction adjoint, fine rows: given pb = P rcbar (fine rows, computed by
+// the prolongation kernel), phibar = pb, rbar = w1 phibar + w2 M^T phibar;
+// dots (wR1, wR2) with the residual r.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __restrict__ rcbar,
+__global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __restrict__ pb,
                                                            const T* __restrict__ r,
                                                            T* __restrict__ rbar, int B,
                                                            const T* __restrict__ prm,
@@ -161,11 +162,11 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
     int i, b;
     split_rb(t, B, i, b);
     const T w1 = prm[P_WR1], w2 = prm[P_WR2];
-    const T phib = prolong_at(L, i, rcbar, B, b);
+    const T phib = pb[t];
     T mt = T(0), sr = T(0);
     for_nb<T, false>(L, i, [&](int c, T, bool nb) {
       const T w = nb ? L.invdeg[c] : T(0);
-      mt = fma(w, prolong_at(L, c, rcbar, B, b), mt);
+      mt = fma(w, pb[(size_t)c * B + b], mt);
       const T rv = r[(size_t)c * B + b];
       sr += nb ? rv : T(0);
     });
@@ -176,44 +177,38 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
   block_dots<2>(v, partial);
 }
 
-// Prolongation adjoint, coarse rows: ebar_I = sum_children P_iI (w1 ubar_i +
-// w2 (M^T ubar)_i).
+// Prolongation adjoint, fine rows: g_i = w1 ubar_i + w2 (M^T ubar)_i; the
+// coarse adjoint ebar = P^T g is then the restriction gather.
 template <class T>
-__global__ void __launch_bounds__(kThreads) k_adj_prolong(LV<T> L, const T* __restrict__ ubar,
-                                                          T* __restrict__ ebar, int B,
-                                                          const T* __restrict__ prm) {
+__global__ void __launch_bounds__(kThreads) k_adj_prolong_fine(LV<T> L, const T* __restrict__ ubar,
+                                                               T* __restrict__ g, int B,
+                                                               const T* __restrict__ prm) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)L.nc * B) return;
-  const int I = (int)(t / B), b = (int)(t - (size_t)I * B);
+  if (t >= (size_t)L.n * B) return;
+  int i, b;
+  split_rb(t, B, i, b);
   const T w1 = prm[P_WP1], w2 = prm[P_WP2];
-  T acc = T(0);
-  for (int k = 0; k < L.KR; ++k) {
-    const int i = L.r_idx[(size_t)k * L.nc + I];
-    if (i < 0) break;
-    const T g = fma(w1, ubar[(size_t)i * B + b], w2 * row_mt(L, i, ubar, B, b));
-    acc = fma(L.r_w[(size_t)k * L.nc + I], g, acc);
-  }
-  ebar[t] = acc;
+  g[t] = fma(w1, ubar[t], w2 * row_mt(L, i, ubar, B, b));
 }
 
-// Prolongation parameter dots, fine rows: <ubar, P e>, <ubar, M P e>.
+// Prolongation parameter dots, fine rows: <ubar, P e>, <ubar, M P e>, given
+// pe = P e (fine rows, computed by the prolongation kernel).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T* __restrict__ ubar,
-                                                               const T* __restrict__ ec, int B,
+                                                               const T* __restrict__ pe, int B,
                                                                double* __restrict__ partial) {
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   T v[2] = {T(0), T(0)};
   if (t < (size_t)L.n * B) {
     int i, b;
     split_rb(t, B, i, b);
-    const T pe = prolong_at(L, i, ec, B, b);
     T s = T(0);
     for_nb<T, false>(L, i, [&](int c, T, bool nb) {
-      const T pv = prolong_at(L, c, ec, B, b);
+      const T pv = pe[(size_t)c * B + b];
       s += nb ? pv : T(0);
     });
     const T ub = ubar[t];
-    v[0] = ub * pe;
+    v[0] = ub * pe[t];
     v[1] = ub * (L.invdeg[i] * s);
   }
   block_dots<2>(v, partial);

@@ -198,10 +198,14 @@ struct Backward {
     // prolongation: ebar = P^T Phi_P^T ubar, dots <ubar, P e>, <ubar, M P e>
     T* ebar = V(c->bw_ubar[lev + 1]);
     const dim3 gf = grid_for((size_t)D.n * B);
-    mgk::k_adj_prolong<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(D.view(), ubar, ebar, B,
-                                                                          is.P(lev));
-    mgk::k_adj_prolong_dots<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, ec, B, c->bw_partial);
-    is.nk += 2;
+    // g = Phi_P^T ubar per fine row, ebar = P^T g (the gather of the
+    // restriction), P e per fine row for the dots; D.t and D.u2 are free here
+    mgk::k_adj_prolong_fine<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, D.t, B, is.P(lev));
+    is.nk++;
+    is.op_gather(lev, D.t, ebar, 0);
+    is.op_pe(lev, ec, D.u2);
+    mgk::k_adj_prolong_dots<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, D.u2, B, c->bw_partial);
+    is.nk++;
     accum(lev, 2, gf.x, mgk::P_WP1, mgk::P_WP2, -1, -1);
     // coarse level (its input iterate is zero)
     T* fcbar = V(c->bw_fbar[lev + 1]);
@@ -211,7 +215,8 @@ struct Backward {
     T* r = V(c->bw_r[lev]);
     T* rbar = V(c->bw_rbar[lev]);
     is.op_residual(lev, f, V(it[np]), r, 0, zero_in && np == 0);
-    mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), fcbar, r, rbar, B, is.P(lev),
+    is.op_pe(lev, fcbar, D.t);  // P rcbar per fine row
+    mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), D.t, r, rbar, B, is.P(lev),
                                                     c->bw_partial);
     accum(lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
     if (const int bv = is.mbv()) {
