@@ -191,6 +191,26 @@ def vcycle(H: Hierarchy, p: Params, f: np.ndarray, u: np.ndarray) -> np.ndarray:
     return lmg(H, p, 0, f, u)
 
 
+def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:
+    """Full multigrid (nested iteration), the preconditioner of the Sec. 5
+    Krylov experiments.  The right-hand side goes to every level through the
+    cycle's restriction P^T Phi_R; the coarsest level is solved exactly; on
+    each finer level the coarser solution, through the cycle's prolongation
+    Phi_P P, is the initial guess of one V-cycle (Algorithm 2 started on that
+    level).  One V-cycle per level, as in the paper."""
+    J = H.J
+    fs = [f]
+    for lev in range(J - 1):
+        L = H.levels[lev]
+        fs.append(L.P.T @ conv(L, fs[lev], p.wR[lev][0], p.wR[lev][1]))
+    u = sla.cho_solve(H.chol, fs[J - 1])
+    for lev in range(J - 2, -1, -1):
+        L = H.levels[lev]
+        u0 = conv(L, L.P @ u, p.wP[lev][0], p.wP[lev][1])
+        u = lmg(H, p, lev, fs[lev], u0)
+    return u
+
+
 def residual(H: Hierarchy, f, u):
     return f - H.levels[0].A @ u
 

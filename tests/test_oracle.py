@@ -148,6 +148,64 @@ def dense_error_propagation(H, p):
     return E
 
 
+def dense_fmg(H, p):
+    """Full multigrid as dense matrices: f_l = P^T Phi_R f_{l-1}; u_{J-1} =
+    A_{J-1}^{-1} f_{J-1}; on level l one V-cycle from u0 = Phi_P P u_{l+1}, i.e.
+    u_l = E_l u0 + (I - E_l) A_l^{-1} f_l with E_l the error propagation of
+    the V-cycle started on level l (E_{J-1} = 0).  Returns the matrix f -> u."""
+    J = H.J
+    mats = []
+    E = np.zeros((H.levels[-1].A.shape[0],) * 2)
+    Es = [None] * J
+    Es[J - 1] = E
+    for lev in range(J - 2, -1, -1):  # E_l, the same recursion as dense_error_propagation
+        L, Lc = H.levels[lev], H.levels[lev + 1]
+        A = L.A.toarray()
+        n = A.shape[0]
+        Ag = L.inv_deg[:, None] * L.G.toarray()
+        phi = lambda w: w[0] * np.eye(n) + w[1] * Ag  # noqa: E731
+        S = np.eye(n) - p.eta[lev] * p.theta[lev] * phi(p.wB[lev]) @ (A / L.diag[:, None])
+        P = L.P.toarray()
+        Ac = Lc.A.toarray()
+        C = phi(p.wP[lev]) @ P @ (np.eye(Ac.shape[0]) - Es[lev + 1]) @ np.linalg.solve(
+            Ac, P.T @ phi(p.wR[lev]) @ A)
+        Es[lev] = np.linalg.matrix_power(S, p.nu_post) @ (np.eye(n) - C) @ \
+            np.linalg.matrix_power(S, p.nu_pre)
+    # restriction of f to every level
+    Rs = [np.eye(H.levels[0].A.shape[0])]
+    for lev in range(J - 1):
+        L = H.levels[lev]
+        n = L.A.shape[0]
+        phiR = p.wR[lev][0] * np.eye(n) + p.wR[lev][1] * (L.inv_deg[:, None] * L.G.toarray())
+        Rs.append(L.P.toarray().T @ phiR @ Rs[lev])
+    M = np.linalg.solve(H.levels[J - 1].A.toarray(), Rs[J - 1])
+    for lev in range(J - 2, -1, -1):
+        L = H.levels[lev]
+        A = L.A.toarray()
+        n = A.shape[0]
+        phiP = p.wP[lev][0] * np.eye(n) + p.wP[lev][1] * (L.inv_deg[:, None] * L.G.toarray())
+        U0 = phiP @ L.P.toarray() @ M
+        M = Es[lev] @ U0 + (np.eye(n) - Es[lev]) @ np.linalg.solve(A, Rs[lev])
+    return M
+
+
+@pytest.mark.parametrize("which", ["identity", "random"])
+def test_fmg_matches_dense_nested_iteration(poisson33, checker17, which):
+    """Full multigrid (Sec. 5 preconditioner) against its dense construction
+    from the per-level error propagation matrices, on Poisson and on a jump
+    coefficient; and it is linear in f."""
+    for case, seed in ((poisson33, 5), (checker17, 6)):
+        prob, H = case
+        th = O.Params.identity(H.J) if which == "identity" else random_params(H.J, seed)
+        n = H.levels[0].A.shape[0]
+        f = np.random.default_rng(seed).standard_normal((n, 2))
+        got = O.fmg(H, th, f)
+        ref = dense_fmg(H, th) @ f
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        g2 = O.fmg(H, th, 2.0 * f[:, :1] - 3.0 * f[:, 1:])
+        assert np.abs(g2 - (2.0 * got[:, :1] - 3.0 * got[:, 1:])).max() <= 1e-12 * np.abs(got).max()
+
+
 @pytest.mark.parametrize("which", ["identity", "random"])
 def test_vcycle_matches_dense_error_propagation(poisson33, which):
     p, H = poisson33
