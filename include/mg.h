@@ -163,6 +163,16 @@ mg_status mg_set_params(mg_ctx* ctx, const mg_params* p);
  * must not overlap.  1 <= nrhs <= max_batch. */
 mg_status mg_vcycle(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, void* stream);
 
+/* One full multigrid (nested iteration) application, the preconditioner of
+ * the paper's Sec. 5 Krylov experiments: f is restricted to every level with
+ * the cycle's restriction P^T Phi_R, the coarsest level is solved exactly,
+ * and on each finer level the coarser solution, prolongated with the cycle's
+ * Phi_P P, is the initial guess of one V-cycle (Algorithm 2 started on that
+ * level).  u_dev receives the result (its input is not read); f_dev, u_dev:
+ * [n_0][nrhs] in the context precision, not overlapping; 1 <= nrhs <=
+ * max_batch.  Uses the context's level buffers (not thread-safe). */
+mg_status mg_fmg(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, void* stream);
+
 /* Solves A u = f to ||f - A u||_2 / ||f||_2 < tol for every right-hand side.
  * f_dev, u_dev: FP64 [n_0][nrhs] on the device; u_dev holds the initial guess.
  * precision 64: u <- LMG(f, u) repeated (plain stationary multigrid);
@@ -242,13 +252,18 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     is at least H rows, tile plus halos fit in 48 KB for
  *                     the batch, and the first stage over all tiles fits in
  *                     one wave of the GPU; otherwise the two-kernel form.
- *                     Other values than [0, 2^30]: MG_ERR_INVALID. */
+ *                     Other values than [0, 2^30]: MG_ERR_INVALID.
+ *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg: 0 (default) one
+ *                     V-cycle from zero, 1 one full multigrid (mg_fmg).  This
+ *                     option changes results (another preconditioner); the
+ *                     others only change launch shapes. */
 typedef enum {
   MG_OPT_TAIL_WORK = 0,
   MG_OPT_PDL = 1,
   MG_OPT_MULTI_RHS = 2,
   MG_OPT_DEVICE_LOOP = 3,
-  MG_OPT_HALO_ROWS = 4
+  MG_OPT_HALO_ROWS = 4,
+  MG_OPT_FCG_PRECOND = 5
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

@@ -65,7 +65,8 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
   c->solve_ctl[1] = (double)max_iter;
   MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
 
-  // z = M(r): one V-cycle from zero on the (scaled) residual
+  // z = M(r): one V-cycle from zero, or one full multigrid
+  // (MG_OPT_FCG_PRECOND), on the (scaled) residual
   auto precondition = [&](cudaStream_t cs) {
     int nk = 0;
     if (p32) {
@@ -73,13 +74,19 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
       is0.launch(mgk::k_scale_to_f32, grid_for(N), dim3(kThreads), 0, (const double*)c->k_r,
                  (const int*)c->sexp, c->rhat32, n0, (int)B);
       Issue<float> is{c, c->d32, c->prm32, cs, B};
-      is.vcycle(c->rhat32, c->c32, true);
+      if (c->opt_fcg_precond == 1)
+        is.fmg(c->rhat32, c->c32);
+      else
+        is.vcycle(c->rhat32, c->c32, true);
       is.launch(mgk::k_scale_from_f32, grid_for(N), dim3(kThreads), 0, (const float*)c->c32,
                 (const int*)c->sexp, c->k_z, n0, (int)B);
       nk += is0.nk + is.nk;
     } else {
       Issue<double> is{c, c->d64, c->prm64, cs, B};
-      is.vcycle(c->k_r, c->k_z, true);
+      if (c->opt_fcg_precond == 1)
+        is.fmg(c->k_r, c->k_z);
+      else
+        is.vcycle(c->k_r, c->k_z, true);
       nk += is.nk;
     }
     return nk;

@@ -287,6 +287,7 @@ struct mg_ctx {
   int opt_pdl = 1;               // programmatic dependent launch between kernels
   int opt_multi_rhs = 1;         // multi-rhs kernels: 0 off, 1 widest tile, else max tile
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
+  int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
   int64_t wave_threads = 148 * 2048;  // SMs x resident threads per SM (set in mg_setup)
   // training state (device buffers in the context precision)
@@ -745,7 +746,8 @@ struct Issue {
   // First level handled by the single-block tail for this batch size (J-1:
   // no tail, only the coarse solve).
   // Small-level arguments for every level (lt chosen by the caller).
-  void tail_args(mgk::TailArgs<T>& a, const T* f0, T* u0, bool u0_zero) const {
+  // l0: the level whose vectors are (f0, u0) (the cycle's first level).
+  void tail_args(mgk::TailArgs<T>& a, const T* f0, T* u0, bool u0_zero, int l0 = 0) const {
     std::memset(&a, 0, sizeof(a));
     a.J = c->J;
     a.B = B;
@@ -758,8 +760,8 @@ struct Issue {
       a.L[l] = L[l].view();
       a.nsl[l] = L[l].ndia > 0 ? 0 : L[l].nsl;
       a.nent[l] = L[l].ndia > 0 ? 0 : (int)L[l].nent;
-      a.f[l] = l == 0 ? f0 : Fl(l);
-      a.u[l] = l == 0 ? u0 : Ul(l);
+      a.f[l] = l == l0 ? f0 : Fl(l);
+      a.u[l] = l == l0 ? u0 : Ul(l);
       a.t[l] = L[l].t;
       a.u2[l] = L[l].u2;
       if (l < c->J - 1) {
@@ -792,11 +794,11 @@ struct Issue {
     return lt;
   }
 
-  void tail(int lt, const T* f0, T* u0, bool u0_zero) {
+  void tail(int lt, const T* f0, T* u0, bool u0_zero, int l0 = 0) {
     mgk::TailArgs<T> a;
-    tail_args(a, f0, u0, u0_zero);
+    tail_args(a, f0, u0, u0_zero, l0);
     a.lt = lt;
-    if (lt > 0) a.lt_zero = 1;  // coarse levels start from zero
+    if (lt > l0) a.lt_zero = 1;  // levels below the cycle's first start from zero
     pre(MG_K_TAIL, lt);
     launch(mgk::k_tail<T>, dim3(1), dim3(mgk::kTailThreads), mgk::tail_smem_bytes<T>(a, lt), a);
     post();
@@ -808,24 +810,70 @@ struct Issue {
   T* Fl(int lev) const { return fov ? fov[lev] : L[lev].f; }
   T* Ul(int lev) const { return uov ? uov[lev] : L[lev].u; }
 
-  void vcycle(const T* f0, T* u0, bool u0_zero) {
+  void vcycle(const T* f0, T* u0, bool u0_zero) { vcycle_from(0, f0, u0, u0_zero); }
+
+  // Algorithm 2 started on level l0 with right-hand side f0 and iterate u0
+  // (the vectors of levels below l0 are the level buffers).
+  void vcycle_from(int l0, const T* f0, T* u0, bool u0_zero) {
     const int J = c->J;
-    const int lt = tail_level();
-    for (int lev = 0; lev < lt; ++lev) {
-      const T* f = lev == 0 ? f0 : Fl(lev);
-      T* u = lev == 0 ? u0 : Ul(lev);
-      smooth(lev, f, u, c->nu_pre, lev == 0 ? u0_zero : true);
+    if (l0 == J - 1) {  // the coarsest level: the exact solve
+      coarse(f0, u0);
+      return;
+    }
+    const int lt = std::max(tail_level(), l0);
+    for (int lev = l0; lev < lt; ++lev) {
+      const T* f = lev == l0 ? f0 : Fl(lev);
+      T* u = lev == l0 ? u0 : Ul(lev);
+      smooth(lev, f, u, c->nu_pre, lev == l0 ? u0_zero : true);
       restrict_(lev, f, u);
     }
     if (lt < J - 1)
-      tail(lt, f0, u0, u0_zero);
+      tail(lt, lt == l0 ? f0 : Fl(lt), lt == l0 ? u0 : Ul(lt), lt == l0 ? u0_zero : true, lt);
     else
       coarse(Fl(J - 1), Ul(J - 1));
-    for (int lev = lt - 1; lev >= 0; --lev) {
-      const T* f = lev == 0 ? f0 : Fl(lev);
-      T* u = lev == 0 ? u0 : Ul(lev);
+    for (int lev = lt - 1; lev >= l0; --lev) {
+      const T* f = lev == l0 ? f0 : Fl(lev);
+      T* u = lev == l0 ? u0 : Ul(lev);
       prolong(lev, Ul(lev + 1), u);
       smooth(lev, f, u, c->nu_post, false);
+    }
+  }
+
+  // f_{l+1} = P^T Phi_R(f_l) into the level buffer Fl(lev + 1): the cycle's
+  // restriction applied to a right-hand side.
+  void restrict_f(int lev, const T* f) {
+    DevLevel<T>& D = L[lev];
+    if (conv(lev, mgk::P_WR2)) {
+      pre(MG_K_CONV_R, lev);
+      op_conv_r(lev, f, D.u2);
+      post();
+      pre(MG_K_RESTRICT, lev);
+      op_gather(lev, D.u2, Fl(lev + 1), 0);
+      post();
+    } else {
+      pre(MG_K_RESTRICT, lev);
+      op_gather(lev, f, Fl(lev + 1), 1);
+      post();
+    }
+  }
+
+  // Full multigrid (nested iteration, the preconditioner of the paper's
+  // Sec. 5 Krylov experiments): f restricted to every level by the cycle's
+  // restriction, the coarsest level solved exactly, then on each finer level
+  // the coarser solution through the cycle's prolongation (Phi_P P, from a
+  // zero iterate) is the initial guess of one V-cycle started on that level.
+  // The V-cycle on level l reuses the buffers of levels > l, whose FMG
+  // values (f_{l+1}, u_{l+1}) are consumed by then.
+  void fmg(const T* f0, T* u0) {
+    const int J = c->J;
+    for (int lev = 0; lev < J - 1; ++lev) restrict_f(lev, lev == 0 ? f0 : Fl(lev));
+    coarse(Fl(J - 1), Ul(J - 1));
+    for (int lev = J - 2; lev >= 0; --lev) {
+      const T* f = lev == 0 ? f0 : Fl(lev);
+      T* u = lev == 0 ? u0 : Ul(lev);
+      cudaMemsetAsync(u, 0, (size_t)L[lev].n * B * sizeof(T), s);
+      prolong(lev, Ul(lev + 1), u);
+      vcycle_from(lev, f, u, false);
     }
   }
 };
@@ -1238,6 +1286,27 @@ extern "C" mg_status mg_vcycle(mg_ctx* c, const void* f, void* u, int32_t B, voi
   });
 }
 
+extern "C" mg_status mg_fmg(mg_ctx* c, const void* f, void* u, int32_t B, void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_fmg: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB) return c->fail(MG_ERR_INVALID, "mg_fmg: bad arguments");
+  if (f == u) return c->fail(MG_ERR_INVALID, "mg_fmg: f and u must not alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  auto key = std::make_tuple(6, f, (const void*)u, (int)B, c->structure);
+  if (c->prec == 64)
+    return run_graph(c, key, s, [&](cudaStream_t cs) {
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
+      is.fmg((const double*)f, (double*)u);
+      return is.nk;
+    });
+  return run_graph(c, key, s, [&](cudaStream_t cs) {
+    Issue<float> is{c, c->d32, c->prm32, cs, B};
+    is.fmg((const float*)f, (float*)u);
+    return is.nk;
+  });
+}
+
 namespace {
 
 __global__ void k_init_solve(const double* __restrict__ fsum, int B, int* __restrict__ active,
@@ -1535,6 +1604,11 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       break;
     case MG_OPT_DEVICE_LOOP:
       c->opt_device_loop = value != 0;
+      break;
+    case MG_OPT_FCG_PRECOND:
+      if (value != 0 && value != 1)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: FCG preconditioner must be 0 or 1");
+      c->opt_fcg_precond = (int)value;
       break;
     case MG_OPT_HALO_ROWS:
       if (value < 0 || value > (1 << 30))

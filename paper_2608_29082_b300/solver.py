@@ -144,6 +144,15 @@ class Solver:
                                    f2.shape[1], _stream_handle()), self.ctx)
         return u
 
+    def fmg(self, f: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+        """u <- one full multigrid application (nested iteration) on f; u's
+        input is not read (context precision)."""
+        f2 = self._vec(f, self.n[0], self.dtype, "f")
+        u2 = self._vec(u, self.n[0], self.dtype, "u")
+        L.check(self.lib.mg_fmg(self.ctx, C.c_void_p(f2.data_ptr()), C.c_void_p(u2.data_ptr()),
+                                f2.shape[1], _stream_handle()), self.ctx)
+        return u
+
     def solve(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-8,
               max_iter: int = 100, method: str = "refine") -> tuple[torch.Tensor, SolveInfo]:
         """FP64 f, u (u = initial guess, zero if None) -> (u, info).
@@ -203,8 +212,9 @@ class Solver:
                 for k in range(n.value)]
 
     def set_option(self, name: str, value: int):
-        """Launch-shape options ("tail_work", "pdl", "multi_rhs", "device_loop"); results are
-        bitwise unchanged."""
+        """Launch-shape options ("tail_work", "pdl", "multi_rhs", "device_loop",
+        "halo_rows"; results bitwise unchanged) and the flexible-CG
+        preconditioner ("fcg_precond": 0 V-cycle, 1 full multigrid)."""
         L.check(self.lib.mg_set_option(self.ctx, L.OPTIONS[name], int(value)), self.ctx)
 
     # ------------------------------------------------------------ training
