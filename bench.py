@@ -279,9 +279,17 @@ def run_ours(args):
     u32 = u.clone()
     # the same learned cycle as preconditioner of flexible CG (FP64 outer)
     msfcg, infofcg, nkfcg = timed(S32, method="fcg")
+    # classical (identity) Theta as the FP32 preconditioner of flexible CG:
+    # one V-cycle, and one full multigrid (nested iteration)
+    S32c = lmg.Solver(hier, plain, precision=32, max_batch=1)
+    msccg, infoccg, _ = timed(S32c, method="fcg")
+    S32c.set_option("fcg_precond", 1)
+    msfmg, infofmg, nkfmg = timed(S32c, method="fcg")
+    S32c.close()
     # max over ranks
     if pg:
-        ms32, ms64, msfcg = max_over_ranks([ms32, ms64, msfcg], pg, dev)
+        ms32, ms64, msfcg, msccg, msfmg = max_over_ranks([ms32, ms64, msfcg, msccg, msfmg], pg,
+                                                         dev)
 
     # end to end through the public host API (pinned host buffers)
     fh = torch.tensor(prob.f, dtype=torch.float64).pin_memory().numpy()
@@ -372,12 +380,18 @@ def run_ours(args):
             "learned_fcg_ms": round(msfcg, 4),
             "learned_fcg_iters": int(infofcg.iters[0]),
             "learned_fcg_relres": float(infofcg.relres[0]),
+            "classical_fp32_fcg_ms": round(msccg, 4),
+            "classical_fp32_fcg_iters": int(infoccg.iters[0]),
+            "classical_fp32_fcg_fmg_ms": round(msfmg, 4),
+            "classical_fp32_fcg_fmg_iters": int(infofmg.iters[0]),
+            "classical_fp32_fcg_fmg_relres": float(infofmg.relres[0]),
             "speedup_vs_plain_fp64": round(ms64 / ms32, 3),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms/solve",
                     "h2d_bytes_per_step": int(2 * fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)},
             "gpu_launches": int(nk32),
             "gpu_launches_by_region": {"learned_refinement": int(nk32), "plain_fp64": int(nk64),
-                                       "learned_fcg": int(nkfcg)},
+                                       "learned_fcg": int(nkfcg),
+                                       "classical_fcg_fmg": int(nkfmg)},
             "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),

@@ -155,6 +155,9 @@ def run_lshape(a):
     ms32, info32, u32 = timed_solve(S32, f64, a.tol)
     kt32, cyc32 = kernel_table(S32, hier, f64.float())
     msf32, infof32, uf32 = timed_solve(S32, f64, a.tol, method="fcg")
+    S32.set_option("fcg_precond", 1)  # full multigrid as the preconditioner
+    msg32, infog32, ug32 = timed_solve(S32, f64, a.tol, method="fcg")
+    S32.set_option("fcg_precond", 0)
     S64 = Solver(hier, plain, precision=64, max_batch=a.batch)
     ms64, info64, _ = timed_solve(S64, f64, a.tol)
     msf64, infof64, _ = timed_solve(S64, f64, a.tol, method="fcg")
@@ -169,6 +172,7 @@ def run_lshape(a):
         return np.sqrt((r * r).sum(0)) / np.sqrt((prob.f * prob.f).sum(0))
     rr = oracle_relres(u32)
     rrf = oracle_relres(uf32)
+    rrg = oracle_relres(ug32)
     out = {"workload": f"L-shape anisotropic, {a.refinements} red refinements, {hier.sizes[0]} DOF, "
                        f"{J} levels, {a.batch} rhs, tol {a.tol}",
            "levels": hier.sizes, "generate_s": round(t_gen, 1), "setup_s": round(t_setup, 1),
@@ -178,6 +182,9 @@ def run_lshape(a):
            "speedup": round(ms64 / ms32, 3), "oracle_max_relres": float(rr.max()),
            "learned_fp32_fcg_ms": round(msf32, 3), "learned_fcg_iters": int(infof32.iters.max()),
            "oracle_max_relres_fcg": float(rrf.max()),
+           "learned_fp32_fcg_fmg_ms": round(msg32, 3),
+           "learned_fcg_fmg_iters": int(infog32.iters.max()),
+           "oracle_max_relres_fcg_fmg": float(rrg.max()),
            "plain_fp64_fcg_ms": round(msf64, 3), "plain_fcg_iters": int(infof64.iters.max()),
            "speedup_fcg_learned_vs_plain_stationary": round(ms64 / msf32, 3),
            "cycle_us_fp32_profiled": round(cyc32, 1), "cycle_us_fp64_profiled": round(cyc64, 1),
