@@ -211,6 +211,61 @@ def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:
     return u
 
 
+def fgmres(A, f: np.ndarray, precond, tol: float, restart: int = 30, max_iter: int = 300):
+    """Restarted flexible GMRES with right preconditioning (Saad 1993), the
+    outer Krylov method the paper pairs with its V-cycle and FMG
+    preconditioners (Sec. 5), for one right-hand side f (1-D).  precond(v)
+    returns z ~ A^{-1} v and may change between calls.  Modified Gram-Schmidt
+    Arnoldi, Givens rotations on the Hessenberg matrix; stops when the
+    recurrence's residual estimate |g_{j+1}| < tol ||f||, or after max_iter
+    inner steps.  Returns (u, iterations, residual estimates per step)."""
+    n = f.shape[0]
+    u = np.zeros(n)
+    fn = np.linalg.norm(f)
+    hist, its = [], 0
+    while its < max_iter:
+        r = f - A @ u
+        beta = np.linalg.norm(r)
+        if beta < tol * fn:
+            break
+        V = np.zeros((n, restart + 1))
+        Z = np.zeros((n, restart))
+        Hm = np.zeros((restart + 1, restart))
+        cs, sn = np.zeros(restart), np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        V[:, 0] = r / beta
+        jl = -1
+        for j in range(restart):
+            Z[:, j] = precond(V[:, j])
+            w = A @ Z[:, j]
+            for i in range(j + 1):
+                Hm[i, j] = w @ V[:, i]
+                w = w - Hm[i, j] * V[:, i]
+            Hm[j + 1, j] = np.linalg.norm(w)
+            if Hm[j + 1, j] > 0:
+                V[:, j + 1] = w / Hm[j + 1, j]
+            for i in range(j):
+                t = cs[i] * Hm[i, j] + sn[i] * Hm[i + 1, j]
+                Hm[i + 1, j] = -sn[i] * Hm[i, j] + cs[i] * Hm[i + 1, j]
+                Hm[i, j] = t
+            rr = np.hypot(Hm[j, j], Hm[j + 1, j])
+            cs[j], sn[j] = (Hm[j, j] / rr, Hm[j + 1, j] / rr) if rr > 0 else (1.0, 0.0)
+            Hm[j, j], Hm[j + 1, j] = rr, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            its += 1
+            jl = j
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) < tol * fn or its >= max_iter:
+                break
+        y = np.linalg.solve(np.triu(Hm[:jl + 1, :jl + 1]), g[:jl + 1])
+        u = u + Z[:, :jl + 1] @ y
+        if hist and hist[-1] < tol * fn:
+            break
+    return u, its, np.array(hist)
+
+
 def residual(H: Hierarchy, f, u):
     return f - H.levels[0].A @ u
 

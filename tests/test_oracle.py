@@ -362,3 +362,37 @@ def test_shared_weight_gradient_is_sum_over_levels(checker17):
     x[:, 5] += 1e-30j  # wR2 at every level
     lc = O.unrolled_loss(H, O.Params.from_flat(x.ravel()), p.f.astype(np.complex128), 2)
     assert abs(np.imag(lc) / 1e-30 - g[:, 5].sum()) < 1e-12 * max(1.0, abs(g[:, 5]).sum())
+
+
+def test_fgmres_reduces_to_gmres_and_exact_preconditioner(poisson33):
+    """Without preconditioning the oracle's FGMRES is GMRES: its residual
+    estimates equal scipy's GMRES residual history (restart 20); with the
+    exact inverse as preconditioner it converges in one step."""
+    p, H = poisson33
+    A = H.levels[0].A.tocsc()
+    f = p.f[:, 0]
+    u, its, hist = O.fgmres(A, f, lambda v: v, 1e-8, restart=20, max_iter=60)
+    ref = []
+    spla.gmres(A, f, rtol=1e-8, restart=20, maxiter=3, callback=lambda x: ref.append(x),
+               callback_type="pr_norm")
+    ref = np.array(ref) * np.linalg.norm(f)  # scipy reports ||r|| / ||f||
+    k = min(len(ref), len(hist), 40)
+    assert k >= 20
+    assert np.abs(hist[:k] - ref[:k]).max() <= 1e-10 * np.linalg.norm(f)
+    # at the end of a restart cycle the estimate is the true residual
+    assert abs(np.linalg.norm(f - A @ u) - hist[-1]) <= 1e-10 * np.linalg.norm(f)
+    lu = spla.splu(A)
+    u1, its1, _ = O.fgmres(A, f, lu.solve, 1e-10, restart=5, max_iter=10)
+    assert its1 == 1 and np.linalg.norm(f - A @ u1) < 1e-10 * np.linalg.norm(f)
+
+
+def test_fgmres_with_fmg_preconditioner(checker17):
+    """FGMRES with the learnable FMG (random Theta, a nonsymmetric
+    preconditioner) converges to the tolerance."""
+    p, H = checker17
+    th = random_params(H.J, 9)
+    A = H.levels[0].A
+    f = p.f[:, 0]
+    u, its, hist = O.fgmres(A, f, lambda v: O.fmg(H, th, v[:, None])[:, 0], 1e-10, restart=10)
+    assert np.linalg.norm(f - A @ u) < 1e-9 * np.linalg.norm(f)
+    assert its < 60
