@@ -192,6 +192,22 @@ mg_status mg_solve(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs
  * relres reported is that of the true residual f - A u of the final iterate.
  * Krylov acceleration of the cycle is the paper's preconditioner use (Sec. 4.2),
  * with flexible CG in place of FGMRES for SPD operators. */
+/* Restarted flexible GMRES, FGMRES(restart) with right preconditioning
+ * (Saad 1993), the outer Krylov method the paper uses with its V-cycle and
+ * FMG preconditioners (Sec. 5): FP64 Arnoldi (classical Gram-Schmidt applied
+ * twice), Givens rotations per right-hand side, the preconditioner one
+ * V-cycle from zero or one full multigrid (MG_OPT_FCG_PRECOND) in the
+ * context precision.  Arguments and results as mg_solve; u_dev is the
+ * initial guess; 1 <= restart <= 64; max_iter counts Arnoldi steps (one
+ * preconditioner application each, shared by the batch).  Each right-hand
+ * side stops updating once its true residual meets tol at a restart.  The
+ * host reads the convergence counts after every step (one synchronisation
+ * per step).  Workspace: (2 restart + 1) vectors of [n_0][max_batch] FP64,
+ * allocated on first use. */
+mg_status mg_solve_fgmres(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs,
+                          double tol, int32_t max_iter, int32_t restart, int32_t* iters_out,
+                          double* relres_out, void* stream);
+
 mg_status mg_solve_fcg(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
                        int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
 
@@ -253,8 +269,9 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     the batch, and the first stage over all tiles fits in
  *                     one wave of the GPU; otherwise the two-kernel form.
  *                     Other values than [0, 2^30]: MG_ERR_INVALID.
- *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg: 0 (default) one
- *                     V-cycle from zero, 1 one full multigrid (mg_fmg).  This
+ *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg and mg_solve_fgmres:
+ *                     0 (default) one V-cycle from zero, 1 one full
+ *                     multigrid (mg_fmg).  This
  *                     option changes results (another preconditioner); the
  *                     others only change launch shapes. */
 typedef enum {

@@ -78,6 +78,8 @@ def lib() -> C.CDLL:
         "mg_fmg": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_solve": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
         "mg_solve_fcg": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
+        "mg_solve_fgmres": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, i32p, f64p,
+                             vp], C.c_int),
         "mg_solve_host": ([vp, f64p, f64p, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp],
                           C.c_int),
         "mg_level_apply": ([vp, C.c_int32, C.c_int32, vp, vp, vp, C.c_int32, vp], C.c_int),

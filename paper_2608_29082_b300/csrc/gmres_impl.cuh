@@ -1,0 +1,212 @@
+// mg_solve_fgmres: restarted flexible GMRES (gmres.cuh) with the learnable
+// V-cycle or full multigrid as the right preconditioner.  Included at the end
+// of mg_api.cu (same translation unit), after krylov_impl.cuh.
+//
+// The host drives the restart cycle: a restart graph (true residual, beta,
+// v_0), one graph per Arnoldi step j (preconditioner, A z_j, CGS2, the
+// rotations), and an end-of-cycle graph (y, u += Z y).  After the restart
+// and after every step the host reads the convergence counts.
+
+namespace {
+
+mg_status gm_buffers(mg_ctx* c, int m) {
+  if (c->gm_m == m && c->gm_V) return MG_OK;
+  // graphs captured earlier point at the old workspace
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+  c->graphs.clear();
+  for (void* p : {(void*)c->gm_V, (void*)c->gm_Z, (void*)c->gm_small, (void*)c->gm_h,
+                  (void*)c->gm_vec, (void*)c->gm_partial, (void*)c->gm_zexp})
+    if (p) cudaFree(p);
+  c->gm_V = c->gm_Z = c->gm_small = c->gm_h = c->gm_vec = c->gm_partial = nullptr;
+  c->gm_zexp = nullptr;
+  c->gm_m = 0;
+  const size_t v = (size_t)c->n[0] * c->maxB * sizeof(double);
+  const size_t nblk = ((size_t)c->n[0] + mgk::kRedRows - 1) / mgk::kRedRows;
+  const size_t mb = (size_t)c->maxB;
+  MG_CUDA(cudaMalloc(&c->gm_V, v * (m + 1)));
+  MG_CUDA(cudaMalloc(&c->gm_Z, v * m));
+  MG_CUDA(cudaMalloc(&c->gm_small, mb * mgk::gm_stride(m) * sizeof(double)));
+  MG_CUDA(cudaMalloc(&c->gm_h, 2 * (m + 1) * mb * sizeof(double)));
+  MG_CUDA(cudaMalloc(&c->gm_vec, 2 * mb * sizeof(double)));
+  MG_CUDA(cudaMalloc(&c->gm_partial, nblk * (m + 1) * mb * sizeof(double)));
+  MG_CUDA(cudaMalloc(&c->gm_zexp, mb * sizeof(int)));
+  MG_CUDA(cudaMemset(c->gm_zexp, 0, mb * sizeof(int)));
+  c->gm_m = m;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
+                                     int32_t max_iter, int32_t restart, int32_t* iters_out,
+                                     double* relres_out, void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve_fgmres: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB || max_iter < 0 || !(tol > 0.0) || restart < 1 ||
+      restart > 64)
+    return c->fail(MG_ERR_INVALID, "mg_solve_fgmres: bad arguments");
+  if ((const void*)f == (const void*)u)
+    return c->fail(MG_ERR_INVALID, "mg_solve_fgmres: f and u alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  st = fcg_buffers(c);
+  if (st != MG_OK) return st;
+  const int m = restart;
+  st = gm_buffers(c, m);
+  if (st != MG_OK) return st;
+  const int n0 = c->n[0];
+  const int bt = std::min((int)B, 32);  // reduction tiling (kernels.cuh red_tile)
+  const int nblk = (n0 + mgk::kRedRows - 1) / mgk::kRedRows;
+  const dim3 rgrid(nblk, (B + bt - 1) / bt), rblock(mgk::kRedRows * bt);
+  const LV<double> L0 = c->d64[0].view();
+  const bool p32 = c->prec == 32;
+  const size_t N = (size_t)n0 * B;
+  const size_t vs = N;  // stride between basis vectors
+  double* h1 = c->gm_h;
+  double* h2 = c->gm_h + (size_t)(m + 1) * B;
+  double* wn = c->gm_vec;
+  double* inv = c->gm_vec + B;
+  c->solve_ctl[0] = tol;
+  c->solve_ctl[1] = (double)max_iter;
+  MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
+  auto key = [&](int id) {
+    return std::make_tuple(id, (const void*)f, (const void*)u, (int)B, c->structure);
+  };
+  auto read_state = [&]() -> mg_status {
+    MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    MG_CUDA(cudaStreamSynchronize(s));
+    return MG_OK;
+  };
+
+  // ||f||, every right-hand side active, no iterations yet
+  st = run_graph(c, key(7000), s, [&](cudaStream_t cs) {
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->fsum);
+    is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B, c->active,
+              c->iters, c->sexp);
+    return is.nk;
+  });
+  if (st != MG_OK) return st;
+  int total = 0;
+  bool diverged = false;
+  for (;;) {
+    // restart: r = f - A u, beta = ||r||, the test, v_0 = r / beta
+    st = run_graph(c, key(7001), s, [&](cudaStream_t cs) {
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
+      is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u, c->k_r,
+                (int)B);
+      is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r, (const double*)c->k_r,
+                (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
+      is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+                c->rsum);
+      is.launch(mgk::k_gm_restart, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+                (const double*)c->fsum, (const double*)c->tol_dev, m, (int)B, c->active,
+                c->relres, c->gm_small, inv, c->state);
+      is.launch(mgk::k_gm_scale, grid_for(N), dim3(kThreads), 0, (const double*)c->k_r,
+                (const double*)inv, c->gm_V, n0, (int)B);
+      return is.nk;
+    });
+    if (st != MG_OK) return st;
+    if ((st = read_state()) != MG_OK) return st;
+    if (c->h_state[1]) {
+      diverged = true;
+      break;
+    }
+    if (c->h_state[0] == 0 || total >= max_iter) break;
+    int jl = -1;
+    for (int j = 0; j < m && total < max_iter; ++j) {
+      st = run_graph(c, key(7100 + j), s, [&](cudaStream_t cs) {
+        double* Vj = c->gm_V + (size_t)j * vs;
+        double* Vn = c->gm_V + (size_t)(j + 1) * vs;
+        double* Zj = c->gm_Z + (size_t)j * vs;
+        int nk = 0;
+        // z_j = M(v_j) (||v_j|| = 1, so the FP32 copy needs no scaling)
+        if (p32) {
+          Issue<double> is0{c, c->d64, c->prm64, cs, B};
+          is0.launch(mgk::k_scale_to_f32, grid_for(N), dim3(kThreads), 0, (const double*)Vj,
+                     (const int*)c->gm_zexp, c->rhat32, n0, (int)B);
+          Issue<float> is{c, c->d32, c->prm32, cs, B};
+          if (c->opt_fcg_precond == 1)
+            is.fmg(c->rhat32, c->c32);
+          else
+            is.vcycle(c->rhat32, c->c32, true);
+          is.launch(mgk::k_scale_from_f32, grid_for(N), dim3(kThreads), 0, (const float*)c->c32,
+                    (const int*)c->gm_zexp, Zj, n0, (int)B);
+          nk += is0.nk + is.nk;
+        } else {
+          Issue<double> is{c, c->d64, c->prm64, cs, B};
+          if (c->opt_fcg_precond == 1)
+            is.fmg(Vj, Zj);
+          else
+            is.vcycle(Vj, Zj, true);
+          nk += is.nk;
+        }
+        Issue<double> is2{c, c->d64, c->prm64, cs, B};
+        // w = A z_j, in the slot of v_{j+1}
+        is2.launch(mgk::k_spmv_dots, rgrid, rblock, 0, L0, (const double*)Zj, (const double*)Vj,
+                   Vn, (int)B, c->k_partial);
+        // classical Gram-Schmidt, twice
+        for (int pass = 0; pass < 2; ++pass) {
+          double* h = pass == 0 ? h1 : h2;
+          is2.launch(mgk::k_gm_dots, rgrid, rblock, 0, (const double*)c->gm_V, vs,
+                     (const double*)Vn, j + 1, n0, (int)B, c->gm_partial);
+          is2.launch(mgk::k_reduce, dim3((j + 1) * B), dim3(kThreads), 0,
+                     (const double*)c->gm_partial, nblk, (int)((j + 1) * B), h);
+          is2.launch(mgk::k_gm_orth, rgrid, rblock, 0, (const double*)c->gm_V, vs, Vn,
+                     (const double*)h, j + 1, n0, (int)B, c->partial);
+        }
+        is2.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
+                   (int)B, wn);
+        is2.launch(mgk::k_gm_arnoldi, dim3(1), dim3(kThreads), 0, c->gm_small,
+                   (const double*)h1, (const double*)h2, (const double*)wn,
+                   (const double*)c->fsum, (const double*)c->tol_dev, m, j, (int)B,
+                   (const int*)c->active, c->iters, inv, c->relres, c->state);
+        is2.launch(mgk::k_gm_scale, grid_for(N), dim3(kThreads), 0, (const double*)Vn,
+                   (const double*)inv, Vn, n0, (int)B);
+        return nk + is2.nk;
+      });
+      if (st != MG_OK) return st;
+      ++total;
+      jl = j;
+      if ((st = read_state()) != MG_OK) return st;
+      if (c->h_state[3] == 0) break;
+    }
+    if (jl < 0) break;
+    // end of the cycle: y, u += Z y
+    st = run_graph(c, key(7300 + jl), s, [&](cudaStream_t cs) {
+      Issue<double> is{c, c->d64, c->prm64, cs, B};
+      is.launch(mgk::k_gm_solve_y, dim3(1), dim3(kThreads), 0, c->gm_small, m, jl, (int)B,
+                (const int*)c->active);
+      is.launch(mgk::k_gm_update, grid_for(N), dim3(kThreads), 0, u, (const double*)c->gm_Z, vs,
+                (const double*)c->gm_small, m, jl + 1, (const int*)c->active, n0, (int)B);
+      return is.nk;
+    });
+    if (st != MG_OK) return st;
+  }
+  // the true residual of the final iterate
+  st = run_graph(c, key(7002), s, [&](cudaStream_t cs) {
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_outer_residual64, rgrid, rblock, 0, L0, f, (const double*)u, c->k_r, (int)B);
+    is.launch(mgk::k_dots<1>, rgrid, rblock, 0, (const double*)c->k_r, (const double*)c->k_r,
+              (const double*)nullptr, (const double*)nullptr, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->rsum);
+    is.launch(k_true_relres, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, (int)B, c->relres);
+    return is.nk;
+  });
+  if (st != MG_OK) return st;
+  std::vector<double> rel(B);
+  MG_CUDA(cudaMemcpy(rel.data(), c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
+  if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
+  if (relres_out) std::copy(rel.begin(), rel.end(), relres_out);
+  mg_status result = MG_OK;
+  for (double r : rel)
+    if (!(r < tol)) result = MG_NOT_CONVERGED;
+  if (diverged) result = MG_ERR_DIVERGED;
+  if (result == MG_ERR_DIVERGED) c->err = "mg_solve_fgmres: non-finite residual";
+  if (result == MG_NOT_CONVERGED) c->err = "mg_solve_fgmres: tolerance not met within max_iter";
+  return result;
+}

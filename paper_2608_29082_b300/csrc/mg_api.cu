@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 
 #include "adjoint.cuh"
+#include "gmres.cuh"
 #include "halo.cuh"
 #include "kernels.cuh"
 #include "krylov.cuh"
@@ -262,6 +263,11 @@ struct mg_ctx {
   // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
   double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
   double *k_partial = nullptr, *k_small = nullptr;
+  // flexible GMRES workspace (mg_solve_fgmres), for restart length gm_m
+  int gm_m = 0;
+  double *gm_V = nullptr, *gm_Z = nullptr, *gm_small = nullptr, *gm_h = nullptr;
+  double *gm_vec = nullptr, *gm_partial = nullptr;
+  int* gm_zexp = nullptr;
   int nu_pre = 2, nu_post = 2;
   std::vector<double> prm;  // [J-1][P_COUNT]
   double* prm64 = nullptr;
@@ -917,7 +923,7 @@ mg_status run_graph(mg_ctx* c, const std::tuple<int, const void*, const void*, i
     cudaGraphDestroy(g);
     if (e3 != cudaSuccess)
       return c->fail(MG_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e3));
-    if (c->graphs.size() > 64) {  // bounded cache
+    if (c->graphs.size() > 512) {  // bounded cache
       for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
       c->graphs.clear();
     }
@@ -1013,7 +1019,7 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
     cudaGraphDestroy(g);
     if (e != cudaSuccess)
       return c->fail(MG_ERR_CUDA, std::string(who) + ": instantiate: " + cudaGetErrorString(e));
-    if (c->graphs.size() > 64) {
+    if (c->graphs.size() > 512) {
       for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
       c->graphs.clear();
     }
@@ -1052,7 +1058,9 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (auto& L : c->d64) free_level(L);
   for (auto& L : c->d32) free_level(L);
   for (void* p : {(void*)c->cholP, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
-                  (void*)c->k_partial, (void*)c->k_small})
+                  (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
+                  (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
+                  (void*)c->gm_zexp})
     if (p) cudaFree(p);
   void* ptrs[] = {c->cholL,  c->cholU,  c->cholDinv, c->prm64,  c->prm32, c->partial,
                   c->rsum,   c->fsum,   c->relres,   c->w64,    c->active, c->iters,
@@ -1586,6 +1594,7 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
 
 #include "train_impl.cuh"
 #include "krylov_impl.cuh"
+#include "gmres_impl.cuh"
 
 extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_option: ctx is NULL");

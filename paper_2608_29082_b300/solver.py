@@ -154,11 +154,13 @@ class Solver:
         return u
 
     def solve(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-8,
-              max_iter: int = 100, method: str = "refine") -> tuple[torch.Tensor, SolveInfo]:
+              max_iter: int = 100, method: str = "refine",
+              restart: int = 30) -> tuple[torch.Tensor, SolveInfo]:
         """FP64 f, u (u = initial guess, zero if None) -> (u, info).
         method "refine": stationary cycles (FP64 context) or FP64 iterative
-        refinement around FP32 cycles; "fcg": flexible CG with the cycle as
-        preconditioner."""
+        refinement around FP32 cycles; "fcg": flexible CG with the cycle (or
+        full multigrid, option "fcg_precond") as preconditioner; "fgmres":
+        restarted flexible GMRES (restart) with the same preconditioners."""
         f2 = self._vec(f, self.n[0], torch.float64, "f")
         if u is None:
             u = torch.zeros_like(f)
@@ -166,10 +168,16 @@ class Solver:
         B = f2.shape[1]
         iters = np.zeros(B, dtype=np.int32)
         relres = np.zeros(B)
-        fn = {"refine": self.lib.mg_solve, "fcg": self.lib.mg_solve_fcg}[method]
-        st = fn(self.ctx, C.c_void_p(f2.data_ptr()), C.c_void_p(u2.data_ptr()), B,
-                float(tol), int(max_iter), L.ptr(iters, L.i32p),
-                L.ptr(relres, L.f64p), _stream_handle())
+        if method == "fgmres":
+            st = self.lib.mg_solve_fgmres(self.ctx, C.c_void_p(f2.data_ptr()),
+                                          C.c_void_p(u2.data_ptr()), B, float(tol), int(max_iter),
+                                          int(restart), L.ptr(iters, L.i32p),
+                                          L.ptr(relres, L.f64p), _stream_handle())
+        else:
+            fn = {"refine": self.lib.mg_solve, "fcg": self.lib.mg_solve_fcg}[method]
+            st = fn(self.ctx, C.c_void_p(f2.data_ptr()), C.c_void_p(u2.data_ptr()), B,
+                    float(tol), int(max_iter), L.ptr(iters, L.i32p),
+                    L.ptr(relres, L.f64p), _stream_handle())
         L.check(st, self.ctx, allow=(L.MG_OK, L.MG_NOT_CONVERGED))
         return u, SolveInfo(st, iters, relres)
 
