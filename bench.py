@@ -279,6 +279,12 @@ def run_ours(args):
     u32 = u.clone()
     # the same learned cycle as preconditioner of flexible CG (FP64 outer)
     msfcg, infofcg, nkfcg = timed(S32, method="fcg")
+    # the learned cycle, nonsymmetric, as the preconditioner of restarted
+    # flexible GMRES: one V-cycle, and one full multigrid (Sec. 5)
+    msgmv, infogmv, nkgmv = timed(S32, method="fgmres")
+    S32.set_option("fcg_precond", 1)
+    msgmf, infogmf, nkgmf = timed(S32, method="fgmres")
+    S32.set_option("fcg_precond", 0)
     # classical (identity) Theta as the FP32 preconditioner of flexible CG:
     # one V-cycle, and one full multigrid (nested iteration)
     S32c = lmg.Solver(hier, plain, precision=32, max_batch=1)
@@ -288,8 +294,8 @@ def run_ours(args):
     S32c.close()
     # max over ranks
     if pg:
-        ms32, ms64, msfcg, msccg, msfmg = max_over_ranks([ms32, ms64, msfcg, msccg, msfmg], pg,
-                                                         dev)
+        ms32, ms64, msfcg, msgmv, msgmf, msccg, msfmg = max_over_ranks(
+            [ms32, ms64, msfcg, msgmv, msgmf, msccg, msfmg], pg, dev)
 
     # end to end through the public host API (pinned host buffers)
     fh = torch.tensor(prob.f, dtype=torch.float64).pin_memory().numpy()
@@ -380,6 +386,12 @@ def run_ours(args):
             "learned_fcg_ms": round(msfcg, 4),
             "learned_fcg_iters": int(infofcg.iters[0]),
             "learned_fcg_relres": float(infofcg.relres[0]),
+            "learned_fgmres_ms": round(msgmv, 4),
+            "learned_fgmres_iters": int(infogmv.iters[0]),
+            "learned_fgmres_relres": float(infogmv.relres[0]),
+            "learned_fgmres_fmg_ms": round(msgmf, 4),
+            "learned_fgmres_fmg_iters": int(infogmf.iters[0]),
+            "learned_fgmres_fmg_relres": float(infogmf.relres[0]),
             "classical_fp32_fcg_ms": round(msccg, 4),
             "classical_fp32_fcg_iters": int(infoccg.iters[0]),
             "classical_fp32_fcg_fmg_ms": round(msfmg, 4),
@@ -391,6 +403,8 @@ def run_ours(args):
             "gpu_launches": int(nk32),
             "gpu_launches_by_region": {"learned_refinement": int(nk32), "plain_fp64": int(nk64),
                                        "learned_fcg": int(nkfcg),
+                                       "learned_fgmres": int(nkgmv),
+                                       "learned_fgmres_fmg": int(nkgmf),
                                        "classical_fcg_fmg": int(nkfmg)},
             "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

@@ -2,10 +2,13 @@
 // V-cycle or full multigrid as the right preconditioner.  Included at the end
 // of mg_api.cu (same translation unit), after krylov_impl.cuh.
 //
-// The host drives the restart cycle: a restart graph (true residual, beta,
-// v_0), one graph per Arnoldi step j (preconditioner, A z_j, CGS2, the
-// rotations), and an end-of-cycle graph (y, u += Z y).  After the restart
-// and after every step the host reads the convergence counts.
+// The host drives the restart cycle: a restart graph (FP64 true residual,
+// beta, v_0), one graph per Arnoldi step j (preconditioner, K z_j, CGS2, the
+// rotations) in the context precision, and an end-of-cycle graph (y, u += Z
+// y in FP64).  After the restart and after every step the host reads the
+// convergence counts.  In an FP32 context this is FGMRES-based iterative
+// refinement: FP32 cycles, each ending at most kGmFp32Floor below its
+// starting residual, corrected by FP64 restarts.
 
 namespace {
 
@@ -14,26 +17,84 @@ mg_status gm_buffers(mg_ctx* c, int m) {
   // graphs captured earlier point at the old workspace
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
-  for (void* p : {(void*)c->gm_V, (void*)c->gm_Z, (void*)c->gm_small, (void*)c->gm_h,
-                  (void*)c->gm_vec, (void*)c->gm_partial, (void*)c->gm_zexp})
+  for (void* p : {c->gm_V, c->gm_Z, (void*)c->gm_zero32, (void*)c->gm_small, (void*)c->gm_h,
+                  (void*)c->gm_vec, (void*)c->gm_partial, (void*)c->gm_done})
     if (p) cudaFree(p);
-  c->gm_V = c->gm_Z = c->gm_small = c->gm_h = c->gm_vec = c->gm_partial = nullptr;
-  c->gm_zexp = nullptr;
+  c->gm_V = c->gm_Z = nullptr;
+  c->gm_zero32 = nullptr;
+  c->gm_small = c->gm_h = c->gm_vec = c->gm_partial = nullptr;
+  c->gm_done = nullptr;
   c->gm_m = 0;
-  const size_t v = (size_t)c->n[0] * c->maxB * sizeof(double);
-  const size_t nblk = ((size_t)c->n[0] + mgk::kRedRows - 1) / mgk::kRedRows;
+  const size_t N = (size_t)c->n[0] * c->maxB;
+  const size_t v = N * (c->prec == 32 ? sizeof(float) : sizeof(double));
+  const size_t nblk = ((size_t)c->n[0] + mgk::kGmTile - 1) / mgk::kGmTile;
   const size_t mb = (size_t)c->maxB;
   MG_CUDA(cudaMalloc(&c->gm_V, v * (m + 1)));
   MG_CUDA(cudaMalloc(&c->gm_Z, v * m));
+  if (c->prec == 32) {
+    MG_CUDA(cudaMalloc(&c->gm_zero32, N * sizeof(float)));
+    MG_CUDA(cudaMemset(c->gm_zero32, 0, N * sizeof(float)));
+  }
   MG_CUDA(cudaMalloc(&c->gm_small, mb * mgk::gm_stride(m) * sizeof(double)));
   MG_CUDA(cudaMalloc(&c->gm_h, 2 * (m + 1) * mb * sizeof(double)));
   MG_CUDA(cudaMalloc(&c->gm_vec, 2 * mb * sizeof(double)));
   MG_CUDA(cudaMalloc(&c->gm_partial, nblk * (m + 1) * mb * sizeof(double)));
-  MG_CUDA(cudaMalloc(&c->gm_zexp, mb * sizeof(int)));
-  MG_CUDA(cudaMemset(c->gm_zexp, 0, mb * sizeof(int)));
+  MG_CUDA(cudaMalloc(&c->gm_done, mb * sizeof(int)));
   c->gm_m = m;
   return MG_OK;
 }
+
+// Launch shapes and scratch of one FGMRES solve.
+struct GmShape {
+  int m, B, n0, gblk;
+  size_t vs;  // stride between basis vectors
+  dim3 ggrid, gblock, rgrid, rblock;
+  double *h1, *h2, *wn, *inv;
+  double rho;
+};
+
+// Arnoldi step j in vector type T: z_j = M(v_j), w = K z_j into the slot of
+// v_{j+1} (K = A in FP64; K = -A in FP32, as 0 - A z from the residual
+// kernel, undone by the update's sign), CGS2, the rotations, v_{j+1}.
+template <class T>
+void gm_step(mg_ctx* c, Issue<T>& is, const GmShape& g, int j, const LV<double>& L0) {
+  T* V = (T*)c->gm_V;
+  T* Z = (T*)c->gm_Z;
+  T* Vj = V + (size_t)j * g.vs;
+  T* Vn = V + (size_t)(j + 1) * g.vs;
+  T* Zj = Z + (size_t)j * g.vs;
+  if (c->opt_fcg_precond == 1)
+    is.fmg(Vj, Zj);
+  else
+    is.vcycle(Vj, Zj, true);
+  if constexpr (sizeof(T) == sizeof(float))
+    is.op_residual(0, c->gm_zero32, Zj, Vn, 0, 0);
+  else
+    is.launch(mgk::k_spmv_dots, g.rgrid, g.rblock, 0, L0, (const double*)Zj, (const double*)Vj,
+              (double*)Vn, g.B, c->k_partial);
+  for (int pass = 0; pass < 2; ++pass) {
+    double* h = pass == 0 ? g.h1 : g.h2;
+    is.launch(mgk::k_gm_dots<T>, g.ggrid, g.gblock, 0, (const T*)V, g.vs, (const T*)Vn, j + 1,
+              g.n0, g.B, c->gm_partial);
+    is.launch(mgk::k_reduce, dim3((j + 1) * g.B), dim3(kThreads), 0,
+              (const double*)c->gm_partial, g.gblk, (int)((j + 1) * g.B), h);
+    is.launch(mgk::k_gm_orth<T>, g.ggrid, g.gblock, 0, (const T*)V, g.vs, Vn, (const double*)h,
+              j + 1, g.n0, g.B, c->partial);
+  }
+  is.launch(mgk::k_reduce, dim3(g.B), dim3(kThreads), 0, (const double*)c->partial, g.gblk, g.B,
+            g.wn);
+  is.launch(mgk::k_gm_arnoldi, dim3(1), dim3(kThreads), 0, c->gm_small, (const double*)g.h1,
+            (const double*)g.h2, (const double*)g.wn, (const double*)c->fsum,
+            (const double*)c->tol_dev, g.m, j, g.B, g.rho, (const int*)c->active, c->iters, g.inv,
+            c->relres, c->gm_done, c->state);
+  is.launch(mgk::k_gm_scale<T, T>, grid_for((size_t)g.n0 * g.B), dim3(kThreads), 0,
+            (const T*)Vn, (const double*)g.inv, Vn, g.n0, g.B);
+}
+
+// FP32 Arnoldi cycles end when their estimate has fallen by this factor:
+// about what CGS2 and A z in FP32 resolve; the next cycle starts from the
+// FP64 residual.
+constexpr double kGmFp32Floor = 1e-5;
 
 }  // namespace
 
@@ -61,11 +122,24 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
   const LV<double> L0 = c->d64[0].view();
   const bool p32 = c->prec == 32;
   const size_t N = (size_t)n0 * B;
-  const size_t vs = N;  // stride between basis vectors
-  double* h1 = c->gm_h;
-  double* h2 = c->gm_h + (size_t)(m + 1) * B;
-  double* wn = c->gm_vec;
-  double* inv = c->gm_vec + B;
+  GmShape g;
+  g.m = m;
+  g.B = B;
+  g.n0 = n0;
+  // Gram-Schmidt tiling (gmres.cuh): 256 rows x min(B, 16) columns a block
+  const int gbt = std::min((int)B, mgk::kGmBt);
+  g.gblk = (n0 + mgk::kGmTile - 1) / mgk::kGmTile;
+  g.ggrid = dim3(g.gblk, (B + gbt - 1) / gbt);
+  g.gblock = dim3(mgk::kRedRows * gbt);
+  g.rgrid = rgrid;
+  g.rblock = rblock;
+  g.vs = N;
+  g.h1 = c->gm_h;
+  g.h2 = c->gm_h + (size_t)(m + 1) * B;
+  g.wn = c->gm_vec;
+  g.inv = c->gm_vec + B;
+  g.rho = p32 ? kGmFp32Floor : 0.0;
+  const double sgn = p32 ? -1.0 : 1.0;
   c->solve_ctl[0] = tol;
   c->solve_ctl[1] = (double)max_iter;
   MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -103,9 +177,13 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
                 c->rsum);
       is.launch(mgk::k_gm_restart, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
                 (const double*)c->fsum, (const double*)c->tol_dev, m, (int)B, c->active,
-                c->relres, c->gm_small, inv, c->state);
-      is.launch(mgk::k_gm_scale, grid_for(N), dim3(kThreads), 0, (const double*)c->k_r,
-                (const double*)inv, c->gm_V, n0, (int)B);
+                c->relres, c->gm_small, g.inv, c->gm_done, c->state);
+      if (p32)
+        is.launch(mgk::k_gm_scale<double, float>, grid_for(N), dim3(kThreads), 0,
+                  (const double*)c->k_r, (const double*)g.inv, (float*)c->gm_V, n0, (int)B);
+      else
+        is.launch(mgk::k_gm_scale<double, double>, grid_for(N), dim3(kThreads), 0,
+                  (const double*)c->k_r, (const double*)g.inv, (double*)c->gm_V, n0, (int)B);
       return is.nk;
     });
     if (st != MG_OK) return st;
@@ -118,54 +196,14 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
     int jl = -1;
     for (int j = 0; j < m && total < max_iter; ++j) {
       st = run_graph(c, key(7100 + j), s, [&](cudaStream_t cs) {
-        double* Vj = c->gm_V + (size_t)j * vs;
-        double* Vn = c->gm_V + (size_t)(j + 1) * vs;
-        double* Zj = c->gm_Z + (size_t)j * vs;
-        int nk = 0;
-        // z_j = M(v_j) (||v_j|| = 1, so the FP32 copy needs no scaling)
         if (p32) {
-          Issue<double> is0{c, c->d64, c->prm64, cs, B};
-          is0.launch(mgk::k_scale_to_f32, grid_for(N), dim3(kThreads), 0, (const double*)Vj,
-                     (const int*)c->gm_zexp, c->rhat32, n0, (int)B);
           Issue<float> is{c, c->d32, c->prm32, cs, B};
-          if (c->opt_fcg_precond == 1)
-            is.fmg(c->rhat32, c->c32);
-          else
-            is.vcycle(c->rhat32, c->c32, true);
-          is.launch(mgk::k_scale_from_f32, grid_for(N), dim3(kThreads), 0, (const float*)c->c32,
-                    (const int*)c->gm_zexp, Zj, n0, (int)B);
-          nk += is0.nk + is.nk;
-        } else {
-          Issue<double> is{c, c->d64, c->prm64, cs, B};
-          if (c->opt_fcg_precond == 1)
-            is.fmg(Vj, Zj);
-          else
-            is.vcycle(Vj, Zj, true);
-          nk += is.nk;
+          gm_step(c, is, g, j, L0);
+          return is.nk;
         }
-        Issue<double> is2{c, c->d64, c->prm64, cs, B};
-        // w = A z_j, in the slot of v_{j+1}
-        is2.launch(mgk::k_spmv_dots, rgrid, rblock, 0, L0, (const double*)Zj, (const double*)Vj,
-                   Vn, (int)B, c->k_partial);
-        // classical Gram-Schmidt, twice
-        for (int pass = 0; pass < 2; ++pass) {
-          double* h = pass == 0 ? h1 : h2;
-          is2.launch(mgk::k_gm_dots, rgrid, rblock, 0, (const double*)c->gm_V, vs,
-                     (const double*)Vn, j + 1, n0, (int)B, c->gm_partial);
-          is2.launch(mgk::k_reduce, dim3((j + 1) * B), dim3(kThreads), 0,
-                     (const double*)c->gm_partial, nblk, (int)((j + 1) * B), h);
-          is2.launch(mgk::k_gm_orth, rgrid, rblock, 0, (const double*)c->gm_V, vs, Vn,
-                     (const double*)h, j + 1, n0, (int)B, c->partial);
-        }
-        is2.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk,
-                   (int)B, wn);
-        is2.launch(mgk::k_gm_arnoldi, dim3(1), dim3(kThreads), 0, c->gm_small,
-                   (const double*)h1, (const double*)h2, (const double*)wn,
-                   (const double*)c->fsum, (const double*)c->tol_dev, m, j, (int)B,
-                   (const int*)c->active, c->iters, inv, c->relres, c->state);
-        is2.launch(mgk::k_gm_scale, grid_for(N), dim3(kThreads), 0, (const double*)Vn,
-                   (const double*)inv, Vn, n0, (int)B);
-        return nk + is2.nk;
+        Issue<double> is{c, c->d64, c->prm64, cs, B};
+        gm_step(c, is, g, j, L0);
+        return is.nk;
       });
       if (st != MG_OK) return st;
       ++total;
@@ -178,9 +216,15 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
     st = run_graph(c, key(7300 + jl), s, [&](cudaStream_t cs) {
       Issue<double> is{c, c->d64, c->prm64, cs, B};
       is.launch(mgk::k_gm_solve_y, dim3(1), dim3(kThreads), 0, c->gm_small, m, jl, (int)B,
-                (const int*)c->active);
-      is.launch(mgk::k_gm_update, grid_for(N), dim3(kThreads), 0, u, (const double*)c->gm_Z, vs,
-                (const double*)c->gm_small, m, jl + 1, (const int*)c->active, n0, (int)B);
+                (const int*)c->active, (const int*)c->gm_done);
+      if (p32)
+        is.launch(mgk::k_gm_update<float>, grid_for(N), dim3(kThreads), 0, u,
+                  (const float*)c->gm_Z, g.vs, (const double*)c->gm_small, m, jl + 1, sgn,
+                  (const int*)c->active, n0, (int)B);
+      else
+        is.launch(mgk::k_gm_update<double>, grid_for(N), dim3(kThreads), 0, u,
+                  (const double*)c->gm_Z, g.vs, (const double*)c->gm_small, m, jl + 1, sgn,
+                  (const int*)c->active, n0, (int)B);
       return is.nk;
     });
     if (st != MG_OK) return st;

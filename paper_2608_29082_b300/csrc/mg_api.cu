@@ -263,11 +263,14 @@ struct mg_ctx {
   // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
   double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
   double *k_partial = nullptr, *k_small = nullptr;
-  // flexible GMRES workspace (mg_solve_fgmres), for restart length gm_m
+  // flexible GMRES workspace (mg_solve_fgmres), for restart length gm_m:
+  // basis and directions in the context precision (gm_V, gm_Z: void), an
+  // FP32 zero vector (the right-hand side of w = 0 - A z), per-rhs cycle ends
   int gm_m = 0;
-  double *gm_V = nullptr, *gm_Z = nullptr, *gm_small = nullptr, *gm_h = nullptr;
-  double *gm_vec = nullptr, *gm_partial = nullptr;
-  int* gm_zexp = nullptr;
+  void *gm_V = nullptr, *gm_Z = nullptr;
+  float* gm_zero32 = nullptr;
+  double *gm_small = nullptr, *gm_h = nullptr, *gm_vec = nullptr, *gm_partial = nullptr;
+  int* gm_done = nullptr;
   int nu_pre = 2, nu_post = 2;
   std::vector<double> prm;  // [J-1][P_COUNT]
   double* prm64 = nullptr;
@@ -1060,7 +1063,7 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (void* p : {(void*)c->cholP, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
                   (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
                   (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
-                  (void*)c->gm_zexp})
+                  (void*)c->gm_zero32, (void*)c->gm_done})
     if (p) cudaFree(p);
   void* ptrs[] = {c->cholL,  c->cholU,  c->cholDinv, c->prm64,  c->prm32, c->partial,
                   c->rsum,   c->fsum,   c->relres,   c->w64,    c->active, c->iters,

@@ -157,7 +157,10 @@ def run_lshape(a):
     msf32, infof32, uf32 = timed_solve(S32, f64, a.tol, method="fcg")
     S32.set_option("fcg_precond", 1)  # full multigrid as the preconditioner
     msg32, infog32, ug32 = timed_solve(S32, f64, a.tol, method="fcg")
+    # restarted flexible GMRES(30) takes the nonsymmetric preconditioners as they are
+    msq32, infoq32, uq32 = timed_solve(S32, f64, a.tol, method="fgmres")
     S32.set_option("fcg_precond", 0)
+    msr32, infor32, ur32 = timed_solve(S32, f64, a.tol, method="fgmres")
     S64 = Solver(hier, plain, precision=64, max_batch=a.batch)
     ms64, info64, _ = timed_solve(S64, f64, a.tol)
     msf64, infof64, _ = timed_solve(S64, f64, a.tol, method="fcg")
@@ -173,6 +176,8 @@ def run_lshape(a):
     rr = oracle_relres(u32)
     rrf = oracle_relres(uf32)
     rrg = oracle_relres(ug32)
+    rrr = oracle_relres(ur32)
+    rrq = oracle_relres(uq32)
     out = {"workload": f"L-shape anisotropic, {a.refinements} red refinements, {hier.sizes[0]} DOF, "
                        f"{J} levels, {a.batch} rhs, tol {a.tol}",
            "levels": hier.sizes, "generate_s": round(t_gen, 1), "setup_s": round(t_setup, 1),
@@ -185,6 +190,12 @@ def run_lshape(a):
            "learned_fp32_fcg_fmg_ms": round(msg32, 3),
            "learned_fcg_fmg_iters": int(infog32.iters.max()),
            "oracle_max_relres_fcg_fmg": float(rrg.max()),
+           "learned_fp32_fgmres_ms": round(msr32, 3),
+           "learned_fgmres_iters": int(infor32.iters.max()),
+           "oracle_max_relres_fgmres": float(rrr.max()),
+           "learned_fp32_fgmres_fmg_ms": round(msq32, 3),
+           "learned_fgmres_fmg_iters": int(infoq32.iters.max()),
+           "oracle_max_relres_fgmres_fmg": float(rrq.max()),
            "plain_fp64_fcg_ms": round(msf64, 3), "plain_fcg_iters": int(infof64.iters.max()),
            "speedup_fcg_learned_vs_plain_stationary": round(ms64 / msf32, 3),
            "cycle_us_fp32_profiled": round(cyc32, 1), "cycle_us_fp64_profiled": round(cyc64, 1),
