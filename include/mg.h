@@ -271,16 +271,24 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     Other values than [0, 2^30]: MG_ERR_INVALID.
  *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg and mg_solve_fgmres:
  *                     0 (default) one V-cycle from zero, 1 one full
- *                     multigrid (mg_fmg).  This
- *                     option changes results (another preconditioner); the
- *                     others only change launch shapes. */
+ *                     multigrid (mg_fmg).
+ *   MG_OPT_FGMRES_FLOOR FP32 contexts: an Arnoldi cycle of mg_solve_fgmres
+ *                     ends (and an FP64 restart follows) once its residual
+ *                     estimate is below 10^-value times the cycle's initial
+ *                     residual; default 4, 0: no floor, at most 15.  FP64
+ *                     contexts ignore it.  An FP32 cycle resolves about
+ *                     1e-4..1e-7 of its start (CGS2 and K z in FP32);
+ *                     a lower floor spends steps below that.
+ * MG_OPT_FCG_PRECOND and MG_OPT_FGMRES_FLOOR change results (another
+ * preconditioner, other restart points); the others only launch shapes. */
 typedef enum {
   MG_OPT_TAIL_WORK = 0,
   MG_OPT_PDL = 1,
   MG_OPT_MULTI_RHS = 2,
   MG_OPT_DEVICE_LOOP = 3,
   MG_OPT_HALO_ROWS = 4,
-  MG_OPT_FCG_PRECOND = 5
+  MG_OPT_FCG_PRECOND = 5,
+  MG_OPT_FGMRES_FLOOR = 6
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

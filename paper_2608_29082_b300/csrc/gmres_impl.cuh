@@ -7,8 +7,8 @@
 // rotations) in the context precision, and an end-of-cycle graph (y, u += Z
 // y in FP64).  After the restart and after every step the host reads the
 // convergence counts.  In an FP32 context this is FGMRES-based iterative
-// refinement: FP32 cycles, each ending at most kGmFp32Floor below its
-// starting residual, corrected by FP64 restarts.
+// refinement: FP32 cycles, each ending at most MG_OPT_FGMRES_FLOOR decades
+// below its starting residual, corrected by FP64 restarts.
 
 namespace {
 
@@ -91,11 +91,6 @@ void gm_step(mg_ctx* c, Issue<T>& is, const GmShape& g, int j, const LV<double>&
             (const T*)Vn, (const double*)g.inv, Vn, g.n0, g.B);
 }
 
-// FP32 Arnoldi cycles end when their estimate has fallen by this factor:
-// about what CGS2 and A z in FP32 resolve; the next cycle starts from the
-// FP64 residual.
-constexpr double kGmFp32Floor = 1e-5;
-
 }  // namespace
 
 extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
@@ -138,7 +133,10 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
   g.h2 = c->gm_h + (size_t)(m + 1) * B;
   g.wn = c->gm_vec;
   g.inv = c->gm_vec + B;
-  g.rho = p32 ? kGmFp32Floor : 0.0;
+  // an FP32 cycle resolves its residual to about 1e-4..1e-7 of its start
+  // (CGS2 and K z in FP32, depending on the operator's conditioning); below
+  // that the FP64 restart takes over
+  g.rho = p32 && c->opt_fgmres_floor > 0 ? std::pow(10.0, -c->opt_fgmres_floor) : 0.0;
   const double sgn = p32 ? -1.0 : 1.0;
   c->solve_ctl[0] = tol;
   c->solve_ctl[1] = (double)max_iter;

@@ -297,6 +297,7 @@ struct mg_ctx {
   int opt_multi_rhs = 1;         // multi-rhs kernels: 0 off, 1 widest tile, else max tile
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
   int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
+  int opt_fgmres_floor = 4;      // FP32 FGMRES cycle floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
   int64_t wave_threads = 148 * 2048;  // SMs x resident threads per SM (set in mg_setup)
   // training state (device buffers in the context precision)
@@ -1621,6 +1622,11 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       if (value != 0 && value != 1)
         return c->fail(MG_ERR_INVALID, "mg_set_option: FCG preconditioner must be 0 or 1");
       c->opt_fcg_precond = (int)value;
+      break;
+    case MG_OPT_FGMRES_FLOOR:
+      if (value < 0 || value > 15)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: FGMRES floor must be in [0, 15]");
+      c->opt_fgmres_floor = (int)value;
       break;
     case MG_OPT_HALO_ROWS:
       if (value < 0 || value > (1 << 30))

@@ -580,3 +580,40 @@ def test_fgmres_zero_rhs_and_not_converged():
     u, info = S.solve(t64(p.f), tol=1e-14, max_iter=3, method="fgmres", restart=10)
     assert info.status == 1 and info.iters.max() == 3
     S.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("name", ["lognormal65", "poisson33"])
+def test_fgmres_batch_independent(name, prec):
+    """A right-hand side's FGMRES run does not depend on the rest of the
+    batch: the reductions group terms independently of B, and a right-hand
+    side whose cycle ended early waits with its own columns only."""
+    p, Ho, Hp = problem(name)
+    assert p.f.shape[1] >= 2
+    S = Solver(Hp, rand_params(Hp.J, 29, 0.2), precision=prec, max_batch=p.f.shape[1])
+    ub, ib = S.solve(t64(p.f), tol=1e-8, max_iter=300, method="fgmres", restart=8)
+    assert ib.status == 0
+    for b in range(p.f.shape[1]):
+        u1, i1 = S.solve(t64(p.f[:, b:b + 1]), tol=1e-8, max_iter=300, method="fgmres",
+                         restart=8)
+        assert int(i1.iters[0]) == int(ib.iters[b])
+        assert torch.equal(u1[:, 0], ub[:, b])
+    S.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("floor", [0, 7])
+def test_fgmres_fp32_floor(floor):
+    """FP32 cycles with another floor (0: none) still reach 1e-8 through the
+    FP64 restarts; out-of-range floors are rejected."""
+    p, Ho, Hp = problem("checker65")
+    S = Solver(Hp, rand_params(Hp.J, 29, 0.2), precision=32, max_batch=p.f.shape[1])
+    S.set_option("fgmres_floor", floor)
+    u, info = S.solve(t64(p.f), tol=1e-8, max_iter=300, method="fgmres", restart=10)
+    assert info.status == 0
+    assert (O.relres(Ho, p.f, u.cpu().numpy()) < 1e-8).all()
+    for bad in (-1, 16):
+        with pytest.raises(MGError):
+            S.set_option("fgmres_floor", bad)
+    S.close()
