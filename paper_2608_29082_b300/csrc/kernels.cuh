@@ -844,6 +844,16 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 constexpr int kRedRows = 32;
 constexpr int kRedMax = 1024;  // kRedRows x 32 columns
 
+// x * 2^e.  For -1022 <= e <= 1023, 2^e is a normal binary64 number (biased
+// exponent e + 1023, zero fraction), so one multiply gives the exact scaled
+// value, rounded once if it is subnormal: bitwise what ldexp returns, without
+// ldexp's FP64 special-case arithmetic (B300's FP64 pipe is narrow).  Other e
+// go through ldexp.
+__device__ __forceinline__ double scale2(double x, int e) {
+  return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52)
+                                   : ldexp(x, e);
+}
+
 // (row, rhs) of this thread in the reduction tiling.
 __device__ __forceinline__ void red_tile(int n, int B, int& i, int& b, bool& ok) {
   const int bt = blockDim.x / kRedRows;
@@ -889,7 +899,7 @@ __global__ void __launch_bounds__(kRedMax) k_resid64(LV<double> L, const double*
     const size_t k = (size_t)i * B + b;
     const double ax = row_ax(L, i, u, B, b);
     r = fma(-L.diag[i], u[k], f[k]) - ax;
-    if (rhat) rhat[k] = (float)ldexp(r, -sexp[b]);
+    if (rhat) rhat[k] = (float)scale2(r, -sexp[b]);
   }
   sh[threadIdx.x] = r * r;
   __syncthreads();
@@ -1036,7 +1046,7 @@ __global__ void __launch_bounds__(kThreads) k_refine_update(double* __restrict__
   if (t < (size_t)B && active[t]) iters[t] += 1;
   if (t >= (size_t)n * B) return;
   const int b = (int)(t % B);
-  if (active[b]) u[t] += ldexp((double)c[t], sexp[b]);
+  if (active[b]) u[t] += scale2((double)c[t], sexp[b]);
 }
 
 // u <- w for the right-hand sides still active (plain solve, B > 1).

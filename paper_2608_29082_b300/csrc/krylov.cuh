@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_to_f32(const double* __restr
   pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * B) return;
-  rhat[t] = (float)ldexp(r[t], -sexp[t % B]);
+  rhat[t] = (float)scale2(r[t], -sexp[t % B]);
 }
 
 // z = 2^sexp[b] * c (preconditioner output back in FP64).
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kThreads) k_scale_from_f32(const float* __rest
   pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * B) return;
-  z[t] = ldexp((double)c[t], sexp[t % B]);
+  z[t] = scale2((double)c[t], sexp[t % B]);
 }
 
 }  // namespace mgk
