@@ -3,6 +3,6 @@
 Only tests, the package smoke check and the benchmark's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.
 """
-from .lmg import (Hierarchy, Level, Params, build_hierarchy, conv, fgmres, fmg, lmg,  # noqa: F401
-                  loss_gradient_complex_step, loss_gradient_fd, relres, residual,
+from .lmg import (Hierarchy, Level, Params, build_hierarchy, cheb_conv, conv, fgmres,  # noqa: F401
+                  fmg, lap_hat, lmg, loss_gradient_complex_step, loss_gradient_fd, relres, residual,
                   smooth, solve_refinement, solve_vcycles, unrolled_loss, vcycle)

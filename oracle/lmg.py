@@ -17,6 +17,9 @@ Every function follows the paper's definitions in the paper's order:
                                 Phi = w1 I + w2 D_g^{-1} A_g)
   learnable smoother (Sec. 3)  delta = theta B (f - A u),  B = D_A^{-1};
                                u <- u + eta Phi_B(delta)
+  ChebConv smoother (Sec. 3.3, remark on polynomial smoothers)
+                               Phi_B(delta) = sum_k c_k T_k(Lhat) delta,
+                               Lhat = D_g^{-1} L_g - I = -D_g^{-1} A_g
   learnable transfers (Sec. 3) r_c = R Phi_R(r);  e = Phi_P(P e_c)
   learnable V-cycle            Algorithm 2
   training loss                mean_b ||r_K||^2 / ||r_0||^2 after K cycles
@@ -30,7 +33,11 @@ path and listed with reasons in the design notes):
     and columns are removed, so the mean divides by the full stencil count
     while the removed boundary values enter as zero;
   * the convolutions carry no bias, so the cycle is linear in (f, u);
-  * the coarsest level is solved exactly by a dense Cholesky factorisation.
+  * the coarsest level is solved exactly by a dense Cholesky factorisation;
+  * ChebConv uses the random-walk normalised Laplacian D_g^{-1} L_g (the
+    mean aggregation of the SAGEConv smoother) scaled by lambda_max = 2, and
+    "order K" is the polynomial degree K (coefficients c_0..c_K), so degree 1
+    is the SAGEConv smoother with w1 = c_0, w2 = -c_1.
 """
 from __future__ import annotations
 
@@ -127,6 +134,9 @@ class Params:
     wP: np.ndarray
     nu_pre: int = 2
     nu_post: int = 2
+    # ChebConv smoother coefficients c_{l,0..K} per level (J-1, K+1); None:
+    # the SAGEConv smoother with wB
+    cheb: np.ndarray | None = None
 
     @staticmethod
     def identity(J: int, omega: float = 2.0 / 3.0, nu: int = 2) -> "Params":
@@ -138,11 +148,13 @@ class Params:
 
     def copy(self) -> "Params":
         return Params(self.theta.copy(), self.eta.copy(), self.wB.copy(), self.wR.copy(),
-                      self.wP.copy(), self.nu_pre, self.nu_post)
+                      self.wP.copy(), self.nu_pre, self.nu_post,
+                      None if self.cheb is None else self.cheb.copy())
 
     def astype(self, dtype) -> "Params":
         return Params(self.theta.astype(dtype), self.eta.astype(dtype), self.wB.astype(dtype),
-                      self.wR.astype(dtype), self.wP.astype(dtype), self.nu_pre, self.nu_post)
+                      self.wR.astype(dtype), self.wP.astype(dtype), self.nu_pre, self.nu_post,
+                      None if self.cheb is None else self.cheb.astype(dtype))
 
     # flat view used for gradients: per level [theta, eta, wB1, wB2, wR1, wR2, wP1, wP2]
     def flat(self) -> np.ndarray:
@@ -163,10 +175,31 @@ def conv(L: Level, x: np.ndarray, w1, w2) -> np.ndarray:
     return w1 * x + w2 * (L.inv_deg[:, None] * (L.G @ x))
 
 
-def smooth(L: Level, f, u, theta, eta, wB):
+def lap_hat(L: Level, x: np.ndarray) -> np.ndarray:
+    """The scaled normalised graph Laplacian of ChebConv with lambda_max = 2:
+    Lhat x = (D_g^{-1} L_g - I) x = -D_g^{-1} A_g x, L_g = D_g - A_g."""
+    return -(L.inv_deg[:, None] * (L.G @ x))
+
+
+def cheb_conv(L: Level, x: np.ndarray, c) -> np.ndarray:
+    """ChebConv of degree K = len(c) - 1 >= 1 (Defferrard et al.; Sec. 3.3):
+    sum_k c_k T_k(Lhat) x with the Chebyshev recurrence T_0 = I,
+    T_1 = Lhat, T_k = 2 Lhat T_{k-1} - T_{k-2}."""
+    t_prev, t = x, lap_hat(L, x)
+    out = c[0] * t_prev + c[1] * t
+    for k in range(2, len(c)):
+        t_prev, t = t, 2.0 * lap_hat(L, t) - t_prev
+        out = out + c[k] * t
+    return out
+
+
+def smooth(L: Level, f, u, theta, eta, wB, cheb=None):
     """One learnable smoothing step (Sec. 3): delta = theta D_A^{-1}(f - A u),
-    u <- u + eta Phi_B(delta)."""
+    u <- u + eta Phi_B(delta); Phi_B is SAGEConv (wB) or, with cheb, the
+    ChebConv polynomial smoother."""
     delta = theta * (f - L.A @ u) / L.diag[:, None]
+    if cheb is not None:
+        return u + eta * cheb_conv(L, delta, cheb)
     return u + eta * conv(L, delta, wB[0], wB[1])
 
 
@@ -175,15 +208,16 @@ def lmg(H: Hierarchy, p: Params, lev: int, f: np.ndarray, u: np.ndarray) -> np.n
     if lev == H.J - 1:
         return sla.cho_solve(H.chol, f)
     L = H.levels[lev]
+    cb = None if p.cheb is None else p.cheb[lev]
     for _ in range(p.nu_pre):
-        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev])
+        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev], cb)
     r = f - L.A @ u
     rc = L.P.T @ conv(L, r, p.wR[lev][0], p.wR[lev][1])
     ec = lmg(H, p, lev + 1, rc, np.zeros_like(rc))
     e = conv(L, L.P @ ec, p.wP[lev][0], p.wP[lev][1])
     u = u + e
     for _ in range(p.nu_post):
-        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev])
+        u = smooth(L, f, u, p.theta[lev], p.eta[lev], p.wB[lev], cb)
     return u
 
 

@@ -127,6 +127,83 @@ def test_jacobi_recovery(poisson33):
     assert np.abs(S - ref).max() < 1e-15
 
 
+# ------------------------------------------------------ ChebConv smoother ----
+
+def ring_level(n):
+    import scipy.sparse as sp
+    i = np.arange(n)
+    G = sp.csr_matrix((np.ones(2 * n), (np.r_[i, i], np.r_[(i + 1) % n, (i - 1) % n])),
+                      shape=(n, n))
+    return O.Level(A=G, diag=np.ones(n), G=G, inv_deg=np.full(n, 0.5), P=None)
+
+
+@pytest.mark.parametrize("K", [1, 2, 5])
+def test_cheb_conv_ring_modes(K):
+    """On a ring every Fourier mode is an eigenvector of the mean operator
+    D_g^{-1} A_g with eigenvalue cos(theta), so Lhat = -D_g^{-1} A_g acts as
+    cos(pi - theta) and T_k(Lhat) as cos(k (pi - theta)), because
+    T_k(cos phi) = cos(k phi)."""
+    n = 24
+    L = ring_level(n)
+    c = np.random.default_rng(K).uniform(-1, 1, K + 1)
+    i = np.arange(n)
+    for m in range(n // 2 + 1):
+        th = 2 * np.pi * m / n
+        for v in (np.cos(th * i), np.sin(th * i)):
+            if np.abs(v).max() < 1e-9:
+                continue
+            got = O.cheb_conv(L, v[:, None], c)[:, 0]
+            ref = sum(c[k] * np.cos(k * (np.pi - th)) for k in range(K + 1)) * v
+            assert np.abs(got - ref).max() < 1e-12, (K, m)
+
+
+def test_cheb_degree_one_is_sage(poisson33):
+    """Degree 1: c_0 I + c_1 Lhat = c_0 I - c_1 D_g^{-1} A_g, the SAGEConv
+    mean with w1 = c_0, w2 = -c_1 (the degree-1 polynomial of the Sec. 3.3
+    remark)."""
+    _, H = poisson33
+    L = H.levels[0]
+    x = np.random.default_rng(3).standard_normal((L.A.shape[0], 2))
+    assert np.array_equal(O.cheb_conv(L, x, [0.8, 0.35]), O.conv(L, x, 0.8, -0.35))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_cheb_smoother_spectrum_closed_form(poisson33, seed):
+    """Degree-3 ChebConv smoother on the five-point Laplacian (Sec. 3.3
+    remark: a degree-K polynomial smoother): with lambda = 1 - (cos p pi h +
+    cos q pi h)/2 the eigenvalues of D_A^{-1} A and lambda_hat = 1 - lambda
+    those of D_g^{-1} A_g, sigma = 1 - eta theta poly lambda where
+    poly = sum_k c_k cos(k arccos(-lambda_hat))."""
+    _, H = poisson33
+    r = np.random.default_rng(10 + seed)
+    theta, eta = r.uniform(0.3, 1.0), r.uniform(0.5, 1.5)
+    c = r.uniform(-0.5, 0.5, 4)
+    c[0] += 1.0
+    L = H.levels[0]
+    n = L.A.shape[0]
+    S = O.smooth(L, np.zeros((n, n)), np.eye(n), theta, eta, None, c)
+    h = 1.0 / 32
+    pq = np.arange(1, 32)
+    lam = 1 - (np.cos(pq[:, None] * np.pi * h) + np.cos(pq[None, :] * np.pi * h)) / 2
+    lam_hat = 1 - lam
+    poly = sum(c[k] * np.cos(k * np.arccos(-lam_hat)) for k in range(4))
+    sigma = 1 - eta * theta * poly * lam
+    ev = np.sort(np.linalg.eigvals(S).real)
+    assert np.abs(ev - np.sort(sigma.ravel())).max() < 1e-12
+
+
+def test_cheb_identity_polynomial_is_jacobi_cycle(poisson33):
+    """Coefficients (1, 0, 0): Phi_B = T_0 = I, so the cycle is the SAGEConv
+    cycle with W1 = 1, W2 = 0 (damped Jacobi smoothing, Sec. 3 remark)."""
+    p, H = poisson33
+    th = random_params(H.J, 5)
+    th.wB[:, 0], th.wB[:, 1] = 1.0, 0.0
+    tc = th.copy()
+    tc.cheb = np.tile([1.0, 0.0, 0.0], (H.J - 1, 1))
+    u0 = np.zeros_like(p.f)
+    assert np.array_equal(O.vcycle(H, th, p.f, u0), O.vcycle(H, tc, p.f, u0))
+
+
 # ---------------------------------------------------------------- cycle ----
 
 def dense_error_propagation(H, p):
