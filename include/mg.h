@@ -157,6 +157,29 @@ mg_status mg_set_layout_policy(int32_t policy);
  * call's stream.  Changing whether a w2 is zero switches kernels. */
 mg_status mg_set_params(mg_ctx* ctx, const mg_params* p);
 
+/* Highest degree mg_set_cheb accepts. */
+#define MG_CHEB_MAX_DEGREE 8
+
+/* ChebConv smoother (Sec. 3.3, remark on polynomial smoothers: a ChebConv
+ * of order K in place of SAGEConv gives a degree-K polynomial smoother).
+ * With K >= 1, every smoothing step of the cycle becomes
+ *   delta = theta_l D_A^{-1} (f - A u),
+ *   u <- u + eta_l sum_{k=0..K} c_{l,k} T_k(Lhat) delta,
+ *   Lhat = D_g^{-1} L_g - I = -D_g^{-1} A_g   (T_0 = I, T_1 = Lhat,
+ *   T_k = 2 Lhat T_{k-1} - T_{k-2}),
+ * i.e. the random-walk normalised Laplacian of the SAGEConv mean, scaled by
+ * lambda_max = 2; degree 1 is SAGEConv with w1 = c_0, w2 = -c_1.  W_B of
+ * mg_params is then unused; theta, eta, Phi_R and Phi_P are kept.
+ *  K     0 (back to the SAGEConv smoother; coef may be NULL) to
+ *        MG_CHEB_MAX_DEGREE
+ *  coef  host [J-1][K+1], level-major (level l's c_0..c_K), copied.
+ * Costs K extra neighbour-mean passes per smoothing step; with K >= 1 all
+ * levels run as grid kernels (the single-block small-level kernel
+ * implements SAGEConv steps only).  Training (mg_forward_record) rejects a
+ * context with K >= 1: the adjoint covers the SAGEConv smoother.
+ * MG_ERR_INVALID for K out of range, a NULL or non-finite coef. */
+mg_status mg_set_cheb(mg_ctx* ctx, int32_t K, const double* coef);
+
 /* One learnable V-cycle (Algorithm 2) on level 0: u <- LMG(A, f, u, 1, Theta).
  * f_dev, u_dev: [n_0][nrhs] in the context precision (double for 64, float
  * for 32); u_dev is the initial guess and is overwritten; f_dev and u_dev
@@ -308,7 +331,8 @@ typedef enum {
   MG_K_PE = 10,             /* P e_c per fine row (then MG_K_PROLONG applies Phi_P) */
   MG_K_SMOOTH_HALO = 11,    /* smoothing step, both stages in one halo-tiled kernel */
   MG_K_RESTRICT_HALO = 12,  /* r and Phi_R(r) in one halo-tiled kernel            */
-  MG_K_PROLONG_HALO = 13    /* u += Phi_P(P e_c) in one halo-tiled kernel         */
+  MG_K_PROLONG_HALO = 13,   /* u += Phi_P(P e_c) in one halo-tiled kernel         */
+  MG_K_CHEB_STEP = 14       /* one Chebyshev pass: T_k and u += eta c_k T_k       */
 } mg_kernel_kind;
 
 typedef struct {

@@ -75,6 +75,7 @@ def lib() -> C.CDLL:
         "mg_setup": ([C.POINTER(vp), C.POINTER(Hier), C.POINTER(CSR), C.POINTER(Params),
                       C.c_int32, C.c_int32, vp], C.c_int),
         "mg_set_params": ([vp, C.POINTER(Params)], C.c_int),
+        "mg_set_cheb": ([vp, C.c_int32, f64p], C.c_int),
         "mg_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_fmg": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_solve": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),

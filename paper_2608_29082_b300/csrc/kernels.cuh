@@ -450,6 +450,40 @@ __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __re
   pdl_launch();
 }
 
+// One pass of the ChebConv smoother (polynomial smoother of Sec. 3.3): with
+// Lhat = D_g^{-1} L_g - I = -D_g^{-1} A_g (mean aggregation, lambda_max = 2)
+// and the Chebyshev recurrence,
+//   k = 1:   T_1 = Lhat T_0;                  u <- u + eta (c_0 T_0 + c_1 T_1)
+//   k >= 2:  T_k = 2 Lhat T_{k-1} - T_{k-2};  u <- u + eta c_k T_k
+// tprev = T_{k-1}, tpp = T_{k-2} (T_0 when k = 1), out = T_k.  out may be tpp:
+// each entry of tpp is read, then overwritten, by the same thread.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_cheb_step(LV<T> L, const T* __restrict__ tprev,
+                                                        const T* tpp, T* out, T* __restrict__ u,
+                                                        int B, const T* __restrict__ prm,
+                                                        const T* __restrict__ coef, int k,
+                                                        int u_zero) {
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
+  if (in_range) {
+    int i, b;
+    split_rb(t, B, i, b);
+    const T lt = -(L.invdeg[i] * row_sum(L, i, tprev, B, b));
+    const T q = tpp[t];
+    T tk, upd;
+    if (k == 1) {
+      tk = lt;
+      upd = fma(coef[1], tk, coef[0] * q);
+    } else {
+      tk = fma(T(2), lt, -q);
+      upd = coef[k] * tk;
+    }
+    out[t] = tk;
+    const T u0 = u_zero ? T(0) : u[t];
+    u[t] = fma(prm[P_ETA], upd, u0);
+  }
+  pdl_launch();
+}
+
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
                                                      const T* __restrict__ uin, T* __restrict__ uout,

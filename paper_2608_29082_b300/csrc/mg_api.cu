@@ -276,6 +276,13 @@ struct mg_ctx {
   double* prm64 = nullptr;
   float* prm32 = nullptr;
   bool prm_dirty = true;
+  // ChebConv smoother (mg_set_cheb): degree (0: SAGEConv), coefficients
+  // [J][MG_CHEB_MAX_DEGREE + 1] on the host and, in the context precision,
+  // on the device
+  int cheb_K = 0;
+  std::vector<double> cheb_host;
+  void* cheb_dev = nullptr;
+  bool cheb_dirty = false;
   uint32_t structure = 0;
   // outer-loop workspace
   int nblk_max = 0;
@@ -444,6 +451,9 @@ struct Issue {
   }
 
   const T* P(int lev) const { return prm + (size_t)lev * mgk::P_COUNT; }
+  const T* chebc(int lev) const {
+    return (const T*)c->cheb_dev + (size_t)lev * (MG_CHEB_MAX_DEGREE + 1);
+  }
   bool conv(int lev, int which) const {
     return c->prm[(size_t)lev * mgk::P_COUNT + which] != 0.0;
   }
@@ -634,6 +644,28 @@ struct Issue {
       if (zero) cudaMemsetAsync(u, 0, N * sizeof(T), s);
       return;
     }
+    if (c->cheb_K > 0) {  // ChebConv smoother: delta, then K recurrence passes
+      for (int k = 0; k < nu; ++k) {
+        const int z = zero && k == 0;
+        pre(MG_K_RESIDUAL_SCALED, lev);
+        op_residual(lev, f, u, D.t, 1, z);
+        post();
+        T* tpp = D.t;  // T_{j-2}
+        T* tp = D.u2;  // T_{j-1}
+        pre(MG_K_CHEB_STEP, lev);
+        launch(mgk::k_cheb_step<T>, g, kThreads, 0, D.view(), (const T*)D.t, (const T*)D.t,
+               D.u2, u, B, P(lev), chebc(lev), 1, z);
+        post();
+        for (int j = 2; j <= c->cheb_K; ++j) {
+          pre(MG_K_CHEB_STEP, lev);
+          launch(mgk::k_cheb_step<T>, g, kThreads, 0, D.view(), (const T*)tp, (const T*)tpp, tpp,
+                 u, B, P(lev), chebc(lev), j, 0);
+          post();
+          std::swap(tp, tpp);
+        }
+      }
+      return;
+    }
     if (!conv(lev, mgk::P_WB2)) {
       T* cur = u;
       T* oth = D.u2;
@@ -794,7 +826,7 @@ struct Issue {
   // rows x rhs <= the threshold, reduced until their data fits in shared
   // memory.
   int tail_level() const {
-    if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels) return c->J - 1;
+    if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels || c->cheb_K > 0) return c->J - 1;
     int lt = c->J - 1;
     while (lt > 0 && (int64_t)c->n[lt - 1] * B <= c->opt_tail_work) --lt;
     if (lt == c->J - 1) return lt;
@@ -889,6 +921,19 @@ struct Issue {
 };
 
 mg_status sync_params(mg_ctx* c, cudaStream_t s) {
+  if (c->cheb_dirty) {
+    // pageable sources that go out of scope: make each copy complete
+    if (c->prec == 64) {
+      MG_CUDA(cudaMemcpyAsync(c->cheb_dev, c->cheb_host.data(),
+                              c->cheb_host.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    } else {
+      std::vector<float> f(c->cheb_host.begin(), c->cheb_host.end());
+      MG_CUDA(cudaMemcpyAsync(c->cheb_dev, f.data(), f.size() * sizeof(float),
+                              cudaMemcpyHostToDevice, s));
+    }
+    MG_CUDA(cudaStreamSynchronize(s));
+    c->cheb_dirty = false;
+  }
   if (!c->prm_dirty) return MG_OK;
   if (c->prec == 64) {
     MG_CUDA(cudaMemcpyAsync(c->prm64, c->prm.data(), c->prm.size() * sizeof(double),
@@ -1064,7 +1109,7 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (void* p : {(void*)c->cholP, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
                   (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
                   (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
-                  (void*)c->gm_zero32, (void*)c->gm_done})
+                  (void*)c->gm_zero32, (void*)c->gm_done, c->cheb_dev})
     if (p) cudaFree(p);
   void* ptrs[] = {c->cholL,  c->cholU,  c->cholDinv, c->prm64,  c->prm32, c->partial,
                   c->rsum,   c->fsum,   c->relres,   c->w64,    c->active, c->iters,
@@ -1265,6 +1310,32 @@ extern "C" mg_status mg_set_params(mg_ctx* c, const mg_params* p) {
   c->nu_post = b;
   c->structure = structure_of(prm, c->J);
   c->prm_dirty = true;
+  c->param_version++;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_set_cheb(mg_ctx* c, int32_t K, const double* coef) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_cheb: ctx is NULL");
+  if (K < 0 || K > MG_CHEB_MAX_DEGREE)
+    return c->fail(MG_ERR_INVALID, "mg_set_cheb: degree out of range");
+  if (K > 0 && !coef) return c->fail(MG_ERR_INVALID, "mg_set_cheb: coef is NULL");
+  const int S = MG_CHEB_MAX_DEGREE + 1;
+  std::vector<double> v((size_t)c->J * S, 0.0);
+  for (int l = 0; K > 0 && l < c->J - 1; ++l)
+    for (int k = 0; k <= K; ++k) {
+      const double x = coef[(size_t)l * (K + 1) + k];
+      if (!std::isfinite(x)) return c->fail(MG_ERR_INVALID, "mg_set_cheb: non-finite coef");
+      v[(size_t)l * S + k] = x;
+    }
+  if (!c->cheb_dev)
+    MG_CUDA(cudaMalloc(&c->cheb_dev, v.size() * (c->prec == 64 ? sizeof(double) : sizeof(float))));
+  if (K != c->cheb_K) {  // other kernels in the cycle
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
+    c->graphs.clear();
+  }
+  c->cheb_host = v;
+  c->cheb_K = K;
+  c->cheb_dirty = true;
   c->param_version++;
   return MG_OK;
 }
@@ -1552,6 +1623,7 @@ extern "C" const char* mg_kernel_name(int32_t kind) {
     case MG_K_SMOOTH_HALO: return "smooth_halo";
     case MG_K_RESTRICT_HALO: return "restrict_conv_halo";
     case MG_K_PROLONG_HALO: return "prolong_halo";
+    case MG_K_CHEB_STEP: return "cheb_conv_update";
     default: return "unknown";
   }
 }

@@ -322,6 +322,10 @@ extern "C" mg_status mg_forward_record(mg_ctx* c, const void* f, void* u, int32_
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_forward_record: ctx is NULL");
   if (!f || !u || f == u || B < 1 || B > c->maxB || K < 1 || K > 1000)
     return c->fail(MG_ERR_INVALID, "mg_forward_record: bad arguments");
+  if (c->cheb_K > 0)
+    return c->fail(MG_ERR_INVALID,
+                   "mg_forward_record: the adjoint covers the SAGEConv smoother, not ChebConv "
+                   "(mg_set_cheb degree > 0)");
   cudaStream_t s = (cudaStream_t)stream;
   mg_status st = sync_params(c, s);
   if (st != MG_OK) return st;

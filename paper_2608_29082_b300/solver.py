@@ -127,6 +127,17 @@ class Solver:
         L.check(self.lib.mg_set_params(self.ctx, C.byref(p)), self.ctx)
         self.params = params
 
+    def set_cheb(self, coef: np.ndarray | None):
+        """ChebConv smoother of degree K = coef.shape[1] - 1 (coef [J-1, K+1],
+        level l's c_0..c_K), or None for the SAGEConv smoother (mg_set_cheb)."""
+        if coef is None:
+            L.check(self.lib.mg_set_cheb(self.ctx, 0, None), self.ctx)
+            return
+        c = np.ascontiguousarray(coef, dtype=np.float64)
+        if c.ndim != 2 or c.shape[0] != self.hier.J - 1 or c.shape[1] < 2:
+            raise ValueError(f"coef: expected shape ({self.hier.J - 1}, K+1) with K >= 1")
+        L.check(self.lib.mg_set_cheb(self.ctx, c.shape[1] - 1, L.ptr(c, L.f64p)), self.ctx)
+
     def _vec(self, x: torch.Tensor, n: int, dtype, name: str) -> torch.Tensor:
         if x.device != self.device or x.dtype != dtype or not x.is_contiguous():
             raise ValueError(f"{name}: expected a contiguous {dtype} tensor on {self.device}")
