@@ -530,6 +530,19 @@ struct Issue {
              P(lev), zero);
     }
   }
+  // One ChebConv recurrence pass (k_cheb_step); out may be tpp.
+  void op_cheb(int lev, const T* tprev, const T* tpp, T* out, T* u, int k, int zero) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto kk) {
+        launch(mgk::k_cheb_step_mb<T, decltype(kk)::value>, mb_grid(D.n, bv), kThreads, 0,
+               D.view(), tprev, tpp, out, u, B, P(lev), chebc(lev), k, zero);
+      });
+    } else {
+      launch(mgk::k_cheb_step<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), tprev, tpp,
+             out, u, B, P(lev), chebc(lev), k, zero);
+    }
+  }
   void op_jacobi(int lev, const T* f, const T* uin, T* uout, int zero) {
     DevLevel<T>& D = L[lev];
     if (const int bv = mbv()) {
@@ -653,13 +666,11 @@ struct Issue {
         T* tpp = D.t;  // T_{j-2}
         T* tp = D.u2;  // T_{j-1}
         pre(MG_K_CHEB_STEP, lev);
-        launch(mgk::k_cheb_step<T>, g, kThreads, 0, D.view(), (const T*)D.t, (const T*)D.t,
-               D.u2, u, B, P(lev), chebc(lev), 1, z);
+        op_cheb(lev, D.t, D.t, D.u2, u, 1, z);
         post();
         for (int j = 2; j <= c->cheb_K; ++j) {
           pre(MG_K_CHEB_STEP, lev);
-          launch(mgk::k_cheb_step<T>, g, kThreads, 0, D.view(), (const T*)tp, (const T*)tpp, tpp,
-                 u, B, P(lev), chebc(lev), j, 0);
+          op_cheb(lev, tp, tpp, tpp, u, j, 0);
           post();
           std::swap(tp, tpp);
         }

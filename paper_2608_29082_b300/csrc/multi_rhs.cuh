@@ -143,6 +143,44 @@ __global__ void __launch_bounds__(kThreads) k_conv_update_mb(LV<T> L, const T* _
   stv<T, BV>(u, base, uu);
 }
 
+// k_cheb_step (kernels.cuh) for a tile of BV right-hand sides: the row's
+// neighbour pattern is read once for the tile; same arithmetic per entry.
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __restrict__ tprev,
+                                                           const T* tpp, T* out,
+                                                           T* __restrict__ u, int B,
+                                                           const T* __restrict__ prm,
+                                                           const T* __restrict__ coef, int k,
+                                                           int u_zero) {
+  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
+  T s[BV], q[BV], uu[BV];
+  row_sum_mb<T, BV>(L, i, tprev, B, b0, s);
+  ldv<T, BV>(tpp, base, q);
+  if (u_zero) {
+#pragma unroll
+    for (int b = 0; b < BV; ++b) uu[b] = T(0);
+  } else {
+    ldv<T, BV>(u, base, uu);
+  }
+  const T id = L.invdeg[i], eta = prm[P_ETA], c0 = coef[0], ck = coef[k];
+#pragma unroll
+  for (int b = 0; b < BV; ++b) {
+    const T lt = -(id * s[b]);
+    T tk, upd;
+    if (k == 1) {
+      tk = lt;
+      upd = fma(ck, tk, c0 * q[b]);
+    } else {
+      tk = fma(T(2), lt, -q[b]);
+      upd = ck * tk;
+    }
+    q[b] = tk;
+    uu[b] = fma(eta, upd, uu[b]);
+  }
+  stv<T, BV>(out, base, q);
+  stv<T, BV>(u, base, uu);
+}
+
 template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __restrict__ f,
                                                         const T* __restrict__ uin,

@@ -11,6 +11,11 @@
         One training step of Algorithm 3 on the 257^2 workloads: K = 10
         unrolled FP32 cycles with per-level checkpoints, the residual loss
         and the hand-written adjoint, for 64 right-hand sides.
+    python -m paper_2608_29082_b300.workload_bench cheb [--refinements 7 --batch 16]
+        ChebConv smoother (mg_set_cheb) of degree 1, 2, 4 against the
+        SAGEConv smoother: FP32 cycle time on the L-shape (16 rhs) and on the
+        513^2 checkerboard (1 rhs), and the level-0 Chebyshev pass's achieved
+        bandwidth against the measured HBM peak.
 """
 from __future__ import annotations
 
@@ -53,6 +58,7 @@ def level_bytes(name: str, hier, lev: int, B: int, b: int) -> float:
         "jacobi_smooth": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
         "residual_scaled": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
         "sage_conv_update": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
+        "cheb_conv_update": nnz_off * (col_b or b) + n * b + 5 * B * n * b,
         "residual": nnz_off * (col_b + b) + n * b + 3 * B * n * b,
         "restrict_conv_fine": nnz_off * (col_b or b) + n * b + 2 * B * n * b,
         "restrict_conv": nnzP * (4 + b) + B * n * b + B * nc * b,
@@ -203,6 +209,52 @@ def run_lshape(a):
     print(json.dumps(out), flush=True)
 
 
+def cycle_ms(S: Solver, f: torch.Tensor, reps: int = 20) -> float:
+    """Median CUDA-event time of one FP32 cycle (graph replay), from zero."""
+    u = torch.zeros_like(f)
+    for _ in range(3):
+        S.vcycle(f, u)
+    ms = []
+    for _ in range(reps):
+        u.zero_()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        S.vcycle(f, u)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return float(np.median(ms))
+
+
+def run_cheb(a):
+    import workloads as W
+    dev = torch.device("cuda")
+    out = {"workload": "ChebConv smoother vs SAGEConv, FP32 cycle, identity-initialised "
+                       "coefficients (c_0 = 1, c_k = 0.1 / k)"}
+    for tag, prob in (("lshape", W.lshape_anisotropic(refinements=a.refinements, batch=a.batch,
+                                                       seed=a.seed)),
+                      ("checker513", W.checkerboard_square(N=513, J=9, ncell=8,
+                                                           values=(1.0, 1e4), batch=1,
+                                                           seed=a.seed))):
+        hier = Hierarchy.from_problem(prob)
+        S = Solver(hier, LMGParams.identity(hier.J), precision=32, max_batch=prob.f.shape[1])
+        f = torch.tensor(prob.f, dtype=torch.float32, device=dev)
+        res = {"dof": hier.sizes[0], "rhs": prob.f.shape[1], "sage_cycle_ms": cycle_ms(S, f)}
+        for K in (1, 2, 4):
+            c = np.zeros((hier.J - 1, K + 1))
+            c[:, 0] = 1.0
+            c[:, 1:] = 0.1 / np.arange(1, K + 1)
+            S.set_cheb(c)
+            res[f"cheb{K}_cycle_ms"] = cycle_ms(S, f)
+            if K == 4 and tag == "lshape":
+                kt, _ = kernel_table(S, hier, f)
+                res["cheb4_level0"] = [r for r in kt if r["level"] == 0][:4]
+        S.close()
+        out[tag] = res
+    out["hbm_peak_gbs"] = hbm_peak()
+    print(json.dumps(out), flush=True)
+
+
 def run_training(a):
     import workloads as W
     prob = W.training_square(a.kind, N=257, J=8, batch=a.batch, seed=a.seed)
@@ -252,6 +304,10 @@ if __name__ == "__main__":
     t.add_argument("--steps", type=int, default=5)
     t.add_argument("--epochs", type=int, default=30)
     t.add_argument("--seed", type=int, default=0)
+    c = sub.add_parser("cheb")
+    c.add_argument("--refinements", type=int, default=7)
+    c.add_argument("--batch", type=int, default=16)
+    c.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    run_lshape(a) if a.cmd == "lshape" else run_training(a)
+    {"lshape": run_lshape, "training": run_training, "cheb": run_cheb}[a.cmd](a)

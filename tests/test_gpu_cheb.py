@@ -168,3 +168,27 @@ def test_cheb_rejects_bad_input_and_training():
     with pytest.raises(MGError):
         S.forward_record(f, torch.zeros_like(f), 2)
     S.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("tile", [2, 4, 8])
+def test_cheb_multi_rhs_tile_bitwise(prec, tile):
+    """The right-hand-side-tiled Chebyshev pass computes every entry with the
+    scalar pass's arithmetic: cycles agree bitwise for every tile width."""
+    p, Ho, Hp = problem("checker65")
+    prm = params(Hp.J, 9)
+    c = cheb_coef(Hp.J, 3, 9)
+    f = np.random.default_rng(4).standard_normal((Hp.sizes[0], 8))
+    dt = torch.float64 if prec == 64 else torch.float32
+    res = []
+    for opt in (0, tile):
+        S = Solver(Hp, prm, precision=prec, max_batch=8)
+        S.set_cheb(c)
+        S.set_option("multi_rhs", opt)
+        u = torch.zeros((Hp.sizes[0], 8), dtype=dt, device=DEV)
+        fg = t64(f).to(dt)
+        for _ in range(2):
+            S.vcycle(fg, u)
+        res.append(u)
+        S.close()
+    assert torch.equal(res[0], res[1])
