@@ -35,10 +35,12 @@ __host__ __device__ inline int gm_stride(int m) { return m * (m + 1) + 4 * m + 2
 // (blockDim = 32 * bt); thread (r, c) owns rows base + r + 32 k, k <
 // kGmRows, of column c.  Loads use clamped in-range addresses (their values
 // are masked afterwards) so that all kGmRows * kGmQ of a round are issued
-// before the arithmetic.  Each thread sums its rows in k order and the 32
-// row-threads of a column are added by a fixed tree, so a right-hand side's
-// results do not depend on the batch.  partial[blk][q][b] as read by
-// k_reduce (nblk = ceil(n / 256)).
+// before the arithmetic; w and the first round are issued together, and
+// each next round is issued before the current round's reduction tree.
+// Each thread sums its rows in k order and the 32 row-threads of a column
+// are added by a fixed tree, so a right-hand side's results do not depend
+// on the batch.  partial[blk][q][b] as read by k_reduce (nblk = ceil(n /
+// 256)).
 constexpr int kGmRows = 8;
 constexpr int kGmQ = 4;
 constexpr int kGmTile = kRedRows * kGmRows;
@@ -65,6 +67,12 @@ struct GmTile {
   __device__ bool ok(int k, int n) const { return okb && i0 + k * kRedRows < n; }
 };
 
+// Right-hand side of entry t of an [n][B] vector (32-bit modulo when the
+// vector has fewer than 2^32 entries).
+__device__ __forceinline__ int gm_col(size_t t, int n, int B) {
+  return (size_t)n * B <= 0xffffffffull ? (int)((unsigned)t % (unsigned)B) : (int)(t % B);
+}
+
 // sh[qq][r * bt + c] summed over the 32 rows r into sh[qq][c], qq < nv
 template <class T>
 __device__ __forceinline__ void gm_rows_reduce(T (*sh)[kGmThreads], int nv) {
@@ -78,6 +86,19 @@ __device__ __forceinline__ void gm_rows_reduce(T (*sh)[kGmThreads], int nv) {
   }
 }
 
+// v[qq][k] = V_{min(q0 + qq, nq - 1)} at this thread's clamped row k
+template <class T>
+__device__ __forceinline__ void gm_load_round(const GmTile& g, const T* __restrict__ V,
+                                              size_t vstride, int q0, int nq, int n, int B,
+                                              T (&v)[kGmQ][kGmRows]) {
+#pragma unroll
+  for (int qq = 0; qq < kGmQ; ++qq) {
+    const T* Vq = V + (size_t)min(q0 + qq, nq - 1) * vstride;
+#pragma unroll
+    for (int k = 0; k < kGmRows; ++k) v[qq][k] = Vq[g.off(k, n, B)];
+  }
+}
+
 // partial[blk][q][b] = the block's rows of V_q . w, q < nq (sums in T)
 template <class T>
 __global__ void __launch_bounds__(kGmThreads) k_gm_dots(const T* __restrict__ V, size_t vstride,
@@ -86,30 +107,23 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_dots(const T* __restrict__ V,
   pdl_wait();
   __shared__ T sh[kGmQ][kGmThreads];
   const GmTile g(B);
-  size_t off[kGmRows];
   T wk[kGmRows];
 #pragma unroll
-  for (int k = 0; k < kGmRows; ++k) {
-    off[k] = g.off(k, n, B);
-    const T v = w[off[k]];
-    wk[k] = g.ok(k, n) ? v : T(0);
-  }
+  for (int k = 0; k < kGmRows; ++k) wk[k] = w[g.off(k, n, B)];
+  T v[kGmQ][kGmRows];
+  gm_load_round(g, V, vstride, 0, nq, n, B, v);
+#pragma unroll
+  for (int k = 0; k < kGmRows; ++k) wk[k] = g.ok(k, n) ? wk[k] : T(0);
   for (int q0 = 0; q0 < nq; q0 += kGmQ) {
     const int nv = min(kGmQ, nq - q0);
-    T v[kGmQ][kGmRows];
-#pragma unroll
-    for (int qq = 0; qq < kGmQ; ++qq) {
-      const T* Vq = V + (size_t)min(q0 + qq, nq - 1) * vstride;
-#pragma unroll
-      for (int k = 0; k < kGmRows; ++k) v[qq][k] = Vq[off[k]];
-    }
 #pragma unroll
     for (int qq = 0; qq < kGmQ; ++qq) {
       T acc = T(0);
 #pragma unroll
-      for (int k = 0; k < kGmRows; ++k) acc = g.ok(k, n) ? fma(v[qq][k], wk[k], acc) : acc;
+      for (int k = 0; k < kGmRows; ++k) acc = fma(v[qq][k], wk[k], acc);
       sh[qq][g.t] = acc;
     }
+    if (q0 + kGmQ < nq) gm_load_round(g, V, vstride, q0 + kGmQ, nq, n, B, v);
     __syncthreads();
     gm_rows_reduce(sh, nv);
     if (g.r == 0 && g.okb)
@@ -129,36 +143,28 @@ __global__ void __launch_bounds__(kGmThreads) k_gm_orth(const T* __restrict__ V,
   pdl_wait();
   __shared__ T sh[1][kGmThreads];
   const GmTile g(B);
-  size_t off[kGmRows];
   T wk[kGmRows];
 #pragma unroll
-  for (int k = 0; k < kGmRows; ++k) {
-    off[k] = g.off(k, n, B);
-    wk[k] = w[off[k]];
-  }
+  for (int k = 0; k < kGmRows; ++k) wk[k] = w[g.off(k, n, B)];
+  T v[kGmQ][kGmRows];
+  gm_load_round(g, V, vstride, 0, nq, n, B, v);
   for (int q0 = 0; q0 < nq; q0 += kGmQ) {
-    T v[kGmQ][kGmRows];
     T hq[kGmQ];
 #pragma unroll
-    for (int qq = 0; qq < kGmQ; ++qq) {
-      const int q = min(q0 + qq, nq - 1);
-      hq[qq] = (T)h[(size_t)q * B + g.bc];
-      const T* Vq = V + (size_t)q * vstride;
-#pragma unroll
-      for (int k = 0; k < kGmRows; ++k) v[qq][k] = Vq[off[k]];
-    }
+    for (int qq = 0; qq < kGmQ; ++qq) hq[qq] = (T)h[(size_t)min(q0 + qq, nq - 1) * B + g.bc];
 #pragma unroll
     for (int qq = 0; qq < kGmQ; ++qq) {
       const bool live = q0 + qq < nq;
 #pragma unroll
       for (int k = 0; k < kGmRows; ++k) wk[k] = live ? fma(-hq[qq], v[qq][k], wk[k]) : wk[k];
     }
+    if (q0 + kGmQ < nq) gm_load_round(g, V, vstride, q0 + kGmQ, nq, n, B, v);
   }
   T ss = T(0);
 #pragma unroll
   for (int k = 0; k < kGmRows; ++k) {
     if (g.ok(k, n)) {
-      w[off[k]] = wk[k];
+      w[g.off(k, n, B)] = wk[k];
       ss = fma(wk[k], wk[k], ss);
     }
   }
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_gm_update(double* __restrict__ u,
   pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * B) return;
-  const int b = (int)(t % B);
+  const int b = gm_col(t, n, B);
   if (!active[b]) return;
   const double* y = small + (size_t)b * gm_stride(m) + m * (m + 1) + 3 * m + 1;
   double acc = 0.0;
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(kThreads) k_gm_scale(const T* w, const double*
   pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)n * B) return;
-  v[t] = (V)(w[t] * (T)inv[t % B]);
+  v[t] = (V)(w[t] * (T)inv[gm_col(t, n, B)]);
 }
 
 }  // namespace mgk

@@ -16,6 +16,10 @@
         SAGEConv smoother: FP32 cycle time on the L-shape (16 rhs) and on the
         513^2 checkerboard (1 rhs), and the level-0 Chebyshev pass's achieved
         bandwidth against the measured HBM peak.
+    python -m paper_2608_29082_b300.workload_bench profile_case
+        A short, fixed case for a profiler's kernel captures: on the L-shape
+        (3.1M DOF, 16 rhs, FP32) one cycle with a degree-2 ChebConv smoother,
+        then one FGMRES(4) cycle (4 Arnoldi steps) with the V-cycle.
 """
 from __future__ import annotations
 
@@ -255,6 +259,26 @@ def run_cheb(a):
     print(json.dumps(out), flush=True)
 
 
+def run_profile_case(a):
+    import workloads as W
+    prob = W.lshape_anisotropic(refinements=a.refinements, batch=a.batch, seed=a.seed)
+    hier = Hierarchy.from_problem(prob)
+    S = Solver(hier, LMGParams.identity(hier.J), precision=32, max_batch=a.batch)
+    f32 = torch.tensor(prob.f, dtype=torch.float32, device="cuda")
+    f64 = torch.tensor(prob.f, dtype=torch.float64, device="cuda")
+    c = np.zeros((hier.J - 1, 3))
+    c[:, 0], c[:, 1:] = 1.0, 0.1
+    S.set_cheb(c)
+    S.vcycle(f32, torch.zeros_like(f32))
+    S.set_cheb(None)
+    _, info = S.solve(f64, torch.zeros_like(f64), tol=1e-12, max_iter=4, method="fgmres",
+                      restart=4)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": f"L-shape {hier.sizes[0]} DOF, {a.batch} rhs",
+                      "fgmres_steps": int(info.iters.max())}), flush=True)
+    S.close()
+
+
 def run_training(a):
     import workloads as W
     prob = W.training_square(a.kind, N=257, J=8, batch=a.batch, seed=a.seed)
@@ -308,6 +332,11 @@ if __name__ == "__main__":
     c.add_argument("--refinements", type=int, default=7)
     c.add_argument("--batch", type=int, default=16)
     c.add_argument("--seed", type=int, default=0)
+    pc = sub.add_parser("profile_case")
+    pc.add_argument("--refinements", type=int, default=7)
+    pc.add_argument("--batch", type=int, default=16)
+    pc.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     torch.cuda.set_device(0)
-    {"lshape": run_lshape, "training": run_training, "cheb": run_cheb}[a.cmd](a)
+    {"lshape": run_lshape, "training": run_training, "cheb": run_cheb,
+     "profile_case": run_profile_case}[a.cmd](a)
