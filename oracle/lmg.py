@@ -87,7 +87,8 @@ class Level:
 @dataclass
 class Hierarchy:
     levels: list[Level]
-    chol: tuple                 # cho_factor of A_J (dense)
+    chol: tuple | None          # cho_factor of A_J (dense), real SPD operators
+    lu: tuple | None = None     # lu_factor of A_J, complex (Helmholtz) operators
 
     @property
     def J(self) -> int:
@@ -102,8 +103,8 @@ def build_hierarchy(problem) -> Hierarchy:
     levels = []
     for lev, ML in enumerate(mesh.levels):
         I = ML.interior
-        pattern = A_full.copy()
-        pattern.data = np.ones_like(pattern.data)
+        pattern = sp.csr_matrix((np.ones(A_full.nnz), A_full.indices.copy(),
+                                 A_full.indptr.copy()), shape=A_full.shape)
         pattern.setdiag(0)
         pattern.eliminate_zeros()
         deg = np.asarray(pattern.sum(axis=1)).ravel()[I]
@@ -118,6 +119,8 @@ def build_hierarchy(problem) -> Hierarchy:
             A_full = drop_small((P_full.T @ A_full @ P_full).tocsr())
         levels.append(Level(A=A, diag=A.diagonal().copy(), G=G, inv_deg=1.0 / deg, P=P))
     AJ = levels[-1].A.toarray()
+    if np.iscomplexobj(AJ):  # complex symmetric, not Hermitian: LU
+        return Hierarchy(levels, None, sla.lu_factor(AJ))
     return Hierarchy(levels, sla.cho_factor(AJ, lower=True))
 
 
@@ -223,6 +226,77 @@ def lmg(H: Hierarchy, p: Params, lev: int, f: np.ndarray, u: np.ndarray) -> np.n
 
 def vcycle(H: Hierarchy, p: Params, f: np.ndarray, u: np.ndarray) -> np.ndarray:
     return lmg(H, p, 0, f, u)
+
+
+# -------------------------------------------- two features per node (d = 2) ----
+
+@dataclass
+class Params2:
+    """Theta with two features per node: each SAGEConv holds W_1, W_2 in
+    R^{2x2} (Sec. 3.2).  The Helmholtz experiment (Sec. 4.3) carries the real
+    and imaginary parts of the complex solution as the two features.
+    WB, WR, WP: (J-1, 2, 2, 2), per level (W_1, W_2)."""
+    theta: np.ndarray
+    eta: np.ndarray
+    WB: np.ndarray
+    WR: np.ndarray
+    WP: np.ndarray
+    nu_pre: int = 1
+    nu_post: int = 1
+
+    @staticmethod
+    def identity(J: int, omega: float = 2.0 / 3.0, nu: int = 1) -> "Params2":
+        """W_1 = I, W_2 = 0, theta = omega, eta = 1 (the initialisation of the
+        Helmholtz experiment): the classical damped-Jacobi cycle on the complex
+        system."""
+        W = np.zeros((J - 1, 2, 2, 2))
+        W[:, 0] = np.eye(2)
+        return Params2(np.full(J - 1, omega), np.ones(J - 1), W.copy(), W.copy(), W.copy(), nu, nu)
+
+
+def features(x: np.ndarray) -> np.ndarray:
+    """Complex (n, B) -> node features (n, B, 2) = (Re, Im)."""
+    return np.stack([x.real, x.imag], axis=-1)
+
+
+def conv2(L: Level, x: np.ndarray, W: np.ndarray) -> np.ndarray:
+    """SAGEConv, mean aggregation, two features per node (Sec. 3.2):
+    Phi(x)_i = W_1 x_i + W_2 mean_{N(i)} x_j for the feature vectors
+    x_i = (Re, Im) of the complex input; returns the complex form."""
+    n, B = x.shape
+    X = features(x)
+    mean = (L.inv_deg[:, None] * (L.G @ X.reshape(n, 2 * B))).reshape(n, B, 2)
+    Y = np.einsum("pq,nbq->nbp", W[0], X) + np.einsum("pq,nbq->nbp", W[1], mean)
+    return Y[..., 0] + 1j * Y[..., 1]
+
+
+def smooth2(L: Level, f, u, theta, eta, WB):
+    """Learnable smoothing step (Sec. 3) on a complex system with two-feature
+    convolutions: delta = theta D_A^{-1}(f - A u) in complex arithmetic,
+    u <- u + eta Phi_B(delta)."""
+    delta = theta * (f - L.A @ u) / L.diag[:, None]
+    return u + eta * conv2(L, delta, WB)
+
+
+def lmg2(H: Hierarchy, p: Params2, lev: int, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    """Algorithm 2 with two features per node on a complex operator; the
+    coarsest level is solved exactly (dense LU)."""
+    if lev == H.J - 1:
+        return sla.lu_solve(H.lu, f)
+    L = H.levels[lev]
+    for _ in range(p.nu_pre):
+        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
+    r = f - L.A @ u
+    rc = L.P.T @ conv2(L, r, p.WR[lev])
+    ec = lmg2(H, p, lev + 1, rc, np.zeros_like(rc))
+    u = u + conv2(L, L.P @ ec, p.WP[lev])
+    for _ in range(p.nu_post):
+        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
+    return u
+
+
+def vcycle2(H: Hierarchy, p: Params2, f: np.ndarray, u: np.ndarray) -> np.ndarray:
+    return lmg2(H, p, 0, f, u)
 
 
 def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:

@@ -473,3 +473,106 @@ def test_fgmres_with_fmg_preconditioner(checker17):
     u, its, hist = O.fgmres(A, f, lambda v: O.fmg(H, th, v[:, None])[:, 0], 1e-10, restart=10)
     assert np.linalg.norm(f - A @ u) < 1e-9 * np.linalg.norm(f)
     assert its < 60
+
+
+# ------------------------------------------ two features per node (d = 2) ----
+
+@pytest.fixture(scope="module", params=[2, 3])
+def helmholtz17(request):
+    p = W.helmholtz_square(17, request.param, k=2 * np.pi, batch=2, seed=3)
+    return p, O.build_hierarchy(p)
+
+
+def random_params2(J, seed, spread=0.3):
+    r = np.random.default_rng(seed)
+    p = O.Params2.identity(J)
+    p.theta = p.theta * (1 + spread * r.uniform(-1, 1, J - 1))
+    p.eta = p.eta * (1 + spread * r.uniform(-1, 1, J - 1))
+    for Wt in (p.WB, p.WR, p.WP):
+        Wt += spread * r.uniform(-1, 1, Wt.shape)
+    return p
+
+
+def test_helmholtz_operator(helmholtz17):
+    """K - k^2 M - i k B is complex symmetric; its imaginary part lives on the
+    boundary (the impedance term) and integrates to -k times the perimeter;
+    coarse operators are the Galerkin products P^T A P (Sec. 2.2)."""
+    p, H = helmholtz17
+    A = H.levels[0].A
+    assert abs(A - A.T).max() == 0
+    k = p.info["wave_number"]
+    assert abs(A.imag.sum() + k * 4.0) < 1e-12
+    for lev in range(H.J - 1):
+        L = H.levels[lev]
+        ref = (L.P.T @ L.A @ L.P).toarray()
+        assert np.abs(H.levels[lev + 1].A.toarray() - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_conv2_complex_weights_are_complex_products(helmholtz17):
+    """W = [[a, -b], [b, a]] acts on (Re, Im) as multiplication by a + ib, so
+    W_1, W_2 of that form give the scalar SAGEConv with complex weights."""
+    _, H = helmholtz17
+    L = H.levels[0]
+    n = L.A.shape[0]
+    r = np.random.default_rng(1)
+    x = r.standard_normal((n, 2)) + 1j * r.standard_normal((n, 2))
+    a, b, c, d = 0.7, -0.4, 0.3, 0.9
+    Wt = np.array([[[a, -b], [b, a]], [[c, -d], [d, c]]])
+    assert np.abs(O.conv2(L, x, Wt) - O.conv(L, x, a + 1j * b, c + 1j * d)).max() < 1e-14
+
+
+def test_conv2_orientation(helmholtz17):
+    """W_1 = [[0, 1], [0, 0]], W_2 = 0 maps the feature vector (Re, Im) to
+    (Im, 0): W acts on feature columns, not transposed."""
+    _, H = helmholtz17
+    L = H.levels[0]
+    n = L.A.shape[0]
+    r = np.random.default_rng(2)
+    x = r.standard_normal((n, 3)) + 1j * r.standard_normal((n, 3))
+    Wt = np.zeros((2, 2, 2))
+    Wt[0] = [[0.0, 1.0], [0.0, 0.0]]
+    assert np.array_equal(O.conv2(L, x, Wt), x.imag + 0j)
+
+
+def real_form(Z):
+    """Complex n x m -> the real 2n x 2m map on [Re; Im]."""
+    return np.block([[Z.real, -Z.imag], [Z.imag, Z.real]])
+
+
+def conv2_matrix(L, Wt):
+    """C(W) = W_1 (x) I + W_2 (x) D_g^{-1} A_g on [Re; Im] (features outer)."""
+    n = L.A.shape[0]
+    return np.kron(Wt[0], np.eye(n)) + np.kron(Wt[1], L.inv_deg[:, None] * L.G.toarray())
+
+
+def dense_error2(H, p, lev=0):
+    """E_l = S^nu_post (I - C_P P (I - E_{l+1}) A_{l+1}^{-1} P^T C_R A_l)
+    S^nu_pre in the real 2n form, E_J = 0, S = I - eta theta C_B D_A^{-1} A."""
+    L = H.levels[lev]
+    n2 = 2 * L.A.shape[0]
+    A = real_form(L.A.toarray())
+    S = np.eye(n2) - p.eta[lev] * p.theta[lev] * conv2_matrix(L, p.WB[lev]) @ \
+        real_form(np.diag(1.0 / L.diag)) @ A
+    P = np.kron(np.eye(2), L.P.toarray())
+    Ac = real_form(H.levels[lev + 1].A.toarray())
+    inner = np.eye(Ac.shape[0]) if lev + 1 == H.J - 1 else \
+        np.eye(Ac.shape[0]) - dense_error2(H, p, lev + 1)
+    cgc = np.eye(n2) - conv2_matrix(L, p.WP[lev]) @ P @ inner @ np.linalg.solve(
+        Ac, P.T @ conv2_matrix(L, p.WR[lev]) @ A)
+    return (np.linalg.matrix_power(S, p.nu_post) @ cgc @ np.linalg.matrix_power(S, p.nu_pre))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_vcycle2_dense_error_propagation(helmholtz17, seed):
+    """The two-feature cycle on the complex Helmholtz system against its error
+    propagation built densely in the real 2n form, applied to every real
+    basis direction (u = e_k and u = i e_k, f = 0)."""
+    _, H = helmholtz17
+    th = random_params2(H.J, seed)
+    th.nu_pre, th.nu_post = 1, 2
+    n = H.levels[0].A.shape[0]
+    U = np.concatenate([np.eye(n), 1j * np.eye(n)], axis=1)
+    out = O.vcycle2(H, th, np.zeros_like(U), U)
+    Eo = np.concatenate([out.real, out.imag], axis=0)
+    E = dense_error2(H, th)
+    assert np.abs(E - Eo).max() < 1e-10 * max(1.0, np.abs(E).max())

@@ -13,6 +13,11 @@ vertices.  The five workloads and their sizes:
                       with correlation length 0.1 (serving requests)
   lshape_anisotropic  jittered L-shape, 7 red refinements (about 3.1M DOF),
                       8 levels, K = R(30 deg) diag(1, 1e-3) R(30 deg)^T
+  helmholtz_square    -Laplace u - k^2 u = f with the impedance condition
+                      du/dn - i k u = 0 on the unit square centred at the
+                      origin: complex A = K - k^2 M - i k B, every vertex a
+                      DOF; column 0 the smoothed-disk training source, the
+                      others seeded complex N(0, 1)
 """
 from __future__ import annotations
 
@@ -92,3 +97,28 @@ def lshape_anisotropic(refinements: int = 7, batch: int = 16, seed: int = 0,
     return Problem(f"lshape_r{refinements}", H, A, fields.rhs(n, batch, seed),
                    dict(refinements=refinements, J=H.J, batch=batch, seed=seed,
                         coefficient=f"anisotropic diag(1,{eps}) rotated {angle} deg"))
+
+
+def helmholtz_square(N: int = 33, J: int = 3, k: float = 2 * np.pi, batch: int = 1,
+                     seed: int = 0) -> Problem:
+    """Helmholtz with the impedance boundary condition (Sec. 4.3) on uniform
+    meshes of [-1/2, 1/2]^2.  The impedance condition keeps every vertex a
+    DOF (no Dirichlet boundary).  A_full is complex symmetric:
+    K - k^2 M - i k B with the P1 stiffness, mass and boundary-edge mass."""
+    H = meshes.square_hierarchy(N, J)
+    for L in H.levels:
+        L.xy = L.xy - 0.5
+        L.boundary = np.zeros(L.nv, dtype=bool)
+    L0 = H.levels[0]
+    A = (fields.assemble_p1(L0).astype(np.complex128) - k * k * fields.assemble_mass_p1(L0)
+         - 1j * k * fields.assemble_boundary_mass_p1(L0)).tocsr()
+    A.sort_indices()
+    M = fields.assemble_mass_p1(L0)
+    f = np.zeros((L0.nv, batch), dtype=np.complex128)
+    f[:, 0] = M @ fields.disk_source(L0.xy, [(0.0, 0.0)])
+    if batch > 1:
+        r = meshes._rng(seed, 1)
+        f[:, 1:] = r.standard_normal((L0.nv, batch - 1)) + 1j * r.standard_normal((L0.nv, batch - 1))
+    return Problem(f"helmholtz_{N}", H, A, f,
+                   dict(N=N, J=J, batch=batch, seed=seed, wave_number=k,
+                        coefficient="Helmholtz, impedance boundary"))

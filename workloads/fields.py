@@ -98,6 +98,54 @@ def assemble_p1(L: MeshLevel, k: np.ndarray | None = None,
     return A
 
 
+def assemble_mass_p1(L: MeshLevel) -> sp.csr_matrix:
+    """P1 mass matrix over all vertices: M_ab = int phi_a phi_b, per element
+    |T|/12 (1 + delta_ab)."""
+    p = L.xy[L.tri]
+    x, y = p[:, :, 0], p[:, :, 1]
+    area = 0.5 * np.abs((x[:, 1] - x[:, 0]) * (y[:, 2] - y[:, 0])
+                        - (x[:, 2] - x[:, 0]) * (y[:, 1] - y[:, 0]))
+    me = (np.ones((3, 3)) + np.eye(3))[None] * (area / 12.0)[:, None, None]
+    rows = np.repeat(L.tri, 3, axis=1).ravel()
+    cols = np.tile(L.tri, (1, 3)).ravel()
+    M = sp.coo_matrix((me.ravel(), (rows, cols)), shape=(L.nv, L.nv)).tocsr()
+    M.sum_duplicates()
+    M.sort_indices()
+    return M
+
+
+def boundary_edges(L: MeshLevel) -> np.ndarray:
+    """(ne, 2) vertex pairs of the edges that belong to one triangle only."""
+    e = np.concatenate([L.tri[:, [0, 1]], L.tri[:, [1, 2]], L.tri[:, [2, 0]]], 0)
+    e = np.sort(e, axis=1)
+    u, cnt = np.unique(e, axis=0, return_counts=True)
+    return u[cnt == 1]
+
+
+def assemble_boundary_mass_p1(L: MeshLevel) -> sp.csr_matrix:
+    """P1 boundary mass over the domain boundary: int_{boundary} phi_a phi_b,
+    per boundary edge |e|/6 (1 + delta_ab)."""
+    e = boundary_edges(L)
+    ln = np.linalg.norm(L.xy[e[:, 0]] - L.xy[e[:, 1]], axis=1)
+    be = (np.ones((2, 2)) + np.eye(2))[None] * (ln / 6.0)[:, None, None]
+    rows = np.repeat(e, 2, axis=1).ravel()
+    cols = np.tile(e, (1, 2)).ravel()
+    Bm = sp.coo_matrix((be.ravel(), (rows, cols)), shape=(L.nv, L.nv)).tocsr()
+    Bm.sum_duplicates()
+    Bm.sort_indices()
+    return Bm
+
+
+def disk_source(xy: np.ndarray, centers, r_s: float = 0.02, eps_s: float = 0.001) -> np.ndarray:
+    """Smoothed disk sources of the Helmholtz experiment (Sec. 4.3): 100 (1 -
+    prod_c tanh((|x - c|^2 - r_s^2) / eps_s)); one centre for training, two
+    for testing."""
+    t = np.ones(xy.shape[0])
+    for c in centers:
+        t = t * np.tanh((((xy - np.asarray(c)) ** 2).sum(1) - r_s ** 2) / eps_s)
+    return 100.0 * (1.0 - t)
+
+
 def rhs(n: int, batch: int, seed: int) -> np.ndarray:
     """f ~ N(0,1) i.i.d. per interior DOF and right-hand side, shape (n, batch),
     right-hand-side index fastest (the node-feature layout X[n][B])."""
