@@ -436,6 +436,61 @@ mg_status mg_smooth_noalloc(int32_t n, const int32_t* rowptr_dev, const int32_t*
                             double* u_dev, int32_t nrhs, int32_t nu, double theta, double eta,
                             double w1, double w2, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Two features per node (d = 2): complex systems
+ *
+ * The Helmholtz experiment (Sec. 4.3) solves a complex system and carries
+ * (Re u, Im u) as two node features; every SAGEConv then holds
+ * W_1, W_2 in R^{2x2} (Sec. 3.2) and may mix them.  An mg2 context runs
+ * that cycle (Algorithm 2):
+ *   delta = theta_l D_A^{-1} (f - A u)       (complex arithmetic)
+ *   u <- u + eta_l Phi_B(delta),  Phi(x)_i = W_1 x_i + W_2 mean_{N(i)} x_j
+ *   r_c = P^T Phi_R(f - A u),  u <- u + Phi_P(P e_c)   (real P)
+ *   coarsest level: e = A_J^{-1} r (A_J inverted in FP64 at set-up)
+ * N(i) is the off-diagonal pattern of row i of A; the mean divides by
+ * 1/inv_deg[i] (which may count eliminated neighbours, as in mg_eliminate).
+ * Vectors: device, [n][nrhs] complex with (Re, Im) adjacent (C99 complex /
+ * torch.complex64 or complex128 layout), in the context precision.
+ * ------------------------------------------------------------------- */
+typedef struct mg2_ctx mg2_ctx;
+
+typedef struct {
+  int32_t n;                /* rows (DOFs) of this level                      */
+  const int32_t* A_indptr;  /* [n+1], CSR of the complex operator A_l          */
+  const int32_t* A_indices; /* [nnz], diagonal included                        */
+  const double* A_vals;     /* [2*nnz], (Re, Im) per entry                     */
+  const double* inv_deg;    /* [n], 1/deg of the convolution graph             */
+  const int32_t* P_indptr;  /* [n+1], real prolongation n x n_{l+1};           */
+  const int32_t* P_indices; /*   all three NULL on the coarsest level          */
+  const double* P_vals;
+} mg2_level;
+
+/* Copies a J-level complex hierarchy (host arrays, copied; the caller keeps
+ * ownership) to the device: CSR operators, prolongations and their
+ * transposes, per-level workspace for max_batch right-hand sides, and the
+ * inverse of the coarsest operator (n_{J-1} <= 4096; MG_ERR_NOT_SPD if it is
+ * singular).  precision 64 or 32.  Parameters start at the classical cycle:
+ * W_1 = I, W_2 = 0, theta = 2/3, eta = 1, one pre- and one post-smoothing
+ * step.  Errors (message via mg_last_error(NULL, ...)): MG_ERR_INVALID for
+ * missing arrays or out-of-range indices, MG_ERR_OOM / MG_ERR_CUDA. */
+mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels, int32_t max_batch,
+                    int32_t precision);
+
+/* Theta for J-1 levels (host, copied): theta[l], eta[l]; WB, WR, WP
+ * [J-1][2][2][2] = per level (W_1, W_2), each row-major 2 x 2 acting on the
+ * feature column (Re, Im).  MG_ERR_INVALID for NULL or non-finite values or
+ * nu outside [0, 16]. */
+mg_status mg2_set_params(mg2_ctx* ctx, const double* theta, const double* eta, const double* WB,
+                         const double* WR, const double* WP, int32_t nu_pre, int32_t nu_post);
+
+/* One cycle on level 0: u <- LMG(A, f, u) for nrhs complex right-hand sides
+ * (device f and u, distinct; 1 <= nrhs <= max_batch).  Queued on stream,
+ * not waited for. */
+mg_status mg2_vcycle(mg2_ctx* ctx, const void* f, void* u, int32_t nrhs, void* stream);
+
+/* Frees every device buffer of the context (synchronises the device). */
+void mg2_destroy(mg2_ctx* ctx);
+
 #ifdef __cplusplus
 }
 #endif

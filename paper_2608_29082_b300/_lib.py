@@ -43,6 +43,12 @@ class Params(C.Structure):
                 ("theta", f64p), ("eta", f64p), ("wB", f64p), ("wR", f64p), ("wP", f64p)]
 
 
+class Level2(C.Structure):
+    """mg2_level: one level of a complex (two-feature) hierarchy."""
+    _fields_ = [("n", C.c_int32), ("A_indptr", i32p), ("A_indices", i32p), ("A_vals", f64p),
+                ("inv_deg", f64p), ("P_indptr", i32p), ("P_indices", i32p), ("P_vals", f64p)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("kernel", C.c_int32), ("level", C.c_int32), ("ms", C.c_float)]
 
@@ -76,6 +82,11 @@ def lib() -> C.CDLL:
                       C.c_int32, C.c_int32, vp], C.c_int),
         "mg_set_params": ([vp, C.POINTER(Params)], C.c_int),
         "mg_set_cheb": ([vp, C.c_int32, f64p], C.c_int),
+        "mg2_setup": ([C.POINTER(vp), C.c_int32, C.POINTER(Level2), C.c_int32, C.c_int32],
+                      C.c_int),
+        "mg2_set_params": ([vp, f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_int32], C.c_int),
+        "mg2_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
+        "mg2_destroy": ([vp], None),
         "mg_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_fmg": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_solve": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmg.so")
 
-SOURCES = ["mg_api.cu", "setup_host.cpp", "noalloc.cu"]
+SOURCES = ["mg_api.cu", "setup_host.cpp", "noalloc.cu", "features2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -16,6 +16,10 @@
         SAGEConv smoother: FP32 cycle time on the L-shape (16 rhs) and on the
         513^2 checkerboard (1 rhs), and the level-0 Chebyshev pass's achieved
         bandwidth against the measured HBM peak.
+    python -m paper_2608_29082_b300.workload_bench features2
+        Two features per node (mg2_*): the Helmholtz operator with impedance
+        boundary at the paper's resolution (h = 1/256, k = 16 pi, J = 5);
+        cycle time in FP32 and FP64 for 1 and 16 right-hand sides.
     python -m paper_2608_29082_b300.workload_bench profile_case
         A short, fixed case for a profiler's kernel captures: on the L-shape
         (3.1M DOF, 16 rhs, FP32) one cycle with a degree-2 ChebConv smoother,
@@ -279,6 +283,40 @@ def run_profile_case(a):
     S.close()
 
 
+def run_features2(a):
+    import workloads as W
+    from paper_2608_29082_b300.features2 import Hierarchy2, Params2, Solver2
+    out = {"workload": f"Helmholtz, impedance boundary, {a.N}x{a.N} vertices (h = 1/{a.N - 1}), "
+                       f"k = {a.k_over_pi:g} pi, J = {a.J}, two features (Re, Im), W_1 = I, "
+                       "W_2 = 0.1 on the smoother"}
+    for B in (1, 16):
+        prob = W.helmholtz_square(a.N, a.J, k=a.k_over_pi * np.pi, batch=B, seed=a.seed)
+        hier = Hierarchy2.from_problem(prob)
+        prm = Params2.identity(hier.J)
+        prm.WB[:, 1] = 0.1 * np.eye(2)
+        for prec in (32, 64):
+            S = Solver2(hier, prm, precision=prec, max_batch=B)
+            dt = torch.complex64 if prec == 32 else torch.complex128
+            f = torch.tensor(prob.f, dtype=dt, device="cuda")
+            u = torch.zeros_like(f)
+            for _ in range(3):
+                S.vcycle(f, u)
+            ms = []
+            for _ in range(20):
+                u.zero_()
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record()
+                S.vcycle(f, u)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out[f"fp{prec}_rhs{B}_cycle_ms"] = round(float(np.median(ms)), 4)
+            S.close()
+        out["dof"] = hier.sizes[0]
+        out["levels"] = hier.sizes
+    print(json.dumps(out), flush=True)
+
+
 def run_training(a):
     import workloads as W
     prob = W.training_square(a.kind, N=257, J=8, batch=a.batch, seed=a.seed)
@@ -332,6 +370,11 @@ if __name__ == "__main__":
     c.add_argument("--refinements", type=int, default=7)
     c.add_argument("--batch", type=int, default=16)
     c.add_argument("--seed", type=int, default=0)
+    f2 = sub.add_parser("features2")
+    f2.add_argument("--N", type=int, default=257)
+    f2.add_argument("--J", type=int, default=5)
+    f2.add_argument("--k-over-pi", type=float, default=16.0)
+    f2.add_argument("--seed", type=int, default=0)
     pc = sub.add_parser("profile_case")
     pc.add_argument("--refinements", type=int, default=7)
     pc.add_argument("--batch", type=int, default=16)
@@ -339,4 +382,4 @@ if __name__ == "__main__":
     a = ap.parse_args()
     torch.cuda.set_device(0)
     {"lshape": run_lshape, "training": run_training, "cheb": run_cheb,
-     "profile_case": run_profile_case}[a.cmd](a)
+     "profile_case": run_profile_case, "features2": run_features2}[a.cmd](a)

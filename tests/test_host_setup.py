@@ -51,3 +51,23 @@ def test_footprint_positive():
     b64 = Hp.footprint_bytes(4, 64)
     b32 = Hp.footprint_bytes(4, 32)
     assert b64 > 0 and b32 > 0
+
+
+@pytest.mark.parametrize("N,J", [(17, 2), (33, 3)])
+def test_complex_hierarchy_matches_oracle(N, J):
+    """The two-feature path's host set-up (native Galerkin on the real and
+    imaginary parts, merged, round-off dropped on complex magnitudes) gives
+    the oracle's complex hierarchy: same patterns, degrees and P."""
+    import oracle as O
+    import workloads as W
+    from paper_2608_29082_b300.features2 import Hierarchy2
+    p = W.helmholtz_square(N, J, k=2 * np.pi, batch=1, seed=0)
+    Ho, Hp = O.build_hierarchy(p), Hierarchy2.from_problem(p)
+    assert Hp.J == Ho.J == J
+    for lev in range(J):
+        a, b = Ho.levels[lev].A, Hp.A[lev]
+        assert ((a != 0) != (b != 0)).nnz == 0
+        assert abs(a - b).max() <= 1e-15 * abs(a).max()
+        assert np.array_equal(Ho.levels[lev].inv_deg, Hp.inv_deg[lev])
+        if lev < J - 1:
+            assert abs(Ho.levels[lev].P - Hp.P[lev]).max() == 0
