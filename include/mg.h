@@ -485,7 +485,9 @@ mg_status mg2_set_params(mg2_ctx* ctx, const double* theta, const double* eta, c
 
 /* One cycle on level 0: u <- LMG(A, f, u) for nrhs complex right-hand sides
  * (device f and u, distinct; 1 <= nrhs <= max_batch).  Queued on stream,
- * not waited for. */
+ * not waited for.  The cycle is captured into a CUDA graph on first use
+ * for each (f, u, nrhs) and replayed afterwards; mg2_set_params drops the
+ * captured graphs (parameters are kernel arguments). */
 mg_status mg2_vcycle(mg2_ctx* ctx, const void* f, void* u, int32_t nrhs, void* stream);
 
 /* Frees every device buffer of the context (synchronises the device). */

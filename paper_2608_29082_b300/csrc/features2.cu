@@ -11,10 +11,15 @@
 // Vectors are [n][nrhs] complex, (Re, Im) adjacent, in the context's
 // precision; operators are CSR with complex values.  One thread per (row,
 // right-hand side).  The context owns every device buffer it allocates.
+// A cycle is captured once per (f, u, nrhs) into a CUDA graph on a private
+// stream and replayed on the caller's stream; parameters are kernel
+// arguments, so mg2_set_params drops the captured graphs.
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -174,6 +179,12 @@ struct mg2_ctx {
   std::vector<double> theta, eta, WB, WR, WP;
   int nu_pre = 1, nu_post = 1;
   std::vector<void*> owned;
+  cudaStream_t cap = nullptr;  // capture stream
+  std::map<std::tuple<const void*, const void*, int>, cudaGraphExec_t> graphs;
+  void drop_graphs() {
+    for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
+    graphs.clear();
+  }
 };
 
 namespace {
@@ -387,6 +398,10 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
   }
   if (levels[J - 1].n > 4096) return fail("mg2_setup: coarsest level larger than 4096 rows");
   mg2_ctx* c = new mg2_ctx;
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return fail("mg2_setup: stream creation failed", MG_ERR_CUDA);
+  }
   c->J = J;
   c->prec = precision;
   c->maxB = max_batch;
@@ -428,6 +443,7 @@ extern "C" mg_status mg2_set_params(mg2_ctx* c, const double* theta, const doubl
   c->WP.assign(WP, WP + (size_t)m * 8);
   c->nu_pre = nu_pre;
   c->nu_post = nu_post;
+  c->drop_graphs();
   return MG_OK;
 }
 
@@ -435,11 +451,33 @@ extern "C" mg_status mg2_vcycle(mg2_ctx* c, const void* f, void* u, int32_t nrhs
   if (!c) return fail("mg2_vcycle: ctx is NULL");
   if (!f || !u || f == u || nrhs < 1 || nrhs > c->maxB) return fail("mg2_vcycle: bad arguments");
   cudaStream_t s = (cudaStream_t)stream;
-  if (c->prec == 64)
-    cycle<double>(c, 0, (const double2*)f, (double2*)u, nrhs, s);
-  else
-    cycle<float>(c, 0, (const float2*)f, (float2*)u, nrhs, s);
-  const cudaError_t e = cudaGetLastError();
+  const auto key = std::make_tuple(f, (const void*)u, (int)nrhs);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(std::string("mg2_vcycle: ") + cudaGetErrorString(e), MG_ERR_CUDA);
+    if (c->prec == 64)
+      cycle<double>(c, 0, (const double2*)f, (double2*)u, nrhs, c->cap);
+    else
+      cycle<float>(c, 0, (const float2*)f, (float2*)u, nrhs, c->cap);
+    const cudaError_t e1 = cudaGetLastError();
+    const cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      return fail(std::string("mg2_vcycle: capture: ") +
+                      cudaGetErrorString(e1 != cudaSuccess ? e1 : e2),
+                  MG_ERR_CUDA);
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e3 = cudaGraphInstantiate(&exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e3 != cudaSuccess)
+      return fail(std::string("mg2_vcycle: instantiate: ") + cudaGetErrorString(e3), MG_ERR_CUDA);
+    if (c->graphs.size() >= 256) c->drop_graphs();  // bounded cache
+    it = c->graphs.emplace(key, exec).first;
+  }
+  const cudaError_t e = cudaGraphLaunch(it->second, s);
   if (e != cudaSuccess)
     return fail(std::string("mg2_vcycle: ") + cudaGetErrorString(e), MG_ERR_CUDA);
   return MG_OK;
@@ -448,6 +486,8 @@ extern "C" mg_status mg2_vcycle(mg2_ctx* c, const void* f, void* u, int32_t nrhs
 extern "C" void mg2_destroy(mg2_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  c->drop_graphs();
+  if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->owned)
     if (p) cudaFree(p);
   delete c;

@@ -117,3 +117,19 @@ def test_two_feature_errors():
     with pytest.raises(MGError):
         S.set_params(bad)
     S.close()
+
+
+def test_set_params_recaptures_the_cycle():
+    """The cycle is replayed from a graph per (f, u, nrhs); new parameters
+    must reach the next cycle on the same buffers."""
+    p, Ho, Hp = problem("helmholtz33")
+    a, b = params(Hp.J, 21), params(Hp.J, 22)
+    S = Solver2(Hp, a, precision=64, max_batch=p.f.shape[1])
+    f = torch.tensor(p.f, dtype=torch.complex128, device="cuda")
+    u = torch.zeros_like(f)
+    S.vcycle(f, u)
+    u_in = u.cpu().numpy()
+    S.set_params(b)
+    S.vcycle(f, u)
+    assert rel(u.cpu().numpy(), O.vcycle2(Ho, to_oracle(b), p.f, u_in)) < 1e-12
+    S.close()
