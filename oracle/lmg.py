@@ -299,6 +299,57 @@ def vcycle2(H: Hierarchy, p: Params2, f: np.ndarray, u: np.ndarray) -> np.ndarra
     return lmg2(H, p, 0, f, u)
 
 
+def fmg2(H: Hierarchy, p: Params2, f: np.ndarray) -> np.ndarray:
+    """Full multigrid with two-feature convolutions: f restricted to every
+    level by P^T Phi_R, the coarsest level solved exactly, on each finer level
+    Phi_P(P u_{l+1}) from a zero iterate as the initial guess of one cycle
+    started on that level (the FMG of the Sec. 4.3 preconditioner tables)."""
+    J = H.J
+    fs = [f]
+    for lev in range(J - 1):
+        L = H.levels[lev]
+        fs.append(L.P.T @ conv2(L, fs[lev], p.WR[lev]))
+    u = sla.lu_solve(H.lu, fs[J - 1])
+    for lev in range(J - 2, -1, -1):
+        L = H.levels[lev]
+        u = lmg2(H, p, lev, fs[lev], conv2(L, L.P @ u, p.WP[lev]))
+    return u
+
+
+def real_vec(z: np.ndarray) -> np.ndarray:
+    """Complex (n,) -> the real 2n vector [Re z; Im z]."""
+    return np.concatenate([z.real, z.imag])
+
+
+def complex_vec(v: np.ndarray) -> np.ndarray:
+    """The real 2n vector [Re; Im] -> complex (n,)."""
+    n = v.shape[0] // 2
+    return v[:n] + 1j * v[n:]
+
+
+def fgmres2(H: Hierarchy, p: Params2, f: np.ndarray, tol: float, precond: str = "vcycle",
+            restart: int = 30, max_iter: int = 300):
+    """FGMRES on a complex system with the two-feature cycle (or FMG) as the
+    right preconditioner, one right-hand side f (complex, 1-D).  With W_1, W_2
+    mixing the features the preconditioner is real-linear, not complex-linear,
+    so the Krylov method runs on the equivalent real system of size 2n,
+    [[Re A, -Im A], [Im A, Re A]] [Re u; Im u] = [Re f; Im f], with real inner
+    products.  Returns (u complex, iterations, residual estimates)."""
+    A = H.levels[0].A
+    Ar = sp.bmat([[A.real, -A.imag], [A.imag, A.real]]).tocsr()
+
+    def M(v):
+        z = complex_vec(v)[:, None]
+        if precond == "fmg":
+            out = fmg2(H, p, z)
+        else:
+            out = lmg2(H, p, 0, z, np.zeros_like(z))
+        return real_vec(out[:, 0])
+
+    u, its, hist = fgmres(Ar, real_vec(f), M, tol, restart=restart, max_iter=max_iter)
+    return complex_vec(u), its, hist
+
+
 def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:
     """Full multigrid (nested iteration), the preconditioner of the Sec. 5
     Krylov experiments.  The right-hand side goes to every level through the

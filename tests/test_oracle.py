@@ -576,3 +576,48 @@ def test_vcycle2_dense_error_propagation(helmholtz17, seed):
     Eo = np.concatenate([out.real, out.imag], axis=0)
     E = dense_error2(H, th)
     assert np.abs(E - Eo).max() < 1e-10 * max(1.0, np.abs(E).max())
+
+
+@pytest.mark.parametrize("precond", ["vcycle", "fmg"])
+@pytest.mark.parametrize("which", ["classical", "random"])
+def test_fgmres2_reaches_the_direct_solution(precond, which):
+    """FGMRES on the real 2n form with the two-feature cycle or FMG as the
+    right preconditioner converges to scipy's direct complex solve."""
+    import scipy.sparse.linalg as spla_
+    p = W.helmholtz_square(33, 3, k=2 * np.pi, batch=2, seed=1)
+    H = O.build_hierarchy(p)
+    th = O.Params2.identity(H.J) if which == "classical" else random_params2(H.J, 4, 0.1)
+    A = H.levels[0].A.tocsc()
+    for b in range(2):
+        ex = spla_.spsolve(A, p.f[:, b])
+        u, its, hist = O.fgmres2(H, th, p.f[:, b], 1e-10, precond=precond)
+        assert hist[-1] < 1e-10 * np.linalg.norm(p.f[:, b]) and its < 60
+        assert np.linalg.norm(u - ex) / np.linalg.norm(ex) < 1e-8
+
+
+def dense_fmg2(H, p, lev=0):
+    """FMG map f -> u in the real 2n form: f_{l+1} = P^T C_R f_l, u_J =
+    A_J^{-1} f_J, and on level l one cycle from u_0 = C_P P u_{l+1}; a
+    consistent cycle is affine, u = E_l (u_0 - u*) + u*, u* = A_l^{-1} f_l."""
+    L = H.levels[lev]
+    A = real_form(L.A.toarray())
+    Ainv = np.linalg.inv(A)
+    if lev == H.J - 1:
+        return Ainv
+    P = np.kron(np.eye(2), L.P.toarray())
+    R = P.T @ conv2_matrix(L, p.WR[lev])
+    U0 = conv2_matrix(L, p.WP[lev]) @ P @ dense_fmg2(H, p, lev + 1) @ R
+    E = dense_error2(H, p, lev)
+    return E @ (U0 - Ainv) + Ainv
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_fmg2_dense_nested_iteration(helmholtz17, seed):
+    _, H = helmholtz17
+    th = random_params2(H.J, 30 + seed)
+    n = H.levels[0].A.shape[0]
+    F = np.concatenate([np.eye(n), 1j * np.eye(n)], axis=1)
+    out = O.fmg2(H, th, F)
+    Mo = np.concatenate([out.real, out.imag], axis=0)
+    M = dense_fmg2(H, th)
+    assert np.abs(M - Mo).max() < 1e-10 * max(1.0, np.abs(M).max())
