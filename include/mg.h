@@ -490,6 +490,25 @@ mg_status mg2_set_params(mg2_ctx* ctx, const double* theta, const double* eta, c
  * captured graphs (parameters are kernel arguments). */
 mg_status mg2_vcycle(mg2_ctx* ctx, const void* f, void* u, int32_t nrhs, void* stream);
 
+/* Restarted flexible GMRES on the complex system, with one two-feature
+ * cycle from zero (precond 0) or one full multigrid (precond 1) as right
+ * preconditioner: the pairing of the paper's Helmholtz preconditioner
+ * tables (Sec. 4.3).  W_1, W_2 mix Re and Im, so the preconditioner is
+ * real-linear, not complex-linear: the Krylov method runs on the equivalent
+ * real system of size 2n, [[Re A, -Im A], [Im A, Re A]], with real inner
+ * products sum_i (Re x_i Re y_i + Im x_i Im y_i) per right-hand side.
+ * Classical Gram-Schmidt twice, FP64 Hessenberg with Givens rotations; the
+ * host drives the restarts (restart = m, 1..64).  f and u: device, FP64
+ * complex [n][nrhs] whatever the context precision (the preconditioner runs
+ * in the context precision); u is the initial guess and receives the
+ * iterate.  iters_out / relres_out (host, [nrhs], may be NULL): Arnoldi
+ * steps and the true final relative residual per right-hand side.  Returns
+ * MG_OK, MG_NOT_CONVERGED (max_iter steps without meeting tol),
+ * MG_ERR_DIVERGED (non-finite residual) or an error; synchronises stream. */
+mg_status mg2_solve_fgmres(mg2_ctx* ctx, const void* f, void* u, int32_t nrhs, double tol,
+                           int32_t max_iter, int32_t restart, int32_t precond,
+                           int32_t* iters_out, double* relres_out, void* stream);
+
 /* Frees every device buffer of the context (synchronises the device). */
 void mg2_destroy(mg2_ctx* ctx);
 

@@ -86,6 +86,8 @@ def lib() -> C.CDLL:
                       C.c_int),
         "mg2_set_params": ([vp, f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_int32], C.c_int),
         "mg2_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
+        "mg2_solve_fgmres": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                              i32p, f64p, vp], C.c_int),
         "mg2_destroy": ([vp], None),
         "mg_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg_fmg": ([vp, vp, vp, C.c_int32, vp], C.c_int),

@@ -159,6 +159,226 @@ __global__ void __launch_bounds__(kF2Threads)
 
 dim3 grid_of(size_t work) { return dim3((unsigned)((work + kF2Threads - 1) / kF2Threads)); }
 
+// ---- FGMRES on the real form (FP64 vectors, double2 = (Re, Im)) ----------
+// A right-hand side's vectors are real 2n vectors [Re; Im]; inner products
+// are sum_i Re x_i Re y_i + Im x_i Im y_i.  Each (vector, rhs) sum is one
+// block over the rows in a fixed order, so results do not depend on B.
+
+// w = A z (complex CSR, FP64)
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_apply(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+              const double2* __restrict__ av, const double2* __restrict__ z,
+              double2* __restrict__ w, int B) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * B) return;
+  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
+  double sx = 0.0, sy = 0.0;
+  for (int e = rp[i]; e < rp[i + 1]; ++e) {
+    const double2 a = av[e];
+    const double2 x = z[(size_t)ci[e] * B + b];
+    sx += a.x * x.x - a.y * x.y;
+    sy += a.x * x.y + a.y * x.x;
+  }
+  w[t] = make_double2(sx, sy);
+}
+
+// out[q * B + b] = <V_q, w>_b for block (q, b); V_q = V + q * vstride
+// (w = nullptr: <V_q, V_q>)
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_dots(const double2* __restrict__ V, size_t vstride, const double2* __restrict__ w,
+             int n, int B, double* __restrict__ out) {
+  __shared__ double sh[kF2Threads];
+  const int q = blockIdx.x, b = blockIdx.y;
+  const double2* x = V + (size_t)q * vstride;
+  const double2* y = w ? w : x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 a = x[(size_t)i * B + b], c = y[(size_t)i * B + b];
+    s += a.x * c.x + a.y * c.y;
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int k = blockDim.x / 2; k >= 1; k >>= 1) {
+    if ((int)threadIdx.x < k) sh[threadIdx.x] += sh[threadIdx.x + k];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[(size_t)q * B + b] = sh[0];
+}
+
+// w -= sum_{q < nq} h[q * B + b] V_q
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_orth(const double2* __restrict__ V, size_t vstride, double2* __restrict__ w,
+             const double* __restrict__ h, int nq, int n, int B) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * B) return;
+  const int b = (int)(t % B);
+  double2 o = w[t];
+  for (int q = 0; q < nq; ++q) {
+    const double hq = h[(size_t)q * B + b];
+    const double2 v = V[(size_t)q * vstride + t];
+    o.x -= hq * v.x;
+    o.y -= hq * v.y;
+  }
+  w[t] = o;
+}
+
+// v = w * inv[b]
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_scale(const double2* w, const double* __restrict__ inv, double2* v, int n, int B) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * B) return;
+  const double s = inv[t % B];
+  const double2 x = w[t];
+  v[t] = make_double2(x.x * s, x.y * s);
+}
+
+// u += sum_{q < nq} y_q Z_q for the active right-hand sides
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_update(double2* __restrict__ u, const double2* __restrict__ Z, size_t vstride,
+               const double* __restrict__ y, int ystride, int nq, const int* __restrict__ active,
+               int n, int B) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)n * B) return;
+  const int b = (int)(t % B);
+  if (!active[b]) return;
+  const double* yb = y + (size_t)b * ystride;
+  double2 o = u[t];
+  for (int q = 0; q < nq; ++q) {
+    const double2 z = Z[(size_t)q * vstride + t];
+    o.x += yb[q] * z.x;
+    o.y += yb[q] * z.y;
+  }
+  u[t] = o;
+}
+
+// FP64 <-> context precision copies of level-0 vectors
+template <class T>
+__global__ void __launch_bounds__(kF2Threads)
+    k2g_convert(const void* __restrict__ x, void* __restrict__ y, size_t N, int to_ctx) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= N) return;
+  using P2 = typename Pair<T>::type;
+  if (to_ctx) {
+    const double2 v = ((const double2*)x)[t];
+    P2 o;
+    o.x = (T)v.x;
+    o.y = (T)v.y;
+    ((P2*)y)[t] = o;
+  } else {
+    const P2 v = ((const P2*)x)[t];
+    ((double2*)y)[t] = make_double2((double)v.x, (double)v.y);
+  }
+}
+
+// Per right-hand side b, small[b * stride]: H (m+1) x m (column j at
+// j (m+1)), cs[m], sn[m], g[m+1], y[m].
+__host__ __device__ inline int k2g_stride(int m) { return m * (m + 1) + 4 * m + 1; }
+
+// Restart: beta = ||r||, relres, the active set, g = beta e_1, inv = 1/beta,
+// done = 0; state[0] = active count, state[1] = 1 if non-finite.  One block.
+__global__ void k2g_restart(const double* __restrict__ rsum, const double* __restrict__ fsum,
+                            double tol, int m, int B, int* __restrict__ active,
+                            double* __restrict__ relres, double* __restrict__ small,
+                            double* __restrict__ inv, int* __restrict__ done,
+                            int* __restrict__ state) {
+  __shared__ int cnt, bad;
+  if (threadIdx.x == 0) {
+    cnt = 0;
+    bad = 0;
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    const double beta = sqrt(rsum[b]), fn = sqrt(fsum[b]);
+    const double rel = fn > 0.0 ? beta / fn : beta;
+    relres[b] = rel;
+    if (!isfinite(rel)) atomicAdd(&bad, 1);
+    if (active[b] && !(rel < tol) && isfinite(rel))
+      atomicAdd(&cnt, 1);
+    else
+      active[b] = 0;
+    double* g = small + (size_t)b * k2g_stride(m) + m * (m + 1) + 2 * m;
+    for (int i = 0; i <= m; ++i) g[i] = 0.0;
+    g[0] = beta;
+    inv[b] = beta > 0.0 && isfinite(beta) ? 1.0 / beta : 0.0;
+    done[b] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    state[0] = cnt;
+    state[1] = bad;
+  }
+}
+
+// Arnoldi step j: H column j = h1 + h2 and ||w||, rotations, the estimate;
+// a right-hand side in its cycle counts the step and finishes it (done =
+// j + 1) when the estimate meets tol or is not finite.  state[3] = right-hand
+// sides still in their cycle.  One block.
+__global__ void k2g_arnoldi(double* __restrict__ small, const double* __restrict__ h1,
+                            const double* __restrict__ h2, const double* __restrict__ wn,
+                            const double* __restrict__ fsum, double tol, int m, int j, int B,
+                            const int* __restrict__ active, int* __restrict__ iters,
+                            double* __restrict__ inv, double* __restrict__ relres,
+                            int* __restrict__ done, int* __restrict__ state) {
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    double* sb = small + (size_t)b * k2g_stride(m);
+    double* cs = sb + m * (m + 1);
+    double* sn = cs + m;
+    double* g = sn + m;
+    double* Hj = sb + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = h1[(size_t)i * B + b] + h2[(size_t)i * B + b];
+    const double hn = sqrt(wn[b]);
+    Hj[j + 1] = hn;
+    inv[b] = hn > 0.0 && isfinite(hn) ? 1.0 / hn : 0.0;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+      Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+      Hj[i] = t;
+    }
+    const double a = Hj[j], c2 = Hj[j + 1];
+    const double r = sqrt(a * a + c2 * c2);
+    cs[j] = r > 0.0 ? a / r : 1.0;
+    sn[j] = r > 0.0 ? c2 / r : 0.0;
+    Hj[j] = r;
+    Hj[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    if (active[b] && !done[b]) {
+      const double fn = sqrt(fsum[b]);
+      const double est = fn > 0.0 ? fabs(g[j + 1]) / fn : fabs(g[j + 1]);
+      iters[b] += 1;
+      relres[b] = est;
+      if (est < tol || !isfinite(est))
+        done[b] = j + 1;
+      else
+        atomicAdd(&cnt, 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) state[3] = cnt;
+}
+
+// y = H^{-1} g over the columns each right-hand side used; y = 0 beyond.
+__global__ void k2g_solve_y(double* __restrict__ small, int m, int jl, int B,
+                            const int* __restrict__ active, const int* __restrict__ done) {
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    if (!active[b]) continue;
+    double* sb = small + (size_t)b * k2g_stride(m);
+    const double* g = sb + m * (m + 1) + 2 * m;
+    double* y = sb + m * (m + 1) + 3 * m + 1;
+    const int jb = done[b] ? min(done[b] - 1, jl) : jl;
+    for (int i = jl; i > jb; --i) y[i] = 0.0;
+    for (int i = jb; i >= 0; --i) {
+      double t = g[i];
+      for (int k = i + 1; k <= jb; ++k) t -= sb[(size_t)k * (m + 1) + i] * y[k];
+      const double d = sb[(size_t)i * (m + 1) + i];
+      y[i] = d != 0.0 ? t / d : 0.0;
+    }
+  }
+}
+
 }  // namespace
 
 struct mg2_ctx {
@@ -180,6 +400,13 @@ struct mg2_ctx {
   int nu_pre = 1, nu_post = 1;
   std::vector<void*> owned;
   cudaStream_t cap = nullptr;  // capture stream
+  // FGMRES (mg2_solve_fgmres): the FP64 level-0 operator, and the workspace
+  // for restart length gm_m (allocated on first use)
+  void* av64 = nullptr;  // double2, level 0 (= lev[0].av in FP64 contexts)
+  int gm_m = 0;
+  double *gmV = nullptr, *gmZ = nullptr, *gmR = nullptr, *gmSmall = nullptr, *gmH = nullptr;
+  double* gmVec = nullptr;  // fsum, rsum, wn, inv, relres: 5 * maxB
+  int* gmInt = nullptr;     // active, iters, done: 3 * maxB; state: 4
   std::map<std::tuple<const void*, const void*, int>, cudaGraphExec_t> graphs;
   void drop_graphs() {
     for (auto& kv : graphs) cudaGraphExecDestroy(kv.second);
@@ -310,6 +537,15 @@ mg_status setup_typed(mg2_ctx* c, const mg2_level* L) {
         return fail("mg2_setup: device allocation or copy failed", MG_ERR_CUDA);
     }
   }
+  // the level-0 operator in FP64 for FGMRES's outer products
+  if (sizeof(T) == sizeof(double)) {
+    c->av64 = c->lev[0].av;
+  } else {
+    std::vector<double> a64(2 * (size_t)c->lev[0].nnz);
+    std::copy(L[0].A_vals, L[0].A_vals + a64.size(), a64.begin());
+    if (!upload(c, &c->av64, a64.data(), a64.size()))
+      return fail("mg2_setup: device allocation or copy failed", MG_ERR_CUDA);
+  }
   // the coarsest operator, inverted in FP64 on the host
   const mg2_level& s = L[J - 1];
   const int n = s.n;
@@ -371,6 +607,72 @@ void cycle(mg2_ctx* c, int l, const typename Pair<T>::type* f, typename Pair<T>:
   k2_spmv_real<T><<<g, kF2Threads, 0, s>>>(L.n, L.prp, L.pci, (const T*)L.pv, (const P2*)C.u, t, B);
   k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, t, u, B, wp, T(1), 2);
   smooth(c->nu_post);
+}
+
+// Full multigrid with two-feature convolutions: f restricted to every level
+// by P^T Phi_R, the coarsest level solved exactly, then on each finer level
+// Phi_P(P u_{l+1}) (from a zero iterate) starts one cycle on that level.
+// Levels below 0 use their own f / u buffers; a level's cycle reuses the
+// buffers of the levels below it once their FMG values are consumed.
+template <class T>
+void fmg(mg2_ctx* c, const typename Pair<T>::type* f0, typename Pair<T>::type* u0, int B,
+         cudaStream_t s) {
+  using P2 = typename Pair<T>::type;
+  const int J = c->J;
+  for (int l = 0; l < J - 1; ++l) {
+    mg2_ctx::Lev& L = c->lev[l];
+    mg2_ctx::Lev& C = c->lev[l + 1];
+    const P2* fl = l == 0 ? f0 : (const P2*)L.f;
+    k2_conv<T><<<grid_of((size_t)L.n * B), kF2Threads, 0, s>>>(
+        L.n, L.rp, L.ci, (const T*)L.invdeg, fl, (P2*)L.t2, B, conv_of<T>(c->WR, l), T(1), 0);
+    k2_spmv_real<T><<<grid_of((size_t)C.n * B), kF2Threads, 0, s>>>(
+        C.n, L.trp, L.tci, (const T*)L.tv, (const P2*)L.t2, (P2*)C.f, B);
+  }
+  mg2_ctx::Lev& LJ = c->lev[J - 1];
+  const P2* fJ = J == 1 ? f0 : (const P2*)LJ.f;
+  P2* uJ = J == 1 ? u0 : (P2*)LJ.u;
+  k2_dense<T><<<grid_of((size_t)LJ.n * B), kF2Threads, 0, s>>>(LJ.n, (const P2*)c->cinv, fJ, uJ, B);
+  for (int l = J - 2; l >= 0; --l) {
+    mg2_ctx::Lev& L = c->lev[l];
+    mg2_ctx::Lev& C = c->lev[l + 1];
+    const P2* fl = l == 0 ? f0 : (const P2*)L.f;
+    P2* ul = l == 0 ? u0 : (P2*)L.u;
+    const dim3 g = grid_of((size_t)L.n * B);
+    k2_spmv_real<T><<<g, kF2Threads, 0, s>>>(L.n, L.prp, L.pci, (const T*)L.pv, (const P2*)C.u,
+                                             (P2*)L.t, B);
+    k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, (const P2*)L.t, ul,
+                                        B, conv_of<T>(c->WP, l), T(1), 0);
+    cycle<T>(c, l, fl, ul, B, s);
+  }
+}
+
+// z = M(v) for FP64 level-0 vectors: one cycle from zero (which = 0) or one
+// FMG (1) in the context precision.
+template <class T>
+void precondition(mg2_ctx* c, int which, const double2* v, double2* z, int B, cudaStream_t s) {
+  using P2 = typename Pair<T>::type;
+  mg2_ctx::Lev& L0 = c->lev[0];
+  const size_t N = (size_t)L0.n * B;
+  const bool fp64 = sizeof(T) == sizeof(double);
+  const P2* fin = fp64 ? (const P2*)v : (const P2*)L0.f;
+  P2* uout = fp64 ? (P2*)z : (P2*)L0.u;
+  if (!fp64) k2g_convert<T><<<grid_of(N), kF2Threads, 0, s>>>(v, L0.f, N, 1);
+  if (which == 1) {
+    fmg<T>(c, fin, uout, B, s);
+  } else {
+    cudaMemsetAsync(uout, 0, N * sizeof(P2), s);
+    cycle<T>(c, 0, fin, uout, B, s);
+  }
+  if (!fp64) k2g_convert<T><<<grid_of(N), kF2Threads, 0, s>>>(L0.u, z, N, 0);
+}
+
+void free_gm(mg2_ctx* c) {
+  for (void* p : {(void*)c->gmV, (void*)c->gmZ, (void*)c->gmR, (void*)c->gmSmall, (void*)c->gmH,
+                  (void*)c->gmVec, (void*)c->gmInt})
+    if (p) cudaFree(p);
+  c->gmV = c->gmZ = c->gmR = c->gmSmall = c->gmH = c->gmVec = nullptr;
+  c->gmInt = nullptr;
+  c->gm_m = 0;
 }
 
 }  // namespace
@@ -483,9 +785,131 @@ extern "C" mg_status mg2_vcycle(mg2_ctx* c, const void* f, void* u, int32_t nrhs
   return MG_OK;
 }
 
+extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_t B, double tol,
+                                      int32_t max_iter, int32_t restart, int32_t precond,
+                                      int32_t* iters_out, double* relres_out, void* stream) {
+  if (!c) return fail("mg2_solve_fgmres: ctx is NULL");
+  if (!f || !u || f == u || B < 1 || B > c->maxB || !(tol > 0.0) || max_iter < 0 || restart < 1 ||
+      restart > 64 || (precond != 0 && precond != 1))
+    return fail("mg2_solve_fgmres: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int m = restart;
+  const int n0 = c->lev[0].n;
+  const size_t N0 = (size_t)n0 * c->maxB;
+  const size_t mb = (size_t)c->maxB;
+  if (c->gm_m != m) {
+    cudaDeviceSynchronize();
+    free_gm(c);
+    const bool ok =
+        cudaMalloc(&c->gmV, (m + 1) * N0 * sizeof(double2)) == cudaSuccess &&
+        cudaMalloc(&c->gmZ, m * N0 * sizeof(double2)) == cudaSuccess &&
+        cudaMalloc(&c->gmR, N0 * sizeof(double2)) == cudaSuccess &&
+        cudaMalloc(&c->gmSmall, mb * k2g_stride(m) * sizeof(double)) == cudaSuccess &&
+        cudaMalloc(&c->gmH, 2 * (m + 1) * mb * sizeof(double)) == cudaSuccess &&
+        cudaMalloc(&c->gmVec, 5 * mb * sizeof(double)) == cudaSuccess &&
+        cudaMalloc(&c->gmInt, (3 * mb + 4) * sizeof(int)) == cudaSuccess;
+    if (!ok) {
+      free_gm(c);
+      return fail("mg2_solve_fgmres: device allocation failed", MG_ERR_OOM);
+    }
+    c->gm_m = m;
+  }
+  const size_t vs = (size_t)n0 * B;  // stride between basis vectors (double2)
+  double2* V = (double2*)c->gmV;
+  double2* Z = (double2*)c->gmZ;
+  double2* r = (double2*)c->gmR;
+  double* h1 = c->gmH;
+  double* h2 = c->gmH + (size_t)(m + 1) * B;
+  double *fsum = c->gmVec, *rsum = c->gmVec + mb, *wn = c->gmVec + 2 * mb;
+  double *inv = c->gmVec + 3 * mb, *relres = c->gmVec + 4 * mb;
+  int *active = c->gmInt, *iters = c->gmInt + mb, *done = c->gmInt + 2 * mb;
+  int* state = c->gmInt + 3 * mb;
+  const mg2_ctx::Lev& L0 = c->lev[0];
+  const dim3 g = grid_of(vs), gb(1, B);
+  const double2* fd = (const double2*)f;
+  double2* ud = (double2*)u;
+  std::vector<int> ones(B, 1);
+  int hs[4] = {0, 0, 0, 0};
+  auto read_state = [&]() -> bool {
+    return cudaMemcpyAsync(hs, state, sizeof(hs), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+           cudaStreamSynchronize(s) == cudaSuccess;
+  };
+  k2g_dots<<<gb, kF2Threads, 0, s>>>(fd, 0, nullptr, n0, B, fsum);
+  cudaMemsetAsync(iters, 0, B * sizeof(int), s);
+  cudaMemcpyAsync(active, ones.data(), B * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return fail("mg2_solve_fgmres: set-up failed", MG_ERR_CUDA);
+  int total = 0;
+  bool diverged = false;
+  for (;;) {
+    k2_residual<double><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd,
+                                                 ud, r, B, (const double2*)nullptr, 0.0, 0, 0);
+    k2g_dots<<<gb, kF2Threads, 0, s>>>(r, 0, nullptr, n0, B, rsum);
+    k2g_restart<<<1, kF2Threads, 0, s>>>(rsum, fsum, tol, m, B, active, relres, c->gmSmall, inv,
+                                         done, state);
+    k2g_scale<<<g, kF2Threads, 0, s>>>(r, inv, V, n0, B);
+    if (!read_state()) return fail("mg2_solve_fgmres: restart failed", MG_ERR_CUDA);
+    if (hs[1]) {
+      diverged = true;
+      break;
+    }
+    if (hs[0] == 0 || total >= max_iter) break;
+    int jl = -1;
+    for (int j = 0; j < m && total < max_iter; ++j) {
+      double2* Vj = V + (size_t)j * vs;
+      double2* Vn = V + (size_t)(j + 1) * vs;
+      double2* Zj = Z + (size_t)j * vs;
+      if (c->prec == 64)
+        precondition<double>(c, precond, Vj, Zj, B, s);
+      else
+        precondition<float>(c, precond, Vj, Zj, B, s);
+      k2g_apply<<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, Zj, Vn, B);
+      for (int pass = 0; pass < 2; ++pass) {  // classical Gram-Schmidt, twice
+        double* h = pass == 0 ? h1 : h2;
+        k2g_dots<<<dim3(j + 1, B), kF2Threads, 0, s>>>(V, vs, Vn, n0, B, h);
+        k2g_orth<<<g, kF2Threads, 0, s>>>(V, vs, Vn, h, j + 1, n0, B);
+      }
+      k2g_dots<<<gb, kF2Threads, 0, s>>>(Vn, 0, nullptr, n0, B, wn);
+      k2g_arnoldi<<<1, kF2Threads, 0, s>>>(c->gmSmall, h1, h2, wn, fsum, tol, m, j, B, active,
+                                           iters, inv, relres, done, state);
+      k2g_scale<<<g, kF2Threads, 0, s>>>(Vn, inv, Vn, n0, B);
+      ++total;
+      jl = j;
+      if (!read_state()) return fail("mg2_solve_fgmres: Arnoldi step failed", MG_ERR_CUDA);
+      if (hs[3] == 0) break;
+    }
+    if (jl < 0) break;
+    k2g_solve_y<<<1, kF2Threads, 0, s>>>(c->gmSmall, m, jl, B, active, done);
+    k2g_update<<<g, kF2Threads, 0, s>>>(ud, Z, vs, c->gmSmall + m * (m + 1) + 3 * m + 1,
+                                        k2g_stride(m), jl + 1, active, n0, B);
+  }
+  // the true residual of the final iterate
+  k2_residual<double><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd, ud,
+                                               r, B, (const double2*)nullptr, 0.0, 0, 0);
+  k2g_dots<<<gb, kF2Threads, 0, s>>>(r, 0, nullptr, n0, B, rsum);
+  std::vector<double> hr(B), hf(B);
+  std::vector<int> hi(B);
+  if (cudaMemcpyAsync(hr.data(), rsum, B * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hf.data(), fsum, B * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaMemcpyAsync(hi.data(), iters, B * sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return fail(std::string("mg2_solve_fgmres: ") + cudaGetErrorString(cudaGetLastError()),
+                MG_ERR_CUDA);
+  mg_status st = MG_OK;
+  for (int b = 0; b < B; ++b) {
+    const double rel = hf[b] > 0.0 ? std::sqrt(hr[b] / hf[b]) : std::sqrt(hr[b]);
+    if (relres_out) relres_out[b] = rel;
+    if (iters_out) iters_out[b] = hi[b];
+    if (!(rel < tol)) st = MG_NOT_CONVERGED;
+  }
+  if (diverged) return fail("mg2_solve_fgmres: non-finite residual", MG_ERR_DIVERGED);
+  if (st == MG_NOT_CONVERGED) mgi::set_global_error(st, "mg2_solve_fgmres: tolerance not met");
+  return st;
+}
+
 extern "C" void mg2_destroy(mg2_ctx* c) {
   if (!c) return;
   cudaDeviceSynchronize();
+  free_gm(c);
   c->drop_graphs();
   if (c->cap) cudaStreamDestroy(c->cap);
   for (void* p : c->owned)

@@ -17,7 +17,7 @@ import scipy.sparse as sp
 import torch
 
 from . import _lib as L
-from .solver import _stream_handle
+from .solver import SolveInfo, _stream_handle
 
 DROP_TOL = 1e-12
 
@@ -171,6 +171,33 @@ class Solver2:
         L.check(self.lib.mg2_vcycle(self.ctx, C.c_void_p(f.data_ptr()), C.c_void_p(u.data_ptr()),
                                     f.shape[1], _stream_handle()))
         return u
+
+    def solve_fgmres(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-8,
+                     max_iter: int = 300, restart: int = 30,
+                     precond: str = "vcycle") -> tuple[torch.Tensor, SolveInfo]:
+        """Restarted flexible GMRES on the real 2n form with the two-feature
+        cycle ("vcycle") or full multigrid ("fmg") as right preconditioner
+        (mg2_solve_fgmres).  f, u: complex128 CUDA tensors (n, nrhs)."""
+        if u is None:
+            u = torch.zeros_like(f)
+        for name, x in (("f", f), ("u", u)):
+            if (x.dtype != torch.complex128 or not x.is_cuda or not x.is_contiguous()
+                    or x.dim() != 2 or x.shape[0] != self.n[0]
+                    or not 1 <= x.shape[1] <= self.max_batch):
+                raise ValueError(f"{name}: expected a contiguous complex128 CUDA tensor "
+                                 f"({self.n[0]}, 1..{self.max_batch})")
+        if f.shape != u.shape:
+            raise ValueError("f and u differ in shape")
+        B = f.shape[1]
+        iters = np.zeros(B, dtype=np.int32)
+        relres = np.zeros(B)
+        st = self.lib.mg2_solve_fgmres(self.ctx, C.c_void_p(f.data_ptr()),
+                                       C.c_void_p(u.data_ptr()), B, float(tol), int(max_iter),
+                                       int(restart), {"vcycle": 0, "fmg": 1}[precond],
+                                       L.ptr(iters, L.i32p), L.ptr(relres, L.f64p),
+                                       _stream_handle())
+        L.check(st, None, allow=(L.MG_OK, L.MG_NOT_CONVERGED))
+        return u, SolveInfo(st, iters, relres)
 
     def close(self):
         if getattr(self, "ctx", None):

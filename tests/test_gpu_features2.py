@@ -133,3 +133,44 @@ def test_set_params_recaptures_the_cycle():
     S.vcycle(f, u)
     assert rel(u.cpu().numpy(), O.vcycle2(Ho, to_oracle(b), p.f, u_in)) < 1e-12
     S.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("precond", ["vcycle", "fmg"])
+@pytest.mark.parametrize("which", ["classical", "random"])
+def test_fgmres2_reaches_tolerance(prec, precond, which):
+    """FGMRES on the real 2n form with the two-feature cycle or FMG as right
+    preconditioner reaches 1e-8 (re-checked against the oracle's operator);
+    in FP64 each right-hand side takes the oracle's iteration count to within
+    one step (CGS2 here, MGS there)."""
+    p = W.helmholtz_square(33, 3, k=2 * np.pi, batch=2, seed=1)
+    Ho, Hp = O.build_hierarchy(p), Hierarchy2.from_problem(p)
+    prm = Params2.identity(Hp.J) if which == "classical" else params(Hp.J, 4, 0.1)
+    S = Solver2(Hp, prm, precision=prec, max_batch=2)
+    f = torch.tensor(p.f, dtype=torch.complex128, device="cuda")
+    u, info = S.solve_fgmres(f, tol=1e-8, precond=precond)
+    assert info.status == 0
+    A = Ho.levels[0].A
+    ug = u.cpu().numpy()
+    for b in range(2):
+        assert np.linalg.norm(p.f[:, b] - A @ ug[:, b]) / np.linalg.norm(p.f[:, b]) < 1e-8
+        if prec == 64:
+            _, its, _ = O.fgmres2(Ho, to_oracle(prm), p.f[:, b], 1e-8, precond=precond)
+            assert abs(int(info.iters[b]) - its) <= 1, (b, info.iters[b], its)
+    S.close()
+
+
+def test_fgmres2_zero_rhs_and_not_converged():
+    p = W.helmholtz_square(33, 3, k=2 * np.pi, batch=2, seed=1)
+    Hp = Hierarchy2.from_problem(p)
+    S = Solver2(Hp, Params2.identity(Hp.J), precision=32, max_batch=2)
+    f = np.array(p.f)
+    f[:, 1] = 0.0
+    u, info = S.solve_fgmres(torch.tensor(f, dtype=torch.complex128, device="cuda"), tol=1e-8)
+    assert info.status == 0 and info.iters[1] == 0 and torch.all(u[:, 1] == 0)
+    ft = torch.tensor(p.f, dtype=torch.complex128, device="cuda")
+    u, info = S.solve_fgmres(ft, tol=1e-14, max_iter=3, restart=10)
+    assert info.status == 1 and info.iters.max() == 3
+    with pytest.raises(MGError):
+        S.solve_fgmres(ft, restart=0)
+    S.close()
