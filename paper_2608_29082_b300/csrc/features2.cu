@@ -13,7 +13,9 @@
 // right-hand side).  The context owns every device buffer it allocates.
 // A cycle is captured once per (f, u, nrhs) into a CUDA graph on a private
 // stream and replayed on the caller's stream; parameters are kernel
-// arguments, so mg2_set_params drops the captured graphs.
+// arguments, so mg2_set_params drops the captured graphs.  mg2_solve_fgmres
+// wraps the cycle (or full multigrid) in restarted flexible GMRES on the
+// equivalent real system of size 2n.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -698,7 +700,8 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
         if (s.P_indices[e] < 0 || s.P_indices[e] >= nn)
           return fail("mg2_setup: prolongation column out of range");
   }
-  if (levels[J - 1].n > 4096) return fail("mg2_setup: coarsest level larger than 4096 rows");
+  // the host inverts the coarsest operator in O(n^3): keep it a coarse level
+  if (levels[J - 1].n > 2048) return fail("mg2_setup: coarsest level larger than 2048 rows");
   mg2_ctx* c = new mg2_ctx;
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
