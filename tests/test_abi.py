@@ -18,7 +18,8 @@ def declared_functions():
             continue
         src = open(os.path.join(ROOT, "include", fn)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:mg_status|void|int64_t)\s+(mg_\w+)\s*\(", src, flags=re.M)
+        names += re.findall(r"^\s*(?:mg_status|void|int64_t)\s+(mg2?_\w+)\s*\(", src,
+                            flags=re.M)
     return sorted(set(names))
 
 
@@ -57,3 +58,38 @@ def test_galerkin_helper_small():
     Ac = L.take_owned(o).to_scipy().toarray()
     ref = 0.5 * (np.diag([1, 2, 1.0]) - np.diag(np.ones(2), 1) - np.diag(np.ones(2), -1))
     assert np.allclose(Ac, ref, atol=1e-15)
+
+
+def test_two_feature_entry_points_reject_bad_input_without_gpu():
+    """mg2_setup validates every array before its first CUDA call; the other
+    mg2 entry points and mg_set_cheb reject a NULL context."""
+    lib = L.lib()
+    assert "mg2_setup" in declared_functions() and "mg2_solve_fgmres" in declared_functions()
+    ctx = C.c_void_p()
+    assert lib.mg2_setup(C.byref(ctx), 0, None, 1, 64) == -1 and not ctx.value
+    # one level, 2 x 2 complex operator with a column index out of range
+    rp = np.array([0, 1, 2], dtype=np.int32)
+    ci = np.array([0, 7], dtype=np.int32)
+    av = np.array([1.0, 0.0, 1.0, 0.0])
+    deg = np.ones(2)
+    lv = (L.Level2 * 1)()
+    lv[0].n = 2
+    lv[0].A_indptr, lv[0].A_indices = L.ptr(rp, L.i32p), L.ptr(ci, L.i32p)
+    lv[0].A_vals, lv[0].inv_deg = L.ptr(av, L.f64p), L.ptr(deg, L.f64p)
+    assert lib.mg2_setup(C.byref(ctx), 1, lv, 1, 64) == -1
+    assert "column" in L.last_error()
+    # two levels without a prolongation on level 0
+    lv2 = (L.Level2 * 2)()
+    for k in range(2):
+        lv2[k].n = 2
+        lv2[k].A_indptr, lv2[k].A_indices = L.ptr(rp, L.i32p), L.ptr(np.array([0, 1], dtype=np.int32), L.i32p)
+        lv2[k].A_vals, lv2[k].inv_deg = L.ptr(av, L.f64p), L.ptr(deg, L.f64p)
+    assert lib.mg2_setup(C.byref(ctx), 2, lv2, 1, 64) == -1
+    assert "prolongation" in L.last_error()
+    assert lib.mg2_setup(C.byref(ctx), 1, lv2, 1, 16) == -1  # precision
+    x = np.zeros(4)
+    assert lib.mg2_set_params(None, L.ptr(x, L.f64p), L.ptr(x, L.f64p), L.ptr(x, L.f64p),
+                              L.ptr(x, L.f64p), L.ptr(x, L.f64p), 1, 1) == -1
+    assert lib.mg2_vcycle(None, None, None, 1, None) == -1
+    assert lib.mg2_solve_fgmres(None, None, None, 1, 1e-8, 10, 10, 0, None, None, None) == -1
+    assert lib.mg_set_cheb(None, 2, L.ptr(x, L.f64p)) == -1
