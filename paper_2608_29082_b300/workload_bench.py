@@ -19,7 +19,8 @@
     python -m paper_2608_29082_b300.workload_bench features2
         Two features per node (mg2_*): the Helmholtz operator with impedance
         boundary at the paper's resolution (h = 1/256, k = 16 pi, J = 5);
-        cycle time in FP32 and FP64 for 1 and 16 right-hand sides.
+        cycle time in FP32 and FP64 for 1 and 16 right-hand sides, and time
+        to 1e-8 with FGMRES and the cycle or FMG (129^2, k = 8 pi, J = 3).
     python -m paper_2608_29082_b300.workload_bench profile_case
         A short, fixed case for a profiler's kernel captures: on the L-shape
         (3.1M DOF, 16 rhs, FP32) one cycle with a degree-2 ChebConv smoother,
@@ -314,6 +315,35 @@ def run_features2(a):
             S.close()
         out["dof"] = hier.sizes[0]
         out["levels"] = hier.sizes
+    # time to 1e-8 with FGMRES(30), classical two-feature weights, FP32
+    # cycle: half the resolution at the same k h (129^2, k = 8 pi), on a
+    # hierarchy shallow enough for Jacobi-type smoothing on every level
+    # (coarsest h = 1/32; the paper's deeper runs use GMRES smoothers)
+    Jk = a.krylov_J
+    out["fgmres_workload"] = (f"{a.krylov_N}x{a.krylov_N}, k = {a.krylov_k_over_pi:g} pi, "
+                              f"J = {Jk}, FP32 cycle, FGMRES(30), tol 1e-8")
+    for B in (1, 16):
+        prob = W.helmholtz_square(a.krylov_N, Jk, k=a.krylov_k_over_pi * np.pi, batch=B,
+                                  seed=a.seed)
+        hier = Hierarchy2.from_problem(prob)
+        S = Solver2(hier, Params2.identity(hier.J), precision=32, max_batch=B)
+        f = torch.tensor(prob.f, dtype=torch.complex128, device="cuda")
+        for pc in ("vcycle", "fmg"):
+            u = torch.zeros_like(f)
+            S.solve_fgmres(f, u, tol=1e-8, precond=pc)
+            ms = []
+            for _ in range(3):
+                u.zero_()
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record()
+                _, info = S.solve_fgmres(f, u, tol=1e-8, precond=pc)
+                e1.record()
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            out[f"fgmres_{pc}_J{Jk}_rhs{B}"] = {"ms": round(float(np.median(ms)), 3),
+                                               "iters": int(info.iters.max()),
+                                               "relres": float(info.relres.max())}
+        S.close()
     print(json.dumps(out), flush=True)
 
 
@@ -375,6 +405,9 @@ if __name__ == "__main__":
     f2.add_argument("--J", type=int, default=5)
     f2.add_argument("--k-over-pi", type=float, default=16.0)
     f2.add_argument("--seed", type=int, default=0)
+    f2.add_argument("--krylov-J", type=int, default=3)
+    f2.add_argument("--krylov-N", type=int, default=129)
+    f2.add_argument("--krylov-k-over-pi", type=float, default=8.0)
     pc = sub.add_parser("profile_case")
     pc.add_argument("--refinements", type=int, default=7)
     pc.add_argument("--batch", type=int, default=16)
