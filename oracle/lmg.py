@@ -243,6 +243,13 @@ class Params2:
     WP: np.ndarray
     nu_pre: int = 1
     nu_post: int = 1
+    # per level: None (Jacobi-type smoothing) or the number of inner GMRES
+    # steps of the GMRES smoother; nu_pre_gmres / nu_post_gmres smoothing
+    # steps on those levels (the Helmholtz setting of Sec. 4.3: GMRES with 4
+    # inner steps, one pre- and two post-smoothing steps where k h_l > 0.5)
+    gmres: list | None = None
+    nu_pre_gmres: int = 1
+    nu_post_gmres: int = 2
 
     @staticmethod
     def identity(J: int, omega: float = 2.0 / 3.0, nu: int = 1) -> "Params2":
@@ -278,21 +285,65 @@ def smooth2(L: Level, f, u, theta, eta, WB):
     return u + eta * conv2(L, delta, WB)
 
 
+def gmres_update(A, r: np.ndarray, k: int) -> np.ndarray:
+    """k steps of GMRES from zero on A delta = r, per column of r (complex):
+    the delta in the Krylov space span{r, A r, ..., A^{k-1} r} that
+    minimises ||r - A delta||_2 (Arnoldi with modified Gram-Schmidt, the
+    small least-squares problem solved directly)."""
+    out = np.zeros_like(r)
+    for b in range(r.shape[1]):
+        beta = np.linalg.norm(r[:, b])
+        if beta == 0.0:
+            continue
+        V = [r[:, b] / beta]
+        Hm = np.zeros((k + 1, k), dtype=complex)
+        m = k
+        for j in range(k):
+            w = A @ V[j]
+            for i in range(j + 1):
+                Hm[i, j] = np.vdot(V[i], w)
+                w = w - Hm[i, j] * V[i]
+            Hm[j + 1, j] = np.linalg.norm(w)
+            if Hm[j + 1, j] == 0.0:
+                m = j + 1
+                break
+            V.append(w / Hm[j + 1, j])
+        e1 = np.zeros(m + 1, dtype=complex)
+        e1[0] = beta
+        y = np.linalg.lstsq(Hm[:m + 1, :m], e1, rcond=None)[0]
+        out[:, b] = np.stack(V[:m], axis=1) @ y
+    return out
+
+
+def smooth2_gmres(L: Level, f, u, eta, WB, k: int):
+    """Learnable GMRES smoothing step (the coarse-level smoother of the
+    Helmholtz setting, Sec. 4.3): the classical smoother's update
+    delta = GMRES_k(A, f - A u) passes through the convolution,
+    u <- u + eta Phi_B(delta)."""
+    return u + eta * conv2(L, gmres_update(L.A, f - L.A @ u, k), WB)
+
+
 def lmg2(H: Hierarchy, p: Params2, lev: int, f: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Algorithm 2 with two features per node on a complex operator; the
     coarsest level is solved exactly (dense LU)."""
     if lev == H.J - 1:
         return sla.lu_solve(H.lu, f)
     L = H.levels[lev]
-    for _ in range(p.nu_pre):
-        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
+    kg = None if p.gmres is None else p.gmres[lev]
+
+    def smooth(u, nu_j, nu_g):
+        for _ in range(nu_j if kg is None else nu_g):
+            if kg is None:
+                u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
+            else:
+                u = smooth2_gmres(L, f, u, p.eta[lev], p.WB[lev], kg)
+        return u
+    u = smooth(u, p.nu_pre, p.nu_pre_gmres)
     r = f - L.A @ u
     rc = L.P.T @ conv2(L, r, p.WR[lev])
     ec = lmg2(H, p, lev + 1, rc, np.zeros_like(rc))
     u = u + conv2(L, L.P @ ec, p.WP[lev])
-    for _ in range(p.nu_post):
-        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
-    return u
+    return smooth(u, p.nu_post, p.nu_post_gmres)
 
 
 def vcycle2(H: Hierarchy, p: Params2, f: np.ndarray, u: np.ndarray) -> np.ndarray:

@@ -621,3 +621,32 @@ def test_fmg2_dense_nested_iteration(helmholtz17, seed):
     Mo = np.concatenate([out.real, out.imag], axis=0)
     M = dense_fmg2(H, th)
     assert np.abs(M - Mo).max() < 1e-10 * max(1.0, np.abs(M).max())
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+def test_gmres_update_is_the_krylov_least_squares_minimiser(helmholtz17, k):
+    """k GMRES steps from zero: the delta in span{r, A r, ..., A^{k-1} r}
+    minimising ||r - A delta||, here against the least-squares solution over
+    the explicit (monomial) Krylov basis."""
+    _, H = helmholtz17
+    A = H.levels[0].A
+    r = np.random.default_rng(k).standard_normal((A.shape[0], 2)) + 0j
+    got = O.gmres_update(A, r, k)
+    for b in range(2):
+        K = [r[:, b]]
+        for _ in range(k - 1):
+            K.append(A @ K[-1])
+        K = np.stack(K, axis=1)
+        c = np.linalg.lstsq(A @ K, r[:, b], rcond=None)[0]
+        ref = K @ c
+        assert np.linalg.norm(got[:, b] - ref) < 1e-9 * np.linalg.norm(ref)
+
+
+def test_gmres_update_full_space_is_the_solve(helmholtz17):
+    """With as many steps as unknowns (coarsest level) GMRES solves exactly."""
+    _, H = helmholtz17
+    A = H.levels[-1].A
+    r = np.random.default_rng(0).standard_normal((A.shape[0], 1)) + 1j
+    got = O.gmres_update(A, r, A.shape[0])
+    ref = np.linalg.solve(A.toarray(), r)
+    assert np.linalg.norm(got - ref) < 1e-8 * np.linalg.norm(ref)
