@@ -467,7 +467,7 @@ typedef struct {
 
 /* Copies a J-level complex hierarchy (host arrays, copied; the caller keeps
  * ownership) to the device: CSR operators, prolongations and their
- * transposes, per-level workspace for max_batch right-hand sides, and the
+ * transposes, per-level workspace for max_batch (1..65535) right-hand sides, and the
  * inverse of the coarsest operator (n_{J-1} <= 2048; MG_ERR_NOT_SPD if it is
  * singular).  precision 64 or 32.  Parameters start at the classical cycle:
  * W_1 = I, W_2 = 0, theta = 2/3, eta = 1, one pre- and one post-smoothing

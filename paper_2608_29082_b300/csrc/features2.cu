@@ -683,7 +683,9 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
                                int32_t max_batch, int32_t precision) {
   if (!out) return fail("mg2_setup: out is NULL");
   *out = nullptr;
-  if (J < 1 || J > 32 || !levels || max_batch < 1 || (precision != 32 && precision != 64))
+  // max_batch: FGMRES's per-(vector, rhs) sums run on a grid with nrhs rows
+  if (J < 1 || J > 32 || !levels || max_batch < 1 || max_batch > 65535 ||
+      (precision != 32 && precision != 64))
     return fail("mg2_setup: bad arguments");
   for (int l = 0; l < J; ++l) {
     const mg2_level& s = levels[l];
