@@ -116,6 +116,31 @@ def test_smoother_spectrum_closed_form(poisson33, seed):
     assert np.abs(ev - np.sort(sigma.ravel())).max() < 1e-12
 
 
+def test_proposition_learnable_smoother_beats_optimal_jacobi(poisson33):
+    """Proposition (Sec. 3.3): min over (w1, w2, eta, theta) of rho(S) is at
+    most rho(S_{omega*}).  On the five-point Laplacian both minima have
+    closed forms over the spectrum [a, b] of D_A^{-1} A, mu = (b+a)/(b-a):
+    damped Jacobi gives 1/mu at omega* = 2/(a+b); the learnable factor
+    1 - eta theta (w1 + w2 (1 - lambda)) lambda is a quadratic with value 1
+    at 0, whose minimax on [a, b] is the shifted Chebyshev polynomial, value
+    1/T_2(mu) = 1/(2 mu^2 - 1) (strictly smaller, the Remark's frequency-
+    dependent damping).  The oracle's smoother at the parameters realising
+    each has exactly these spectral radii."""
+    _, H = poisson33
+    L = H.levels[0]
+    h = 1.0 / 32
+    a, b = 1 - np.cos(np.pi * h), 1 + np.cos(np.pi * h)
+    mu, sc = (b + a) / (b - a), 2.0 / (b - a)
+    rho_j = np.abs(np.linalg.eigvals(dense_smoother(L, 2.0 / (a + b), 1.0, (1.0, 0.0)))).max()
+    assert abs(rho_j - 1.0 / mu) < 1e-12
+    t2 = 2 * mu * mu - 1
+    w2 = 2 * sc * sc / t2
+    w1 = 4 * mu * sc / t2 - w2
+    rho_l = np.abs(np.linalg.eigvals(dense_smoother(L, 1.0, 1.0, (w1, w2)))).max()
+    assert abs(rho_l - 1.0 / t2) < 1e-12
+    assert rho_l < rho_j
+
+
 def test_jacobi_recovery(poisson33):
     """Remark (recovery of classical methods): w1=1, w2=0, theta=omega, eta=1
     gives S = I - omega D_A^{-1} A with eigenvalues 1 - omega lambda."""
