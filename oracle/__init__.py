@@ -4,6 +4,7 @@ Only tests, the package smoke check and the benchmark's CPU-baseline leg may
 import this package.  It shares no code with the CUDA library.
 """
 from .lmg import (Hierarchy, Level, Params, Params2, build_hierarchy, cheb_conv,  # noqa: F401
+                  cheb_gradient_complex_step, cheb_gradient_fd,
                   complex_vec, conv, conv2, features, fgmres, fgmres2, fmg, fmg2,
                   gmres_update, lap_hat,
                   lmg, lmg2, real_vec,

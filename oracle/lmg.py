@@ -569,9 +569,43 @@ def loss_gradient_complex_step(H: Hierarchy, p: Params, f: np.ndarray, K: int,
     for k in range(x.size):
         xc = x.astype(np.complex128)
         xc[k] += 1j * h
-        pc = Params.from_flat(xc, p.nu_pre, p.nu_post)
+        pc = _same_smoother(Params.from_flat(xc, p.nu_pre, p.nu_post), p)
         g[k] = np.imag(unrolled_loss(H, pc, fc, K, u0c)) / h
     return unrolled_loss(H, p, f, K, u0), g
+
+
+def _same_smoother(q: Params, p: Params) -> Params:
+    """q with p's smoother choice (the ChebConv coefficients are not part of
+    the flat Theta vector)."""
+    q.cheb = None if p.cheb is None else p.cheb.astype(q.theta.dtype)
+    return q
+
+
+def cheb_gradient_complex_step(H: Hierarchy, p: Params, f: np.ndarray, K: int,
+                               u0: np.ndarray | None = None, h: float = 1e-30) -> np.ndarray:
+    """d loss / d c_{l,k} of the ChebConv smoother's coefficients by complex
+    step (the loss is a polynomial in them, so exact to rounding)."""
+    g = np.zeros_like(p.cheb)
+    fc = f.astype(np.complex128)
+    u0c = None if u0 is None else u0.astype(np.complex128)
+    for idx in np.ndindex(*p.cheb.shape):
+        pc = p.astype(np.complex128)
+        pc.cheb[idx] += 1j * h
+        g[idx] = np.imag(unrolled_loss(H, pc, fc, K, u0c)) / h
+    return g
+
+
+def cheb_gradient_fd(H: Hierarchy, p: Params, f: np.ndarray, K: int,
+                     u0: np.ndarray | None = None, h: float = 1e-6) -> np.ndarray:
+    """Central finite differences of the same loss in the ChebConv coefficients."""
+    g = np.zeros_like(p.cheb)
+    for idx in np.ndindex(*p.cheb.shape):
+        step = h * max(1.0, abs(p.cheb[idx]))
+        pp, pm = p.copy(), p.copy()
+        pp.cheb[idx] += step
+        pm.cheb[idx] -= step
+        g[idx] = (unrolled_loss(H, pp, f, K, u0) - unrolled_loss(H, pm, f, K, u0)) / (2 * step)
+    return g
 
 
 def loss_gradient_fd(H: Hierarchy, p: Params, f: np.ndarray, K: int,
@@ -584,7 +618,9 @@ def loss_gradient_fd(H: Hierarchy, p: Params, f: np.ndarray, K: int,
         step = h * max(1.0, abs(x[k]))
         xp[k] += step
         xm[k] -= step
-        lp = unrolled_loss(H, Params.from_flat(xp, p.nu_pre, p.nu_post), f, K, u0)
-        lm = unrolled_loss(H, Params.from_flat(xm, p.nu_pre, p.nu_post), f, K, u0)
+        lp = unrolled_loss(H, _same_smoother(Params.from_flat(xp, p.nu_pre, p.nu_post), p), f,
+                           K, u0)
+        lm = unrolled_loss(H, _same_smoother(Params.from_flat(xm, p.nu_pre, p.nu_post), p), f,
+                           K, u0)
         g[k] = (lp - lm) / (2 * step)
     return g

@@ -675,3 +675,22 @@ def test_gmres_update_full_space_is_the_solve(helmholtz17):
     got = O.gmres_update(A, r, A.shape[0])
     ref = np.linalg.solve(A.toarray(), r)
     assert np.linalg.norm(got - ref) < 1e-8 * np.linalg.norm(ref)
+
+
+def test_cheb_coefficient_gradient(checker17):
+    """Gradients of the unrolled loss (Algorithm 3) in the ChebConv
+    smoother's coefficients: complex step equals central differences; with
+    the ChebConv smoother on, the unused SAGEConv smoother weights W_B have
+    exactly zero gradient and the other parameters' gradients still agree."""
+    p, H = checker17
+    th = random_params(H.J, 8, 0.2)
+    th.cheb = np.tile([1.0, 0.15, -0.05], (H.J - 1, 1))
+    gc = O.cheb_gradient_complex_step(H, th, p.f, 2)
+    gf = O.cheb_gradient_fd(H, th, p.f, 2)
+    assert np.abs(gc - gf).max() < 1e-5 * np.abs(gc).max()
+    loss, g = O.loss_gradient_complex_step(H, th, p.f, 2)
+    assert loss == O.unrolled_loss(H, th, p.f, 2)
+    g = g.reshape(-1, 8)
+    assert np.all(g[:, 2:4] == 0.0)
+    gfd = O.loss_gradient_fd(H, th, p.f, 2).reshape(-1, 8)
+    assert np.abs(g - gfd).max() < 1e-5 * np.abs(g).max()
