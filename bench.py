@@ -280,7 +280,8 @@ def run_ours(args):
     # the same learned cycle as preconditioner of flexible CG (FP64 outer)
     msfcg, infofcg, nkfcg = timed(S32, method="fcg")
     # the learned cycle, nonsymmetric, as the preconditioner of restarted
-    # flexible GMRES: one V-cycle, and one full multigrid (Sec. 5)
+    # flexible GMRES: one V-cycle, and one full multigrid (Sec. 4.2,
+    # tab:helmholtz-results-precond)
     msgmv, infogmv, nkgmv = timed(S32, method="fgmres")
     S32.set_option("fcg_precond", 1)
     msgmf, infogmf, nkgmf = timed(S32, method="fgmres")

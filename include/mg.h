@@ -137,10 +137,13 @@ void mg_csr_owned_free(mg_csr_owned* m);
  *            32: the V-cycle runs in FP32 (values, weights, accumulation)
  *            and mg_solve wraps it in FP64 iterative refinement.
  *  max_batch largest nrhs any later call will pass (sizes the workspace).
- * The coarsest operator is factorised by dense FP64 Cholesky here
- * (MG_ERR_NOT_SPD if that fails; n_{J-1} <= 2048).  Matrices are stored as
- * SELL-32 slices (off-diagonals) plus diagonal arrays.  *out is NULL on
- * failure; the message is then available from mg_last_error(NULL, ...). */
+ * The coarsest operator is factorised by dense FP64 Cholesky here, on the
+ * host before any device allocation (MG_ERR_NOT_SPD if that fails;
+ * n_{J-1} <= 2048; a non-positive diagonal entry is MG_ERR_INVALID).  The
+ * off-diagonals of each level are stored as DIA (values on at most 8
+ * diagonals, no column indices) where they fit, else as SELL-32 slices
+ * (mg_set_layout_policy), next to diagonal arrays.  *out is NULL on failure;
+ * the message is then available from mg_last_error(NULL, ...). */
 mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr* A_levels,
                    const mg_params* p, int32_t max_batch, int32_t precision, void* stream);
 
@@ -187,7 +190,8 @@ mg_status mg_set_cheb(mg_ctx* ctx, int32_t K, const double* coef);
 mg_status mg_vcycle(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, void* stream);
 
 /* One full multigrid (nested iteration) application, the preconditioner of
- * the paper's Sec. 5 Krylov experiments: f is restricted to every level with
+ * the paper's Krylov experiments (Sec. 4.2, tab:helmholtz-results-precond):
+ * f is restricted to every level with
  * the cycle's restriction P^T Phi_R, the coarsest level is solved exactly,
  * and on each finer level the coarser solution, prolongated with the cycle's
  * Phi_P P, is the initial guess of one V-cycle (Algorithm 2 started on that
@@ -208,29 +212,43 @@ mg_status mg_fmg(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs, void
 mg_status mg_solve(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
                    int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
 
-/* Flexible conjugate gradients (one stored direction, Notay's FCG) in FP64
- * with the context's V-cycle as a variable preconditioner: z = LMG(A, r, 0),
- * in FP32 on a power-of-two-scaled residual for precision-32 contexts.
- * Same arguments, stopping rule and batch independence as mg_solve; the
- * relres reported is that of the true residual f - A u of the final iterate.
- * Krylov acceleration of the cycle is the paper's preconditioner use (Sec. 4.2),
- * with flexible CG in place of FGMRES for SPD operators. */
 /* Restarted flexible GMRES, FGMRES(restart) with right preconditioning
  * (Saad 1993), the outer Krylov method the paper uses with its V-cycle and
- * FMG preconditioners (Sec. 5): FP64 Arnoldi (classical Gram-Schmidt applied
- * twice), Givens rotations per right-hand side, the preconditioner one
- * V-cycle from zero or one full multigrid (MG_OPT_FCG_PRECOND) in the
- * context precision.  Arguments and results as mg_solve; u_dev is the
- * initial guess; 1 <= restart <= 64; max_iter counts Arnoldi steps (one
- * preconditioner application each, shared by the batch).  Each right-hand
- * side stops updating once its true residual meets tol at a restart.  The
- * host reads the convergence counts after every step (one synchronisation
- * per step).  Workspace: (2 restart + 1) vectors of [n_0][max_batch] FP64,
- * allocated on first use. */
+ * FMG preconditioners (Sec. 4.2, tab:helmholtz-results-precond).  The
+ * preconditioner is one V-cycle from zero or one full multigrid
+ * (MG_OPT_FCG_PRECOND).  Orthogonalisation is classical Gram-Schmidt applied
+ * twice; the Hessenberg least-squares problem is FP64 with Givens rotations
+ * per right-hand side.  The Arnoldi cycle runs in the context precision:
+ *  - precision 64: FP64 basis, directions and K z = A z;
+ *  - precision 32: an FP32 basis and FP32 directions (K z = -A z in FP32)
+ *    within a restart cycle, and every restart recomputes r = f - A u and
+ *    applies u += Z y in FP64 (GMRES-based iterative refinement).  A cycle
+ *    also ends once its residual estimate falls below 10^-MG_OPT_FGMRES_FLOOR
+ *    times its start, the accuracy an FP32 cycle resolves.
+ * Arguments and results as mg_solve; u_dev is the initial guess;
+ * 1 <= restart <= 64; max_iter counts Arnoldi steps (one preconditioner
+ * application each, shared by the batch).  Each right-hand side stops
+ * updating once its true residual meets tol at a restart.  The host reads
+ * the convergence counts after every step (one synchronisation per step).
+ * Workspace, allocated on first use with a given restart: restart + 1 basis
+ * and restart direction vectors of [n_0][max_batch] in the context precision
+ * (plus an FP32 zero vector in FP32 contexts). */
 mg_status mg_solve_fgmres(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs,
                           double tol, int32_t max_iter, int32_t restart, int32_t* iters_out,
                           double* relres_out, void* stream);
 
+/* Flexible conjugate gradients, FCG(1) of Notay (one stored direction), in
+ * FP64 with the context's cycle as a variable preconditioner: z = LMG(A, r,
+ * 0), or one full multigrid with MG_OPT_FCG_PRECOND = 1, in FP32 on a
+ * power-of-two-scaled residual for precision-32 contexts.  Iteration:
+ * u += alpha p, r -= alpha q, the test ||r||/||f|| < tol on this recurrence
+ * residual, z = M(r), p = z - ((z, q)/(p, q)) p, q = A p,
+ * alpha = (p, r)/(p, q).  The paper's preconditioner use (Sec. 4.2,
+ * tab:helmholtz-results-precond) is FGMRES; flexible CG is its counterpart
+ * for SPD operators.  Same arguments, stopping rule and batch independence
+ * as mg_solve; max_iter counts iterations; the relres reported is that of
+ * the true residual f - A u of the final iterate.  Synchronises the stream.
+ * Workspace (four FP64 vectors [n_0][max_batch]) is allocated on first use. */
 mg_status mg_solve_fcg(mg_ctx* ctx, const double* f_dev, double* u_dev, int32_t nrhs, double tol,
                        int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
 
@@ -250,6 +268,12 @@ mg_status mg_solve_host(mg_ctx* ctx, const double* f_host, double* u_host, int32
  *   MG_OP_OUTER_RESIDUAL  out = f - A u in FP64 on level 0 whatever the
  *                   context precision (the refinement residual); x = f,
  *                   y = u, out double
+ *   MG_OP_REFINE_RESIDUAL the first residual step of mg_solve's FP64
+ *                   refinement, as its kernels compute it: r = f - A u in
+ *                   FP64 and its scaled FP32 copy, out[i][b] =
+ *                   float(r[i][b] * 2^-s_b) with s_b = ilogb(||f_b||_2)
+ *                   (0 when ||f_b|| is 0 or not finite), the input of the
+ *                   FP32 cycle; x = f, y = u (FP64), out float, level 0
  */
 typedef enum {
   MG_OP_SMOOTH = 0,
@@ -257,7 +281,8 @@ typedef enum {
   MG_OP_RESTRICT = 2,
   MG_OP_PROLONG = 3,
   MG_OP_COARSE = 4,
-  MG_OP_OUTER_RESIDUAL = 5
+  MG_OP_OUTER_RESIDUAL = 5,
+  MG_OP_REFINE_RESIDUAL = 6
 } mg_op;
 
 mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, const void* y,
@@ -439,9 +464,9 @@ mg_status mg_smooth_noalloc(int32_t n, const int32_t* rowptr_dev, const int32_t*
 /* ---------------------------------------------------------------------
  * Two features per node (d = 2): complex systems
  *
- * The Helmholtz experiment (Sec. 4.3) solves a complex system and carries
+ * The Helmholtz experiment (Sec. 4.2) solves a complex system and carries
  * (Re u, Im u) as two node features; every SAGEConv then holds
- * W_1, W_2 in R^{2x2} (Sec. 3.2) and may mix them.  An mg2 context runs
+ * W_1, W_2 in R^{2x2} (the weight matrices of Sec. 3.2) and may mix them.  An mg2 context runs
  * that cycle (Algorithm 2):
  *   delta = theta_l D_A^{-1} (f - A u)       (complex arithmetic)
  *   u <- u + eta_l Phi_B(delta),  Phi(x)_i = W_1 x_i + W_2 mean_{N(i)} x_j
@@ -467,12 +492,15 @@ typedef struct {
 
 /* Copies a J-level complex hierarchy (host arrays, copied; the caller keeps
  * ownership) to the device: CSR operators, prolongations and their
- * transposes, per-level workspace for max_batch (1..65535) right-hand sides, and the
- * inverse of the coarsest operator (n_{J-1} <= 2048; MG_ERR_NOT_SPD if it is
- * singular).  precision 64 or 32.  Parameters start at the classical cycle:
- * W_1 = I, W_2 = 0, theta = 2/3, eta = 1, one pre- and one post-smoothing
- * step.  Errors (message via mg_last_error(NULL, ...)): MG_ERR_INVALID for
- * missing arrays or out-of-range indices, MG_ERR_OOM / MG_ERR_CUDA. */
+ * transposes, per-level workspace for max_batch (1..65535) right-hand
+ * sides, and the inverse of the coarsest operator (n_{J-1} <= 2048).
+ * precision 64 or 32.  Parameters start at the classical cycle: W_1 = I,
+ * W_2 = 0, theta = 2/3, eta = 1, one pre- and one post-smoothing step.
+ * Every check below runs on the host before the first CUDA call.  Errors
+ * (message via mg_last_error(NULL, ...)): MG_ERR_INVALID for missing arrays,
+ * out-of-range indices or a zero diagonal entry; MG_ERR_NOT_SPD if the
+ * coarsest operator is singular (an exactly zero pivot of its FP64
+ * Gauss-Jordan inverse); MG_ERR_OOM / MG_ERR_CUDA. */
 mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels, int32_t max_batch,
                     int32_t precision);
 
@@ -493,7 +521,8 @@ mg_status mg2_vcycle(mg2_ctx* ctx, const void* f, void* u, int32_t nrhs, void* s
 /* Restarted flexible GMRES on the complex system, with one two-feature
  * cycle from zero (precond 0) or one full multigrid (precond 1) as right
  * preconditioner: the pairing of the paper's Helmholtz preconditioner
- * tables (Sec. 4.3).  W_1, W_2 mix Re and Im, so the preconditioner is
+ * table (Sec. 4.2, tab:helmholtz-results-precond).  W_1, W_2 mix Re and
+ * Im, so the preconditioner is
  * real-linear, not complex-linear: the Krylov method runs on the equivalent
  * real system of size 2n, [[Re A, -Im A], [Im A, Re A]], with real inner
  * products sum_i (Re x_i Re y_i + Im x_i Im y_i) per right-hand side.

@@ -233,7 +233,7 @@ def vcycle(H: Hierarchy, p: Params, f: np.ndarray, u: np.ndarray) -> np.ndarray:
 @dataclass
 class Params2:
     """Theta with two features per node: each SAGEConv holds W_1, W_2 in
-    R^{2x2} (Sec. 3.2).  The Helmholtz experiment (Sec. 4.3) carries the real
+    R^{2x2} (Sec. 3.2).  The Helmholtz experiment (Sec. 4.2) carries the real
     and imaginary parts of the complex solution as the two features.
     WB, WR, WP: (J-1, 2, 2, 2), per level (W_1, W_2)."""
     theta: np.ndarray
@@ -243,13 +243,6 @@ class Params2:
     WP: np.ndarray
     nu_pre: int = 1
     nu_post: int = 1
-    # per level: None (Jacobi-type smoothing) or the number of inner GMRES
-    # steps of the GMRES smoother; nu_pre_gmres / nu_post_gmres smoothing
-    # steps on those levels (the Helmholtz setting of Sec. 4.3: GMRES with 4
-    # inner steps, one pre- and two post-smoothing steps where k h_l > 0.5)
-    gmres: list | None = None
-    nu_pre_gmres: int = 1
-    nu_post_gmres: int = 2
 
     @staticmethod
     def identity(J: int, omega: float = 2.0 / 3.0, nu: int = 1) -> "Params2":
@@ -285,65 +278,21 @@ def smooth2(L: Level, f, u, theta, eta, WB):
     return u + eta * conv2(L, delta, WB)
 
 
-def gmres_update(A, r: np.ndarray, k: int) -> np.ndarray:
-    """k steps of GMRES from zero on A delta = r, per column of r (complex):
-    the delta in the Krylov space span{r, A r, ..., A^{k-1} r} that
-    minimises ||r - A delta||_2 (Arnoldi with modified Gram-Schmidt, the
-    small least-squares problem solved directly)."""
-    out = np.zeros_like(r)
-    for b in range(r.shape[1]):
-        beta = np.linalg.norm(r[:, b])
-        if beta == 0.0:
-            continue
-        V = [r[:, b] / beta]
-        Hm = np.zeros((k + 1, k), dtype=complex)
-        m = k
-        for j in range(k):
-            w = A @ V[j]
-            for i in range(j + 1):
-                Hm[i, j] = np.vdot(V[i], w)
-                w = w - Hm[i, j] * V[i]
-            Hm[j + 1, j] = np.linalg.norm(w)
-            if Hm[j + 1, j] == 0.0:
-                m = j + 1
-                break
-            V.append(w / Hm[j + 1, j])
-        e1 = np.zeros(m + 1, dtype=complex)
-        e1[0] = beta
-        y = np.linalg.lstsq(Hm[:m + 1, :m], e1, rcond=None)[0]
-        out[:, b] = np.stack(V[:m], axis=1) @ y
-    return out
-
-
-def smooth2_gmres(L: Level, f, u, eta, WB, k: int):
-    """Learnable GMRES smoothing step (the coarse-level smoother of the
-    Helmholtz setting, Sec. 4.3): the classical smoother's update
-    delta = GMRES_k(A, f - A u) passes through the convolution,
-    u <- u + eta Phi_B(delta)."""
-    return u + eta * conv2(L, gmres_update(L.A, f - L.A @ u, k), WB)
-
-
 def lmg2(H: Hierarchy, p: Params2, lev: int, f: np.ndarray, u: np.ndarray) -> np.ndarray:
     """Algorithm 2 with two features per node on a complex operator; the
     coarsest level is solved exactly (dense LU)."""
     if lev == H.J - 1:
         return sla.lu_solve(H.lu, f)
     L = H.levels[lev]
-    kg = None if p.gmres is None else p.gmres[lev]
-
-    def smooth(u, nu_j, nu_g):
-        for _ in range(nu_j if kg is None else nu_g):
-            if kg is None:
-                u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
-            else:
-                u = smooth2_gmres(L, f, u, p.eta[lev], p.WB[lev], kg)
-        return u
-    u = smooth(u, p.nu_pre, p.nu_pre_gmres)
+    for _ in range(p.nu_pre):
+        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
     r = f - L.A @ u
     rc = L.P.T @ conv2(L, r, p.WR[lev])
     ec = lmg2(H, p, lev + 1, rc, np.zeros_like(rc))
     u = u + conv2(L, L.P @ ec, p.WP[lev])
-    return smooth(u, p.nu_post, p.nu_post_gmres)
+    for _ in range(p.nu_post):
+        u = smooth2(L, f, u, p.theta[lev], p.eta[lev], p.WB[lev])
+    return u
 
 
 def vcycle2(H: Hierarchy, p: Params2, f: np.ndarray, u: np.ndarray) -> np.ndarray:
@@ -354,7 +303,8 @@ def fmg2(H: Hierarchy, p: Params2, f: np.ndarray) -> np.ndarray:
     """Full multigrid with two-feature convolutions: f restricted to every
     level by P^T Phi_R, the coarsest level solved exactly, on each finer level
     Phi_P(P u_{l+1}) from a zero iterate as the initial guess of one cycle
-    started on that level (the FMG of the Sec. 4.3 preconditioner tables)."""
+    started on that level (the FMG of the Sec. 4.2 preconditioner table,
+    tab:helmholtz-results-precond)."""
     J = H.J
     fs = [f]
     for lev in range(J - 1):
@@ -402,12 +352,13 @@ def fgmres2(H: Hierarchy, p: Params2, f: np.ndarray, tol: float, precond: str = 
 
 
 def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:
-    """Full multigrid (nested iteration), the preconditioner of the Sec. 5
-    Krylov experiments.  The right-hand side goes to every level through the
-    cycle's restriction P^T Phi_R; the coarsest level is solved exactly; on
-    each finer level the coarser solution, through the cycle's prolongation
-    Phi_P P, is the initial guess of one V-cycle (Algorithm 2 started on that
-    level).  One V-cycle per level, as in the paper."""
+    """Full multigrid (nested iteration), the preconditioner of the Krylov
+    experiments of Sec. 4.2 (tab:helmholtz-results-precond).  The right-hand
+    side goes to every level through the cycle's restriction P^T Phi_R; the
+    coarsest level is solved exactly; on each finer level the coarser
+    solution, through the cycle's prolongation Phi_P P, is the initial guess
+    of one V-cycle (Algorithm 2 started on that level).  One V-cycle per
+    level, as in the paper."""
     J = H.J
     fs = [f]
     for lev in range(J - 1):
@@ -424,7 +375,8 @@ def fmg(H: Hierarchy, p: Params, f: np.ndarray) -> np.ndarray:
 def fgmres(A, f: np.ndarray, precond, tol: float, restart: int = 30, max_iter: int = 300):
     """Restarted flexible GMRES with right preconditioning (Saad 1993), the
     outer Krylov method the paper pairs with its V-cycle and FMG
-    preconditioners (Sec. 5), for one right-hand side f (1-D).  precond(v)
+    preconditioners (Sec. 4.2, tab:helmholtz-results-precond), for one
+    right-hand side f (1-D).  precond(v)
     returns z ~ A^{-1} v and may change between calls.  Modified Gram-Schmidt
     Arnoldi, Givens rotations on the Hessenberg matrix; stops when the
     recurrence's residual estimate |g_{j+1}| < tol ||f||, or after max_iter
@@ -474,6 +426,48 @@ def fgmres(A, f: np.ndarray, precond, tol: float, restart: int = 30, max_iter: i
         if hist and hist[-1] < tol * fn:
             break
     return u, its, np.array(hist)
+
+
+def fcg(A, f: np.ndarray, precond, tol: float, max_iter: int = 300, mmax: int = 1):
+    """Flexible conjugate gradients, FCG(mmax) of Notay (SIAM J. Sci. Comput.
+    22, 2000), for one right-hand side f (1-D) from u = 0.  The paper pairs its
+    cycle with FGMRES (Sec. 4.2); for the SPD operators of this path flexible
+    CG is the symmetric counterpart.  precond(v) returns z ~ A^{-1} v and may
+    change between calls.  Iteration i:
+        z_i = precond(r_i)
+        d_i = z_i - sum_{k = i-m_i .. i-1} (z_i, A d_k) / (d_k, A d_k) d_k,
+              m_i = min(i, mmax)   (explicit A-orthogonalisation against the
+                                    last mmax directions)
+        alpha_i = (d_i, r_i) / (d_i, A d_i)
+        u_{i+1} = u_i + alpha_i d_i,   r_{i+1} = r_i - alpha_i A d_i
+    stopping as soon as the recurrence residual ||r_{i+1}|| < tol ||f||, or
+    after max_iter iterations (r_0 = f is tested first).  Returns
+    (u, iterations, recurrence residual norms per iteration, iterates u_1..)."""
+    u = np.zeros_like(f)
+    r = f.copy()
+    fn = np.linalg.norm(f)
+    D, AD = [], []  # last mmax directions and their images
+    hist, iterates = [], []
+    if not np.linalg.norm(r) < tol * fn:
+        for _ in range(max_iter):
+            z = precond(r)
+            d = z.copy()
+            for dk, qk in zip(D, AD):
+                d = d - (z @ qk) / (dk @ qk) * dk
+            q = A @ d
+            alpha = (d @ r) / (d @ q)
+            u = u + alpha * d
+            r = r - alpha * q
+            D.append(d)
+            AD.append(q)
+            if len(D) > mmax:
+                D.pop(0)
+                AD.pop(0)
+            hist.append(np.linalg.norm(r))
+            iterates.append(u.copy())
+            if hist[-1] < tol * fn:
+                break
+    return u, len(hist), np.array(hist), iterates
 
 
 def residual(H: Hierarchy, f, u):

@@ -17,7 +17,7 @@ STATUS = {0: "MG_OK", 1: "MG_NOT_CONVERGED", -1: "MG_ERR_INVALID", -2: "MG_ERR_O
 OPTIONS = {"tail_work": 0, "pdl": 1, "multi_rhs": 2, "device_loop": 3, "halo_rows": 4, "fcg_precond": 5,
            "fgmres_floor": 6}
 OPS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "coarse": 4,
-       "outer_residual": 5}
+       "outer_residual": 5, "refine_residual": 6}
 
 i32p = C.POINTER(C.c_int32)
 f64p = C.POINTER(C.c_double)

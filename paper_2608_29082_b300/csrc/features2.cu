@@ -1,6 +1,6 @@
 // Learnable multigrid with two features per node (d = 2).
 //
-// The paper's Helmholtz experiment (Sec. 4.3) solves a complex system and
+// The paper's Helmholtz experiment (Sec. 4.2) solves a complex system and
 // carries the real and imaginary parts of the solution as two node features;
 // each SAGEConv then holds W_1, W_2 in R^{2x2} (Sec. 3.2) and may mix them.
 // This translation unit is that cycle (Algorithm 2) on complex operators:
@@ -485,7 +485,8 @@ bool invert(int n, std::vector<std::complex<double>>& a, std::vector<std::comple
 }
 
 template <class T>
-mg_status setup_typed(mg2_ctx* c, const mg2_level* L) {
+mg_status setup_typed(mg2_ctx* c, const mg2_level* L,
+                      const std::vector<std::complex<double>>& inv) {
   using P2 = typename Pair<T>::type;
   const int J = c->J;
   for (int l = 0; l < J; ++l) {
@@ -502,8 +503,7 @@ mg_status setup_typed(mg2_ctx* c, const mg2_level* L) {
         av[e].y = (T)s.A_vals[2 * e + 1];
         if (s.A_indices[e] == i) diag += std::complex<double>(s.A_vals[2 * e], s.A_vals[2 * e + 1]);
       }
-      if (!(std::abs(diag) > 0.0)) return fail("mg2_setup: zero diagonal");
-      const std::complex<double> di = 1.0 / diag;
+      const std::complex<double> di = 1.0 / diag;  // nonzero: checked in mg2_setup
       dinv[i].x = (T)di.real();
       dinv[i].y = (T)di.imag();
       invdeg[i] = (T)s.inv_deg[i];
@@ -548,14 +548,7 @@ mg_status setup_typed(mg2_ctx* c, const mg2_level* L) {
     if (!upload(c, &c->av64, a64.data(), a64.size()))
       return fail("mg2_setup: device allocation or copy failed", MG_ERR_CUDA);
   }
-  // the coarsest operator, inverted in FP64 on the host
-  const mg2_level& s = L[J - 1];
-  const int n = s.n;
-  std::vector<std::complex<double>> a((size_t)n * n, 0.0), inv;
-  for (int i = 0; i < n; ++i)
-    for (int e = s.A_indptr[i]; e < s.A_indptr[i + 1]; ++e)
-      a[(size_t)i * n + s.A_indices[e]] += std::complex<double>(s.A_vals[2 * e], s.A_vals[2 * e + 1]);
-  if (!invert(n, a, inv)) return fail("mg2_setup: coarsest operator is singular", MG_ERR_NOT_SPD);
+  // the coarsest operator's inverse (computed on the host by mg2_setup)
   std::vector<P2> ci(inv.size());
   for (size_t k = 0; k < inv.size(); ++k) {
     ci[k].x = (T)inv[k].real();
@@ -704,6 +697,30 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
   }
   // the host inverts the coarsest operator in O(n^3): keep it a coarse level
   if (levels[J - 1].n > 2048) return fail("mg2_setup: coarsest level larger than 2048 rows");
+  // host checks before the first CUDA call: every diagonal nonzero (the
+  // smoother divides by it), the coarsest operator invertible (FP64 dense
+  // inverse by Gauss-Jordan)
+  for (int l = 0; l < J; ++l) {
+    const mg2_level& s = levels[l];
+    for (int i = 0; i < s.n; ++i) {
+      std::complex<double> diag = 0.0;
+      for (int e = s.A_indptr[i]; e < s.A_indptr[i + 1]; ++e)
+        if (s.A_indices[e] == i) diag += std::complex<double>(s.A_vals[2 * e], s.A_vals[2 * e + 1]);
+      if (!(std::abs(diag) > 0.0))
+        return fail("mg2_setup: zero diagonal on level " + std::to_string(l));
+    }
+  }
+  std::vector<std::complex<double>> inv;
+  {
+    const mg2_level& s = levels[J - 1];
+    const int n = s.n;
+    std::vector<std::complex<double>> a((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i)
+      for (int e = s.A_indptr[i]; e < s.A_indptr[i + 1]; ++e)
+        a[(size_t)i * n + s.A_indices[e]] +=
+            std::complex<double>(s.A_vals[2 * e], s.A_vals[2 * e + 1]);
+    if (!invert(n, a, inv)) return fail("mg2_setup: coarsest operator is singular", MG_ERR_NOT_SPD);
+  }
   mg2_ctx* c = new mg2_ctx;
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
     delete c;
@@ -719,7 +736,8 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
     W->assign((size_t)std::max(J - 1, 0) * 8, 0.0);
     for (int l = 0; l < J - 1; ++l) (*W)[(size_t)l * 8 + 0] = (*W)[(size_t)l * 8 + 3] = 1.0;
   }
-  const mg_status st = precision == 64 ? setup_typed<double>(c, levels) : setup_typed<float>(c, levels);
+  const mg_status st =
+      precision == 64 ? setup_typed<double>(c, levels, inv) : setup_typed<float>(c, levels, inv);
   if (st != MG_OK) {
     mg2_destroy(c);
     return st;

@@ -1,7 +1,7 @@
 // Kernels of restarted flexible GMRES, FGMRES(m), with right preconditioning
 // (Saad 1993): the outer Krylov method the paper pairs with its V-cycle and
-// full-multigrid preconditioners (Sec. 5).  Vectors are [n][B]; the Arnoldi
-// basis V_0..V_m and the preconditioned directions Z_0..Z_{m-1} are stored
+// full-multigrid preconditioners (Sec. 4.2, tab:helmholtz-results-precond).
+// Vectors are [n][B]; the Arnoldi basis V_0..V_m and the preconditioned directions Z_0..Z_{m-1} are stored
 // vstride = n * B apart.  Orthogonalisation is classical Gram-Schmidt
 // applied twice (CGS2): each pass forms all dot products from the same
 // vector, so a step needs two multi-dot reductions instead of j + 1

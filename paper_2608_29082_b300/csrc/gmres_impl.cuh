@@ -241,8 +241,7 @@ extern "C" mg_status mg_solve_fgmres(mg_ctx* c, const double* f, double* u, int3
   });
   if (st != MG_OK) return st;
   std::vector<double> rel(B);
-  MG_CUDA(cudaMemcpy(rel.data(), c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
-  if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
+  if ((st = read_results(c, s, (int)B, iters_out, rel.data())) != MG_OK) return st;
   if (relres_out) std::copy(rel.begin(), rel.end(), relres_out);
   mg_status result = MG_OK;
   for (double r : rel)

@@ -161,9 +161,7 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
     result = MG_ERR_DIVERGED;
   else if (c->h_state[0] > 0)
     result = MG_NOT_CONVERGED;
-  if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
-  if (relres_out)
-    MG_CUDA(cudaMemcpy(relres_out, c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
+  if ((st = read_results(c, s, (int)B, iters_out, relres_out)) != MG_OK) return st;
   if (result == MG_ERR_DIVERGED) c->err = "mg_solve_fcg: non-finite residual";
   if (result == MG_NOT_CONVERGED) c->err = "mg_solve_fcg: tolerance not met within max_iter";
   return result;

@@ -911,8 +911,9 @@ struct Issue {
   }
 
   // Full multigrid (nested iteration, the preconditioner of the paper's
-  // Sec. 5 Krylov experiments): f restricted to every level by the cycle's
-  // restriction, the coarsest level solved exactly, then on each finer level
+  // Sec. 4.2 Krylov experiments, tab:helmholtz-results-precond): f
+  // restricted to every level by the cycle's restriction, the coarsest
+  // level solved exactly, then on each finer level
   // the coarser solution through the cycle's prolongation (Phi_P P, from a
   // zero iterate) is the initial guess of one V-cycle started on that level.
   // The V-cycle on level l reuses the buffers of levels > l, whose FMG
@@ -1089,6 +1090,19 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
   MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   MG_CUDA(cudaStreamSynchronize(s));
   c->launches += it->second.nkernels + (int64_t)c->h_state[2] * it->second.nbody;
+  return MG_OK;
+}
+
+// Copies the per-right-hand-side iteration counts and relative residuals of
+// a finished solve to the host (either pointer may be NULL), ordered on the
+// solve's stream s and waited for: s may be a non-blocking stream, which a
+// plain cudaMemcpy on the legacy default stream would not wait for.
+mg_status read_results(mg_ctx* c, cudaStream_t s, int B, int32_t* iters_out, double* relres_out) {
+  if (iters_out)
+    MG_CUDA(cudaMemcpyAsync(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (relres_out)
+    MG_CUDA(cudaMemcpyAsync(relres_out, c->relres, B * sizeof(double), cudaMemcpyDeviceToHost, s));
+  MG_CUDA(cudaStreamSynchronize(s));
   return MG_OK;
 }
 
@@ -1405,6 +1419,7 @@ namespace {
 
 __global__ void k_init_solve(const double* __restrict__ fsum, int B, int* __restrict__ active,
                              int* __restrict__ iters, int* __restrict__ sexp) {
+  mgk::pdl_wait();
   const int b = threadIdx.x + blockIdx.x * blockDim.x;
   if (b >= B) return;
   active[b] = 1;
@@ -1414,11 +1429,13 @@ __global__ void k_init_solve(const double* __restrict__ fsum, int B, int* __rest
 }
 
 __global__ void k_shift_sexp(int* __restrict__ sexp, int* __restrict__ sexp_prev, int B) {
+  mgk::pdl_wait();
   const int b = threadIdx.x;
   if (b < B) sexp_prev[b] = sexp[b];
 }
 
 __global__ void k_bump_iters(const int* __restrict__ active, int* __restrict__ iters, int B) {
+  mgk::pdl_wait();
   const int b = threadIdx.x;
   if (b < B && active[b]) iters[b] += 1;
 }
@@ -1521,9 +1538,7 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
     result = MG_ERR_DIVERGED;
   else if (c->h_state[0] > 0)
     result = MG_NOT_CONVERGED;
-  if (iters_out) MG_CUDA(cudaMemcpy(iters_out, c->iters, B * sizeof(int), cudaMemcpyDeviceToHost));
-  if (relres_out)
-    MG_CUDA(cudaMemcpy(relres_out, c->relres, B * sizeof(double), cudaMemcpyDeviceToHost));
+  if ((st = read_results(c, s, (int)B, iters_out, relres_out)) != MG_OK) return st;
   if (result == MG_ERR_DIVERGED) c->err = "mg_solve: non-finite residual";
   if (result == MG_NOT_CONVERGED) c->err = "mg_solve: tolerance not met within max_iter";
   return result;
@@ -1560,8 +1575,30 @@ extern "C" mg_status mg_level_apply(mg_ctx* c, int32_t lev, int32_t op, const vo
     return c->fail(MG_ERR_INVALID, "mg_level_apply: no transfer/smoother on the coarsest level");
   if (op == MG_OP_COARSE && lev != c->J - 1)
     return c->fail(MG_ERR_INVALID, "mg_level_apply: coarse solve only on the coarsest level");
-  if (op < MG_OP_SMOOTH || op > MG_OP_OUTER_RESIDUAL)
+  if (op < MG_OP_SMOOTH || op > MG_OP_REFINE_RESIDUAL)
     return c->fail(MG_ERR_INVALID, "mg_level_apply: op");
+  if (op == MG_OP_REFINE_RESIDUAL) {
+    // the pre-loop kernels of mg_solve's refinement with the FP32 copy
+    // written to out: ||f||, s = ilogb ||f||, r = f - A u, float(2^-s r)
+    if (lev != 0 || !y) return c->fail(MG_ERR_INVALID, "mg_level_apply: refine residual needs level 0, f, u");
+    if (out == x || out == y) return c->fail(MG_ERR_INVALID, "mg_level_apply: out aliases an input");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int n0 = c->n[0];
+    const int bt = std::min((int)B, 32);
+    const int nblk = (n0 + mgk::kRedRows - 1) / mgk::kRedRows;
+    const dim3 rgrid(nblk, (B + bt - 1) / bt), rblock(mgk::kRedRows * bt);
+    Issue<double> is{c, c->d64, c->prm64, s, B};
+    is.launch(mgk::k_sumsq64, rgrid, rblock, 0, (const double*)x, n0, (int)B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, (int)B,
+              c->fsum);
+    is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B, c->active,
+              c->iters, c->sexp);
+    is.launch(mgk::k_resid64, rgrid, rblock, 0, c->d64[0].view(), (const double*)x,
+              (const double*)y, (float*)out, (const int*)c->sexp, (int)B, c->partial);
+    MG_CUDA(cudaGetLastError());
+    c->launches += is.nk;
+    return MG_OK;
+  }
   if (op == MG_OP_OUTER_RESIDUAL) {
     if (lev != 0 || !y) return c->fail(MG_ERR_INVALID, "mg_level_apply: outer residual needs level 0, f, u");
     if (out == x || out == y) return c->fail(MG_ERR_INVALID, "mg_level_apply: out aliases an input");

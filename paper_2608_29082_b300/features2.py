@@ -1,7 +1,7 @@
 """Two features per node (d = 2): the learnable cycle on complex systems.
 
 Binding of the mg2_* entry points of libmg.so (include/mg.h).  The Helmholtz
-setting of Sec. 4.3 carries (Re u, Im u) as two node features, and every
+setting of Sec. 4.2 carries (Re u, Im u) as two node features, and every
 SAGEConv holds W_1, W_2 in R^{2x2} (Sec. 3.2).  The host set-up uses the
 native Galerkin and prolongation helpers of the real path: P is real, so
 P^T A P = P^T Re(A) P + i P^T Im(A) P, and the two products are merged

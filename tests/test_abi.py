@@ -93,3 +93,63 @@ def test_two_feature_entry_points_reject_bad_input_without_gpu():
     assert lib.mg2_vcycle(None, None, None, 1, None) == -1
     assert lib.mg2_solve_fgmres(None, None, None, 1, 1e-8, 10, 10, 0, None, None, None) == -1
     assert lib.mg_set_cheb(None, 2, L.ptr(x, L.f64p)) == -1
+
+
+def _two_level(AJ):
+    """A 2-level hierarchy: the 3-point 1D Laplacian on 3 rows, P = hat
+    function of the middle row, and the given coarsest operator (1 x 1 or
+    2 x 2, dense)."""
+    import scipy.sparse as sp
+    A0 = L.HostCSR.from_scipy(sp.csr_matrix(np.array([[2.0, -1, 0], [-1, 2, -1], [0, -1, 2]])))
+    nJ = AJ.shape[0]
+    P = L.HostCSR.from_scipy(sp.csr_matrix(np.ones((3, nJ)) * 0.5))
+    AJc = L.HostCSR.from_scipy(sp.csr_matrix(AJ))
+    deg0, degJ = np.full(3, 0.5), np.full(nJ, 1.0)
+    Parr = (L.CSR * 1)(P.c)
+    degs = (L.f64p * 2)(L.ptr(deg0, L.f64p), L.ptr(degJ, L.f64p))
+    Aarr = (L.CSR * 2)(A0.c, AJc.c)
+    h = L.Hier(2, Parr, degs)
+    keep = [A0, P, AJc, deg0, degJ, Parr, degs, Aarr]
+    return h, Aarr, keep
+
+
+def test_setup_rejects_indefinite_coarsest_operator_without_gpu():
+    """Failure detection on the host: a coarsest operator that is not SPD
+    (indefinite, or singular) makes mg_setup return MG_ERR_NOT_SPD before any
+    device allocation; a non-positive diagonal entry (the smoother divides by
+    it) is rejected earlier as MG_ERR_INVALID.  No context is returned."""
+    from paper_2608_29082_b300 import LMGParams
+    lib = L.lib()
+    cases = ((np.array([[1.0, 2.0], [2.0, 1.0]]), -3, "not SPD"),
+             (np.array([[1.0, 1.0], [1.0, 1.0]]), -3, "not SPD"),
+             (np.array([[-1.0]]), -1, "non-positive diagonal"))
+    for AJ, want, msg in cases:
+        h, Aarr, keep = _two_level(AJ)
+        prm = LMGParams.identity(2)
+        p, pkeep = prm.c_struct()
+        for prec in (64, 32):
+            ctx = C.c_void_p()
+            st = lib.mg_setup(C.byref(ctx), C.byref(h), Aarr, C.byref(p), 1, prec, None)
+            assert st == want and not ctx.value, (AJ, prec, st)
+            assert msg in L.last_error()
+
+
+def test_two_feature_setup_rejects_singular_coarsest_operator_without_gpu():
+    """mg2_setup inverts the complex coarsest operator on the host before
+    any CUDA call: an exactly singular one gives MG_ERR_NOT_SPD, a zero
+    diagonal MG_ERR_INVALID."""
+    lib = L.lib()
+    rp = np.array([0, 2, 4], dtype=np.int32)
+    ci = np.array([0, 1, 0, 1], dtype=np.int32)
+    deg = np.ones(2)
+    singular = np.array([1.0, 1.0, 2.0, 2.0, 1.0, 1.0, 2.0, 2.0])  # rows (1+i, 2+2i) twice
+    zero_diag = np.array([0.0, 0.0, 1.0, 0.0, 1.0, 0.0, 1.0, 0.0])
+    for vals, want, msg in ((singular, -3, "singular"), (zero_diag, -1, "zero diagonal")):
+        lv = (L.Level2 * 1)()
+        lv[0].n = 2
+        lv[0].A_indptr, lv[0].A_indices = L.ptr(rp, L.i32p), L.ptr(ci, L.i32p)
+        lv[0].A_vals, lv[0].inv_deg = L.ptr(vals, L.f64p), L.ptr(deg, L.f64p)
+        for prec in (64, 32):
+            ctx = C.c_void_p()
+            assert lib.mg2_setup(C.byref(ctx), 1, lv, 1, prec) == want and not ctx.value
+            assert msg in L.last_error()

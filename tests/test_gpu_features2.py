@@ -1,6 +1,6 @@
 """Two features per node (mg2_*) against the FP64 oracle, through the C ABI.
 
-The complex Helmholtz operator with impedance boundary (Sec. 4.3) and
+The complex Helmholtz operator with impedance boundary (Sec. 4.2) and
 random two-feature weights W_1, W_2 in R^{2x2}.  Per-cycle parity: the GPU
 cycle and the oracle cycle map the same iterate; FP64 within 1e-12
 relative.  FP32 against the FP64 oracle applied to the FP32 input: 1e-5 for

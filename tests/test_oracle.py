@@ -293,7 +293,7 @@ def dense_fmg(H, p):
 
 @pytest.mark.parametrize("which", ["identity", "random"])
 def test_fmg_matches_dense_nested_iteration(poisson33, checker17, which):
-    """Full multigrid (Sec. 5 preconditioner) against its dense construction
+    """Full multigrid (the Sec. 4.2 preconditioner) against its dense construction
     from the per-level error propagation matrices, on Poisson and on a jump
     coefficient; and it is linear in f."""
     for case, seed in ((poisson33, 5), (checker17, 6)):
@@ -500,6 +500,81 @@ def test_fgmres_with_fmg_preconditioner(checker17):
     assert its < 60
 
 
+def _cg_iterates(A, f, M=None, k=15):
+    """scipy's (preconditioned) conjugate gradients from zero: the first k
+    iterates, recorded by its callback."""
+    xs = []
+    spla.cg(A, f, rtol=1e-300, atol=0.0, maxiter=k, M=M, callback=lambda x: xs.append(x.copy()))
+    return xs
+
+
+def test_fcg_identity_preconditioner_is_cg(poisson33):
+    """FCG(1) with the identity as preconditioner is the conjugate gradient
+    method: its iterates equal scipy's CG iterates."""
+    p, H = poisson33
+    A = H.levels[0].A
+    f = p.f[:, 0]
+    ref = _cg_iterates(A, f, k=15)
+    _, its, hist, us = O.fcg(A, f, lambda v: v.copy(), 1e-300, max_iter=15)
+    assert its == 15 and len(ref) == 15
+    for k in range(15):
+        assert np.linalg.norm(us[k] - ref[k]) <= 1e-10 * np.linalg.norm(ref[k]), k
+        # the recurrence residual is the true residual (exact arithmetic)
+        assert abs(hist[k] - np.linalg.norm(f - A @ us[k])) <= 1e-10 * np.linalg.norm(f), k
+
+
+def test_fcg_fixed_spd_preconditioner_is_pcg(checker17):
+    """With a fixed SPD preconditioner (symmetric Gauss-Seidel on the
+    jump-coefficient operator) FCG(1) is preconditioned CG: same iterates as
+    scipy's PCG with the same operator."""
+    p, H = checker17
+    A = H.levels[0].A.tocsr()
+    Ad = A.toarray()
+    Lo = np.tril(Ad)
+    Dg = np.diag(Ad)
+
+    def sgs(v):
+        return sla.solve_triangular(Lo.T, Dg * sla.solve_triangular(Lo, v, lower=True),
+                                    lower=False)
+    f = p.f[:, 1]
+    M = spla.LinearOperator(A.shape, matvec=sgs)
+    ref = _cg_iterates(A, f, M=M, k=8)
+    _, its, _, us = O.fcg(A, f, sgs, 1e-300, max_iter=8)
+    assert its == 8 and len(ref) == 8
+    for k in range(8):
+        assert np.linalg.norm(us[k] - ref[k]) <= 1e-10 * np.linalg.norm(ref[k]), k
+
+
+def test_fcg_exact_preconditioner_converges_in_one_step(checker17):
+    p, H = checker17
+    A = H.levels[0].A.tocsc()
+    f = p.f[:, 0]
+    u, its, hist, _ = O.fcg(A, f, spla.splu(A).solve, 1e-12)
+    assert its == 1 and np.linalg.norm(f - A @ u) < 1e-12 * np.linalg.norm(f)
+
+
+def test_fcg_variable_preconditioner_orthogonality(checker17):
+    """With a variable, nonsymmetric preconditioner (the learnable cycle with
+    random Theta) FCG(1) still makes each new direction d_i = (u_{i+1} -
+    u_i)/alpha_i A-orthogonal to the previous one and each new residual
+    orthogonal to the last direction: the two properties that fix beta and
+    alpha.  It converges to the tolerance."""
+    p, H = checker17
+    th = random_params(H.J, 31, 0.1)
+    A = H.levels[0].A
+    f = p.f[:, 0]
+    M = lambda v: O.vcycle(H, th, v[:, None], np.zeros((v.size, 1)))[:, 0]  # noqa: E731
+    u, its, hist, us = O.fcg(A, f, M, 1e-10, max_iter=200)
+    assert np.linalg.norm(f - A @ u) < 1e-9 * np.linalg.norm(f)
+    us = [np.zeros_like(f)] + us
+    anorm = lambda x: np.sqrt(x @ (A @ x))  # noqa: E731
+    for i in range(1, min(len(us) - 1, 12)):
+        d_prev, d = us[i] - us[i - 1], us[i + 1] - us[i]
+        assert abs(d @ (A @ d_prev)) <= 1e-10 * anorm(d) * anorm(d_prev), i
+        r_next = f - A @ us[i + 1]
+        assert abs(d @ r_next) <= 1e-10 * np.linalg.norm(d) * np.linalg.norm(f), i
+
+
 # ------------------------------------------ two features per node (d = 2) ----
 
 @pytest.fixture(scope="module", params=[2, 3])
@@ -646,35 +721,6 @@ def test_fmg2_dense_nested_iteration(helmholtz17, seed):
     Mo = np.concatenate([out.real, out.imag], axis=0)
     M = dense_fmg2(H, th)
     assert np.abs(M - Mo).max() < 1e-10 * max(1.0, np.abs(M).max())
-
-
-@pytest.mark.parametrize("k", [1, 2, 4])
-def test_gmres_update_is_the_krylov_least_squares_minimiser(helmholtz17, k):
-    """k GMRES steps from zero: the delta in span{r, A r, ..., A^{k-1} r}
-    minimising ||r - A delta||, here against the least-squares solution over
-    the explicit (monomial) Krylov basis."""
-    _, H = helmholtz17
-    A = H.levels[0].A
-    r = np.random.default_rng(k).standard_normal((A.shape[0], 2)) + 0j
-    got = O.gmres_update(A, r, k)
-    for b in range(2):
-        K = [r[:, b]]
-        for _ in range(k - 1):
-            K.append(A @ K[-1])
-        K = np.stack(K, axis=1)
-        c = np.linalg.lstsq(A @ K, r[:, b], rcond=None)[0]
-        ref = K @ c
-        assert np.linalg.norm(got[:, b] - ref) < 1e-9 * np.linalg.norm(ref)
-
-
-def test_gmres_update_full_space_is_the_solve(helmholtz17):
-    """With as many steps as unknowns (coarsest level) GMRES solves exactly."""
-    _, H = helmholtz17
-    A = H.levels[-1].A
-    r = np.random.default_rng(0).standard_normal((A.shape[0], 1)) + 1j
-    got = O.gmres_update(A, r, A.shape[0])
-    ref = np.linalg.solve(A.toarray(), r)
-    assert np.linalg.norm(got - ref) < 1e-8 * np.linalg.norm(ref)
 
 
 def test_cheb_coefficient_gradient(checker17):

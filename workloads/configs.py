@@ -101,7 +101,7 @@ def lshape_anisotropic(refinements: int = 7, batch: int = 16, seed: int = 0,
 
 def helmholtz_square(N: int = 33, J: int = 3, k: float = 2 * np.pi, batch: int = 1,
                      seed: int = 0) -> Problem:
-    """Helmholtz with the impedance boundary condition (Sec. 4.3) on uniform
+    """Helmholtz with the impedance boundary condition (Sec. 4.2) on uniform
     meshes of [-1/2, 1/2]^2.  The impedance condition keeps every vertex a
     DOF (no Dirichlet boundary).  A_full is complex symmetric:
     K - k^2 M - i k B with the P1 stiffness, mass and boundary-edge mass."""

@@ -137,7 +137,7 @@ def assemble_boundary_mass_p1(L: MeshLevel) -> sp.csr_matrix:
 
 
 def disk_source(xy: np.ndarray, centers, r_s: float = 0.02, eps_s: float = 0.001) -> np.ndarray:
-    """Smoothed disk sources of the Helmholtz experiment (Sec. 4.3): 100 (1 -
+    """Smoothed disk sources of the Helmholtz experiment (Sec. 4.2): 100 (1 -
     prod_c tanh((|x - c|^2 - r_s^2) / eps_s)); one centre for training, two
     for testing."""
     t = np.ones(xy.shape[0])
