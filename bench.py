@@ -69,6 +69,15 @@ def make_problem(seed: int):
     return W.checkerboard_square(N=513, J=9, ncell=8, values=(1.0, 1e4), batch=1, seed=seed)
 
 
+def bench_config(args, ws: int) -> dict:
+    """The workload both arms measure (the same dict in both JSON lines)."""
+    from paper_2608_29082_b300 import trained
+    return {"workload": WORKLOAD, "dof": 261121, "levels": 9, "nrhs": 1, "tol": TOL,
+            "params": trained.describe(args.params),
+            "parallelism": "replicas" if ws > 1 else "single GPU",
+            "l2": "GPU arm: flushed (256 MB write) before every timed solve"}
+
+
 # ------------------------------------------------------------ clocks -------
 
 class ClockSampler:
@@ -218,12 +227,12 @@ def run_ours(args):
     hier = lmg.Hierarchy.from_problem(prob)
     J = hier.J
     plain = lmg.LMGParams.identity(J)
+    # the headline solves with the committed trained set (the reference arm
+    # solves with the same one); Algorithm 3 also runs here, on this
+    # operator, to measure the training cost and check the committed set
+    learned = trained.load(args.params, J)
     training = None
-    if args.params:
-        learned = trained.load(args.params, J)
-    else:
-        # Algorithm 3 on this operator, FP32 forward/adjoint, Rprop; training
-        # right-hand sides come from a different seed than the solved source
+    if not args.params:
         from paper_2608_29082_b300.train_cli import PRESETS
         from paper_2608_29082_b300.training import ParamMap, Trainer
         from workloads import fields
@@ -234,21 +243,24 @@ def run_ours(args):
         log = Trainer(Str, ParamMap(J, **PRESETS[TRAIN_PRESET]), n_cycles=TRAIN_K).train(
             ftr, plain, max_epochs=TRAIN_EPOCHS)
         torch.cuda.synchronize()
-        learned = log.params
         training = {"preset": TRAIN_PRESET, "epochs": len(log.losses), "unrolled_cycles": TRAIN_K,
                     "rhs": TRAIN_BATCH, "seconds": round(time.perf_counter() - t0, 2),
-                    "loss_ratio": float(log.best_loss / log.losses[0])}
+                    "loss_ratio": float(log.best_loss / log.losses[0]),
+                    "max_abs_diff_vs_committed": float(np.abs(log.params.flat()
+                                                              - learned.flat()).max())}
         Str.close()
     S32 = lmg.Solver(hier, learned, precision=32, max_batch=1)
     S64 = lmg.Solver(hier, plain, precision=64, max_batch=1)
+    S32c = lmg.Solver(hier, plain, precision=32, max_batch=1)
     if args.host_loop:
-        S32.set_option("device_loop", 0)
-        S64.set_option("device_loop", 0)
+        for S in (S32, S64, S32c):
+            S.set_option("device_loop", 0)
     f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
     u = torch.zeros_like(f)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
 
-    def timed(S, method="refine"):
+    def timed(S, method="refine", pc=0):
+        S.set_option("fcg_precond", pc)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         for _ in range(args.warmup):
@@ -270,6 +282,7 @@ def run_ours(args):
         if pg:
             pg.barrier()
         ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        S.set_option("fcg_precond", 0)
         return float(np.mean(ms)), infos[-1], S.kernel_launches() - k0
 
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -277,26 +290,27 @@ def run_ours(args):
         ms64, info64, nk64 = timed(S64)
     clocks = clk.summary()
     u32 = u.clone()
-    # the same learned cycle as preconditioner of flexible CG (FP64 outer)
-    msfcg, infofcg, nkfcg = timed(S32, method="fcg")
-    # the learned cycle, nonsymmetric, as the preconditioner of restarted
-    # flexible GMRES: one V-cycle, and one full multigrid (Sec. 4.2,
-    # tab:helmholtz-results-precond)
-    msgmv, infogmv, nkgmv = timed(S32, method="fgmres")
-    S32.set_option("fcg_precond", 1)
-    msgmf, infogmf, nkgmf = timed(S32, method="fgmres")
-    S32.set_option("fcg_precond", 0)
-    # classical (identity) Theta as the FP32 preconditioner of flexible CG:
-    # one V-cycle, and one full multigrid (nested iteration)
-    S32c = lmg.Solver(hier, plain, precision=32, max_batch=1)
-    msccg, infoccg, _ = timed(S32c, method="fcg")
-    S32c.set_option("fcg_precond", 1)
-    msfmg, infofmg, nkfmg = timed(S32c, method="fcg")
-    S32c.close()
+    # the same comparison with Krylov outer loops (Sec. 4.2's preconditioner
+    # use; tab:helmholtz-results-precond) and with the classical Theta in
+    # the same FP32 cycle: every variant to the same tolerance
+    variants = {}
+    for tag, S, method, pc in (("learned_fcg", S32, "fcg", 0),
+                               ("learned_fgmres", S32, "fgmres", 0),
+                               ("learned_fgmres_fmg", S32, "fgmres", 1),
+                               ("classical_fp32_refine", S32c, "refine", 0),
+                               ("classical_fp32_fcg", S32c, "fcg", 0),
+                               ("classical_fp32_fcg_fmg", S32c, "fcg", 1),
+                               ("classical_fp32_fgmres", S32c, "fgmres", 0),
+                               ("plain_fp64_fcg", S64, "fcg", 0)):
+        ms, info, nk = timed(S, method, pc)
+        variants[tag] = (ms, info, nk)
     # max over ranks
     if pg:
-        ms32, ms64, msfcg, msgmv, msgmf, msccg, msfmg = max_over_ranks(
-            [ms32, ms64, msfcg, msgmv, msgmf, msccg, msfmg], pg, dev)
+        tags = list(variants)
+        vals = max_over_ranks([ms32, ms64] + [variants[t][0] for t in tags], pg, dev)
+        ms32, ms64 = vals[0], vals[1]
+        for t, v in zip(tags, vals[2:]):
+            variants[t] = (v,) + variants[t][1:]
 
     # end to end through the public host API (pinned host buffers)
     fh = torch.tensor(prob.f, dtype=torch.float64).pin_memory().numpy()
@@ -312,17 +326,20 @@ def run_ours(args):
     e2e_ms = float(np.mean(e2e))
 
     # dominant kernel: per-launch device times from CUDA events on the stream
-    rhat = (f / torch.linalg.norm(f)).float()
-    c = torch.zeros_like(rhat)
-    agg = {}
-    reps = 5
-    for _ in range(reps):
-        c.zero_()
-        for name, lev, t in S32.vcycle_profile(rhat, c):
-            key = (name, lev)
-            a = agg.setdefault(key, [0.0, 0])
-            a[0] += t
-            a[1] += 1
+    def cycle_profile(S, dtype):
+        rhat = (f / torch.linalg.norm(f)).to(dtype)
+        c = torch.zeros_like(rhat)
+        agg = {}
+        reps = 5
+        for _ in range(reps):
+            c.zero_()
+            for name, lev, t in S.vcycle_profile(rhat, c):
+                a = agg.setdefault((name, lev), [0.0, 0])
+                a[0] += t
+                a[1] += 1
+        return agg, reps
+
+    agg, reps = cycle_profile(S32, torch.float32)
     # the FP64 refinement residual, once per iteration
     r64 = torch.empty_like(f)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -349,10 +366,32 @@ def run_ours(args):
     shares = sorted(((f"{k[0]}@L{k[1]}", round(v / total, 4)) for k, v in per_cycle.items()),
                     key=lambda kv: -kv[1])[:8]
 
-    # HBM-bound workload: the L-shape level kernels, working set > L2
-    lshape = None
+    # HBM GB/s of whole solves: algorithmic bytes of every launch of a
+    # cycle (the profiled launch sequence) plus the per-iteration FP64
+    # residual and update, times the iterations, over the solve time
+    def solve_gbs(S, dtype, iters, ms, fp32_cycle):
+        a, r = cycle_profile(S, dtype)
+        bb = 4 if fp32_cycle else 8
+        cyc = sum(kernel_bytes(nm, lv, hier, 1, bb) * cnt / r for (nm, lv), (_, cnt) in a.items())
+        n0 = hier.sizes[0]
+        nnz_off = hier.A[0].data.size - n0
+        resid = nnz_off * 8 + 2 * n0 * 8 + n0 * (8 + 8 + (4 if fp32_cycle else 0))
+        update = n0 * (4 + 8 + 8) if fp32_cycle else 0
+        tot = iters * (cyc + resid + update) + resid
+        return round(tot / (ms * 1e-3) / 1e9, 1), int(tot)
+
+    plain_gbs, plain_bytes = solve_gbs(S64, torch.float64, int(info64.iters[0]), ms64, False)
+    learned_gbs, learned_bytes = solve_gbs(S32, torch.float32, int(info32.iters[0]), ms32, True)
+    for S in (S32, S64, S32c):
+        S.close()
+
+    # HBM-bound workload: the L-shape (config 4), working set > L2
+    lshape = lshape_solves = None
     if rank == 0 and not args.no_lshape:
-        lshape = lshape_roofline(dev, peak)
+        lshape, lshape_solves = lshape_section(dev, peak, args)
+    train_step = None
+    if rank == 0 and not args.no_lshape:
+        train_step = training_step_section(dev)
 
     # oracle on the host cores, same workload (rank 0 at N=1 only)
     cpu = None
@@ -360,6 +399,11 @@ def run_ours(args):
         cpu = cpu_baseline(prob, learned)
 
     if rank == 0:
+        def var(tag):
+            ms, info, _ = variants[tag]
+            return {"ms": round(ms, 4), "iters": int(info.iters[0]),
+                    "relres": float(info.relres[0])}
+        best_tag = min(variants, key=lambda t: variants[t][0])
         out = {
             "metric": "time to 1e-8 relative residual (learned FP32 V-cycle + FP64 refinement)",
             "value": round(ms32, 4),
@@ -373,40 +417,29 @@ def run_ours(args):
             "vs_baseline": None,
             "dtype": "f32 cycle + f64 refinement",
             "data": "synthetic (seeded checkerboard coefficient and N(0,1) source)",
-            "config": {"workload": WORKLOAD, "dof": hier.sizes[0], "levels": J, "nrhs": 1,
-                       "parallelism": "replicas" if ws > 1 else "single GPU",
-                       "l2": "flushed (256 MB write) before every timed solve",
-                       "params": trained.describe(args.params) if args.params else
-                       "trained at start-up (Algorithm 3, see training)"},
+            "config": bench_config(args, ws),
             "training": training,
             "learned_iters": int(info32.iters[0]),
             "learned_relres": float(info32.relres[0]),
+            "learned_hbm_gbs": learned_gbs,
+            "learned_algorithmic_bytes_per_solve": learned_bytes,
             "plain_fp64_ms": round(ms64, 4),
             "plain_fp64_iters": int(info64.iters[0]),
             "plain_fp64_relres": float(info64.relres[0]),
-            "learned_fcg_ms": round(msfcg, 4),
-            "learned_fcg_iters": int(infofcg.iters[0]),
-            "learned_fcg_relres": float(infofcg.relres[0]),
-            "learned_fgmres_ms": round(msgmv, 4),
-            "learned_fgmres_iters": int(infogmv.iters[0]),
-            "learned_fgmres_relres": float(infogmv.relres[0]),
-            "learned_fgmres_fmg_ms": round(msgmf, 4),
-            "learned_fgmres_fmg_iters": int(infogmf.iters[0]),
-            "learned_fgmres_fmg_relres": float(infogmf.relres[0]),
-            "classical_fp32_fcg_ms": round(msccg, 4),
-            "classical_fp32_fcg_iters": int(infoccg.iters[0]),
-            "classical_fp32_fcg_fmg_ms": round(msfmg, 4),
-            "classical_fp32_fcg_fmg_iters": int(infofmg.iters[0]),
-            "classical_fp32_fcg_fmg_relres": float(infofmg.relres[0]),
+            "plain_fp64_hbm_gbs": plain_gbs,
+            "plain_fp64_algorithmic_bytes_per_solve": plain_bytes,
             "speedup_vs_plain_fp64": round(ms64 / ms32, 3),
+            "outer_loops": {t: var(t) for t in variants},
+            "fastest_variant": best_tag,
+            "break_even_solves_vs_plain_fp64": (
+                round(training["seconds"] * 1e3 / (ms64 - ms32), 1)
+                if training and ms64 > ms32 else None),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms/solve",
                     "h2d_bytes_per_step": int(2 * fh.nbytes), "d2h_bytes_per_step": int(uh.nbytes)},
             "gpu_launches": int(nk32),
-            "gpu_launches_by_region": {"learned_refinement": int(nk32), "plain_fp64": int(nk64),
-                                       "learned_fcg": int(nkfcg),
-                                       "learned_fgmres": int(nkgmv),
-                                       "learned_fgmres_fmg": int(nkgmf),
-                                       "classical_fcg_fmg": int(nkfmg)},
+            "gpu_launches_by_region": dict({"learned_refinement": int(nk32),
+                                            "plain_fp64": int(nk64)},
+                                           **{t: int(variants[t][2]) for t in variants}),
             "roofline": {"bound": "hbm", "kernel": f"{dname}@level{dlev}",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4),
@@ -419,6 +452,8 @@ def run_ours(args):
                          "note": "latency-bound: the whole FP32 hierarchy (about 30 MB) stays "
                                  "in L2 during a solve; the HBM-bound case is roofline_lshape"},
             "roofline_lshape": lshape,
+            "lshape_time_to_tol": lshape_solves,
+            "training_step": train_step,
             "kernel_shares_per_vcycle": shares,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -428,17 +463,29 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
-def lshape_roofline(dev, peak):
-    """The dominant FP32 V-cycle kernel on the jittered anisotropic L-shape
-    (7 red refinements, 3141633 DOF, 16 rhs): per-launch CUDA-event times of
-    the eagerly launched cycle, algorithmic bytes per launch, achieved GB/s."""
+LSHAPE_PARAMS = os.path.join(ROOT, "paper_2608_29082_b300", "params", "lshape7_learned.json")
+
+
+def lshape_section(dev, peak, args):
+    """Config 4, the jittered anisotropic L-shape (7 red refinements, 3141633
+    DOF, 8 levels, 16 rhs).  (1) The dominant FP32 V-cycle kernel: per-launch
+    CUDA-event times of the eagerly launched cycle, algorithmic bytes per
+    launch, achieved GB/s, and the smoothing step's bytes over its time.
+    (2) Time to 1e-8 for every rhs: the learned FP32 cycle (the committed set
+    trained on this operator) in FGMRES and FCG against the plain FP64 cycle
+    in FCG and the classical FP32 cycle; the final relative residuals are
+    recomputed on the host in FP64 from the workload's own finest operator.
+    The stationary iterations (refinement, plain multigrid) do not reach 1e-8
+    here (point smoothers on a 1e-3 anisotropy) and are not timed."""
     import torch
     import paper_2608_29082_b300 as lmg
     import workloads as W
-    from paper_2608_29082_b300.workload_bench import kernel_table
+    from paper_2608_29082_b300 import trained
+    from paper_2608_29082_b300.workload_bench import kernel_table, level_bytes
     t0 = time.perf_counter()
     prob = W.lshape_anisotropic(refinements=7, batch=16, seed=0)
     hier = lmg.Hierarchy.from_problem(prob)
+    setup_s = time.perf_counter() - t0
     p = lmg.LMGParams.identity(hier.J)
     p.wB[:, 1], p.wR[:, 1], p.wP[:, 1] = 0.1, 0.05, -0.05  # convolutions active on every level
     S = lmg.Solver(hier, p, precision=32, max_batch=16)
@@ -450,7 +497,18 @@ def lshape_roofline(dev, peak):
     S.close()
     top = rows[0]
     hbm = [r for r in rows if r["GBps"] and r["level"] == 0]
-    return {"workload": f"L-shape anisotropic, {hier.sizes[0]} DOF, {hier.J} levels, 16 rhs, "
+    # the level-0 smoothing step: SURVEY-style algorithmic bytes
+    # s (b_v + 4) + 3 B b_x + 4 per row over the time of one step
+    n0 = hier.sizes[0]
+    nnz0 = hier.A[0].data.size
+    step_bytes = nnz0 * (4 + 4) + 3 * 16 * n0 * 4 + 4 * n0
+    step_us = sum(r["us_per_launch"] for r in rows
+                  if r["level"] == 0 and r["kernel"] in ("smooth_halo",))
+    if not step_us:
+        step_us = sum(r["us_per_launch"] for r in rows
+                      if r["level"] == 0 and r["kernel"] in ("residual_scaled", "sage_conv_update"))
+    step_gbs = step_bytes / (step_us * 1e-6) / 1e9 if step_us else None
+    roof = {"workload": f"L-shape anisotropic, {n0} DOF, {hier.J} levels, 16 rhs, "
                         "FP32 learned cycle",
             "bound": "hbm", "kernel": f"{top['kernel']}@level{top['level']}",
             "achieved": top["GBps"], "peak": peak, "unit": "GB/s",
@@ -461,8 +519,77 @@ def lshape_roofline(dev, peak):
             "algorithmic_bytes_per_launch": int(top["algorithmic_MB"] * 1e6),
             "avg_launch_us": top["us_per_launch"], "share_of_cycle": top["share"],
             "cycle_us": round(cycle_us, 1),
+            "smoothing_step": {"algorithmic_bytes": int(step_bytes), "us": round(step_us, 2),
+                               "GBps": round(step_gbs, 1) if step_gbs else None,
+                               "frac": round(step_gbs / peak, 4) if step_gbs else None},
             "level0_kernels": [[r["kernel"], r["GBps"], r["frac_of_hbm"]] for r in hbm],
-            "setup_s": round(time.perf_counter() - t0, 1)}
+            "setup_s": round(setup_s, 1)}
+    # time to tolerance
+    I = prob.mesh.levels[0].interior
+    A_int = prob.A_full.tocsr()[I][:, I]
+    f64 = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    fn = np.sqrt((prob.f * prob.f).sum(0))
+    learned = trained.read(LSHAPE_PARAMS).with_levels(hier.J)
+    plain = lmg.LMGParams.identity(hier.J)
+    out = {"workload": f"L-shape anisotropic, {n0} DOF, {hier.J} levels, 16 rhs, tol {TOL}",
+           "params": trained.describe(LSHAPE_PARAMS)}
+    reps = 2
+    for tag, prm, prec, method in (("learned_fp32_fgmres", learned, 32, "fgmres"),
+                                   ("learned_fp32_fcg", learned, 32, "fcg"),
+                                   ("classical_fp32_fgmres", plain, 32, "fgmres"),
+                                   ("classical_fp32_fcg", plain, 32, "fcg"),
+                                   ("plain_fp64_fcg", plain, 64, "fcg")):
+        S = lmg.Solver(hier, prm, precision=prec, max_batch=16)
+        uu = torch.zeros_like(f64)
+        S.solve(f64, uu, tol=TOL, max_iter=MAX_ITER, method=method)
+        ms = []
+        for _ in range(reps):
+            uu.zero_()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            _, info = S.solve(f64, uu, tol=TOL, max_iter=MAX_ITER, method=method)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        r = prob.f - A_int @ uu.cpu().numpy()
+        rr = np.sqrt((r * r).sum(0)) / fn
+        out[tag] = {"ms": round(float(np.mean(ms)), 2), "iters_max": int(info.iters.max()),
+                    "status": int(info.status), "max_relres_recheck": float(rr.max())}
+        S.close()
+    return roof, out
+
+
+def training_step_section(dev):
+    """Config 2: one training step of Algorithm 3 (K = 10 unrolled FP32
+    cycles recorded with per-level checkpoints, the residual loss, the
+    hand-written adjoint and the parameter gradients) on the 257^2 4x4
+    {1, 1e3} checkerboard, 8 levels, 64 rhs; CUDA events over 10 steps."""
+    import torch
+    import paper_2608_29082_b300 as lmg
+    import workloads as W
+    from paper_2608_29082_b300.training import ParamMap, Trainer
+    prob = W.training_square("checker", N=257, J=8, batch=64, seed=0)
+    hier = lmg.Hierarchy.from_problem(prob)
+    p = lmg.LMGParams.identity(hier.J)
+    S = lmg.Solver(hier, p, precision=32, max_batch=64)
+    f = torch.tensor(prob.f, dtype=torch.float32, device=dev)
+    tr = Trainer(S, ParamMap(hier.J, shared=("wB1", "wB2", "wR1", "wR2", "wP1", "wP2")),
+                 n_cycles=10)
+    for _ in range(3):
+        tr.loss_and_grad(p, f, torch.zeros_like(f))
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    steps = 10
+    e0.record()
+    for _ in range(steps):
+        loss, g, _ = tr.loss_and_grad(p, f, torch.zeros_like(f))
+    e1.record()
+    torch.cuda.synchronize()
+    S.close()
+    return {"workload": f"training: checkerboard 257^2 (4x4 cells, k in {{1,1e3}}), {hier.J} "
+                        "levels, 64 rhs, K=10 unrolled cycles, FP32, shared SAGEConv weights",
+            "ms_per_step": round(e0.elapsed_time(e1) / steps, 3), "steps": steps,
+            "loss": float(loss)}
 
 
 def cpu_baseline(prob, params):
@@ -478,6 +605,7 @@ def cpu_baseline(prob, params):
                            capture_output=True, text=True, env=env, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": "ms/solve", "cores": 1, "kind": "oracle",
+                "host_cpus": os.cpu_count(),
                 "sample": "oracle leg failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
     return json.loads(r.stdout.strip().splitlines()[-1])
 
@@ -498,9 +626,11 @@ def oracle_leg(path):
     dt = time.perf_counter() - t0
     print(json.dumps({
         "value": round(dt * 1e3, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
+        "host_cpus": os.cpu_count(),
         "sample": f"one full FP64 refinement solve ({int(r.iters[0])} V-cycles, the same learned "
                   f"parameters, final relres {float(r.relres[0]):.2e}) of the same workload; "
-                  f"setup {setup:.2f}s excluded; one thread (BLAS/OpenMP pools set to 1)"}),
+                  f"setup {setup:.2f}s excluded; one thread (BLAS/OpenMP pools set to 1; the "
+                  f"oracle's sparse products are single-threaded, so more cores do not apply)"}),
         flush=True)
 
 
@@ -533,8 +663,9 @@ def run_reference(args):
            "value": round(v, 2), "unit": "ms/solve", "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": round(v, 2), "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "nrhs": 1},
+           "config": bench_config(args, ws),
            "cpu_baseline": {"value": round(v, 2), "unit": "ms/solve", "cores": 1, "kind": "oracle",
+                            "host_cpus": os.cpu_count(),
                             "sample": f"full FP64 oracle refinement solve ({iters} V-cycles, "
                                       f"learned parameters: {trained.describe(args.params)}) "
                                       "per step"},

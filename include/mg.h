@@ -317,6 +317,18 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     the batch, and the first stage over all tiles fits in
  *                     one wave of the GPU; otherwise the two-kernel form.
  *                     Other values than [0, 2^30]: MG_ERR_INVALID.
+ *   MG_OPT_SELL_HALO_ROWS rows per tile of the halo-fused steps on SELL
+ *                     levels (default 256; 0: unfused; a multiple of 32 up
+ *                     to 8192, else MG_ERR_INVALID).  At set-up (and when
+ *                     this value changes) the host lists, per tile of
+ *                     consecutive rows, the outside rows that neighbour it
+ *                     and the local slot of every column; a block then
+ *                     evaluates a step's first stage (delta, r or P e_c) on
+ *                     its rows and that halo in shared memory and applies
+ *                     the SAGEConv mean from there: one kernel per step, and
+ *                     the first stage never written to device memory.  Used
+ *                     on a level while (rows + halo) * nrhs values fit
+ *                     160 KB.  Changing it synchronises the device.
  *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg and mg_solve_fgmres:
  *                     0 (default) one V-cycle from zero, 1 one full
  *                     multigrid (mg_fmg).
@@ -336,7 +348,8 @@ typedef enum {
   MG_OPT_DEVICE_LOOP = 3,
   MG_OPT_HALO_ROWS = 4,
   MG_OPT_FCG_PRECOND = 5,
-  MG_OPT_FGMRES_FLOOR = 6
+  MG_OPT_FGMRES_FLOOR = 6,
+  MG_OPT_SELL_HALO_ROWS = 7
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

@@ -21,6 +21,7 @@
 #include "adjoint.cuh"
 #include "gmres.cuh"
 #include "halo.cuh"
+#include "halo_sell.cuh"
 #include "kernels.cuh"
 #include "krylov.cuh"
 #include "multi_rhs.cuh"
@@ -70,6 +71,14 @@ struct DevLevel {
   T *val = nullptr, *diag = nullptr, *dinv = nullptr, *invdeg = nullptr, *p_w = nullptr,
     *r_w = nullptr, *dval = nullptr;
   T *u = nullptr, *f = nullptr, *t = nullptr, *u2 = nullptr;  // workspace [n][maxB]
+  // SELL levels: halo tables of the fused steps (halo_sell.cuh) for tiles of
+  // hs_tr rows (0: none), and the host copy of the SELL pattern they are
+  // rebuilt from when the tile size changes
+  int hs_tr = 0, hs_hmax = 0;
+  int *hs_ptr = nullptr, *hs_row = nullptr;
+  int16_t* hs_lcol = nullptr;
+  std::vector<int> h_slptr, h_col;
+  mgk::SellHalo halo() const { return mgk::SellHalo{hs_tr, hs_ptr, hs_row, hs_lcol}; }
   LV<T> view() const {
     LV<T> v;
     v.n = n;
@@ -94,8 +103,9 @@ struct DevLevel {
 
 template <class T>
 void free_level(DevLevel<T>& L) {
-  void* ptrs[] = {L.sl_ptr, L.col, L.p_idx, L.r_idx, L.val, L.diag, L.dinv, L.invdeg,
-                  L.p_w,    L.r_w, L.u,     L.f,     L.t,   L.u2,  L.dval};
+  void* ptrs[] = {L.sl_ptr, L.col, L.p_idx, L.r_idx, L.val,  L.diag,   L.dinv,  L.invdeg, L.p_w,
+                  L.r_w,    L.u,   L.f,     L.t,     L.u2,   L.dval,   L.hs_ptr, L.hs_row,
+                  L.hs_lcol};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = DevLevel<T>();
@@ -220,6 +230,47 @@ std::string pack_level(const mg_csr& A, const double* invdeg, const mg_csr* P, H
   return "";
 }
 
+// Halo tables of a SELL level for tiles of TR rows (halo_sell.cuh): per tile
+// the ascending list of outside rows that neighbour a tile row, and per SELL
+// entry of a tile row the local slot of its column.  Returns false when a
+// tile's slots would not fit int16 (the kernel then is not used).
+bool build_sell_halo(int n, const std::vector<int>& sl_ptr, const std::vector<int>& col, int TR,
+                     std::vector<int>& hptr, std::vector<int>& hrow, std::vector<int16_t>& lcol,
+                     int& hmax) {
+  const int ntiles = (n + TR - 1) / TR;
+  hptr.assign(1, 0);
+  hrow.clear();
+  lcol.assign(col.size(), (int16_t)-1);
+  hmax = 0;
+  std::vector<int> ext;
+  for (int t = 0; t < ntiles; ++t) {
+    const int r0 = t * TR, r1 = std::min(n, r0 + TR);
+    ext.clear();
+    for (int i = r0; i < r1; ++i)
+      for (int e = sl_ptr[i >> 5] + (i & 31); e < sl_ptr[(i >> 5) + 1]; e += mgk::kSlice) {
+        const int c = col[e];
+        if (c >= 0 && (c < r0 || c >= r1)) ext.push_back(c);
+      }
+    std::sort(ext.begin(), ext.end());
+    ext.erase(std::unique(ext.begin(), ext.end()), ext.end());
+    if ((r1 - r0) + (int64_t)ext.size() > 32767) return false;
+    for (int i = r0; i < r1; ++i)
+      for (int e = sl_ptr[i >> 5] + (i & 31); e < sl_ptr[(i >> 5) + 1]; e += mgk::kSlice) {
+        const int c = col[e];
+        if (c < 0) continue;
+        const int slot = (c >= r0 && c < r1)
+                             ? c - r0
+                             : (r1 - r0) + (int)(std::lower_bound(ext.begin(), ext.end(), c) -
+                                                 ext.begin());
+        lcol[e] = (int16_t)slot;
+      }
+    hrow.insert(hrow.end(), ext.begin(), ext.end());
+    hptr.push_back((int)hrow.size());
+    hmax = std::max(hmax, (int)ext.size());
+  }
+  return true;
+}
+
 // Dense FP64 Cholesky A = L L^T (column-major L).  Returns false if A is not
 // numerically SPD.
 bool cholesky(const mg_csr& A, std::vector<double>& Lc) {
@@ -306,6 +357,7 @@ struct mg_ctx {
   int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
   int opt_fgmres_floor = 4;      // FP32 FGMRES cycle floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
+  int opt_sell_halo_rows = 256;  // rows per tile of the halo-fused SELL steps (0: unfused)
   int64_t wave_threads = 148 * 2048;  // SMs x resident threads per SM (set in mg_setup)
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
@@ -381,6 +433,35 @@ cudaError_t upload_level(const HostLevel& H, DevLevel<T>& D, int maxB, bool vect
   return cudaSuccess;
 }
 
+// (Re)builds the SELL halo tables of levels 0..J-2 for tiles of TR rows (0:
+// frees them).  Levels stored as DIA, levels without workspace vectors (the
+// FP64 finest copy of an FP32 context) and levels whose tiles do not fit the
+// kernel's int16 slots keep the two-kernel form.  The caller makes sure no
+// work that reads the old tables is in flight.
+template <class T>
+cudaError_t upload_sell_halo(std::vector<DevLevel<T>>& Ls, int TR, int J) {
+  for (int l = 0; l < J - 1 && l < (int)Ls.size(); ++l) {
+    DevLevel<T>& D = Ls[l];
+    for (void* p : {(void*)D.hs_ptr, (void*)D.hs_row, (void*)D.hs_lcol})
+      if (p) cudaFree(p);
+    D.hs_ptr = D.hs_row = nullptr;
+    D.hs_lcol = nullptr;
+    D.hs_tr = D.hs_hmax = 0;
+    if (TR <= 0 || D.ndia > 0 || D.h_col.empty() || !D.u) continue;
+    std::vector<int> hptr, hrow;
+    std::vector<int16_t> lcol;
+    int hmax = 0;
+    if (!build_sell_halo(D.n, D.h_slptr, D.h_col, TR, hptr, hrow, lcol, hmax)) continue;
+    cudaError_t e;
+    if ((e = upload(&D.hs_ptr, hptr)) != cudaSuccess) return e;
+    if ((e = upload(&D.hs_row, hrow)) != cudaSuccess) return e;
+    if ((e = upload(&D.hs_lcol, lcol)) != cudaSuccess) return e;
+    D.hs_tr = TR;
+    D.hs_hmax = hmax;
+  }
+  return cudaSuccess;
+}
+
 uint32_t structure_of(const std::vector<double>& prm, int J) {
   uint32_t s = 0;
   for (int l = 0; l < J - 1 && l < 10; ++l) {
@@ -425,6 +506,8 @@ inline dim3 grid_for(size_t work) { return dim3((unsigned)((work + kThreads - 1)
 constexpr size_t kTailSmemMax = 200 * 1024;
 // Shared memory of a halo-fused block (default limit, no opt-in needed).
 constexpr size_t kHaloSmemMax = 48 * 1024;
+// Shared memory of a SELL halo tile (opted in at set-up for every instance).
+constexpr size_t kSellHaloSmemMax = 160 * 1024;
 
 // Issues the kernels of one V-cycle (or one level step) on a stream.
 template <class T>
@@ -641,6 +724,29 @@ struct Issue {
     threads = (int)std::min<int64_t>(mgk::kTailThreads, (span * B + 31) / 32 * 32);
     return (int)tr;
   }
+  // Halo-tiled fused steps on a SELL level (halo_sell.cuh): the tile's
+  // shared bytes, or 0 (two-kernel form) when the level has no halo tables
+  // or the tile does not fit kSellHaloSmemMax for B right-hand sides.
+  size_t sell_halo(int lev) const {
+    const DevLevel<T>& D = L[lev];
+    if (D.ndia > 0 || D.hs_tr <= 0 || !D.hs_ptr) return 0;
+    const size_t smem = (size_t)(D.hs_tr + D.hs_hmax) * B * sizeof(T);
+    return smem <= kSellHaloSmemMax ? smem : 0;
+  }
+  template <int MODE>
+  void op_halo_sell(int lev, size_t smem, const T* f, const T* x, T* y, int zero) {
+    DevLevel<T>& D = L[lev];
+    const dim3 grid((unsigned)((D.n + D.hs_tr - 1) / D.hs_tr));
+    if (const int bv = mbv()) {
+      with_bv(bv, [&](auto k) {
+        launch(mgk::k_halo_sell<T, decltype(k)::value, MODE>, grid, kThreads, smem, D.view(),
+               D.halo(), f, x, y, B, P(lev), zero);
+      });
+    } else {
+      launch(mgk::k_halo_sell<T, 1, MODE>, grid, kThreads, smem, D.view(), D.halo(), f, x, y, B,
+             P(lev), zero);
+    }
+  }
   template <int MODE>
   void op_halo(int lev, int TR, int H, size_t smem, int threads, const T* f, const T* x, T* y,
                int zero) {
@@ -703,6 +809,18 @@ struct Issue {
       if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
       return;
     }
+    if (const size_t hsm = sell_halo(lev)) {  // SELL: one fused kernel per step
+      T* cur = u;
+      T* oth = D.u2;
+      for (int k = 0; k < nu; ++k) {
+        pre(MG_K_SMOOTH_HALO, lev);
+        op_halo_sell<mgk::HALO_SMOOTH>(lev, hsm, f, cur, oth, (int)(zero && k == 0));
+        post();
+        std::swap(cur, oth);
+      }
+      if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
+      return;
+    }
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       pre(MG_K_RESIDUAL_SCALED, lev);
@@ -727,6 +845,17 @@ struct Issue {
       op_gather(lev, D.u2, Fl(lev + 1), 0);
       post();
       return;
+    }
+    if (conv(lev, mgk::P_WR2)) {
+      if (const size_t hsm = sell_halo(lev)) {  // SELL: r and Phi_R(r) in one kernel
+        pre(MG_K_RESTRICT_HALO, lev);
+        op_halo_sell<mgk::HALO_RESTRICT>(lev, hsm, f, u, D.u2, 0);
+        post();
+        pre(MG_K_RESTRICT, lev);
+        op_gather(lev, D.u2, Fl(lev + 1), 0);
+        post();
+        return;
+      }
     }
     pre(MG_K_RESIDUAL, lev);
     op_residual(lev, f, u, D.t, 0, 0);
@@ -755,6 +884,14 @@ struct Issue {
       op_halo<mgk::HALO_PROLONG>(lev, TR, H, smem, nth, (const T*)nullptr, ec, u, 0);
       post();
       return;
+    }
+    if (conv(lev, mgk::P_WP2)) {
+      if (const size_t hsm = sell_halo(lev)) {  // SELL: P e_c, Phi_P and the update
+        pre(MG_K_PROLONG_HALO, lev);
+        op_halo_sell<mgk::HALO_PROLONG>(lev, hsm, (const T*)nullptr, ec, u, 0);
+        post();
+        return;
+      }
     }
     if (conv(lev, mgk::P_WP2)) {  // P e_c per fine row, then Phi_P and the update
       pre(MG_K_PE, lev);
@@ -1149,6 +1286,36 @@ extern "C" void mg_destroy(mg_ctx* c) {
   delete c;
 }
 
+// Opts every SELL halo kernel instance in to kSellHaloSmemMax bytes of
+// dynamic shared memory.
+template <class T, int MODE>
+static cudaError_t sell_halo_attrs_mode() {
+  const int bytes = (int)kSellHaloSmemMax;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(mgk::k_halo_sell<T, 1, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(mgk::k_halo_sell<T, 2, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(mgk::k_halo_sell<T, 4, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(mgk::k_halo_sell<T, 8, MODE>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)) != cudaSuccess)
+    return e;
+  return cudaFuncSetAttribute(mgk::k_halo_sell<T, 16, MODE>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <class T>
+static cudaError_t sell_halo_attrs() {
+  cudaError_t e;
+  if ((e = sell_halo_attrs_mode<T, mgk::HALO_SMOOTH>()) != cudaSuccess) return e;
+  if ((e = sell_halo_attrs_mode<T, mgk::HALO_RESTRICT>()) != cudaSuccess) return e;
+  return sell_halo_attrs_mode<T, mgk::HALO_PROLONG>();
+}
+
 static mg_status validate_hierarchy(const mg_hierarchy* h, const mg_csr* A, int32_t maxB,
                                     int32_t precision, std::string& why) {
   if (!h || !A) { why = "hierarchy or A_levels is NULL"; return MG_ERR_INVALID; }
@@ -1271,15 +1438,29 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)) !=
       cudaSuccess)
     return bail(e);
+  if ((e = sell_halo_attrs<float>()) != cudaSuccess) return bail(e);
+  if ((e = sell_halo_attrs<double>()) != cudaSuccess) return bail(e);
+  // host copies of the SELL patterns the halo tables are built from
+  auto keep_pattern = [&](auto& levels) {
+    for (int l = 0; l < J - 1; ++l)
+      if (H[l].ndia == 0) {
+        levels[l].h_slptr = H[l].sl_ptr;
+        levels[l].h_col = H[l].col;
+      }
+  };
   if (precision == 64) {
     c->d64.resize(J);
     for (int l = 0; l < J; ++l)
       if ((e = upload_level(H[l], c->d64[l], maxB, true)) != cudaSuccess) return bail(e);
+    keep_pattern(c->d64);
+    if ((e = upload_sell_halo(c->d64, c->opt_sell_halo_rows, J)) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&c->prm64, c->prm.size() * sizeof(double))) != cudaSuccess) return bail(e);
   } else {
     c->d32.resize(J);
     for (int l = 0; l < J; ++l)
       if ((e = upload_level(H[l], c->d32[l], maxB, true)) != cudaSuccess) return bail(e);
+    keep_pattern(c->d32);
+    if ((e = upload_sell_halo(c->d32, c->opt_sell_halo_rows, J)) != cudaSuccess) return bail(e);
     c->d64.resize(1);  // FP64 finest operator for the refinement residual
     HostLevel H0 = H[0];
     H0.p_idx.clear(); H0.p_w.clear(); H0.r_idx.clear(); H0.r_w.clear(); H0.nc = 0; H0.KR = 0;
@@ -1753,6 +1934,18 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
         return c->fail(MG_ERR_INVALID, "mg_set_option: halo rows must be in [0, 2^30]");
       c->opt_halo_rows = value;
       break;
+    case MG_OPT_SELL_HALO_ROWS: {
+      if (value < 0 || value > 8192 || value % mgk::kSlice != 0)
+        return c->fail(MG_ERR_INVALID,
+                       "mg_set_option: SELL halo rows must be 0 or a multiple of 32 up to 8192");
+      if (value == c->opt_sell_halo_rows) return MG_OK;
+      // work in flight may read the old tables
+      MG_CUDA(cudaDeviceSynchronize());
+      c->opt_sell_halo_rows = (int)value;
+      MG_CUDA(c->prec == 64 ? upload_sell_halo(c->d64, (int)value, c->J)
+                            : upload_sell_halo(c->d32, (int)value, c->J));
+      break;
+    }
     default:
       return c->fail(MG_ERR_INVALID, "mg_set_option: unknown option");
   }

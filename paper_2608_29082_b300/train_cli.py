@@ -46,6 +46,8 @@ def make(workload: str, batch: int, seed: int):
         return W.training_square("checker", batch=batch, seed=seed)
     if workload == "train257_poisson":
         return W.training_square("poisson", batch=batch, seed=seed)
+    if workload == "lshape7":  # the anisotropic L-shape, 7 red refinements (3141633 DOF)
+        return W.lshape_anisotropic(refinements=7, batch=batch, seed=seed)
     if workload.startswith("lognormal"):  # lognormal513, lognormal1025 (serving classes)
         return W.lognormal_square(int(workload[len("lognormal"):]), seed=seed, batch=batch)
     raise ValueError(workload)

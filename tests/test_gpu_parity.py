@@ -617,3 +617,70 @@ def test_fgmres_fp32_floor(floor):
         with pytest.raises(MGError):
             S.set_option("fgmres_floor", bad)
     S.close()
+
+
+# ------------------------------------------------- SELL halo-tiled steps --
+
+CASES["lshape_r3"] = lambda: W.lshape_anisotropic(refinements=3, batch=2, seed=4)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("conv", [False, True])
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_sell_halo_tiles_are_bitwise_neutral(prec, conv, nrhs):
+    """On SELL levels (the jittered L-shape) the halo-tiled fused steps
+    (one kernel per smoothing step, residual + Phi_R, P e_c + Phi_P) give
+    bitwise the two-kernel cycle and solve, for every tile size (tiles
+    smaller than a halo, a ragged last tile, one tile for a whole level)
+    and right-hand-side tile width (16 rhs: 8 per thread; 3: one)."""
+    for name in ("lshape_r2", "lshape_r3"):
+        p, Ho, Hp = problem(name)
+        prm = rand_params(Hp.J, 73, 0.1, conv=conv)
+        dt = torch.float64 if prec == 64 else torch.float32
+        f = np.random.default_rng(nrhs).standard_normal((Hp.sizes[0], nrhs))
+        outs = []
+        for rows in (0, 32, 96, 256, 1024, 8192):
+            S = Solver(Hp, prm, precision=prec, max_batch=nrhs)
+            S.set_option("sell_halo_rows", rows)
+            S.set_option("tail_work", 0)  # every level a grid level
+            u = torch.zeros((Hp.sizes[0], nrhs), dtype=dt, device=DEV)
+            fd = torch.tensor(f, dtype=dt, device=DEV)
+            S.vcycle(fd, u)
+            S.vcycle(fd, u)
+            us, info = S.solve(t64(f), tol=1e-9, max_iter=100, method="fcg")
+            outs.append((u.clone(), us.clone(), info.iters.copy()))
+            S.close()
+        assert torch.isfinite(outs[0][0]).all()
+        for u, us, it in outs[1:]:
+            assert torch.equal(u, outs[0][0]), name
+            assert torch.equal(us, outs[0][1]), name
+            assert np.array_equal(it, outs[0][2]), name
+
+
+def test_sell_halo_cycle_matches_oracle_and_steps():
+    """The fused SELL path against the oracle directly: single FP64 smoothing
+    steps (1e-13) and cycles (1e-12) on the L-shape, and the option is
+    validated."""
+    p, Ho, Hp = problem("lshape_r3")
+    prm = rand_params(Hp.J, 79, 0.2)
+    po = to_oracle(prm)
+    S = Solver(Hp, prm, precision=64, max_batch=2)
+    S.set_option("sell_halo_rows", 64)
+    r = np.random.default_rng(3)
+    for lev in range(Hp.J - 1):
+        n = Hp.sizes[lev]
+        f, u = r.standard_normal((n, 2)), r.standard_normal((n, 2))
+        out = torch.empty((n, 2), dtype=torch.float64, device=DEV)
+        S.level_apply(lev, "smooth", t64(f), t64(u), out)
+        ref = O.smooth(Ho.levels[lev], f, u, po.theta[lev], po.eta[lev], po.wB[lev])
+        assert rel(out.cpu().numpy(), ref) < 1e-13, lev
+    ug = torch.zeros((Hp.sizes[0], 2), dtype=torch.float64, device=DEV)
+    uo = np.zeros_like(p.f)
+    for m in range(4):
+        S.vcycle(t64(p.f), ug)
+        uo = O.vcycle(Ho, po, p.f, uo)
+        assert rel(ug.cpu().numpy(), uo) < 1e-12, m
+    for bad in (-32, 33, 8224):
+        with pytest.raises(MGError):
+            S.set_option("sell_halo_rows", bad)
+    S.close()
