@@ -318,7 +318,7 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     one wave of the GPU; otherwise the two-kernel form.
  *                     Other values than [0, 2^30]: MG_ERR_INVALID.
  *   MG_OPT_SELL_HALO_ROWS rows per tile of the halo-fused steps on SELL
- *                     levels (default 256; 0: unfused; a multiple of 32 up
+ *                     levels (default 0: unfused; else a multiple of 32 up
  *                     to 8192, else MG_ERR_INVALID).  At set-up (and when
  *                     this value changes) the host lists, per tile of
  *                     consecutive rows, the outside rows that neighbour it
@@ -329,6 +329,11 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     the first stage never written to device memory.  Used
  *                     on a level while (rows + halo) * nrhs values fit
  *                     160 KB.  Changing it synchronises the device.
+ *   MG_OPT_SELL_HALO_THREADS threads per block of those steps (default 256;
+ *                     a multiple of 32 up to 1024, else MG_ERR_INVALID)
+ *   MG_OPT_SELL_HALO_MAX_BYTES the smoothing and restriction steps of a SELL
+ *                     level use the halo form only while rows * nrhs * value
+ *                     bytes is at most this (the prolongation: always); >= 0
  *   MG_OPT_FCG_PRECOND preconditioner of mg_solve_fcg and mg_solve_fgmres:
  *                     0 (default) one V-cycle from zero, 1 one full
  *                     multigrid (mg_fmg).
@@ -339,8 +344,17 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     contexts ignore it.  An FP32 cycle resolves about
  *                     1e-4..1e-7 of its start (CGS2 and K z in FP32);
  *                     a lower floor spends steps below that.
- * MG_OPT_FCG_PRECOND and MG_OPT_FGMRES_FLOOR change results (another
- * preconditioner, other restart points); the others only launch shapes. */
+ *   MG_OPT_COARSE_INVERSE coarsest-level solve: 1 (default) a dense product
+ *                     with the explicit FP64 inverse of A_J, one FP64 dot
+ *                     per (row, rhs) spread over SMs, where set-up formed it
+ *                     (32 <= n_{J-1} <= 512 and ||A_J||_1 ||A_J^{-1}||_1
+ *                     <= 1e6; otherwise, and with 0, the two Cholesky
+ *                     substitutions, whose 2 n_{J-1} dependent FP64 steps
+ *                     run on one SM per right-hand side).  Both forms agree
+ *                     to a few units of rounding times the condition number.
+ * MG_OPT_FCG_PRECOND, MG_OPT_FGMRES_FLOOR and MG_OPT_COARSE_INVERSE change
+ * results (another preconditioner, other restart points, other rounding of
+ * the coarsest solve); the others only launch shapes. */
 typedef enum {
   MG_OPT_TAIL_WORK = 0,
   MG_OPT_PDL = 1,
@@ -349,7 +363,10 @@ typedef enum {
   MG_OPT_HALO_ROWS = 4,
   MG_OPT_FCG_PRECOND = 5,
   MG_OPT_FGMRES_FLOOR = 6,
-  MG_OPT_SELL_HALO_ROWS = 7
+  MG_OPT_SELL_HALO_ROWS = 7,
+  MG_OPT_SELL_HALO_THREADS = 8,
+  MG_OPT_SELL_HALO_MAX_BYTES = 9,
+  MG_OPT_COARSE_INVERSE = 10
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

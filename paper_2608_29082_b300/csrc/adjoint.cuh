@@ -283,8 +283,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth_mb(LV<T> L, const T* __
     const size_t base = (size_t)i * B + b0;
     const T theta = prm[P_THETA], eta = prm[P_ETA], w1 = prm[P_WB1], w2 = prm[P_WB2];
     T ub[BV], rr[BV], mt[BV], sd[BV], rb[BV];
-    ldv<T, BV>(ubar, base, ub);
-    ldv<T, BV>(r, base, rr);
+    ldg<T, BV>(ubar, base, ub);
+    ldg<T, BV>(r, base, rr);
 #pragma unroll
     for (int b = 0; b < BV; ++b) mt[b] = sd[b] = T(0);
     // M^T ubar and sum_{N(i)} dinv_j r_j, each accumulated in row_mt's and
@@ -293,8 +293,8 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth_mb(LV<T> L, const T* __
       const T wm = nb ? L.invdeg[c] : T(0);
       const T wd = nb ? L.dinv[c] : T(0);
       T uc[BV], rc[BV];
-      ldv<T, BV>(ubar, (size_t)c * B + b0, uc);
-      ldv<T, BV>(r, (size_t)c * B + b0, rc);
+      ldg<T, BV>(ubar, (size_t)c * B + b0, uc);
+      ldg<T, BV>(r, (size_t)c * B + b0, rc);
 #pragma unroll
       for (int b = 0; b < BV; ++b) {
         mt[b] = fma(wm, uc[b], mt[b]);
@@ -316,7 +316,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth_mb(LV<T> L, const T* __
       v[2] += eta * (ub[b] * mdelta);
       v[3] += deltab * dr;
     }
-    stv<T, BV>(rbar, base, rb);
+    stg<T, BV>(rbar, base, rb);
   }
   block_dots<4>(v, partial);
 }
@@ -334,26 +334,26 @@ __global__ void __launch_bounds__(kThreads) k_adj_apply_a_mb(LV<T> L, T* __restr
   const int b0 = (g - i * nq) * BV;
   const size_t base = (size_t)i * B + b0;
   T rb[BV];
-  ldv<T, BV>(rbar, base, rb);
+  ldg<T, BV>(rbar, base, rb);
   if (ubar) {
     T ax[BV], ub[BV];
     row_ax_mb<T, BV>(L, i, rbar, B, b0, ax);
-    ldv<T, BV>(ubar, base, ub);
+    ldg<T, BV>(ubar, base, ub);
     const T d = L.diag[i];
 #pragma unroll
     for (int b = 0; b < BV; ++b) ub[b] = ub[b] - fma(d, rb[b], ax[b]);
-    stv<T, BV>(ubar, base, ub);
+    stg<T, BV>(ubar, base, ub);
   }
   T fb[BV];
   if (fbar_set) {
 #pragma unroll
     for (int b = 0; b < BV; ++b) fb[b] = rb[b];
   } else {
-    ldv<T, BV>(fbar, base, fb);
+    ldg<T, BV>(fbar, base, fb);
 #pragma unroll
     for (int b = 0; b < BV; ++b) fb[b] = fb[b] + rb[b];
   }
-  stv<T, BV>(fbar, base, fb);
+  stg<T, BV>(fbar, base, fb);
 }
 
 }  // namespace mgk

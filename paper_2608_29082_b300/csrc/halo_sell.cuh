@@ -30,8 +30,9 @@
 //   HALO_PROLONG   z = P x                            (x = e_c)
 //                  y = y + wP1 z + wP2 mean z         (y = u, in place per row)
 //
-// Launch: one block of kThreads threads per tile; a thread takes items
-// (slot, tile of BV right-hand sides) in turn.  Dynamic shared memory
+// Launch: one block per tile, of at most kTailThreads threads (a launch-shape
+// choice: results do not depend on it); a thread takes items (slot, tile of
+// BV right-hand sides) in turn.  Dynamic shared memory
 // (TR + max halo) * B * sizeof(T).
 #pragma once
 
@@ -50,7 +51,7 @@ struct SellHalo {
 };
 
 template <class T, int BV, int MODE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kTailThreads)
     k_halo_sell(LV<T> L, SellHalo hs, const T* __restrict__ f, const T* __restrict__ x, T* y,
                 int B, const T* __restrict__ prm, int zero) {
   extern __shared__ __align__(16) unsigned char halo_raw[];
@@ -81,11 +82,11 @@ __global__ void __launch_bounds__(kThreads)
     if constexpr (MODE == HALO_PROLONG) {
       prolong_at_mb<T, BV>(L, j, x, B, b0, z);
     } else {
-      ldv<T, BV>(f, base, z);
+      ldg<T, BV>(f, base, z);
       if (!zero) {
         T ax[BV], uu[BV];
         row_ax_mb<T, BV>(L, j, x, B, b0, ax);
-        ldv<T, BV>(x, base, uu);
+        ldg<T, BV>(x, base, uu);
         const T d = L.diag[j];
 #pragma unroll
         for (int b = 0; b < BV; ++b) z[b] = fma(-d, uu[b], z[b]) - ax[b];
@@ -128,7 +129,7 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
         for (int b = 0; b < BV; ++b) uu[b] = T(0);
       } else {
-        ldv<T, BV>(x, base, uu);
+        ldg<T, BV>(x, base, uu);
       }
       const T w1 = prm[P_WB1], w2 = prm[P_WB2], eta = prm[P_ETA];
 #pragma unroll
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kThreads)
         const T phi = fma(w1, zi[b], w2 * (id * s[b]));
         uu[b] = fma(eta, phi, uu[b]);
       }
-      stv<T, BV>(y, base, uu);
+      stg<T, BV>(y, base, uu);
     } else if constexpr (MODE == HALO_RESTRICT) {
       const T w1 = prm[P_WR1], w2 = prm[P_WR2];
 #pragma unroll
@@ -144,17 +145,17 @@ __global__ void __launch_bounds__(kThreads)
         const T p = w1 * zi[b];
         zi[b] = fma(w2, id * s[b], p);
       }
-      stv<T, BV>(y, base, zi);
+      stg<T, BV>(y, base, zi);
     } else {
       T uu[BV];
-      ldv<T, BV>(y, base, uu);
+      ldg<T, BV>(y, base, uu);
       const T w1 = prm[P_WP1], w2 = prm[P_WP2];
 #pragma unroll
       for (int b = 0; b < BV; ++b) {
         const T p = w1 * zi[b];
         uu[b] = uu[b] + fma(w2, id * s[b], p);
       }
-      stv<T, BV>(y, base, uu);
+      stg<T, BV>(y, base, uu);
     }
   }
 }

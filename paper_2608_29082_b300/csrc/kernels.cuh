@@ -585,6 +585,7 @@ struct TailArgs {
   const double* cL;
   const double* cU;
   const double* cDinv;
+  const double* cInv;  // explicit inverse of A_J (row-major), or NULL: substitutions
 };
 
 // Vectors of the small levels: in shared memory when a.smem_vectors (the
@@ -671,10 +672,42 @@ __device__ __forceinline__ size_t packed_col(int n, int j) {
   return (size_t)j * n - (size_t)j * (j - 1) / 2;
 }
 
+// u = A_J^{-1} f with the explicit FP64 inverse (row-major n x n, formed
+// on the host from the Cholesky factor): one thread per (row, rhs) output,
+// the products summed in column order.  Every output is independent, so the
+// step spreads over many SMs instead of running the 2n dependent steps of
+// the substitutions on one (B300's FP64 pipe makes those slow).
+template <class T>
+__device__ __forceinline__ void coarse_inv_el(const double* __restrict__ Ainv, int n,
+                                              const T* __restrict__ f, T* __restrict__ u, int B,
+                                              size_t t) {
+  int i, b;
+  split_rb(t, B, i, b);
+  const double* row = Ainv + (size_t)i * n;
+  double acc = 0.0;
+#pragma unroll 8
+  for (int j = 0; j < n; ++j) acc = fma(row[j], (double)f[(size_t)j * B + b], acc);
+  u[t] = (T)acc;
+}
+
+constexpr int kCoarseInvThreads = 64;
+
+template <class T>
+__global__ void __launch_bounds__(kCoarseInvThreads)
+    k_coarse_inv(const double* __restrict__ Ainv, int n, const T* __restrict__ f,
+                 T* __restrict__ u, int B) {
+  pdl_wait();
+  pdl_launch();
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < (size_t)n * B) coarse_inv_el(Ainv, n, f, u, B, t);
+}
+
 // The same substitutions as coarse_chol_block with the factor staged in
 // shared memory as a packed lower triangle (column j holds rows j..n-1):
 // every step reads the factor at shared-memory latency.  Same values and
-// order, hence the same results.
+// order, hence the same results.  Warp w of block k takes right-hand sides
+// k * nw + w, + nw * gridDim.x, ...: a grid of several blocks spreads the
+// right-hand sides over SMs, whose FP64 pipes bound the substitutions.
 template <class T>
 __global__ void k_coarse_chol_packed(const double* __restrict__ Lp, const double* __restrict__ dinv,
                                      int n, const T* __restrict__ f, T* __restrict__ u, int B) {
@@ -689,7 +722,7 @@ __global__ void k_coarse_chol_packed(const double* __restrict__ Lp, const double
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   double* y = ys + (size_t)warp * n;
-  for (int b = warp; b < B; b += nw) {
+  for (int b = blockIdx.x * nw + warp; b < B; b += nw * gridDim.x) {
     for (int i = lane; i < n; i += 32) y[i] = (double)f[(size_t)i * B + b];
     __syncwarp();
     for (int j = 0; j < n; ++j) {  // L y = f
@@ -838,8 +871,13 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     }
     __syncthreads();
   }
-  coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, a.cwarps,
-                    ys);
+  if (a.cInv) {
+    for (size_t t = threadIdx.x; t < (size_t)a.nJ * a.B; t += blockDim.x)
+      coarse_inv_el(a.cInv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
+  } else {
+    coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, a.cwarps,
+                      ys);
+  }
   __syncthreads();
   for (int l = J - 2; l >= lt; --l) {
     const LV<T>& L = sL[l];

@@ -5,6 +5,7 @@
 // batch) into a CUDA graph and replayed; parameters live in device memory so
 // that changing Theta (training) does not invalidate the graphs.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -294,6 +295,45 @@ bool cholesky(const mg_csr& A, std::vector<double>& Lc) {
   return true;
 }
 
+// Explicit inverse of the coarsest operator from its Cholesky factor
+// (column-major L): A^{-1} e_k by the two substitutions for every k, then
+// symmetrised; row-major.  Empty when the 1-norm condition number
+// ||A||_1 ||A^{-1}||_1 exceeds 1e6 (the substitutions are kept there: an
+// explicit inverse loses about cond(A) units of rounding).
+std::vector<double> coarse_inverse(const mg_csr& A, const std::vector<double>& Lc, int n) {
+  std::vector<double> X((size_t)n * n, 0.0), y(n);
+  for (int k = 0; k < n; ++k) {
+    std::fill(y.begin(), y.end(), 0.0);
+    y[k] = 1.0;
+    for (int j = 0; j < n; ++j) {  // L y = e_k
+      y[j] /= Lc[j + (size_t)j * n];
+      for (int i = j + 1; i < n; ++i) y[i] -= Lc[i + (size_t)j * n] * y[j];
+    }
+    for (int j = n - 1; j >= 0; --j) {  // L^T x = y
+      y[j] /= Lc[j + (size_t)j * n];
+      for (int i = 0; i < j; ++i) y[i] -= Lc[j + (size_t)i * n] * y[j];
+    }
+    for (int i = 0; i < n; ++i) X[(size_t)i * n + k] = y[i];
+  }
+  double an = 0.0, in = 0.0;
+  std::vector<double> colsum(n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = A.rowptr[i]; k < A.rowptr[i + 1]; ++k) colsum[A.col[k]] += std::fabs(A.val[k]);
+  for (double v : colsum) an = std::max(an, v);
+  for (int k = 0; k < n; ++k) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += std::fabs(X[(size_t)i * n + k]);
+    in = std::max(in, s);
+  }
+  if (!(an * in <= 1e6)) return {};
+  for (int i = 0; i < n; ++i)
+    for (int k = i + 1; k < n; ++k) {
+      const double m = 0.5 * (X[(size_t)i * n + k] + X[(size_t)k * n + i]);
+      X[(size_t)i * n + k] = X[(size_t)k * n + i] = m;
+    }
+  return X;
+}
+
 struct GraphEntry {
   cudaGraphExec_t exec = nullptr;
   int nkernels = 0;  // kernels per launch (outside any loop body)
@@ -311,6 +351,10 @@ struct mg_ctx {
   std::vector<DevLevel<float>> d32;
   double *cholL = nullptr, *cholU = nullptr, *cholDinv = nullptr;
   double* cholP = nullptr;  // packed column-major lower triangle of the factor
+  // explicit inverse of A_J (row-major), formed at set-up when the coarsest
+  // level is 32..512 rows and well conditioned; used when coarse_inv is set
+  double* cholInv = nullptr;
+  bool coarse_inv = false;
   // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
   double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
   double *k_partial = nullptr, *k_small = nullptr;
@@ -357,7 +401,11 @@ struct mg_ctx {
   int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
   int opt_fgmres_floor = 4;      // FP32 FGMRES cycle floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
-  int opt_sell_halo_rows = 256;  // rows per tile of the halo-fused SELL steps (0: unfused)
+  int opt_sell_halo_rows = 0;  // rows per tile of the halo-fused SELL steps (0: unfused)
+  int opt_sell_halo_threads = 256;  // threads per block of those steps
+  // largest level vector (rows x rhs x value bytes) whose smoothing and
+  // restriction steps use the SELL halo form (prolongation: every level)
+  int64_t opt_sell_halo_max_bytes = INT64_MAX;
   int64_t wave_threads = 148 * 2048;  // SMs x resident threads per SM (set in mg_setup)
   // training state (device buffers in the context precision)
   int64_t param_version = 0, rec_version = -1;
@@ -727,9 +775,10 @@ struct Issue {
   // Halo-tiled fused steps on a SELL level (halo_sell.cuh): the tile's
   // shared bytes, or 0 (two-kernel form) when the level has no halo tables
   // or the tile does not fit kSellHaloSmemMax for B right-hand sides.
-  size_t sell_halo(int lev) const {
+  size_t sell_halo(int lev, bool size_cap = true) const {
     const DevLevel<T>& D = L[lev];
     if (D.ndia > 0 || D.hs_tr <= 0 || !D.hs_ptr) return 0;
+    if (size_cap && (int64_t)D.n * B * (int64_t)sizeof(T) > c->opt_sell_halo_max_bytes) return 0;
     const size_t smem = (size_t)(D.hs_tr + D.hs_hmax) * B * sizeof(T);
     return smem <= kSellHaloSmemMax ? smem : 0;
   }
@@ -739,12 +788,13 @@ struct Issue {
     const dim3 grid((unsigned)((D.n + D.hs_tr - 1) / D.hs_tr));
     if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
-        launch(mgk::k_halo_sell<T, decltype(k)::value, MODE>, grid, kThreads, smem, D.view(),
-               D.halo(), f, x, y, B, P(lev), zero);
+        launch(mgk::k_halo_sell<T, decltype(k)::value, MODE>, grid,
+               dim3(c->opt_sell_halo_threads), smem, D.view(), D.halo(), f, x, y, B, P(lev),
+               zero);
       });
     } else {
-      launch(mgk::k_halo_sell<T, 1, MODE>, grid, kThreads, smem, D.view(), D.halo(), f, x, y, B,
-             P(lev), zero);
+      launch(mgk::k_halo_sell<T, 1, MODE>, grid, dim3(c->opt_sell_halo_threads), smem, D.view(),
+             D.halo(), f, x, y, B, P(lev), zero);
     }
   }
   template <int MODE>
@@ -886,7 +936,7 @@ struct Issue {
       return;
     }
     if (conv(lev, mgk::P_WP2)) {
-      if (const size_t hsm = sell_halo(lev)) {  // SELL: P e_c, Phi_P and the update
+      if (const size_t hsm = sell_halo(lev, false)) {  // SELL: P e_c, Phi_P and the update
         pre(MG_K_PROLONG_HALO, lev);
         op_halo_sell<mgk::HALO_PROLONG>(lev, hsm, (const T*)nullptr, ec, u, 0);
         post();
@@ -913,13 +963,23 @@ struct Issue {
 
   void coarse(const T* f, T* u) {
     const size_t nJ = (size_t)c->nJ;
+    if (c->coarse_inv) {  // one FP64 dot per (row, rhs), spread over SMs
+      pre(MG_K_COARSE_CHOL, c->J - 1);
+      launch(mgk::k_coarse_inv<T>,
+             dim3((unsigned)((nJ * B + mgk::kCoarseInvThreads - 1) / mgk::kCoarseInvThreads)),
+             dim3(mgk::kCoarseInvThreads), 0, (const double*)c->cholInv, c->nJ, f, u, B);
+      post();
+      return;
+    }
     const size_t fixed = mgk::tail_align(nJ * (nJ + 1) / 2 * sizeof(double)) +
                          mgk::tail_align(nJ * sizeof(double));
-    const int nwp = std::max(1, std::min(B, 32));
+    // factor staged in shared memory as a packed triangle; past a few rows
+    // the FP64 substitutions of one SM bound the step, so each right-hand
+    // side gets a block (one warp) of its own on another SM
+    const int nwp = nJ >= 32 ? 1 : std::max(1, std::min(B, 32));
     if (fixed + (size_t)nwp * nJ * sizeof(double) <= kTailSmemMax) {
-      // factor staged in shared memory as a packed triangle
       pre(MG_K_COARSE_CHOL, c->J - 1);
-      launch(mgk::k_coarse_chol_packed<T>, dim3(1), dim3(32 * nwp),
+      launch(mgk::k_coarse_chol_packed<T>, dim3((unsigned)((B + nwp - 1) / nwp)), dim3(32 * nwp),
              fixed + (size_t)nwp * nJ * sizeof(double), (const double*)c->cholP,
              (const double*)c->cholDinv, c->nJ, f, u, B);
       post();
@@ -964,6 +1024,7 @@ struct Issue {
     a.cL = c->cholL;
     a.cU = c->cholU;
     a.cDinv = c->cholDinv;
+    a.cInv = c->coarse_inv ? c->cholInv : nullptr;
     // a recorded forward must leave every level's f and u in its checkpoint
     // buffers, so it keeps the small levels' vectors in global memory
     a.smem_vectors = fov == nullptr && uov == nullptr ? 1 : 0;
@@ -1268,7 +1329,7 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   for (auto& L : c->d64) free_level(L);
   for (auto& L : c->d32) free_level(L);
-  for (void* p : {(void*)c->cholP, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
+  for (void* p : {(void*)c->cholP, (void*)c->cholInv, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
                   (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
                   (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
                   (void*)c->gm_zero32, (void*)c->gm_done, c->cheb_dev})
@@ -1412,6 +1473,8 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   }
   const int nJ = A[J - 1].n_rows;
   c->nJ = nJ;
+  std::vector<double> Ainv;
+  if (nJ >= 32 && nJ <= 512) Ainv = coarse_inverse(A[J - 1], Lc, nJ);
   std::vector<double> Uc((size_t)nJ * nJ), dj(nJ);
   for (int i = 0; i < nJ; ++i)
     for (int j = 0; j < nJ; ++j) Uc[i + (size_t)j * nJ] = Lc[j + (size_t)i * nJ];
@@ -1470,6 +1533,10 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   if ((e = upload(&c->cholL, Lc)) != cudaSuccess) return bail(e);
   if ((e = upload(&c->cholU, Uc)) != cudaSuccess) return bail(e);
   if ((e = upload(&c->cholDinv, dj)) != cudaSuccess) return bail(e);
+  if (!Ainv.empty()) {
+    if ((e = upload(&c->cholInv, Ainv)) != cudaSuccess) return bail(e);
+    c->coarse_inv = true;
+  }
   {
     std::vector<double> Pk;
     Pk.reserve((size_t)nJ * (nJ + 1) / 2);
@@ -1933,6 +2000,21 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > (1 << 30))
         return c->fail(MG_ERR_INVALID, "mg_set_option: halo rows must be in [0, 2^30]");
       c->opt_halo_rows = value;
+      break;
+    case MG_OPT_COARSE_INVERSE:
+      if (value != 0 && value != 1)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: coarse inverse must be 0 or 1");
+      c->coarse_inv = value == 1 && c->cholInv != nullptr;
+      break;
+    case MG_OPT_SELL_HALO_MAX_BYTES:
+      if (value < 0) return c->fail(MG_ERR_INVALID, "mg_set_option: byte cap must be >= 0");
+      c->opt_sell_halo_max_bytes = value;
+      break;
+    case MG_OPT_SELL_HALO_THREADS:
+      if (value < 32 || value > mgk::kTailThreads || value % 32 != 0)
+        return c->fail(MG_ERR_INVALID,
+                       "mg_set_option: SELL halo threads must be a multiple of 32 up to 1024");
+      c->opt_sell_halo_threads = (int)value;
       break;
     case MG_OPT_SELL_HALO_ROWS: {
       if (value < 0 || value > 8192 || value % mgk::kSlice != 0)

@@ -50,6 +50,63 @@ __device__ __forceinline__ void stv(T* __restrict__ x, size_t off, const T (&in)
   }
 }
 
+// Global-memory forms of ldv / stv.  A thread's BV values are 32 bytes for
+// BV = 8 in FP32 (4 in FP64); one 256-bit access (ld/st.global.v8.b32)
+// moves them where the address is 32-byte aligned, so that the two threads
+// of a row fill whole 32-byte sectors with one request each, instead of two
+// 16-byte requests that each use half of every sector they touch (the
+// neighbour gathers of the level steps are bound by L1 sector throughput).
+// Other sizes and alignments take the 16-byte path.  The values are the
+// same either way.
+__device__ __forceinline__ void ld256(const void* p, uint32_t (&w)[8]) {
+  asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+        "=r"(w[7])
+      : "l"(p));
+}
+
+__device__ __forceinline__ void st256(void* p, const uint32_t (&w)[8]) {
+  asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
+               "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+               : "memory");
+}
+
+template <class T, int BV>
+__device__ __forceinline__ void ldg(const T* __restrict__ x, size_t off, T (&out)[BV]) {
+  constexpr int W32 = 32 / (int)sizeof(T);
+  if constexpr (BV % W32 == 0) {
+    const T* p = x + off;
+    if (__builtin_expect(((uintptr_t)p & 31) == 0, 1)) {
+#pragma unroll
+      for (int k = 0; k < BV / W32; ++k) {
+        uint32_t w[8];
+        ld256(p + k * W32, w);
+        memcpy(&out[k * W32], w, 32);
+      }
+      return;
+    }
+  }
+  ldv<T, BV>(x, off, out);
+}
+
+template <class T, int BV>
+__device__ __forceinline__ void stg(T* __restrict__ x, size_t off, const T (&in)[BV]) {
+  constexpr int W32 = 32 / (int)sizeof(T);
+  if constexpr (BV % W32 == 0) {
+    T* p = x + off;
+    if (((uintptr_t)p & 31) == 0) {
+#pragma unroll
+      for (int k = 0; k < BV / W32; ++k) {
+        uint32_t w[8];
+        memcpy(w, &in[k * W32], 32);
+        st256(p + k * W32, w);
+      }
+      return;
+    }
+  }
+  stv<T, BV>(x, off, in);
+}
+
 // Launch: 1-D grid of ceil(NROWS * (B / BV) / kThreads) blocks.  PF: the
 // row's read-only prefetch (kernels.cuh), before griddepcontrol.wait.
 #define MG_MB_PROLOGUE(NROWS, PF)                               \
@@ -72,7 +129,7 @@ __device__ __forceinline__ void row_ax_mb(const LV<T>& L, int i, const T* __rest
   for (int b = 0; b < BV; ++b) ax[b] = T(0);
   for_nb<T, true, true>(L, i, [&](int c, T v, bool) {
     T xv[BV];
-    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+    ldg<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
     for (int b = 0; b < BV; ++b) ax[b] = fma(v, xv[b], ax[b]);
   });
@@ -88,7 +145,7 @@ __device__ __forceinline__ void row_sum_mb(const LV<T>& L, int i, const T* __res
   for (int b = 0; b < BV; ++b) s[b] = T(0);
   for_nb<T, false, kPre>(L, i, [&](int c, T, bool nb) {
     T xv[BV];
-    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+    ldg<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
     for (int b = 0; b < BV; ++b) s[b] += nb ? xv[b] : T(0);
   });
@@ -102,11 +159,11 @@ __global__ void __launch_bounds__(kThreads) k_residual_mb(LV<T> L, const T* __re
                                                           int u_zero) {
   MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T r[BV];
-  ldv<T, BV>(f, base, r);
+  ldg<T, BV>(f, base, r);
   if (!u_zero) {
     T ax[BV], uu[BV];
     row_ax_mb<T, BV>(L, i, u, B, b0, ax);
-    ldv<T, BV>(u, base, uu);
+    ldg<T, BV>(u, base, uu);
     const T d = L.diag[i];
 #pragma unroll
     for (int b = 0; b < BV; ++b) r[b] = fma(-d, uu[b], r[b]) - ax[b];
@@ -116,23 +173,30 @@ __global__ void __launch_bounds__(kThreads) k_residual_mb(LV<T> L, const T* __re
 #pragma unroll
     for (int b = 0; b < BV; ++b) r[b] = th * (r[b] * di);
   }
-  stv<T, BV>(out, base, r);
+  stg<T, BV>(out, base, r);
 }
 
+// Resident blocks asked of the compiler for the mean-only step: it is
+// bound by the latency of its neighbour gathers, so tiles of up to 32
+// bytes a thread keep 7 blocks (36 registers) per SM.
 template <class T, int BV>
-__global__ void __launch_bounds__(kThreads) k_conv_update_mb(LV<T> L, const T* __restrict__ x,
+constexpr int kConvMinBlocks = BV * sizeof(T) <= 32 ? 7 : 1;
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads, kConvMinBlocks<T, BV>)
+    k_conv_update_mb(LV<T> L, const T* __restrict__ x,
                                                              T* __restrict__ u, int B,
                                                              const T* __restrict__ prm,
                                                              int u_zero) {
   MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T s[BV], xi[BV], uu[BV];
   row_sum_mb<T, BV>(L, i, x, B, b0, s);
-  ldv<T, BV>(x, base, xi);
+  ldg<T, BV>(x, base, xi);
   if (u_zero) {
 #pragma unroll
     for (int b = 0; b < BV; ++b) uu[b] = T(0);
   } else {
-    ldv<T, BV>(u, base, uu);
+    ldg<T, BV>(u, base, uu);
   }
   const T w1 = prm[P_WB1], w2 = prm[P_WB2], eta = prm[P_ETA], id = L.invdeg[i];
 #pragma unroll
@@ -140,7 +204,7 @@ __global__ void __launch_bounds__(kThreads) k_conv_update_mb(LV<T> L, const T* _
     const T phi = fma(w1, xi[b], w2 * (id * s[b]));
     uu[b] = fma(eta, phi, uu[b]);
   }
-  stv<T, BV>(u, base, uu);
+  stg<T, BV>(u, base, uu);
 }
 
 // k_cheb_step (kernels.cuh) for a tile of BV right-hand sides: the row's
@@ -155,12 +219,12 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __r
   MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T s[BV], q[BV], uu[BV];
   row_sum_mb<T, BV>(L, i, tprev, B, b0, s);
-  ldv<T, BV>(tpp, base, q);
+  ldg<T, BV>(tpp, base, q);
   if (u_zero) {
 #pragma unroll
     for (int b = 0; b < BV; ++b) uu[b] = T(0);
   } else {
-    ldv<T, BV>(u, base, uu);
+    ldg<T, BV>(u, base, uu);
   }
   const T id = L.invdeg[i], eta = prm[P_ETA], c0 = coef[0], ck = coef[k];
 #pragma unroll
@@ -177,8 +241,8 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __r
     q[b] = tk;
     uu[b] = fma(eta, upd, uu[b]);
   }
-  stv<T, BV>(out, base, q);
-  stv<T, BV>(u, base, uu);
+  stg<T, BV>(out, base, q);
+  stg<T, BV>(u, base, uu);
 }
 
 template <class T, int BV>
@@ -188,13 +252,13 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __rest
                                                         const T* __restrict__ prm, int u_zero) {
   MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T r[BV], u0[BV];
-  ldv<T, BV>(f, base, r);
+  ldg<T, BV>(f, base, r);
   if (u_zero) {
 #pragma unroll
     for (int b = 0; b < BV; ++b) u0[b] = T(0);
   } else {
     T ax[BV];
-    ldv<T, BV>(uin, base, u0);
+    ldg<T, BV>(uin, base, u0);
     row_ax_mb<T, BV>(L, i, uin, B, b0, ax);
     const T d = L.diag[i];
 #pragma unroll
@@ -206,7 +270,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __rest
     const T delta = th * (r[b] * di);
     r[b] = fma(eta, w1 * delta, u0[b]);
   }
-  stv<T, BV>(uout, base, r);
+  stg<T, BV>(uout, base, r);
 }
 
 // phi_i = wR1 r_i + wR2 mean_{N(i)} r
@@ -217,14 +281,14 @@ __global__ void __launch_bounds__(kThreads) k_conv_r_mb(LV<T> L, const T* __rest
   MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
   T s[BV], ri[BV];
   row_sum_mb<T, BV>(L, i, r, B, b0, s);
-  ldv<T, BV>(r, base, ri);
+  ldg<T, BV>(r, base, ri);
   const T w1 = prm[P_WR1], w2 = prm[P_WR2], id = L.invdeg[i];
 #pragma unroll
   for (int b = 0; b < BV; ++b) {
     T p = w1 * ri[b];
     ri[b] = fma(w2, id * s[b], p);
   }
-  stv<T, BV>(phi, base, ri);
+  stg<T, BV>(phi, base, ri);
 }
 
 // fc_I = sum_children P_iI phi_i (coarse rows); scale: phi = w1 * x (plain
@@ -243,11 +307,11 @@ __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __rest
     if (c < 0) break;
     const T w = L.r_w[(size_t)k * L.nc + i];
     T xv[BV];
-    ldv<T, BV>(x, (size_t)c * B + b0, xv);
+    ldg<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
     for (int b = 0; b < BV; ++b) acc[b] = fma(w, scale ? w1 * xv[b] : xv[b], acc[b]);
   }
-  stv<T, BV>(fc, base, acc);
+  stg<T, BV>(fc, base, acc);
 }
 
 // pe_i = (P ec)_i
@@ -259,14 +323,14 @@ __device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __
   for (int b = 0; b < BV; ++b) v[b] = T(0);
   if (a >= 0) {
     T e[BV];
-    ldv<T, BV>(ec, (size_t)a * B + b0, e);
+    ldg<T, BV>(ec, (size_t)a * B + b0, e);
     const T w = L.p_w[j];
 #pragma unroll
     for (int b = 0; b < BV; ++b) v[b] = w * e[b];
   }
   if (c >= 0) {
     T e[BV];
-    ldv<T, BV>(ec, (size_t)c * B + b0, e);
+    ldg<T, BV>(ec, (size_t)c * B + b0, e);
     const T w = L.p_w[(size_t)L.n + j];
 #pragma unroll
     for (int b = 0; b < BV; ++b) v[b] = fma(w, e[b], v[b]);
@@ -279,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) k_pe_mb(LV<T> L, const T* __restrict
   MG_MB_PROLOGUE(L.n, prefetch_p(L, i))
   T v[BV];
   prolong_at_mb<T, BV>(L, i, ec, B, b0, v);
-  stv<T, BV>(pe, base, v);
+  stg<T, BV>(pe, base, v);
 }
 
 // u_i = uin_i + wP1 x_i + wP2 mean_{N(i)} x with x = pe (conv), or
@@ -293,7 +357,7 @@ __global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __res
   const T w1 = prm[P_WP1];
   if (conv) {
     T s[BV], xi[BV];
-    ldv<T, BV>(x, base, xi);
+    ldg<T, BV>(x, base, xi);
     row_sum_mb<T, BV, true>(L, i, x, B, b0, s);
     const T w2 = prm[P_WP2], id = L.invdeg[i];
 #pragma unroll
@@ -307,10 +371,10 @@ __global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __res
 #pragma unroll
     for (int b = 0; b < BV; ++b) phi[b] = w1 * v[b];
   }
-  ldv<T, BV>(uin, base, ui);
+  ldg<T, BV>(uin, base, ui);
 #pragma unroll
   for (int b = 0; b < BV; ++b) ui[b] = ui[b] + phi[b];
-  stv<T, BV>(u, base, ui);
+  stg<T, BV>(u, base, ui);
 }
 
 #undef MG_MB_PROLOGUE

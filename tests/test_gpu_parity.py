@@ -333,16 +333,36 @@ def test_fcg_result_independent_of_batch():
         assert torch.equal(u1[:, 0], u3[:, b])
 
 
-def test_packed_coarse_solve_matches_cholesky():
-    """The L-shape coarsest level (161 rows) uses the shared-memory packed
-    factor: same values as scipy's Cholesky solve."""
+@pytest.mark.parametrize("inverse", [1, 0])
+@pytest.mark.parametrize("nrhs", [1, 4, 16])
+def test_coarse_solve_matches_cholesky(inverse, nrhs):
+    """The L-shape coarsest level (161 rows): the explicit-inverse product
+    (default) and the shared-memory packed-factor substitutions (option off,
+    one block per right-hand side) both give scipy's Cholesky solve to
+    1e-13; the cycle with the inverse stays within 1e-12 of the oracle's,
+    and in the small-levels block (tail) it is bitwise the grid kernel's."""
     p, Ho, Hp = problem("lshape_r2")
-    S = Solver(Hp, rand_params(Hp.J, 59), precision=64, max_batch=4)
+    prm = rand_params(Hp.J, 59)
+    S = Solver(Hp, prm, precision=64, max_batch=16)
+    S.set_option("coarse_inverse", inverse)
     nJ = Hp.sizes[-1]
-    fJ = np.random.default_rng(2).standard_normal((nJ, 4))
-    out = torch.empty((nJ, 4), dtype=torch.float64, device=DEV)
+    fJ = np.random.default_rng(2).standard_normal((nJ, nrhs))
+    out = torch.empty((nJ, nrhs), dtype=torch.float64, device=DEV)
     S.level_apply(Hp.J - 1, "coarse", t64(fJ), None, out)
     assert rel(out.cpu().numpy(), sla.cho_solve(Ho.chol, fJ)) < 1e-13
+    f = p.f[:, :1] if nrhs == 1 else np.concatenate([p.f] * (nrhs // 2), axis=1)
+    outs = []
+    for tail in (0, 1 << 30):
+        S.set_option("tail_work", tail)
+        ug = torch.zeros((Hp.sizes[0], nrhs), dtype=torch.float64, device=DEV)
+        S.vcycle(t64(f), ug)
+        outs.append(ug.clone())
+    assert torch.equal(outs[0], outs[1])
+    uo = O.vcycle(Ho, to_oracle(prm), f, np.zeros_like(f))
+    assert rel(outs[0].cpu().numpy(), uo) < 1e-12
+    with pytest.raises(MGError):
+        S.set_option("coarse_inverse", 2)
+    S.close()
 
 
 # --------------------------------------------------------- launch options --
