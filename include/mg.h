@@ -460,6 +460,58 @@ int64_t mg_kernel_launches(const mg_ctx* ctx);
 void mg_destroy(mg_ctx* ctx);
 
 /* ---------------------------------------------------------------------
+ * Stacked contexts: one operator per request on a structured square mesh
+ * (serving).  A context holds `slots` independent systems -div(k grad u) = f
+ * on the same N x N uniform right-triangle mesh of the unit square (every
+ * cell split by its SW->NE diagonal, Dirichlet boundary), each with its own
+ * element coefficients.  Every level stores the block-diagonal stack of the
+ * slots' interior operators (block b = rows [b m_l, (b+1) m_l), m_l =
+ * (N_l - 2)^2); the learnable cycle (Algorithm 2) runs on the stack, and a
+ * block's rows only ever read their own block, so each system's result does
+ * not depend on the others.  Vectors of the context: level-0 stacks, FP64
+ * [slots * m_0].
+ * ------------------------------------------------------------------- */
+
+/* Creates a stacked context: N vertices per side (N - 1 divisible by
+ * 2^(J-1)), J levels down to 3 x 3 vertices (one interior vertex, solved by
+ * its explicit inverse), 1 <= slots <= 2048, Theta p, precision 64 or 32.
+ * The transfers (natural inclusion between the nested grids, Sec. 2.2) and
+ * the DIA layout are built here, once; the blocks' operators are placeholders
+ * until mg_square_set_block writes them.  Errors as mg_setup, MG_ERR_INVALID
+ * for sizes that do not coarsen to 3 x 3. */
+mg_status mg_setup_square(mg_ctx** out, int32_t N, int32_t J, int32_t slots, const mg_params* p,
+                          int32_t precision, void* stream);
+
+/* Writes one request's operator into block `block` of a stacked context, on
+ * the device (no host work, no allocation): the P1 stiffness of
+ * -div(k grad u) from the element coefficients (Sec. 2.1's discretisation;
+ * on these right isosceles triangles the element matrix is k_T/2 times the
+ * reference one), Galerkin coarse operators A_{l+1} = P^T A_l P over all
+ * vertices (Sec. 2.2), the drop of round-off couplings |a_ij| <= 1e-12
+ * max(|a_ii|, |a_jj|), the graph degree before Dirichlet elimination, the
+ * interior rows' DIA values, diagonals, 1/diagonals and 1/degrees, and the
+ * coarsest vertex's inverse.  ke: DEVICE FP64 [2 (N-1)^2], element e =
+ * 2 (cy (N-1) + cx) + t for cell (cx, cy) (x fastest), t = 0 the lower
+ * triangle (SW, SE, NE), t = 1 the upper one (SW, NE, NW); it is read before
+ * the call's work completes (stream order).  Queued on stream, not waited
+ * for; uses the context's set-up scratch, so calls on one context must be
+ * ordered on one stream. */
+mg_status mg_square_set_block(mg_ctx* ctx, int32_t block, const double* ke_dev, void* stream);
+
+/* Solves every block of a stacked context to its own tolerance:
+ * ||f_b - A_b u_b||_2 / ||f_b||_2 < tol per block b, with mg_solve's methods
+ * applied per block (precision 32: FP32 cycles inside FP64 refinement, the
+ * residual of each block scaled by its own power of two; precision 64: the
+ * stationary FP64 cycle), each block stopping as soon as it meets tol.  One
+ * CUDA graph (a while node) per solve.  f_dev, u_dev: DEVICE FP64 level-0
+ * stacks [slots * m_0]; u is the initial guess; a block whose f is zero is
+ * idle (relres 0, no iterations).  iters_out, relres_out: host [slots] (may
+ * be NULL).  Synchronises the stream.  Returns MG_NOT_CONVERGED if a block
+ * missed tol within max_iter, MG_ERR_DIVERGED on a non-finite residual. */
+mg_status mg_solve_blocks(mg_ctx* ctx, const double* f_dev, double* u_dev, double tol,
+                          int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
+
+/* ---------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is an
  * interface for callers that cannot call cudaMalloc (a host application
  * that owns all device memory and forbids plug-ins to allocate, or a

@@ -112,6 +112,10 @@ def lib() -> C.CDLL:
         "mg_residual_loss": ([vp, vp, vp, C.c_int32, vp, vp, vp, vp, vp], C.c_int),
         "mg_smooth_noalloc": ([C.c_int32, vp, vp, vp, vp, vp, vp, C.c_int32, C.c_int32,
                                C.c_double, C.c_double, C.c_double, C.c_double, vp], C.c_int),
+        "mg_setup_square": ([C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.POINTER(Params),
+                             C.c_int32, vp], C.c_int),
+        "mg_square_set_block": ([vp, C.c_int32, vp, vp], C.c_int),
+        "mg_solve_blocks": ([vp, vp, vp, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
         "mg_last_error": ([vp, C.c_char_p, C.c_size_t], C.c_int),
         "mg_kernel_launches": ([vp], C.c_int64),
         "mg_destroy": ([vp], None),

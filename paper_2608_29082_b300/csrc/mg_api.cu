@@ -26,6 +26,7 @@
 #include "kernels.cuh"
 #include "krylov.cuh"
 #include "multi_rhs.cuh"
+#include "square.cuh"
 #include "mg.h"
 #include "mg_internal.h"
 
@@ -355,6 +356,15 @@ struct mg_ctx {
   // level is 32..512 rows and well conditioned; used when coarse_inv is set
   double* cholInv = nullptr;
   bool coarse_inv = false;
+  // stacked square-mesh contexts (square_impl.cuh): requests per context
+  // (0: an ordinary context), vertices per side per level, the set-up
+  // scratch (7-point stencils over all vertices of every level) and the
+  // per-block solve state
+  int sq_slots = 0;
+  std::vector<int> sq_N;
+  double* sq_scratch = nullptr;
+  void* blk_state = nullptr;
+  int maxB_blocks = 0;
   // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
   double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
   double *k_partial = nullptr, *k_small = nullptr;
@@ -1329,7 +1339,8 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   for (auto& L : c->d64) free_level(L);
   for (auto& L : c->d32) free_level(L);
-  for (void* p : {(void*)c->cholP, (void*)c->cholInv, (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
+  for (void* p : {(void*)c->cholP, (void*)c->cholInv, (void*)c->sq_scratch, c->blk_state,
+                  (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
                   (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
                   (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
                   (void*)c->gm_zero32, (void*)c->gm_done, c->cheb_dev})
@@ -1967,6 +1978,7 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
 #include "train_impl.cuh"
 #include "krylov_impl.cuh"
 #include "gmres_impl.cuh"
+#include "square_impl.cuh"
 
 extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_option: ctx is NULL");

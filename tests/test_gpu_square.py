@@ -1,0 +1,203 @@
+"""Stacked contexts (one operator per request on the square mesh) against the
+oracle: the device set-up (P1 assembly, Galerkin coarsening, drop rule,
+degrees, coarsest inverse) level by level, the cycle per block, and block
+solves that equal each system solved alone, bitwise, through the C ABI.
+
+Tolerances: FP64 operator application and single steps 1e-13 relative per
+block (the device sums the Galerkin products in another order than the
+oracle's sparse products); FP64 cycles 1e-12; FP32 cycles 1e-5; solves to
+1e-8 re-evaluated by the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import workloads as W
+from paper_2608_29082_b300 import LMGParams
+from paper_2608_29082_b300.square import SquareBatch, levels_for
+from workloads import fields, meshes
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda"
+
+
+def coefficients(N, kind, seed):
+    L = meshes.square_level(N)
+    if kind == "poisson":
+        return np.ones(L.tri.shape[0])
+    if kind == "checker":
+        return fields.checkerboard(L, 4, (1.0, 1e3), seed)
+    return fields.lognormal(L, 1.5, 0.1, seed)
+
+
+def systems(N, kinds, seed=0):
+    n = (N - 2) ** 2
+    out = []
+    for b, kind in enumerate(kinds):
+        k = coefficients(N, kind, seed + b)
+        f = fields.rhs(n, 1, seed + 100 + b)[:, 0]
+        p = W.square_with_coefficients(N, k, f)
+        out.append((k, f, p, O.build_hierarchy(p)))
+    return out
+
+
+def rand_params(J, seed, spread=0.2):
+    r = np.random.default_rng(seed)
+    p = LMGParams.identity(J)
+    m = J - 1
+    p.theta = p.theta * (1 + spread * r.uniform(-1, 1, m))
+    p.eta = p.eta * (1 + spread * r.uniform(-1, 1, m))
+    for w in (p.wB, p.wR, p.wP):
+        w[:, 0] += spread * r.uniform(-1, 1, m)
+        w[:, 1] += spread * r.uniform(-1, 1, m)
+    return p
+
+
+def to_oracle(p):
+    return O.Params(p.theta.copy(), p.eta.copy(), p.wB.copy(), p.wR.copy(), p.wP.copy(),
+                    p.nu_pre, p.nu_post)
+
+
+def t64(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def fill(batch, sys_list):
+    for b, (k, f, p, H) in enumerate(sys_list):
+        batch.set_block(b, t64(k))
+
+
+@pytest.mark.parametrize("N", [17, 33])
+def test_device_setup_matches_oracle_per_level(N):
+    """For every level and block: A u (the residual step with f = 0), the
+    learnable smoothing step (diagonal, 1/diagonal and 1/degree through the
+    SAGEConv mean) and the coarsest solve equal the oracle's for that
+    block's own system."""
+    sys_list = systems(N, ["lognormal", "checker", "poisson"], seed=3)
+    J = levels_for(N)
+    prm = rand_params(J, 5)
+    po = to_oracle(prm)
+    S = SquareBatch(N, 3, prm, precision=64)
+    fill(S, sys_list)
+    r = np.random.default_rng(1)
+    for lev in range(J):
+        m = S.sizes[lev] // 3
+        u = r.standard_normal(3 * m)
+        f = r.standard_normal(3 * m)
+        out = torch.empty(3 * m, dtype=torch.float64, device=DEV)
+        if lev == J - 1:
+            S.level_apply(lev, "coarse", t64(f), None, out)
+            for b, (_, _, _, H) in enumerate(sys_list):
+                ref = f[b * m:(b + 1) * m] / H.levels[lev].A.toarray()[0, 0]
+                got = out.cpu().numpy()[b * m:(b + 1) * m]
+                assert np.abs(got - ref).max() <= 1e-15 * np.abs(ref).max(), (lev, b)
+            continue
+        S.level_apply(lev, "residual", t64(np.zeros(3 * m)), t64(u), out)
+        got = -out.cpu().numpy()
+        for b, (_, _, _, H) in enumerate(sys_list):
+            ref = H.levels[lev].A @ u[b * m:(b + 1) * m]
+            err = np.linalg.norm(got[b * m:(b + 1) * m] - ref) / np.linalg.norm(ref)
+            assert err < 1e-13, (N, lev, b, err)
+        S.level_apply(lev, "smooth", t64(f), t64(u), out)
+        got = out.cpu().numpy()
+        for b, (_, _, _, H) in enumerate(sys_list):
+            sl = slice(b * m, (b + 1) * m)
+            ref = O.smooth(H.levels[lev], f[sl, None], u[sl, None], po.theta[lev], po.eta[lev],
+                           po.wB[lev])[:, 0]
+            err = np.linalg.norm(got[sl] - ref) / np.linalg.norm(ref)
+            assert err < 1e-13, (N, lev, b, err)
+    S.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_cycle_per_block_matches_oracle(prec):
+    N = 33
+    sys_list = systems(N, ["lognormal", "lognormal", "checker", "lognormal"], seed=11)
+    J = levels_for(N)
+    prm = rand_params(J, 7)
+    po = to_oracle(prm)
+    S = SquareBatch(N, 4, prm, precision=prec)
+    fill(S, sys_list)
+    m = S.m
+    fs = np.concatenate([f for (_, f, _, _) in sys_list])
+    dt = torch.float64 if prec == 64 else torch.float32
+    fd = torch.tensor(fs, dtype=dt, device=DEV)
+    u = torch.zeros(4 * m, dtype=dt, device=DEV)
+    uo = [np.zeros((m, 1)) for _ in sys_list]
+    for cyc in range(3):
+        if prec == 32:  # the oracle from the same FP32-representable iterate
+            cur = u.double().cpu().numpy()
+            uo = [cur[b * m:(b + 1) * m, None] for b in range(4)]
+        S.vcycle(fd, u)
+        got = u.double().cpu().numpy()
+        for b, (_, f, p, H) in enumerate(sys_list):
+            fo = f.astype(np.float32).astype(np.float64) if prec == 32 else f
+            uo[b] = O.vcycle(H, po, fo[:, None], uo[b])
+            err = np.linalg.norm(got[b * m:(b + 1) * m] - uo[b][:, 0]) / np.linalg.norm(uo[b])
+            assert err < (1e-12 if prec == 64 else 1e-5), (prec, cyc, b, err)
+    S.close()
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_block_solves_in_the_mix_equal_alone(prec):
+    """Four systems in one stacked context, iterated in ticks of 3 with
+    systems entering and leaving between ticks, give each system's result
+    solved alone in a one-slot context in one call: same iterate bitwise,
+    same iteration count; the oracle re-checks relres < 1e-8.  An idle block
+    (f = 0) takes no iterations."""
+    N = 65
+    kinds = ["lognormal", "lognormal", "checker", "lognormal"]
+    sys_list = systems(N, kinds, seed=21)
+    J = levels_for(N)
+    prm = LMGParams.identity(J)
+    prm.wB[:, 1], prm.wR[:, 1], prm.wP[:, 1] = 0.1, 0.05, -0.05
+    S = SquareBatch(N, 4, prm, precision=prec)
+    m = S.m
+    f = torch.zeros(4 * m, dtype=torch.float64, device=DEV)
+    u = torch.zeros_like(f)
+    iters = np.zeros(4, dtype=int)
+    done = {}
+    # block b enters at tick 2 b; ticks of 3 iterations
+    for tick in range(200):
+        for b in range(4):
+            if tick == 2 * b:
+                S.set_block(b, t64(sys_list[b][0]))
+                f[b * m:(b + 1) * m] = t64(sys_list[b][1])
+                u[b * m:(b + 1) * m] = 0
+        info = S.solve(f, u, tol=1e-8, max_iter=3)
+        for b in range(4):
+            if tick < 2 * b or b in done:
+                assert info.iters[b] == 0
+                continue
+            iters[b] += info.iters[b]
+            if info.relres[b] < 1e-8:
+                done[b] = u[b * m:(b + 1) * m].cpu().numpy().copy()
+                f[b * m:(b + 1) * m] = 0
+                u[b * m:(b + 1) * m] = 0
+        if len(done) == 4:
+            break
+    assert len(done) == 4
+    S.close()
+    for b, (k, fb, p, H) in enumerate(sys_list):
+        A1 = SquareBatch(N, 1, prm, precision=prec)
+        A1.set_block(0, t64(k))
+        ua = torch.zeros(m, dtype=torch.float64, device=DEV)
+        info = A1.solve(t64(fb), ua, tol=1e-8, max_iter=400)
+        assert int(info.iters[0]) == iters[b], (b, info.iters, iters)
+        assert np.array_equal(ua.cpu().numpy(), done[b]), b
+        assert O.relres(H, fb[:, None], done[b][:, None])[0] < 1e-8
+        A1.close()
+
+
+def test_invalid_square_arguments():
+    from paper_2608_29082_b300._lib import MGError
+    with pytest.raises(MGError):
+        SquareBatch(33, 0, LMGParams.identity(5))
+    S = SquareBatch(17, 2, LMGParams.identity(4))
+    with pytest.raises(ValueError):
+        S.set_block(0, torch.zeros(10, dtype=torch.float64, device=DEV))
+    with pytest.raises(MGError):
+        S.set_block(2, torch.ones(S.n_elements, dtype=torch.float64, device=DEV))
+    S.close()

@@ -88,6 +88,20 @@ def lognormal_square(N: int, seed: int, sigma: float = 1.5, corr_len: float = 0.
                         coefficient=f"lognormal sigma={sigma} corr={corr_len}"))
 
 
+def square_with_coefficients(N: int, k: np.ndarray, f: np.ndarray, J: int | None = None,
+                             name: str = "square") -> Problem:
+    """-div(k grad u) = f on the N x N square mesh with given element
+    coefficients k (the mesh's element order: cells x fastest, lower then
+    upper triangle) and interior source f ((n,) or (n, batch)); J levels
+    down to 3 x 3 vertices by default.  A serving request's system."""
+    J = J if J is not None else int(round(np.log2(N - 1)))
+    H = meshes.square_hierarchy(N, J)
+    A = fields.assemble_p1(H.levels[0], k=np.asarray(k, dtype=np.float64))
+    f = np.asarray(f, dtype=np.float64)
+    return Problem(name, H, A, f[:, None] if f.ndim == 1 else f,
+                   dict(N=N, J=J, coefficient="given per element"))
+
+
 def lshape_anisotropic(refinements: int = 7, batch: int = 16, seed: int = 0,
                        eps: float = 1e-3, angle: float = 30.0) -> Problem:
     H = meshes.lshape_hierarchy(refinements, 8, 0.2, seed)
