@@ -119,6 +119,18 @@ mg_status mg_galerkin(const mg_csr* A_full, const int32_t* parent, int32_t nv_co
 mg_status mg_eliminate(const mg_csr* A_full, const uint8_t* boundary, double drop_tol,
                        mg_csr_owned* A_int, double* inv_deg_out);
 
+/* Complex-valued forms of mg_galerkin and mg_eliminate, for the complex
+ * operators of two features per node (Sec. 3.2's W_1, W_2 acting on (Re u,
+ * Im u); the Helmholtz experiment of Sec. 4.2): the val arrays of A_full and
+ * of the result hold 2 * nnz doubles, (Re, Im) of each entry adjacent (C99
+ * complex / numpy complex128 layout); the drop rule compares complex
+ * moduli.  P is real, so the product sums each part exactly as the real
+ * routine would. */
+mg_status mg_galerkin_complex(const mg_csr* A_full, const int32_t* parent, int32_t nv_coarse,
+                              double drop_tol, mg_csr_owned* out);
+mg_status mg_eliminate_complex(const mg_csr* A_full, const uint8_t* boundary, double drop_tol,
+                               mg_csr_owned* A_int, double* inv_deg_out);
+
 /* Interior prolongation P (n_int_fine x n_int_coarse) from the parent map:
  * the natural inclusion (Sec. 2.2) restricted to interior vertices. */
 mg_status mg_prolongation(const int32_t* parent, int32_t nv_fine, const uint8_t* boundary_fine,

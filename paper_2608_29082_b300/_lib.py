@@ -77,6 +77,10 @@ def lib() -> C.CDLL:
     sig = {
         "mg_galerkin": ([C.POINTER(CSR), i32p, C.c_int32, C.c_double, C.POINTER(CSROwned)], C.c_int),
         "mg_eliminate": ([C.POINTER(CSR), u8p, C.c_double, C.POINTER(CSROwned), f64p], C.c_int),
+        "mg_galerkin_complex": ([C.POINTER(CSR), i32p, C.c_int32, C.c_double,
+                                 C.POINTER(CSROwned)], C.c_int),
+        "mg_eliminate_complex": ([C.POINTER(CSR), u8p, C.c_double, C.POINTER(CSROwned), f64p],
+                                 C.c_int),
         "mg_prolongation": ([i32p, C.c_int32, u8p, C.c_int32, u8p, C.POINTER(CSROwned)], C.c_int),
         "mg_csr_owned_free": ([C.POINTER(CSROwned)], None),
         "mg_setup": ([C.POINTER(vp), C.POINTER(Hier), C.POINTER(CSR), C.POINTER(Params),
@@ -171,6 +175,44 @@ class HostCSR:
     def to_scipy(self):
         import scipy.sparse as sp
         return sp.csr_matrix((self.data, self.indices, self.indptr), shape=self.shape)
+
+
+class HostCSRComplex:
+    """Keeps the arrays of an mg_csr whose values are complex (2 doubles per
+    entry, (Re, Im) adjacent)."""
+
+    def __init__(self, indptr, indices, data, shape):
+        self.indptr, self.indices = as_i32(indptr), as_i32(indices)
+        self.data = np.ascontiguousarray(data, dtype=np.complex128)
+        self.shape = (int(shape[0]), int(shape[1]))
+        pairs = self.data.view(np.float64)
+        self.c = CSR(self.shape[0], self.shape[1], int(self.data.size), ptr(self.indptr, i32p),
+                     ptr(self.indices, i32p), ptr(pairs, f64p))
+
+    @staticmethod
+    def from_scipy(m) -> "HostCSRComplex":
+        m = m.tocsr()
+        return HostCSRComplex(m.indptr, m.indices, m.data, m.shape)
+
+    def to_scipy(self):
+        import scipy.sparse as sp
+        return sp.csr_matrix((self.data, self.indices, self.indptr), shape=self.shape)
+
+
+def take_owned_complex(o: CSROwned) -> HostCSRComplex:
+    """take_owned for a library-allocated CSR with complex values."""
+    try:
+        n, nnz = o.n_rows, o.nnz
+        indptr = np.ctypeslib.as_array(o.rowptr, shape=(n + 1,)).copy()
+        if nnz > 0:
+            indices = np.ctypeslib.as_array(o.col, shape=(nnz,)).copy()
+            data = np.ctypeslib.as_array(o.val, shape=(2 * nnz,)).copy().view(np.complex128)
+        else:
+            indices = np.zeros(0, np.int32)
+            data = np.zeros(0, np.complex128)
+        return HostCSRComplex(indptr, indices, data, (o.n_rows, o.n_cols))
+    finally:
+        lib().mg_csr_owned_free(C.byref(o))
 
 
 def take_owned(o: CSROwned) -> HostCSR:

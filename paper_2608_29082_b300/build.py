@@ -41,7 +41,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
     # -fmad=false: the kernels fuse multiply-adds only where they call fma()
     # explicitly, so every launch form of a step rounds identically
     cmd = [nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC,-O2",
-           "-shared", "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp", *sources(), "-lcudart"]
+           "-shared", "-I", INCLUDE, "-I", CSRC, "-o", LIB + ".tmp", *sources(), "-lcudart", "-ldl"]
     if ptxas_v:
         cmd.insert(1, "-Xptxas=-v")
     if verbose:

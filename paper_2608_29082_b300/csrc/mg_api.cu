@@ -18,6 +18,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "adjoint.cuh"
 #include "gmres.cuh"
@@ -581,6 +582,11 @@ struct Issue {
 
   void pre(int kind, int lev) {
     if (!rec) return;
+    // an NVTX range per step and level around its launch (host timeline of
+    // a tracing tool), next to the CUDA event pair on the stream
+    char name[64];
+    snprintf(name, sizeof name, "L%d %s", lev, mg_kernel_name(kind));
+    nvtxRangePushA(name);
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
@@ -588,7 +594,9 @@ struct Issue {
     rec->emplace_back(kind, lev, a, b);
   }
   void post() {
-    if (rec) cudaEventRecord(std::get<3>(rec->back()), s);
+    if (!rec) return;
+    cudaEventRecord(std::get<3>(rec->back()), s);
+    nvtxRangePop();
   }
 
   const T* P(int lev) const { return prm + (size_t)lev * mgk::P_COUNT; }

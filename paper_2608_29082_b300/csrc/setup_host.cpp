@@ -5,6 +5,7 @@
 // the mean aggregation of the SAGEConv (Sec. 3.2).
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -15,13 +16,14 @@
 
 namespace {
 
-bool alloc_csr(mg_csr_owned* o, int nr, int nc, long long nnz) {
+// vw: doubles per value (1 real, 2 complex with (Re, Im) adjacent)
+bool alloc_csr(mg_csr_owned* o, int nr, int nc, long long nnz, int vw = 1) {
   o->n_rows = nr;
   o->n_cols = nc;
   o->nnz = (int32_t)nnz;
   o->rowptr = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)(nr + 1));
   o->col = (int32_t*)std::malloc(sizeof(int32_t) * (size_t)std::max<long long>(nnz, 1));
-  o->val = (double*)std::malloc(sizeof(double) * (size_t)std::max<long long>(nnz, 1));
+  o->val = (double*)std::malloc(sizeof(double) * vw * (size_t)std::max<long long>(nnz, 1));
   if (!o->rowptr || !o->col || !o->val) {
     mg_csr_owned_free(o);
     return false;
@@ -41,25 +43,37 @@ bool csr_ok(const mg_csr* A) {
 }
 
 // Row-wise sparse accumulator: values for columns touched in the current row.
+template <class V>
 struct Spa {
-  std::vector<double> acc;
+  std::vector<V> acc;
   std::vector<int> mark, cols;
-  explicit Spa(int n) : acc(n, 0.0), mark(n, -1) {}
-  void add(int row, int j, double v) {
+  explicit Spa(int n) : acc(n, V(0)), mark(n, -1) {}
+  void add(int row, int j, V v) {
     if (mark[j] != row) {
       mark[j] = row;
-      acc[j] = 0.0;
+      acc[j] = V(0);
       cols.push_back(j);
     }
     acc[j] += v;
   }
 };
 
+template <class V>
 struct Csr {
   int nr = 0, nc = 0;
   std::vector<int> ptr, col;
-  std::vector<double> val;
+  std::vector<V> val;
 };
+
+// Magnitude used by the drop rule: |a| for real values, the complex modulus
+// for complex ones.
+inline double mag(double a) { return std::fabs(a); }
+inline double mag(const std::complex<double>& a) { return std::abs(a); }
+
+template <class V>
+constexpr int value_width() {
+  return sizeof(V) / sizeof(double);
+}
 
 }  // namespace
 
@@ -74,12 +88,19 @@ extern "C" void mg_csr_owned_free(mg_csr_owned* m) {
   m->n_rows = m->n_cols = m->nnz = 0;
 }
 
-extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t nv_c,
-                                 double drop_tol, mg_csr_owned* out) {
-  if (!out) return mgi::set_global_error(MG_ERR_INVALID, "mg_galerkin: out is NULL");
+namespace {
+
+// P^T A P over all vertices with P from the parent map; values V (real, or
+// complex (Re, Im) adjacent: P is real, so both parts go through the same
+// sums in the same order as two real products would).
+template <class V>
+mg_status galerkin_impl(const mg_csr* A, const V* Aval, const int32_t* parent, int32_t nv_c,
+                        double drop_tol, mg_csr_owned* out, const char* who) {
+  if (!out) return mgi::set_global_error(MG_ERR_INVALID, std::string(who) + ": out is NULL");
   std::memset(out, 0, sizeof(*out));
   if (!csr_ok(A) || A->n_rows != A->n_cols || !parent || nv_c <= 0)
-    return mgi::set_global_error(MG_ERR_INVALID, "mg_galerkin: invalid matrix or parent map");
+    return mgi::set_global_error(MG_ERR_INVALID,
+                                 std::string(who) + ": invalid matrix or parent map");
   const int nf = A->n_rows;
   // P rows from the parent map (natural inclusion).
   std::vector<int> pc(2 * (size_t)nf);
@@ -87,24 +108,25 @@ extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t
   for (int i = 0; i < nf; ++i) {
     int a = parent[2 * i], b = parent[2 * i + 1];
     if (a < 0 || a >= nv_c || b >= nv_c)
-      return mgi::set_global_error(MG_ERR_INVALID, "mg_galerkin: parent index out of range");
+      return mgi::set_global_error(MG_ERR_INVALID,
+                                   std::string(who) + ": parent index out of range");
     pc[2 * i] = a;
     pc[2 * i + 1] = b;
     pw[2 * i] = b < 0 ? 1.0 : 0.5;
     pw[2 * i + 1] = b < 0 ? 0.0 : 0.5;
   }
   // AP = A P, row by row.
-  Csr AP;
+  Csr<V> AP;
   AP.nr = nf;
   AP.nc = nv_c;
   AP.ptr.assign(nf + 1, 0);
   {
-    Spa spa(nv_c);
+    Spa<V> spa(nv_c);
     for (int i = 0; i < nf; ++i) {
       spa.cols.clear();
       for (int k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
         int j = A->col[k];
-        double a = A->val[k];
+        const V a = Aval[k];
         spa.add(i, pc[2 * j], a * pw[2 * j]);
         if (pc[2 * j + 1] >= 0) spa.add(i, pc[2 * j + 1], a * pw[2 * j + 1]);
       }
@@ -137,11 +159,11 @@ extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t
       }
   }
   // C = P^T (A P).
-  Csr C;
+  Csr<V> C;
   C.nr = C.nc = nv_c;
   C.ptr.assign(nv_c + 1, 0);
   {
-    Spa spa(nv_c);
+    Spa<V> spa(nv_c);
     for (int I = 0; I < nv_c; ++I) {
       spa.cols.clear();
       for (int t = tcount[I]; t < tcount[I + 1]; ++t) {
@@ -161,25 +183,26 @@ extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t
   std::vector<double> d(nv_c, 0.0);
   for (int I = 0; I < nv_c; ++I)
     for (int k = C.ptr[I]; k < C.ptr[I + 1]; ++k)
-      if (C.col[k] == I) d[I] = std::fabs(C.val[k]);
+      if (C.col[k] == I) d[I] = mag(C.val[k]);
   long long keep = 0;
   std::vector<char> kept(C.col.size(), 0);
   for (int I = 0; I < nv_c; ++I)
     for (int k = C.ptr[I]; k < C.ptr[I + 1]; ++k) {
       int Jc = C.col[k];
-      bool ok = Jc == I || std::fabs(C.val[k]) > drop_tol * std::max(d[I], d[Jc]);
+      bool ok = Jc == I || mag(C.val[k]) > drop_tol * std::max(d[I], d[Jc]);
       kept[k] = ok;
       keep += ok;
     }
-  if (!alloc_csr(out, nv_c, nv_c, keep))
-    return mgi::set_global_error(MG_ERR_OOM, "mg_galerkin: host allocation failed");
+  if (!alloc_csr(out, nv_c, nv_c, keep, value_width<V>()))
+    return mgi::set_global_error(MG_ERR_OOM, std::string(who) + ": host allocation failed");
+  V* oval = reinterpret_cast<V*>(out->val);
   long long w = 0;
   out->rowptr[0] = 0;
   for (int I = 0; I < nv_c; ++I) {
     for (int k = C.ptr[I]; k < C.ptr[I + 1]; ++k)
       if (kept[k]) {
         out->col[w] = C.col[k];
-        out->val[w] = C.val[k];
+        oval[w] = C.val[k];
         ++w;
       }
     out->rowptr[I + 1] = (int32_t)w;
@@ -187,12 +210,14 @@ extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t
   return MG_OK;
 }
 
-extern "C" mg_status mg_eliminate(const mg_csr* A, const uint8_t* bnd, double drop_tol,
-                                  mg_csr_owned* out, double* inv_deg) {
-  if (!out) return mgi::set_global_error(MG_ERR_INVALID, "mg_eliminate: out is NULL");
+// Dirichlet elimination and graph degrees; values V as galerkin_impl.
+template <class V>
+mg_status eliminate_impl(const mg_csr* A, const V* Aval, const uint8_t* bnd, double drop_tol,
+                         mg_csr_owned* out, double* inv_deg, const char* who) {
+  if (!out) return mgi::set_global_error(MG_ERR_INVALID, std::string(who) + ": out is NULL");
   std::memset(out, 0, sizeof(*out));
   if (!csr_ok(A) || A->n_rows != A->n_cols || !bnd || !inv_deg)
-    return mgi::set_global_error(MG_ERR_INVALID, "mg_eliminate: invalid arguments");
+    return mgi::set_global_error(MG_ERR_INVALID, std::string(who) + ": invalid arguments");
   const int nv = A->n_rows;
   std::vector<int> id(nv, -1);
   int ni = 0;
@@ -201,10 +226,10 @@ extern "C" mg_status mg_eliminate(const mg_csr* A, const uint8_t* bnd, double dr
   std::vector<double> d(nv, 0.0);
   for (int i = 0; i < nv; ++i)
     for (int k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k)
-      if (A->col[k] == i) d[i] = std::fabs(A->val[k]);
+      if (A->col[k] == i) d[i] = mag(Aval[k]);
   auto edge = [&](int i, int k) {
     int j = A->col[k];
-    return j != i && std::fabs(A->val[k]) > drop_tol * std::max(d[i], d[j]);
+    return j != i && mag(Aval[k]) > drop_tol * std::max(d[i], d[j]);
   };
   long long nnz = 0;
   for (int i = 0; i < nv; ++i) {
@@ -216,11 +241,13 @@ extern "C" mg_status mg_eliminate(const mg_csr* A, const uint8_t* bnd, double dr
       int j = A->col[k];
       if (id[j] >= 0 && (j == i || e)) ++nnz;
     }
-    if (deg == 0) return mgi::set_global_error(MG_ERR_INVALID, "mg_eliminate: isolated vertex");
+    if (deg == 0)
+      return mgi::set_global_error(MG_ERR_INVALID, std::string(who) + ": isolated vertex");
     inv_deg[id[i]] = 1.0 / (double)deg;
   }
-  if (!alloc_csr(out, ni, ni, nnz))
-    return mgi::set_global_error(MG_ERR_OOM, "mg_eliminate: host allocation failed");
+  if (!alloc_csr(out, ni, ni, nnz, value_width<V>()))
+    return mgi::set_global_error(MG_ERR_OOM, std::string(who) + ": host allocation failed");
+  V* oval = reinterpret_cast<V*>(out->val);
   long long w = 0;
   out->rowptr[0] = 0;
   for (int i = 0; i < nv; ++i) {
@@ -229,13 +256,41 @@ extern "C" mg_status mg_eliminate(const mg_csr* A, const uint8_t* bnd, double dr
       int j = A->col[k];
       if (id[j] >= 0 && (j == i || edge(i, k))) {
         out->col[w] = id[j];
-        out->val[w] = A->val[k];
+        oval[w] = Aval[k];
         ++w;
       }
     }
     out->rowptr[id[i] + 1] = (int32_t)w;
   }
   return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_galerkin(const mg_csr* A, const int32_t* parent, int32_t nv_c,
+                                 double drop_tol, mg_csr_owned* out) {
+  return galerkin_impl<double>(A, A ? A->val : nullptr, parent, nv_c, drop_tol, out,
+                               "mg_galerkin");
+}
+
+extern "C" mg_status mg_galerkin_complex(const mg_csr* A, const int32_t* parent, int32_t nv_c,
+                                         double drop_tol, mg_csr_owned* out) {
+  return galerkin_impl<std::complex<double>>(
+      A, A ? reinterpret_cast<const std::complex<double>*>(A->val) : nullptr, parent, nv_c,
+      drop_tol, out, "mg_galerkin_complex");
+}
+
+extern "C" mg_status mg_eliminate(const mg_csr* A, const uint8_t* bnd, double drop_tol,
+                                  mg_csr_owned* out, double* inv_deg) {
+  return eliminate_impl<double>(A, A ? A->val : nullptr, bnd, drop_tol, out, inv_deg,
+                                "mg_eliminate");
+}
+
+extern "C" mg_status mg_eliminate_complex(const mg_csr* A, const uint8_t* bnd, double drop_tol,
+                                          mg_csr_owned* out, double* inv_deg) {
+  return eliminate_impl<std::complex<double>>(
+      A, A ? reinterpret_cast<const std::complex<double>*>(A->val) : nullptr, bnd, drop_tol, out,
+      inv_deg, "mg_eliminate_complex");
 }
 
 extern "C" mg_status mg_prolongation(const int32_t* parent, int32_t nv_f, const uint8_t* bnd_f,

@@ -2,10 +2,9 @@
 
 Binding of the mg2_* entry points of libmg.so (include/mg.h).  The Helmholtz
 setting of Sec. 4.2 carries (Re u, Im u) as two node features, and every
-SAGEConv holds W_1, W_2 in R^{2x2} (Sec. 3.2).  The host set-up uses the
-native Galerkin and prolongation helpers of the real path: P is real, so
-P^T A P = P^T Re(A) P + i P^T Im(A) P, and the two products are merged
-before round-off entries are dropped on complex magnitudes.
+SAGEConv holds W_1, W_2 in R^{2x2} (Sec. 3.2).  The host set-up runs in the
+library's native complex Galerkin and elimination helpers (the drop rule on
+complex moduli); this module only marshals arrays.
 """
 from __future__ import annotations
 
@@ -13,36 +12,12 @@ import ctypes as C
 from dataclasses import dataclass
 
 import numpy as np
-import scipy.sparse as sp
 import torch
 
 from . import _lib as L
 from .solver import SolveInfo, _stream_handle
 
 DROP_TOL = 1e-12
-
-
-def _drop(A: sp.csr_matrix) -> sp.csr_matrix:
-    """Removes off-diagonal entries with |a_ij| <= 1e-12 max(|a_ii|, |a_jj|)
-    (round-off of the Galerkin products), the rule of mg_galerkin."""
-    Cm = A.tocoo()
-    d = np.abs(A.diagonal())
-    keep = (Cm.row == Cm.col) | (np.abs(Cm.data) > DROP_TOL * np.maximum(d[Cm.row], d[Cm.col]))
-    out = sp.csr_matrix((Cm.data[keep], (Cm.row[keep], Cm.col[keep])), shape=A.shape)
-    out.sort_indices()
-    return out
-
-
-def _galerkin(Af: sp.csr_matrix, parent: np.ndarray, nv_coarse: int) -> sp.csr_matrix:
-    lib = L.lib()
-    par = L.as_i32(parent)
-    parts = []
-    for part in (Af.real.tocsr(), Af.imag.tocsr()):
-        h = L.HostCSR.from_scipy(part)
-        o = L.CSROwned()
-        L.check(lib.mg_galerkin(C.byref(h.c), L.ptr(par, L.i32p), nv_coarse, 0.0, C.byref(o)))
-        parts.append(L.take_owned(o).to_scipy())
-    return _drop((parts[0] + 1j * parts[1]).tocsr())
 
 
 @dataclass
@@ -62,31 +37,34 @@ class Hierarchy2:
         return [a.shape[0] for a in self.A]
 
     @staticmethod
-    def from_problem(problem) -> "Hierarchy2":
+    def from_problem(problem, drop_tol: float = DROP_TOL) -> "Hierarchy2":
         """Duck-typed: .mesh.levels[l].{nv, boundary, parent}, .A_full
-        (scipy CSR, complex, all vertices of the finest level)."""
+        (scipy CSR, complex, all vertices of the finest level).  Every step
+        of the set-up runs in libmg.so (mg_eliminate_complex, mg_prolongation,
+        mg_galerkin_complex); numpy only holds arrays."""
         lib = L.lib()
         lv = problem.mesh.levels
-        Af = _drop(problem.A_full.tocsr().astype(np.complex128))
+        Af = L.HostCSRComplex.from_scipy(problem.A_full.tocsr().astype(np.complex128))
         A, P, inv_deg = [], [], []
         for lev, ML in enumerate(lv):
-            interior = np.flatnonzero(~np.asarray(ML.boundary, dtype=bool))
-            pattern = sp.csr_matrix((np.ones(Af.nnz), Af.indices.copy(), Af.indptr.copy()),
-                                    shape=Af.shape)
-            pattern.setdiag(0)
-            pattern.eliminate_zeros()
-            deg = np.asarray(pattern.sum(axis=1)).ravel()[interior]
-            A.append(Af[interior][:, interior].tocsr())
-            inv_deg.append(1.0 / deg)
+            bnd = np.ascontiguousarray(ML.boundary, dtype=np.uint8)
+            deg = np.zeros(int((bnd == 0).sum()))
+            o = L.CSROwned()
+            L.check(lib.mg_eliminate_complex(C.byref(Af.c), L.ptr(bnd, L.u8p), drop_tol, C.byref(o),
+                                             L.ptr(deg, L.f64p)))
+            A.append(L.take_owned_complex(o).to_scipy())
+            inv_deg.append(deg)
             if lev < len(lv) - 1:
                 par = L.as_i32(ML.parent)
-                bnd = np.ascontiguousarray(ML.boundary, dtype=np.uint8)
                 bc = np.ascontiguousarray(lv[lev + 1].boundary, dtype=np.uint8)
                 o = L.CSROwned()
                 L.check(lib.mg_prolongation(L.ptr(par, L.i32p), ML.nv, L.ptr(bnd, L.u8p),
                                             lv[lev + 1].nv, L.ptr(bc, L.u8p), C.byref(o)))
                 P.append(L.take_owned(o).to_scipy())
-                Af = _galerkin(Af, ML.parent, lv[lev + 1].nv)
+                o = L.CSROwned()
+                L.check(lib.mg_galerkin_complex(C.byref(Af.c), L.ptr(par, L.i32p), lv[lev + 1].nv,
+                                                drop_tol, C.byref(o)))
+                Af = L.take_owned_complex(o)
         return Hierarchy2(A, P, inv_deg)
 
 
