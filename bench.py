@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-lshape", action="store_true",
                     help="skip the L-shape (3.1M DOF, 16 rhs) bandwidth section")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the serving section (Poisson arrivals, an operator per request)")
     ap.add_argument("--oracle-leg", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--host-loop", action="store_true",
                     help="drive the solve iterations from the host (plain CUDA graphs) so that "
@@ -392,6 +394,9 @@ def run_ours(args):
     train_step = None
     if rank == 0 and not args.no_lshape:
         train_step = training_step_section(dev)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        serving = serving_section(dev)
 
     # oracle on the host cores, same workload (rank 0 at N=1 only)
     cpu = None
@@ -454,6 +459,7 @@ def run_ours(args):
             "roofline_lshape": lshape,
             "lshape_time_to_tol": lshape_solves,
             "training_step": train_step,
+            "serving": serving,
             "kernel_shares_per_vcycle": shares,
             "clocks": clocks,
             "cpu_baseline": cpu,
@@ -590,6 +596,43 @@ def training_step_section(dev):
                         "levels, 64 rhs, K=10 unrolled cycles, FP32, shared SAGEConv weights",
             "ms_per_step": round(e0.elapsed_time(e1) / steps, 3), "steps": steps,
             "loss": float(loss)}
+
+
+def serving_section(dev, rate=2000.0, duration=2.0):
+    """Config 3: Poisson arrivals (2000 req/s, 2 s of arrivals) of solves on
+    65^2 .. 1025^2 meshes, each request with its own lognormal coefficient
+    field (from a pool of 8 per class) and N(0,1) source; its operator is
+    assembled and coarsened on the GPU inside its latency, then iterated to
+    1e-8 (learned FP32 cycle + FP64 refinement) in the class's stacked
+    contexts.  Latency = completion - arrival."""
+    import paper_2608_29082_b300.serve as sv
+    from paper_2608_29082_b300 import trained
+    classes = [65, 129, 257, 513, 1025]
+    slots = {65: 64, 129: 64, 257: 32, 513: 16, 1025: 8}
+    ctxs = {65: 1, 129: 1, 257: 1, 513: 2, 1025: 3}
+    t0 = time.perf_counter()
+    coefs, src = sv.make_pools(classes, 8, 8, seed=0, device=dev)
+    base = trained.load(None, 10)
+    params = {k: (trained.read(trained.LOGNORMAL1025) if k == 1025 else base) for k in classes}
+    srv = sv.Server(coefs, src, params, slots=slots, iters_per_tick=6, grow=False)
+    srv.warm(ctxs)
+    srv.run([sv.Request(-1 - i, k, i % 8, 0, 0.0)
+             for i, k in enumerate(c for c in classes for _ in range(2))])
+    prep = time.perf_counter() - t0
+    reqs = sv.poisson_requests(rate, duration, classes, 8, 8, seed=0)
+    t1 = time.perf_counter()
+    done = srv.run(reqs, t1)
+    wall = time.perf_counter() - t1
+    peak = srv.peak
+    srv.close()
+    out = {"workload": f"Poisson arrivals {rate:g}/s for {duration:g} s, classes "
+                       f"{classes} (N x N meshes), lognormal k (sigma 1.5, corr 0.1) per request, "
+                       "tol 1e-8; operator set-up on the GPU inside each latency",
+           "slots": {str(k): v for k, v in slots.items()},
+           "contexts": {str(k): v for k, v in ctxs.items()},
+           "wall_s": round(wall, 2), "prep_s": round(prep, 1), "peak_device_bytes": peak}
+    out.update(sv.summarize(done, wall))
+    return out
 
 
 def cpu_baseline(prob, params):

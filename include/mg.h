@@ -305,6 +305,13 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *   MG_OPT_TAIL_WORK  levels with rows * nrhs <= value, and all coarser ones,
  *                     run in one thread block with block barriers instead of
  *                     one grid kernel per step (default 2048; 0 disables)
+ *   MG_OPT_TAIL_TEAMS k >= 1 (default 1): in that block each level runs on
+ *                     the first W warps only (about k entries per thread, W
+ *                     a power of two, no larger than the finer level's), whose
+ *                     steps are separated by barriers among those W warps
+ *                     (a named barrier, or a warp sync for one warp) instead
+ *                     of all 1024 threads; 0: every level on the whole block;
+ *                     at most 64
  *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
  *                     dependent launch; 0: plain stream order
  *   MG_OPT_MULTI_RHS  with nrhs > 1, one thread owns a row and a tile of
@@ -378,7 +385,8 @@ typedef enum {
   MG_OPT_SELL_HALO_ROWS = 7,
   MG_OPT_SELL_HALO_THREADS = 8,
   MG_OPT_SELL_HALO_MAX_BYTES = 9,
-  MG_OPT_COARSE_INVERSE = 10
+  MG_OPT_COARSE_INVERSE = 10,
+  MG_OPT_TAIL_TEAMS = 11
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

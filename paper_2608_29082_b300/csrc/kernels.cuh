@@ -586,6 +586,31 @@ struct TailArgs {
   const double* cU;
   const double* cDinv;
   const double* cInv;  // explicit inverse of A_J (row-major), or NULL: substitutions
+  int tw[kMaxLevels];  // warps of the team that runs level l (a power of two <= 32)
+};
+
+// The threads that run one small level of k_tail: the first W warps of the
+// block.  A level's steps are separated by a barrier among exactly those
+// threads: __syncthreads for the whole block, the named barrier log2(W)
+// (bar.sync with W * 32 threads) for 2..16 warps, __syncwarp for one warp.
+// Coarser levels have no more warps than finer ones, so a level's team
+// contains the teams of all coarser levels; a level small enough for a few
+// warps thus pays for cheap barriers instead of a barrier of 1024 threads.
+// Which thread computes an entry never changes its value.
+struct Team {
+  int W;
+  __device__ __forceinline__ bool member() const { return (int)(threadIdx.x >> 5) < W; }
+  __device__ __forceinline__ int size() const { return W * 32; }
+  __device__ __forceinline__ void sync() const {
+    if (W * 32 >= (int)blockDim.x) {
+      __syncthreads();
+    } else if (W == 1) {
+      __syncwarp();
+    } else {
+      const int id = 31 - __clz(W);  // 1..4
+      asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(W * 32) : "memory");
+    }
+  }
 };
 
 // Vectors of the small levels: in shared memory when a.smem_vectors (the
@@ -748,40 +773,42 @@ __global__ void k_coarse_chol_packed(const double* __restrict__ Lp, const double
 
 template <class T>
 __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* Ls,
-                                            const TailVecs<T>& v, int l, int nu, bool zero) {
+                                            const TailVecs<T>& v, int l, int nu, bool zero,
+                                            const Team& tm) {
   const LV<T>& L = Ls[l];
   const size_t N = (size_t)L.n * a.B;
   const T* prm = a.prm + (size_t)l * P_COUNT;
+  const size_t t0 = threadIdx.x, dt = tm.size();
   if ((a.convB >> l) & 1u) {
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      for (size_t t = t0; t < N; t += dt)
         residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 1, z, t);
-      __syncthreads();
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      tm.sync();
+      for (size_t t = t0; t < N; t += dt)
         conv_update_el(L, (const T*)v.t[l], v.u[l], a.B, prm, z, t);
-      __syncthreads();
+      tm.sync();
     }
   } else {
     T* cur = v.u[l];
     T* oth = v.u2[l];
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      for (size_t t = t0; t < N; t += dt)
         jacobi_el(L, (const T*)v.f[l], (const T*)cur, oth, a.B, prm, z, t);
-      __syncthreads();
+      tm.sync();
       T* tmp = cur;
       cur = oth;
       oth = tmp;
     }
     if (cur != v.u[l]) {
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x) v.u[l][t] = cur[t];
-      __syncthreads();
+      for (size_t t = t0; t < N; t += dt) v.u[l][t] = cur[t];
+      tm.sync();
     }
   }
   if (nu == 0 && zero) {
-    for (size_t t = threadIdx.x; t < N; t += blockDim.x) v.u[l][t] = T(0);
-    __syncthreads();
+    for (size_t t = t0; t < N; t += dt) v.u[l][t] = T(0);
+    tm.sync();
   }
 }
 
@@ -850,52 +877,63 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
   }
   cp_async_wait_all();
   __syncthreads();
+  // descent: level l by its team (teams shrink towards the coarsest level)
   for (int l = lt; l < J - 1; ++l) {
+    const Team tm{a.tw[l]};
+    if (!tm.member()) break;
     const LV<T>& L = sL[l];
     const T* prm = a.prm + (size_t)l * P_COUNT;
-    tail_smooth(a, sL, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true);
+    const size_t t0 = threadIdx.x, dt = tm.size();
+    tail_smooth(a, sL, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true, tm);
     const size_t N = (size_t)L.n * a.B;
-    for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+    for (size_t t = t0; t < N; t += dt)
       residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 0, 0, t);
-    __syncthreads();
+    tm.sync();
     const size_t Nc = (size_t)L.nc * a.B;
     if ((a.convR >> l) & 1u) {  // Phi_R per fine row, then the gather P^T
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
-        conv_r_el(L, (const T*)v.t[l], v.u2[l], a.B, prm, t);
-      __syncthreads();
-      for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
-        gather_el(L, (const T*)v.u2[l], v.f[l + 1], a.B, t);
+      for (size_t t = t0; t < N; t += dt) conv_r_el(L, (const T*)v.t[l], v.u2[l], a.B, prm, t);
+      tm.sync();
+      for (size_t t = t0; t < Nc; t += dt) gather_el(L, (const T*)v.u2[l], v.f[l + 1], a.B, t);
     } else {
-      for (size_t t = threadIdx.x; t < Nc; t += blockDim.x)
+      for (size_t t = t0; t < Nc; t += dt)
         restrict_el(L, (const T*)v.t[l], v.f[l + 1], a.B, prm, 0, t);
     }
-    __syncthreads();
+    tm.sync();
   }
-  if (a.cInv) {
-    for (size_t t = threadIdx.x; t < (size_t)a.nJ * a.B; t += blockDim.x)
-      coarse_inv_el(a.cInv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
-  } else {
-    coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, a.cwarps,
-                      ys);
+  {
+    const Team tm{a.tw[J - 1]};
+    if (tm.member()) {
+      if (a.cInv) {
+        for (size_t t = threadIdx.x; t < (size_t)a.nJ * a.B; t += tm.size())
+          coarse_inv_el(a.cInv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
+      } else {
+        coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B,
+                          min(a.cwarps, tm.W), ys);
+      }
+    }
   }
-  __syncthreads();
+  // ascent: each team first waits for the coarser levels' (sub-)team
   for (int l = J - 2; l >= lt; --l) {
+    const Team tm{a.tw[l]};
+    if (!tm.member()) continue;
+    tm.sync();
     const LV<T>& L = sL[l];
     const T* prm = a.prm + (size_t)l * P_COUNT;
+    const size_t t0 = threadIdx.x, dt = tm.size();
     const size_t N = (size_t)L.n * a.B;
     if ((a.convP >> l) & 1u) {  // P e_c per fine row, then Phi_P and the update
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
-        pe_el(L, (const T*)v.u[l + 1], v.t[l], a.B, t);
-      __syncthreads();
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      for (size_t t = t0; t < N; t += dt) pe_el(L, (const T*)v.u[l + 1], v.t[l], a.B, t);
+      tm.sync();
+      for (size_t t = t0; t < N; t += dt)
         prolong_conv_el(L, (const T*)v.t[l], (const T*)v.u[l], v.u[l], a.B, prm, t);
     } else {
-      for (size_t t = threadIdx.x; t < N; t += blockDim.x)
+      for (size_t t = t0; t < N; t += dt)
         prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], a.B, prm, 0, t);
     }
-    __syncthreads();
-    tail_smooth(a, sL, v, l, a.nu_post, false);
+    tm.sync();
+    tail_smooth(a, sL, v, l, a.nu_post, false, tm);
   }
+  __syncthreads();
   if (a.smem_vectors) {
     const size_t N = (size_t)a.L[lt].n * a.B;
     for (size_t t = threadIdx.x; t < N; t += blockDim.x) a.u[lt][t] = v.u[lt][t];

@@ -406,6 +406,7 @@ struct mg_ctx {
   int64_t launches = 0;
   // options (mg_set_option)
   int64_t opt_tail_work = 2048;  // rows x rhs at or below which levels run in k_tail
+  int opt_tail_teams = 1;  // k_tail levels by teams of warps, entries per thread (0: whole block)
   int opt_pdl = 1;               // programmatic dependent launch between kernels
   int opt_multi_rhs = 1;         // multi-rhs kernels: 0 off, 1 widest tile, else max tile
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
@@ -1043,6 +1044,21 @@ struct Issue {
     a.cU = c->cholU;
     a.cDinv = c->cholDinv;
     a.cInv = c->coarse_inv ? c->cholInv : nullptr;
+    // the team of a small level: about opt_tail_teams entries (row, rhs) per
+    // thread, a power of two of warps, never more warps than the finer
+    // level's team
+    int prev = 32;
+    for (int l = 0; l < mgk::kMaxLevels; ++l) {
+      int w = 32;
+      if (c->opt_tail_teams > 0 && l < c->J) {
+        const int64_t per_warp = 32 * (int64_t)c->opt_tail_teams;
+        const int64_t need = ((int64_t)L[l].n * B + per_warp - 1) / per_warp;
+        w = 1;
+        while (w < 32 && w < need) w *= 2;
+      }
+      a.tw[l] = std::min(w, prev);
+      prev = a.tw[l];
+    }
     // a recorded forward must leave every level's f and u in its checkpoint
     // buffers, so it keeps the small levels' vectors in global memory
     a.smem_vectors = fov == nullptr && uov == nullptr ? 1 : 0;
@@ -2020,6 +2036,11 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > (1 << 30))
         return c->fail(MG_ERR_INVALID, "mg_set_option: halo rows must be in [0, 2^30]");
       c->opt_halo_rows = value;
+      break;
+    case MG_OPT_TAIL_TEAMS:
+      if (value < 0 || value > 64)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: tail teams must be in [0, 64]");
+      c->opt_tail_teams = (int)value;
       break;
     case MG_OPT_COARSE_INVERSE:
       if (value != 0 && value != 1)

@@ -381,12 +381,15 @@ def test_launch_options_are_bitwise_neutral(prec, conv, nrhs):
     dt = torch.float64 if prec == 64 else torch.float32
     outs = []
     f4 = np.concatenate([p.f, 0.5 * p.f[:, ::-1]], axis=1)[:, :nrhs]
-    for tail, pdl, mrhs, halo in [(8192, 1, 1, 2048), (0, 1, 1, 2048), (8192, 0, 1, 2048),
-                                  (1 << 30, 1, 1, 2048), (8192, 1, 0, 2048), (0, 1, 0, 2048),
-                                  (8192, 1, 1, 0), (0, 1, 1, 256), (0, 1, 0, 50),
-                                  (0, 0, 1, 1 << 20)]:
+    for tail, pdl, mrhs, halo, teams in [(8192, 1, 1, 2048, 1), (0, 1, 1, 2048, 1),
+                                         (8192, 0, 1, 2048, 1), (1 << 30, 1, 1, 2048, 1),
+                                         (8192, 1, 0, 2048, 1), (0, 1, 0, 2048, 1),
+                                         (8192, 1, 1, 0, 1), (0, 1, 1, 256, 1), (0, 1, 0, 50, 1),
+                                         (0, 0, 1, 1 << 20, 1), (8192, 1, 1, 2048, 0),
+                                         (1 << 30, 1, 1, 2048, 0)]:
         S = Solver(Hp, prm, precision=prec, max_batch=4)
         S.set_option("tail_work", tail)
+        S.set_option("tail_teams", teams)
         S.set_option("pdl", pdl)
         S.set_option("multi_rhs", mrhs)
         S.set_option("halo_rows", halo)
