@@ -371,9 +371,28 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     substitutions, whose 2 n_{J-1} dependent FP64 steps
  *                     run on one SM per right-hand side).  Both forms agree
  *                     to a few units of rounding times the condition number.
- * MG_OPT_FCG_PRECOND, MG_OPT_FGMRES_FLOOR and MG_OPT_COARSE_INVERSE change
- * results (another preconditioner, other restart points, other rounding of
- * the coarsest solve); the others only launch shapes. */
+ *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1
+ *                     (default): FP32 vectors in phases of FCG(1) on the
+ *                     scaled correction equation, each phase ended by an FP64
+ *                     restart (u += 2^s e, the true residual f - A u in FP64,
+ *                     the test, a fresh direction); 0: FP64 vectors
+ *                     throughout, the FP32 cycle on the scaled residual.
+ *                     FP64 contexts ignore it.
+ *   MG_OPT_FCG_FLOOR  the phase of a right-hand side ends once its
+ *                     recurrence residual is below 10^-value times the
+ *                     phase's first (default 2; 0: no floor; at most 15), or
+ *                     once its scaled estimate is below tol ||f||, or at the
+ *                     last iteration.  A phase solves the system of the FP32
+ *                     operator, which differs from A by FP32 rounding: on
+ *                     ill-conditioned operators its true residual stops
+ *                     following the recurrence after a few digits, so deep
+ *                     floors waste steps (measured: 10^-2 best on the 3.1M-row
+ *                     anisotropic L-shape, 10^-1 .. 10^-3 within 10 % on the
+ *                     513^2 checkerboard).
+ * MG_OPT_FCG_PRECOND, MG_OPT_FGMRES_FLOOR, MG_OPT_COARSE_INVERSE,
+ * MG_OPT_FCG_FP32 and MG_OPT_FCG_FLOOR change results (another
+ * preconditioner, other restart points, other rounding of the coarsest
+ * solve, other vector precision); the others only launch shapes. */
 typedef enum {
   MG_OPT_TAIL_WORK = 0,
   MG_OPT_PDL = 1,
@@ -386,7 +405,9 @@ typedef enum {
   MG_OPT_SELL_HALO_THREADS = 8,
   MG_OPT_SELL_HALO_MAX_BYTES = 9,
   MG_OPT_COARSE_INVERSE = 10,
-  MG_OPT_TAIL_TEAMS = 11
+  MG_OPT_TAIL_TEAMS = 11,
+  MG_OPT_FCG_FP32 = 12,
+  MG_OPT_FCG_FLOOR = 13
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);
@@ -518,18 +539,25 @@ mg_status mg_setup_square(mg_ctx** out, int32_t N, int32_t J, int32_t slots, con
  * ordered on one stream. */
 mg_status mg_square_set_block(mg_ctx* ctx, int32_t block, const double* ke_dev, void* stream);
 
-/* Solves every block of a stacked context to its own tolerance:
+/* Solves the leading nblocks blocks of a stacked context (blocks
+ * 0 .. nblocks-1; 1 <= nblocks <= slots), each to its own tolerance:
  * ||f_b - A_b u_b||_2 / ||f_b||_2 < tol per block b, with mg_solve's methods
  * applied per block (precision 32: FP32 cycles inside FP64 refinement, the
  * residual of each block scaled by its own power of two; precision 64: the
- * stationary FP64 cycle), each block stopping as soon as it meets tol.  One
- * CUDA graph (a while node) per solve.  f_dev, u_dev: DEVICE FP64 level-0
- * stacks [slots * m_0]; u is the initial guess; a block whose f is zero is
- * idle (relres 0, no iterations).  iters_out, relres_out: host [slots] (may
- * be NULL).  Synchronises the stream.  Returns MG_NOT_CONVERGED if a block
- * missed tol within max_iter, MG_ERR_DIVERGED on a non-finite residual. */
-mg_status mg_solve_blocks(mg_ctx* ctx, const double* f_dev, double* u_dev, double tol,
-                          int32_t max_iter, int32_t* iters_out, double* relres_out, void* stream);
+ * stationary FP64 cycle), each block stopping as soon as it meets tol.  The
+ * leading blocks are the leading rows of every level, so the work is that of
+ * nblocks blocks, not of the whole context, and each block's result does not
+ * depend on nblocks (bitwise).  One CUDA graph (a while node) per solve,
+ * kept per (f, u, nblocks).  f_dev, u_dev: DEVICE FP64 level-0 stacks
+ * [slots * m_0], of which the leading nblocks * m_0 entries are read and
+ * written; u is the initial guess; a block whose f is zero is idle (relres 0,
+ * no iterations).  iters_out, relres_out: host [nblocks] (may be NULL).
+ * Synchronises the stream.  Returns MG_ERR_INVALID for an nblocks outside
+ * 1 .. slots, MG_NOT_CONVERGED if a block missed tol within max_iter,
+ * MG_ERR_DIVERGED on a non-finite residual. */
+mg_status mg_solve_blocks(mg_ctx* ctx, int32_t nblocks, const double* f_dev, double* u_dev,
+                          double tol, int32_t max_iter, int32_t* iters_out, double* relres_out,
+                          void* stream);
 
 /* ---------------------------------------------------------------------
  * Allocation-free entry point.  The paper has no counterpart: this is an

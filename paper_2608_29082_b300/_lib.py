@@ -17,7 +17,7 @@ STATUS = {0: "MG_OK", 1: "MG_NOT_CONVERGED", -1: "MG_ERR_INVALID", -2: "MG_ERR_O
 OPTIONS = {"tail_work": 0, "pdl": 1, "multi_rhs": 2, "device_loop": 3, "halo_rows": 4, "fcg_precond": 5,
            "fgmres_floor": 6, "sell_halo_rows": 7,
            "sell_halo_threads": 8, "sell_halo_max_bytes": 9, "coarse_inverse": 10,
-           "tail_teams": 11}
+           "tail_teams": 11, "fcg_fp32": 12, "fcg_floor": 13}
 OPS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "coarse": 4,
        "outer_residual": 5, "refine_residual": 6}
 
@@ -120,7 +120,8 @@ def lib() -> C.CDLL:
         "mg_setup_square": ([C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.POINTER(Params),
                              C.c_int32, vp], C.c_int),
         "mg_square_set_block": ([vp, C.c_int32, vp, vp], C.c_int),
-        "mg_solve_blocks": ([vp, vp, vp, C.c_double, C.c_int32, i32p, f64p, vp], C.c_int),
+        "mg_solve_blocks": ([vp, C.c_int32, vp, vp, C.c_double, C.c_int32, i32p, f64p, vp],
+                            C.c_int),
         "mg_last_error": ([vp, C.c_char_p, C.c_size_t], C.c_int),
         "mg_kernel_launches": ([vp], C.c_int64),
         "mg_destroy": ([vp], None),

@@ -48,9 +48,13 @@ constexpr int kMaxKR = 8;  // restriction children handled with a fixed trip cou
 // and values dval[k][n] (zero where row i has no entry on diagonal k).  The
 // graph neighbours of i are exactly its nonzero off-diagonals in either form,
 // visited in ascending column order, so both forms give the same arithmetic.
+// ld and ldc are the row strides of the [k][.] arrays (dval, p_idx, p_w with
+// ld; r_idx, r_w with ldc): n and nc, except in a view of the leading rows of
+// a stacked level, where they stay those of the whole level.
 template <class T>
 struct LV {
   int n, nc, KR;
+  int ld, ldc;
   int ndia;
   int doff[kMaxDia];
   const T* __restrict__ dval;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void prefetch_row(const LV<T>& L, int i) {
   if (L.ndia > 0) {
 #pragma unroll
     for (int k = 0; k < kMaxDia; ++k)
-      if (k < L.ndia) prefetch_l1(L.dval + (size_t)k * L.n + i);
+      if (k < L.ndia) prefetch_l1(L.dval + (size_t)k * L.ld + i);
   } else {
     prefetch_l1(L.sl_ptr + (i >> 5));
   }
@@ -113,17 +117,17 @@ __device__ __forceinline__ void prefetch_row(const LV<T>& L, int i) {
 template <class T>
 __device__ __forceinline__ void prefetch_p(const LV<T>& L, int i) {
   prefetch_l1(L.p_idx + i);
-  prefetch_l1(L.p_idx + (size_t)L.n + i);
+  prefetch_l1(L.p_idx + (size_t)L.ld + i);
   prefetch_l1(L.p_w + i);
-  prefetch_l1(L.p_w + (size_t)L.n + i);
+  prefetch_l1(L.p_w + (size_t)L.ld + i);
 }
 
 // Coarse row I's restriction gather list.
 template <class T>
 __device__ __forceinline__ void prefetch_r(const LV<T>& L, int I) {
   for (int k = 0; k < L.KR && k < kMaxKR; ++k) {
-    prefetch_l1(L.r_idx + (size_t)k * L.nc + I);
-    prefetch_l1(L.r_w + (size_t)k * L.nc + I);
+    prefetch_l1(L.r_idx + (size_t)k * L.ldc + I);
+    prefetch_l1(L.r_w + (size_t)k * L.ldc + I);
   }
 }
 
@@ -149,7 +153,7 @@ __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
 #pragma unroll
     for (int k = 0; k < kMaxDia; ++k) {
       if (k < L.ndia) {
-        const T v = L.dval[(size_t)k * L.n + i];
+        const T v = L.dval[(size_t)k * L.ld + i];
         const int c = min(max(i + L.doff[k], 0), L.n - 1);
         fn(c, v, v != T(0));
       }
@@ -201,10 +205,10 @@ __device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict_
 template <class T>
 __device__ __forceinline__ T prolong_at(const LV<T>& L, int j, const T* __restrict__ ec, int B,
                                         int b) {
-  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
+  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.ld + j];
   T v = T(0);
   if (a >= 0) v = L.p_w[j] * ec[(size_t)a * B + b];
-  if (c >= 0) v = fma(L.p_w[(size_t)L.n + j], ec[(size_t)c * B + b], v);
+  if (c >= 0) v = fma(L.p_w[(size_t)L.ld + j], ec[(size_t)c * B + b], v);
   return v;
 }
 
@@ -276,8 +280,8 @@ __device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict_
     T wk[kMaxKR];
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k) {
-      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.nc + I] : -1;
-      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.nc + I] : T(0);
+      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.ldc + I] : -1;
+      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.ldc + I] : T(0);
     }
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k) {
@@ -290,11 +294,11 @@ __device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict_
     }
   } else {
     for (int k = 0; k < L.KR; ++k) {
-      const int i = L.r_idx[(size_t)k * L.nc + I];
+      const int i = L.r_idx[(size_t)k * L.ldc + I];
       if (i < 0) break;
       T phi = w1 * r[(size_t)i * B + b];
       if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
-      acc = fma(L.r_w[(size_t)k * L.nc + I], phi, acc);
+      acc = fma(L.r_w[(size_t)k * L.ldc + I], phi, acc);
     }
   }
   fc[t] = acc;
@@ -348,17 +352,17 @@ __device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ 
     T wk[kMaxKR];
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k) {
-      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.nc + I] : -1;
-      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.nc + I] : T(0);
+      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.ldc + I] : -1;
+      wk[k] = k < L.KR ? L.r_w[(size_t)k * L.ldc + I] : T(0);
     }
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k)
       if (idx[k] >= 0) acc = fma(wk[k], phi[(size_t)idx[k] * B + b], acc);
   } else {
     for (int k = 0; k < L.KR; ++k) {
-      const int i = L.r_idx[(size_t)k * L.nc + I];
+      const int i = L.r_idx[(size_t)k * L.ldc + I];
       if (i < 0) break;
-      acc = fma(L.r_w[(size_t)k * L.nc + I], phi[(size_t)i * B + b], acc);
+      acc = fma(L.r_w[(size_t)k * L.ldc + I], phi[(size_t)i * B + b], acc);
     }
   }
   fc[t] = acc;
@@ -586,6 +590,7 @@ struct TailArgs {
   const double* cU;
   const double* cDinv;
   const double* cInv;  // explicit inverse of A_J (row-major), or NULL: substitutions
+  int cInvLd;          // its row stride
   int tw[kMaxLevels];  // warps of the team that runs level l (a power of two <= 32)
 };
 
@@ -625,26 +630,35 @@ struct TailVecs {
 
 __host__ __device__ inline size_t tail_align(size_t x) { return (x + 15) & ~size_t(15); }
 
+// Shared-memory bytes of nchunk rows of count elements whose global row
+// stride is ld: one block when the rows are contiguous (ld == count), else
+// rows padded to a multiple of 4 elements (smem_take_rows).
+template <class U>
+__host__ __device__ inline size_t rows_bytes(int count, int ld, int nchunk) {
+  if (ld == count) return tail_align((size_t)nchunk * count * sizeof(U));
+  return (size_t)nchunk * ((count + 3) & ~3) * sizeof(U);
+}
+
 // Shared-memory bytes of one small level: its four vectors (vec) and its
 // read-only arrays (mat): DIA values or SELL slices, diag, dinv, invdeg and,
 // above the coarsest level, the prolongation and restriction lists.
 template <class T>
-__host__ __device__ inline size_t tail_level_bytes(int n, int nc, int KR, int ndia, int nsl,
-                                                   int nent, int B, bool last, bool vec,
-                                                   bool mat) {
+__host__ __device__ inline size_t tail_level_bytes(const LV<T>& L, int nsl, int nent, int B,
+                                                   bool last, bool vec, bool mat) {
+  const int n = L.n, nc = L.nc;
   size_t s = 0;
   if (vec) s += 4 * tail_align((size_t)n * B * sizeof(T));
   if (mat) {
-    if (ndia > 0) {
-      s += tail_align((size_t)ndia * n * sizeof(T));
+    if (L.ndia > 0) {
+      s += rows_bytes<T>(n, L.ld, L.ndia);
     } else {
       s += tail_align((size_t)(nsl + 1) * sizeof(int)) + tail_align((size_t)nent * sizeof(int)) +
            tail_align((size_t)nent * sizeof(T));
     }
     s += 3 * tail_align((size_t)n * sizeof(T));
     if (!last) {
-      s += tail_align((size_t)2 * n * sizeof(int)) + tail_align((size_t)2 * n * sizeof(T));
-      s += tail_align((size_t)KR * nc * sizeof(int)) + tail_align((size_t)KR * nc * sizeof(T));
+      s += rows_bytes<int>(n, L.ld, 2) + rows_bytes<T>(n, L.ld, 2);
+      s += rows_bytes<int>(nc, L.ldc, L.KR) + rows_bytes<T>(nc, L.ldc, L.KR);
     }
   }
   return s;
@@ -656,8 +670,8 @@ template <class T>
 __host__ __device__ inline size_t tail_smem_bytes(const TailArgs<T>& a, int lt) {
   size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
   for (int l = lt; l < a.J; ++l)
-    off += tail_level_bytes<T>(a.L[l].n, a.L[l].nc, a.L[l].KR, a.L[l].ndia, a.nsl[l], a.nent[l],
-                               a.B, l == a.J - 1, a.smem_vectors != 0, a.smem_matrix != 0);
+    off += tail_level_bytes<T>(a.L[l], a.nsl[l], a.nent[l], a.B, l == a.J - 1,
+                               a.smem_vectors != 0, a.smem_matrix != 0);
   return off;
 }
 
@@ -692,23 +706,46 @@ __device__ __forceinline__ U* smem_take(unsigned char* base, size_t& off, const 
   return dst;
 }
 
+// smem_take of nchunk rows of count elements, row k at src + k * ld: one
+// copy when the rows are contiguous, else row by row into rows padded to a
+// multiple of 4 elements (16 bytes for 4- and 8-byte types).  ld_out is the
+// shared-memory row stride (the layout rows_bytes counts).
+template <class U>
+__device__ __forceinline__ U* smem_take_rows(unsigned char* base, size_t& off, const U* src,
+                                             int count, int ld, int nchunk, int& ld_out) {
+  if (ld == count) {
+    ld_out = count;
+    return smem_take(base, off, src, (size_t)nchunk * count);
+  }
+  const int lds = (count + 3) & ~3;
+  U* dst = (U*)(base + off);
+  for (int k = 0; k < nchunk; ++k) {
+    size_t o = off + (size_t)k * lds * sizeof(U);
+    smem_take(base, o, src + (size_t)k * ld, (size_t)count);
+  }
+  off += (size_t)nchunk * lds * sizeof(U);
+  ld_out = lds;
+  return dst;
+}
+
 // Offset of column j of a packed column-major lower triangle of order n.
 __device__ __forceinline__ size_t packed_col(int n, int j) {
   return (size_t)j * n - (size_t)j * (j - 1) / 2;
 }
 
-// u = A_J^{-1} f with the explicit FP64 inverse (row-major n x n, formed
-// on the host from the Cholesky factor): one thread per (row, rhs) output,
+// u = A_J^{-1} f with the explicit FP64 inverse (row-major n x n with row
+// stride ld, formed on the host from the Cholesky factor; a leading block of
+// it for the leading blocks of a stacked context): one thread per (row, rhs) output,
 // the products summed in column order.  Every output is independent, so the
 // step spreads over many SMs instead of running the 2n dependent steps of
 // the substitutions on one (B300's FP64 pipe makes those slow).
 template <class T>
-__device__ __forceinline__ void coarse_inv_el(const double* __restrict__ Ainv, int n,
+__device__ __forceinline__ void coarse_inv_el(const double* __restrict__ Ainv, int n, int ld,
                                               const T* __restrict__ f, T* __restrict__ u, int B,
                                               size_t t) {
   int i, b;
   split_rb(t, B, i, b);
-  const double* row = Ainv + (size_t)i * n;
+  const double* row = Ainv + (size_t)i * ld;
   double acc = 0.0;
 #pragma unroll 8
   for (int j = 0; j < n; ++j) acc = fma(row[j], (double)f[(size_t)j * B + b], acc);
@@ -719,12 +756,12 @@ constexpr int kCoarseInvThreads = 64;
 
 template <class T>
 __global__ void __launch_bounds__(kCoarseInvThreads)
-    k_coarse_inv(const double* __restrict__ Ainv, int n, const T* __restrict__ f,
+    k_coarse_inv(const double* __restrict__ Ainv, int n, int ld, const T* __restrict__ f,
                  T* __restrict__ u, int B) {
   pdl_wait();
   pdl_launch();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (size_t)n * B) coarse_inv_el(Ainv, n, f, u, B, t);
+  if (t < (size_t)n * B) coarse_inv_el(Ainv, n, ld, f, u, B, t);
 }
 
 // The same substitutions as coarse_chol_block with the factor staged in
@@ -846,7 +883,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     LV<T> S = G;
     if (a.smem_matrix) {
       if (G.ndia > 0) {
-        S.dval = smem_take(tail_smem, off, G.dval, (size_t)G.ndia * G.n);
+        S.dval = smem_take_rows(tail_smem, off, G.dval, G.n, G.ld, G.ndia, S.ld);
       } else {
         S.sl_ptr = smem_take(tail_smem, off, G.sl_ptr, (size_t)a.nsl[l] + 1);
         S.col = smem_take(tail_smem, off, G.col, (size_t)a.nent[l]);
@@ -856,10 +893,10 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
       S.dinv = smem_take(tail_smem, off, G.dinv, (size_t)G.n);
       S.invdeg = smem_take(tail_smem, off, G.invdeg, (size_t)G.n);
       if (l < J - 1) {
-        S.p_idx = smem_take(tail_smem, off, G.p_idx, (size_t)2 * G.n);
-        S.p_w = smem_take(tail_smem, off, G.p_w, (size_t)2 * G.n);
-        S.r_idx = smem_take(tail_smem, off, G.r_idx, (size_t)G.KR * G.nc);
-        S.r_w = smem_take(tail_smem, off, G.r_w, (size_t)G.KR * G.nc);
+        S.p_idx = smem_take_rows(tail_smem, off, G.p_idx, G.n, G.ld, 2, S.ld);
+        S.p_w = smem_take_rows(tail_smem, off, G.p_w, G.n, G.ld, 2, S.ld);
+        S.r_idx = smem_take_rows(tail_smem, off, G.r_idx, G.nc, G.ldc, G.KR, S.ldc);
+        S.r_w = smem_take_rows(tail_smem, off, G.r_w, G.nc, G.ldc, G.KR, S.ldc);
       }
     }
     if (threadIdx.x == 0) sL[l] = S;
@@ -905,7 +942,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     if (tm.member()) {
       if (a.cInv) {
         for (size_t t = threadIdx.x; t < (size_t)a.nJ * a.B; t += tm.size())
-          coarse_inv_el(a.cInv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
+          coarse_inv_el(a.cInv, a.nJ, a.cInvLd, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
       } else {
         coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B,
                           min(a.cwarps, tm.W), ys);

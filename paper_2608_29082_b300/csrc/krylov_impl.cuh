@@ -1,14 +1,17 @@
-// mg_solve_fcg: flexible conjugate gradients in FP64 with the context's
-// learnable V-cycle (FP32 or FP64) as a variable preconditioner.  Included at
-// the end of mg_api.cu (same translation unit).
+// mg_solve_fcg: flexible conjugate gradients with the context's learnable
+// V-cycle (FP32 or FP64) as a variable preconditioner.  Included at the end
+// of mg_api.cu (same translation unit).
 //
 // Notay's flexible CG with one stored direction, per right-hand side:
 //   r = f - A u, z = M(r), p = z, q = A p, alpha = (p, r)/(p, q)
 //   repeat: u += alpha p, r -= alpha q, test ||r||/||f|| < tol,
 //           z = M(r), beta = -(z, q)/(p, q), p = z + beta p,
 //           q = A p, alpha = (p, r)/(p, q)
-// The FP32 cycle sees r scaled by an exact power of two (2^-ilogb||r||).
-// One CUDA graph holds the set-up and a while-node around the iteration.
+// fcg64: FP64 vectors; an FP32 cycle sees r scaled by an exact power of two
+// (2^-ilogb||r||).  fcg32 (precision-32 contexts, the default there): the
+// same recurrence in FP32 on the scaled correction equation, in phases
+// ended by FP64 restarts that form and test the true residual.  One CUDA
+// graph holds the set-up and a while-node around the iteration.
 
 namespace {
 
@@ -36,19 +39,120 @@ mg_status fcg_buffers(mg_ctx* c) {
   return MG_OK;
 }
 
+mg_status fcg32_buffers(mg_ctx* c) {
+  if (c->k32_p) return MG_OK;
+  const size_t v = (size_t)c->n[0] * c->maxB * sizeof(float);
+  for (float** q : {&c->k32_p, &c->k32_q, &c->k32_e}) MG_CUDA(cudaMalloc(q, v));
+  MG_CUDA(cudaMalloc(&c->k32_small, (size_t)4 * c->maxB * sizeof(double) +
+                                        (size_t)(2 * c->maxB + 1) * sizeof(int)));
+  return MG_OK;
+}
+
+// mg_solve_fcg of a precision-32 context with FP32 vectors: phases of FCG(1)
+// on the scaled correction equation A e = 2^-s r in FP32, ended per
+// right-hand side by an FP64 restart (kernels in krylov.cuh).  One graph: the
+// first restart (r = f - A u, the test) before a while node whose body is one
+// FP32 step, the phase test and the (predicated) restart.
+mg_status fcg32(mg_ctx* c, const double* f, double* u, int B, cudaStream_t s) {
+  mg_status st = fcg32_buffers(c);
+  if (st != MG_OK) return st;
+  const int n0 = c->n[0];
+  const int bt = std::min(B, 32);
+  const int nblk = (n0 + mgk::kRedRows - 1) / mgk::kRedRows;
+  const dim3 rgrid(nblk, (B + bt - 1) / bt), rblock(mgk::kRedRows * bt);
+  const int nb32 = (n0 + mgk::kF32BlockRows - 1) / mgk::kF32BlockRows;
+  const dim3 g32(nb32, (B + bt - 1) / bt);
+  const LV<double> L0 = c->d64[0].view();
+  const LV<float> L32 = c->d32[0].view();
+  double* alpha = (double*)c->k32_small;
+  double* beta = alpha + c->maxB;
+  double* pq = beta + c->maxB;
+  double* rr0 = pq + c->maxB;
+  int* fresh = (int*)(rr0 + c->maxB);
+  int* restart = fresh + c->maxB;
+  int* any = restart + c->maxB;
+  float* r = c->rhat32;  // the phase's recurrence residual (the cycle's input)
+  float* z = c->c32;     // the preconditioned residual (the cycle's output)
+  // the FP64 restart for the right-hand sides whose phase ends: u += 2^s e,
+  // r = f - A u, the test, rhat = 2^-s r, a fresh direction
+  auto restart_step = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
+    is.launch(mgk::k32_fold, g32, rblock, 0, u, c->k32_e, (const int*)c->sexp_prev,
+              (const int*)restart, (const int*)any, n0, B);
+    is.launch(mgk::k_resid64_restart, rgrid, rblock, 0, L0, f, (const double*)u, r,
+              (const int*)c->sexp, (const int*)restart, (const int*)any, B, c->partial);
+    is.launch(mgk::k_reduce_if, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, B,
+              (const int*)any, c->rsum);
+    is.launch(mgk::k32_restart_check, dim3(1), dim3(kThreads), 0, (const double*)c->rsum,
+              (const double*)c->fsum, B, (const double*)c->tol_dev, c->active, c->relres, c->sexp,
+              c->sexp_prev, rr0, fresh, restart, any, c->state, inc, h, cond);
+  };
+  auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    Issue<double> is{c, c->d64, c->prm64, cs, B};
+    is.launch(mgk::k_sumsq64, rgrid, rblock, 0, f, n0, B, c->partial);
+    is.launch(mgk::k_reduce, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nblk, B,
+              c->fsum);
+    is.launch(mgk::k32_init, dim3((B + kThreads - 1) / kThreads), dim3(kThreads), 0,
+              (const double*)c->fsum, B, c->active, c->iters, c->sexp, restart, any);
+    cudaMemsetAsync(c->k32_e, 0, (size_t)n0 * B * sizeof(float), cs);
+    restart_step(is, h, 0, cond);
+    return is.nk;
+  };
+  auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
+    int nk = 0;
+    Issue<float> is{c, c->d32, c->prm32, cs, B};
+    if (c->opt_fcg_precond == 1)
+      is.fmg(r, z);
+    else
+      is.vcycle(r, z, true);
+    // beta from (z, q_prev), the direction, q = A p and alpha, the update
+    is.launch(mgk::k32_dot, g32, rblock, 0, (const float*)z, (const float*)c->k32_q, n0, B,
+              c->partial);
+    is.launch(mgk::k32_reduce_beta, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nb32,
+              B, (const double*)pq, (const int*)fresh, beta);
+    is.launch(mgk::k32_direction, g32, rblock, 0, c->k32_p, (const float*)z, (const double*)beta,
+              (const int*)fresh, n0, B);
+    // q = A p on right-hand-side tiles of BV columns (BV | B)
+    const int bv = B % 8 == 0 ? 8 : B % 4 == 0 ? 4 : B % 2 == 0 ? 2 : 1;
+    const dim3 tblock(mgk::kRedRows * bt / bv);
+    auto spmv = [&](auto kern) {
+      is.launch(kern, g32, tblock, 0, L32, (const float*)c->k32_p, (const float*)r, c->k32_q, B,
+                c->partial);
+    };
+    if (bv == 8)
+      spmv(mgk::k32_spmv_dots_mb<8>);
+    else if (bv == 4)
+      spmv(mgk::k32_spmv_dots_mb<4>);
+    else if (bv == 2)
+      spmv(mgk::k32_spmv_dots_mb<2>);
+    else
+      spmv(mgk::k32_spmv_dots_mb<1>);
+    is.launch(mgk::k32_reduce_alpha, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nb32,
+              B, (const int*)c->active, alpha, pq, fresh);
+    is.launch(mgk::k32_fcg_update, g32, rblock, 0, c->k32_e, r, (const float*)c->k32_p,
+              (const float*)c->k32_q, (const double*)alpha, (const int*)c->active, n0, B,
+              c->partial);
+    is.launch(mgk::k32_phase_check, dim3(B), dim3(kThreads), 0, (const double*)c->partial, nb32,
+              B, (const int*)c->active, (const double*)rr0, (const double*)c->fsum,
+              (const int*)c->sexp_prev, (const double*)c->tol_dev, (const int*)c->state,
+              c->iters, restart, any);
+    nk += is.nk;
+    Issue<double> is2{c, c->d64, c->prm64, cs, B};
+    restart_step(is2, h, 1, cond);
+    return nk + is2.nk;
+  };
+  return run_loop(c, 45, f, u, B, s, "mg_solve_fcg", pre, body,
+                  [](cudaStream_t) { return 0; }, false);
+}
+
 }  // namespace
 
-extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
-                                  int32_t max_iter, int32_t* iters_out, double* relres_out,
-                                  void* stream) {
-  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve_fcg: ctx is NULL");
-  if (!f || !u || B < 1 || B > c->maxB || max_iter < 0 || !(tol > 0.0))
-    return c->fail(MG_ERR_INVALID, "mg_solve_fcg: bad arguments");
-  if ((const void*)f == (const void*)u) return c->fail(MG_ERR_INVALID, "mg_solve_fcg: f and u alias");
-  cudaStream_t s = (cudaStream_t)stream;
-  mg_status st = sync_params(c, s);
-  if (st != MG_OK) return st;
-  st = fcg_buffers(c);
+namespace {
+
+// mg_solve_fcg with FP64 vectors (FP64 contexts, and precision-32 contexts
+// with MG_OPT_FCG_FP32 = 0): the FP32 cycle, if any, on the scaled residual.
+mg_status fcg64(mg_ctx* c, const double* f, double* u, int B, double tol, int max_iter,
+                cudaStream_t s) {
+  mg_status st = fcg_buffers(c);
   if (st != MG_OK) return st;
   const int n0 = c->n[0];
   const int bt = std::min((int)B, 32);  // reduction tiling (kernels.cuh red_tile)
@@ -154,7 +258,32 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
               (const double*)c->fsum, (int)B, c->relres);
     return is.nk;
   };
-  st = run_loop(c, 40, f, u, (int)B, s, "mg_solve_fcg", pre, body, post, true);
+  return run_loop(c, 40, f, u, B, s, "mg_solve_fcg", pre, body, post, true);
+}
+
+}  // namespace
+
+extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t B, double tol,
+                                  int32_t max_iter, int32_t* iters_out, double* relres_out,
+                                  void* stream) {
+  if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve_fcg: ctx is NULL");
+  if (!f || !u || B < 1 || B > c->maxB || max_iter < 0 || !(tol > 0.0))
+    return c->fail(MG_ERR_INVALID, "mg_solve_fcg: bad arguments");
+  if ((const void*)f == (const void*)u) return c->fail(MG_ERR_INVALID, "mg_solve_fcg: f and u alias");
+  cudaStream_t s = (cudaStream_t)stream;
+  mg_status st = sync_params(c, s);
+  if (st != MG_OK) return st;
+  if (c->prec == 32 && c->opt_fcg_fp32) {
+    const double fl = c->opt_fcg_floor > 0 ? std::pow(10.0, -c->opt_fcg_floor) : 0.0;
+    c->solve_ctl[0] = tol;
+    c->solve_ctl[1] = (double)max_iter;
+    c->solve_ctl[2] = fl * fl;
+    MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 3 * sizeof(double), cudaMemcpyHostToDevice,
+                            s));
+    st = fcg32(c, f, u, (int)B, s);
+  } else {
+    st = fcg64(c, f, u, (int)B, tol, max_iter, s);
+  }
   if (st != MG_OK) return st;
   mg_status result = MG_OK;
   if (c->h_state[1])

@@ -68,6 +68,9 @@ int g_layout_policy = 0;
 template <class T>
 struct DevLevel {
   int n = 0, nc = 0, KR = 0, nsl = 0, ndia = 0;
+  // row strides of the [k][.] arrays when they differ from n / nc (a view of
+  // the leading blocks of a stacked level; 0: n / nc)
+  int ld = 0, ldc = 0;
   int doff[mgk::kMaxDia] = {0};
   size_t nent = 0;
   int *sl_ptr = nullptr, *col = nullptr, *p_idx = nullptr, *r_idx = nullptr;
@@ -86,6 +89,8 @@ struct DevLevel {
     LV<T> v;
     v.n = n;
     v.nc = nc;
+    v.ld = ld ? ld : n;
+    v.ldc = ldc ? ldc : nc;
     v.KR = KR;
     v.ndia = ndia;
     for (int k = 0; k < mgk::kMaxDia; ++k) v.doff[k] = doff[k];
@@ -369,6 +374,11 @@ struct mg_ctx {
   // flexible-CG workspace (allocated on first use): r, z, p, q [n0][maxB]
   double *k_r = nullptr, *k_z = nullptr, *k_p = nullptr, *k_q = nullptr;
   double *k_partial = nullptr, *k_small = nullptr;
+  // FCG with FP32 vectors (precision-32 contexts): p, q, e [n0][maxB] in
+  // FP32 (r and z are rhat32 and c32), per-rhs alpha, beta, (p, q), rr0
+  // (double) and fresh, restart flags and the any-restart flag (int)
+  float *k32_p = nullptr, *k32_q = nullptr, *k32_e = nullptr;
+  void* k32_small = nullptr;
   // flexible GMRES workspace (mg_solve_fgmres), for restart length gm_m:
   // basis and directions in the context precision (gm_V, gm_Z: void), an
   // FP32 zero vector (the right-hand side of w = 0 - A z), per-rhs cycle ends
@@ -397,8 +407,8 @@ struct mg_ctx {
       *state = nullptr;
   float *c32 = nullptr, *rhat32 = nullptr;
   int* h_state = nullptr;  // pinned [2]
-  double* tol_dev = nullptr;      // device [2]: tol, max_iter
-  double solve_ctl[2] = {0, 0};   // host staging of tol_dev
+  double* tol_dev = nullptr;      // device [3]: tol, max_iter, and a loop's own bound
+  double solve_ctl[3] = {0, 0, 0};  // host staging of tol_dev
   double *hf = nullptr, *hu = nullptr;  // device buffers for mg_solve_host
   cudaStream_t cap = nullptr;
   std::map<std::tuple<int, const void*, const void*, int, uint32_t>, GraphEntry> graphs;
@@ -412,6 +422,8 @@ struct mg_ctx {
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
   int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
   int opt_fgmres_floor = 4;      // FP32 FGMRES cycle floor, 10^-value (0: none)
+  int opt_fcg_fp32 = 1;          // precision-32 FCG: 1 FP32 vectors + FP64 restarts, 0 FP64
+  int opt_fcg_floor = 2;         // its phase floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
   int opt_sell_halo_rows = 0;  // rows per tile of the halo-fused SELL steps (0: unfused)
   int opt_sell_halo_threads = 256;  // threads per block of those steps
@@ -976,17 +988,23 @@ struct Issue {
     }
   }
 
+  // rows of the coarsest level in this issue's view (fewer than the
+  // context's in a view of the leading blocks of a stacked context, which
+  // always solves with the explicit inverse)
+  int rowsJ() const { return L[c->J - 1].n; }
+
   int coarse_warps(int cap) const {
-    return std::max(1, std::min(std::min(B, cap), 6144 / std::max(1, c->nJ)));
+    return std::max(1, std::min(std::min(B, cap), 6144 / std::max(1, rowsJ())));
   }
 
   void coarse(const T* f, T* u) {
-    const size_t nJ = (size_t)c->nJ;
+    const size_t nJ = (size_t)rowsJ();
     if (c->coarse_inv) {  // one FP64 dot per (row, rhs), spread over SMs
       pre(MG_K_COARSE_CHOL, c->J - 1);
       launch(mgk::k_coarse_inv<T>,
              dim3((unsigned)((nJ * B + mgk::kCoarseInvThreads - 1) / mgk::kCoarseInvThreads)),
-             dim3(mgk::kCoarseInvThreads), 0, (const double*)c->cholInv, c->nJ, f, u, B);
+             dim3(mgk::kCoarseInvThreads), 0, (const double*)c->cholInv, (int)nJ, c->nJ, f, u,
+             B);
       post();
       return;
     }
@@ -1022,7 +1040,7 @@ struct Issue {
     a.B = B;
     a.nu_pre = c->nu_pre;
     a.nu_post = c->nu_post;
-    a.nJ = c->nJ;
+    a.nJ = rowsJ();
     a.cwarps = coarse_warps(32);
     a.lt_zero = (int)u0_zero;
     for (int l = 0; l < c->J; ++l) {
@@ -1044,6 +1062,7 @@ struct Issue {
     a.cU = c->cholU;
     a.cDinv = c->cholDinv;
     a.cInv = c->coarse_inv ? c->cholInv : nullptr;
+    a.cInvLd = c->nJ;
     // the team of a small level: about opt_tail_teams entries (row, rhs) per
     // thread, a power of two of warps, never more warps than the finer
     // level's team
@@ -1071,7 +1090,7 @@ struct Issue {
   int tail_level() const {
     if (c->opt_tail_work <= 0 || c->J > mgk::kMaxLevels || c->cheb_K > 0) return c->J - 1;
     int lt = c->J - 1;
-    while (lt > 0 && (int64_t)c->n[lt - 1] * B <= c->opt_tail_work) --lt;
+    while (lt > 0 && (int64_t)L[lt - 1].n * B <= c->opt_tail_work) --lt;
     if (lt == c->J - 1) return lt;
     mgk::TailArgs<T> a;
     tail_args(a, nullptr, nullptr, false);
@@ -1365,7 +1384,8 @@ extern "C" void mg_destroy(mg_ctx* c) {
   for (auto& L : c->d32) free_level(L);
   for (void* p : {(void*)c->cholP, (void*)c->cholInv, (void*)c->sq_scratch, c->blk_state,
                   (void*)c->k_r, (void*)c->k_z, (void*)c->k_p, (void*)c->k_q,
-                  (void*)c->k_partial, (void*)c->k_small, (void*)c->gm_V, (void*)c->gm_Z,
+                  (void*)c->k_partial, (void*)c->k_small, (void*)c->k32_p, (void*)c->k32_q,
+                  (void*)c->k32_e, c->k32_small, (void*)c->gm_V, (void*)c->gm_Z,
                   (void*)c->gm_small, (void*)c->gm_h, (void*)c->gm_vec, (void*)c->gm_partial,
                   (void*)c->gm_zero32, (void*)c->gm_done, c->cheb_dev})
     if (p) cudaFree(p);
@@ -1589,7 +1609,7 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   for (int** q : {&c->active, &c->iters, &c->sexp, &c->sexp_prev})
     if ((e = cudaMalloc(q, maxB * sizeof(int))) != cudaSuccess) return bail(e);
   if ((e = cudaMalloc(&c->state, 4 * sizeof(int))) != cudaSuccess) return bail(e);
-  if ((e = cudaMalloc(&c->tol_dev, 2 * sizeof(double))) != cudaSuccess) return bail(e);
+  if ((e = cudaMalloc(&c->tol_dev, 3 * sizeof(double))) != cudaSuccess) return bail(e);
   if ((e = cudaMallocHost(&c->h_state, 4 * sizeof(int))) != cudaSuccess) return bail(e);
   if (precision == 64) {
     if ((e = cudaMalloc(&c->w64, v64)) != cudaSuccess) return bail(e);
@@ -2031,6 +2051,16 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > 15)
         return c->fail(MG_ERR_INVALID, "mg_set_option: FGMRES floor must be in [0, 15]");
       c->opt_fgmres_floor = (int)value;
+      break;
+    case MG_OPT_FCG_FP32:
+      if (value != 0 && value != 1)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: FCG FP32 must be 0 or 1");
+      c->opt_fcg_fp32 = (int)value;
+      break;
+    case MG_OPT_FCG_FLOOR:
+      if (value < 0 || value > 15)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: FCG floor must be in [0, 15]");
+      c->opt_fcg_floor = (int)value;
       break;
     case MG_OPT_HALO_ROWS:
       if (value < 0 || value > (1 << 30))

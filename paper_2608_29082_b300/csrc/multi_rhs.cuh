@@ -303,9 +303,9 @@ __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __rest
   for (int b = 0; b < BV; ++b) acc[b] = T(0);
   const T w1 = prm[P_WR1];
   for (int k = 0; k < L.KR; ++k) {
-    const int c = L.r_idx[(size_t)k * L.nc + i];
+    const int c = L.r_idx[(size_t)k * L.ldc + i];
     if (c < 0) break;
-    const T w = L.r_w[(size_t)k * L.nc + i];
+    const T w = L.r_w[(size_t)k * L.ldc + i];
     T xv[BV];
     ldg<T, BV>(x, (size_t)c * B + b0, xv);
 #pragma unroll
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __rest
 template <class T, int BV>
 __device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __restrict__ ec,
                                               int B, int b0, T (&v)[BV]) {
-  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.n + j];
+  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.ld + j];
 #pragma unroll
   for (int b = 0; b < BV; ++b) v[b] = T(0);
   if (a >= 0) {
@@ -331,7 +331,7 @@ __device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __
   if (c >= 0) {
     T e[BV];
     ldg<T, BV>(ec, (size_t)c * B + b0, e);
-    const T w = L.p_w[(size_t)L.n + j];
+    const T w = L.p_w[(size_t)L.ld + j];
 #pragma unroll
     for (int b = 0; b < BV; ++b) v[b] = fma(w, e[b], v[b]);
   }

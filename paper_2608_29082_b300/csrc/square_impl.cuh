@@ -223,45 +223,64 @@ extern "C" mg_status mg_square_set_block(mg_ctx* c, int32_t block, const double*
   return MG_OK;
 }
 
-extern "C" mg_status mg_solve_blocks(mg_ctx* c, const double* f, double* u, double tol,
-                                     int32_t max_iter, int32_t* iters_out, double* relres_out,
-                                     void* stream) {
+extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f, double* u,
+                                     double tol, int32_t max_iter, int32_t* iters_out,
+                                     double* relres_out, void* stream) {
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_solve_blocks: ctx is NULL");
   if (c->sq_slots <= 0) return c->fail(MG_ERR_INVALID, "mg_solve_blocks: not a square context");
-  if (!f || !u || max_iter < 0 || !(tol > 0.0))
+  if (!f || !u || max_iter < 0 || !(tol > 0.0) || nblocks < 1 || nblocks > c->sq_slots)
     return c->fail(MG_ERR_INVALID, "mg_solve_blocks: bad arguments");
   if ((const void*)f == (const void*)u) return c->fail(MG_ERR_INVALID, "mg_solve_blocks: f and u alias");
+  if (!c->coarse_inv) return c->fail(MG_ERR_INVALID, "mg_solve_blocks: no coarsest inverse");
   cudaStream_t s = (cudaStream_t)stream;
   mg_status st = sync_params(c, s);
   if (st != MG_OK) return st;
-  const int S = c->sq_slots;
-  const int n0 = c->n[0];
-  const int m = n0 / S;
+  // The leading S of the context's blocks: at every level they are its
+  // leading rows, so the cycle runs on views of the levels with fewer rows
+  // and the strides of the whole level (blocks never couple).
+  const int S = nblocks;
+  const int m = c->n[0] / c->sq_slots;
+  const int n0 = m * S;
+  auto lead = [&](auto& all) {
+    auto v = all;
+    if (S == c->sq_slots) return v;
+    for (auto& D : v) {
+      D.ld = D.n;
+      D.ldc = D.nc;
+      D.n = D.n / c->sq_slots * S;
+      D.nc = D.nc / c->sq_slots * S;
+    }
+    return v;
+  };
+  std::vector<DevLevel<float>> v32 = lead(c->d32);
+  std::vector<DevLevel<double>> v64 = lead(c->d64);
   const dim3 bgrid((unsigned)((m + kThreads - 1) / kThreads), (unsigned)S);
   const int nchunk = (int)bgrid.x;
-  const LV<double> L0 = c->d64[0].view();
+  const LV<double> L0 = v64[0].view();
   const bool p32 = c->prec == 32;
   c->solve_ctl[0] = tol;
   c->solve_ctl[1] = (double)max_iter;
   MG_CUDA(cudaMemcpyAsync(c->tol_dev, c->solve_ctl, 2 * sizeof(double), cudaMemcpyHostToDevice, s));
   if ((int64_t)nchunk * S > (int64_t)c->nblk_max * c->maxB)
     return c->fail(MG_ERR_INVALID, "mg_solve_blocks: partial-sum workspace too small");
-  if (S > c->maxB_blocks) {  // per-block state arrays: active, iters, sexp, norms
-    for (void* q : {(void*)c->blk_state})
-      if (q) cudaFree(q);
-    c->blk_state = nullptr;
-    MG_CUDA(cudaMalloc(&c->blk_state, (size_t)S * (4 * sizeof(int) + 3 * sizeof(double))));
-    c->maxB_blocks = S;
+  // per-block state arrays (active, iters, sexp, norms), allocated once for
+  // all the context's blocks: the captured graphs of every block count keep
+  // these pointers
+  if (!c->blk_state) {
+    MG_CUDA(cudaMalloc(&c->blk_state,
+                       (size_t)c->sq_slots * (4 * sizeof(int) + 3 * sizeof(double))));
+    c->maxB_blocks = c->sq_slots;
   }
   // per-block state in its own arrays (the context's per-rhs arrays are
   // sized for one column)
+  const int SA = c->sq_slots;
   int* active = (int*)c->blk_state;
-  int* iters = active + S;
-  int* sexp = iters + S;
-  int* sexp_prev = sexp + S;
-  double* rsum = (double*)(sexp_prev + S);
-  double* fsum = rsum + S;
-  double* relres = fsum + S;
+  int* iters = active + SA;
+  int* sexp = iters + SA;
+  int* sexp_prev = sexp + SA;
+  double* rsum = (double*)(sexp_prev + SA);
+  double* fsum = rsum + SA;
+  double* relres = fsum + SA;
   auto check = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
     is.launch(mgk::k_blk_resid64, bgrid, dim3(kThreads), 0, L0, f, (const double*)u,
               p32 ? c->rhat32 : (float*)nullptr, (const int*)sexp, m, S, c->partial);
@@ -279,7 +298,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, const double* f, double* u, doub
     }
   };
   auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
-    Issue<double> is{c, c->d64, c->prm64, cs, 1};
+    Issue<double> is{c, v64, c->prm64, cs, 1};
     is.launch(mgk::k_blk_sumsq, bgrid, dim3(kThreads), 0, f, m, S, c->partial);
     is.launch(mgk::k_reduce, dim3(S), dim3(kThreads), 0, (const double*)c->partial, nchunk, S,
               fsum);
@@ -291,16 +310,16 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, const double* f, double* u, doub
   auto body = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
     int nk = 0;
     if (p32) {
-      Issue<float> is{c, c->d32, c->prm32, cs, 1};
+      Issue<float> is{c, v32, c->prm32, cs, 1};
       is.vcycle(c->rhat32, c->c32, true);
       is.launch(mgk::k_blk_refine_update, grid_for((size_t)n0), dim3(kThreads), 0, u,
                 (const float*)c->c32, (const int*)sexp_prev, (const int*)active, m, S, iters);
       nk += is.nk;
-      Issue<double> is2{c, c->d64, c->prm64, cs, 1};
+      Issue<double> is2{c, v64, c->prm64, cs, 1};
       check(is2, h, 1, cond);
       nk += is2.nk;
     } else {
-      Issue<double> is{c, c->d64, c->prm64, cs, 1};
+      Issue<double> is{c, v64, c->prm64, cs, 1};
       is.launch(mgk::k_copy<double>, grid_for((size_t)n0), dim3(kThreads), 0, (const double*)u,
                 c->w64, (size_t)n0);
       is.vcycle(f, c->w64, false);
@@ -311,7 +330,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, const double* f, double* u, doub
     }
     return nk;
   };
-  st = run_loop(c, 60, f, u, 1, s, "mg_solve_blocks", pre, body,
+  st = run_loop(c, 60, f, u, S, s, "mg_solve_blocks", pre, body,
                 [](cudaStream_t) { return 0; }, false);
   if (st != MG_OK) return st;
   mg_status result = MG_OK;

@@ -13,7 +13,9 @@ size class loops:
      mg_square_set_block) and clear the slot's iterate.  A new context is
      created only while the device budget allows it; under memory pressure
      idle contexts (of any class) are evicted;
-  2. tick: one mg_solve_blocks call per context with occupied slots runs
+  2. tick: one mg_solve_blocks call per context with occupied slots (over its
+     leading blocks up to the last occupied one; admission fills the lowest
+     free slot) runs
      `iters_per_tick` FP64-refinement iterations (FP32 learned V-cycles) on
      all of its requests at once, each block masked and tested on its own;
   3. retire the slots whose relative residual met the tolerance.
@@ -97,10 +99,20 @@ class BatchContext:
         return sum(r is not None for r in self.req)
 
     def free_slot(self) -> int:
+        """The lowest free slot: occupied slots stay packed towards the front,
+        so a tick iterates the leading blocks only (lead)."""
         for k, r in enumerate(self.req):
             if r is None:
                 return k
         return -1
+
+    @property
+    def lead(self) -> int:
+        """Leading blocks a tick iterates: up to the last occupied slot."""
+        for k in range(self.S - 1, -1, -1):
+            if self.req[k] is not None:
+                return k + 1
+        return 0
 
     def block(self, x: torch.Tensor, k: int) -> torch.Tensor:
         return x[k * self.m:(k + 1) * self.m]
@@ -187,7 +199,8 @@ class ClassWorker(threading.Thread):
         for ctx in list(S.contexts[self.klass].values()):
             if ctx.busy == 0:
                 continue
-            info = ctx.batch.solve(ctx.f, ctx.u, tol=S.tol, max_iter=S.iters_per_tick)
+            info = ctx.batch.solve(ctx.f, ctx.u, tol=S.tol, max_iter=S.iters_per_tick,
+                                   nblocks=ctx.lead)
             ctx.last_used = time.perf_counter()
             for k, r in enumerate(ctx.req):
                 if r is None:

@@ -70,18 +70,22 @@ class SquareBatch:
                                              _stream_handle()), self.ctx)
 
     def solve(self, f: torch.Tensor, u: torch.Tensor, tol: float = 1e-8,
-              max_iter: int = 100) -> SolveInfo:
-        """f, u: device FP64 stacks [slots * m] (u: initial guess, updated)."""
+              max_iter: int = 100, nblocks: int | None = None) -> SolveInfo:
+        """f, u: device FP64 stacks [slots * m] (u: initial guess, updated).
+        Only the leading `nblocks` blocks (all if None) are iterated; the
+        returned counts and residuals of the others are zero."""
         for x, nm in ((f, "f"), (u, "u")):
             if x.device != self.device or x.dtype != torch.float64 or not x.is_contiguous() \
                     or x.numel() != self.slots * self.m:
                 raise ValueError(f"{nm}: expected a contiguous FP64 stack of "
                                  f"{self.slots * self.m} values on {self.device}")
+        k = self.slots if nblocks is None else int(nblocks)
         iters = np.zeros(self.slots, dtype=np.int32)
         relres = np.zeros(self.slots)
-        st = self.lib.mg_solve_blocks(self.ctx, C.c_void_p(f.data_ptr()), C.c_void_p(u.data_ptr()),
-                                      float(tol), int(max_iter), L.ptr(iters, L.i32p),
-                                      L.ptr(relres, L.f64p), _stream_handle())
+        st = self.lib.mg_solve_blocks(self.ctx, k, C.c_void_p(f.data_ptr()),
+                                      C.c_void_p(u.data_ptr()), float(tol), int(max_iter),
+                                      L.ptr(iters, L.i32p), L.ptr(relres, L.f64p),
+                                      _stream_handle())
         L.check(st, self.ctx, allow=(L.MG_OK, L.MG_NOT_CONVERGED))
         return SolveInfo(st, iters, relres)
 

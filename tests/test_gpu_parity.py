@@ -319,18 +319,72 @@ def test_fcg_reaches_tolerance_with_fewer_iterations(name, prec):
     assert info.iters.max() <= info_r.iters.max()
 
 
-def test_fcg_result_independent_of_batch():
+@pytest.mark.parametrize("nrhs", [3, 12, 16])
+@pytest.mark.parametrize("fp32", [1, 0])
+def test_fcg_result_independent_of_batch(nrhs, fp32):
+    """Each right-hand side's FCG result and count are bitwise those of its
+    solve alone, with FP32 vectors (right-hand-side tiles of 1, 4 and 8
+    columns in the product q = A p for 3, 12 and 16 rhs; 1 alone) and with
+    FP64 vectors."""
     p, Ho, Hp = problem("lognormal65")
     prm = rand_params(Hp.J, 53, 0.05)
-    f = np.random.default_rng(8).standard_normal((Hp.sizes[0], 3))
+    f = np.random.default_rng(8).standard_normal((Hp.sizes[0], nrhs))
     f[:, 1] *= 1e-4
-    S3 = Solver(Hp, prm, precision=32, max_batch=3)
+    S3 = Solver(Hp, prm, precision=32, max_batch=nrhs)
     S1 = Solver(Hp, prm, precision=32, max_batch=1)
+    for S in (S3, S1):
+        S.set_option("fcg_fp32", fp32)
     u3, i3 = S3.solve(t64(f), tol=1e-8, max_iter=200, method="fcg")
-    for b in range(3):
+    for b in sorted({0, 1, 2, nrhs - 1}):
         u1, i1 = S1.solve(t64(f[:, [b]]), tol=1e-8, max_iter=200, method="fcg")
-        assert i1.iters[0] == i3.iters[b]
-        assert torch.equal(u1[:, 0], u3[:, b])
+        assert i1.iters[0] == i3.iters[b], (b, i1.iters, i3.iters)
+        assert torch.equal(u1[:, 0], u3[:, b]), b
+
+
+@pytest.mark.parametrize("name", ["poisson33", "checker65", "lshape_r2"])
+def test_fcg_fp32_vectors_against_fp64_vectors(name):
+    """Precision-32 FCG with FP32 vectors and FP64 restarts (the default) and
+    with FP64 vectors both reach 1e-8 for every right-hand side, re-checked
+    by the oracle from the returned iterate; the reported relres is the
+    restart's FP64 residual (the oracle's within 1e-6 relative); the FP32
+    form takes at most a few steps more (a restart drops the one kept
+    direction).  Phase floors 10^-3 .. 10^-6 and none all converge."""
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 61, 0.05)
+    S = Solver(Hp, prm, precision=32, max_batch=p.f.shape[1])
+    out = {}
+    for fp32, floor in ((0, 4), (1, 4), (1, 3), (1, 6), (1, 0)):
+        S.set_option("fcg_fp32", fp32)
+        S.set_option("fcg_floor", floor)
+        u, info = S.solve(t64(p.f), tol=1e-8, max_iter=400, method="fcg")
+        assert info.status == 0, (fp32, floor)
+        rr = O.relres(Ho, p.f, u.cpu().numpy())
+        assert (rr < 1e-8).all(), (fp32, floor, rr)
+        assert np.allclose(info.relres, rr, rtol=1e-6, atol=0.0), (fp32, floor)
+        out[(fp32, floor)] = info.iters.max()
+    assert out[(1, 4)] <= out[(0, 4)] + 5, out
+    for bad in (-1, 16):
+        with pytest.raises(MGError):
+            S.set_option("fcg_floor", bad)
+    with pytest.raises(MGError):
+        S.set_option("fcg_fp32", 2)
+    S.close()
+
+
+def test_fcg_fp32_last_iteration_restarts():
+    """Stopped by max_iter, the FP32 form still folds its correction into u
+    and reports the FP64 residual of that u (MG_NOT_CONVERGED), which the
+    oracle re-computes; the count is max_iter."""
+    p, Ho, Hp = problem("checker65")
+    prm = rand_params(Hp.J, 61, 0.05)
+    S = Solver(Hp, prm, precision=32, max_batch=p.f.shape[1])
+    for k in (1, 3, 7):
+        u, info = S.solve(t64(p.f), tol=1e-14, max_iter=k, method="fcg")
+        assert info.status == 1 and (info.iters == k).all(), (k, info.iters)
+        rr = O.relres(Ho, p.f, u.cpu().numpy())
+        assert np.allclose(info.relres, rr, rtol=1e-6, atol=0.0), (k, info.relres, rr)
+        assert np.isfinite(rr).all()
+    S.close()
 
 
 @pytest.mark.parametrize("inverse", [1, 0])

@@ -1,7 +1,8 @@
 """Stacked contexts (one operator per request on the square mesh) against the
 oracle: the device set-up (P1 assembly, Galerkin coarsening, drop rule,
-degrees, coarsest inverse) level by level, the cycle per block, and block
-solves that equal each system solved alone, bitwise, through the C ABI.
+degrees, coarsest inverse) level by level, the cycle per block, block
+solves that equal each system solved alone, bitwise, and solves over the
+leading blocks that equal solves over all of them, through the C ABI.
 
 Tolerances: FP64 operator application and single steps 1e-13 relative per
 block (the device sums the Galerkin products in another order than the
@@ -191,6 +192,39 @@ def test_block_solves_in_the_mix_equal_alone(prec):
         A1.close()
 
 
+@pytest.mark.parametrize("N,prec", [(33, 32), (65, 32), (33, 64)])
+def test_leading_blocks_solve_equals_whole_context(N, prec):
+    """A solve over the leading k blocks (views of every level with fewer rows
+    and the whole level's strides; on 33^2 with k = 1 every level runs in the
+    single-block kernel, whose shared-memory copy then takes the strided
+    rows) gives those blocks the results of a solve over all blocks: same
+    iterates bitwise, same counts.  The other blocks' iterates are not
+    touched, and their counts are reported as zero."""
+    kinds = ["lognormal", "checker", "lognormal", "poisson", "lognormal"]
+    sys_list = systems(N, kinds, seed=31)
+    prm = LMGParams.identity(levels_for(N))
+    prm.wB[:, 1], prm.wR[:, 1], prm.wP[:, 1] = 0.1, 0.05, -0.05
+    S = SquareBatch(N, 5, prm, precision=prec)
+    fill(S, sys_list)
+    m = S.m
+    f = t64(np.concatenate([x[1] for x in sys_list]))
+    u_all = torch.zeros_like(f)
+    info_all = S.solve(f, u_all, tol=1e-8, max_iter=300)
+    assert info_all.status == 0
+    for k in (1, 3, 5):
+        u = torch.full_like(f, 7.0)
+        u[:k * m] = 0
+        info = S.solve(f, u, tol=1e-8, max_iter=300, nblocks=k)
+        assert info.status == 0
+        assert np.array_equal(info.iters[:k], info_all.iters[:k]), (k, info.iters, info_all.iters)
+        assert np.all(info.iters[k:] == 0)
+        assert torch.equal(u[:k * m], u_all[:k * m]), k
+        assert torch.all(u[k * m:] == 7.0), k
+    for b, (_, fb, _, H) in enumerate(sys_list):
+        assert O.relres(H, fb[:, None], u_all[b * m:(b + 1) * m].cpu().numpy()[:, None])[0] < 1e-8
+    S.close()
+
+
 def test_invalid_square_arguments():
     from paper_2608_29082_b300._lib import MGError
     with pytest.raises(MGError):
@@ -200,4 +234,9 @@ def test_invalid_square_arguments():
         S.set_block(0, torch.zeros(10, dtype=torch.float64, device=DEV))
     with pytest.raises(MGError):
         S.set_block(2, torch.ones(S.n_elements, dtype=torch.float64, device=DEV))
+    f = torch.zeros(2 * S.m, dtype=torch.float64, device=DEV)
+    u = torch.zeros_like(f)
+    for k in (0, 3, -1):
+        with pytest.raises(MGError):
+            S.solve(f, u, nblocks=k)
     S.close()

@@ -11,9 +11,11 @@ import threading
 import time
 from collections import OrderedDict, deque
 
+import numpy as np
 import torch
 
 from paper_2608_29082_b300.serve import BatchContext, ClassWorker, Request, Server, batch_footprint
+from paper_2608_29082_b300.solver import SolveInfo
 
 
 class FakeBatch:
@@ -199,3 +201,37 @@ def test_waiting_requests_keep_their_order():
 def test_footprint_grows_with_slots_and_size():
     assert batch_footprint(129, 8, 32) > batch_footprint(65, 8, 32) > 0
     assert batch_footprint(65, 16, 32) > batch_footprint(65, 8, 32)
+
+
+def test_tick_iterates_the_leading_blocks_up_to_the_last_occupied_slot():
+    """Admission fills the lowest free slot; a tick passes the count of
+    leading blocks up to the last occupied slot (holes below it included)."""
+    S, _ = fake_server(budget=100, need={65: 10}, slots=4)
+    w = fake_worker(S)
+    rs = [Request(rid=i, klass=65, coef=0, src=0) for i in range(3)]
+    for r in rs:
+        w.submit(r)
+    w._admit()
+    ctx = S.contexts[65][(65, 1)]
+    assert ctx.lead == 3
+    seen = []
+
+    def solve(f, u, tol, max_iter, nblocks):
+        seen.append(nblocks)
+        it = np.zeros(4, dtype=np.int32)
+        it[:nblocks] = 1
+        rr = np.zeros(4)
+        rr[:nblocks] = 1.0
+        return SolveInfo(1, it, rr)
+
+    ctx.batch.solve = solve
+    S.tol, S.max_iter, S.iters_per_tick, S.keep_results = 1e-8, 100, 1, False
+    ctx.req[2] = None                     # the last request leaves
+    assert ctx.lead == 2
+    ctx.req[0] = None                     # a hole below the last occupied slot
+    assert ctx.lead == 2 and ctx.busy == 1
+    w._tick()
+    assert seen == [2] and rs[1].iters == 1
+    ctx.req[1] = None
+    assert ctx.lead == 0
+
