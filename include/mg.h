@@ -641,6 +641,27 @@ mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels, int32_t m
 mg_status mg2_set_params(mg2_ctx* ctx, const double* theta, const double* eta, const double* WB,
                          const double* WR, const double* WP, int32_t nu_pre, int32_t nu_post);
 
+/* Launch shapes of the two-feature cycle (results are bitwise the same):
+ *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
+ *                     dependent launch; 0: plain launches.
+ *   MG_OPT_MULTI_RHS  1 (default): a thread owns a row and a tile of the
+ *                     widest of 4 (precision 32) or 2 (precision 64) complex
+ *                     right-hand sides (32 bytes) that divides nrhs, so a
+ *                     row's entries are read once per tile; 0: one thread
+ *                     per (row, rhs).
+ * Other options: MG_ERR_INVALID.  Drops the captured cycle graphs. */
+mg_status mg2_set_option(mg2_ctx* ctx, int32_t option, int64_t value);
+
+/* One cycle exactly like mg2_vcycle (same kernels, same result), launched
+ * directly with a CUDA event pair around every kernel on `stream`.  Records
+ * (launch order, up to max_out) use mg_kernel_kind: MG_K_RESIDUAL_SCALED and
+ * MG_K_CONV_UPDATE (smoothing), MG_K_RESIDUAL and MG_K_CONV_R (restriction's
+ * residual and Phi_R), MG_K_RESTRICT (the P^T product), MG_K_PE (P e_c),
+ * MG_K_PROLONG (Phi_P added to u), MG_K_COARSE_CHOL (the coarsest product).
+ * Synchronises the stream. */
+mg_status mg2_vcycle_profile(mg2_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs,
+                             mg_kernel_time* out, int32_t max_out, int32_t* n_out, void* stream);
+
 /* One cycle on level 0: u <- LMG(A, f, u) for nrhs complex right-hand sides
  * (device f and u, distinct; 1 <= nrhs <= max_batch).  Queued on stream,
  * not waited for.  The cycle is captured into a CUDA graph on first use

@@ -91,6 +91,9 @@ def lib() -> C.CDLL:
         "mg2_setup": ([C.POINTER(vp), C.c_int32, C.POINTER(Level2), C.c_int32, C.c_int32],
                       C.c_int),
         "mg2_set_params": ([vp, f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_int32], C.c_int),
+        "mg2_set_option": ([vp, C.c_int32, C.c_int64], C.c_int),
+        "mg2_vcycle_profile": ([vp, vp, vp, C.c_int32, C.POINTER(KernelTime), C.c_int32,
+                                C.POINTER(C.c_int32), vp], C.c_int),
         "mg2_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),
         "mg2_solve_fgmres": ([vp, vp, vp, C.c_int32, C.c_double, C.c_int32, C.c_int32, C.c_int32,
                               i32p, f64p, vp], C.c_int),

@@ -22,7 +22,11 @@
 #include <map>
 #include <string>
 #include <tuple>
+#include <type_traits>
 #include <vector>
+
+#include <cstdint>
+#include <cstring>
 
 #include <cuda_runtime.h>
 
@@ -50,9 +54,69 @@ struct Conv2 {
   T w[2][2][2];
 };
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.launch_dependents;"); }
+
+// BV consecutive complex values x[off .. off+BV) (Pair<T> = (Re, Im)): one
+// 32-byte access where BV pairs are 32 bytes and the address is 32-byte
+// aligned (ld.global.v8.b32), else pair by pair.
+template <class T, int BV>
+__device__ __forceinline__ void ld_pairs(const typename Pair<T>::type* __restrict__ x, size_t off,
+                                         typename Pair<T>::type (&out)[BV]) {
+  const typename Pair<T>::type* p = x + off;
+  if constexpr (BV * sizeof(typename Pair<T>::type) == 32) {
+    if (((uintptr_t)p & 31) == 0) {
+      uint32_t w[8];
+      asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+          : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
+            "=r"(w[7])
+          : "l"(p));
+      memcpy(out, w, 32);
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < BV; ++j) out[j] = p[j];
+}
+
+template <class T, int BV>
+__device__ __forceinline__ void st_pairs(typename Pair<T>::type* __restrict__ x, size_t off,
+                                         const typename Pair<T>::type (&in)[BV]) {
+  typename Pair<T>::type* p = x + off;
+  if constexpr (BV * sizeof(typename Pair<T>::type) == 32) {
+    if (((uintptr_t)p & 31) == 0) {
+      uint32_t w[8];
+      memcpy(w, in, 32);
+      asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
+                   "r"(w[1]), "r"(w[2]), "r"(w[3]), "r"(w[4]), "r"(w[5]), "r"(w[6]), "r"(w[7])
+                   : "memory");
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < BV; ++j) p[j] = in[j];
+}
+
+// Thread layout of the cycle kernels: thread g owns row i = g / (B / BV) and
+// the BV consecutive right-hand sides b0.. (BV | B); the B / BV threads of a
+// row are adjacent lanes, so a warp reads whole runs of a neighbour's values
+// and a row's matrix entries once per BV columns.  For every (row, rhs) the
+// arithmetic is the same as with BV = 1.  Every kernel waits on its
+// predecessor (griddepcontrol.wait) before touching memory, so it may be
+// launched with programmatic dependent launch.
+#define MG2_PROLOGUE(NROWS)                              \
+  pdl_wait();                                             \
+  pdl_launch();                                           \
+  const int nq = B / BV;                                  \
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;    \
+  const int i = g / nq;                                   \
+  if (i >= (NROWS)) return;                               \
+  const int b0 = (g - i * nq) * BV;                       \
+  const size_t base = (size_t)i * B + b0;
+
 // out = f - A u (u_zero: u = 0), then optionally out = theta * out / A_ii
 // (dinv = 1 / A_ii, complex)
-template <class T>
+template <class T, int BV>
 __global__ void __launch_bounds__(kF2Threads)
     k2_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                 const typename Pair<T>::type* __restrict__ av,
@@ -60,103 +124,149 @@ __global__ void __launch_bounds__(kF2Threads)
                 const typename Pair<T>::type* __restrict__ u, typename Pair<T>::type* __restrict__ out,
                 int B, const typename Pair<T>::type* __restrict__ dinv, T theta, int scale,
                 int u_zero) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * B) return;
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
-  typename Pair<T>::type r = f[t];
+  using P2 = typename Pair<T>::type;
+  MG2_PROLOGUE(n)
+  P2 r[BV];
+  ld_pairs<T, BV>(f, base, r);
   if (!u_zero) {
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
-      const typename Pair<T>::type a = av[e];
-      const typename Pair<T>::type x = u[(size_t)ci[e] * B + b];
-      r.x -= a.x * x.x - a.y * x.y;
-      r.y -= a.x * x.y + a.y * x.x;
+      const P2 a = av[e];
+      P2 x[BV];
+      ld_pairs<T, BV>(u, (size_t)ci[e] * B + b0, x);
+#pragma unroll
+      for (int j = 0; j < BV; ++j) {
+        r[j].x -= a.x * x[j].x - a.y * x[j].y;
+        r[j].y -= a.x * x[j].y + a.y * x[j].x;
+      }
     }
   }
   if (scale) {
-    const typename Pair<T>::type d = dinv[i];
-    const T re = r.x * d.x - r.y * d.y, im = r.x * d.y + r.y * d.x;
-    r.x = theta * re;
-    r.y = theta * im;
+    const P2 d = dinv[i];
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      const T re = r[j].x * d.x - r[j].y * d.y, im = r[j].x * d.y + r[j].y * d.x;
+      r[j].x = theta * re;
+      r[j].y = theta * im;
+    }
   }
-  out[t] = r;
+  st_pairs<T, BV>(out, base, r);
 }
 
 // phi_i = W_1 x_i + W_2 inv_deg_i sum_{j != i in row i} x_j; mode 0: y = phi,
 // 1: y += eta phi, 2: y += phi.  x and y are distinct buffers.
-template <class T>
+template <class T, int BV>
 __global__ void __launch_bounds__(kF2Threads)
     k2_conv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
             const T* __restrict__ invdeg, const typename Pair<T>::type* __restrict__ x,
             typename Pair<T>::type* __restrict__ y, int B, Conv2<T> w, T eta, int mode) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * B) return;
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
-  T sx = T(0), sy = T(0);
+  using P2 = typename Pair<T>::type;
+  MG2_PROLOGUE(n)
+  T sx[BV], sy[BV];
+#pragma unroll
+  for (int j = 0; j < BV; ++j) sx[j] = sy[j] = T(0);
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     const int c = ci[e];
     if (c == i) continue;
-    const typename Pair<T>::type v = x[(size_t)c * B + b];
-    sx += v.x;
-    sy += v.y;
+    P2 v[BV];
+    ld_pairs<T, BV>(x, (size_t)c * B + b0, v);
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      sx[j] += v[j].x;
+      sy[j] += v[j].y;
+    }
   }
-  const T mx = invdeg[i] * sx, my = invdeg[i] * sy;
-  const typename Pair<T>::type xi = x[t];
-  typename Pair<T>::type phi;
-  phi.x = w.w[0][0][0] * xi.x + w.w[0][0][1] * xi.y + (w.w[1][0][0] * mx + w.w[1][0][1] * my);
-  phi.y = w.w[0][1][0] * xi.x + w.w[0][1][1] * xi.y + (w.w[1][1][0] * mx + w.w[1][1][1] * my);
-  if (mode == 0) {
-    y[t] = phi;
-  } else {
-    typename Pair<T>::type o = y[t];
-    const T s = mode == 1 ? eta : T(1);
-    o.x += s * phi.x;
-    o.y += s * phi.y;
-    y[t] = o;
+  const T id = invdeg[i];
+  P2 xi[BV], o[BV];
+  ld_pairs<T, BV>(x, base, xi);
+  if (mode != 0) ld_pairs<T, BV>(y, base, o);
+#pragma unroll
+  for (int j = 0; j < BV; ++j) {
+    const T mx = id * sx[j], my = id * sy[j];
+    P2 phi;
+    phi.x = w.w[0][0][0] * xi[j].x + w.w[0][0][1] * xi[j].y + (w.w[1][0][0] * mx + w.w[1][0][1] * my);
+    phi.y = w.w[0][1][0] * xi[j].x + w.w[0][1][1] * xi[j].y + (w.w[1][1][0] * mx + w.w[1][1][1] * my);
+    if (mode == 0) {
+      o[j] = phi;
+    } else {
+      const T s = mode == 1 ? eta : T(1);
+      o[j].x += s * phi.x;
+      o[j].y += s * phi.y;
+    }
   }
+  st_pairs<T, BV>(y, base, o);
 }
 
 // y = M x for a real CSR matrix M (n rows) on complex vectors
-template <class T>
+template <class T, int BV>
 __global__ void __launch_bounds__(kF2Threads)
     k2_spmv_real(int n, const int* __restrict__ rp, const int* __restrict__ ci,
                  const T* __restrict__ mv, const typename Pair<T>::type* __restrict__ x,
                  typename Pair<T>::type* __restrict__ y, int B) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * B) return;
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
-  T sx = T(0), sy = T(0);
+  using P2 = typename Pair<T>::type;
+  MG2_PROLOGUE(n)
+  P2 o[BV];
+#pragma unroll
+  for (int j = 0; j < BV; ++j) o[j].x = o[j].y = T(0);
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     const T m = mv[e];
-    const typename Pair<T>::type v = x[(size_t)ci[e] * B + b];
-    sx += m * v.x;
-    sy += m * v.y;
+    P2 v[BV];
+    ld_pairs<T, BV>(x, (size_t)ci[e] * B + b0, v);
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      o[j].x += m * v[j].x;
+      o[j].y += m * v[j].y;
+    }
   }
-  typename Pair<T>::type o;
-  o.x = sx;
-  o.y = sy;
-  y[t] = o;
+  st_pairs<T, BV>(y, base, o);
 }
 
-// e = A_J^{-1} r with the dense inverse (row-major, complex)
-template <class T>
+// e = A_J^{-1} r with the dense inverse (row-major, complex): one warp per
+// (row i, tile of BV right-hand sides); lane l sums the products of columns
+// l, l + 32, ... in order, then the lanes' sums are added by a fixed
+// butterfly.  The order of every (row, rhs) sum does not depend on BV.
+template <class T, int BV>
 __global__ void __launch_bounds__(kF2Threads)
     k2_dense(int n, const typename Pair<T>::type* __restrict__ inv,
              const typename Pair<T>::type* __restrict__ r, typename Pair<T>::type* __restrict__ e,
              int B) {
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (size_t)n * B) return;
-  const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
-  T sx = T(0), sy = T(0);
-  for (int j = 0; j < n; ++j) {
-    const typename Pair<T>::type a = inv[(size_t)i * n + j];
-    const typename Pair<T>::type v = r[(size_t)j * B + b];
-    sx += a.x * v.x - a.y * v.y;
-    sy += a.x * v.y + a.y * v.x;
+  using P2 = typename Pair<T>::type;
+  pdl_wait();
+  pdl_launch();
+  const int nq = B / BV;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int i = w / nq;
+  if (i >= n) return;
+  const int b0 = (w - i * nq) * BV;
+  T sx[BV], sy[BV];
+#pragma unroll
+  for (int j = 0; j < BV; ++j) sx[j] = sy[j] = T(0);
+  for (int k = lane; k < n; k += 32) {
+    const P2 a = inv[(size_t)i * n + k];
+    P2 v[BV];
+    ld_pairs<T, BV>(r, (size_t)k * B + b0, v);
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      sx[j] += a.x * v[j].x - a.y * v[j].y;
+      sy[j] += a.x * v[j].y + a.y * v[j].x;
+    }
   }
-  typename Pair<T>::type o;
-  o.x = sx;
-  o.y = sy;
-  e[t] = o;
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      sx[j] += __shfl_xor_sync(0xffffffffu, sx[j], m);
+      sy[j] += __shfl_xor_sync(0xffffffffu, sy[j], m);
+    }
+  if (lane == 0) {
+    P2 o[BV];
+#pragma unroll
+    for (int j = 0; j < BV; ++j) {
+      o[j].x = sx[j];
+      o[j].y = sy[j];
+    }
+    st_pairs<T, BV>(e, (size_t)i * B + b0, o);
+  }
 }
 
 dim3 grid_of(size_t work) { return dim3((unsigned)((work + kF2Threads - 1) / kF2Threads)); }
@@ -400,6 +510,10 @@ struct mg2_ctx {
   void* cinv = nullptr;  // Pair<T>, n_J x n_J
   std::vector<double> theta, eta, WB, WR, WP;
   int nu_pre = 1, nu_post = 1;
+  int opt_pdl = 1;   // programmatic dependent launch between the cycle's kernels
+  int opt_tile = 1;  // right-hand-side tiles of the cycle's kernels (0: one per thread)
+  // mg2_vcycle_profile: (kind, level, start, end) per launch while set
+  std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>>* prof = nullptr;
   std::vector<void*> owned;
   cudaStream_t cap = nullptr;  // capture stream
   // FGMRES (mg2_solve_fgmres): the FP64 level-0 operator, and the workspace
@@ -568,15 +682,95 @@ Conv2<T> conv_of(const std::vector<double>& W, int l) {
   return w;
 }
 
+// Launches of the cycle kernels: right-hand-side tiles of BV columns (the
+// widest of 4 (FP32) or 2 (FP64) complex values, 32 bytes, that divides B;
+// 1 with tiling off) and programmatic dependent launch (option).
+template <class T>
+struct Launch2 {
+  mg2_ctx* c;
+  cudaStream_t s;
+  int B;
+  int bv() const {
+    if (!c->opt_tile) return 1;
+    for (int v = sizeof(T) == 4 ? 4 : 2; v > 1; v /= 2)
+      if (B % v == 0) return v;
+    return 1;
+  }
+  template <class... KArgs, class... Args>
+  void go(int kind, int lev, void (*k)(KArgs...), int n, Args... args) const {
+    if (c->prof) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      cudaEventRecord(a, s);
+      c->prof->emplace_back(kind, lev, a, b);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid_of((size_t)n * (B / bv()));
+    cfg.blockDim = dim3(kF2Threads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->opt_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, args...);
+    if (c->prof) cudaEventRecord(std::get<3>(c->prof->back()), s);
+  }
+  // f(std::integral_constant<int, BV>) for this launch's tile width
+  template <class F>
+  void with_bv(F&& f) const {
+    const int v = bv();
+    if constexpr (sizeof(T) == 4) {
+      if (v == 4) return f(std::integral_constant<int, 4>{});
+    }
+    if (v == 2) return f(std::integral_constant<int, 2>{});
+    f(std::integral_constant<int, 1>{});
+  }
+  using P2 = typename Pair<T>::type;
+  // profile kinds (mg_kernel_kind): the smoothing residual, the smoothing
+  // conv, the restriction's residual and Phi_R, the P^T gather, P e_c, the
+  // prolongation's Phi_P and the coarsest product
+  void residual(int lev, const mg2_ctx::Lev& L, const P2* f, const P2* u, P2* out, T theta,
+                int scale, int u_zero) const {
+    with_bv([&](auto V) {
+      go(scale ? MG_K_RESIDUAL_SCALED : MG_K_RESIDUAL, lev, k2_residual<T, decltype(V)::value>,
+         L.n, L.n, (const int*)L.rp, (const int*)L.ci, (const P2*)L.av, f, u, out, B,
+         (const P2*)L.dinv, theta, scale, u_zero);
+    });
+  }
+  void conv(int lev, const mg2_ctx::Lev& L, const P2* x, P2* y, Conv2<T> w, T eta,
+            int mode) const {
+    const int kind = mode == 1 ? MG_K_CONV_UPDATE : mode == 0 ? MG_K_CONV_R : MG_K_PROLONG;
+    with_bv([&](auto V) {
+      go(kind, lev, k2_conv<T, decltype(V)::value>, L.n, L.n, (const int*)L.rp,
+         (const int*)L.ci, (const T*)L.invdeg, x, y, B, w, eta, mode);
+    });
+  }
+  void spmv(int kind, int lev, int n, const int* rp, const int* ci, const void* mv, const P2* x,
+            P2* y) const {
+    with_bv([&](auto V) {
+      go(kind, lev, k2_spmv_real<T, decltype(V)::value>, n, n, rp, ci, (const T*)mv, x, y, B);
+    });
+  }
+  void dense(int lev, int n, const P2* r, P2* e) const {
+    // one warp per (row, tile): 32 threads per output
+    with_bv([&](auto V) {
+      go(MG_K_COARSE_CHOL, lev, k2_dense<T, decltype(V)::value>, 32 * n, n, (const P2*)c->cinv,
+         r, e, B);
+    });
+  }
+};
+
 // Algorithm 2 on level l with two-feature convolutions.
 template <class T>
 void cycle(mg2_ctx* c, int l, const typename Pair<T>::type* f, typename Pair<T>::type* u, int B,
            cudaStream_t s) {
   using P2 = typename Pair<T>::type;
+  const Launch2<T> k{c, s, B};
   mg2_ctx::Lev& L = c->lev[l];
-  const dim3 g = grid_of((size_t)L.n * B);
   if (l == c->J - 1) {
-    k2_dense<T><<<g, kF2Threads, 0, s>>>(L.n, (const P2*)c->cinv, f, u, B);
+    k.dense(l, L.n, f, u);
     return;
   }
   const T theta = (T)c->theta[l], eta = (T)c->eta[l];
@@ -584,23 +778,20 @@ void cycle(mg2_ctx* c, int l, const typename Pair<T>::type* f, typename Pair<T>:
   P2* t = (P2*)L.t;
   P2* t2 = (P2*)L.t2;
   auto smooth = [&](int nu) {
-    for (int k = 0; k < nu; ++k) {
-      k2_residual<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const P2*)L.av, f, u, t, B,
-                                              (const P2*)L.dinv, theta, 1, 0);
-      k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, t, u, B, wb, eta, 1);
+    for (int q = 0; q < nu; ++q) {
+      k.residual(l, L, f, u, t, theta, 1, 0);
+      k.conv(l, L, t, u, wb, eta, 1);
     }
   };
   smooth(c->nu_pre);
-  k2_residual<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const P2*)L.av, f, u, t, B,
-                                          (const P2*)L.dinv, theta, 0, 0);
-  k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, t, t2, B, wr, T(1), 0);
+  k.residual(l, L, f, u, t, theta, 0, 0);
+  k.conv(l, L, t, t2, wr, T(1), 0);
   mg2_ctx::Lev& C = c->lev[l + 1];
-  const dim3 gc = grid_of((size_t)C.n * B);
-  k2_spmv_real<T><<<gc, kF2Threads, 0, s>>>(C.n, L.trp, L.tci, (const T*)L.tv, t2, (P2*)C.f, B);
+  k.spmv(MG_K_RESTRICT, l, C.n, L.trp, L.tci, L.tv, t2, (P2*)C.f);
   cudaMemsetAsync(C.u, 0, (size_t)C.n * B * sizeof(P2), s);
   cycle<T>(c, l + 1, (const P2*)C.f, (P2*)C.u, B, s);
-  k2_spmv_real<T><<<g, kF2Threads, 0, s>>>(L.n, L.prp, L.pci, (const T*)L.pv, (const P2*)C.u, t, B);
-  k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, t, u, B, wp, T(1), 2);
+  k.spmv(MG_K_PE, l, L.n, L.prp, L.pci, L.pv, (const P2*)C.u, t);
+  k.conv(l, L, t, u, wp, T(1), 2);
   smooth(c->nu_post);
 }
 
@@ -613,30 +804,26 @@ template <class T>
 void fmg(mg2_ctx* c, const typename Pair<T>::type* f0, typename Pair<T>::type* u0, int B,
          cudaStream_t s) {
   using P2 = typename Pair<T>::type;
+  const Launch2<T> k{c, s, B};
   const int J = c->J;
   for (int l = 0; l < J - 1; ++l) {
     mg2_ctx::Lev& L = c->lev[l];
     mg2_ctx::Lev& C = c->lev[l + 1];
     const P2* fl = l == 0 ? f0 : (const P2*)L.f;
-    k2_conv<T><<<grid_of((size_t)L.n * B), kF2Threads, 0, s>>>(
-        L.n, L.rp, L.ci, (const T*)L.invdeg, fl, (P2*)L.t2, B, conv_of<T>(c->WR, l), T(1), 0);
-    k2_spmv_real<T><<<grid_of((size_t)C.n * B), kF2Threads, 0, s>>>(
-        C.n, L.trp, L.tci, (const T*)L.tv, (const P2*)L.t2, (P2*)C.f, B);
+    k.conv(l, L, fl, (P2*)L.t2, conv_of<T>(c->WR, l), T(1), 0);
+    k.spmv(MG_K_RESTRICT, l, C.n, L.trp, L.tci, L.tv, (const P2*)L.t2, (P2*)C.f);
   }
   mg2_ctx::Lev& LJ = c->lev[J - 1];
   const P2* fJ = J == 1 ? f0 : (const P2*)LJ.f;
   P2* uJ = J == 1 ? u0 : (P2*)LJ.u;
-  k2_dense<T><<<grid_of((size_t)LJ.n * B), kF2Threads, 0, s>>>(LJ.n, (const P2*)c->cinv, fJ, uJ, B);
+  k.dense(J - 1, LJ.n, fJ, uJ);
   for (int l = J - 2; l >= 0; --l) {
     mg2_ctx::Lev& L = c->lev[l];
     mg2_ctx::Lev& C = c->lev[l + 1];
     const P2* fl = l == 0 ? f0 : (const P2*)L.f;
     P2* ul = l == 0 ? u0 : (P2*)L.u;
-    const dim3 g = grid_of((size_t)L.n * B);
-    k2_spmv_real<T><<<g, kF2Threads, 0, s>>>(L.n, L.prp, L.pci, (const T*)L.pv, (const P2*)C.u,
-                                             (P2*)L.t, B);
-    k2_conv<T><<<g, kF2Threads, 0, s>>>(L.n, L.rp, L.ci, (const T*)L.invdeg, (const P2*)L.t, ul,
-                                        B, conv_of<T>(c->WP, l), T(1), 0);
+    k.spmv(MG_K_PE, l, L.n, L.prp, L.pci, L.pv, (const P2*)C.u, (P2*)L.t);
+    k.conv(l, L, (const P2*)L.t, ul, conv_of<T>(c->WP, l), T(1), 0);
     cycle<T>(c, l, fl, ul, B, s);
   }
 }
@@ -746,6 +933,23 @@ extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels
   return MG_OK;
 }
 
+extern "C" mg_status mg2_set_option(mg2_ctx* c, int32_t option, int64_t value) {
+  if (!c) return fail("mg2_set_option: ctx is NULL");
+  switch (option) {
+    case MG_OPT_PDL:
+      c->opt_pdl = value != 0;
+      break;
+    case MG_OPT_MULTI_RHS:
+      if (value != 0 && value != 1) return fail("mg2_set_option: tile option must be 0 or 1");
+      c->opt_tile = (int)value;
+      break;
+    default:
+      return fail("mg2_set_option: unknown option");
+  }
+  c->drop_graphs();
+  return MG_OK;
+}
+
 extern "C" mg_status mg2_set_params(mg2_ctx* c, const double* theta, const double* eta,
                                     const double* WB, const double* WR, const double* WP,
                                     int32_t nu_pre, int32_t nu_post) {
@@ -808,6 +1012,40 @@ extern "C" mg_status mg2_vcycle(mg2_ctx* c, const void* f, void* u, int32_t nrhs
   return MG_OK;
 }
 
+extern "C" mg_status mg2_vcycle_profile(mg2_ctx* c, const void* f, void* u, int32_t nrhs,
+                                        mg_kernel_time* out, int32_t max_out, int32_t* n_out,
+                                        void* stream) {
+  if (!c) return fail("mg2_vcycle_profile: ctx is NULL");
+  if (!f || !u || f == u || nrhs < 1 || nrhs > c->maxB || !out || max_out < 0 || !n_out)
+    return fail("mg2_vcycle_profile: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>> rec;
+  c->prof = &rec;
+  if (c->prec == 64)
+    cycle<double>(c, 0, (const double2*)f, (double2*)u, nrhs, s);
+  else
+    cycle<float>(c, 0, (const float2*)f, (float2*)u, nrhs, s);
+  c->prof = nullptr;
+  cudaError_t e = cudaStreamSynchronize(s);
+  int k = 0;
+  for (auto& r : rec) {
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, std::get<2>(r), std::get<3>(r));
+    if (k < max_out) {
+      out[k].kernel = std::get<0>(r);
+      out[k].level = std::get<1>(r);
+      out[k].ms = ms;
+      ++k;
+    }
+    cudaEventDestroy(std::get<2>(r));
+    cudaEventDestroy(std::get<3>(r));
+  }
+  *n_out = k;
+  if (e != cudaSuccess)
+    return fail(std::string("mg2_vcycle_profile: ") + cudaGetErrorString(e), MG_ERR_CUDA);
+  return MG_OK;
+}
+
 extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_t B, double tol,
                                       int32_t max_iter, int32_t restart, int32_t precond,
                                       int32_t* iters_out, double* relres_out, void* stream) {
@@ -864,7 +1102,7 @@ extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_
   int total = 0;
   bool diverged = false;
   for (;;) {
-    k2_residual<double><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd,
+    k2_residual<double, 1><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd,
                                                  ud, r, B, (const double2*)nullptr, 0.0, 0, 0);
     k2g_dots<<<gb, kF2Threads, 0, s>>>(r, 0, nullptr, n0, B, rsum);
     k2g_restart<<<1, kF2Threads, 0, s>>>(rsum, fsum, tol, m, B, active, relres, c->gmSmall, inv,
@@ -906,7 +1144,7 @@ extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_
                                         k2g_stride(m), jl + 1, active, n0, B);
   }
   // the true residual of the final iterate
-  k2_residual<double><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd, ud,
+  k2_residual<double, 1><<<g, kF2Threads, 0, s>>>(n0, L0.rp, L0.ci, (const double2*)c->av64, fd, ud,
                                                r, B, (const double2*)nullptr, 0.0, 0, 0);
   k2g_dots<<<gb, kF2Threads, 0, s>>>(r, 0, nullptr, n0, B, rsum);
   std::vector<double> hr(B), hf(B);

@@ -137,8 +137,13 @@ class Solver2:
                                         int(p.nu_pre), int(p.nu_post)))
         self.params = p
 
-    def vcycle(self, f: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
-        """u <- one two-feature cycle (Algorithm 2) on level 0, in place."""
+    def set_option(self, name: str, value: int):
+        """Launch shapes of the cycle ("pdl", "multi_rhs"; mg2_set_option)."""
+        if name not in ("pdl", "multi_rhs"):
+            raise ValueError(f"unknown two-feature option {name!r}")
+        L.check(self.lib.mg2_set_option(self.ctx, L.OPTIONS[name], int(value)))
+
+    def _check_cycle_args(self, f: torch.Tensor, u: torch.Tensor):
         for name, x in (("f", f), ("u", u)):
             if (x.dtype != self.dtype or not x.is_cuda or not x.is_contiguous() or x.dim() != 2
                     or x.shape[0] != self.n[0] or not 1 <= x.shape[1] <= self.max_batch):
@@ -146,9 +151,25 @@ class Solver2:
                                  f"({self.n[0]}, 1..{self.max_batch})")
         if f.shape != u.shape:
             raise ValueError("f and u differ in shape")
+
+    def vcycle(self, f: torch.Tensor, u: torch.Tensor) -> torch.Tensor:
+        """u <- one two-feature cycle (Algorithm 2) on level 0, in place."""
+        self._check_cycle_args(f, u)
         L.check(self.lib.mg2_vcycle(self.ctx, C.c_void_p(f.data_ptr()), C.c_void_p(u.data_ptr()),
                                     f.shape[1], _stream_handle()))
         return u
+
+    def vcycle_profile(self, f: torch.Tensor, u: torch.Tensor) -> list[tuple[str, int, float]]:
+        """One cycle with CUDA events around every kernel: [(name, level, ms)]."""
+        self._check_cycle_args(f, u)
+        cap = 4096
+        buf = (L.KernelTime * cap)()
+        n = C.c_int32(0)
+        L.check(self.lib.mg2_vcycle_profile(self.ctx, C.c_void_p(f.data_ptr()),
+                                            C.c_void_p(u.data_ptr()), f.shape[1], buf, cap,
+                                            C.byref(n), _stream_handle()))
+        return [(self.lib.mg_kernel_name(buf[k].kernel).decode(), buf[k].level, buf[k].ms)
+                for k in range(n.value)]
 
     def solve_fgmres(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-8,
                      max_iter: int = 300, restart: int = 30,

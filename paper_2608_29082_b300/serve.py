@@ -14,8 +14,8 @@ size class loops:
      created only while the device budget allows it; under memory pressure
      idle contexts (of any class) are evicted;
   2. tick: one mg_solve_blocks call per context with occupied slots (over its
-     leading blocks up to the last occupied one; admission fills the lowest
-     free slot) runs
+     leading blocks up to the last occupied one, rounded up to a multiple of
+     an eighth of the context; admission fills the lowest free slot) runs
      `iters_per_tick` FP64-refinement iterations (FP32 learned V-cycles) on
      all of its requests at once, each block masked and tested on its own;
   3. retire the slots whose relative residual met the tolerance.
@@ -108,11 +108,28 @@ class BatchContext:
 
     @property
     def lead(self) -> int:
-        """Leading blocks a tick iterates: up to the last occupied slot."""
+        """Leading blocks up to the last occupied slot."""
         for k in range(self.S - 1, -1, -1):
             if self.req[k] is not None:
                 return k + 1
         return 0
+
+    @property
+    def quantum(self) -> int:
+        return max(1, self.S // 8)
+
+    @property
+    def tick_blocks(self) -> int:
+        """Blocks a tick iterates: lead rounded up to a multiple of S / 8, so
+        that a context uses at most 8 solve graphs (one per block count)."""
+        q = self.quantum
+        return min(self.S, -(-self.lead // q) * q)
+
+    def capture(self):
+        """Builds the solve graph of every block count a tick can use (on the
+        context's zero stacks: every block idle, no iterations)."""
+        for k in range(self.quantum, self.S + 1, self.quantum):
+            self.batch.solve(self.f, self.u, tol=1e-8, max_iter=1, nblocks=k)
 
     def block(self, x: torch.Tensor, k: int) -> torch.Tensor:
         return x[k * self.m:(k + 1) * self.m]
@@ -200,7 +217,7 @@ class ClassWorker(threading.Thread):
             if ctx.busy == 0:
                 continue
             info = ctx.batch.solve(ctx.f, ctx.u, tol=S.tol, max_iter=S.iters_per_tick,
-                                   nblocks=ctx.lead)
+                                   nblocks=ctx.tick_blocks)
             ctx.last_used = time.perf_counter()
             for k, r in enumerate(ctx.req):
                 if r is None:
@@ -312,7 +329,7 @@ class Server:
             count = per_class.get(k, 1) if isinstance(per_class, dict) else int(per_class)
             for _ in range(count):
                 if self.reserve(self.need[k]):
-                    self.create(k)
+                    self.create(k).capture()
 
     def close(self):
         for k in self.classes:

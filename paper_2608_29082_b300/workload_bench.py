@@ -284,9 +284,91 @@ def run_profile_case(a):
     S.close()
 
 
+def level_bytes2(name: str, hier, lev: int, B: int, b: int) -> float:
+    """Algorithmic bytes of one two-feature launch: CSR row pointers and
+    column indices (4 B), complex matrix values (2 b), real P / P^T values
+    (b), complex vectors (2 b per entry), each array read or written once."""
+    A = hier.A[lev]
+    n, nnz = A.shape[0], A.nnz
+    c2 = 2 * b
+    nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
+    nnzP = hier.P[lev].nnz if lev < hier.J - 1 else 0
+    rp = (n + 1) * 4
+    table = {
+        "residual_scaled": rp + nnz * (4 + c2) + n * c2 + 3 * B * n * c2,
+        "residual": rp + nnz * (4 + c2) + 3 * B * n * c2,
+        "sage_conv_update": rp + nnz * 4 + n * b + 3 * B * n * c2,
+        "restrict_conv_fine": rp + nnz * 4 + n * b + 2 * B * n * c2,
+        "restrict_conv": (nc + 1) * 4 + nnzP * (4 + b) + B * n * c2 + B * nc * c2,
+        "prolong_fine": rp + nnzP * (4 + b) + B * nc * c2 + B * n * c2,
+        "prolong_conv": rp + nnz * 4 + n * b + 3 * B * n * c2,
+    }
+    return table.get(name, float("nan"))
+
+
+def features2_roofline(a):
+    """Per-kernel time (CUDA events around each launch of an eager cycle) and
+    algorithmic GB/s of the two-feature cycle on a case whose level-0 vectors
+    exceed L2: Helmholtz with impedance boundary on roof_N^2 vertices, 16
+    rhs, FP32."""
+    import workloads as W
+    from paper_2608_29082_b300.features2 import Hierarchy2, Params2, Solver2
+    B = 16
+    prob = W.helmholtz_square(a.roof_N, a.roof_J, k=a.roof_k_over_pi * np.pi, batch=B,
+                              seed=a.seed)
+    hier = Hierarchy2.from_problem(prob)
+    prm = Params2.identity(hier.J)
+    prm.WB[:, 1] = 0.1 * np.eye(2)
+    prm.WR[:, 1] = 0.05 * np.eye(2)
+    prm.WP[:, 1] = -0.05 * np.eye(2)
+    S = Solver2(hier, prm, precision=32, max_batch=B)
+    f = torch.tensor(prob.f, dtype=torch.complex64, device="cuda")
+    u = torch.zeros_like(f)
+    for _ in range(3):
+        S.vcycle(f, u)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+    ms = []
+    for _ in range(10):
+        u.zero_()
+        e0.record()
+        S.vcycle(f, u)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    agg, reps = {}, 3
+    for _ in range(reps):
+        u.zero_()
+        for name, lev, t in S.vcycle_profile(f, u):
+            x = agg.setdefault((name, lev), [0.0, 0])
+            x[0] += t
+            x[1] += 1
+    S.close()
+    peak = hbm_peak()
+    total = sum(v[0] for v in agg.values()) / reps
+    rows = []
+    for (name, lev), (t, cnt) in sorted(agg.items(), key=lambda kv: -kv[1][0]):
+        per = t / cnt
+        nb = level_bytes2(name, hier, lev, B, 4)
+        gbs = nb / (per * 1e-3) / 1e9 if np.isfinite(nb) else None
+        rows.append({"kernel": name, "level": lev, "us_per_launch": round(per * 1e3, 2),
+                     "share": round(t / reps / total, 4),
+                     "algorithmic_MB": round(nb / 1e6, 2) if np.isfinite(nb) else None,
+                     "GBps": round(gbs, 1) if gbs else None,
+                     "frac_of_hbm": round(gbs / peak, 3) if gbs else None})
+    return {"workload": f"Helmholtz, impedance boundary, {a.roof_N}x{a.roof_N} vertices "
+                        f"({hier.sizes[0]} DOF), k = {a.roof_k_over_pi:g} pi, J = {hier.J}, "
+                        f"{B} rhs, FP32, two features",
+            "cycle_ms_graph": round(float(np.median(ms)), 3),
+            "cycle_ms_eager_events": round(total, 3), "hbm_peak_gbs": peak,
+            "kernels": rows[:10]}
+
+
 def run_features2(a):
     import workloads as W
     from paper_2608_29082_b300.features2 import Hierarchy2, Params2, Solver2
+    if a.roof_N:
+        print(json.dumps({"roofline": features2_roofline(a)}), flush=True)
     out = {"workload": f"Helmholtz, impedance boundary, {a.N}x{a.N} vertices (h = 1/{a.N - 1}), "
                        f"k = {a.k_over_pi:g} pi, J = {a.J}, two features (Re, Im), W_1 = I, "
                        "W_2 = 0.1 on the smoother"}
@@ -408,6 +490,10 @@ if __name__ == "__main__":
     f2.add_argument("--krylov-J", type=int, default=3)
     f2.add_argument("--krylov-N", type=int, default=129)
     f2.add_argument("--krylov-k-over-pi", type=float, default=8.0)
+    f2.add_argument("--roof-N", type=int, default=1025,
+                    help="size of the per-kernel roofline case (0: skip)")
+    f2.add_argument("--roof-J", type=int, default=6)
+    f2.add_argument("--roof-k-over-pi", type=float, default=16.0)
     pc = sub.add_parser("profile_case")
     pc.add_argument("--refinements", type=int, default=7)
     pc.add_argument("--batch", type=int, default=16)

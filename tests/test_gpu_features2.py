@@ -174,3 +174,45 @@ def test_fgmres2_zero_rhs_and_not_converged():
     with pytest.raises(MGError):
         S.solve_fgmres(ft, restart=0)
     S.close()
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 8, 16])
+def test_tiles_and_pdl_are_bitwise_neutral(prec, nrhs):
+    """Right-hand-side tiles (4 complex values per thread in FP32, 2 in FP64,
+    the widest dividing nrhs) and programmatic dependent launch give bitwise
+    the cycle, full multigrid and FGMRES of the one-thread-per-(row, rhs)
+    plain launches."""
+    p, Ho, Hp = problem("helmholtz65")
+    prm = params(Hp.J, 19)
+    dt = torch.complex128 if prec == 64 else torch.complex64
+    r = np.random.default_rng(nrhs)
+    fc = r.standard_normal((Hp.sizes[0], nrhs)) + 1j * r.standard_normal((Hp.sizes[0], nrhs))
+    outs = []
+    for tile, pdl in ((0, 0), (1, 0), (0, 1), (1, 1)):
+        S = Solver2(Hp, prm, precision=prec, max_batch=nrhs)
+        S.set_option("multi_rhs", tile)
+        S.set_option("pdl", pdl)
+        f = torch.tensor(fc, dtype=dt, device="cuda")
+        u = torch.zeros_like(f)
+        for _ in range(3):
+            S.vcycle(f, u)
+        f64 = torch.tensor(fc, dtype=torch.complex128, device="cuda")
+        ug, ig = S.solve_fgmres(f64, tol=1e-8, max_iter=200, restart=10, precond="fmg")
+        outs.append((u.clone(), ug.clone(), ig.iters.copy()))
+        S.close()
+    assert torch.isfinite(torch.view_as_real(outs[0][0])).all()
+    for u, ug, it in outs[1:]:
+        assert torch.equal(u, outs[0][0])
+        assert torch.equal(ug, outs[0][1])
+        assert np.array_equal(it, outs[0][2])
+
+
+def test_two_feature_option_errors():
+    p, Ho, Hp = problem("helmholtz33")
+    S = Solver2(Hp, params(Hp.J, 3), precision=32, max_batch=2)
+    with pytest.raises(MGError):
+        S.set_option("multi_rhs", 2)
+    with pytest.raises(ValueError):
+        S.set_option("tail_work", 0)
+    S.close()

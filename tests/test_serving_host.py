@@ -235,3 +235,22 @@ def test_tick_iterates_the_leading_blocks_up_to_the_last_occupied_slot():
     ctx.req[1] = None
     assert ctx.lead == 0
 
+
+def test_tick_block_counts_are_multiples_of_an_eighth():
+    """A tick's block count is the lead rounded up to a multiple of S / 8
+    (at most 8 solve graphs per context), and capture builds exactly those."""
+    S, _ = fake_server(budget=1000, need={65: 10}, slots=64)
+    ctx = S.create(65)
+    calls = []
+    ctx.batch.solve = lambda f, u, tol, max_iter, nblocks: calls.append(nblocks)
+    for lead, want in ((1, 8), (8, 8), (9, 16), (63, 64), (64, 64)):
+        ctx.req = [None] * 64
+        ctx.req[lead - 1] = object()
+        assert ctx.tick_blocks == want, (lead, ctx.tick_blocks)
+    ctx.capture()
+    assert calls == [8, 16, 24, 32, 40, 48, 56, 64]
+    S4, _ = fake_server(budget=1000, need={65: 10}, slots=4)
+    c4 = S4.create(65)
+    c4.req = [None, None, object(), None]
+    assert c4.quantum == 1 and c4.tick_blocks == 3
+
