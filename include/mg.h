@@ -371,6 +371,17 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     substitutions, whose 2 n_{J-1} dependent FP64 steps
  *                     run on one SM per right-hand side).  Both forms agree
  *                     to a few units of rounding times the condition number.
+ *   MG_OPT_HALO2D_BYTES DIA levels (square meshes) whose vectors (rows *
+ *                     nrhs * value bytes) are at least this large, and that
+ *                     the one-wave rule of MG_OPT_HALO_ROWS leaves unfused,
+ *                     run each smoothing step (and the restriction's residual
+ *                     with Phi_R, and P e_c with Phi_P) as one kernel over 2D
+ *                     tiles of 32 x 8 grid points plus a one-point ring,
+ *                     where the tile fits 48 KB of shared memory for nrhs
+ *                     right-hand sides.  0 (default): never.  Bitwise
+ *                     neutral; measured slower than the two-kernel form on
+ *                     the 8.4M-row stacked 1025^2 level (201 against 164 us
+ *                     per smoothing step), so it is off.
  *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1
  *                     (default): FP32 vectors in phases of FCG(1) on the
  *                     scaled correction equation, each phase ended by an FP64
@@ -407,7 +418,8 @@ typedef enum {
   MG_OPT_COARSE_INVERSE = 10,
   MG_OPT_TAIL_TEAMS = 11,
   MG_OPT_FCG_FP32 = 12,
-  MG_OPT_FCG_FLOOR = 13
+  MG_OPT_FCG_FLOOR = 13,
+  MG_OPT_HALO2D_BYTES = 14
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

@@ -17,7 +17,8 @@ STATUS = {0: "MG_OK", 1: "MG_NOT_CONVERGED", -1: "MG_ERR_INVALID", -2: "MG_ERR_O
 OPTIONS = {"tail_work": 0, "pdl": 1, "multi_rhs": 2, "device_loop": 3, "halo_rows": 4, "fcg_precond": 5,
            "fgmres_floor": 6, "sell_halo_rows": 7,
            "sell_halo_threads": 8, "sell_halo_max_bytes": 9, "coarse_inverse": 10,
-           "tail_teams": 11, "fcg_fp32": 12, "fcg_floor": 13}
+           "tail_teams": 11, "fcg_fp32": 12, "fcg_floor": 13,
+           "halo2d_bytes": 14}
 OPS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "coarse": 4,
        "outer_residual": 5, "refine_residual": 6}
 

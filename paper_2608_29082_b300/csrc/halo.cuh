@@ -97,4 +97,110 @@ __global__ void __launch_bounds__(kTailThreads)
   }
 }
 
+// The same fused steps with 2D tiles, for DIA levels laid out on a grid of
+// width w whose offsets are 0, +-1, +-w, +-(w-1) or +-(w+1) (every square
+// mesh here; the stacked contexts are grids of width w and slots * w rows).
+// A 1D tile of TR rows needs a halo of H = w + 1 rows on each side, which
+// for a large level is several times the tile; a tile of kH2X x kH2Y grid
+// points needs a ring of one point: (kH2X + 2)(kH2Y + 2) first-stage points
+// for kH2X * kH2Y outputs.  Neighbour k of row i sits at grid shift
+// (dx[k], dy[k]); a region point outside the grid's columns or rows holds 0
+// and is only ever met through an absent (zero) entry.  Same arithmetic as
+// k_halo_dia and the two-kernel form.  Launch: tiles_x * tiles_y blocks,
+// (kH2X + 2)(kH2Y + 2) * B * sizeof(T) bytes of dynamic shared memory.
+// Measured on the 8-slot stacked 1025^2 context (8.4M rows, one rhs per
+// block): the fused smoothing step takes 201 us against 164 us for the two
+// kernels, although it moves about 40 instead of 68 bytes per row; each
+// thread's short chain of dependent loads and the block barrier keep it at
+// 1.7 TB/s (64 x 8 tiles: 227 us).  Off by default (MG_OPT_HALO2D_BYTES).
+constexpr int kH2X = 32, kH2Y = 8;
+constexpr int kH2RX = kH2X + 2, kH2RY = kH2Y + 2;
+
+struct DiaShift {
+  int8_t dx[kMaxDia], dy[kMaxDia];
+};
+
+template <class T, int MODE>
+__global__ void __launch_bounds__(kTailThreads)
+    k_halo_dia2(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B,
+                const T* __restrict__ prm, int w, int tiles_x, DiaShift sh, int zero) {
+  extern __shared__ __align__(16) unsigned char halo_raw[];
+  T* sz = reinterpret_cast<T*>(halo_raw);
+  const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
+  const int gx0 = tx * kH2X - 1, gy0 = ty * kH2Y - 1;  // grid point of region (0, 0)
+  auto row_at = [&](int lx, int ly) -> int {  // row of a region point, or -1
+    const int gx = gx0 + lx, gy = gy0 + ly;
+    if (gx < 0 || gx >= w || gy < 0) return -1;
+    const long long r = (long long)gy * w + gx;
+    return r < L.n ? (int)r : -1;
+  };
+  const int npts = kH2RX * kH2RY;
+  for (int e = threadIdx.x; e < npts; e += blockDim.x) {
+    const int j = row_at(e % kH2RX, e / kH2RX);
+    if (j >= 0) {
+      if constexpr (MODE == HALO_PROLONG) prefetch_p(L, j);
+      prefetch_row(L, j);
+    }
+  }
+  pdl_wait();
+  pdl_launch();
+
+  // first stage on the region (own points and the one-point ring)
+  const int nz = npts * B;
+  for (int e = threadIdx.x; e < nz; e += blockDim.x) {
+    const int pt = e / B, b = e - pt * B;
+    const int j = row_at(pt % kH2RX, pt / kH2RX);
+    T z = T(0);
+    if (j >= 0) {
+      const size_t t = (size_t)j * B + b;
+      if constexpr (MODE == HALO_PROLONG) {
+        z = prolong_at(L, j, x, B, b);
+      } else {
+        z = f[t];
+        if (!zero) {
+          const T ax = row_ax(L, j, x, B, b);
+          z = fma(-L.diag[j], x[t], z) - ax;
+        }
+        if constexpr (MODE == HALO_SMOOTH) z = prm[P_THETA] * (z * L.dinv[j]);
+      }
+    }
+    sz[e] = z;
+  }
+  __syncthreads();
+
+  // second stage on the own points
+  const int nown = kH2X * kH2Y * B;
+  for (int e = threadIdx.x; e < nown; e += blockDim.x) {
+    const int pt = e / B, b = e - pt * B;
+    const int lx = 1 + pt % kH2X, ly = 1 + pt / kH2X;
+    const int i = row_at(lx, ly);
+    if (i < 0) continue;
+    const size_t t = (size_t)i * B + b;
+    const int me = ly * kH2RX + lx;
+    T s = T(0);
+#pragma unroll
+    for (int k = 0; k < kMaxDia; ++k) {
+      if (k < L.ndia) {
+        const bool nb = L.dval[(size_t)k * L.ld + i] != T(0);
+        const T zv = nb ? sz[(size_t)(me + sh.dy[k] * kH2RX + sh.dx[k]) * B + b] : T(0);
+        s += nb ? zv : T(0);
+      }
+    }
+    const T zi = sz[(size_t)me * B + b];
+    if constexpr (MODE == HALO_SMOOTH) {
+      const T phi = fma(prm[P_WB1], zi, prm[P_WB2] * (L.invdeg[i] * s));
+      const T u0 = zero ? T(0) : x[t];
+      y[t] = fma(prm[P_ETA], phi, u0);
+    } else if constexpr (MODE == HALO_RESTRICT) {
+      T p = prm[P_WR1] * zi;
+      p = fma(prm[P_WR2], L.invdeg[i] * s, p);
+      y[t] = p;
+    } else {
+      T phi = prm[P_WP1] * zi;
+      phi = fma(prm[P_WP2], L.invdeg[i] * s, phi);
+      y[t] = y[t] + phi;
+    }
+  }
+}
+
 }  // namespace mgk

@@ -425,6 +425,10 @@ struct mg_ctx {
   int opt_fcg_fp32 = 1;          // precision-32 FCG: 1 FP32 vectors + FP64 restarts, 0 FP64
   int opt_fcg_floor = 2;         // its phase floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
+  // DIA levels whose vectors (rows x rhs x value bytes) are at least this
+  // large use the 2D-tiled fused steps (0: never; measured slower than the
+  // two-kernel form on the large stacked levels, so off)
+  int64_t opt_halo2d_bytes = 0;
   int opt_sell_halo_rows = 0;  // rows per tile of the halo-fused SELL steps (0: unfused)
   int opt_sell_halo_threads = 256;  // threads per block of those steps
   // largest level vector (rows x rhs x value bytes) whose smoothing and
@@ -803,6 +807,59 @@ struct Issue {
     threads = (int)std::min<int64_t>(mgk::kTailThreads, (span * B + 31) / 32 * 32);
     return (int)tr;
   }
+  // 2D-tiled fused steps (k_halo_dia2) on a DIA level whose vectors are at
+  // least opt_halo2d_bytes: its grid width w (the offsets must be 0, +-1,
+  // +-w, +-(w-1) or +-(w+1)), the tiles and every diagonal's grid shift;
+  // false (another form) otherwise, or when the tile's shared memory for B
+  // right-hand sides exceeds kHaloSmemMax.
+  struct Halo2 {
+    int w = 0, tiles_x = 0;
+    unsigned tiles = 0;
+    size_t smem = 0;
+    mgk::DiaShift sh;
+  };
+  bool halo2d(int lev, Halo2& h) const {
+    const DevLevel<T>& D = L[lev];
+    if (c->opt_halo2d_bytes <= 0 || D.ndia == 0) return false;
+    if ((int64_t)D.n * B * (int64_t)sizeof(T) < c->opt_halo2d_bytes) return false;
+    h.smem = (size_t)mgk::kH2RX * mgk::kH2RY * B * sizeof(T);
+    if (h.smem > kHaloSmemMax) return false;
+    int m = INT_MAX;
+    for (int k = 0; k < D.ndia; ++k)
+      if (std::abs(D.doff[k]) > 1) m = std::min(m, std::abs(D.doff[k]));
+    if (m == INT_MAX) return false;
+    for (int w : {m, m + 1, m - 1}) {
+      if (w < 3) continue;
+      bool ok = true;
+      for (int k = 0; k < D.ndia && ok; ++k) {
+        ok = false;
+        for (int dy = -1; dy <= 1 && !ok; ++dy) {
+          const int dx = D.doff[k] - dy * w;
+          if (dx >= -1 && dx <= 1) {
+            h.sh.dx[k] = (int8_t)dx;
+            h.sh.dy[k] = (int8_t)dy;
+            ok = true;
+          }
+        }
+      }
+      if (!ok) continue;
+      for (int k = D.ndia; k < mgk::kMaxDia; ++k) h.sh.dx[k] = h.sh.dy[k] = 0;
+      h.w = w;
+      h.tiles_x = (w + mgk::kH2X - 1) / mgk::kH2X;
+      const int64_t rows = (D.n + (int64_t)w - 1) / w;
+      const int64_t tiles = h.tiles_x * ((rows + mgk::kH2Y - 1) / mgk::kH2Y);
+      if (tiles >= ((int64_t)1 << 31)) return false;
+      h.tiles = (unsigned)tiles;
+      return true;
+    }
+    return false;
+  }
+  template <int MODE>
+  void op_halo2(int lev, const Halo2& h, const T* f, const T* x, T* y, int zero) {
+    DevLevel<T>& D = L[lev];
+    launch(mgk::k_halo_dia2<T, MODE>, dim3(h.tiles), dim3(256), h.smem, D.view(), f, x, y, B,
+           P(lev), h.w, h.tiles_x, h.sh, zero);
+  }
   // Halo-tiled fused steps on a SELL level (halo_sell.cuh): the tile's
   // shared bytes, or 0 (two-kernel form) when the level has no halo tables
   // or the tile does not fit kSellHaloSmemMax for B right-hand sides.
@@ -890,6 +947,19 @@ struct Issue {
       if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
       return;
     }
+    Halo2 h2;
+    if (halo2d(lev, h2)) {  // large DIA level: one 2D-tiled fused kernel per step
+      T* cur = u;
+      T* oth = D.u2;
+      for (int k = 0; k < nu; ++k) {
+        pre(MG_K_SMOOTH_HALO, lev);
+        op_halo2<mgk::HALO_SMOOTH>(lev, h2, f, cur, oth, (int)(zero && k == 0));
+        post();
+        std::swap(cur, oth);
+      }
+      if (cur != u) launch(mgk::k_copy<T>, g, kThreads, 0, (const T*)cur, u, N);
+      return;
+    }
     if (const size_t hsm = sell_halo(lev)) {  // SELL: one fused kernel per step
       T* cur = u;
       T* oth = D.u2;
@@ -921,6 +991,16 @@ struct Issue {
     if (TR) {  // residual and Phi_R in one kernel, then the gather P^T
       pre(MG_K_RESTRICT_HALO, lev);
       op_halo<mgk::HALO_RESTRICT>(lev, TR, H, smem, nth, f, u, D.u2, 0);
+      post();
+      pre(MG_K_RESTRICT, lev);
+      op_gather(lev, D.u2, Fl(lev + 1), 0);
+      post();
+      return;
+    }
+    Halo2 h2;
+    if (conv(lev, mgk::P_WR2) && halo2d(lev, h2)) {  // large DIA level: 2D tiles
+      pre(MG_K_RESTRICT_HALO, lev);
+      op_halo2<mgk::HALO_RESTRICT>(lev, h2, f, u, D.u2, 0);
       post();
       pre(MG_K_RESTRICT, lev);
       op_gather(lev, D.u2, Fl(lev + 1), 0);
@@ -963,6 +1043,13 @@ struct Issue {
     if (TR) {  // P e_c, Phi_P and the update in one kernel
       pre(MG_K_PROLONG_HALO, lev);
       op_halo<mgk::HALO_PROLONG>(lev, TR, H, smem, nth, (const T*)nullptr, ec, u, 0);
+      post();
+      return;
+    }
+    Halo2 h2;
+    if (conv(lev, mgk::P_WP2) && halo2d(lev, h2)) {  // large DIA level: 2D tiles
+      pre(MG_K_PROLONG_HALO, lev);
+      op_halo2<mgk::HALO_PROLONG>(lev, h2, (const T*)nullptr, ec, u, 0);
       post();
       return;
     }
@@ -2066,6 +2153,10 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       if (value < 0 || value > (1 << 30))
         return c->fail(MG_ERR_INVALID, "mg_set_option: halo rows must be in [0, 2^30]");
       c->opt_halo_rows = value;
+      break;
+    case MG_OPT_HALO2D_BYTES:
+      if (value < 0) return c->fail(MG_ERR_INVALID, "mg_set_option: 2D halo bytes must be >= 0");
+      c->opt_halo2d_bytes = value;
       break;
     case MG_OPT_TAIL_TEAMS:
       if (value < 0 || value > 64)

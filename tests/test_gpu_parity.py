@@ -460,6 +460,39 @@ def test_launch_options_are_bitwise_neutral(prec, conv, nrhs):
         assert np.array_equal(it, outs[0][2])
 
 
+@pytest.mark.parametrize("name", ["poisson33", "checker65", "lognormal65"])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("nrhs", [1, 3, 16])
+def test_halo2d_tiles_are_bitwise_neutral(name, prec, nrhs):
+    """The 2D-tiled fused steps on DIA levels (forced on every grid level:
+    the byte threshold 1, no 1D halo, no single-block kernel; tiles wider
+    and taller than the coarse grids, ragged last tiles, 5- and 7-point
+    offsets) give the two-kernel cycle and solve bitwise, with and without
+    the convolutions."""
+    p, Ho, Hp = problem(name)
+    dt = torch.float64 if prec == 64 else torch.float32
+    f = np.random.default_rng(nrhs).standard_normal((Hp.sizes[0], nrhs))
+    for conv in (True, False):
+        prm = rand_params(Hp.J, 41, 0.1, conv=conv)
+        outs = []
+        for bytes_ in (0, 1):
+            S = Solver(Hp, prm, precision=prec, max_batch=nrhs)
+            S.set_option("tail_work", 0)
+            S.set_option("halo_rows", 0)
+            S.set_option("halo2d_bytes", bytes_)
+            u = torch.zeros((Hp.sizes[0], nrhs), dtype=dt, device=DEV)
+            fd = torch.tensor(f, dtype=dt, device=DEV)
+            for _ in range(3):
+                S.vcycle(fd, u)
+            us, info = S.solve(t64(f), tol=1e-9, max_iter=300)
+            outs.append((u.clone(), us.clone(), info.iters.copy()))
+            S.close()
+        assert torch.isfinite(outs[0][0]).all()
+        assert torch.equal(outs[1][0], outs[0][0]), (name, conv)
+        assert torch.equal(outs[1][1], outs[0][1]), (name, conv)
+        assert np.array_equal(outs[1][2], outs[0][2])
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("method", ["refine", "fcg"])
 @pytest.mark.parametrize("nrhs", [1, 3])

@@ -225,6 +225,34 @@ def test_leading_blocks_solve_equals_whole_context(N, prec):
     S.close()
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_stacked_halo2d_is_bitwise_neutral(prec):
+    """On a stacked context (a grid of width N - 2 and slots (N - 2) rows,
+    zero couplings between blocks) the 2D-tiled fused steps give the
+    two-kernel block solve bitwise, for all blocks and for leading blocks."""
+    N = 65
+    sys_list = systems(N, ["lognormal", "checker", "lognormal"], seed=7)
+    prm = LMGParams.identity(levels_for(N))
+    prm.wB[:, 1], prm.wR[:, 1], prm.wP[:, 1] = 0.1, 0.05, -0.05
+    f = t64(np.concatenate([x[1] for x in sys_list]))
+    outs = []
+    for bytes_ in (0, 1):
+        S = SquareBatch(N, 3, prm, precision=prec)
+        fill(S, sys_list)
+        S.set_option("tail_work", 0)
+        S.set_option("halo_rows", 0)
+        S.set_option("halo2d_bytes", bytes_)
+        res = []
+        for k in (3, 2):
+            u = torch.zeros_like(f)
+            info = S.solve(f, u, tol=1e-8, max_iter=300, nblocks=k)
+            res.append((u.clone(), info.iters.copy()))
+        outs.append(res)
+        S.close()
+    for (u1, i1), (u0, i0) in zip(outs[1], outs[0]):
+        assert torch.equal(u1, u0) and np.array_equal(i1, i0)
+
+
 def test_invalid_square_arguments():
     from paper_2608_29082_b300._lib import MGError
     with pytest.raises(MGError):
