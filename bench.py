@@ -391,9 +391,10 @@ def run_ours(args):
     lshape = lshape_solves = None
     if rank == 0 and not args.no_lshape:
         lshape, lshape_solves = lshape_section(dev, peak, args)
-    train_step = None
+    train_step = feat2 = None
     if rank == 0 and not args.no_lshape:
         train_step = training_step_section(dev)
+        feat2 = features2_section()
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_section(dev)
@@ -459,6 +460,7 @@ def run_ours(args):
             "roofline_lshape": lshape,
             "lshape_time_to_tol": lshape_solves,
             "training_step": train_step,
+            "roofline_features2": feat2,
             "serving": serving,
             "kernel_shares_per_vcycle": shares,
             "clocks": clocks,
@@ -563,6 +565,20 @@ def lshape_section(dev, peak, args):
                     "status": int(info.status), "max_relres_recheck": float(rr.max())}
         S.close()
     return roof, out
+
+
+def features2_section():
+    """Two features per node (the complex Helmholtz cycle, W_1, W_2 in every
+    SAGEConv): per-kernel CUDA-event times and algorithmic GB/s of an eager
+    FP32 cycle with 16 rhs on 1025^2 vertices, whose level-0 vectors exceed
+    L2, and the cycle time replayed as a graph."""
+    from types import SimpleNamespace
+    from paper_2608_29082_b300.workload_bench import features2_roofline
+    r = features2_roofline(SimpleNamespace(roof_N=1025, roof_J=6, roof_k_over_pi=16.0, seed=0))
+    top = r["kernels"][0]
+    r["dominant"] = {"kernel": f"{top['kernel']}@level{top['level']}", "achieved": top["GBps"],
+                     "peak": r["hbm_peak_gbs"], "unit": "GB/s", "frac": top["frac_of_hbm"]}
+    return r
 
 
 def training_step_section(dev):

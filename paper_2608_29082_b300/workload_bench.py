@@ -278,10 +278,33 @@ def run_profile_case(a):
     S.set_cheb(None)
     _, info = S.solve(f64, torch.zeros_like(f64), tol=1e-12, max_iter=4, method="fgmres",
                       restart=4)
+    # flexible CG with FP32 vectors, iterations driven from the host (plain
+    # graphs, which a profiler traces): a first restart, a few FP32 steps,
+    # the forced restart of the last one
+    S.set_option("device_loop", 0)
+    _, info_c = S.solve(f64, torch.zeros_like(f64), tol=1e-12, max_iter=a.fcg_steps,
+                        method="fcg")
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": f"L-shape {hier.sizes[0]} DOF, {a.batch} rhs",
-                      "fgmres_steps": int(info.iters.max())}), flush=True)
+                      "fgmres_steps": int(info.iters.max()),
+                      "fcg_steps": int(info_c.iters.max())}), flush=True)
     S.close()
+    if a.features2:
+        # the two-feature cycle on 1025^2 vertices, 16 rhs, FP32: three cycles
+        from paper_2608_29082_b300.features2 import Hierarchy2, Params2, Solver2
+        p2 = W.helmholtz_square(1025, 6, k=16 * np.pi, batch=16, seed=a.seed)
+        h2 = Hierarchy2.from_problem(p2)
+        prm = Params2.identity(h2.J)
+        prm.WB[:, 1] = 0.1 * np.eye(2)
+        S2 = Solver2(h2, prm, precision=32, max_batch=16)
+        f2 = torch.tensor(p2.f, dtype=torch.complex64, device="cuda")
+        u2 = torch.zeros_like(f2)
+        for _ in range(3):
+            S2.vcycle(f2, u2)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": f"two features, {h2.sizes[0]} DOF, 16 rhs",
+                          "max_abs_u": float(u2.abs().max())}), flush=True)
+        S2.close()
 
 
 def level_bytes2(name: str, hier, lev: int, B: int, b: int) -> float:
@@ -498,6 +521,9 @@ if __name__ == "__main__":
     pc.add_argument("--refinements", type=int, default=7)
     pc.add_argument("--batch", type=int, default=16)
     pc.add_argument("--seed", type=int, default=0)
+    pc.add_argument("--fcg-steps", type=int, default=3)
+    pc.add_argument("--features2", type=int, default=1,
+                    help="also run three two-feature cycles on 1025^2 vertices")
     a = ap.parse_args()
     torch.cuda.set_device(0)
     {"lshape": run_lshape, "training": run_training, "cheb": run_cheb,
