@@ -141,6 +141,8 @@ def run_lshape(a):
         p = LMGParams.identity(J)
         p.wB[:, 1], p.wR[:, 1], p.wP[:, 1] = 0.1, 0.05, -0.05
         S = Solver(hier, p, precision=32, max_batch=a.batch)
+        if a.sell_halo_rows:
+            S.set_option("sell_halo_rows", a.sell_halo_rows)
         f = torch.tensor(prob.f, dtype=torch.float32, device=dev)
         u = torch.zeros_like(f)
         for _ in range(a.cycles_only):
@@ -492,6 +494,8 @@ if __name__ == "__main__":
     l.add_argument("--K", type=int, default=10)
     l.add_argument("--preset", default="shared_conv")
     l.add_argument("--seed", type=int, default=0)
+    l.add_argument("--sell-halo-rows", type=int, default=0,
+                   help="with --cycles-only: the fused SELL steps' tile rows (0: two kernels)")
     l.add_argument("--cycles-only", type=int, default=0,
                    help="only run this many FP32 cycles and the per-kernel table")
     t = sub.add_parser("training")
