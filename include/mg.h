@@ -456,6 +456,18 @@ typedef struct {
 mg_status mg_vcycle_profile(mg_ctx* ctx, const void* f_dev, void* u_dev, int32_t nrhs,
                             mg_kernel_time* out, int32_t max_out, int32_t* n_out, void* stream);
 
+/* Debug builds.  A library compiled with -DMG_BOUNDS_CHECK (python -m
+ * paper_2608_29082_b300.build --debug: libmg_debug.so) checks every gathered
+ * index that comes from a table (SELL columns, prolongation parents,
+ * restriction children, fused-step halo rows and local columns) against its
+ * range, skips an out-of-range access and records the first one; mg_vcycle,
+ * mg_fmg and the solves then synchronise and return MG_ERR_INVALID with the
+ * check site and index in the message.  mg_debug_bounds returns 1 in such a
+ * build and writes (and clears) the raw record to *word (0: none; else
+ * ((site << 32) | index) + 1), 0 in a release build (*word = 0), -1 on a CUDA
+ * error.  word may be NULL. */
+int32_t mg_debug_bounds(uint64_t* word);
+
 /* Static name of a kernel kind ("unknown" if out of range). */
 const char* mg_kernel_name(int32_t kind);
 

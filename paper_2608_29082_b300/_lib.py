@@ -7,7 +7,9 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libmg.so")
+# MG_LIB_VARIANT=debug loads the index-checked build (libmg_debug.so)
+LIB_PATH = os.path.join(HERE, "libmg_debug.so" if os.environ.get("MG_LIB_VARIANT") == "debug"
+                        else "libmg.so")
 
 MG_OK = 0
 MG_NOT_CONVERGED = 1
@@ -93,6 +95,7 @@ def lib() -> C.CDLL:
                       C.c_int),
         "mg2_set_params": ([vp, f64p, f64p, f64p, f64p, f64p, C.c_int32, C.c_int32], C.c_int),
         "mg2_set_option": ([vp, C.c_int32, C.c_int64], C.c_int),
+        "mg_debug_bounds": ([C.POINTER(C.c_uint64)], C.c_int32),
         "mg2_vcycle_profile": ([vp, vp, vp, C.c_int32, C.POINTER(KernelTime), C.c_int32,
                                 C.POINTER(C.c_int32), vp], C.c_int),
         "mg2_vcycle": ([vp, vp, vp, C.c_int32, vp], C.c_int),

@@ -76,7 +76,10 @@ __global__ void __launch_bounds__(kTailThreads)
   for (int it = threadIdx.x; it < nitem; it += blockDim.x) {
     const int l = it / nq;
     const int b0 = (it - l * nq) * BV;
-    const int j = l < nown ? r0 + l : hs.hrow[h0 + (l - nown)];
+    const int j = l < nown ? r0 + l : idx_ok(hs.hrow[h0 + (l - nown)], L.n, 4);
+#ifdef MG_BOUNDS_CHECK
+    if (j < 0) continue;  // recorded; the slot is never read through a valid lcol
+#endif
     const size_t base = (size_t)j * B + b0;
     T z[BV];
     if constexpr (MODE == HALO_PROLONG) {
@@ -113,7 +116,7 @@ __global__ void __launch_bounds__(kTailThreads)
     for (int b = 0; b < BV; ++b) s[b] = T(0);
     const int end = L.sl_ptr[(i >> 5) + 1];
     for (int e = L.sl_ptr[i >> 5] + (i & 31); e < end; e += kSlice) {
-      const int lc = hs.lcol[e];
+      const int lc = idx_ok(hs.lcol[e], nown + nh, 5);
       if (lc >= 0) {
         T zv[BV];
         ldv<T, BV>(sz, (size_t)lc * B + b0, zv);

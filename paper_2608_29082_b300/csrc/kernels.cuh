@@ -30,6 +30,24 @@
 
 namespace mgk {
 
+// Index checks of the debug build (-DMG_BOUNDS_CHECK).  idx_ok(v, n, site)
+// returns v when 0 <= v < n, else -1 (the entry is then treated as absent,
+// so the access is skipped) and records the first violation in
+// g_bounds_error as ((site << 32) | (uint32_t)v) + 1; -1 passes unchanged
+// (padding).  Sites: 1 SELL column, 2 prolongation parent, 3 restriction
+// child, 4 halo row, 5 halo local column.  Without the macro idx_ok is v.
+#ifdef MG_BOUNDS_CHECK
+__device__ unsigned long long g_bounds_error = 0;
+__device__ __forceinline__ int idx_ok(int v, int n, int site) {
+  if (v == -1 || (v >= 0 && v < n)) return v;
+  atomicCAS(&g_bounds_error, 0ull,
+            (((unsigned long long)site << 32) | (unsigned long long)(unsigned)v) + 1ull);
+  return -1;
+}
+#else
+__device__ __forceinline__ int idx_ok(int v, int, int) { return v; }
+#endif
+
 constexpr int kThreads = 256;
 constexpr int kSlice = 32;
 constexpr int kMaxLevels = 16;
@@ -168,7 +186,7 @@ __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
 #pragma unroll
       for (int k = 0; k < kMaxDia; ++k) {
         const int e = beg + k * kSlice;
-        cs[k] = e < end ? L.col[e] : -1;
+        cs[k] = e < end ? idx_ok(L.col[e], L.n, 1) : -1;
         vs[k] = kVal && e < end ? L.val[e] : T(0);
       }
 #pragma unroll
@@ -176,7 +194,7 @@ __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
         if (cs[k] >= 0) fn(cs[k], vs[k], true);
     } else {
       for (int e = beg; e < end; e += kSlice) {
-        const int c = L.col[e];
+        const int c = idx_ok(L.col[e], L.n, 1);
         if (c >= 0) fn(c, kVal ? L.val[e] : T(0), true);
       }
     }
@@ -205,7 +223,7 @@ __device__ __forceinline__ T row_sum(const LV<T>& L, int i, const T* __restrict_
 template <class T>
 __device__ __forceinline__ T prolong_at(const LV<T>& L, int j, const T* __restrict__ ec, int B,
                                         int b) {
-  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.ld + j];
+  const int a = idx_ok(L.p_idx[j], L.nc, 2), c = idx_ok(L.p_idx[(size_t)L.ld + j], L.nc, 2);
   T v = T(0);
   if (a >= 0) v = L.p_w[j] * ec[(size_t)a * B + b];
   if (c >= 0) v = fma(L.p_w[(size_t)L.ld + j], ec[(size_t)c * B + b], v);
@@ -280,7 +298,7 @@ __device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict_
     T wk[kMaxKR];
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k) {
-      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.ldc + I] : -1;
+      idx[k] = k < L.KR ? idx_ok(L.r_idx[(size_t)k * L.ldc + I], L.n, 3) : -1;
       wk[k] = k < L.KR ? L.r_w[(size_t)k * L.ldc + I] : T(0);
     }
 #pragma unroll
@@ -294,7 +312,7 @@ __device__ __forceinline__ void restrict_el(const LV<T>& L, const T* __restrict_
     }
   } else {
     for (int k = 0; k < L.KR; ++k) {
-      const int i = L.r_idx[(size_t)k * L.ldc + I];
+      const int i = idx_ok(L.r_idx[(size_t)k * L.ldc + I], L.n, 3);
       if (i < 0) break;
       T phi = w1 * r[(size_t)i * B + b];
       if (conv) phi = fma(w2, L.invdeg[i] * row_sum(L, i, r, B, b), phi);
@@ -352,7 +370,7 @@ __device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ 
     T wk[kMaxKR];
 #pragma unroll
     for (int k = 0; k < kMaxKR; ++k) {
-      idx[k] = k < L.KR ? L.r_idx[(size_t)k * L.ldc + I] : -1;
+      idx[k] = k < L.KR ? idx_ok(L.r_idx[(size_t)k * L.ldc + I], L.n, 3) : -1;
       wk[k] = k < L.KR ? L.r_w[(size_t)k * L.ldc + I] : T(0);
     }
 #pragma unroll
@@ -360,7 +378,7 @@ __device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ 
       if (idx[k] >= 0) acc = fma(wk[k], phi[(size_t)idx[k] * B + b], acc);
   } else {
     for (int k = 0; k < L.KR; ++k) {
-      const int i = L.r_idx[(size_t)k * L.ldc + I];
+      const int i = idx_ok(L.r_idx[(size_t)k * L.ldc + I], L.n, 3);
       if (i < 0) break;
       acc = fma(L.r_w[(size_t)k * L.ldc + I], phi[(size_t)i * B + b], acc);
     }

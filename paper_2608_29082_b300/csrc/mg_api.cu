@@ -1299,6 +1299,30 @@ mg_status sync_params(mg_ctx* c, cudaStream_t s) {
   return MG_OK;
 }
 
+// Debug build (-DMG_BOUNDS_CHECK): the first out-of-range index a kernel met
+// (kernels.cuh idx_ok) becomes MG_ERR_INVALID of the call that launched it;
+// the record is cleared.  Synchronises s.  Other builds: MG_OK.
+mg_status bounds_status(mg_ctx* c, cudaStream_t s, const char* who) {
+#ifdef MG_BOUNDS_CHECK
+  unsigned long long w = 0;
+  MG_CUDA(cudaStreamSynchronize(s));
+  MG_CUDA(cudaMemcpyFromSymbol(&w, mgk::g_bounds_error, sizeof(w)));
+  if (w) {
+    const unsigned long long zero = 0;
+    MG_CUDA(cudaMemcpyToSymbol(mgk::g_bounds_error, &zero, sizeof(zero)));
+    char buf[192];
+    snprintf(buf, sizeof buf, "%s: index out of range (check site %llu, index %d)", who,
+             (w - 1) >> 32, (int)(unsigned)((w - 1) & 0xffffffffull));
+    return c->fail(MG_ERR_INVALID, buf);
+  }
+#else
+  (void)c;
+  (void)s;
+  (void)who;
+#endif
+  return MG_OK;
+}
+
 // Captures fn(stream) into a graph stored under key (or reuses it) and
 // launches it on s.
 template <class Fn>
@@ -1330,7 +1354,7 @@ mg_status run_graph(mg_ctx* c, const std::tuple<int, const void*, const void*, i
   }
   MG_CUDA(cudaGraphLaunch(it->second.exec, s));
   c->launches += it->second.nkernels;
-  return MG_OK;
+  return bounds_status(c, s, "mg_vcycle / mg_fmg / a solve step");
 }
 
 // An iterative solve: pre once (it ends with k_check), then body while
@@ -1363,7 +1387,7 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
       if (st != MG_OK) return st;
       MG_CUDA(cudaStreamSynchronize(s));
     }
-    return MG_OK;
+    return bounds_status(c, s, who);
   }
   auto key = std::make_tuple(id, f, u, B, c->structure);
   auto it = c->graphs.find(key);
@@ -1428,7 +1452,7 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
   MG_CUDA(cudaMemcpyAsync(c->h_state, c->state, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   MG_CUDA(cudaStreamSynchronize(s));
   c->launches += it->second.nkernels + (int64_t)c->h_state[2] * it->second.nbody;
-  return MG_OK;
+  return bounds_status(c, s, who);
 }
 
 // Copies the per-right-hand-side iteration counts and relative residuals of
@@ -2196,6 +2220,20 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   c->graphs.clear();
   return MG_OK;
+}
+
+extern "C" int32_t mg_debug_bounds(uint64_t* word) {
+#ifdef MG_BOUNDS_CHECK
+  unsigned long long w = 0;
+  if (cudaMemcpyFromSymbol(&w, mgk::g_bounds_error, sizeof(w)) != cudaSuccess) return -1;
+  const unsigned long long zero = 0;
+  if (w && cudaMemcpyToSymbol(mgk::g_bounds_error, &zero, sizeof(zero)) != cudaSuccess) return -1;
+  if (word) *word = w;
+  return 1;
+#else
+  if (word) *word = 0;
+  return 0;
+#endif
 }
 
 extern "C" mg_status mg_set_layout_policy(int32_t policy) {

@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __rest
   for (int b = 0; b < BV; ++b) acc[b] = T(0);
   const T w1 = prm[P_WR1];
   for (int k = 0; k < L.KR; ++k) {
-    const int c = L.r_idx[(size_t)k * L.ldc + i];
+    const int c = idx_ok(L.r_idx[(size_t)k * L.ldc + i], L.n, 3);
     if (c < 0) break;
     const T w = L.r_w[(size_t)k * L.ldc + i];
     T xv[BV];
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_mb(LV<T> L, const T* __rest
 template <class T, int BV>
 __device__ __forceinline__ void prolong_at_mb(const LV<T>& L, int j, const T* __restrict__ ec,
                                               int B, int b0, T (&v)[BV]) {
-  const int a = L.p_idx[j], c = L.p_idx[(size_t)L.ld + j];
+  const int a = idx_ok(L.p_idx[j], L.nc, 2), c = idx_ok(L.p_idx[(size_t)L.ld + j], L.nc, 2);
 #pragma unroll
   for (int b = 0; b < BV; ++b) v[b] = T(0);
   if (a >= 0) {

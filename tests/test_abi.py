@@ -18,7 +18,7 @@ def declared_functions():
             continue
         src = open(os.path.join(ROOT, "include", fn)).read()
         src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-        names += re.findall(r"^\s*(?:mg_status|void|int64_t)\s+(mg2?_\w+)\s*\(", src,
+        names += re.findall(r"^\s*(?:mg_status|void|int64_t|int32_t)\s+(mg2?_\w+)\s*\(", src,
                             flags=re.M)
     return sorted(set(names))
 
@@ -29,6 +29,21 @@ def test_every_declared_symbol_is_exported():
     assert len(names) >= 15
     missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, missing
+
+
+def test_release_build_has_no_index_checks_and_debug_build_exports_the_abi():
+    """mg_debug_bounds reports a release build without touching the device;
+    the index-checked build, when it has been built, exports the same
+    functions."""
+    lib = L.lib()
+    w = C.c_uint64(5)
+    assert lib.mg_debug_bounds(C.byref(w)) == 0 and w.value == 0
+    assert lib.mg_debug_bounds(None) == 0
+    dbg = os.path.join(os.path.dirname(L.LIB_PATH), "libmg_debug.so")
+    if os.path.exists(dbg):
+        d = C.CDLL(dbg)
+        missing = [n for n in declared_functions() if not hasattr(d, n)]
+        assert not missing, missing
 
 
 def test_invalid_arguments_are_rejected_without_gpu():
