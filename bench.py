@@ -505,7 +505,7 @@ def lshape_section(dev, peak, args):
     S.close()
     top = rows[0]
     hbm = [r for r in rows if r["GBps"] and r["level"] == 0]
-    # the level-0 smoothing step: SURVEY-style algorithmic bytes
+    # the level-0 smoothing step: its algorithmic bytes (each array once)
     # s (b_v + 4) + 3 B b_x + 4 per row over the time of one step
     n0 = hier.sizes[0]
     nnz0 = hier.A[0].data.size
