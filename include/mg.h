@@ -382,13 +382,18 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     neutral; measured slower than the two-kernel form on
  *                     the 8.4M-row stacked 1025^2 level (201 against 164 us
  *                     per smoothing step), so it is off.
- *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1
- *                     (default): FP32 vectors in phases of FCG(1) on the
- *                     scaled correction equation, each phase ended by an FP64
+ *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1:
+ *                     FP32 vectors in phases of FCG(1) on the scaled
+ *                     correction equation, each phase ended by an FP64
  *                     restart (u += 2^s e, the true residual f - A u in FP64,
  *                     the test, a fresh direction); 0: FP64 vectors
- *                     throughout, the FP32 cycle on the scaled residual.
- *                     FP64 contexts ignore it.
+ *                     throughout, the FP32 cycle on the scaled residual; 2
+ *                     (default): FP32 vectors when level 0 has at least 2^20
+ *                     rows (there the FP64 vector work, bound by the FP64
+ *                     pipe, dominates a step; measured 2.5x on the 3.1M-row
+ *                     L-shape), else FP64 vectors (fewer steps: 17 against
+ *                     23 on the 513^2 checkerboard).  The choice depends on
+ *                     the operator, not the batch.  FP64 contexts ignore it.
  *   MG_OPT_FCG_FLOOR  the phase of a right-hand side ends once its
  *                     recurrence residual is below 10^-value times the
  *                     phase's first (default 2; 0: no floor; at most 15), or

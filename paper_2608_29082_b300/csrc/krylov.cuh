@@ -285,18 +285,19 @@ __global__ void __launch_bounds__(kRedRows * 32 / BV) k32_spmv_dots_mb(LV<float>
       const int i = i0 + kRedRows * k;
       if (i >= L.n) break;
       const size_t base = (size_t)i * B + b0;
-      float pv[BV], rv[BV], ax[BV], qv[BV];
-      ldg<float, BV>(p, base, pv);
-      ldg<float, BV>(r, base, rv);
+      float pv[BV], ax[BV];
       row_ax_mb<float, BV>(L, i, p, B, b0, ax);
+      ldg<float, BV>(p, base, pv);
       const float d = L.diag[i];
 #pragma unroll
       for (int j = 0; j < BV; ++j) {
-        qv[j] = fmaf(d, pv[j], ax[j]);
-        pq[j] = fmaf(pv[j], qv[j], pq[j]);
-        pr[j] = fmaf(pv[j], rv[j], pr[j]);
+        ax[j] = fmaf(d, pv[j], ax[j]);  // q
+        pq[j] = fmaf(pv[j], ax[j], pq[j]);
       }
-      stg<float, BV>(q, base, qv);
+      stg<float, BV>(q, base, ax);
+      ldg<float, BV>(r, base, ax);  // r, in the registers q no longer needs
+#pragma unroll
+      for (int j = 0; j < BV; ++j) pr[j] = fmaf(pv[j], ax[j], pr[j]);
     }
   }
   // column c of the block is right-hand side blockIdx.y * bt + c; row g of

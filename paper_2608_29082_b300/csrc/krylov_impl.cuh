@@ -39,6 +39,9 @@ mg_status fcg_buffers(mg_ctx* c) {
   return MG_OK;
 }
 
+// MG_OPT_FCG_FP32 = 2: FP32 vectors from this many level-0 rows on
+constexpr int kFcg32Rows = 1 << 20;
+
 mg_status fcg32_buffers(mg_ctx* c) {
   if (c->k32_p) return MG_OK;
   const size_t v = (size_t)c->n[0] * c->maxB * sizeof(float);
@@ -273,7 +276,12 @@ extern "C" mg_status mg_solve_fcg(mg_ctx* c, const double* f, double* u, int32_t
   cudaStream_t s = (cudaStream_t)stream;
   mg_status st = sync_params(c, s);
   if (st != MG_OK) return st;
-  if (c->prec == 32 && c->opt_fcg_fp32) {
+  // FP32 vectors where the FP64 vector work is large (it is bound by B300's
+  // FP64 pipe); on smaller levels the FP64 form converges in fewer steps.
+  // The choice depends on the operator only, never on the batch.
+  const bool fp32_vectors =
+      c->prec == 32 && (c->opt_fcg_fp32 == 1 || (c->opt_fcg_fp32 == 2 && c->n[0] >= kFcg32Rows));
+  if (fp32_vectors) {
     const double fl = c->opt_fcg_floor > 0 ? std::pow(10.0, -c->opt_fcg_floor) : 0.0;
     c->solve_ctl[0] = tol;
     c->solve_ctl[1] = (double)max_iter;

@@ -422,7 +422,9 @@ struct mg_ctx {
   int opt_device_loop = 1;       // solve loops as while nodes (0: host-driven plain graphs)
   int opt_fcg_precond = 0;       // preconditioner of mg_solve_fcg: 0 V-cycle, 1 full multigrid
   int opt_fgmres_floor = 4;      // FP32 FGMRES cycle floor, 10^-value (0: none)
-  int opt_fcg_fp32 = 1;          // precision-32 FCG: 1 FP32 vectors + FP64 restarts, 0 FP64
+  // precision-32 FCG: 1 FP32 vectors + FP64 restarts, 0 FP64 vectors, 2 FP32
+  // vectors from kFcg32Rows level-0 rows on
+  int opt_fcg_fp32 = 2;
   int opt_fcg_floor = 2;         // its phase floor, 10^-value (0: none)
   int64_t opt_halo_rows = 256;   // rows per block of the halo-fused DIA steps (0: unfused)
   // DIA levels whose vectors (rows x rhs x value bytes) are at least this
@@ -2164,8 +2166,8 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
       c->opt_fgmres_floor = (int)value;
       break;
     case MG_OPT_FCG_FP32:
-      if (value != 0 && value != 1)
-        return c->fail(MG_ERR_INVALID, "mg_set_option: FCG FP32 must be 0 or 1");
+      if (value != 0 && value != 1 && value != 2)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: FCG FP32 must be 0, 1 or 2");
       c->opt_fcg_fp32 = (int)value;
       break;
     case MG_OPT_FCG_FLOOR:

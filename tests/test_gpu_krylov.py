@@ -170,7 +170,7 @@ def test_fgmres_iterates_and_estimates_match_oracle(name, pc):
 
 # ----------------------------------------------- a caller's own stream ----
 
-@pytest.mark.parametrize("method", ["refine", "fcg", "fgmres"])
+@pytest.mark.parametrize("method", ["refine", "fcg", "fcg32", "fgmres"])
 @pytest.mark.parametrize("prec", [64, 32])
 def test_solve_on_nonblocking_stream_reports_its_own_results(method, prec):
     """On a torch stream (non-blocking with respect to the legacy default
@@ -181,6 +181,9 @@ def test_solve_on_nonblocking_stream_reports_its_own_results(method, prec):
     prm = rand_params(Hp.J, 17, 0.05)
     B = p.f.shape[1]
     S = Solver(Hp, prm, precision=prec, max_batch=B)
+    if method == "fcg32":  # flexible CG with FP32 vectors
+        S.set_option("fcg_fp32", 1)
+        method = "fcg"
     # a previous solve with a looser tolerance leaves other counts behind
     S.solve(t64(p.f), tol=1e-2, max_iter=300, method=method, restart=10)
     side = torch.cuda.Stream()
@@ -199,16 +202,21 @@ def test_solve_on_nonblocking_stream_reports_its_own_results(method, prec):
 
 # ------------------------------------------------- failure detection ------
 
-@pytest.mark.parametrize("method", ["refine", "fcg", "fgmres"])
+@pytest.mark.parametrize("method", ["refine", "fcg", "fcg32", "fgmres"])
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("where", ["f", "u"])
 def test_nonfinite_input_returns_diverged(method, prec, where):
     """A NaN or Inf in a host-built right-hand side or initial guess is a
     non-finite residual: the solve returns MG_ERR_DIVERGED (no device fault),
-    and the context keeps working for the next solve."""
+    and the context keeps working for the next solve ("fcg32": flexible CG
+    with FP32 vectors, whose first FP64 restart meets the non-finite
+    residual)."""
     p, Ho, Hp = problem("checker65")
     B = p.f.shape[1]
     S = Solver(Hp, LMGParams.identity(Hp.J), precision=prec, max_batch=B)
+    if method == "fcg32":
+        S.set_option("fcg_fp32", 1)
+        method = "fcg"
     f = np.array(p.f)
     u0 = np.zeros_like(f)
     if where == "f":

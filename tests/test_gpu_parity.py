@@ -367,7 +367,7 @@ def test_fcg_fp32_vectors_against_fp64_vectors(name):
         with pytest.raises(MGError):
             S.set_option("fcg_floor", bad)
     with pytest.raises(MGError):
-        S.set_option("fcg_fp32", 2)
+        S.set_option("fcg_fp32", 3)
     S.close()
 
 
@@ -378,6 +378,7 @@ def test_fcg_fp32_last_iteration_restarts():
     p, Ho, Hp = problem("checker65")
     prm = rand_params(Hp.J, 61, 0.05)
     S = Solver(Hp, prm, precision=32, max_batch=p.f.shape[1])
+    S.set_option("fcg_fp32", 1)
     for k in (1, 3, 7):
         u, info = S.solve(t64(p.f), tol=1e-14, max_iter=k, method="fcg")
         assert info.status == 1 and (info.iters == k).all(), (k, info.iters)
