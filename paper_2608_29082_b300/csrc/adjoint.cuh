@@ -57,12 +57,12 @@ __device__ __forceinline__ void block_dots(const W (&v)[Q], double* __restrict__
   }
 }
 
-// grad[idx_q] += sum_k partial[k*Q + q]; one block per q.
-__global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restrict__ partial,
-                                                         int nblk, int Q, double* __restrict__ grad,
-                                                         int i0, int i1, int i2, int i3) {
+// grad[idx] += sum_k partial[k*Q + q] by one block of kThreads threads
+// (strided per thread, then a fixed tree).
+__device__ __forceinline__ void grad_accum_block(const double* __restrict__ partial, int nblk,
+                                                 int Q, int q, double* __restrict__ grad,
+                                                 int idx) {
   __shared__ double sh[kThreads];
-  const int q = blockIdx.x;
   double s = 0.0;
   for (int k = threadIdx.x; k < nblk; k += kThreads) s += partial[(size_t)k * Q + q];
   sh[threadIdx.x] = s;
@@ -71,10 +71,40 @@ __global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restric
     if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const int idx = q == 0 ? i0 : q == 1 ? i1 : q == 2 ? i2 : i3;
-    grad[idx] += sh[0];
-  }
+  if (threadIdx.x == 0) grad[idx] += sh[0];
+}
+
+// grad[idx_q] += sum_k partial[k*Q + q]; one block per q.
+__global__ void __launch_bounds__(kThreads) k_grad_accum(const double* __restrict__ partial,
+                                                         int nblk, int Q, double* __restrict__ grad,
+                                                         int i0, int i1, int i2, int i3) {
+  const int q = blockIdx.x;
+  grad_accum_block(partial, nblk, Q, q, grad, q == 0 ? i0 : q == 1 ? i1 : q == 2 ? i2 : i3);
+}
+
+// Parameter-gradient sums folded into the kernel that follows their
+// producers: up to two jobs, each the cross-block sum of a dot kernel's
+// partials into Q gradient entries (k_grad_accum's work, block by block).
+// The host kernel runs its own nwork blocks and Q[0] + Q[1] more, one per
+// entry.  Folding saves a launch per job; every entry still receives its
+// sums in the order the jobs were issued.
+struct GradJobs {
+  const double* partial[2];
+  int nblk[2], Q[2];
+  int idx[2][4];
+  int nwork;
+  double* grad;
+};
+
+// true (and the job's block done) for the extra blocks of a host kernel
+__device__ __forceinline__ bool grad_job_block(const GradJobs& a) {
+  const int k = (int)blockIdx.x - a.nwork;
+  if (k < 0) return false;
+  if (k < a.Q[0])
+    grad_accum_block(a.partial[0], a.nblk[0], a.Q[0], k, a.grad, a.idx[0][k]);
+  else if (k < a.Q[0] + a.Q[1])
+    grad_accum_block(a.partial[1], a.nblk[1], a.Q[1], k - a.Q[0], a.grad, a.idx[1][k - a.Q[0]]);
+  return true;
 }
 
 // sum_{j in N(i)} invdeg_j x_j   (row i of M^T x, without the outer factor)
@@ -108,6 +138,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth(LV<T> L, const T* __res
                                                          T* __restrict__ rbar, int B,
                                                          const T* __restrict__ prm,
                                                          double* __restrict__ partial) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   T v[4] = {T(0), T(0), T(0), T(0)};
   if (t < (size_t)L.n * B) {
@@ -135,7 +166,9 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_adj_apply_a(LV<T> L, T* __restrict__ ubar,
                                                           const T* __restrict__ rbar,
                                                           T* __restrict__ fbar, int B,
-                                                          int fbar_set) {
+                                                          int fbar_set, GradJobs acc) {
+  pdl_wait();
+  if (grad_job_block(acc)) return;
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)L.n * B) return;
   const int i = (int)(t / B), b = (int)(t - (size_t)i * B);
@@ -156,6 +189,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_restrict(LV<T> L, const T* __r
                                                            T* __restrict__ rbar, int B,
                                                            const T* __restrict__ prm,
                                                            double* __restrict__ partial) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   T v[2] = {T(0), T(0)};
   if (t < (size_t)L.n * B) {
@@ -183,6 +217,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_adj_prolong_fine(LV<T> L, const T* __restrict__ ubar,
                                                                T* __restrict__ g, int B,
                                                                const T* __restrict__ prm) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)L.n * B) return;
   int i, b;
@@ -197,6 +232,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_adj_prolong_dots(LV<T> L, const T* __restrict__ ubar,
                                                                const T* __restrict__ pe, int B,
                                                                double* __restrict__ partial) {
+  pdl_wait();
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   T v[2] = {T(0), T(0)};
   if (t < (size_t)L.n * B) {
@@ -274,6 +310,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_smooth_mb(LV<T> L, const T* __
                                                             T* __restrict__ rbar, int B,
                                                             const T* __restrict__ prm,
                                                             double* __restrict__ partial) {
+  pdl_wait();
   const int nq = B / BV;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = g / nq;
@@ -326,7 +363,9 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_adj_apply_a_mb(LV<T> L, T* __restrict__ ubar,
                                                              const T* __restrict__ rbar,
                                                              T* __restrict__ fbar, int B,
-                                                             int fbar_set) {
+                                                             int fbar_set, GradJobs acc) {
+  pdl_wait();
+  if (grad_job_block(acc)) return;
   const int nq = B / BV;
   const int g = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = g / nq;

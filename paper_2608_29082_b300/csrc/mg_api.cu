@@ -446,6 +446,10 @@ struct mg_ctx {
   std::vector<void*> ck_u, bw_ubar, bw_fbar, bw_r, bw_rbar;
   void* ck_f0 = nullptr;
   double* bw_partial = nullptr;
+  // per level: the prolongation-adjoint dots, summed into the gradient by
+  // the same level's restriction adjoint (after the coarse levels ran)
+  double* bw_partial_p = nullptr;
+  size_t bw_nblk = 0;
   double* bw_gp = nullptr;  // parameter gradients of the captured backward [J-1][P_COUNT]
 
   mg_status fail(mg_status s, const std::string& m) {

@@ -48,6 +48,8 @@ void train_free(mg_ctx* c) {
   c->bw_rbar.clear();
   c->ck_f0 = nullptr;
   c->bw_partial = nullptr;
+  c->bw_partial_p = nullptr;
+  c->bw_nblk = 0;
   c->bw_gp = nullptr;
   c->trK = c->trB = 0;
   c->tr_recorded = false;
@@ -92,6 +94,10 @@ mg_status ensure_train(mg_ctx* c, int K, int B) {
   }
   const size_t nblk = ((size_t)c->n[0] * B + kThreads - 1) / kThreads + 1;
   if ((st = train_alloc(c, (void**)&c->bw_partial, nblk * 4 * sizeof(double))) != MG_OK) return st;
+  if ((st = train_alloc(c, (void**)&c->bw_partial_p, (size_t)J * nblk * 2 * sizeof(double))) !=
+      MG_OK)
+    return st;
+  c->bw_nblk = nblk;
   if ((st = train_alloc(c, (void**)&c->bw_gp, (size_t)(J - 1) * mgk::P_COUNT * sizeof(double))) !=
       MG_OK)
     return st;
@@ -132,12 +138,42 @@ struct Backward {
     }
   }
 
-  void accum(int lev, int Q, size_t nblk, int a, int b2, int c2, int d) {
+  // A gradient job (adjoint.cuh GradJobs): the cross-block sums of a dot
+  // kernel's nblk x Q partials into the level's entries a, b2, c2, d.
+  void job(mgk::GradJobs& g, int j, const double* partial, int lev, int Q, size_t nblk, int a,
+           int b2, int c2, int d) const {
     const int base = lev * mgk::P_COUNT;
-    mgk::k_grad_accum<<<Q, kThreads, 0, s>>>(c->bw_partial, (int)nblk, Q, grad, base + a,
-                                             base + b2, base + (c2 < 0 ? a : c2),
-                                             base + (d < 0 ? a : d));
-    is.nk++;
+    g.partial[j] = partial;
+    g.nblk[j] = (int)nblk;
+    g.Q[j] = Q;
+    g.idx[j][0] = base + a;
+    g.idx[j][1] = base + b2;
+    g.idx[j][2] = base + (c2 < 0 ? a : c2);
+    g.idx[j][3] = base + (d < 0 ? a : d);
+    g.grad = grad;
+  }
+  static mgk::GradJobs no_jobs() {
+    mgk::GradJobs g;
+    std::memset(&g, 0, sizeof(g));
+    return g;
+  }
+  // ubar -= A rbar, fbar += rbar, with the gradient jobs' sums in extra blocks
+  void apply_a(int lev, T* ubar, const T* rbar, T* fbar, mgk::GradJobs acc) {
+    DevLevel<T>& D = L[lev];
+    if (const int bv = is.mbv()) {
+      is.with_bv(bv, [&](auto kk) {
+        const dim3 gm = is.mb_grid(D.n, bv);
+        acc.nwork = (int)gm.x;
+        is.launch(mgk::k_adj_apply_a_mb<T, decltype(kk)::value>,
+                  dim3(gm.x + acc.Q[0] + acc.Q[1]), dim3(kThreads), 0, D.view(), ubar, rbar, fbar,
+                  B, 0, acc);
+      });
+    } else {
+      const dim3 g = grid_for((size_t)D.n * B);
+      acc.nwork = (int)g.x;
+      is.launch(mgk::k_adj_apply_a<T>, dim3(g.x + acc.Q[0] + acc.Q[1]), dim3(kThreads), 0,
+                D.view(), ubar, rbar, fbar, B, 0, acc);
+    }
   }
 
   // Adjoint of the smoothing step uin -> (next); ubar holds the adjoint of
@@ -149,22 +185,22 @@ struct Backward {
     T* r = V(c->bw_r[lev]);
     T* rbar = V(c->bw_rbar[lev]);
     is.op_residual(lev, f, uin, r, 0, zero);
+    mgk::GradJobs acc = no_jobs();
     if (const int bv = is.mbv()) {  // multi-rhs forms (B > 1)
       is.with_bv(bv, [&](auto kk) {
         constexpr int BV = decltype(kk)::value;
         const dim3 gm = is.mb_grid(D.n, bv);
-        mgk::k_adj_smooth_mb<T, BV><<<gm, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B,
-                                                             is.P(lev), c->bw_partial);
-        accum(lev, 4, gm.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
-        mgk::k_adj_apply_a_mb<T, BV><<<gm, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+        is.launch(mgk::k_adj_smooth_mb<T, BV>, gm, dim3(kThreads), 0, D.view(), (const T*)ubar,
+                  (const T*)r, rbar, B, is.P(lev), c->bw_partial);
+        job(acc, 0, c->bw_partial, lev, 4, gm.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2,
+            mgk::P_THETA);
       });
     } else {
-      mgk::k_adj_smooth<T><<<g, kThreads, 0, s>>>(D.view(), ubar, r, rbar, B, is.P(lev),
-                                                   c->bw_partial);
-      accum(lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
-      mgk::k_adj_apply_a<T><<<g, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
+      is.launch(mgk::k_adj_smooth<T>, g, dim3(kThreads), 0, D.view(), (const T*)ubar,
+                (const T*)r, rbar, B, is.P(lev), c->bw_partial);
+      job(acc, 0, c->bw_partial, lev, 4, g.x, mgk::P_ETA, mgk::P_WB1, mgk::P_WB2, mgk::P_THETA);
     }
-    is.nk += 2;
+    apply_a(lev, ubar, rbar, fbar, acc);
   }
 
   // Level lev of cycle k: ubar (adjoint of the level's output) -> adjoint of
@@ -200,13 +236,15 @@ struct Backward {
     const dim3 gf = grid_for((size_t)D.n * B);
     // g = Phi_P^T ubar per fine row, ebar = P^T g (the gather of the
     // restriction), P e per fine row for the dots; D.t and D.u2 are free here
-    mgk::k_adj_prolong_fine<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, D.t, B, is.P(lev));
-    is.nk++;
+    is.launch(mgk::k_adj_prolong_fine<T>, gf, dim3(kThreads), 0, D.view(), (const T*)ubar, D.t, B,
+              is.P(lev));
     is.op_gather(lev, D.t, ebar, 0);
     is.op_pe(lev, ec, D.u2);
-    mgk::k_adj_prolong_dots<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, D.u2, B, c->bw_partial);
-    is.nk++;
-    accum(lev, 2, gf.x, mgk::P_WP1, mgk::P_WP2, -1, -1);
+    // the dots go to this level's own partials: the coarse levels below
+    // reuse bw_partial before the restriction adjoint sums them
+    double* pdots = c->bw_partial_p + (size_t)lev * c->bw_nblk * 2;
+    is.launch(mgk::k_adj_prolong_dots<T>, gf, dim3(kThreads), 0, D.view(), (const T*)ubar,
+              (const T*)D.u2, B, pdots);
     // coarse level (its input iterate is zero)
     T* fcbar = V(c->bw_fbar[lev + 1]);
     cudaMemsetAsync(fcbar, 0, vbytes(lev + 1), s);
@@ -216,18 +254,12 @@ struct Backward {
     T* rbar = V(c->bw_rbar[lev]);
     is.op_residual(lev, f, V(it[np]), r, 0, zero_in && np == 0);
     is.op_pe(lev, fcbar, D.t);  // P rcbar per fine row
-    mgk::k_adj_restrict<T><<<gf, kThreads, 0, s>>>(D.view(), D.t, r, rbar, B, is.P(lev),
-                                                    c->bw_partial);
-    accum(lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
-    if (const int bv = is.mbv()) {
-      is.with_bv(bv, [&](auto kk) {
-        mgk::k_adj_apply_a_mb<T, decltype(kk)::value><<<is.mb_grid(D.n, bv), kThreads, 0, s>>>(
-            D.view(), ubar, rbar, fbar, B, 0);
-      });
-    } else {
-      mgk::k_adj_apply_a<T><<<gf, kThreads, 0, s>>>(D.view(), ubar, rbar, fbar, B, 0);
-    }
-    is.nk += 2;
+    is.launch(mgk::k_adj_restrict<T>, gf, dim3(kThreads), 0, D.view(), (const T*)D.t,
+              (const T*)r, rbar, B, is.P(lev), c->bw_partial);
+    mgk::GradJobs acc = no_jobs();
+    job(acc, 0, c->bw_partial, lev, 2, gf.x, mgk::P_WR1, mgk::P_WR2, -1, -1);
+    job(acc, 1, pdots, lev, 2, gf.x, mgk::P_WP1, mgk::P_WP2, -1, -1);
+    apply_a(lev, ubar, rbar, fbar, acc);
     // reverse: pre-smoothing
     for (int j = np - 1; j >= 0; --j) adj_step(lev, f, V(it[j]), zero_in && j == 0, ubar, fbar);
   }
