@@ -678,6 +678,14 @@ mg_status mg2_set_params(mg2_ctx* ctx, const double* theta, const double* eta, c
  *                     right-hand sides (32 bytes) that divides nrhs, so a
  *                     row's entries are read once per tile; 0: one thread
  *                     per (row, rhs).
+ *   MG_OPT_TAIL_WORK  levels with rows * nrhs <= value, and every coarser
+ *                     one but the coarsest, run in one thread block with block
+ *                     barriers between the steps (two launches around the
+ *                     coarsest product), when that covers a level above the
+ *                     coarsest (at most 8 levels).  0 (default): never; at
+ *                     257^2 with one rhs it measured no faster in precision
+ *                     32 (0.102 ms per cycle either way) and slower in
+ *                     precision 64 (0.31 against 0.23 ms).
  * Other options: MG_ERR_INVALID.  Drops the captured cycle graphs. */
 mg_status mg2_set_option(mg2_ctx* ctx, int32_t option, int64_t value);
 

@@ -111,21 +111,25 @@ __device__ __forceinline__ void st_pairs(typename Pair<T>::type* __restrict__ x,
   const int g = blockIdx.x * blockDim.x + threadIdx.x;    \
   const int i = g / nq;                                   \
   if (i >= (NROWS)) return;                               \
-  const int b0 = (g - i * nq) * BV;                       \
-  const size_t base = (size_t)i * B + b0;
+  const int b0 = (g - i * nq) * BV;
+
+// ---- element steps: row i, right-hand sides b0 .. b0 + BV - 1 ----------
+// (the grid kernels below and the single-block small-levels kernel k2_tail
+// run the same functions, so every launch form rounds alike)
 
 // out = f - A u (u_zero: u = 0), then optionally out = theta * out / A_ii
 // (dinv = 1 / A_ii, complex)
 template <class T, int BV>
-__global__ void __launch_bounds__(kF2Threads)
-    k2_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                const typename Pair<T>::type* __restrict__ av,
-                const typename Pair<T>::type* __restrict__ f,
-                const typename Pair<T>::type* __restrict__ u, typename Pair<T>::type* __restrict__ out,
-                int B, const typename Pair<T>::type* __restrict__ dinv, T theta, int scale,
-                int u_zero) {
+__device__ __forceinline__ void res2_el(int i, int b0, const int* __restrict__ rp,
+                                        const int* __restrict__ ci,
+                                        const typename Pair<T>::type* __restrict__ av,
+                                        const typename Pair<T>::type* __restrict__ f,
+                                        const typename Pair<T>::type* __restrict__ u,
+                                        typename Pair<T>::type* __restrict__ out, int B,
+                                        const typename Pair<T>::type* __restrict__ dinv, T theta,
+                                        int scale, int u_zero) {
   using P2 = typename Pair<T>::type;
-  MG2_PROLOGUE(n)
+  const size_t base = (size_t)i * B + b0;
   P2 r[BV];
   ld_pairs<T, BV>(f, base, r);
   if (!u_zero) {
@@ -155,12 +159,13 @@ __global__ void __launch_bounds__(kF2Threads)
 // phi_i = W_1 x_i + W_2 inv_deg_i sum_{j != i in row i} x_j; mode 0: y = phi,
 // 1: y += eta phi, 2: y += phi.  x and y are distinct buffers.
 template <class T, int BV>
-__global__ void __launch_bounds__(kF2Threads)
-    k2_conv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-            const T* __restrict__ invdeg, const typename Pair<T>::type* __restrict__ x,
-            typename Pair<T>::type* __restrict__ y, int B, Conv2<T> w, T eta, int mode) {
+__device__ __forceinline__ void conv2_el(int i, int b0, const int* __restrict__ rp,
+                                         const int* __restrict__ ci, const T* __restrict__ invdeg,
+                                         const typename Pair<T>::type* __restrict__ x,
+                                         typename Pair<T>::type* __restrict__ y, int B,
+                                         const Conv2<T>& w, T eta, int mode) {
   using P2 = typename Pair<T>::type;
-  MG2_PROLOGUE(n)
+  const size_t base = (size_t)i * B + b0;
   T sx[BV], sy[BV];
 #pragma unroll
   for (int j = 0; j < BV; ++j) sx[j] = sy[j] = T(0);
@@ -196,14 +201,13 @@ __global__ void __launch_bounds__(kF2Threads)
   st_pairs<T, BV>(y, base, o);
 }
 
-// y = M x for a real CSR matrix M (n rows) on complex vectors
+// y = M x for a real CSR matrix M on complex vectors
 template <class T, int BV>
-__global__ void __launch_bounds__(kF2Threads)
-    k2_spmv_real(int n, const int* __restrict__ rp, const int* __restrict__ ci,
-                 const T* __restrict__ mv, const typename Pair<T>::type* __restrict__ x,
-                 typename Pair<T>::type* __restrict__ y, int B) {
+__device__ __forceinline__ void spmv2_el(int i, int b0, const int* __restrict__ rp,
+                                         const int* __restrict__ ci, const T* __restrict__ mv,
+                                         const typename Pair<T>::type* __restrict__ x,
+                                         typename Pair<T>::type* __restrict__ y, int B) {
   using P2 = typename Pair<T>::type;
-  MG2_PROLOGUE(n)
   P2 o[BV];
 #pragma unroll
   for (int j = 0; j < BV; ++j) o[j].x = o[j].y = T(0);
@@ -217,27 +221,20 @@ __global__ void __launch_bounds__(kF2Threads)
       o[j].y += m * v[j].y;
     }
   }
-  st_pairs<T, BV>(y, base, o);
+  st_pairs<T, BV>(y, (size_t)i * B + b0, o);
 }
 
-// e = A_J^{-1} r with the dense inverse (row-major, complex): one warp per
-// (row i, tile of BV right-hand sides); lane l sums the products of columns
-// l, l + 32, ... in order, then the lanes' sums are added by a fixed
-// butterfly.  The order of every (row, rhs) sum does not depend on BV.
+// e = A_J^{-1} r with the dense inverse (row-major, complex) for row i,
+// right-hand sides b0..: called by the 32 lanes of a warp; lane l sums the
+// products of columns l, l + 32, ... in order, then the lanes' sums are added
+// by a fixed butterfly and lane 0 stores.  The order of every (row, rhs) sum
+// does not depend on BV.
 template <class T, int BV>
-__global__ void __launch_bounds__(kF2Threads)
-    k2_dense(int n, const typename Pair<T>::type* __restrict__ inv,
-             const typename Pair<T>::type* __restrict__ r, typename Pair<T>::type* __restrict__ e,
-             int B) {
+__device__ __forceinline__ void dense2_warp(int i, int b0, int lane, int n,
+                                            const typename Pair<T>::type* __restrict__ inv,
+                                            const typename Pair<T>::type* __restrict__ r,
+                                            typename Pair<T>::type* __restrict__ e, int B) {
   using P2 = typename Pair<T>::type;
-  pdl_wait();
-  pdl_launch();
-  const int nq = B / BV;
-  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int i = w / nq;
-  if (i >= n) return;
-  const int b0 = (w - i * nq) * BV;
   T sx[BV], sy[BV];
 #pragma unroll
   for (int j = 0; j < BV; ++j) sx[j] = sy[j] = T(0);
@@ -266,6 +263,136 @@ __global__ void __launch_bounds__(kF2Threads)
       o[j].y = sy[j];
     }
     st_pairs<T, BV>(e, (size_t)i * B + b0, o);
+  }
+}
+
+// ---- grid kernels ---------------------------------------------------------
+template <class T, int BV>
+__global__ void __launch_bounds__(kF2Threads)
+    k2_residual(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                const typename Pair<T>::type* __restrict__ av,
+                const typename Pair<T>::type* __restrict__ f,
+                const typename Pair<T>::type* __restrict__ u, typename Pair<T>::type* __restrict__ out,
+                int B, const typename Pair<T>::type* __restrict__ dinv, T theta, int scale,
+                int u_zero) {
+  MG2_PROLOGUE(n)
+  res2_el<T, BV>(i, b0, rp, ci, av, f, u, out, B, dinv, theta, scale, u_zero);
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kF2Threads)
+    k2_conv(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+            const T* __restrict__ invdeg, const typename Pair<T>::type* __restrict__ x,
+            typename Pair<T>::type* __restrict__ y, int B, Conv2<T> w, T eta, int mode) {
+  MG2_PROLOGUE(n)
+  conv2_el<T, BV>(i, b0, rp, ci, invdeg, x, y, B, w, eta, mode);
+}
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kF2Threads)
+    k2_spmv_real(int n, const int* __restrict__ rp, const int* __restrict__ ci,
+                 const T* __restrict__ mv, const typename Pair<T>::type* __restrict__ x,
+                 typename Pair<T>::type* __restrict__ y, int B) {
+  MG2_PROLOGUE(n)
+  spmv2_el<T, BV>(i, b0, rp, ci, mv, x, y, B);
+}
+
+// one warp per (row, tile of BV right-hand sides)
+template <class T, int BV>
+__global__ void __launch_bounds__(kF2Threads)
+    k2_dense(int n, const typename Pair<T>::type* __restrict__ inv,
+             const typename Pair<T>::type* __restrict__ r, typename Pair<T>::type* __restrict__ e,
+             int B) {
+  pdl_wait();
+  pdl_launch();
+  const int nq = B / BV;
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int i = w / nq;
+  if (i >= n) return;
+  dense2_warp<T, BV>(i, (w - i * nq) * BV, lane, n, inv, r, e, B);
+}
+
+// ---- single-block small levels ---------------------------------------------
+// Levels lt .. J-2 of a cycle (rows x rhs at most the tail threshold on
+// level lt) in one block of kT2Threads threads, steps separated by block
+// barriers, in two launches around the coarsest product: the descent
+// (smoothing, restriction, down to f_J) and, after the grid kernel of the
+// dense coarsest product (a warp per output over many SMs: on one SM its
+// FP64 products took longer than the launches it saved), the ascent.  The
+// same element steps as the grid kernels (one rhs per thread step).
+// Operator arrays stay in global memory (L2).  Slot k holds level lt + k.
+constexpr int kT2Max = 8;
+constexpr int kT2Threads = 1024;
+
+template <class T>
+struct Tail2 {
+  using P2 = typename Pair<T>::type;
+  int lt, J, B, nu_pre, nu_post, nJ;
+  int ascent;  // 0: the descent to f_J, 1: the ascent from u_J
+  int n[kT2Max];
+  const int *rp[kT2Max], *ci[kT2Max], *prp[kT2Max], *pci[kT2Max], *trp[kT2Max], *tci[kT2Max];
+  const P2 *av[kT2Max], *dinv[kT2Max];
+  const T *invdeg[kT2Max], *pv[kT2Max], *tv[kT2Max];
+  const P2* f[kT2Max];
+  P2 *u[kT2Max], *t[kT2Max], *t2[kT2Max];
+  T theta[kT2Max], eta[kT2Max];
+  Conv2<T> wb[kT2Max], wr[kT2Max], wp[kT2Max];
+  const P2* cinv;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kT2Threads) k2_tail(Tail2<T> a) {
+  using P2 = typename Pair<T>::type;
+  pdl_wait();
+  pdl_launch();
+  const int B = a.B;
+  // fn(i, b) for every (row, rhs) of a level, then a block barrier
+  auto each = [&](int n, auto&& fn) {
+    for (int e = threadIdx.x; e < n * B; e += blockDim.x) fn(e / B, e - (e / B) * B);
+    __syncthreads();
+  };
+  auto smooth = [&](int k, int nu) {
+    for (int q = 0; q < nu; ++q) {
+      each(a.n[k], [&](int i, int b) {
+        res2_el<T, 1>(i, b, a.rp[k], a.ci[k], a.av[k], a.f[k], a.u[k], a.t[k], B, a.dinv[k],
+                      a.theta[k], 1, 0);
+      });
+      each(a.n[k], [&](int i, int b) {
+        conv2_el<T, 1>(i, b, a.rp[k], a.ci[k], a.invdeg[k], a.t[k], a.u[k], B, a.wb[k],
+                       a.eta[k], 1);
+      });
+    }
+  };
+  const int kJ = a.J - 1 - a.lt;
+  if (a.ascent) {
+    for (int k = kJ - 1; k >= 0; --k) {
+      each(a.n[k], [&](int i, int b) {
+        spmv2_el<T, 1>(i, b, a.prp[k], a.pci[k], a.pv[k], a.u[k + 1], a.t[k], B);
+      });
+      each(a.n[k], [&](int i, int b) {
+        conv2_el<T, 1>(i, b, a.rp[k], a.ci[k], a.invdeg[k], a.t[k], a.u[k], B, a.wp[k], T(1),
+                       2);
+      });
+      smooth(k, a.nu_post);
+    }
+    return;
+  }
+  for (int k = 0; k < kJ; ++k) {
+    smooth(k, a.nu_pre);
+    each(a.n[k], [&](int i, int b) {
+      res2_el<T, 1>(i, b, a.rp[k], a.ci[k], a.av[k], a.f[k], a.u[k], a.t[k], B, a.dinv[k],
+                    a.theta[k], 0, 0);
+    });
+    each(a.n[k], [&](int i, int b) {
+      conv2_el<T, 1>(i, b, a.rp[k], a.ci[k], a.invdeg[k], a.t[k], a.t2[k], B, a.wr[k], T(1), 0);
+    });
+    each(a.n[k + 1], [&](int i, int b) {
+      spmv2_el<T, 1>(i, b, a.trp[k], a.tci[k], a.tv[k], a.t2[k], (P2*)a.f[k + 1], B);
+      P2 z;
+      z.x = z.y = T(0);
+      a.u[k + 1][(size_t)i * B + b] = z;
+    });
   }
 }
 
@@ -512,6 +639,10 @@ struct mg2_ctx {
   int nu_pre = 1, nu_post = 1;
   int opt_pdl = 1;   // programmatic dependent launch between the cycle's kernels
   int opt_tile = 1;  // right-hand-side tiles of the cycle's kernels (0: one per thread)
+  // levels with rows x rhs at most this (and all coarser) run in k2_tail
+  // (0: never, the default: measured no faster in FP32 and slower in FP64,
+  // where one SM's FP64 pipe carries the small levels' complex products)
+  int64_t opt_tail_work = 0;
   // mg2_vcycle_profile: (kind, level, start, end) per launch while set
   std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>>* prof = nullptr;
   std::vector<void*> owned;
@@ -753,6 +884,75 @@ struct Launch2 {
       go(kind, lev, k2_spmv_real<T, decltype(V)::value>, n, n, rp, ci, (const T*)mv, x, y, B);
     });
   }
+  // first level the single-block kernel runs for this batch (J - 1: none;
+  // it needs a level above the coarsest)
+  int tail_level() const {
+    const int J = c->J;
+    if (c->opt_tail_work <= 0 || J < 2) return J - 1;
+    int lt = J - 1;
+    while (lt > 0 && (int64_t)c->lev[lt - 1].n * B <= c->opt_tail_work) --lt;
+    if (lt == J - 1 || J - lt > kT2Max) return J - 1;
+    return lt;
+  }
+  // the descent (ascent = 0) or ascent (1) of the cycle from level l
+  // (>= tail_level()) on (f, u), in one block
+  void tail(int l, const P2* f, P2* u, int ascent) const {
+    Tail2<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.lt = l;
+    a.ascent = ascent;
+    a.J = c->J;
+    a.B = B;
+    a.nu_pre = c->nu_pre;
+    a.nu_post = c->nu_post;
+    a.nJ = c->lev[c->J - 1].n;
+    a.cinv = (const P2*)c->cinv;
+    for (int lv = l; lv < c->J; ++lv) {
+      const int k = lv - l;
+      const mg2_ctx::Lev& L = c->lev[lv];
+      a.n[k] = L.n;
+      a.rp[k] = L.rp;
+      a.ci[k] = L.ci;
+      a.av[k] = (const P2*)L.av;
+      a.dinv[k] = (const P2*)L.dinv;
+      a.invdeg[k] = (const T*)L.invdeg;
+      a.prp[k] = L.prp;
+      a.pci[k] = L.pci;
+      a.pv[k] = (const T*)L.pv;
+      a.trp[k] = L.trp;
+      a.tci[k] = L.tci;
+      a.tv[k] = (const T*)L.tv;
+      a.f[k] = k == 0 ? f : (const P2*)L.f;
+      a.u[k] = k == 0 ? u : (P2*)L.u;
+      a.t[k] = (P2*)L.t;
+      a.t2[k] = (P2*)L.t2;
+      if (lv < c->J - 1) {
+        a.theta[k] = (T)c->theta[lv];
+        a.eta[k] = (T)c->eta[lv];
+        a.wb[k] = conv_of<T>(c->WB, lv);
+        a.wr[k] = conv_of<T>(c->WR, lv);
+        a.wp[k] = conv_of<T>(c->WP, lv);
+      }
+    }
+    if (c->prof) {
+      cudaEvent_t e0, e1;
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+      cudaEventRecord(e0, s);
+      c->prof->emplace_back(MG_K_TAIL, l, e0, e1);
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(1);
+    cfg.blockDim = dim3(kT2Threads);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = c->opt_pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k2_tail<T>, a);
+    if (c->prof) cudaEventRecord(std::get<3>(c->prof->back()), s);
+  }
   void dense(int lev, int n, const P2* r, P2* e) const {
     // one warp per (row, tile): 32 threads per output
     with_bv([&](auto V) {
@@ -771,6 +971,13 @@ void cycle(mg2_ctx* c, int l, const typename Pair<T>::type* f, typename Pair<T>:
   mg2_ctx::Lev& L = c->lev[l];
   if (l == c->J - 1) {
     k.dense(l, L.n, f, u);
+    return;
+  }
+  if (l >= k.tail_level()) {  // this level and every coarser one in one block,
+    k.tail(l, f, u, 0);        // in two launches around the coarsest product
+    k.dense(c->J - 1, c->lev[c->J - 1].n, (const P2*)c->lev[c->J - 1].f,
+            (P2*)c->lev[c->J - 1].u);
+    k.tail(l, f, u, 1);
     return;
   }
   const T theta = (T)c->theta[l], eta = (T)c->eta[l];
@@ -942,6 +1149,10 @@ extern "C" mg_status mg2_set_option(mg2_ctx* c, int32_t option, int64_t value) {
     case MG_OPT_MULTI_RHS:
       if (value != 0 && value != 1) return fail("mg2_set_option: tile option must be 0 or 1");
       c->opt_tile = (int)value;
+      break;
+    case MG_OPT_TAIL_WORK:
+      if (value < 0) return fail("mg2_set_option: tail work must be >= 0");
+      c->opt_tail_work = value;
       break;
     default:
       return fail("mg2_set_option: unknown option");

@@ -138,8 +138,9 @@ class Solver2:
         self.params = p
 
     def set_option(self, name: str, value: int):
-        """Launch shapes of the cycle ("pdl", "multi_rhs"; mg2_set_option)."""
-        if name not in ("pdl", "multi_rhs"):
+        """Launch shapes of the cycle ("pdl", "multi_rhs", "tail_work";
+        mg2_set_option)."""
+        if name not in ("pdl", "multi_rhs", "tail_work"):
             raise ValueError(f"unknown two-feature option {name!r}")
         L.check(self.lib.mg2_set_option(self.ctx, L.OPTIONS[name], int(value)))
 

@@ -180,19 +180,23 @@ def test_fgmres2_zero_rhs_and_not_converged():
 @pytest.mark.parametrize("nrhs", [1, 2, 3, 4, 8, 16])
 def test_tiles_and_pdl_are_bitwise_neutral(prec, nrhs):
     """Right-hand-side tiles (4 complex values per thread in FP32, 2 in FP64,
-    the widest dividing nrhs) and programmatic dependent launch give bitwise
-    the cycle, full multigrid and FGMRES of the one-thread-per-(row, rhs)
-    plain launches."""
+    the widest dividing nrhs), programmatic dependent launch and the
+    single-block kernel for the small levels (option; threshold 2048, and
+    every level of the 65^2 hierarchy from level 0 on) give bitwise the cycle,
+    full multigrid and FGMRES of the one-thread-per-(row, rhs) plain grid
+    launches."""
     p, Ho, Hp = problem("helmholtz65")
     prm = params(Hp.J, 19)
     dt = torch.complex128 if prec == 64 else torch.complex64
     r = np.random.default_rng(nrhs)
     fc = r.standard_normal((Hp.sizes[0], nrhs)) + 1j * r.standard_normal((Hp.sizes[0], nrhs))
     outs = []
-    for tile, pdl in ((0, 0), (1, 0), (0, 1), (1, 1)):
+    for tile, pdl, tail in ((0, 0, 0), (1, 0, 0), (0, 1, 0), (1, 1, 0), (1, 1, 2048),
+                            (0, 1, 1 << 20)):
         S = Solver2(Hp, prm, precision=prec, max_batch=nrhs)
         S.set_option("multi_rhs", tile)
         S.set_option("pdl", pdl)
+        S.set_option("tail_work", tail)
         f = torch.tensor(fc, dtype=dt, device="cuda")
         u = torch.zeros_like(f)
         for _ in range(3):
@@ -214,5 +218,7 @@ def test_two_feature_option_errors():
     with pytest.raises(MGError):
         S.set_option("multi_rhs", 2)
     with pytest.raises(ValueError):
-        S.set_option("tail_work", 0)
+        S.set_option("halo_rows", 0)
+    with pytest.raises(MGError):
+        S.set_option("tail_work", -1)
     S.close()
