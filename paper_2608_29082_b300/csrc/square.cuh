@@ -189,14 +189,20 @@ __global__ void k_sq_coarse(const double* __restrict__ S, int block, int slots,
 // k_reduce_check read with B = slots).  A block's sums do not depend on the
 // other blocks.
 
+// The block's kThreads values summed in a fixed order: a butterfly within
+// each warp, then warp 0 adds the kThreads / 32 warp sums the same way.
+// Valid in thread 0.
 __device__ __forceinline__ double block_tree_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) sh[warp] = v;
   __syncthreads();
-  for (int s = kThreads / 2; s >= 1; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < kThreads / 32 ? sh[lane] : 0.0;
+    for (int o = 16; o >= 1; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   }
-  return sh[0];
+  return s;
 }
 
 __global__ void __launch_bounds__(kThreads) k_blk_sumsq(const double* __restrict__ x, int m,
@@ -239,6 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_blk_resid64(LV<double> L, const do
 }
 
 // u += 2^sexp_b c on the rows of the blocks still active; iteration counts.
+// Grid (chunks of kThreads rows, slots): block b of the stack is blockIdx.y.
 __global__ void __launch_bounds__(kThreads) k_blk_refine_update(double* __restrict__ u,
                                                                 const float* __restrict__ c,
                                                                 const int* __restrict__ sexp,
@@ -246,24 +253,28 @@ __global__ void __launch_bounds__(kThreads) k_blk_refine_update(double* __restri
                                                                 int m, int slots,
                                                                 int* __restrict__ iters) {
   pdl_wait();
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (size_t)slots && active[t]) iters[t] += 1;
-  if (t >= (size_t)m * slots) return;
-  const int b = (int)(t / (size_t)m);
-  if (active[b]) u[t] += scale2((double)c[t], sexp[b]);
+  const int b = blockIdx.y;
+  const int r = blockIdx.x * kThreads + threadIdx.x;
+  if (r == 0 && active[b]) iters[b] += 1;
+  if (r >= m || !active[b]) return;
+  const size_t t = (size_t)b * m + r;
+  u[t] += scale2((double)c[t], sexp[b]);
 }
 
-// u <- w on the rows of the blocks still active (stationary FP64 solve).
+// u <- w on the rows of the blocks still active (stationary FP64 solve);
+// grid as k_blk_refine_update.
 __global__ void __launch_bounds__(kThreads) k_blk_masked_copy(double* __restrict__ u,
                                                               const double* __restrict__ w,
                                                               const int* __restrict__ active,
                                                               int m, int slots,
                                                               int* __restrict__ iters) {
   pdl_wait();
-  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < (size_t)slots && active[t]) iters[t] += 1;
-  if (t >= (size_t)m * slots) return;
-  if (active[t / (size_t)m]) u[t] = w[t];
+  const int b = blockIdx.y;
+  const int r = blockIdx.x * kThreads + threadIdx.x;
+  if (r == 0 && active[b]) iters[b] += 1;
+  if (r >= m || !active[b]) return;
+  const size_t t = (size_t)b * m + r;
+  u[t] = w[t];
 }
 
 }  // namespace mgk

@@ -312,7 +312,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
     if (p32) {
       Issue<float> is{c, v32, c->prm32, cs, 1};
       is.vcycle(c->rhat32, c->c32, true);
-      is.launch(mgk::k_blk_refine_update, grid_for((size_t)n0), dim3(kThreads), 0, u,
+      is.launch(mgk::k_blk_refine_update, bgrid, dim3(kThreads), 0, u,
                 (const float*)c->c32, (const int*)sexp_prev, (const int*)active, m, S, iters);
       nk += is.nk;
       Issue<double> is2{c, v64, c->prm64, cs, 1};
@@ -323,7 +323,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
       is.launch(mgk::k_copy<double>, grid_for((size_t)n0), dim3(kThreads), 0, (const double*)u,
                 c->w64, (size_t)n0);
       is.vcycle(f, c->w64, false);
-      is.launch(mgk::k_blk_masked_copy, grid_for((size_t)n0), dim3(kThreads), 0, u,
+      is.launch(mgk::k_blk_masked_copy, bgrid, dim3(kThreads), 0, u,
                 (const double*)c->w64, (const int*)active, m, S, iters);
       check(is, h, 1, cond);
       nk += is.nk;
