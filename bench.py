@@ -391,10 +391,11 @@ def run_ours(args):
     lshape = lshape_solves = None
     if rank == 0 and not args.no_lshape:
         lshape, lshape_solves = lshape_section(dev, peak, args)
-    train_step = feat2 = None
+    train_step = feat2 = others = None
     if rank == 0 and not args.no_lshape:
         train_step = training_step_section(dev)
         feat2 = features2_section()
+        others = other_configs_section(dev, learned)
     serving = None
     if rank == 0 and not args.no_serving:
         serving = serving_section(dev)
@@ -461,6 +462,7 @@ def run_ours(args):
             "lshape_time_to_tol": lshape_solves,
             "training_step": train_step,
             "roofline_features2": feat2,
+            "other_configs": others,
             "serving": serving,
             "kernel_shares_per_vcycle": shares,
             "clocks": clocks,
@@ -579,6 +581,60 @@ def features2_section():
     r["dominant"] = {"kernel": f"{top['kernel']}@level{top['level']}", "achieved": top["GBps"],
                      "peak": r["hbm_peak_gbs"], "unit": "GB/s", "frac": top["frac_of_hbm"]}
     return r
+
+
+def other_configs_section(dev, learned):
+    """Config 0 (33^2 Poisson, 4 levels, the damped-Jacobi-equivalent
+    parameters, nu = 2/2, FP64, one rhs: cycles to 1e-10 and time per cycle)
+    and the 16-rhs variant of config 1 (the 513^2 checkerboard solved for 16
+    seeded N(0,1) right-hand sides at once, learned FP32 cycle + FP64
+    refinement to 1e-8)."""
+    import torch
+    import paper_2608_29082_b300 as lmg
+    import workloads as W
+    from workloads import fields
+    out = {}
+    p0 = W.poisson_square(33, 4, batch=1, seed=0)
+    h0 = lmg.Hierarchy.from_problem(p0)
+    S = lmg.Solver(h0, lmg.LMGParams.identity(h0.J), precision=64, max_batch=1)
+    f = torch.tensor(p0.f, dtype=torch.float64, device=dev)
+    u = torch.zeros_like(f)
+    S.solve(f, u, tol=1e-10, max_iter=200)
+    ms = []
+    for _ in range(5):
+        u.zero_()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        _, info = S.solve(f, u, tol=1e-10, max_iter=200)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    it = int(info.iters[0])
+    out["config0_poisson33"] = {"cycles_to_1e-10": it, "ms": round(float(np.median(ms)), 4),
+                                "us_per_cycle": round(float(np.median(ms)) * 1e3 / it, 2),
+                                "relres": float(info.relres[0])}
+    S.close()
+    prob = make_problem(seed=0)
+    hier = lmg.Hierarchy.from_problem(prob)
+    S = lmg.Solver(hier, learned, precision=32, max_batch=16)
+    f16 = torch.tensor(fields.rhs(hier.sizes[0], 16, 7), dtype=torch.float64, device=dev)
+    u16 = torch.zeros_like(f16)
+    S.solve(f16, u16, tol=TOL, max_iter=MAX_ITER)
+    ms = []
+    for _ in range(3):
+        u16.zero_()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        _, info = S.solve(f16, u16, tol=TOL, max_iter=MAX_ITER)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = float(np.median(ms))
+    out["config1_16rhs"] = {"ms_per_solve_of_16": round(t, 3), "ms_per_rhs": round(t / 16, 4),
+                            "iters_max": int(info.iters.max()),
+                            "max_relres": float(info.relres.max())}
+    S.close()
+    return out
 
 
 def training_step_section(dev):
