@@ -1068,6 +1068,7 @@ void free_gm(mg2_ctx* c) {
 
 extern "C" mg_status mg2_setup(mg2_ctx** out, int32_t J, const mg2_level* levels,
                                int32_t max_batch, int32_t precision) {
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   if (!out) return fail("mg2_setup: out is NULL");
   *out = nullptr;
   // max_batch: FGMRES's per-(vector, rhs) sums run on a grid with nrhs rows
@@ -1194,6 +1195,7 @@ extern "C" mg_status mg2_vcycle(mg2_ctx* c, const void* f, void* u, int32_t nrhs
   const auto key = std::make_tuple(f, (const void*)u, (int)nrhs);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
+    std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return fail(std::string("mg2_vcycle: ") + cudaGetErrorString(e), MG_ERR_CUDA);
@@ -1270,6 +1272,7 @@ extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_
   const size_t N0 = (size_t)n0 * c->maxB;
   const size_t mb = (size_t)c->maxB;
   if (c->gm_m != m) {
+    std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
     cudaDeviceSynchronize();
     free_gm(c);
     const bool ok =
@@ -1380,6 +1383,7 @@ extern "C" mg_status mg2_solve_fgmres(mg2_ctx* c, const void* f, void* u, int32_
 
 extern "C" void mg2_destroy(mg2_ctx* c) {
   if (!c) return;
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   cudaDeviceSynchronize();
   free_gm(c);
   c->drop_graphs();

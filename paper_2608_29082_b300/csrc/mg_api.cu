@@ -42,6 +42,11 @@ std::string g_err;
 }  // namespace
 
 namespace mgi {
+std::recursive_mutex& setup_mutex() {
+  static std::recursive_mutex m;
+  return m;
+}
+
 mg_status set_global_error(mg_status s, const std::string& msg) {
   std::lock_guard<std::mutex> lk(g_err_mu);
   g_err = msg;
@@ -1336,6 +1341,7 @@ mg_status run_graph(mg_ctx* c, const std::tuple<int, const void*, const void*, i
                     cudaStream_t s, Fn&& fn) {
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
+    std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
     cudaGraph_t g = nullptr;
     MG_CUDA(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
     int nk = fn(c->cap);
@@ -1398,6 +1404,7 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
   auto key = std::make_tuple(id, f, u, B, c->structure);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
+    std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
     cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle h;
     int nk_init = 0, nk_body = 0;
@@ -1418,6 +1425,9 @@ mg_status run_loop(mg_ctx* c, int id, const void* f, const void* u, int B, cudaS
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaError_t e = cudaStreamGetCaptureInfo(c->cap, &cst, nullptr, &capg, &deps, &edges, &ndeps);
+    // a capture invalidated on the way (status not active) has no graph to add to
+    if (e == cudaSuccess && (cst != cudaStreamCaptureStatusActive || !capg))
+      e = cudaErrorStreamCaptureInvalidated;
     if (e == cudaSuccess) e = cudaGraphAddNode(&wnode, capg, deps, edges, ndeps, &np);
     if (e == cudaSuccess)
       e = cudaStreamUpdateCaptureDependencies(c->cap, &wnode, nullptr, 1,
@@ -1495,6 +1505,7 @@ extern "C" int64_t mg_kernel_launches(const mg_ctx* ctx) { return ctx ? ctx->lau
 
 extern "C" void mg_destroy(mg_ctx* c) {
   if (!c) return;
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   if (c->cap) cudaStreamSynchronize(c->cap);
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);
   for (auto& L : c->d64) free_level(L);
@@ -1603,6 +1614,7 @@ extern "C" mg_status mg_footprint_bytes(const mg_hierarchy* h, const mg_csr* A, 
 
 extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr* A,
                               const mg_params* p, int32_t maxB, int32_t precision, void* stream) {
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   if (!out) return mgi::set_global_error(MG_ERR_INVALID, "mg_setup: out is NULL");
   *out = nullptr;
   std::string why;
@@ -1734,7 +1746,10 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
     if ((e = cudaMalloc(&c->c32, (size_t)n0 * maxB * sizeof(float))) != cudaSuccess) return bail(e);
     if ((e = cudaMalloc(&c->rhat32, (size_t)n0 * maxB * sizeof(float))) != cudaSuccess) return bail(e);
   }
-  if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(e);
+  // the synchronous copies are complete; wait for the memsets on the legacy
+  // stream only (a device-wide synchronisation would also wait on, and could
+  // disturb, other threads' streams)
+  if ((e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) return bail(e);
   *out = c;
   (void)stream;
   return MG_OK;
@@ -2143,6 +2158,7 @@ extern "C" mg_status mg_vcycle_profile(mg_ctx* c, const void* f, void* u, int32_
 
 extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
   if (!c) return mgi::set_global_error(MG_ERR_INVALID, "mg_set_option: ctx is NULL");
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   switch (option) {
     case MG_OPT_TAIL_WORK:
       if (value < 0) return c->fail(MG_ERR_INVALID, "mg_set_option: tail work must be >= 0");

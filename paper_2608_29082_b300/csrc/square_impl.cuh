@@ -112,6 +112,7 @@ mgk::SqDia square_dia(const int* doff, int ndia, int w) {
 
 extern "C" mg_status mg_setup_square(mg_ctx** out, int32_t N, int32_t J, int32_t slots,
                                      const mg_params* p, int32_t precision, void* stream) {
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   if (!out) return mgi::set_global_error(MG_ERR_INVALID, "mg_setup_square: out is NULL");
   *out = nullptr;
   if (J < 2 || J > 16 || slots < 1 || slots > 2048 || N < 5)
@@ -163,7 +164,7 @@ extern "C" mg_status mg_setup_square(mg_ctx** out, int32_t N, int32_t J, int32_t
       (c->cholInv == nullptr &&
        (e = cudaMalloc(&c->cholInv, (size_t)slots * slots * sizeof(double))) != cudaSuccess) ||
       (e = cudaMemset(c->cholInv, 0, (size_t)slots * slots * sizeof(double))) != cudaSuccess ||
-      (e = cudaDeviceSynchronize()) != cudaSuccess) {
+      (e = cudaStreamSynchronize(cudaStreamLegacy)) != cudaSuccess) {
     mg_destroy(c);
     return mgi::set_global_error(e == cudaErrorMemoryAllocation ? MG_ERR_OOM : MG_ERR_CUDA,
                                  std::string("mg_setup_square: ") + cudaGetErrorString(e));

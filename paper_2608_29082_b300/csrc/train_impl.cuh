@@ -58,6 +58,7 @@ void train_free(mg_ctx* c) {
 mg_status ensure_train(mg_ctx* c, int K, int B) {
   if (c->trK == K && c->trB == B && c->tr_nu_pre == c->nu_pre && c->tr_nu_post == c->nu_post)
     return MG_OK;
+  std::lock_guard<std::recursive_mutex> lk(mgi::setup_mutex());
   cudaDeviceSynchronize();
   // captured forward graphs point at the old checkpoint buffers
   for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second.exec);

@@ -268,3 +268,44 @@ def test_invalid_square_arguments():
         with pytest.raises(MGError):
             S.solve(f, u, nblocks=k)
     S.close()
+
+
+def test_contexts_created_and_solved_from_several_threads():
+    """Set-up, graph capture and destruction on one thread while another
+    thread captures and launches its own solves (the serving pattern): every
+    thread's results equal the same work done on one thread, bitwise."""
+    import threading
+    N = 33
+    sys_list = systems(N, ["lognormal", "checker"], seed=41)
+    prm = LMGParams.identity(levels_for(N))
+    prm.wB[:, 1] = 0.1
+
+    def work(seed, out):
+        torch.cuda.set_device(0)
+        side = torch.cuda.Stream()
+        with torch.cuda.stream(side):
+            res = []
+            for rep in range(3):
+                S = SquareBatch(N, 2, prm, precision=32)
+                fill(S, sys_list)
+                f = t64(np.concatenate([x[1] for x in sys_list]) * (1 + seed))
+                u = torch.zeros_like(f)
+                for k in (1, 2):
+                    S.solve(f, u, tol=1e-8, max_iter=100, nblocks=k)
+                res.append(u.cpu().numpy().copy())
+                S.close()
+            side.synchronize()
+        out[seed] = res
+
+    alone = {}
+    for seed in range(3):
+        work(seed, alone)
+    together = {}
+    threads = [threading.Thread(target=work, args=(seed, together)) for seed in range(3)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    for seed in range(3):
+        for a, b in zip(alone[seed], together[seed]):
+            assert np.array_equal(a, b), seed
