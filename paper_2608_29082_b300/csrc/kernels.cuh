@@ -603,7 +603,7 @@ struct TailArgs {
   T* u[kMaxLevels];
   T* t[kMaxLevels];
   T* u2[kMaxLevels];
-  const T* prm;
+  const T* prm;  // [J-1][P_COUNT]
   const double* cL;
   const double* cU;
   const double* cDinv;
@@ -682,45 +682,69 @@ __host__ __device__ inline size_t tail_level_bytes(const LV<T>& L, int nsl, int 
   return s;
 }
 
-// Dynamic shared memory of k_tail: Cholesky scratch, then every level
-// lt..J-1 as laid out by tail_level_bytes.
+// Dynamic shared memory of k_tail: Cholesky scratch, the parameters of
+// levels 0..J-2, then every level lt..J-1 as laid out by tail_level_bytes.
+template <class T>
+__host__ __device__ inline size_t tail_head_bytes(const TailArgs<T>& a) {
+  return tail_align((size_t)a.cwarps * a.nJ * sizeof(double)) +
+         tail_align((size_t)(a.J - 1) * P_COUNT * sizeof(T));
+}
 template <class T>
 __host__ __device__ inline size_t tail_smem_bytes(const TailArgs<T>& a, int lt) {
-  size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+  size_t off = tail_head_bytes(a);
   for (int l = lt; l < a.J; ++l)
     off += tail_level_bytes<T>(a.L[l], a.nsl[l], a.nent[l], a.B, l == a.J - 1,
                                a.smem_vectors != 0, a.smem_matrix != 0);
   return off;
 }
 
+// The copies carry no compiler memory clobber: their destinations are read
+// only after cp_async_wait_all (which has one) and a barrier, and without
+// it the loads of the next copy's source pointer need not wait for the
+// issue of the previous copy.
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem_src));
 }
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
+// One element of 4 or 8 bytes (both addresses aligned to its size).
+template <class U>
+__device__ __forceinline__ void cp_async_el(U* smem_dst, const U* gmem_src) {
+  static_assert(sizeof(U) == 4 || sizeof(U) == 8, "cp.async element of 4 or 8 bytes");
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  if constexpr (sizeof(U) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem_src));
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gmem_src));
+}
 
 // Starts copying count elements into shared memory at base + off (all
-// threads of the block take part; 16-byte cp.async transfers stay in flight
-// until cp_async_wait_all) and advances off; returns the shared-memory copy.
-// Bytes past the last whole 16-byte chunk are copied with plain loads, so
-// nothing beyond src + count is read.
+// threads of the block take part) and advances off; returns the
+// shared-memory copy.  Every transfer is a cp.async that stays in flight
+// until cp_async_wait_all: 16-byte chunks from a 16-byte aligned source, and
+// element-sized ones for the elements past the last whole chunk or from an
+// unaligned source, so nothing beyond src + count is read and no copy
+// waits for another (a plain load per array would put one memory round trip
+// per array on the block's path).
+// The copies are spread over nlanes threads, this one being lane (the whole
+// block by default).
 template <class U>
 __device__ __forceinline__ U* smem_take(unsigned char* base, size_t& off, const U* src,
-                                        size_t count) {
+                                        size_t count, unsigned lane = threadIdx.x,
+                                        unsigned nlanes = blockDim.x) {
   U* dst = (U*)(base + off);
   off += tail_align(count * sizeof(U));
-  const size_t bytes = count * sizeof(U);
-  const char* s = (const char*)src;
-  char* d = (char*)dst;
-  if ((((uintptr_t)s) & 15) == 0) {
-    const size_t nchunk = bytes / 16;
-    for (size_t k = threadIdx.x; k < nchunk; k += blockDim.x) cp_async16(d + 16 * k, s + 16 * k);
-    for (size_t k = nchunk * 16 + threadIdx.x; k < bytes; k += blockDim.x) d[k] = s[k];
-  } else {
-    for (size_t k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
+  size_t first = 0;  // first element copied one by one
+  if ((((uintptr_t)src) & 15) == 0) {
+    const size_t nchunk = count * sizeof(U) / 16;
+    const char* s = (const char*)src;
+    char* d = (char*)dst;
+    for (size_t k = lane; k < nchunk; k += nlanes) cp_async16(d + 16 * k, s + 16 * k);
+    first = nchunk * 16 / sizeof(U);
   }
+  for (size_t k = first + lane; k < count; k += nlanes) cp_async_el(dst + k, src + k);
   return dst;
 }
 
@@ -730,16 +754,18 @@ __device__ __forceinline__ U* smem_take(unsigned char* base, size_t& off, const 
 // shared-memory row stride (the layout rows_bytes counts).
 template <class U>
 __device__ __forceinline__ U* smem_take_rows(unsigned char* base, size_t& off, const U* src,
-                                             int count, int ld, int nchunk, int& ld_out) {
+                                             int count, int ld, int nchunk, int& ld_out,
+                                             unsigned lane = threadIdx.x,
+                                             unsigned nlanes = blockDim.x) {
   if (ld == count) {
     ld_out = count;
-    return smem_take(base, off, src, (size_t)nchunk * count);
+    return smem_take(base, off, src, (size_t)nchunk * count, lane, nlanes);
   }
   const int lds = (count + 3) & ~3;
   U* dst = (U*)(base + off);
   for (int k = 0; k < nchunk; ++k) {
     size_t o = off + (size_t)k * lds * sizeof(U);
-    smem_take(base, o, src + (size_t)k * ld, (size_t)count);
+    smem_take(base, o, src + (size_t)k * ld, (size_t)count, lane, nlanes);
   }
   off += (size_t)nchunk * lds * sizeof(U);
   ld_out = lds;
@@ -828,20 +854,20 @@ __global__ void k_coarse_chol_packed(const double* __restrict__ Lp, const double
 
 template <class T>
 __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* Ls,
-                                            const TailVecs<T>& v, int l, int nu, bool zero,
-                                            const Team& tm) {
+                                            const T* prm_all, const TailVecs<T>& v, int l, int nu,
+                                            bool zero, const Team& tm, int B) {
   const LV<T>& L = Ls[l];
-  const size_t N = (size_t)L.n * a.B;
-  const T* prm = a.prm + (size_t)l * P_COUNT;
+  const size_t N = (size_t)L.n * B;
+  const T* prm = prm_all + (size_t)l * P_COUNT;
   const size_t t0 = threadIdx.x, dt = tm.size();
   if ((a.convB >> l) & 1u) {
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       for (size_t t = t0; t < N; t += dt)
-        residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 1, z, t);
+        residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], B, prm, 1, z, t);
       tm.sync();
       for (size_t t = t0; t < N; t += dt)
-        conv_update_el(L, (const T*)v.t[l], v.u[l], a.B, prm, z, t);
+        conv_update_el(L, (const T*)v.t[l], v.u[l], B, prm, z, t);
       tm.sync();
     }
   } else {
@@ -850,7 +876,7 @@ __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* L
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
       for (size_t t = t0; t < N; t += dt)
-        jacobi_el(L, (const T*)v.f[l], (const T*)cur, oth, a.B, prm, z, t);
+        jacobi_el(L, (const T*)v.f[l], (const T*)cur, oth, B, prm, z, t);
       tm.sync();
       T* tmp = cur;
       cur = oth;
@@ -867,131 +893,194 @@ __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* L
   }
 }
 
-template <class T>
+// kB = 1: one right-hand side, known at compile time (the index arithmetic
+// of every step folds); kB = 0: B right-hand sides.
+template <class T, int kB>
 __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs<T> a) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
+  // The arguments, the staged level views and the vector pointers live in
+  // shared memory, one copy per block.  Levels are indexed at run time: as
+  // per-thread tables they would sit in local memory (1024 copies, which L1
+  // does not hold, so every step would reload them from L2), and reading
+  // each array's pointer from the argument space after the previous
+  // cp.async would put one argument fetch per array on the block's path.
+  __shared__ TailArgs<T> sa;
   __shared__ LV<T> sL[kMaxLevels];
+  __shared__ TailVecs<T> v;
+  {
+    const unsigned* src = reinterpret_cast<const unsigned*>(&a);
+    unsigned* dst = reinterpret_cast<unsigned*>(&sa);
+    for (int k = threadIdx.x; k < (int)(sizeof(TailArgs<T>) / 4); k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
   double* ys = (double*)tail_smem;
   const int J = a.J, lt = a.lt;
-  TailVecs<T> v;
+  const int B = kB ? kB : a.B;
+  {
+    const unsigned* src = reinterpret_cast<const unsigned*>(&sa.L[lt]);
+    unsigned* dst = reinterpret_cast<unsigned*>(&sL[lt]);
+    const int words = (int)((J - lt) * sizeof(LV<T>) / 4);
+    for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = src[k];
+  }
+  __syncthreads();
   // Lay out every small level in shared memory (the same order as
   // tail_level_bytes): vectors first, then the read-only arrays, copied
-  // once per cycle with all threads.  The read-only arrays never depend on
-  // the preceding kernel, so their copies are issued before
-  // griddepcontrol.wait and overlap its drain; the level-lt vectors it
-  // writes are copied after the wait.
-  size_t off = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
-  const size_t off_lt_vec = off;
-  for (int l = lt; l < J; ++l) {
-    const LV<T>& G = a.L[l];
-    const size_t nB = (size_t)G.n * a.B;
-    if (a.smem_vectors) {
-      const size_t bytes = tail_align(nB * sizeof(T));
-      v.u[l] = (T*)(tail_smem + off);
-      v.f[l] = (T*)(tail_smem + off + bytes);
-      v.t[l] = (T*)(tail_smem + off + 2 * bytes);
-      v.u2[l] = (T*)(tail_smem + off + 3 * bytes);
-      off += 4 * bytes;
-    } else {
-      v.u[l] = a.u[l];
-      v.f[l] = (T*)a.f[l];
-      v.t[l] = a.t[l];
-      v.u2[l] = a.u2[l];
-    }
-    LV<T> S = G;
-    if (a.smem_matrix) {
-      if (G.ndia > 0) {
-        S.dval = smem_take_rows(tail_smem, off, G.dval, G.n, G.ld, G.ndia, S.ld);
-      } else {
-        S.sl_ptr = smem_take(tail_smem, off, G.sl_ptr, (size_t)a.nsl[l] + 1);
-        S.col = smem_take(tail_smem, off, G.col, (size_t)a.nent[l]);
-        S.val = smem_take(tail_smem, off, G.val, (size_t)a.nent[l]);
+  // once per cycle.  Warp l - lt stages level l (its offset is the head
+  // plus the sizes of levels lt..l-1), so the levels' copy loops
+  // run side by side instead of each warp stepping through all of them
+  // (warps take further levels in turn if there are more levels than warps).
+  // The read-only arrays never depend on the preceding kernel, so their
+  // copies are issued before griddepcontrol.wait and overlap its drain; the
+  // level-lt vectors it writes are copied after the wait.  Lane 0 of the
+  // warp records the level's pointers; the barrier after the copies
+  // publishes them.
+  const size_t off_lt_vec = tail_head_bytes(a);
+  for (int l = lt + (int)(threadIdx.x >> 5); l < J; l += (int)(blockDim.x >> 5)) {
+    const unsigned lane = threadIdx.x & 31;
+    const bool w0 = lane == 0;
+    {
+      size_t off = off_lt_vec;
+      for (int k = lt; k < l; ++k)
+        off += tail_level_bytes<T>(sa.L[k], sa.nsl[k], sa.nent[k], B, k == J - 1,
+                                   a.smem_vectors != 0, a.smem_matrix != 0);
+      const LV<T>& G = sa.L[l];
+      LV<T>& S = sL[l];
+      const size_t nB = (size_t)G.n * B;
+      if (a.smem_vectors) {
+        const size_t bytes = tail_align(nB * sizeof(T));
+        if (w0) {
+          v.u[l] = (T*)(tail_smem + off);
+          v.f[l] = (T*)(tail_smem + off + bytes);
+          v.t[l] = (T*)(tail_smem + off + 2 * bytes);
+          v.u2[l] = (T*)(tail_smem + off + 3 * bytes);
+        }
+        off += 4 * bytes;
+      } else if (w0) {
+        v.u[l] = sa.u[l];
+        v.f[l] = (T*)sa.f[l];
+        v.t[l] = sa.t[l];
+        v.u2[l] = sa.u2[l];
       }
-      S.diag = smem_take(tail_smem, off, G.diag, (size_t)G.n);
-      S.dinv = smem_take(tail_smem, off, G.dinv, (size_t)G.n);
-      S.invdeg = smem_take(tail_smem, off, G.invdeg, (size_t)G.n);
-      if (l < J - 1) {
-        S.p_idx = smem_take_rows(tail_smem, off, G.p_idx, G.n, G.ld, 2, S.ld);
-        S.p_w = smem_take_rows(tail_smem, off, G.p_w, G.n, G.ld, 2, S.ld);
-        S.r_idx = smem_take_rows(tail_smem, off, G.r_idx, G.nc, G.ldc, G.KR, S.ldc);
-        S.r_w = smem_take_rows(tail_smem, off, G.r_w, G.nc, G.ldc, G.KR, S.ldc);
+      if (a.smem_matrix) {
+        int ld = G.ld, ldc = G.ldc;
+        if (G.ndia > 0) {
+          const T* dv = smem_take_rows(tail_smem, off, G.dval, G.n, G.ld, G.ndia, ld, lane, 32);
+          if (w0) S.dval = dv;
+        } else {
+          const int* sp = smem_take(tail_smem, off, G.sl_ptr, (size_t)sa.nsl[l] + 1, lane, 32);
+          const int* cl = smem_take(tail_smem, off, G.col, (size_t)sa.nent[l], lane, 32);
+          const T* vl = smem_take(tail_smem, off, G.val, (size_t)sa.nent[l], lane, 32);
+          if (w0) {
+            S.sl_ptr = sp;
+            S.col = cl;
+            S.val = vl;
+          }
+        }
+        const T* dg = smem_take(tail_smem, off, G.diag, (size_t)G.n, lane, 32);
+        const T* di = smem_take(tail_smem, off, G.dinv, (size_t)G.n, lane, 32);
+        const T* ig = smem_take(tail_smem, off, G.invdeg, (size_t)G.n, lane, 32);
+        if (w0) {
+          S.diag = dg;
+          S.dinv = di;
+          S.invdeg = ig;
+        }
+        if (l < J - 1) {
+          const int* pi = smem_take_rows(tail_smem, off, G.p_idx, G.n, G.ld, 2, ld, lane, 32);
+          const T* pw = smem_take_rows(tail_smem, off, G.p_w, G.n, G.ld, 2, ld, lane, 32);
+          const int* ri = smem_take_rows(tail_smem, off, G.r_idx, G.nc, G.ldc, G.KR, ldc, lane, 32);
+          const T* rw = smem_take_rows(tail_smem, off, G.r_w, G.nc, G.ldc, G.KR, ldc, lane, 32);
+          if (w0) {
+            S.p_idx = pi;
+            S.p_w = pw;
+            S.r_idx = ri;
+            S.r_w = rw;
+          }
+        }
+        if (w0) {
+          S.ld = ld;
+          S.ldc = ldc;
+        }
       }
     }
-    if (threadIdx.x == 0) sL[l] = S;
   }
   pdl_wait();
   pdl_launch();
+  // the parameters of levels 0..J-2 (a training step may write them),
+  // after the wait
+  size_t off_prm = tail_align((size_t)a.cwarps * a.nJ * sizeof(double));
+  const T* prm_all = smem_take(tail_smem, off_prm, a.prm, (size_t)(J - 1) * P_COUNT);
   if (a.smem_vectors) {
-    const size_t nB = (size_t)a.L[lt].n * a.B;
+    const size_t nB = (size_t)sa.L[lt].n * B;
     size_t o2 = off_lt_vec + tail_align(nB * sizeof(T));
-    smem_take(tail_smem, o2, a.f[lt], nB);
+    smem_take(tail_smem, o2, sa.f[lt], nB);
     if (!a.lt_zero) {
       o2 = off_lt_vec;
-      smem_take(tail_smem, o2, (const T*)a.u[lt], nB);
+      smem_take(tail_smem, o2, (const T*)sa.u[lt], nB);
     }
   }
   cp_async_wait_all();
   __syncthreads();
   // descent: level l by its team (teams shrink towards the coarsest level)
   for (int l = lt; l < J - 1; ++l) {
-    const Team tm{a.tw[l]};
+    const Team tm{sa.tw[l]};
     if (!tm.member()) break;
     const LV<T>& L = sL[l];
-    const T* prm = a.prm + (size_t)l * P_COUNT;
+    const T* prm = prm_all + (size_t)l * P_COUNT;
     const size_t t0 = threadIdx.x, dt = tm.size();
-    tail_smooth(a, sL, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true, tm);
-    const size_t N = (size_t)L.n * a.B;
+    tail_smooth(a, sL, prm_all, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true, tm, B);
+    const size_t N = (size_t)L.n * B;
     for (size_t t = t0; t < N; t += dt)
-      residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], a.B, prm, 0, 0, t);
+      residual_el(L, (const T*)v.f[l], (const T*)v.u[l], v.t[l], B, prm, 0, 0, t);
     tm.sync();
-    const size_t Nc = (size_t)L.nc * a.B;
+    const size_t Nc = (size_t)L.nc * B;
     if ((a.convR >> l) & 1u) {  // Phi_R per fine row, then the gather P^T
-      for (size_t t = t0; t < N; t += dt) conv_r_el(L, (const T*)v.t[l], v.u2[l], a.B, prm, t);
+      for (size_t t = t0; t < N; t += dt) conv_r_el(L, (const T*)v.t[l], v.u2[l], B, prm, t);
       tm.sync();
-      for (size_t t = t0; t < Nc; t += dt) gather_el(L, (const T*)v.u2[l], v.f[l + 1], a.B, t);
+      for (size_t t = t0; t < Nc; t += dt) gather_el(L, (const T*)v.u2[l], v.f[l + 1], B, t);
     } else {
       for (size_t t = t0; t < Nc; t += dt)
-        restrict_el(L, (const T*)v.t[l], v.f[l + 1], a.B, prm, 0, t);
+        restrict_el(L, (const T*)v.t[l], v.f[l + 1], B, prm, 0, t);
     }
     tm.sync();
   }
   {
-    const Team tm{a.tw[J - 1]};
+    const Team tm{sa.tw[J - 1]};
     if (tm.member()) {
       if (a.cInv) {
-        for (size_t t = threadIdx.x; t < (size_t)a.nJ * a.B; t += tm.size())
-          coarse_inv_el(a.cInv, a.nJ, a.cInvLd, (const T*)v.f[J - 1], v.u[J - 1], a.B, t);
+        for (size_t t = threadIdx.x; t < (size_t)a.nJ * B; t += tm.size())
+          coarse_inv_el(a.cInv, a.nJ, a.cInvLd, (const T*)v.f[J - 1], v.u[J - 1], B, t);
       } else {
-        coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], a.B,
+        coarse_chol_block(a.cL, a.cU, a.cDinv, a.nJ, (const T*)v.f[J - 1], v.u[J - 1], B,
                           min(a.cwarps, tm.W), ys);
       }
     }
   }
   // ascent: each team first waits for the coarser levels' (sub-)team
   for (int l = J - 2; l >= lt; --l) {
-    const Team tm{a.tw[l]};
+    const Team tm{sa.tw[l]};
     if (!tm.member()) continue;
     tm.sync();
     const LV<T>& L = sL[l];
-    const T* prm = a.prm + (size_t)l * P_COUNT;
+    const T* prm = prm_all + (size_t)l * P_COUNT;
     const size_t t0 = threadIdx.x, dt = tm.size();
-    const size_t N = (size_t)L.n * a.B;
+    const size_t N = (size_t)L.n * B;
     if ((a.convP >> l) & 1u) {  // P e_c per fine row, then Phi_P and the update
-      for (size_t t = t0; t < N; t += dt) pe_el(L, (const T*)v.u[l + 1], v.t[l], a.B, t);
+      for (size_t t = t0; t < N; t += dt) pe_el(L, (const T*)v.u[l + 1], v.t[l], B, t);
       tm.sync();
       for (size_t t = t0; t < N; t += dt)
-        prolong_conv_el(L, (const T*)v.t[l], (const T*)v.u[l], v.u[l], a.B, prm, t);
+        prolong_conv_el(L, (const T*)v.t[l], (const T*)v.u[l], v.u[l], B, prm, t);
     } else {
       for (size_t t = t0; t < N; t += dt)
-        prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], a.B, prm, 0, t);
+        prolong_el(L, (const T*)v.u[l + 1], (const T*)v.u[l], v.u[l], B, prm, 0, t);
     }
     tm.sync();
-    tail_smooth(a, sL, v, l, a.nu_post, false, tm);
+    tail_smooth(a, sL, prm_all, v, l, a.nu_post, false, tm, B);
   }
   __syncthreads();
   if (a.smem_vectors) {
-    const size_t N = (size_t)a.L[lt].n * a.B;
-    for (size_t t = threadIdx.x; t < N; t += blockDim.x) a.u[lt][t] = v.u[lt][t];
+    const size_t N = (size_t)sa.L[lt].n * B;
+    T* ug = sa.u[lt];
+    for (size_t t = threadIdx.x; t < N; t += blockDim.x) ug[t] = v.u[lt][t];
   }
   pdl_launch();
 }

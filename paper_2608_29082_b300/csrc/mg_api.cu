@@ -1202,7 +1202,8 @@ struct Issue {
     a.lt = lt;
     if (lt > l0) a.lt_zero = 1;  // levels below the cycle's first start from zero
     pre(MG_K_TAIL, lt);
-    launch(mgk::k_tail<T>, dim3(1), dim3(mgk::kTailThreads), mgk::tail_smem_bytes<T>(a, lt), a);
+    launch(a.B == 1 ? mgk::k_tail<T, 1> : mgk::k_tail<T, 0>, dim3(1), dim3(mgk::kTailThreads),
+           mgk::tail_smem_bytes<T>(a, lt), a);
     post();
   }
 
@@ -1671,12 +1672,11 @@ extern "C" mg_status mg_setup(mg_ctx** out, const mg_hierarchy* h, const mg_csr*
   };
   cudaError_t e;
   if ((e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking)) != cudaSuccess) return bail(e);
-  if ((e = cudaFuncSetAttribute(mgk::k_tail<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kTailSmemMax)) != cudaSuccess)
-    return bail(e);
-  if ((e = cudaFuncSetAttribute(mgk::k_tail<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kTailSmemMax)) != cudaSuccess)
-    return bail(e);
+  for (const void* k : {(const void*)mgk::k_tail<float, 0>, (const void*)mgk::k_tail<float, 1>,
+                        (const void*)mgk::k_tail<double, 0>, (const void*)mgk::k_tail<double, 1>})
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kTailSmemMax)) != cudaSuccess)
+      return bail(e);
   if ((e = cudaFuncSetAttribute(mgk::k_coarse_chol_packed<float>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax)) !=
       cudaSuccess)
