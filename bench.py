@@ -156,28 +156,31 @@ def kernel_bytes(name: str, lev: int, hier, B: int, b: int) -> float:
     col_b = 0 if offs.size <= 8 else 4
     nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
     nnzP = hier.P[lev].data.size if lev < hier.J - 1 else 0
+    # the mean aggregation's neighbour test: SELL column indices, or on
+    # DIA levels one mask byte per row
+    mean_b = nnz_off * col_b if col_b else n
     if name == "jacobi_smooth":
         return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
     if name == "residual_scaled":
         return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
     if name == "sage_conv_update":
-        return nnz_off * (col_b or b) + n * b + 3 * B * n * b
+        return mean_b + n * b + 3 * B * n * b
     if name == "residual":
         return nnz_off * (col_b + b) + n * b + 3 * B * n * b
     if name == "restrict_conv_fine":   # Phi_R(r) per fine row
-        return nnz_off * (col_b or b) + n * b + 2 * B * n * b
+        return mean_b + n * b + 2 * B * n * b
     if name == "restrict_conv":        # gather P^T
         return nnzP * (4 + b) + B * n * b + B * nc * b
     if name == "prolong_fine":         # P e_c per fine row
         return nnzP * (4 + b) + B * nc * b + B * n * b
     if name == "prolong_conv":         # u += Phi_P(P e_c)
-        return nnz_off * (col_b or b) + n * b + 3 * B * n * b
+        return mean_b + n * b + 3 * B * n * b
     if name == "smooth_halo":          # delta and u += eta Phi_B(delta), u_in -> u_out
         return nnz_off * (col_b + b) + 3 * n * b + 3 * B * n * b
     if name == "restrict_conv_halo":   # r and Phi_R(r) per fine row
         return nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b
     if name == "prolong_halo":         # P e_c, Phi_P and u += per fine row
-        return nnzP * (4 + b) + nnz_off * (col_b or b) + n * b + B * nc * b + 2 * B * n * b
+        return nnzP * (4 + b) + mean_b + n * b + B * nc * b + 2 * B * n * b
     if name == "coarse_cholesky":
         return 2 * n * n * 8 + 2 * B * n * b
     if name == "outer_residual_fp64":

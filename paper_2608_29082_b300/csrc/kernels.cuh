@@ -86,6 +86,11 @@ struct LV {
   const T* __restrict__ p_w;
   const int* __restrict__ r_idx;
   const T* __restrict__ r_w;
+  // DIA levels: bit k of nbm[i] is set iff off-diagonal k of row i is
+  // nonzero (in T), the neighbour test of the mean aggregation, so that
+  // the mean-only steps read one byte per row instead of the ndia values;
+  // NULL: the test reads the values
+  const unsigned char* __restrict__ nbm;
 };
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -131,6 +136,24 @@ __device__ __forceinline__ void prefetch_row(const LV<T>& L, int i) {
   prefetch_l1(L.invdeg + i);
 }
 
+// What a mean-only step reads of row i: its neighbour mask (DIA values
+// without one, or the SELL slice pointer) and 1/deg.
+template <class T>
+__device__ __forceinline__ void prefetch_mean(const LV<T>& L, int i) {
+  if (L.ndia > 0) {
+    if (L.nbm) {
+      prefetch_l1(L.nbm + i);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kMaxDia; ++k)
+        if (k < L.ndia) prefetch_l1(L.dval + (size_t)k * L.ld + i);
+    }
+  } else {
+    prefetch_l1(L.sl_ptr + (i >> 5));
+  }
+  prefetch_l1(L.invdeg + i);
+}
+
 // Fine row i's prolongation entries.
 template <class T>
 __device__ __forceinline__ void prefetch_p(const LV<T>& L, int i) {
@@ -168,6 +191,17 @@ __device__ __forceinline__ int row_of(size_t t, int B) {
 template <class T, bool kVal = true, bool kPreload = false, class F>
 __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
   if (L.ndia > 0) {
+    if (!kVal && L.nbm) {  // the neighbour test from the row's mask
+      const unsigned msk = L.nbm[i];
+#pragma unroll
+      for (int k = 0; k < kMaxDia; ++k) {
+        if (k < L.ndia) {
+          const int c = min(max(i + L.doff[k], 0), L.n - 1);
+          fn(c, T(0), ((msk >> k) & 1u) != 0u);
+        }
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < kMaxDia; ++k) {
       if (k < L.ndia) {
@@ -467,7 +501,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
                                                           T* __restrict__ u, int B,
                                                           const T* __restrict__ prm, int u_zero) {
-  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) conv_update_el(L, x, u, B, prm, u_zero, t);
   pdl_launch();
 }
@@ -485,7 +519,7 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(LV<T> L, const T* __rest
                                                         int B, const T* __restrict__ prm,
                                                         const T* __restrict__ coef, int k,
                                                         int u_zero) {
-  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) {
     int i, b;
     split_rb(t, B, i, b);
@@ -537,7 +571,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_conv_r(LV<T> L, const T* __restrict__ r,
                                                      T* __restrict__ phi, int B,
                                                      const T* __restrict__ prm) {
-  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) conv_r_el(L, r, phi, B, prm, t);
   pdl_launch();
 }
@@ -562,7 +596,7 @@ template <class T>
 __global__ void __launch_bounds__(kThreads) k_prolong_conv(LV<T> L, const T* __restrict__ pe,
                                                            const T* uin, T* u, int B,
                                                            const T* __restrict__ prm) {
-  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
+  MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) prolong_conv_el(L, pe, uin, u, B, prm, t);
   pdl_launch();
 }
@@ -999,6 +1033,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
         if (w0) {
           S.ld = ld;
           S.ldc = ldc;
+          S.nbm = nullptr;  // the staged values give the neighbour test
         }
       }
     }

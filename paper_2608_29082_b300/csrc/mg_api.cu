@@ -81,6 +81,7 @@ struct DevLevel {
   int *sl_ptr = nullptr, *col = nullptr, *p_idx = nullptr, *r_idx = nullptr;
   T *val = nullptr, *diag = nullptr, *dinv = nullptr, *invdeg = nullptr, *p_w = nullptr,
     *r_w = nullptr, *dval = nullptr;
+  unsigned char* nbm = nullptr;  // DIA levels: per-row mask of the nonzero off-diagonals (in T)
   T *u = nullptr, *f = nullptr, *t = nullptr, *u2 = nullptr;  // workspace [n][maxB]
   // SELL levels: halo tables of the fused steps (halo_sell.cuh) for tiles of
   // hs_tr rows (0: none), and the host copy of the SELL pattern they are
@@ -110,6 +111,7 @@ struct DevLevel {
     v.p_w = p_w;
     v.r_idx = r_idx;
     v.r_w = r_w;
+    v.nbm = nbm;
     return v;
   }
 };
@@ -118,7 +120,7 @@ template <class T>
 void free_level(DevLevel<T>& L) {
   void* ptrs[] = {L.sl_ptr, L.col, L.p_idx, L.r_idx, L.val,  L.diag,   L.dinv,  L.invdeg, L.p_w,
                   L.r_w,    L.u,   L.f,     L.t,     L.u2,   L.dval,   L.hs_ptr, L.hs_row,
-                  L.hs_lcol};
+                  L.hs_lcol, L.nbm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   L = DevLevel<T>();
@@ -500,6 +502,13 @@ cudaError_t upload_level(const HostLevel& H, DevLevel<T>& D, int maxB, bool vect
   D.ndia = H.ndia;
   for (int k = 0; k < mgk::kMaxDia; ++k) D.doff[k] = H.doff[k];
   if ((e = upload(&D.dval, cast<T>(H.dval))) != cudaSuccess) return e;
+  if (H.ndia > 0) {  // bit k: off-diagonal k of the row is nonzero once rounded to T
+    std::vector<unsigned char> m((size_t)H.n, 0);
+    for (int k = 0; k < H.ndia; ++k)
+      for (int i = 0; i < H.n; ++i)
+        if ((T)H.dval[(size_t)k * H.n + i] != T(0)) m[i] |= (unsigned char)(1u << k);
+    if ((e = upload(&D.nbm, m)) != cudaSuccess) return e;
+  }
   if ((e = upload(&D.sl_ptr, H.sl_ptr)) != cudaSuccess) return e;
   if ((e = upload(&D.col, H.col)) != cudaSuccess) return e;
   if ((e = upload(&D.val, cast<T>(H.val))) != cudaSuccess) return e;

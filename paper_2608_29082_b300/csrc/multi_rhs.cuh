@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, kConvMinBlocks<T, BV>)
                                                              T* __restrict__ u, int B,
                                                              const T* __restrict__ prm,
                                                              int u_zero) {
-  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
+  MG_MB_PROLOGUE(L.n, prefetch_mean(L, i))
   T s[BV], xi[BV], uu[BV];
   row_sum_mb<T, BV>(L, i, x, B, b0, s);
   ldg<T, BV>(x, base, xi);
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __r
                                                            const T* __restrict__ prm,
                                                            const T* __restrict__ coef, int k,
                                                            int u_zero) {
-  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
+  MG_MB_PROLOGUE(L.n, prefetch_mean(L, i))
   T s[BV], q[BV], uu[BV];
   row_sum_mb<T, BV>(L, i, tprev, B, b0, s);
   ldg<T, BV>(tpp, base, q);
@@ -278,7 +278,7 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_conv_r_mb(LV<T> L, const T* __restrict__ r,
                                                         T* __restrict__ phi, int B,
                                                         const T* __restrict__ prm) {
-  MG_MB_PROLOGUE(L.n, prefetch_row(L, i))
+  MG_MB_PROLOGUE(L.n, prefetch_mean(L, i))
   T s[BV], ri[BV];
   row_sum_mb<T, BV>(L, i, r, B, b0, s);
   ldg<T, BV>(r, base, ri);
@@ -352,7 +352,7 @@ template <class T, int BV>
 __global__ void __launch_bounds__(kThreads) k_prolong_mb(LV<T> L, const T* __restrict__ x,
                                                          const T* uin, T* u, int B,
                                                          const T* __restrict__ prm, int conv) {
-  MG_MB_PROLOGUE(L.n, prefetch_row(L, i); prefetch_p(L, i))
+  MG_MB_PROLOGUE(L.n, if (conv) prefetch_mean(L, i); prefetch_p(L, i))
   T phi[BV], ui[BV];
   const T w1 = prm[P_WP1];
   if (conv) {

@@ -138,8 +138,9 @@ template <class T>
 __global__ void k_sq_write(int N, const double* __restrict__ S, int block, SqDia dia,
                            int n_stacked, T* __restrict__ dval, T* __restrict__ diag,
                            T* __restrict__ dinv, T* __restrict__ invdeg,
-                           double* __restrict__ dval64, double* __restrict__ diag64,
-                           double* __restrict__ dinv64) {
+                           unsigned char* __restrict__ nbm, double* __restrict__ dval64,
+                           double* __restrict__ diag64, double* __restrict__ dinv64,
+                           unsigned char* __restrict__ nbm64) {
   const int w = N - 2, m = w * w;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= m) return;
@@ -161,11 +162,16 @@ __global__ void k_sq_write(int N, const double* __restrict__ S, int block, SqDia
     vals[k] = keep && interior ? a : 0.0;
   }
   const size_t R = (size_t)block * m + r;
+  unsigned msk = 0, msk64 = 0;  // the rows' neighbour masks (bit d: value d nonzero)
   for (int d = 0; d < dia.ndia; ++d) {
     const double v = vals[dia.slot[d]];
     dval[(size_t)d * n_stacked + R] = (T)v;
+    msk |= ((T)v != T(0) ? 1u : 0u) << d;
     if (dval64) dval64[(size_t)d * n_stacked + R] = v;
+    msk64 |= (v != 0.0 ? 1u : 0u) << d;
   }
+  if (nbm) nbm[R] = (unsigned char)msk;
+  if (nbm64) nbm64[R] = (unsigned char)msk64;
   const double di = 1.0 / aii;
   diag[R] = (T)aii;
   dinv[R] = (T)di;

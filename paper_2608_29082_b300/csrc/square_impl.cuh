@@ -206,8 +206,9 @@ extern "C" mg_status mg_square_set_block(mg_ctx* c, int32_t block, const double*
         using T = std::remove_pointer_t<decltype(dummy)>;
         const mgk::SqDia dia = square_dia(D.doff, D.ndia, w);
         mgk::k_sq_write<T><<<blocks((size_t)w * w), kThreads, 0, s>>>(
-            Nl, Sl[l], block, dia, D.n, D.dval, D.diag, D.dinv, D.invdeg,
-            D64 ? D64->dval : nullptr, D64 ? D64->diag : nullptr, D64 ? D64->dinv : nullptr);
+            Nl, Sl[l], block, dia, D.n, D.dval, D.diag, D.dinv, D.invdeg, D.nbm,
+            D64 ? D64->dval : nullptr, D64 ? D64->diag : nullptr, D64 ? D64->dinv : nullptr,
+            D64 ? D64->nbm : nullptr);
       };
       if (c->prec == 64)
         write(c->d64[l], (double*)nullptr, (DevLevel<double>*)nullptr);

@@ -63,20 +63,23 @@ def level_bytes(name: str, hier, lev: int, B: int, b: int) -> float:
     col_b = 0 if np.unique(A.indices[m] - rows[m]).size <= 8 else 4
     nc = hier.sizes[lev + 1] if lev + 1 < hier.J else 0
     nnzP = hier.P[lev].data.size if lev < hier.J - 1 else 0
+    # the mean aggregation's neighbour test: SELL column indices, or on
+    # DIA levels one mask byte per row
+    mean_b = nnz_off * col_b if col_b else n
     table = {
         "jacobi_smooth": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
         "residual_scaled": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
-        "sage_conv_update": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
-        "cheb_conv_update": nnz_off * (col_b or b) + n * b + 5 * B * n * b,
+        "sage_conv_update": mean_b + n * b + 3 * B * n * b,
+        "cheb_conv_update": mean_b + n * b + 5 * B * n * b,
         "residual": nnz_off * (col_b + b) + n * b + 3 * B * n * b,
-        "restrict_conv_fine": nnz_off * (col_b or b) + n * b + 2 * B * n * b,
+        "restrict_conv_fine": mean_b + n * b + 2 * B * n * b,
         "restrict_conv": nnzP * (4 + b) + B * n * b + B * nc * b,
         "prolong_fine": nnzP * (4 + b) + B * nc * b + B * n * b,
-        "prolong_conv": nnz_off * (col_b or b) + n * b + 3 * B * n * b,
+        "prolong_conv": mean_b + n * b + 3 * B * n * b,
         "outer_residual_fp64": nnz_off * (col_b + 8) + 2 * n * 8 + B * n * 24,
         "smooth_halo": nnz_off * (col_b + b) + 3 * n * b + 3 * B * n * b,
         "restrict_conv_halo": nnz_off * (col_b + b) + 2 * n * b + 3 * B * n * b,
-        "prolong_halo": nnzP * (4 + b) + nnz_off * (col_b or b) + n * b + B * nc * b
+        "prolong_halo": nnzP * (4 + b) + mean_b + n * b + B * nc * b
                         + 2 * B * n * b,
     }
     return table.get(name, float("nan"))
