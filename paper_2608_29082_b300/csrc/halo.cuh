@@ -106,8 +106,9 @@ __global__ void __launch_bounds__(kTailThreads)
 // for kH2X * kH2Y outputs.  Neighbour k of row i sits at grid shift
 // (dx[k], dy[k]); a region point outside the grid's columns or rows holds 0
 // and is only ever met through an absent (zero) entry.  Same arithmetic as
-// k_halo_dia and the two-kernel form.  Launch: tiles_x * tiles_y blocks,
-// (kH2X + 2)(kH2Y + 2) * B * sizeof(T) bytes of dynamic shared memory.
+// k_halo_dia and the two-kernel form.  Launch: tiles_x * tiles_y blocks of
+// kH2Threads, (kH2X + 2)(kH2Y + 2) * B * sizeof(T) bytes of dynamic shared
+// memory.
 // Measured on the 8-slot stacked 1025^2 context (8.4M rows, one rhs per
 // block): the fused smoothing step takes 201 us against 164 us for the two
 // kernels, although it moves about 40 instead of 68 bytes per row; each
@@ -120,10 +121,30 @@ struct DiaShift {
   int8_t dx[kMaxDia], dy[kMaxDia];
 };
 
-template <class T, int MODE>
-__global__ void __launch_bounds__(kTailThreads)
-    k_halo_dia2(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B,
+// Neighbour bits of row i (bit k: off-diagonal k nonzero): the level's
+// mask, or the test on the values.
+template <class T>
+__device__ __forceinline__ unsigned nb_bits(const LV<T>& L, int i) {
+  if (L.nbm) return L.nbm[i];
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxDia; ++k)
+    if (k < L.ndia && L.dval[(size_t)k * L.ld + i] != T(0)) m |= 1u << k;
+  return m;
+}
+
+// One thread per region point for one right-hand side, so that the first
+// stage is a single round of loads per block.
+constexpr int kH2Threads = (kH2RX * kH2RY + 31) / 32 * 32;
+
+// kB = 1: one right-hand side known at compile time; kB = 0: B of them.
+// No prefetch before the wait: the level spans many waves of blocks, and
+// only the first wave would overlap its predecessor.
+template <class T, int MODE, int kB>
+__global__ void __launch_bounds__(kH2Threads, 4)
+    k_halo_dia2(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B_,
                 const T* __restrict__ prm, int w, int tiles_x, DiaShift sh, int zero) {
+  const int B = kB ? kB : B_;
   extern __shared__ __align__(16) unsigned char halo_raw[];
   T* sz = reinterpret_cast<T*>(halo_raw);
   const int tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
@@ -135,15 +156,27 @@ __global__ void __launch_bounds__(kTailThreads)
     return r < L.n ? (int)r : -1;
   };
   const int npts = kH2RX * kH2RY;
-  for (int e = threadIdx.x; e < npts; e += blockDim.x) {
-    const int j = row_at(e % kH2RX, e / kH2RX);
-    if (j >= 0) {
-      if constexpr (MODE == HALO_PROLONG) prefetch_p(L, j);
-      prefetch_row(L, j);
-    }
-  }
   pdl_wait();
   pdl_launch();
+
+  // The operands of this thread's first second-stage output (its
+  // neighbour bits, 1/deg and the value it updates), loaded before the
+  // barrier so that they travel with the first stage's loads.
+  const int nown = kH2X * kH2Y * B;
+  int i0 = -1;
+  unsigned m0 = 0;
+  T id0 = T(0), v0 = T(0);
+  if ((int)threadIdx.x < nown) {
+    const int pt = threadIdx.x / B, b = threadIdx.x - pt * B;
+    i0 = row_at(1 + pt % kH2X, 1 + pt / kH2X);
+    if (i0 >= 0) {
+      const size_t t = (size_t)i0 * B + b;
+      m0 = nb_bits(L, i0);
+      id0 = L.invdeg[i0];
+      if constexpr (MODE == HALO_SMOOTH) v0 = zero ? T(0) : x[t];
+      if constexpr (MODE == HALO_PROLONG) v0 = y[t];
+    }
+  }
 
   // first stage on the region (own points and the one-point ring)
   const int nz = npts * B;
@@ -169,36 +202,38 @@ __global__ void __launch_bounds__(kTailThreads)
   __syncthreads();
 
   // second stage on the own points
-  const int nown = kH2X * kH2Y * B;
   for (int e = threadIdx.x; e < nown; e += blockDim.x) {
     const int pt = e / B, b = e - pt * B;
     const int lx = 1 + pt % kH2X, ly = 1 + pt / kH2X;
-    const int i = row_at(lx, ly);
+    const bool first = e == (int)threadIdx.x;
+    const int i = first ? i0 : row_at(lx, ly);
     if (i < 0) continue;
     const size_t t = (size_t)i * B + b;
+    const unsigned m = first ? m0 : nb_bits(L, i);
+    const T id = first ? id0 : L.invdeg[i];
     const int me = ly * kH2RX + lx;
     T s = T(0);
 #pragma unroll
     for (int k = 0; k < kMaxDia; ++k) {
       if (k < L.ndia) {
-        const bool nb = L.dval[(size_t)k * L.ld + i] != T(0);
+        const bool nb = ((m >> k) & 1u) != 0u;
         const T zv = nb ? sz[(size_t)(me + sh.dy[k] * kH2RX + sh.dx[k]) * B + b] : T(0);
         s += nb ? zv : T(0);
       }
     }
     const T zi = sz[(size_t)me * B + b];
     if constexpr (MODE == HALO_SMOOTH) {
-      const T phi = fma(prm[P_WB1], zi, prm[P_WB2] * (L.invdeg[i] * s));
-      const T u0 = zero ? T(0) : x[t];
+      const T phi = fma(prm[P_WB1], zi, prm[P_WB2] * (id * s));
+      const T u0 = first ? v0 : (zero ? T(0) : x[t]);
       y[t] = fma(prm[P_ETA], phi, u0);
     } else if constexpr (MODE == HALO_RESTRICT) {
       T p = prm[P_WR1] * zi;
-      p = fma(prm[P_WR2], L.invdeg[i] * s, p);
+      p = fma(prm[P_WR2], id * s, p);
       y[t] = p;
     } else {
       T phi = prm[P_WP1] * zi;
-      phi = fma(prm[P_WP2], L.invdeg[i] * s, phi);
-      y[t] = y[t] + phi;
+      phi = fma(prm[P_WP2], id * s, phi);
+      y[t] = (first ? v0 : y[t]) + phi;
     }
   }
 }

@@ -478,29 +478,39 @@ __device__ __forceinline__ void coarse_chol_block(const double* __restrict__ Lc,
 
 // ------------------------------------------------------- grid kernels ----
 
+// Blocks of the first wave of a 256-thread grid on B300 (148 SMs x 8
+// resident blocks).  Only they can run while the predecessor drains; later
+// blocks start after it, so their prefetches would only add instructions.
+constexpr unsigned kPrefetchBlocks = 148 * 8;
+
 // PF: prefetch statement for the thread's row (read-only data only), run
-// before griddepcontrol.wait.
+// before griddepcontrol.wait by the first wave's blocks.  The grid kernels
+// below take kB = 1 for one right-hand side known at compile time (the
+// row/column split and the neighbour index products fold) and kB = 0 for
+// B_ of them.
 #define MG_GRID_PROLOGUE(N, PF)                                             \
   const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;           \
   const bool in_range = t < (size_t)(N);                                    \
-  if (in_range) { PF; }                                                     \
+  if (in_range && blockIdx.x < kPrefetchBlocks) { PF; }                     \
   pdl_wait();                                                               \
   pdl_launch();
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_residual(LV<T> L, const T* __restrict__ f,
                                                        const T* __restrict__ u, T* __restrict__ out,
-                                                       int B, const T* __restrict__ prm, int scale,
+                                                       int B_, const T* __restrict__ prm, int scale,
                                                        int u_zero) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) residual_el(L, f, u, out, B, prm, scale, u_zero, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __restrict__ x,
-                                                          T* __restrict__ u, int B,
+                                                          T* __restrict__ u, int B_,
                                                           const T* __restrict__ prm, int u_zero) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) conv_update_el(L, x, u, B, prm, u_zero, t);
   pdl_launch();
@@ -513,12 +523,13 @@ __global__ void __launch_bounds__(kThreads) k_conv_update(LV<T> L, const T* __re
 //   k >= 2:  T_k = 2 Lhat T_{k-1} - T_{k-2};  u <- u + eta c_k T_k
 // tprev = T_{k-1}, tpp = T_{k-2} (T_0 when k = 1), out = T_k.  out may be tpp:
 // each entry of tpp is read, then overwritten, by the same thread.
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_cheb_step(LV<T> L, const T* __restrict__ tprev,
                                                         const T* tpp, T* out, T* __restrict__ u,
-                                                        int B, const T* __restrict__ prm,
+                                                        int B_, const T* __restrict__ prm,
                                                         const T* __restrict__ coef, int k,
                                                         int u_zero) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) {
     int i, b;
@@ -540,62 +551,69 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step(LV<T> L, const T* __rest
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_jacobi(LV<T> L, const T* __restrict__ f,
                                                      const T* __restrict__ uin, T* __restrict__ uout,
-                                                     int B, const T* __restrict__ prm, int u_zero) {
+                                                     int B_, const T* __restrict__ prm, int u_zero) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_row(L, row_of(t, B)))
   if (in_range) jacobi_el(L, f, uin, uout, B, prm, u_zero, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_restrict(LV<T> L, const T* __restrict__ r,
-                                                       T* __restrict__ fc, int B,
+                                                       T* __restrict__ fc, int B_,
                                                        const T* __restrict__ prm, int conv) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.nc * B, prefetch_r(L, row_of(t, B)))
   if (in_range) restrict_el(L, r, fc, B, prm, conv, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_prolong(LV<T> L, const T* __restrict__ ec,
-                                                      const T* uin, T* u, int B,
+                                                      const T* uin, T* u, int B_,
                                                       const T* __restrict__ prm, int conv) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_p(L, row_of(t, B)))
   if (in_range) prolong_el(L, ec, uin, u, B, prm, conv, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_conv_r(LV<T> L, const T* __restrict__ r,
-                                                     T* __restrict__ phi, int B,
+                                                     T* __restrict__ phi, int B_,
                                                      const T* __restrict__ prm) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) conv_r_el(L, r, phi, B, prm, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_gather(LV<T> L, const T* __restrict__ phi,
-                                                     T* __restrict__ fc, int B) {
+                                                     T* __restrict__ fc, int B_) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.nc * B, prefetch_r(L, row_of(t, B)))
   if (in_range) gather_el(L, phi, fc, B, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_pe(LV<T> L, const T* __restrict__ ec,
-                                                 T* __restrict__ pe, int B) {
+                                                 T* __restrict__ pe, int B_) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_p(L, row_of(t, B)))
   if (in_range) pe_el(L, ec, pe, B, t);
   pdl_launch();
 }
 
-template <class T>
+template <class T, int kB = 0>
 __global__ void __launch_bounds__(kThreads) k_prolong_conv(LV<T> L, const T* __restrict__ pe,
-                                                           const T* uin, T* u, int B,
+                                                           const T* uin, T* u, int B_,
                                                            const T* __restrict__ prm) {
+  const int B = kB ? kB : B_;
   MG_GRID_PROLOGUE((size_t)L.n * B, prefetch_mean(L, row_of(t, B)))
   if (in_range) prolong_conv_el(L, pe, uin, u, B, prm, t);
   pdl_launch();

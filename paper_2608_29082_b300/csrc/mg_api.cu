@@ -700,7 +700,7 @@ struct Issue {
                D.view(), f, u, out, B, P(lev), scale, zero);
       });
     } else {
-      launch(mgk::k_residual<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, u, out, B,
+      launch(B == 1 ? mgk::k_residual<T, 1> : mgk::k_residual<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, u, out, B,
              P(lev), scale, zero);
     }
   }
@@ -712,7 +712,7 @@ struct Issue {
                D.view(), x, u, B, P(lev), zero);
       });
     } else {
-      launch(mgk::k_conv_update<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, u, B,
+      launch(B == 1 ? mgk::k_conv_update<T, 1> : mgk::k_conv_update<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, u, B,
              P(lev), zero);
     }
   }
@@ -725,7 +725,7 @@ struct Issue {
                D.view(), tprev, tpp, out, u, B, P(lev), chebc(lev), k, zero);
       });
     } else {
-      launch(mgk::k_cheb_step<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), tprev, tpp,
+      launch(B == 1 ? mgk::k_cheb_step<T, 1> : mgk::k_cheb_step<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), tprev, tpp,
              out, u, B, P(lev), chebc(lev), k, zero);
     }
   }
@@ -737,7 +737,7 @@ struct Issue {
                f, uin, uout, B, P(lev), zero);
       });
     } else {
-      launch(mgk::k_jacobi<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, uin, uout, B,
+      launch(B == 1 ? mgk::k_jacobi<T, 1> : mgk::k_jacobi<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), f, uin, uout, B,
              P(lev), zero);
     }
   }
@@ -749,7 +749,7 @@ struct Issue {
                r, phi, B, P(lev));
       });
     } else {
-      launch(mgk::k_conv_r<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), r, phi, B,
+      launch(B == 1 ? mgk::k_conv_r<T, 1> : mgk::k_conv_r<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), r, phi, B,
              P(lev));
     }
   }
@@ -762,10 +762,10 @@ struct Issue {
                D.view(), x, fc, B, P(lev), scale);
       });
     } else if (scale) {
-      launch(mgk::k_restrict<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B,
+      launch(B == 1 ? mgk::k_restrict<T, 1> : mgk::k_restrict<T, 0>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B,
              P(lev), 0);
     } else {
-      launch(mgk::k_gather<T>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B);
+      launch(B == 1 ? mgk::k_gather<T, 1> : mgk::k_gather<T, 0>, grid_for((size_t)D.nc * B), kThreads, 0, D.view(), x, fc, B);
     }
   }
   void op_pe(int lev, const T* ec, T* pe) {
@@ -776,7 +776,7 @@ struct Issue {
                pe, B);
       });
     } else {
-      launch(mgk::k_pe<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec, pe, B);
+      launch(B == 1 ? mgk::k_pe<T, 1> : mgk::k_pe<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), ec, pe, B);
     }
   }
   // u = uin + Phi_P(x) with x = P e_c (conv), or u = uin + wP1 P x (plain)
@@ -788,10 +788,10 @@ struct Issue {
                D.view(), x, uin, u, B, P(lev), conv_p);
       });
     } else if (conv_p) {
-      launch(mgk::k_prolong_conv<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u,
+      launch(B == 1 ? mgk::k_prolong_conv<T, 1> : mgk::k_prolong_conv<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u,
              B, P(lev));
     } else {
-      launch(mgk::k_prolong<T>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u, B,
+      launch(B == 1 ? mgk::k_prolong<T, 1> : mgk::k_prolong<T, 0>, grid_for((size_t)D.n * B), kThreads, 0, D.view(), x, uin, u, B,
              P(lev), 0);
     }
   }
@@ -877,8 +877,8 @@ struct Issue {
   template <int MODE>
   void op_halo2(int lev, const Halo2& h, const T* f, const T* x, T* y, int zero) {
     DevLevel<T>& D = L[lev];
-    launch(mgk::k_halo_dia2<T, MODE>, dim3(h.tiles), dim3(256), h.smem, D.view(), f, x, y, B,
-           P(lev), h.w, h.tiles_x, h.sh, zero);
+    launch(B == 1 ? mgk::k_halo_dia2<T, MODE, 1> : mgk::k_halo_dia2<T, MODE, 0>, dim3(h.tiles),
+           dim3(mgk::kH2Threads), h.smem, D.view(), f, x, y, B, P(lev), h.w, h.tiles_x, h.sh, zero);
   }
   // Halo-tiled fused steps on a SELL level (halo_sell.cuh): the tile's
   // shared bytes, or 0 (two-kernel form) when the level has no halo tables
@@ -2073,17 +2073,17 @@ extern "C" mg_status mg_level_apply(mg_ctx* c, int32_t lev, int32_t op, const vo
         is.smooth(lev, X, O, 1, false);
         break;
       case MG_OP_RESIDUAL:
-        mgk::k_residual<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), X, Y, O, B,
+        (B == 1 ? mgk::k_residual<T, 1> : mgk::k_residual<T, 0>)<<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(D.view(), X, Y, O, B,
                                                                           is.P(lev), 0, 0);
         is.nk++;
         break;
       case MG_OP_RESTRICT:
-        mgk::k_restrict<T><<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
+        (B == 1 ? mgk::k_restrict<T, 1> : mgk::k_restrict<T, 0>)<<<grid_for((size_t)D.nc * B), kThreads, 0, s>>>(
             D.view(), X, O, B, is.P(lev), is.conv(lev, mgk::P_WR2));
         is.nk++;
         break;
       case MG_OP_PROLONG:
-        mgk::k_prolong<T><<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
+        (B == 1 ? mgk::k_prolong<T, 1> : mgk::k_prolong<T, 0>)<<<grid_for((size_t)D.n * B), kThreads, 0, s>>>(
             D.view(), X, Y, O, B, is.P(lev), is.conv(lev, mgk::P_WP2));
         is.nk++;
         break;

@@ -114,7 +114,7 @@ __device__ __forceinline__ void stg(T* __restrict__ x, size_t off, const T (&in)
   const int g = blockIdx.x * blockDim.x + threadIdx.x;          \
   const int i = g / nq;                                         \
   const bool in_rows = i < (NROWS);                             \
-  if (in_rows) { PF; }                                          \
+  if (in_rows && blockIdx.x < kPrefetchBlocks) { PF; }         \
   pdl_wait();                                                   \
   pdl_launch();                                                 \
   if (!in_rows) return;                                         \
