@@ -382,6 +382,11 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     neutral; measured slower than the two-kernel form on
  *                     the 8.4M-row stacked 1025^2 level (201 against 164 us
  *                     per smoothing step), so it is off.
+ *   MG_OPT_DIA_TWO_ROWS one right-hand side on a DIA level: 1 (default) the
+ *                     residual and the mean-only steps (SAGEConv update,
+ *                     Phi_R, Phi_P with the update) take two consecutive
+ *                     rows per thread, sharing each diagonal's address
+ *                     arithmetic; 0: one row per thread.  Bitwise neutral.
  *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1:
  *                     FP32 vectors in phases of FCG(1) on the scaled
  *                     correction equation, each phase ended by an FP64
@@ -424,7 +429,8 @@ typedef enum {
   MG_OPT_TAIL_TEAMS = 11,
   MG_OPT_FCG_FP32 = 12,
   MG_OPT_FCG_FLOOR = 13,
-  MG_OPT_HALO2D_BYTES = 14
+  MG_OPT_HALO2D_BYTES = 14,
+  MG_OPT_DIA_TWO_ROWS = 15
 } mg_option;
 
 mg_status mg_set_option(mg_ctx* ctx, int32_t option, int64_t value);

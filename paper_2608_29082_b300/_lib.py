@@ -20,7 +20,7 @@ OPTIONS = {"tail_work": 0, "pdl": 1, "multi_rhs": 2, "device_loop": 3, "halo_row
            "fgmres_floor": 6, "sell_halo_rows": 7,
            "sell_halo_threads": 8, "sell_halo_max_bytes": 9, "coarse_inverse": 10,
            "tail_teams": 11, "fcg_fp32": 12, "fcg_floor": 13,
-           "halo2d_bytes": 14}
+           "halo2d_bytes": 14, "dia_two_rows": 15}
 OPS = {"smooth": 0, "residual": 1, "restrict": 2, "prolong": 3, "coarse": 4,
        "outer_residual": 5, "refine_residual": 6}
 

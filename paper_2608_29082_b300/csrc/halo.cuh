@@ -121,18 +121,6 @@ struct DiaShift {
   int8_t dx[kMaxDia], dy[kMaxDia];
 };
 
-// Neighbour bits of row i (bit k: off-diagonal k nonzero): the level's
-// mask, or the test on the values.
-template <class T>
-__device__ __forceinline__ unsigned nb_bits(const LV<T>& L, int i) {
-  if (L.nbm) return L.nbm[i];
-  unsigned m = 0;
-#pragma unroll
-  for (int k = 0; k < kMaxDia; ++k)
-    if (k < L.ndia && L.dval[(size_t)k * L.ld + i] != T(0)) m |= 1u << k;
-  return m;
-}
-
 // One thread per region point for one right-hand side, so that the first
 // stage is a single round of loads per block.
 constexpr int kH2Threads = (kH2RX * kH2RY + 31) / 32 * 32;
@@ -171,7 +159,7 @@ __global__ void __launch_bounds__(kH2Threads, 4)
     i0 = row_at(1 + pt % kH2X, 1 + pt / kH2X);
     if (i0 >= 0) {
       const size_t t = (size_t)i0 * B + b;
-      m0 = nb_bits(L, i0);
+      m0 = nb_mask(L, i0);
       id0 = L.invdeg[i0];
       if constexpr (MODE == HALO_SMOOTH) v0 = zero ? T(0) : x[t];
       if constexpr (MODE == HALO_PROLONG) v0 = y[t];
@@ -209,7 +197,7 @@ __global__ void __launch_bounds__(kH2Threads, 4)
     const int i = first ? i0 : row_at(lx, ly);
     if (i < 0) continue;
     const size_t t = (size_t)i * B + b;
-    const unsigned m = first ? m0 : nb_bits(L, i);
+    const unsigned m = first ? m0 : nb_mask(L, i);
     const T id = first ? id0 : L.invdeg[i];
     const int me = ly * kH2RX + lx;
     T s = T(0);

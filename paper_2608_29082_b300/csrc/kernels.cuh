@@ -235,6 +235,18 @@ __device__ __forceinline__ void for_nb(const LV<T>& L, int i, F&& fn) {
   }
 }
 
+// Neighbour bits of DIA row i (bit k: off-diagonal k nonzero): the
+// level's mask, or the test on the values.
+template <class T>
+__device__ __forceinline__ unsigned nb_mask(const LV<T>& L, int i) {
+  if (L.nbm) return L.nbm[i];
+  unsigned m = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxDia; ++k)
+    if (k < L.ndia && L.dval[(size_t)k * L.ld + i] != T(0)) m |= 1u << k;
+  return m;
+}
+
 // sum_{j != i} a_ij x_j
 template <class T>
 __device__ __forceinline__ T row_ax(const LV<T>& L, int i, const T* __restrict__ x, int B, int b) {
@@ -624,6 +636,104 @@ __global__ void __launch_bounds__(kThreads) k_copy(const T* __restrict__ x, T* _
                                                    size_t n) {
   MG_GRID_PROLOGUE(n, (void)0)
   if (in_range) y[t] = x[t];
+  pdl_launch();
+}
+
+// ------------------------------------- one rhs on a DIA level, two rows --
+// A thread takes rows i0 = 2g and i0 + 1: the rows share each diagonal's
+// address arithmetic (32-bit offsets; the host checks ndia * ld < 2^31)
+// and keep twice the loads in flight.  Row by row the arithmetic is that of
+// residual_el, conv_update_el, conv_r_el and prolong_conv_el (same
+// operations in the same order), so the results are bitwise those of the
+// one-row kernels.  Launch: ceil(ceil(n / 2) / kThreads) blocks.
+
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_residual_dia2r(LV<T> L, const T* __restrict__ f, const T* __restrict__ u,
+                     T* __restrict__ out, const T* __restrict__ prm, int scale, int u_zero) {
+  const int i0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 < L.n && blockIdx.x < kPrefetchBlocks) prefetch_row(L, i0);
+  pdl_wait();
+  pdl_launch();
+  if (i0 >= L.n) return;
+  const bool two = i0 + 1 < L.n;
+  const int i1 = two ? i0 + 1 : i0;  // the second row, or the first again
+  T r0 = f[i0], r1 = f[i1];
+  if (!u_zero) {
+    T a0 = T(0), a1 = T(0);
+#pragma unroll
+    for (int k = 0; k < kMaxDia; ++k) {
+      if (k < L.ndia) {
+        const T* dk = L.dval + k * L.ld;
+        const T v0 = dk[i0], v1 = dk[i1];
+        const int c0 = min(max(i0 + L.doff[k], 0), L.n - 1);
+        const int c1 = min(max(i1 + L.doff[k], 0), L.n - 1);
+        a0 = fma(v0, u[c0], a0);
+        a1 = fma(v1, u[c1], a1);
+      }
+    }
+    r0 = fma(-L.diag[i0], u[i0], r0) - a0;
+    r1 = fma(-L.diag[i1], u[i1], r1) - a1;
+  }
+  if (scale) {
+    r0 = prm[P_THETA] * (r0 * L.dinv[i0]);
+    r1 = prm[P_THETA] * (r1 * L.dinv[i1]);
+  }
+  out[i0] = r0;
+  if (two) out[i1] = r1;
+  pdl_launch();
+}
+
+enum { MEAN_CONV_UPDATE = 0, MEAN_CONV_R = 1, MEAN_PROLONG_CONV = 2 };
+
+// The mean-only steps: CONV_UPDATE u = u0 + eta (wB1 x + wB2 mean x) (u0 =
+// 0 when u_zero); CONV_R y = wR1 x + wR2 mean x; PROLONG_CONV u = uin + wP1 x
+// + wP2 mean x.  The neighbour test comes from the level's mask.
+template <class T, int MODE>
+__global__ void __launch_bounds__(kThreads)
+    k_mean_dia2r(LV<T> L, const T* __restrict__ x, const T* uin, T* y,
+                 const T* __restrict__ prm, int u_zero) {
+  const int i0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 < L.n && blockIdx.x < kPrefetchBlocks) prefetch_mean(L, i0);
+  pdl_wait();
+  pdl_launch();
+  if (i0 >= L.n) return;
+  const bool two = i0 + 1 < L.n;
+  const int i1 = two ? i0 + 1 : i0;
+  const unsigned m0 = nb_mask(L, i0), m1 = nb_mask(L, i1);
+  T s0 = T(0), s1 = T(0);
+#pragma unroll
+  for (int k = 0; k < kMaxDia; ++k) {
+    if (k < L.ndia) {
+      const int c0 = min(max(i0 + L.doff[k], 0), L.n - 1);
+      const int c1 = min(max(i1 + L.doff[k], 0), L.n - 1);
+      const T x0 = x[c0], x1 = x[c1];
+      s0 += ((m0 >> k) & 1u) ? x0 : T(0);
+      s1 += ((m1 >> k) & 1u) ? x1 : T(0);
+    }
+  }
+  const T d0 = L.invdeg[i0], d1 = L.invdeg[i1];
+  if constexpr (MODE == MEAN_CONV_UPDATE) {
+    const T p0 = fma(prm[P_WB1], x[i0], prm[P_WB2] * (d0 * s0));
+    const T p1 = fma(prm[P_WB1], x[i1], prm[P_WB2] * (d1 * s1));
+    const T u0 = u_zero ? T(0) : y[i0];
+    const T u1 = u_zero ? T(0) : y[i1];
+    y[i0] = fma(prm[P_ETA], p0, u0);
+    if (two) y[i1] = fma(prm[P_ETA], p1, u1);
+  } else if constexpr (MODE == MEAN_CONV_R) {
+    T p0 = prm[P_WR1] * x[i0], p1 = prm[P_WR1] * x[i1];
+    p0 = fma(prm[P_WR2], d0 * s0, p0);
+    p1 = fma(prm[P_WR2], d1 * s1, p1);
+    y[i0] = p0;
+    if (two) y[i1] = p1;
+  } else {
+    T p0 = prm[P_WP1] * x[i0], p1 = prm[P_WP1] * x[i1];
+    p0 = fma(prm[P_WP2], d0 * s0, p0);
+    p1 = fma(prm[P_WP2], d1 * s1, p1);
+    const T v0 = uin[i0] + p0, v1 = uin[i1] + p1;
+    y[i0] = v0;
+    if (two) y[i1] = v1;
+  }
   pdl_launch();
 }
 

@@ -438,6 +438,7 @@ struct mg_ctx {
   // large use the 2D-tiled fused steps (0: never; measured slower than the
   // two-kernel form on the large stacked levels, so off)
   int64_t opt_halo2d_bytes = 0;
+  int opt_dia_two_rows = 1;  // one rhs on DIA levels: two rows per thread (k_*_dia2r)
   int opt_sell_halo_rows = 0;  // rows per tile of the halo-fused SELL steps (0: unfused)
   int opt_sell_halo_threads = 256;  // threads per block of those steps
   // largest level vector (rows x rhs x value bytes) whose smoothing and
@@ -692,9 +693,18 @@ struct Issue {
     }
   }
 
+  // One rhs on a DIA level whose offsets fit 32 bits: the two-row kernels.
+  bool two_rows(const DevLevel<T>& D) const {
+    const LV<T> v = D.view();
+    return B == 1 && c->opt_dia_two_rows && v.ndia > 0 && (int64_t)v.ndia * v.ld < INT32_MAX;
+  }
+  static dim3 two_row_grid(int n) { return grid_for(((size_t)n + 1) / 2); }
   void op_residual(int lev, const T* f, const T* u, T* out, int scale, int zero) {
     DevLevel<T>& D = L[lev];
-    if (const int bv = mbv()) {
+    if (two_rows(D)) {
+      launch(mgk::k_residual_dia2r<T>, two_row_grid(D.n), kThreads, 0, D.view(), f, u, out,
+             P(lev), scale, zero);
+    } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_residual_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
                D.view(), f, u, out, B, P(lev), scale, zero);
@@ -706,7 +716,10 @@ struct Issue {
   }
   void op_conv_update(int lev, const T* x, T* u, int zero) {
     DevLevel<T>& D = L[lev];
-    if (const int bv = mbv()) {
+    if (two_rows(D)) {
+      launch(mgk::k_mean_dia2r<T, mgk::MEAN_CONV_UPDATE>, two_row_grid(D.n), kThreads, 0,
+             D.view(), x, (const T*)nullptr, u, P(lev), zero);
+    } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_conv_update_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
                D.view(), x, u, B, P(lev), zero);
@@ -743,7 +756,10 @@ struct Issue {
   }
   void op_conv_r(int lev, const T* r, T* phi) {
     DevLevel<T>& D = L[lev];
-    if (const int bv = mbv()) {
+    if (two_rows(D)) {
+      launch(mgk::k_mean_dia2r<T, mgk::MEAN_CONV_R>, two_row_grid(D.n), kThreads, 0, D.view(), r,
+             (const T*)nullptr, phi, P(lev), 0);
+    } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_conv_r_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(),
                r, phi, B, P(lev));
@@ -782,7 +798,10 @@ struct Issue {
   // u = uin + Phi_P(x) with x = P e_c (conv), or u = uin + wP1 P x (plain)
   void op_prolong(int lev, const T* x, const T* uin, T* u, int conv_p) {
     DevLevel<T>& D = L[lev];
-    if (const int bv = mbv()) {
+    if (conv_p && two_rows(D)) {
+      launch(mgk::k_mean_dia2r<T, mgk::MEAN_PROLONG_CONV>, two_row_grid(D.n), kThreads, 0,
+             D.view(), x, uin, u, P(lev), 0);
+    } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_prolong_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
                D.view(), x, uin, u, B, P(lev), conv_p);
@@ -2212,6 +2231,11 @@ extern "C" mg_status mg_set_option(mg_ctx* c, int32_t option, int64_t value) {
     case MG_OPT_HALO2D_BYTES:
       if (value < 0) return c->fail(MG_ERR_INVALID, "mg_set_option: 2D halo bytes must be >= 0");
       c->opt_halo2d_bytes = value;
+      break;
+    case MG_OPT_DIA_TWO_ROWS:
+      if (value != 0 && value != 1)
+        return c->fail(MG_ERR_INVALID, "mg_set_option: DIA two rows must be 0 or 1");
+      c->opt_dia_two_rows = (int)value;
       break;
     case MG_OPT_TAIL_TEAMS:
       if (value < 0 || value > 64)

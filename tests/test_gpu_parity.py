@@ -494,6 +494,45 @@ def test_halo2d_tiles_are_bitwise_neutral(name, prec, nrhs):
         assert np.array_equal(outs[1][2], outs[0][2])
 
 
+@pytest.mark.parametrize("name", ["poisson33", "checker65", "lognormal65"])
+@pytest.mark.parametrize("prec", [64, 32])
+@pytest.mark.parametrize("grid_only", [True, False])
+def test_dia_two_rows_are_bitwise_neutral(name, prec, grid_only):
+    """One right-hand side on DIA levels: the kernels taking two rows per
+    thread (residual, SAGEConv update, Phi_R, Phi_P with the update; odd
+    row counts leave one row to the last thread) give the one-row kernels'
+    cycle, refinement, FCG and FGMRES solves bitwise, with and without the
+    convolutions; grid_only runs every level as grid kernels."""
+    p, Ho, Hp = problem(name)
+    dt = torch.float64 if prec == 64 else torch.float32
+    f = np.random.default_rng(5).standard_normal((Hp.sizes[0], 1))
+    for conv in (True, False):
+        prm = rand_params(Hp.J, 43, 0.1, conv=conv)
+        outs = []
+        for two in (0, 1):
+            S = Solver(Hp, prm, precision=prec, max_batch=1)
+            if grid_only:
+                S.set_option("tail_work", 0)
+                S.set_option("halo_rows", 0)
+            S.set_option("dia_two_rows", two)
+            u = torch.zeros((Hp.sizes[0], 1), dtype=dt, device=DEV)
+            fd = torch.tensor(f, dtype=dt, device=DEV)
+            for _ in range(3):
+                S.vcycle(fd, u)
+            res = [u.clone()]
+            for method in ("refine", "fcg", "fgmres"):
+                us, info = S.solve(t64(f), tol=1e-9, max_iter=300, method=method)
+                res += [us.clone(), info.iters.copy()]
+            outs.append(res)
+            S.close()
+        assert torch.isfinite(outs[0][0]).all()
+        for a, b in zip(outs[1], outs[0]):
+            if isinstance(a, torch.Tensor):
+                assert torch.equal(a, b), (name, conv)
+            else:
+                assert np.array_equal(a, b), (name, conv)
+
+
 @pytest.mark.parametrize("prec", [64, 32])
 @pytest.mark.parametrize("method", ["refine", "fcg"])
 @pytest.mark.parametrize("nrhs", [1, 3])

@@ -253,6 +253,33 @@ def test_stacked_halo2d_is_bitwise_neutral(prec):
         assert torch.equal(u1, u0) and np.array_equal(i1, i0)
 
 
+@pytest.mark.parametrize("prec", [32, 64])
+def test_stacked_two_rows_are_bitwise_neutral(prec):
+    """On a stacked context (one right-hand side per block, DIA levels of
+    odd row counts) the two-rows-per-thread kernels give the one-row
+    kernels' block solves bitwise, for all blocks and for leading blocks."""
+    N = 65
+    sys_list = systems(N, ["lognormal", "checker", "lognormal"], seed=9)
+    prm = LMGParams.identity(levels_for(N))
+    prm.wB[:, 1], prm.wR[:, 1], prm.wP[:, 1] = 0.1, 0.05, -0.05
+    f = t64(np.concatenate([x[1] for x in sys_list]))
+    outs = []
+    for two in (0, 1):
+        S = SquareBatch(N, 3, prm, precision=prec)
+        fill(S, sys_list)
+        S.set_option("tail_work", 0)
+        S.set_option("dia_two_rows", two)
+        res = []
+        for k in (3, 2):
+            u = torch.zeros_like(f)
+            info = S.solve(f, u, tol=1e-8, max_iter=300, nblocks=k)
+            res.append((u.clone(), info.iters.copy()))
+        outs.append(res)
+        S.close()
+    for (u1, i1), (u0, i0) in zip(outs[1], outs[0]):
+        assert torch.equal(u1, u0) and np.array_equal(i1, i0)
+
+
 def test_invalid_square_arguments():
     from paper_2608_29082_b300._lib import MGError
     with pytest.raises(MGError):
