@@ -382,11 +382,12 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     neutral; measured slower than the two-kernel form on
  *                     the 8.4M-row stacked 1025^2 level (201 against 164 us
  *                     per smoothing step), so it is off.
- *   MG_OPT_DIA_TWO_ROWS one right-hand side on a DIA level: 1 (default) the
- *                     residual and the mean-only steps (SAGEConv update,
- *                     Phi_R, Phi_P with the update) take two consecutive
- *                     rows per thread, sharing each diagonal's address
- *                     arithmetic; 0: one row per thread.  Bitwise neutral.
+ *   MG_OPT_DIA_TWO_ROWS one right-hand side: 1 (default) the residual and
+ *                     the mean-only steps (SAGEConv update, Phi_R, Phi_P with
+ *                     the update) on DIA levels, and P e_c on every level,
+ *                     take two consecutive rows per thread, sharing the
+ *                     address arithmetic; 0: one row per thread.  Bitwise
+ *                     neutral.
  *   MG_OPT_FCG_FP32   precision-32 contexts: mg_solve_fcg's vectors.  1:
  *                     FP32 vectors in phases of FCG(1) on the scaled
  *                     correction equation, each phase ended by an FP64

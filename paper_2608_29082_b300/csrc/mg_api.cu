@@ -438,7 +438,7 @@ struct mg_ctx {
   // large use the 2D-tiled fused steps (0: never; measured slower than the
   // two-kernel form on the large stacked levels, so off)
   int64_t opt_halo2d_bytes = 0;
-  int opt_dia_two_rows = 1;  // one rhs on DIA levels: two rows per thread (k_*_dia2r)
+  int opt_dia_two_rows = 1;  // one rhs: two rows per thread (k_*_dia2r, k_pe2r)
   int opt_sell_halo_rows = 0;  // rows per tile of the halo-fused SELL steps (0: unfused)
   int opt_sell_halo_threads = 256;  // threads per block of those steps
   // largest level vector (rows x rhs x value bytes) whose smoothing and
@@ -786,7 +786,9 @@ struct Issue {
   }
   void op_pe(int lev, const T* ec, T* pe) {
     DevLevel<T>& D = L[lev];
-    if (const int bv = mbv()) {
+    if (B == 1 && c->opt_dia_two_rows) {
+      launch(mgk::k_pe2r<T>, two_row_grid(D.n), kThreads, 0, D.view(), ec, pe);
+    } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_pe_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(), ec,
                pe, B);

@@ -485,6 +485,81 @@ def run_training(a):
                       "train_seconds": round(t_train, 2)}), flush=True)
 
 
+
+# Algorithmic bytes per row of the stacked square levels' main kernels for
+# one rhs in FP32 (interior rows: six off-diagonals; DIA, so no column
+# indices): residual_scaled reads f, u, six values, diagonal and its
+# inverse and writes delta; sage_conv_update reads the neighbour mask, 1/deg,
+# delta and u and writes u; residual reads f, u, six values and the diagonal
+# and writes r.
+STACKED_ROW_BYTES = {"residual_scaled": 44, "sage_conv_update": 17, "residual": 40}
+
+
+def run_stacked(a):
+    """An S-slot stacked context of N x N meshes (one seeded lognormal
+    operator per slot, set up on the device): the per-kernel table of an
+    eager FP32 cycle, the graph-replayed cycle and optionally one solve of
+    every slot to 1e-8."""
+    from . import serve, trained
+    from .square import SquareBatch
+    N, S = a.N, a.slots
+    coefs, src = serve.make_pools([N], min(S, 4), 1, a.seed)
+    p = trained.read(trained.LOGNORMAL1025) if os.path.exists(trained.LOGNORMAL1025) \
+        else trained.load(None, 12)
+    sb = SquareBatch(N, S, p, precision=32)
+    for k in range(S):
+        sb.set_block(k, torch.tensor(coefs[(N, k % min(S, 4))], dtype=torch.float64,
+                                     device=sb.device))
+    sb.set_option("dia_two_rows", a.two_rows)
+    sb.set_option("halo2d_bytes", a.halo2d_bytes)
+    g = torch.Generator(device=sb.device).manual_seed(a.seed)
+    f = torch.randn(S * sb.m, dtype=torch.float32, device=sb.device, generator=g)
+    u = torch.zeros_like(f)
+    for _ in range(a.cycles):
+        sb.vcycle(f, u)
+    torch.cuda.synchronize()
+    agg = {}
+    for _ in range(3):
+        u.zero_()
+        for name, lev, ms in sb.vcycle_profile(f, u):
+            r = agg.setdefault((name, lev), [0.0, 0])
+            r[0] += ms
+            r[1] += 1
+    peak = hbm_peak()
+    rows = []
+    for (name, lev), (ms, cnt) in sorted(agg.items(), key=lambda kv: -kv[1][0]):
+        us = 1e3 * ms / cnt
+        rb = STACKED_ROW_BYTES.get(name) if lev == 0 else None
+        gbs = rb * sb.sizes[0] / (us * 1e-6) / 1e9 if rb else None
+        rows.append({"kernel": name, "level": lev, "launches_per_cycle": cnt // 3,
+                     "us_per_launch": round(us, 2),
+                     "GBps": round(gbs, 1) if gbs else None,
+                     "frac_of_hbm": round(gbs / peak, 3) if gbs else None})
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        sb.vcycle(f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    out = {"workload": f"stacked {S} x {N}^2 lognormal, {sb.J} levels, FP32 cycle",
+           "rows": sb.sizes[0], "graph_cycle_ms": round(e0.elapsed_time(e1) / 10, 4),
+           "hbm_peak_gbs": peak, "kernels": rows[:16]}
+    if a.solve:
+        f64 = torch.tensor(np.concatenate([src[(N, 0)]] * S), dtype=torch.float64,
+                           device=sb.device)
+        u64 = torch.zeros_like(f64)
+        sb.solve(f64, u64, tol=1e-8, max_iter=100)
+        u64.zero_()
+        torch.cuda.synchronize()
+        e0.record()
+        info = sb.solve(f64, u64, tol=1e-8, max_iter=100)
+        e1.record()
+        torch.cuda.synchronize()
+        out["solve_ms"] = round(e0.elapsed_time(e1), 3)
+        out["solve_iters_max"] = int(info.iters.max())
+    print(json.dumps(out), flush=True)
+
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -531,7 +606,16 @@ if __name__ == "__main__":
     pc.add_argument("--fcg-steps", type=int, default=3)
     pc.add_argument("--features2", type=int, default=1,
                     help="also run three two-feature cycles on 1025^2 vertices")
+    sq = sub.add_parser("stacked")
+    sq.add_argument("--N", type=int, default=1025)
+    sq.add_argument("--slots", type=int, default=8)
+    sq.add_argument("--cycles", type=int, default=2, help="warm-up cycles")
+    sq.add_argument("--solve", type=int, default=1)
+    sq.add_argument("--two-rows", type=int, default=1)
+    sq.add_argument("--halo2d-bytes", type=int, default=0)
+    sq.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     torch.cuda.set_device(0)
     {"lshape": run_lshape, "training": run_training, "cheb": run_cheb,
-     "profile_case": run_profile_case, "features2": run_features2}[a.cmd](a)
+     "profile_case": run_profile_case, "features2": run_features2,
+     "stacked": run_stacked}[a.cmd](a)
