@@ -737,6 +737,24 @@ __global__ void __launch_bounds__(kThreads)
   pdl_launch();
 }
 
+// P e_c per fine row (prolong_at's arithmetic), one rhs, two rows per
+// thread; any layout (the prolongation lists are per row).
+template <class T>
+__global__ void __launch_bounds__(kThreads)
+    k_pe2r(LV<T> L, const T* __restrict__ ec, T* __restrict__ pe) {
+  const int i0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (i0 < L.n && blockIdx.x < kPrefetchBlocks) prefetch_p(L, i0);
+  pdl_wait();
+  pdl_launch();
+  if (i0 >= L.n) return;
+  const bool two = i0 + 1 < L.n;
+  const int i1 = two ? i0 + 1 : i0;
+  const T v0 = prolong_at(L, i0, ec, 1, 0), v1 = prolong_at(L, i1, ec, 1, 0);
+  pe[i0] = v0;
+  if (two) pe[i1] = v1;
+  pdl_launch();
+}
+
 template <class T>
 __global__ void k_coarse_chol(const double* __restrict__ Lc, const double* __restrict__ Uc,
                               const double* __restrict__ dinv, int n, const T* __restrict__ f,
