@@ -380,8 +380,8 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     where the tile fits 48 KB of shared memory for nrhs
  *                     right-hand sides.  0 (default): never.  Bitwise
  *                     neutral; measured slower than the two-kernel form on
- *                     the 8.4M-row stacked 1025^2 level (201 against 164 us
- *                     per smoothing step), so it is off.
+ *                     the 8.4M-row stacked 1025^2 level (167 against 96 us
+ *                     per smoothing step with one rhs), so it is off.
  *   MG_OPT_DIA_TWO_ROWS one right-hand side: 1 (default) the residual and
  *                     the mean-only steps (SAGEConv update, Phi_R, Phi_P with
  *                     the update) on DIA levels, and P e_c on every level,

@@ -110,10 +110,11 @@ __global__ void __launch_bounds__(kTailThreads)
 // kH2Threads, (kH2X + 2)(kH2Y + 2) * B * sizeof(T) bytes of dynamic shared
 // memory.
 // Measured on the 8-slot stacked 1025^2 context (8.4M rows, one rhs per
-// block): the fused smoothing step takes 201 us against 164 us for the two
-// kernels, although it moves about 40 instead of 68 bytes per row; each
-// thread's short chain of dependent loads and the block barrier keep it at
-// 1.7 TB/s (64 x 8 tiles: 227 us).  Off by default (MG_OPT_HALO2D_BYTES).
+// block): the fused smoothing step takes 167 us against 96 us for the
+// two-row pair (k_residual_dia2r + k_mean_dia2r), although it moves about
+// 40 instead of 68 bytes per row: every region point repeats a full
+// residual, so it issues more instructions per output than the pair, which
+// is no longer DRAM-bound either.  Off by default (MG_OPT_HALO2D_BYTES).
 constexpr int kH2X = 32, kH2Y = 8;
 constexpr int kH2RX = kH2X + 2, kH2RY = kH2Y + 2;
 
