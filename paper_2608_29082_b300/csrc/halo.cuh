@@ -30,10 +30,12 @@ namespace mgk {
 
 enum { HALO_SMOOTH = 0, HALO_RESTRICT = 1, HALO_PROLONG = 2 };
 
-template <class T, int MODE>
+// kB = 1: one right-hand side known at compile time; kB = 0: B of them.
+template <class T, int MODE, int kB>
 __global__ void __launch_bounds__(kTailThreads)
-    k_halo_dia(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B,
+    k_halo_dia(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B_,
                const T* __restrict__ prm, int TR, int H, int zero) {
+  const int B = kB ? kB : B_;
   extern __shared__ __align__(16) unsigned char halo_raw[];
   T* sz = reinterpret_cast<T*>(halo_raw);
   const int r0 = blockIdx.x * TR;
@@ -48,6 +50,24 @@ __global__ void __launch_bounds__(kTailThreads)
   }
   pdl_wait();
   pdl_launch();
+
+  // The operands of this thread's first second-stage element (its row's
+  // neighbour bits, 1/deg and the value it updates), loaded before the
+  // barrier so that they travel with the first stage's loads instead of
+  // costing a second memory round trip after it.
+  const size_t e0 = (size_t)(r0 - lo) * B + threadIdx.x;
+  const size_t e1 = (size_t)(r1 - lo) * B;
+  unsigned m0 = 0;
+  T id0 = T(0), v0 = T(0);
+  if (e0 < e1) {
+    const size_t t = base + e0;
+    int i, b;
+    split_rb(t, B, i, b);
+    m0 = nb_mask(L, i);
+    id0 = L.invdeg[i];
+    if constexpr (MODE == HALO_SMOOTH) v0 = zero ? T(0) : x[t];
+    if constexpr (MODE == HALO_PROLONG) v0 = y[t];
+  }
 
   // first stage on own rows and halo
   for (size_t e = threadIdx.x; e < nz; e += blockDim.x) {
@@ -70,29 +90,36 @@ __global__ void __launch_bounds__(kTailThreads)
   __syncthreads();
 
   // second stage on own rows; every neighbour (clamped index included) is
-  // inside [lo, hi)
-  const size_t e1 = (size_t)(r1 - lo) * B;
-  for (size_t e = (size_t)(r0 - lo) * B + threadIdx.x; e < e1; e += blockDim.x) {
+  // inside [lo, hi).  The neighbour sum is row_sum's (ascending offsets,
+  // absent entries adding +0).
+  for (size_t e = e0; e < e1; e += blockDim.x) {
     const size_t t = base + e;
     int i, b;
     split_rb(t, B, i, b);
+    const bool first = e == e0;
+    const unsigned m = first ? m0 : nb_mask(L, i);
+    const T id = first ? id0 : L.invdeg[i];
     T s = T(0);
-    for_nb<T, false>(L, i, [&](int c, T, bool nb) {
-      const T zv = sz[(size_t)(c - lo) * B + b];
-      s += nb ? zv : T(0);
-    });
+#pragma unroll
+    for (int k = 0; k < kMaxDia; ++k) {
+      if (k < L.ndia) {
+        const int c = min(max(i + L.doff[k], 0), L.n - 1);
+        const T zv = sz[(size_t)(c - lo) * B + b];
+        s += ((m >> k) & 1u) ? zv : T(0);
+      }
+    }
     if constexpr (MODE == HALO_SMOOTH) {
-      const T phi = fma(prm[P_WB1], sz[e], prm[P_WB2] * (L.invdeg[i] * s));
-      const T u0 = zero ? T(0) : x[t];
+      const T phi = fma(prm[P_WB1], sz[e], prm[P_WB2] * (id * s));
+      const T u0 = first ? v0 : (zero ? T(0) : x[t]);
       y[t] = fma(prm[P_ETA], phi, u0);
     } else if constexpr (MODE == HALO_RESTRICT) {
       T p = prm[P_WR1] * sz[e];
-      p = fma(prm[P_WR2], L.invdeg[i] * s, p);
+      p = fma(prm[P_WR2], id * s, p);
       y[t] = p;
     } else {
       T phi = prm[P_WP1] * sz[e];
-      phi = fma(prm[P_WP2], L.invdeg[i] * s, phi);
-      y[t] = y[t] + phi;
+      phi = fma(prm[P_WP2], id * s, phi);
+      y[t] = (first ? v0 : y[t]) + phi;
     }
   }
 }

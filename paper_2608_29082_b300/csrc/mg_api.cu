@@ -930,7 +930,8 @@ struct Issue {
   void op_halo(int lev, int TR, int H, size_t smem, int threads, const T* f, const T* x, T* y,
                int zero) {
     DevLevel<T>& D = L[lev];
-    launch(mgk::k_halo_dia<T, MODE>, dim3((unsigned)((D.n + TR - 1) / TR)), dim3(threads), smem,
+    launch(B == 1 ? mgk::k_halo_dia<T, MODE, 1> : mgk::k_halo_dia<T, MODE, 0>,
+           dim3((unsigned)((D.n + TR - 1) / TR)), dim3(threads), smem,
            D.view(), f, x, y, B, P(lev), TR, H, zero);
   }
 
