@@ -1279,14 +1279,18 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 constexpr int kRedRows = 32;
 constexpr int kRedMax = 1024;  // kRedRows x 32 columns
 
+// ldexp out of line: a call is never evaluated speculatively, so the FP64
+// arithmetic of its special cases stays off the common path of scale2.
+__device__ __noinline__ double ldexp_rare(double x, int e) { return ldexp(x, e); }
+
 // x * 2^e.  For -1022 <= e <= 1023, 2^e is a normal binary64 number (biased
 // exponent e + 1023, zero fraction), so one multiply gives the exact scaled
 // value, rounded once if it is subnormal: bitwise what ldexp returns, without
 // ldexp's FP64 special-case arithmetic (B300's FP64 pipe is narrow).  Other e
 // go through ldexp.
 __device__ __forceinline__ double scale2(double x, int e) {
-  return (e >= -1022 && e <= 1023) ? x * __longlong_as_double((long long)(e + 1023) << 52)
-                                   : ldexp(x, e);
+  if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp_rare(x, e);
 }
 
 // (row, rhs) of this thread in the reduction tiling.

@@ -211,24 +211,61 @@ __device__ __forceinline__ double block_tree_sum(double v, double* sh) {
   return s;
 }
 
+// The per-block norms take kBlkRows rows per thread: a thread adds its
+// rows' squares in row order (fma), then the block adds the threads by a
+// fixed tree.  B300's FP64 pipe bounds these kernels, and one tree per row
+// (ten FP64 shuffle-adds) cost more than the residual itself.  Grid:
+// (ceil(m / (kThreads * kBlkRows)), slots); partial[chunk][slot].
+constexpr int kBlkRows = 4;
+
 __global__ void __launch_bounds__(kThreads) k_blk_sumsq(const double* __restrict__ x, int m,
                                                         int slots,
                                                         double* __restrict__ partial) {
   pdl_wait();
   __shared__ double sh[kThreads];
   const int b = blockIdx.y;
-  const int r = blockIdx.x * kThreads + threadIdx.x;
+  const int r0 = blockIdx.x * kThreads * kBlkRows + threadIdx.x;
   double v = 0.0;
-  if (r < m) {
-    const double e = x[(size_t)b * m + r];
-    v = e * e;
+#pragma unroll
+  for (int k = 0; k < kBlkRows; ++k) {
+    const int r = r0 + k * kThreads;
+    if (r < m) {
+      const double e = x[(size_t)b * m + r];
+      v = fma(e, e, v);
+    }
   }
   const double s = block_tree_sum(v, sh);
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * slots + b] = s;
 }
 
+// The rows of one thread of k_blk_resid64.  kP2: rhat = float(r * p2) with
+// p2 = 2^e exactly (scale2's in-range form); otherwise scale2 itself.  The
+// slot's exponent is uniform, so the choice is one branch per thread and
+// the FP64 pipe, which bounds this kernel on B300, never sees the other
+// form.
+template <bool kP2>
+__device__ __forceinline__ double blk_resid_rows(const LV<double>& L, const double* __restrict__ f,
+                                                 const double* __restrict__ u,
+                                                 float* __restrict__ rhat, int se, double p2,
+                                                 int m, int b, int r0) {
+  double ss = 0.0;
+#pragma unroll
+  for (int k = 0; k < kBlkRows; ++k) {
+    const int r = r0 + k * kThreads;
+    if (r < m) {
+      const int i = b * m + r;
+      const double ax = row_ax(L, i, u, 1, 0);
+      const double rv = fma(-L.diag[i], u[i], f[i]) - ax;
+      if (rhat) rhat[i] = (float)(kP2 ? rv * p2 : scale2(rv, se));
+      ss = fma(rv, rv, ss);
+    }
+  }
+  return ss;
+}
+
 // r = f - A u in FP64 (the arithmetic of k_resid64), rhat = float(2^-sexp_b r)
-// (may be NULL), and the block's partial sums of r^2.
+// (may be NULL), and the block's partial sums of r^2; kBlkRows rows per
+// thread, grid as k_blk_sumsq.
 __global__ void __launch_bounds__(kThreads) k_blk_resid64(LV<double> L, const double* __restrict__ f,
                                                           const double* __restrict__ u,
                                                           float* __restrict__ rhat,
@@ -238,15 +275,13 @@ __global__ void __launch_bounds__(kThreads) k_blk_resid64(LV<double> L, const do
   pdl_wait();
   __shared__ double sh[kThreads];
   const int b = blockIdx.y;
-  const int r = blockIdx.x * kThreads + threadIdx.x;
-  double rv = 0.0;
-  if (r < m) {
-    const int i = b * m + r;
-    const double ax = row_ax(L, i, u, 1, 0);
-    rv = fma(-L.diag[i], u[i], f[i]) - ax;
-    if (rhat) rhat[i] = (float)scale2(rv, -sexp[b]);
-  }
-  const double s = block_tree_sum(rv * rv, sh);
+  const int r0 = blockIdx.x * kThreads * kBlkRows + threadIdx.x;
+  const int se = rhat ? -sexp[b] : 0;
+  const bool p2ok = se >= -1022 && se <= 1023;
+  const double p2 = p2ok ? __longlong_as_double((long long)(se + 1023) << 52) : 0.0;
+  const double ss = p2ok ? blk_resid_rows<true>(L, f, u, rhat, se, p2, m, b, r0)
+                         : blk_resid_rows<false>(L, f, u, rhat, se, p2, m, b, r0);
+  const double s = block_tree_sum(ss, sh);
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * slots + b] = s;
 }
 

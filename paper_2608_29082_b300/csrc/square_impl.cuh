@@ -257,7 +257,10 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
   std::vector<DevLevel<float>> v32 = lead(c->d32);
   std::vector<DevLevel<double>> v64 = lead(c->d64);
   const dim3 bgrid((unsigned)((m + kThreads - 1) / kThreads), (unsigned)S);
-  const int nchunk = (int)bgrid.x;
+  // the norm kernels: kBlkRows rows per thread
+  const dim3 ngrid((unsigned)((m + kThreads * mgk::kBlkRows - 1) / (kThreads * mgk::kBlkRows)),
+                   (unsigned)S);
+  const int nchunk = (int)ngrid.x;
   const LV<double> L0 = v64[0].view();
   const bool p32 = c->prec == 32;
   c->solve_ctl[0] = tol;
@@ -284,7 +287,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
   double* fsum = rsum + SA;
   double* relres = fsum + SA;
   auto check = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
-    is.launch(mgk::k_blk_resid64, bgrid, dim3(kThreads), 0, L0, f, (const double*)u,
+    is.launch(mgk::k_blk_resid64, ngrid, dim3(kThreads), 0, L0, f, (const double*)u,
               p32 ? c->rhat32 : (float*)nullptr, (const int*)sexp, m, S, c->partial);
     if ((int64_t)S * nchunk <= kMergeReduceMax) {
       is.launch(mgk::k_reduce_check, dim3(1), dim3(kThreads), 0, (const double*)c->partial, nchunk,
@@ -301,7 +304,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
   };
   auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
     Issue<double> is{c, v64, c->prm64, cs, 1};
-    is.launch(mgk::k_blk_sumsq, bgrid, dim3(kThreads), 0, f, m, S, c->partial);
+    is.launch(mgk::k_blk_sumsq, ngrid, dim3(kThreads), 0, f, m, S, c->partial);
     is.launch(mgk::k_reduce, dim3(S), dim3(kThreads), 0, (const double*)c->partial, nchunk, S,
               fsum);
     is.launch(k_init_solve, dim3((S + kThreads - 1) / kThreads), dim3(kThreads), 0,

@@ -512,6 +512,8 @@ def run_stacked(a):
                                      device=sb.device))
     sb.set_option("dia_two_rows", a.two_rows)
     sb.set_option("halo2d_bytes", a.halo2d_bytes)
+    if a.host_loop:  # plain graphs per iteration (profilers skip conditional nodes)
+        sb.set_option("device_loop", 0)
     g = torch.Generator(device=sb.device).manual_seed(a.seed)
     f = torch.randn(S * sb.m, dtype=torch.float32, device=sb.device, generator=g)
     u = torch.zeros_like(f)
@@ -613,6 +615,8 @@ if __name__ == "__main__":
     sq.add_argument("--solve", type=int, default=1)
     sq.add_argument("--two-rows", type=int, default=1)
     sq.add_argument("--halo2d-bytes", type=int, default=0)
+    sq.add_argument("--host-loop", action="store_true",
+                    help="iterate the solve from the host (for profilers)")
     sq.add_argument("--seed", type=int, default=0)
     a = ap.parse_args()
     torch.cuda.set_device(0)
