@@ -1323,11 +1323,18 @@ __device__ __forceinline__ void red_store(const double* sh, int B, double* __res
 
 // r = f - A u in FP64; optionally rhat = float(r * 2^-sexp[b]); partial sums
 // of r^2.
+// d0 (may be NULL): also the first smoothing step's delta of the next FP32
+// cycle, which starts from zero on level 0: theta_0 (rhat dinv_0), the
+// arithmetic of residual_el with u_zero (FP32 level-0 dinv0, parameters
+// prm0 of level 0), so that cycle skips that launch.
 __global__ void __launch_bounds__(kRedMax) k_resid64(LV<double> L, const double* __restrict__ f,
                                                      const double* __restrict__ u,
                                                      float* __restrict__ rhat,
                                                      const int* __restrict__ sexp, int B,
-                                                     double* __restrict__ partial) {
+                                                     double* __restrict__ partial,
+                                                     float* __restrict__ d0,
+                                                     const float* __restrict__ dinv0,
+                                                     const float* __restrict__ prm0) {
   pdl_wait();
   __shared__ double sh[kRedMax];
   int i, b;
@@ -1338,7 +1345,11 @@ __global__ void __launch_bounds__(kRedMax) k_resid64(LV<double> L, const double*
     const size_t k = (size_t)i * B + b;
     const double ax = row_ax(L, i, u, B, b);
     r = fma(-L.diag[i], u[k], f[k]) - ax;
-    if (rhat) rhat[k] = (float)scale2(r, -sexp[b]);
+    if (rhat) {
+      const float rh = (float)scale2(r, -sexp[b]);
+      rhat[k] = rh;
+      if (d0) d0[k] = prm0[P_THETA] * (rh * dinv0[i]);
+    }
   }
   sh[threadIdx.x] = r * r;
   __syncthreads();

@@ -615,6 +615,9 @@ struct Issue {
   cudaStream_t s;
   int B;
   int nk = 0;
+  // level 0's first smoothing step from zero has its delta in L[0].t already
+  // (written by k_resid64 with the scaled residual): skip its launch
+  bool delta0_ready = false;
   // optional per-kernel timing: an event pair around every launch
   std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>>* rec = nullptr;
 
@@ -1016,9 +1019,11 @@ struct Issue {
     }
     for (int k = 0; k < nu; ++k) {
       const int z = zero && k == 0;
-      pre(MG_K_RESIDUAL_SCALED, lev);
-      op_residual(lev, f, u, D.t, 1, z);
-      post();
+      if (!(z && lev == 0 && delta0_ready)) {
+        pre(MG_K_RESIDUAL_SCALED, lev);
+        op_residual(lev, f, u, D.t, 1, z);
+        post();
+      }
       pre(MG_K_CONV_UPDATE, lev);
       op_conv_update(lev, D.t, u, z);
       post();
@@ -1953,7 +1958,9 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
   // residual of the current iterate, its norms and the convergence test
   auto check_tail = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
     is.launch(mgk::k_resid64, rgrid, rblock, 0, L0, (const double*)f, (const double*)u,
-              p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B, c->partial);
+              p32 ? c->rhat32 : (float*)nullptr, (const int*)c->sexp, (int)B, c->partial,
+              p32 ? c->d32[0].t : (float*)nullptr,
+              p32 ? (const float*)c->d32[0].dinv : (const float*)nullptr, (const float*)c->prm32);
     reduce_and_check(is, c, nblk, (int)B, p32 ? c->sexp_prev : (int*)nullptr, inc, h, cond);
   };
   auto pre = [&](cudaStream_t cs, cudaGraphConditionalHandle h, int cond) {
@@ -1970,6 +1977,7 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
     int nk = 0;
     if (p32) {
       Issue<float> is{c, c->d32, c->prm32, cs, B};
+      is.delta0_ready = true;  // check_tail's k_resid64 wrote the first step's delta
       is.vcycle(c->rhat32, c->c32, true);
       is.launch(mgk::k_refine_update, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
                 (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0, (int)B,
@@ -2060,7 +2068,8 @@ extern "C" mg_status mg_level_apply(mg_ctx* c, int32_t lev, int32_t op, const vo
     is.launch(k_init_solve, dim3(1), dim3(kThreads), 0, (const double*)c->fsum, (int)B, c->active,
               c->iters, c->sexp);
     is.launch(mgk::k_resid64, rgrid, rblock, 0, c->d64[0].view(), (const double*)x,
-              (const double*)y, (float*)out, (const int*)c->sexp, (int)B, c->partial);
+              (const double*)y, (float*)out, (const int*)c->sexp, (int)B, c->partial,
+              (float*)nullptr, (const float*)nullptr, (const float*)nullptr);
     MG_CUDA(cudaGetLastError());
     c->launches += is.nk;
     return MG_OK;

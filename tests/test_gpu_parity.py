@@ -189,6 +189,37 @@ def test_fp32_refinement_reaches_tolerance(name):
     assert np.all(np.abs(info.iters - ref.iters) <= max(2, 0.1 * ref.iters.max()))
 
 
+@pytest.mark.parametrize("name", ["checker65", "lognormal65", "lshape_r2"])
+@pytest.mark.parametrize("nrhs", [1, 2])
+def test_fp32_refinement_replays_bitwise(name, nrhs):
+    """The FP32 refinement loop (one captured graph: the cycle, u += 2^s c,
+    the FP64 residual with the next cycle's scaled residual and first
+    smoothing delta, the test) equals, bitwise, a host replay of Algorithm
+    2 inside iterative refinement through entry points that fold nothing:
+    r = f - A u in FP64, s = ilogb ||r||, c = one FP32 cycle on float(2^-s r)
+    from zero, u += 2^s c."""
+    p, Ho, Hp = problem(name)
+    prm = rand_params(Hp.J, 23, 0.05)
+    f = t64(np.random.default_rng(31).standard_normal((Hp.sizes[0], nrhs)))
+    S = Solver(Hp, prm, precision=32, max_batch=nrhs)
+    K = 4
+    u = torch.zeros_like(f)
+    r = torch.empty_like(f)
+    for _ in range(K):
+        S.level_apply(0, "outer_residual", f, u, r)
+        rn = np.sqrt((r.cpu().numpy() ** 2).sum(axis=0))
+        sexp = np.frexp(rn)[1] - 1  # ilogb
+        scale = torch.tensor(np.ldexp(1.0, -sexp), dtype=torch.float64, device=DEV)
+        rhat = (r * scale).float()
+        c = torch.zeros_like(rhat)
+        S.vcycle(rhat, c)
+        u = u + c.double() / scale
+    us, info = S.solve(f, tol=1e-300, max_iter=K)
+    assert np.array_equal(info.iters, np.full(nrhs, K))
+    assert torch.equal(us, u), (name, (us - u).abs().max().item())
+    S.close()
+
+
 def test_solve_result_independent_of_batch():
     p, Ho, Hp = problem("lognormal65")
     prm = rand_params(Hp.J, 19, 0.05)
