@@ -247,7 +247,8 @@ template <bool kP2>
 __device__ __forceinline__ double blk_resid_rows(const LV<double>& L, const double* __restrict__ f,
                                                  const double* __restrict__ u,
                                                  float* __restrict__ rhat, int se, double p2,
-                                                 int m, int b, int r0) {
+                                                 int m, int b, int r0, float* __restrict__ d0,
+                                                 const float* __restrict__ dinv0, float theta0) {
   double ss = 0.0;
 #pragma unroll
   for (int k = 0; k < kBlkRows; ++k) {
@@ -256,7 +257,11 @@ __device__ __forceinline__ double blk_resid_rows(const LV<double>& L, const doub
       const int i = b * m + r;
       const double ax = row_ax(L, i, u, 1, 0);
       const double rv = fma(-L.diag[i], u[i], f[i]) - ax;
-      if (rhat) rhat[i] = (float)(kP2 ? rv * p2 : scale2(rv, se));
+      if (rhat) {
+        const float rh = (float)(kP2 ? rv * p2 : scale2(rv, se));
+        rhat[i] = rh;
+        if (d0) d0[i] = theta0 * (rh * dinv0[i]);
+      }
       ss = fma(rv, rv, ss);
     }
   }
@@ -265,13 +270,17 @@ __device__ __forceinline__ double blk_resid_rows(const LV<double>& L, const doub
 
 // r = f - A u in FP64 (the arithmetic of k_resid64), rhat = float(2^-sexp_b r)
 // (may be NULL), and the block's partial sums of r^2; kBlkRows rows per
-// thread, grid as k_blk_sumsq.
+// thread, grid as k_blk_sumsq.  d0 (may be NULL): the next FP32 cycle's first
+// level-0 smoothing delta, as k_resid64's.
 __global__ void __launch_bounds__(kThreads) k_blk_resid64(LV<double> L, const double* __restrict__ f,
                                                           const double* __restrict__ u,
                                                           float* __restrict__ rhat,
                                                           const int* __restrict__ sexp, int m,
                                                           int slots,
-                                                          double* __restrict__ partial) {
+                                                          double* __restrict__ partial,
+                                                          float* __restrict__ d0,
+                                                          const float* __restrict__ dinv0,
+                                                          const float* __restrict__ prm0) {
   pdl_wait();
   __shared__ double sh[kThreads];
   const int b = blockIdx.y;
@@ -279,8 +288,10 @@ __global__ void __launch_bounds__(kThreads) k_blk_resid64(LV<double> L, const do
   const int se = rhat ? -sexp[b] : 0;
   const bool p2ok = se >= -1022 && se <= 1023;
   const double p2 = p2ok ? __longlong_as_double((long long)(se + 1023) << 52) : 0.0;
-  const double ss = p2ok ? blk_resid_rows<true>(L, f, u, rhat, se, p2, m, b, r0)
-                         : blk_resid_rows<false>(L, f, u, rhat, se, p2, m, b, r0);
+  const float theta0 = d0 ? prm0[P_THETA] : 0.0f;
+  const double ss =
+      p2ok ? blk_resid_rows<true>(L, f, u, rhat, se, p2, m, b, r0, d0, dinv0, theta0)
+           : blk_resid_rows<false>(L, f, u, rhat, se, p2, m, b, r0, d0, dinv0, theta0);
   const double s = block_tree_sum(ss, sh);
   if (threadIdx.x == 0) partial[(size_t)blockIdx.x * slots + b] = s;
 }

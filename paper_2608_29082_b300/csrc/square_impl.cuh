@@ -288,7 +288,9 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
   double* relres = fsum + SA;
   auto check = [&](Issue<double>& is, cudaGraphConditionalHandle h, int inc, int cond) {
     is.launch(mgk::k_blk_resid64, ngrid, dim3(kThreads), 0, L0, f, (const double*)u,
-              p32 ? c->rhat32 : (float*)nullptr, (const int*)sexp, m, S, c->partial);
+              p32 ? c->rhat32 : (float*)nullptr, (const int*)sexp, m, S, c->partial,
+              p32 ? c->d32[0].t : (float*)nullptr,
+              p32 ? (const float*)c->d32[0].dinv : (const float*)nullptr, (const float*)c->prm32);
     if ((int64_t)S * nchunk <= kMergeReduceMax) {
       is.launch(mgk::k_reduce_check, dim3(1), dim3(kThreads), 0, (const double*)c->partial, nchunk,
                 rsum, p32 ? sexp_prev : (int*)nullptr, (const double*)fsum, S,
@@ -316,6 +318,7 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
     int nk = 0;
     if (p32) {
       Issue<float> is{c, v32, c->prm32, cs, 1};
+      is.delta0_ready = true;  // check's k_blk_resid64 wrote the first step's delta
       is.vcycle(c->rhat32, c->c32, true);
       is.launch(mgk::k_blk_refine_update, bgrid, dim3(kThreads), 0, u,
                 (const float*)c->c32, (const int*)sexp_prev, (const int*)active, m, S, iters);

@@ -280,6 +280,38 @@ def test_stacked_two_rows_are_bitwise_neutral(prec):
         assert torch.equal(u1, u0) and np.array_equal(i1, i0)
 
 
+def test_stacked_refinement_replays_bitwise():
+    """The stacked FP32 refinement loop (the cycle over all blocks, u += 2^s_b
+    c, the per-block FP64 residual with the next cycle's scaled residual and
+    first smoothing delta, the per-block test) equals, bitwise, a host
+    replay through entry points that fold nothing: r = f - A u in FP64,
+    s_b = ilogb ||r_b||, one FP32 cycle of the stack on float(2^-s_b r_b)
+    from zero, u_b += 2^s_b c_b."""
+    N = 65
+    sys_list = systems(N, ["lognormal", "checker", "poisson"], seed=11)
+    S = SquareBatch(N, 3, rand_params(levels_for(N), 5, 0.1), precision=32)
+    fill(S, sys_list)
+    m = S.m
+    f = t64(np.concatenate([x[1] for x in sys_list]))
+    K = 4
+    u = torch.zeros_like(f)
+    r = torch.empty_like(f)
+    for _ in range(K):
+        S.level_apply(0, "outer_residual", f, u, r)
+        rn = np.sqrt((r.cpu().numpy().reshape(3, m) ** 2).sum(axis=1))
+        sexp = np.frexp(rn)[1] - 1  # ilogb per block
+        scale = torch.tensor(np.repeat(np.ldexp(1.0, -sexp), m), dtype=torch.float64, device=DEV)
+        rhat = (r * scale).float()
+        c = torch.zeros_like(rhat)
+        S.vcycle(rhat, c)
+        u = u + c.double() / scale
+    us = torch.zeros_like(f)
+    info = S.solve(f, us, tol=1e-300, max_iter=K)
+    assert np.array_equal(info.iters, np.full(3, K))
+    assert torch.equal(us, u), (us - u).abs().max().item()
+    S.close()
+
+
 def test_invalid_square_arguments():
     from paper_2608_29082_b300._lib import MGError
     with pytest.raises(MGError):
