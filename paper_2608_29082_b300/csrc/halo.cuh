@@ -28,13 +28,22 @@
 
 namespace mgk {
 
-enum { HALO_SMOOTH = 0, HALO_RESTRICT = 1, HALO_PROLONG = 2 };
+// HALO_SMOOTH_GATHER: the first smoothing step of a level that starts from
+// zero, with the level's right-hand side gathered in the first stage from
+// the finer level's Phi_R values (f_j = (P^T phi)_j, gather_el's arithmetic,
+// for the tile's rows and halo; written to fout for the tile's own rows), so
+// the restriction's separate gather launch is not needed.
+enum { HALO_SMOOTH = 0, HALO_RESTRICT = 1, HALO_PROLONG = 2, HALO_SMOOTH_GATHER = 3 };
 
 // kB = 1: one right-hand side known at compile time; kB = 0: B of them.
+// Lf, phi, fout: the finer level, its Phi_R values and this level's
+// right-hand side (HALO_SMOOTH_GATHER only).
 template <class T, int MODE, int kB>
 __global__ void __launch_bounds__(kTailThreads)
     k_halo_dia(LV<T> L, const T* __restrict__ f, const T* __restrict__ x, T* y, int B_,
-               const T* __restrict__ prm, int TR, int H, int zero) {
+               const T* __restrict__ prm, int TR, int H, int zero, LV<T> Lf,
+               const T* __restrict__ phi, T* __restrict__ fout) {
+  constexpr bool kSmooth = MODE == HALO_SMOOTH || MODE == HALO_SMOOTH_GATHER;
   const int B = kB ? kB : B_;
   extern __shared__ __align__(16) unsigned char halo_raw[];
   T* sz = reinterpret_cast<T*>(halo_raw);
@@ -46,6 +55,7 @@ __global__ void __launch_bounds__(kTailThreads)
   // read-only operator rows of the tile before waiting for the predecessor
   for (int j = lo + (int)threadIdx.x; j < hi; j += blockDim.x) {
     if constexpr (MODE == HALO_PROLONG) prefetch_p(L, j);
+    if constexpr (MODE == HALO_SMOOTH_GATHER) prefetch_r(Lf, j);
     prefetch_row(L, j);
   }
   pdl_wait();
@@ -55,7 +65,8 @@ __global__ void __launch_bounds__(kTailThreads)
   // neighbour bits, 1/deg and the value it updates), loaded before the
   // barrier so that they travel with the first stage's loads instead of
   // costing a second memory round trip after it.
-  const size_t e0 = (size_t)(r0 - lo) * B + threadIdx.x;
+  const size_t eo = (size_t)(r0 - lo) * B;  // the tile's own rows: [eo, e1)
+  const size_t e0 = eo + threadIdx.x;
   const size_t e1 = (size_t)(r1 - lo) * B;
   unsigned m0 = 0;
   T id0 = T(0), v0 = T(0);
@@ -77,6 +88,10 @@ __global__ void __launch_bounds__(kTailThreads)
     T z;
     if constexpr (MODE == HALO_PROLONG) {
       z = prolong_at(L, j, x, B, b);
+    } else if constexpr (MODE == HALO_SMOOTH_GATHER) {  // from zero: delta = theta dinv f
+      const T fj = gather_at(Lf, phi, B, j, b);
+      if (e >= eo && e < e1) fout[t] = fj;
+      z = prm[P_THETA] * (fj * L.dinv[j]);
     } else {
       z = f[t];
       if (!zero) {
@@ -108,18 +123,18 @@ __global__ void __launch_bounds__(kTailThreads)
         s += ((m >> k) & 1u) ? zv : T(0);
       }
     }
-    if constexpr (MODE == HALO_SMOOTH) {
-      const T phi = fma(prm[P_WB1], sz[e], prm[P_WB2] * (id * s));
-      const T u0 = first ? v0 : (zero ? T(0) : x[t]);
-      y[t] = fma(prm[P_ETA], phi, u0);
+    if constexpr (kSmooth) {
+      const T ph = fma(prm[P_WB1], sz[e], prm[P_WB2] * (id * s));
+      const T u0 = MODE == HALO_SMOOTH_GATHER ? T(0) : (first ? v0 : (zero ? T(0) : x[t]));
+      y[t] = fma(prm[P_ETA], ph, u0);
     } else if constexpr (MODE == HALO_RESTRICT) {
       T p = prm[P_WR1] * sz[e];
       p = fma(prm[P_WR2], id * s, p);
       y[t] = p;
     } else {
-      T phi = prm[P_WP1] * sz[e];
-      phi = fma(prm[P_WP2], id * s, phi);
-      y[t] = (first ? v0 : y[t]) + phi;
+      T ph = prm[P_WP1] * sz[e];
+      ph = fma(prm[P_WP2], id * s, ph);
+      y[t] = (first ? v0 : y[t]) + ph;
     }
   }
 }

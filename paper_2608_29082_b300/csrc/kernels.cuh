@@ -406,10 +406,8 @@ __device__ __forceinline__ void conv_r_el(const LV<T>& L, const T* __restrict__ 
 
 // fc_I = sum_{i in children(I)} P_iI phi_i   (coarse rows)
 template <class T>
-__device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ phi,
-                                          T* __restrict__ fc, int B, size_t t) {
-  int I, b;
-  split_rb(t, B, I, b);
+__device__ __forceinline__ T gather_at(const LV<T>& L, const T* __restrict__ phi, int B, int I,
+                                       int b) {
   T acc = T(0);
   if (L.KR <= kMaxKR) {
     int idx[kMaxKR];
@@ -429,7 +427,15 @@ __device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ 
       acc = fma(L.r_w[(size_t)k * L.ldc + I], phi[(size_t)i * B + b], acc);
     }
   }
-  fc[t] = acc;
+  return acc;
+}
+
+template <class T>
+__device__ __forceinline__ void gather_el(const LV<T>& L, const T* __restrict__ phi,
+                                          T* __restrict__ fc, int B, size_t t) {
+  int I, b;
+  split_rb(t, B, I, b);
+  fc[t] = gather_at(L, phi, B, I, b);
 }
 
 // pe_i = (P ec)_i   (fine rows)

@@ -929,14 +929,28 @@ struct Issue {
              D.halo(), f, x, y, B, P(lev), zero);
     }
   }
+  // fine, phi, fout: HALO_SMOOTH_GATHER's finer level, its Phi_R values and
+  // this level's right-hand side (the level itself and NULLs otherwise).
   template <int MODE>
   void op_halo(int lev, int TR, int H, size_t smem, int threads, const T* f, const T* x, T* y,
-               int zero) {
+               int zero, int fine = -1, const T* phi = nullptr, T* fout = nullptr) {
     DevLevel<T>& D = L[lev];
     launch(B == 1 ? mgk::k_halo_dia<T, MODE, 1> : mgk::k_halo_dia<T, MODE, 0>,
-           dim3((unsigned)((D.n + TR - 1) / TR)), dim3(threads), smem,
-           D.view(), f, x, y, B, P(lev), TR, H, zero);
+           dim3((unsigned)((D.n + TR - 1) / TR)), dim3(threads), smem, D.view(), f, x, y, B,
+           P(lev), TR, H, zero, L[fine >= 0 ? fine : lev].view(), phi, fout);
   }
+  // The restriction from level lev leaves its gather to the first smoothing
+  // step of level lev + 1 when that step is a 1D halo-fused kernel from zero
+  // (every level of the descent below the cycle's first starts from zero).
+  bool gather_in_next_smooth(int lev) const {
+    const int nxt = lev + 1;
+    if (c->cheb_K > 0 || c->nu_pre < 1 || nxt >= c->J - 1 || nxt >= tail_level()) return false;
+    if (!conv(nxt, mgk::P_WB2)) return false;
+    int H = 0, nth = 0;
+    size_t smem = 0;
+    return halo_rows(nxt, H, smem, nth) > 0;
+  }
+  int pending_gather = -1;  // the level whose gather the next smoothing does (-1: none)
 
   void smooth(int lev, const T* f, T* u, int nu, bool zero) {
     DevLevel<T>& D = L[lev];
@@ -985,7 +999,13 @@ struct Issue {
       T* oth = D.u2;
       for (int k = 0; k < nu; ++k) {
         pre(MG_K_SMOOTH_HALO, lev);
-        op_halo<mgk::HALO_SMOOTH>(lev, TR, H, smem, nth, f, cur, oth, (int)(zero && k == 0));
+        if (k == 0 && zero && lev > 0 && pending_gather == lev - 1) {  // f gathered here
+          op_halo<mgk::HALO_SMOOTH_GATHER>(lev, TR, H, smem, nth, f, cur, oth, 1, lev - 1,
+                                           L[lev - 1].u2, (T*)f);
+          pending_gather = -1;
+        } else {
+          op_halo<mgk::HALO_SMOOTH>(lev, TR, H, smem, nth, f, cur, oth, (int)(zero && k == 0));
+        }
         post();
         std::swap(cur, oth);
       }
@@ -1030,6 +1050,18 @@ struct Issue {
     }
   }
 
+  // f_{lev+1} = P^T phi with phi = Phi_R(r) in L[lev].u2: now, or in the
+  // first smoothing step of level lev + 1 (gather_in_next_smooth).
+  void gather_phi(int lev) {
+    if (gather_in_next_smooth(lev)) {
+      pending_gather = lev;
+      return;
+    }
+    pre(MG_K_RESTRICT, lev);
+    op_gather(lev, L[lev].u2, Fl(lev + 1), 0);
+    post();
+  }
+
   void restrict_(int lev, const T* f, const T* u) {
     DevLevel<T>& D = L[lev];
     int H = 0, nth = 0;
@@ -1039,9 +1071,7 @@ struct Issue {
       pre(MG_K_RESTRICT_HALO, lev);
       op_halo<mgk::HALO_RESTRICT>(lev, TR, H, smem, nth, f, u, D.u2, 0);
       post();
-      pre(MG_K_RESTRICT, lev);
-      op_gather(lev, D.u2, Fl(lev + 1), 0);
-      post();
+      gather_phi(lev);
       return;
     }
     Halo2 h2;
@@ -1049,9 +1079,7 @@ struct Issue {
       pre(MG_K_RESTRICT_HALO, lev);
       op_halo2<mgk::HALO_RESTRICT>(lev, h2, f, u, D.u2, 0);
       post();
-      pre(MG_K_RESTRICT, lev);
-      op_gather(lev, D.u2, Fl(lev + 1), 0);
-      post();
+      gather_phi(lev);
       return;
     }
     if (conv(lev, mgk::P_WR2)) {
@@ -1059,9 +1087,7 @@ struct Issue {
         pre(MG_K_RESTRICT_HALO, lev);
         op_halo_sell<mgk::HALO_RESTRICT>(lev, hsm, f, u, D.u2, 0);
         post();
-        pre(MG_K_RESTRICT, lev);
-        op_gather(lev, D.u2, Fl(lev + 1), 0);
-        post();
+        gather_phi(lev);
         return;
       }
     }
@@ -1072,9 +1098,7 @@ struct Issue {
       pre(MG_K_CONV_R, lev);
       op_conv_r(lev, D.t, D.u2);
       post();
-      pre(MG_K_RESTRICT, lev);
-      op_gather(lev, D.u2, Fl(lev + 1), 0);
-      post();
+      gather_phi(lev);
     } else {
       pre(MG_K_RESTRICT, lev);
       op_gather(lev, D.t, Fl(lev + 1), 1);
