@@ -108,6 +108,20 @@ __device__ __forceinline__ void split_rb(size_t t, int B, int& i, int& b) {
   }
 }
 
+// ldexp out of line: a call is never evaluated speculatively, so the FP64
+// arithmetic of its special cases stays off the common path of scale2.
+__device__ __noinline__ double ldexp_rare(double x, int e) { return ldexp(x, e); }
+
+// x * 2^e.  For -1022 <= e <= 1023, 2^e is a normal binary64 number (biased
+// exponent e + 1023, zero fraction), so one multiply gives the exact scaled
+// value, rounded once if it is subnormal: bitwise what ldexp returns, without
+// ldexp's FP64 special-case arithmetic (B300's FP64 pipe is narrow).  Other e
+// go through ldexp.
+__device__ __forceinline__ double scale2(double x, int e) {
+  if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp_rare(x, e);
+}
+
 __device__ __forceinline__ int slice_begin(const int* sl_ptr, int i) {
   return sl_ptr[i >> 5] + (i & 31);
 }
@@ -690,7 +704,20 @@ __global__ void __launch_bounds__(kThreads)
   pdl_launch();
 }
 
-enum { MEAN_CONV_UPDATE = 0, MEAN_CONV_R = 1, MEAN_PROLONG_CONV = 2 };
+enum { MEAN_CONV_UPDATE = 0, MEAN_CONV_R = 1, MEAN_PROLONG_CONV = 2, MEAN_CONV_UPDATE_REFINE = 3 };
+
+// The refinement update u += 2^sexp_b c of an FP32 cycle's result c, for
+// blocks of m rows (m = n: one system; the stacked contexts' slots
+// otherwise), applied by the cycle's last level-0 kernel to the rows it
+// writes (MEAN_CONV_UPDATE_REFINE): the arithmetic of k_refine_update and
+// k_blk_refine_update, which it replaces.
+struct RefineEp {
+  double* u;
+  const int* sexp;
+  const int* active;
+  int* iters;
+  int m;
+};
 
 // The mean-only steps: CONV_UPDATE u = u0 + eta (wB1 x + wB2 mean x) (u0 =
 // 0 when u_zero); CONV_R y = wR1 x + wR2 mean x; PROLONG_CONV u = uin + wP1 x
@@ -698,7 +725,7 @@ enum { MEAN_CONV_UPDATE = 0, MEAN_CONV_R = 1, MEAN_PROLONG_CONV = 2 };
 template <class T, int MODE>
 __global__ void __launch_bounds__(kThreads)
     k_mean_dia2r(LV<T> L, const T* __restrict__ x, const T* uin, T* y,
-                 const T* __restrict__ prm, int u_zero) {
+                 const T* __restrict__ prm, int u_zero, RefineEp ep) {
   const int i0 = 2 * (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (i0 < L.n && blockIdx.x < kPrefetchBlocks) prefetch_mean(L, i0);
   pdl_wait();
@@ -719,13 +746,25 @@ __global__ void __launch_bounds__(kThreads)
     }
   }
   const T d0 = L.invdeg[i0], d1 = L.invdeg[i1];
-  if constexpr (MODE == MEAN_CONV_UPDATE) {
+  if constexpr (MODE == MEAN_CONV_UPDATE || MODE == MEAN_CONV_UPDATE_REFINE) {
     const T p0 = fma(prm[P_WB1], x[i0], prm[P_WB2] * (d0 * s0));
     const T p1 = fma(prm[P_WB1], x[i1], prm[P_WB2] * (d1 * s1));
     const T u0 = u_zero ? T(0) : y[i0];
     const T u1 = u_zero ? T(0) : y[i1];
-    y[i0] = fma(prm[P_ETA], p0, u0);
-    if (two) y[i1] = fma(prm[P_ETA], p1, u1);
+    const T c0 = fma(prm[P_ETA], p0, u0), c1 = fma(prm[P_ETA], p1, u1);
+    y[i0] = c0;
+    if (two) y[i1] = c1;
+    if constexpr (MODE == MEAN_CONV_UPDATE_REFINE) {
+      const int b0 = i0 / ep.m, b1 = i1 / ep.m;
+      if (ep.active[b0]) {
+        ep.u[i0] += scale2((double)c0, ep.sexp[b0]);
+        if (i0 - b0 * ep.m == 0) ep.iters[b0] += 1;
+      }
+      if (two && ep.active[b1]) {
+        ep.u[i1] += scale2((double)c1, ep.sexp[b1]);
+        if (i1 - b1 * ep.m == 0) ep.iters[b1] += 1;
+      }
+    }
   } else if constexpr (MODE == MEAN_CONV_R) {
     T p0 = prm[P_WR1] * x[i0], p1 = prm[P_WR1] * x[i1];
     p0 = fma(prm[P_WR2], d0 * s0, p0);
@@ -1284,20 +1323,6 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
 
 constexpr int kRedRows = 32;
 constexpr int kRedMax = 1024;  // kRedRows x 32 columns
-
-// ldexp out of line: a call is never evaluated speculatively, so the FP64
-// arithmetic of its special cases stays off the common path of scale2.
-__device__ __noinline__ double ldexp_rare(double x, int e) { return ldexp(x, e); }
-
-// x * 2^e.  For -1022 <= e <= 1023, 2^e is a normal binary64 number (biased
-// exponent e + 1023, zero fraction), so one multiply gives the exact scaled
-// value, rounded once if it is subnormal: bitwise what ldexp returns, without
-// ldexp's FP64 special-case arithmetic (B300's FP64 pipe is narrow).  Other e
-// go through ldexp.
-__device__ __forceinline__ double scale2(double x, int e) {
-  if (e >= -1022 && e <= 1023) return x * __longlong_as_double((long long)(e + 1023) << 52);
-  return ldexp_rare(x, e);
-}
 
 // (row, rhs) of this thread in the reduction tiling.
 __device__ __forceinline__ void red_tile(int n, int B, int& i, int& b, bool& ok) {

@@ -618,6 +618,11 @@ struct Issue {
   // level 0's first smoothing step from zero has its delta in L[0].t already
   // (written by k_resid64 with the scaled residual): skip its launch
   bool delta0_ready = false;
+  // rfold.u set: level 0's last smoothing step also applies the refinement
+  // update (MEAN_CONV_UPDATE_REFINE) when it is the two-row kernel; then
+  // rfold_done tells the caller to skip its own update launch
+  mgk::RefineEp rfold{};
+  bool rfold_done = false;
   // optional per-kernel timing: an event pair around every launch
   std::vector<std::tuple<int, int, cudaEvent_t, cudaEvent_t>>* rec = nullptr;
 
@@ -721,7 +726,7 @@ struct Issue {
     DevLevel<T>& D = L[lev];
     if (two_rows(D)) {
       launch(mgk::k_mean_dia2r<T, mgk::MEAN_CONV_UPDATE>, two_row_grid(D.n), kThreads, 0,
-             D.view(), x, (const T*)nullptr, u, P(lev), zero);
+             D.view(), x, (const T*)nullptr, u, P(lev), zero, mgk::RefineEp{});
     } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_conv_update_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
@@ -761,7 +766,7 @@ struct Issue {
     DevLevel<T>& D = L[lev];
     if (two_rows(D)) {
       launch(mgk::k_mean_dia2r<T, mgk::MEAN_CONV_R>, two_row_grid(D.n), kThreads, 0, D.view(), r,
-             (const T*)nullptr, phi, P(lev), 0);
+             (const T*)nullptr, phi, P(lev), 0, mgk::RefineEp{});
     } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_conv_r_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0, D.view(),
@@ -805,7 +810,7 @@ struct Issue {
     DevLevel<T>& D = L[lev];
     if (conv_p && two_rows(D)) {
       launch(mgk::k_mean_dia2r<T, mgk::MEAN_PROLONG_CONV>, two_row_grid(D.n), kThreads, 0,
-             D.view(), x, uin, u, P(lev), 0);
+             D.view(), x, uin, u, P(lev), 0, mgk::RefineEp{});
     } else if (const int bv = mbv()) {
       with_bv(bv, [&](auto k) {
         launch(mgk::k_prolong_mb<T, decltype(k)::value>, mb_grid(D.n, bv), kThreads, 0,
@@ -1045,7 +1050,13 @@ struct Issue {
         post();
       }
       pre(MG_K_CONV_UPDATE, lev);
-      op_conv_update(lev, D.t, u, z);
+      if (k == nu - 1 && lev == 0 && !zero && rfold.u && two_rows(D)) {
+        launch(mgk::k_mean_dia2r<T, mgk::MEAN_CONV_UPDATE_REFINE>, two_row_grid(D.n), kThreads,
+               0, D.view(), (const T*)D.t, (const T*)nullptr, u, P(lev), 0, rfold);
+        rfold_done = true;
+      } else {
+        op_conv_update(lev, D.t, u, z);
+      }
       post();
     }
   }
@@ -2002,10 +2013,12 @@ extern "C" mg_status mg_solve(mg_ctx* c, const double* f, double* u, int32_t B, 
     if (p32) {
       Issue<float> is{c, c->d32, c->prm32, cs, B};
       is.delta0_ready = true;  // check_tail's k_resid64 wrote the first step's delta
+      if (B == 1) is.rfold = mgk::RefineEp{u, c->sexp_prev, c->active, c->iters, n0};
       is.vcycle(c->rhat32, c->c32, true);
-      is.launch(mgk::k_refine_update, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
-                (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0, (int)B,
-                c->iters);
+      if (!is.rfold_done)
+        is.launch(mgk::k_refine_update, grid_for((size_t)n0 * B), dim3(kThreads), 0, u,
+                  (const float*)c->c32, (const int*)c->sexp_prev, (const int*)c->active, n0,
+                  (int)B, c->iters);
       nk += is.nk;
       Issue<double> is2{c, c->d64, c->prm64, cs, B};
       check_tail(is2, h, 1, cond);

@@ -319,9 +319,11 @@ extern "C" mg_status mg_solve_blocks(mg_ctx* c, int32_t nblocks, const double* f
     if (p32) {
       Issue<float> is{c, v32, c->prm32, cs, 1};
       is.delta0_ready = true;  // check's k_blk_resid64 wrote the first step's delta
+      is.rfold = mgk::RefineEp{u, sexp_prev, active, iters, m};
       is.vcycle(c->rhat32, c->c32, true);
-      is.launch(mgk::k_blk_refine_update, bgrid, dim3(kThreads), 0, u,
-                (const float*)c->c32, (const int*)sexp_prev, (const int*)active, m, S, iters);
+      if (!is.rfold_done)
+        is.launch(mgk::k_blk_refine_update, bgrid, dim3(kThreads), 0, u,
+                  (const float*)c->c32, (const int*)sexp_prev, (const int*)active, m, S, iters);
       nk += is.nk;
       Issue<double> is2{c, v64, c->prm64, cs, 1};
       check(is2, h, 1, cond);
