@@ -310,7 +310,7 @@ mg_status mg_level_apply(mg_ctx* ctx, int32_t level, int32_t op, const void* x, 
  *                     a power of two, no larger than the finer level's), whose
  *                     steps are separated by barriers among those W warps
  *                     (a named barrier, or a warp sync for one warp) instead
- *                     of all 1024 threads; 0: every level on the whole block;
+ *                     of all 512 threads; 0: every level on the whole block;
  *                     at most 64
  *   MG_OPT_PDL        1 (default): consecutive kernels use programmatic
  *                     dependent launch; 0: plain stream order

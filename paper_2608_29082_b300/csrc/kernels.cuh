@@ -52,6 +52,13 @@ constexpr int kThreads = 256;
 constexpr int kSlice = 32;
 constexpr int kMaxLevels = 16;
 constexpr int kTailThreads = 1024;
+// The small-levels block (k_tail): 512 threads, so that each level's view
+// (offsets, sizes, array pointers) stays in registers across its steps'
+// barriers (up to 128 registers per thread; at 1024 threads the 64-register
+// limit spilled them, and re-reading them from shared memory after every
+// barrier put those loads on each step's dependent chain: 41 against 33 us
+// per 513^2 cycle).
+constexpr int kTailBlock = 512;
 
 // Parameter block per level, in the order used everywhere:
 // theta, eta, wB1, wB2, wR1, wR2, wP1, wP2.
@@ -840,10 +847,10 @@ struct TailArgs {
 // The threads that run one small level of k_tail: the first W warps of the
 // block.  A level's steps are separated by a barrier among exactly those
 // threads: __syncthreads for the whole block, the named barrier log2(W)
-// (bar.sync with W * 32 threads) for 2..16 warps, __syncwarp for one warp.
+// (bar.sync with W * 32 threads) for 2..8 warps, __syncwarp for one warp.
 // Coarser levels have no more warps than finer ones, so a level's team
 // contains the teams of all coarser levels; a level small enough for a few
-// warps thus pays for cheap barriers instead of a barrier of 1024 threads.
+// warps thus pays for cheap barriers instead of a barrier of the whole block.
 // Which thread computes an entry never changes its value.
 struct Team {
   int W;
@@ -1081,7 +1088,7 @@ template <class T>
 __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* Ls,
                                             const T* prm_all, const TailVecs<T>& v, int l, int nu,
                                             bool zero, const Team& tm, int B) {
-  const LV<T>& L = Ls[l];
+  const LV<T> L = Ls[l];  // in registers across the steps' barriers
   const size_t N = (size_t)L.n * B;
   const T* prm = prm_all + (size_t)l * P_COUNT;
   const size_t t0 = threadIdx.x, dt = tm.size();
@@ -1121,7 +1128,7 @@ __device__ __forceinline__ void tail_smooth(const TailArgs<T>& a, const LV<T>* L
 // kB = 1: one right-hand side, known at compile time (the index arithmetic
 // of every step folds); kB = 0: B right-hand sides.
 template <class T, int kB>
-__global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ TailArgs<T> a) {
+__global__ void __launch_bounds__(kTailBlock, 1) k_tail(const __grid_constant__ TailArgs<T> a) {
   extern __shared__ __align__(16) unsigned char tail_smem[];
   // The arguments, the staged level views and the vector pointers live in
   // shared memory, one copy per block.  Levels are indexed at run time: as
@@ -1250,7 +1257,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
   for (int l = lt; l < J - 1; ++l) {
     const Team tm{sa.tw[l]};
     if (!tm.member()) break;
-    const LV<T>& L = sL[l];
+    const LV<T> L = sL[l];
     const T* prm = prm_all + (size_t)l * P_COUNT;
     const size_t t0 = threadIdx.x, dt = tm.size();
     tail_smooth(a, sL, prm_all, v, l, a.nu_pre, l == lt ? (a.lt_zero != 0) : true, tm, B);
@@ -1286,7 +1293,7 @@ __global__ void __launch_bounds__(kTailThreads) k_tail(const __grid_constant__ T
     const Team tm{sa.tw[l]};
     if (!tm.member()) continue;
     tm.sync();
-    const LV<T>& L = sL[l];
+    const LV<T> L = sL[l];
     const T* prm = prm_all + (size_t)l * P_COUNT;
     const size_t t0 = threadIdx.x, dt = tm.size();
     const size_t N = (size_t)L.n * B;

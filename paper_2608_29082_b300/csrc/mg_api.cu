@@ -1235,14 +1235,14 @@ struct Issue {
     // the team of a small level: about opt_tail_teams entries (row, rhs) per
     // thread, a power of two of warps, never more warps than the finer
     // level's team
-    int prev = 32;
+    int prev = mgk::kTailBlock / 32;
     for (int l = 0; l < mgk::kMaxLevels; ++l) {
-      int w = 32;
+      int w = mgk::kTailBlock / 32;
       if (c->opt_tail_teams > 0 && l < c->J) {
         const int64_t per_warp = 32 * (int64_t)c->opt_tail_teams;
         const int64_t need = ((int64_t)L[l].n * B + per_warp - 1) / per_warp;
         w = 1;
-        while (w < 32 && w < need) w *= 2;
+        while (w < mgk::kTailBlock / 32 && w < need) w *= 2;
       }
       a.tw[l] = std::min(w, prev);
       prev = a.tw[l];
@@ -1273,7 +1273,7 @@ struct Issue {
     a.lt = lt;
     if (lt > l0) a.lt_zero = 1;  // levels below the cycle's first start from zero
     pre(MG_K_TAIL, lt);
-    launch(a.B == 1 ? mgk::k_tail<T, 1> : mgk::k_tail<T, 0>, dim3(1), dim3(mgk::kTailThreads),
+    launch(a.B == 1 ? mgk::k_tail<T, 1> : mgk::k_tail<T, 0>, dim3(1), dim3(mgk::kTailBlock),
            mgk::tail_smem_bytes<T>(a, lt), a);
     post();
   }
