@@ -138,7 +138,7 @@ class ClockSampler:
 # names, with the profiles/ summary it comes from.  A kernel changed since
 # its capture must lose its entry (traffic is then reported as null).
 NCU_TRAFFIC = {
-    "small_levels_block@level4": (197888, "profiles/k_tail_f32_checker513.md"),
+    "small_levels_block@level4": (199424, "profiles/k_tail_f32_checker513.md"),
     "lshape:residual_scaled@level0": (770925824, "profiles/k_residual_mb_f32_lshape.md"),
 }
 
