@@ -500,6 +500,12 @@ def run_stacked(a):
     operator per slot, set up on the device): the per-kernel table of an
     eager FP32 cycle, the graph-replayed cycle and optionally one solve of
     every slot to 1e-8."""
+    print(json.dumps(stacked_report(a)), flush=True)
+
+
+def stacked_report(a) -> dict:
+    """run_stacked's measurements as a dict (fields of a: N, slots, cycles,
+    solve, two_rows, halo2d_bytes, host_loop, seed)."""
     from . import serve, trained
     from .square import SquareBatch
     N, S = a.N, a.slots
@@ -560,7 +566,8 @@ def run_stacked(a):
         torch.cuda.synchronize()
         out["solve_ms"] = round(e0.elapsed_time(e1), 3)
         out["solve_iters_max"] = int(info.iters.max())
-    print(json.dumps(out), flush=True)
+    sb.close()
+    return out
 
 if __name__ == "__main__":
     ap = argparse.ArgumentParser()
