@@ -15,6 +15,7 @@
 // overlap on the GPU (different streams, or different host threads on the
 // same device) race on it.
 #include <cmath>
+#include <cstdint>
 #include <mutex>
 #include <string>
 
@@ -85,8 +86,14 @@ extern "C" mg_status mg_smooth_noalloc(int32_t n, const int32_t* rowptr, const i
         MG_ERR_INVALID, "mg_smooth_noalloc: n * nrhs = " + std::to_string((long long)n * nrhs) +
                             " exceeds the static scratch of " +
                             std::to_string(MG_NOALLOC_MAX_ELEMS) + " doubles");
-  if ((const void*)f == (const void*)u)
-    return mgi::set_global_error(MG_ERR_INVALID, "mg_smooth_noalloc: f and u must not alias");
+  {
+    // f and u are [n][nrhs] doubles each: the byte ranges must be disjoint
+    // (u is written while other threads still read f).
+    const uintptr_t fb = (uintptr_t)f, ub = (uintptr_t)u;
+    const uintptr_t len = (uintptr_t)n * (uintptr_t)nrhs * sizeof(double);
+    if (fb < ub + len && ub < fb + len)
+      return mgi::set_global_error(MG_ERR_INVALID, "mg_smooth_noalloc: f and u overlap");
+  }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64)

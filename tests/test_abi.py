@@ -61,6 +61,22 @@ def test_invalid_arguments_are_rejected_without_gpu():
     assert "parent" in L.last_error()
 
 
+def test_noalloc_rejects_overlapping_f_and_u_without_gpu():
+    """mg_smooth_noalloc checks its arguments before any CUDA call: f and u
+    whose [n][nrhs] ranges overlap (equal or shifted by less than their
+    length) are rejected, so these stand-in addresses are never used."""
+    lib = L.lib()
+    base = 1 << 40
+    n, nrhs = 100, 2
+    nbytes = n * nrhs * 8
+    fake = C.c_void_p(base)
+    for shift in (0, 8, nbytes - 8, -8, -(nbytes - 8)):
+        st = lib.mg_smooth_noalloc(n, fake, fake, fake, fake, C.c_void_p(base),
+                                   C.c_void_p(base + shift), nrhs, 1, 1.0, 1.0, 1.0, 0.0, None)
+        assert st == -1, shift
+        assert "overlap" in L.last_error()
+
+
 def test_galerkin_helper_small():
     """1D P1 hat functions: P^T A P of the 3-point Laplacian over all vertices."""
     n = 5
