@@ -139,7 +139,7 @@ class ClockSampler:
 # its capture must lose its entry (traffic is then reported as null).
 NCU_TRAFFIC = {
     "small_levels_block@level4": (199424, "profiles/k_tail_f32_checker513.md"),
-    "lshape:residual_scaled@level0": (758887936, "profiles/k_residual_mb_f32_lshape.md"),
+    "lshape:residual_scaled@level0": (758912256, "profiles/k_residual_mb_f32_lshape.md"),
     "stacked:residual_scaled@level0": (295554304,
                                        "profiles/k_residual_dia2r_k_mean_dia2r_f32_stacked1025.md"),
 }
