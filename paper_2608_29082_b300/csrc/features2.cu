@@ -59,13 +59,15 @@ __device__ __forceinline__ void pdl_launch() { asm volatile("griddepcontrol.laun
 
 // BV consecutive complex values x[off .. off+BV) (Pair<T> = (Re, Im)): one
 // 32-byte access where BV pairs are 32 bytes and the address is 32-byte
-// aligned (ld.global.v8.b32), else pair by pair.
-template <class T, int BV>
+// aligned (ld.global.v8.b32), else pair by pair.  kA: -1 tests each
+// address; 1 or 0 is a launch-wide answer (pairs_aligned), so an access
+// carries no alignment branch.
+template <class T, int BV, int kA = -1>
 __device__ __forceinline__ void ld_pairs(const typename Pair<T>::type* __restrict__ x, size_t off,
                                          typename Pair<T>::type (&out)[BV]) {
   const typename Pair<T>::type* p = x + off;
-  if constexpr (BV * sizeof(typename Pair<T>::type) == 32) {
-    if (((uintptr_t)p & 31) == 0) {
+  if constexpr (BV * sizeof(typename Pair<T>::type) == 32 && kA != 0) {
+    if (kA == 1 || ((uintptr_t)p & 31) == 0) {
       uint32_t w[8];
       asm("ld.global.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
           : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]), "=r"(w[6]),
@@ -79,12 +81,12 @@ __device__ __forceinline__ void ld_pairs(const typename Pair<T>::type* __restric
   for (int j = 0; j < BV; ++j) out[j] = p[j];
 }
 
-template <class T, int BV>
+template <class T, int BV, int kA = -1>
 __device__ __forceinline__ void st_pairs(typename Pair<T>::type* __restrict__ x, size_t off,
                                          const typename Pair<T>::type (&in)[BV]) {
   typename Pair<T>::type* p = x + off;
-  if constexpr (BV * sizeof(typename Pair<T>::type) == 32) {
-    if (((uintptr_t)p & 31) == 0) {
+  if constexpr (BV * sizeof(typename Pair<T>::type) == 32 && kA != 0) {
+    if (kA == 1 || ((uintptr_t)p & 31) == 0) {
       uint32_t w[8];
       memcpy(w, in, 32);
       asm volatile("st.global.v8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "r"(w[0]),
@@ -113,13 +115,34 @@ __device__ __forceinline__ void st_pairs(typename Pair<T>::type* __restrict__ x,
   if (i >= (NROWS)) return;                               \
   const int b0 = (g - i * nq) * BV;
 
+// Whether every [n][B] complex access of a launch is 32-byte aligned (the
+// vectors' bases and the row pitch B * sizeof(pair); a thread's column
+// offset is a multiple of the 32-byte tile).  The grid kernels run their
+// element step with that launch-wide answer in FP32 (the form measured on
+// the real-valued path's multi-rhs kernels) and with a test per access in
+// FP64.
+template <class T>
+__device__ __forceinline__ bool pairs_aligned(int B, const void* a, const void* b,
+                                              const void* c = nullptr) {
+  return ((size_t)B * sizeof(typename Pair<T>::type)) % 32 == 0 &&
+         ((((uintptr_t)a) | ((uintptr_t)b) | ((uintptr_t)c)) & 31) == 0;
+}
+#define MG2_DISPATCH(AL, CALL)          \
+  if constexpr (sizeof(T) != 4) {       \
+    CALL(-1);                           \
+  } else if (AL) {                      \
+    CALL(1);                            \
+  } else {                              \
+    CALL(0);                            \
+  }
+
 // ---- element steps: row i, right-hand sides b0 .. b0 + BV - 1 ----------
 // (the grid kernels below and the single-block small-levels kernel k2_tail
 // run the same functions, so every launch form rounds alike)
 
 // out = f - A u (u_zero: u = 0), then optionally out = theta * out / A_ii
 // (dinv = 1 / A_ii, complex)
-template <class T, int BV>
+template <class T, int BV, int kA = -1>
 __device__ __forceinline__ void res2_el(int i, int b0, const int* __restrict__ rp,
                                         const int* __restrict__ ci,
                                         const typename Pair<T>::type* __restrict__ av,
@@ -131,12 +154,12 @@ __device__ __forceinline__ void res2_el(int i, int b0, const int* __restrict__ r
   using P2 = typename Pair<T>::type;
   const size_t base = (size_t)i * B + b0;
   P2 r[BV];
-  ld_pairs<T, BV>(f, base, r);
+  ld_pairs<T, BV, kA>(f, base, r);
   if (!u_zero) {
     for (int e = rp[i]; e < rp[i + 1]; ++e) {
       const P2 a = av[e];
       P2 x[BV];
-      ld_pairs<T, BV>(u, (size_t)ci[e] * B + b0, x);
+      ld_pairs<T, BV, kA>(u, (size_t)ci[e] * B + b0, x);
 #pragma unroll
       for (int j = 0; j < BV; ++j) {
         r[j].x -= a.x * x[j].x - a.y * x[j].y;
@@ -153,12 +176,12 @@ __device__ __forceinline__ void res2_el(int i, int b0, const int* __restrict__ r
       r[j].y = theta * im;
     }
   }
-  st_pairs<T, BV>(out, base, r);
+  st_pairs<T, BV, kA>(out, base, r);
 }
 
 // phi_i = W_1 x_i + W_2 inv_deg_i sum_{j != i in row i} x_j; mode 0: y = phi,
 // 1: y += eta phi, 2: y += phi.  x and y are distinct buffers.
-template <class T, int BV>
+template <class T, int BV, int kA = -1>
 __device__ __forceinline__ void conv2_el(int i, int b0, const int* __restrict__ rp,
                                          const int* __restrict__ ci, const T* __restrict__ invdeg,
                                          const typename Pair<T>::type* __restrict__ x,
@@ -173,7 +196,7 @@ __device__ __forceinline__ void conv2_el(int i, int b0, const int* __restrict__ 
     const int c = ci[e];
     if (c == i) continue;
     P2 v[BV];
-    ld_pairs<T, BV>(x, (size_t)c * B + b0, v);
+    ld_pairs<T, BV, kA>(x, (size_t)c * B + b0, v);
 #pragma unroll
     for (int j = 0; j < BV; ++j) {
       sx[j] += v[j].x;
@@ -182,8 +205,8 @@ __device__ __forceinline__ void conv2_el(int i, int b0, const int* __restrict__ 
   }
   const T id = invdeg[i];
   P2 xi[BV], o[BV];
-  ld_pairs<T, BV>(x, base, xi);
-  if (mode != 0) ld_pairs<T, BV>(y, base, o);
+  ld_pairs<T, BV, kA>(x, base, xi);
+  if (mode != 0) ld_pairs<T, BV, kA>(y, base, o);
 #pragma unroll
   for (int j = 0; j < BV; ++j) {
     const T mx = id * sx[j], my = id * sy[j];
@@ -198,11 +221,11 @@ __device__ __forceinline__ void conv2_el(int i, int b0, const int* __restrict__ 
       o[j].y += s * phi.y;
     }
   }
-  st_pairs<T, BV>(y, base, o);
+  st_pairs<T, BV, kA>(y, base, o);
 }
 
 // y = M x for a real CSR matrix M on complex vectors
-template <class T, int BV>
+template <class T, int BV, int kA = -1>
 __device__ __forceinline__ void spmv2_el(int i, int b0, const int* __restrict__ rp,
                                          const int* __restrict__ ci, const T* __restrict__ mv,
                                          const typename Pair<T>::type* __restrict__ x,
@@ -214,14 +237,14 @@ __device__ __forceinline__ void spmv2_el(int i, int b0, const int* __restrict__ 
   for (int e = rp[i]; e < rp[i + 1]; ++e) {
     const T m = mv[e];
     P2 v[BV];
-    ld_pairs<T, BV>(x, (size_t)ci[e] * B + b0, v);
+    ld_pairs<T, BV, kA>(x, (size_t)ci[e] * B + b0, v);
 #pragma unroll
     for (int j = 0; j < BV; ++j) {
       o[j].x += m * v[j].x;
       o[j].y += m * v[j].y;
     }
   }
-  st_pairs<T, BV>(y, (size_t)i * B + b0, o);
+  st_pairs<T, BV, kA>(y, (size_t)i * B + b0, o);
 }
 
 // e = A_J^{-1} r with the dense inverse (row-major, complex) for row i,
@@ -276,7 +299,9 @@ __global__ void __launch_bounds__(kF2Threads)
                 int B, const typename Pair<T>::type* __restrict__ dinv, T theta, int scale,
                 int u_zero) {
   MG2_PROLOGUE(n)
-  res2_el<T, BV>(i, b0, rp, ci, av, f, u, out, B, dinv, theta, scale, u_zero);
+#define MG2_CALL(A) res2_el<T, BV, A>(i, b0, rp, ci, av, f, u, out, B, dinv, theta, scale, u_zero)
+  MG2_DISPATCH(pairs_aligned<T>(B, f, u, out), MG2_CALL)
+#undef MG2_CALL
 }
 
 template <class T, int BV>
@@ -285,7 +310,9 @@ __global__ void __launch_bounds__(kF2Threads)
             const T* __restrict__ invdeg, const typename Pair<T>::type* __restrict__ x,
             typename Pair<T>::type* __restrict__ y, int B, Conv2<T> w, T eta, int mode) {
   MG2_PROLOGUE(n)
-  conv2_el<T, BV>(i, b0, rp, ci, invdeg, x, y, B, w, eta, mode);
+#define MG2_CALL(A) conv2_el<T, BV, A>(i, b0, rp, ci, invdeg, x, y, B, w, eta, mode)
+  MG2_DISPATCH(pairs_aligned<T>(B, x, y), MG2_CALL)
+#undef MG2_CALL
 }
 
 template <class T, int BV>
@@ -294,7 +321,9 @@ __global__ void __launch_bounds__(kF2Threads)
                  const T* __restrict__ mv, const typename Pair<T>::type* __restrict__ x,
                  typename Pair<T>::type* __restrict__ y, int B) {
   MG2_PROLOGUE(n)
-  spmv2_el<T, BV>(i, b0, rp, ci, mv, x, y, B);
+#define MG2_CALL(A) spmv2_el<T, BV, A>(i, b0, rp, ci, mv, x, y, B)
+  MG2_DISPATCH(pairs_aligned<T>(B, x, y), MG2_CALL)
+#undef MG2_CALL
 }
 
 // one warp per (row, tile of BV right-hand sides)
