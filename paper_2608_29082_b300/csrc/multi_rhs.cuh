@@ -126,8 +126,8 @@ __device__ __forceinline__ bool mb_aligned(int B, const void* a, const void* b =
 // for the launch, else with kA = 0 (on the 16-rhs L-shape level 0 the
 // residual, the SAGEConv update, Phi_R and P e_c took 3-5 % less time than
 // with a test per access; the prolongation update, which needs more
-// registers in this form, keeps the test per access).  FP64: kA = -1,
-// the test per access.
+// registers in this form, keeps the test per access, and so does the
+// ChebConv step, not measured).  FP64: kA = -1, the test per access.
 #define MG_MB_DISPATCH(AL, BODY)                 \
   if constexpr (sizeof(T) != 4)                  \
     BODY(std::integral_constant<int, -1>{});     \
@@ -136,8 +136,7 @@ __device__ __forceinline__ bool mb_aligned(int B, const void* a, const void* b =
   else                                           \
     BODY(std::integral_constant<int, 0>{});
 
-// The per-access form, for the kernels that measured no faster with a
-// launch-wide answer.
+// The per-access form, for the kernels not moved to the launch-wide answer.
 #define MG_MB_PER_ACCESS(BODY) BODY(std::integral_constant<int, -1>{});
 
 // Launch: 1-D grid of ceil(NROWS * (B / BV) / kThreads) blocks.  PF: the
@@ -299,8 +298,15 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __r
   MG_MB_PER_ACCESS(body)
 }
 
+// FP32 32-byte tiles of the fused Jacobi step: 64 registers (4 blocks per
+// SM), as in the per-access form; unbounded, the launch-wide form takes 66
+// and loses a block.  Measured with the bound (a small spill): the classical
+// FP32 FCG solve of the 16-rhs L-shape, 282 -> 277 ms.
 template <class T, int BV>
-__global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __restrict__ f,
+constexpr int kJacMinBlocks = sizeof(T) == 4 && BV * sizeof(T) == 32 ? 4 : 1;
+
+template <class T, int BV>
+__global__ void __launch_bounds__(kThreads, kJacMinBlocks<T, BV>) k_jacobi_mb(LV<T> L, const T* __restrict__ f,
                                                         const T* __restrict__ uin,
                                                         T* __restrict__ uout, int B,
                                                         const T* __restrict__ prm, int u_zero) {
@@ -328,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_jacobi_mb(LV<T> L, const T* __rest
     }
     stg<T, BV, kA>(uout, base, r);
   };
-  MG_MB_PER_ACCESS(body)
+  MG_MB_DISPATCH(mb_aligned<T>(B, f, uin, uout), body)
 }
 
 // phi_i = wR1 r_i + wR2 mean_{N(i)} r
