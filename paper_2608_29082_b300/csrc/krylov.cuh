@@ -262,8 +262,12 @@ __global__ void __launch_bounds__(kRedMax) k32_spmv_dots(LV<float> L, const floa
 // values in 32-byte pieces (row_ax_mb) instead of once per column.  Every
 // (row, rhs) value and every per-column sum is computed in the order of
 // k32_spmv_dots, so the results are the same.
+// The rows are read with the launch-wide 32-byte alignment answer of
+// multi_rhs.cuh (mb_aligned).  For BV = 8 eight blocks per SM are asked of
+// the compiler: its former 64 registers (a small spill) instead of 70 and
+// one block fewer; the 16-rhs L-shape FCG solves took 1-2 % less time.
 template <int BV>
-__global__ void __launch_bounds__(kRedRows * 32 / BV) k32_spmv_dots_mb(LV<float> L,
+__global__ void __launch_bounds__(kRedRows * 32 / BV, BV == 8 ? 8 : 1) k32_spmv_dots_mb(LV<float> L,
                                                             const float* __restrict__ p,
                                                             const float* __restrict__ r,
                                                             float* __restrict__ q, int B,
@@ -278,28 +282,35 @@ __global__ void __launch_bounds__(kRedRows * 32 / BV) k32_spmv_dots_mb(LV<float>
   float pq[BV], pr[BV];
 #pragma unroll
   for (int j = 0; j < BV; ++j) pq[j] = pr[j] = 0.0f;
-  if (b0 < B) {
-    const int i0 = blockIdx.x * kF32BlockRows + g;
+  auto body = [&](auto A) {
+    constexpr int kA = decltype(A)::value;
+    if (b0 < B) {
+      const int i0 = blockIdx.x * kF32BlockRows + g;
 #pragma unroll 1
-    for (int k = 0; k < kF32Rows; ++k) {
-      const int i = i0 + kRedRows * k;
-      if (i >= L.n) break;
-      const size_t base = (size_t)i * B + b0;
-      float pv[BV], ax[BV];
-      row_ax_mb<float, BV>(L, i, p, B, b0, ax);
-      ldg<float, BV>(p, base, pv);
-      const float d = L.diag[i];
+      for (int k = 0; k < kF32Rows; ++k) {
+        const int i = i0 + kRedRows * k;
+        if (i >= L.n) break;
+        const size_t base = (size_t)i * B + b0;
+        float pv[BV], ax[BV];
+        row_ax_mb<float, BV, kA>(L, i, p, B, b0, ax);
+        ldg<float, BV, kA>(p, base, pv);
+        const float d = L.diag[i];
 #pragma unroll
-      for (int j = 0; j < BV; ++j) {
-        ax[j] = fmaf(d, pv[j], ax[j]);  // q
-        pq[j] = fmaf(pv[j], ax[j], pq[j]);
+        for (int j = 0; j < BV; ++j) {
+          ax[j] = fmaf(d, pv[j], ax[j]);  // q
+          pq[j] = fmaf(pv[j], ax[j], pq[j]);
+        }
+        stg<float, BV, kA>(q, base, ax);
+        ldg<float, BV, kA>(r, base, ax);  // r, in the registers q no longer needs
+#pragma unroll
+        for (int j = 0; j < BV; ++j) pr[j] = fmaf(pv[j], ax[j], pr[j]);
       }
-      stg<float, BV>(q, base, ax);
-      ldg<float, BV>(r, base, ax);  // r, in the registers q no longer needs
-#pragma unroll
-      for (int j = 0; j < BV; ++j) pr[j] = fmaf(pv[j], ax[j], pr[j]);
     }
-  }
+  };
+  if (mb_aligned<float>(B, p, q, r))
+    body(std::integral_constant<int, 1>{});
+  else
+    body(std::integral_constant<int, 0>{});
   // column c of the block is right-hand side blockIdx.y * bt + c; row g of
   // sh[w] holds row group g's sums (the layout block_rows_reduce32 uses)
 #pragma unroll
