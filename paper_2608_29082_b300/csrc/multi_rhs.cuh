@@ -126,8 +126,8 @@ __device__ __forceinline__ bool mb_aligned(int B, const void* a, const void* b =
 // for the launch, else with kA = 0 (on the 16-rhs L-shape level 0 the
 // residual, the SAGEConv update, Phi_R and P e_c took 3-5 % less time than
 // with a test per access; the prolongation update, which needs more
-// registers in this form, keeps the test per access, and so does the
-// ChebConv step, not measured).  FP64: kA = -1, the test per access.
+// registers in this form, keeps the test per access).  FP64: kA = -1,
+// the test per access.
 #define MG_MB_DISPATCH(AL, BODY)                 \
   if constexpr (sizeof(T) != 4)                  \
     BODY(std::integral_constant<int, -1>{});     \
@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_cheb_step_mb(LV<T> L, const T* __r
     stg<T, BV, kA>(out, base, q);
     stg<T, BV, kA>(u, base, uu);
   };
-  MG_MB_PER_ACCESS(body)
+  MG_MB_DISPATCH(mb_aligned<T>(B, tprev, tpp, out, u), body)
 }
 
 // FP32 32-byte tiles of the fused Jacobi step: 64 registers (4 blocks per
